@@ -1,0 +1,213 @@
+"""FP64 CPU oracle of the upscaled LBM -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously-correct restatement of the paper's method (Li & Brown,
+Section 2.2 Eqs. 2, 6, 13-16; Section 3 Eqs. 17-18) used to check the CUDA
+library. Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline may import it. It shares no code with the CUDA path and the CUDA path
+never calls it.
+
+Functions here are thin ctypes marshalling around ``lbm_oracle.c`` plus a few
+pure-numpy helpers (dense steady-state solve by brute force, analytic profiles
+for the closed-form pins). Parity of every function is pinned by the
+``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB = os.path.join(_HERE, "liblbm_oracle.so")
+
+Q = 9
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the system C compiler (plain -O2, OpenMP).
+
+    ``LBM_ORACLE_LIB`` names a prebuilt oracle library to load instead (the
+    mutation tests point it at copies with planted mistakes).
+    """
+    alt = os.environ.get("LBM_ORACLE_LIB")
+    if alt:
+        return alt
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int),
+                ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
+                ("walls", C.c_int),
+                ("gx", C.c_double), ("gy", C.c_double),
+                ("kappa", C.c_void_p), ("ktensor", C.c_void_p), ("gfield", C.c_void_p)]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        dp = C.POINTER(C.c_double)
+        _lib.orc_init_rest.argtypes = [C.POINTER(_Problem), dp]
+        _lib.orc_velocity.argtypes = [C.POINTER(_Problem), dp, dp, dp, dp]
+        _lib.orc_step.argtypes = [C.POINTER(_Problem), dp, dp]
+        _lib.orc_run.argtypes = [C.POINTER(_Problem), dp, C.c_long, C.c_double, C.c_int,
+                                 dp, C.POINTER(C.c_int)]
+        _lib.orc_run.restype = C.c_long
+        _lib.orc_mean_velocity.argtypes = [C.POINTER(_Problem), dp, dp]
+        _lib.orc_local_keff.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_long, C.c_int,
+                                        dp, dp, C.POINTER(C.c_long)]
+        _lib.orc_local_keff.restype = C.c_int
+        _lib.orc_run_mean_steady.argtypes = [C.POINTER(_Problem), dp, C.c_int, C.c_double, C.c_long,
+                                             C.c_int, dp, C.POINTER(C.c_int)]
+        _lib.orc_run_mean_steady.restype = C.c_long
+        _lib.orc_block_average.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
+        _lib.orc_lattice.argtypes = [C.POINTER(C.c_int), dp]
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Problem:
+    """One lattice problem: sizes, tau, nu, eps, boundaries, permeability and force.
+
+    ``kappa``: ``[ny, nx]`` scalar permeability (may contain +inf, or 0), or
+    ``ktensor``: ``[ny, nx, 4]`` (xx, xy, yx, yy). ``g``: constant (gx, gy) or
+    ``gfield``: ``[2, ny, nx]``. ``walls``: half-way bounce-back in y.
+    """
+
+    def __init__(self, tau, nu, eps=1.0, kappa=None, ktensor=None, g=(0.0, 0.0), gfield=None,
+                 walls=False):
+        if kappa is None and ktensor is None:
+            raise ValueError("kappa or ktensor is required")
+        self.kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
+        self.ktensor = None if ktensor is None else np.ascontiguousarray(ktensor, dtype=np.float64)
+        shape = (self.kappa if self.kappa is not None else self.ktensor).shape[:2]
+        self.ny, self.nx = int(shape[0]), int(shape[1])
+        self.gfield = None if gfield is None else np.ascontiguousarray(gfield, dtype=np.float64)
+        self._s = _Problem(self.nx, self.ny, float(tau), float(nu), float(eps), int(bool(walls)),
+                           float(g[0]), float(g[1]),
+                           None if self.kappa is None else self.kappa.ctypes.data,
+                           None if self.ktensor is None else self.ktensor.ctypes.data,
+                           None if self.gfield is None else self.gfield.ctypes.data)
+        self.tau, self.nu, self.eps, self.walls = float(tau), float(nu), float(eps), bool(walls)
+
+    def rest(self) -> np.ndarray:
+        f = np.empty((self.ny, self.nx, Q))
+        _L().orc_init_rest(C.byref(self._s), _dp(f))
+        return f
+
+    def step(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.empty_like(f)
+        _L().orc_step(C.byref(self._s), _dp(f), _dp(out))
+        return out
+
+    def run(self, f: np.ndarray, max_steps: int, tol: float = 0.0, check_every: int = 0):
+        """Step ``f`` in place; returns (steps, residual, converged)."""
+        assert f.flags.c_contiguous and f.dtype == np.float64
+        r = C.c_double(-1.0)
+        conv = C.c_int(0)
+        n = _L().orc_run(C.byref(self._s), _dp(f), int(max_steps), float(tol), int(check_every),
+                         C.byref(r), C.byref(conv))
+        return int(n), float(r.value), bool(conv.value)
+
+    def run_mean_steady(self, f: np.ndarray, d: int, tol: float, max_steps: int,
+                        check_every: int = 64):
+        """Step ``f`` in place until the mean velocity component ``d`` settles.
+
+        Returns (steps, ubar [2], converged); the test is the local-problem one
+        of Section 3 (relative change over ``check_every`` steps <= tol * check_every).
+        """
+        assert f.flags.c_contiguous and f.dtype == np.float64
+        ub = np.empty(2)
+        conv = C.c_int(0)
+        n = _L().orc_run_mean_steady(C.byref(self._s), _dp(f), int(d), float(tol), int(max_steps),
+                                     int(check_every), _dp(ub), C.byref(conv))
+        return int(n), ub, bool(conv.value)
+
+    def fields(self, f: np.ndarray):
+        """(rho, u, v) of the state f, flow velocity of Eq. 15."""
+        rho = np.empty((self.ny, self.nx))
+        u = np.empty_like(rho)
+        v = np.empty_like(rho)
+        _L().orc_velocity(C.byref(self._s), _dp(np.ascontiguousarray(f)), _dp(rho), _dp(u), _dp(v))
+        return rho, u, v
+
+    def mean_velocity(self, f: np.ndarray) -> np.ndarray:
+        out = np.empty(2)
+        _L().orc_mean_velocity(C.byref(self._s), _dp(np.ascontiguousarray(f)), _dp(out))
+        return out
+
+
+def lattice():
+    e = (C.c_int * 18)()
+    w = np.empty(9)
+    _L().orc_lattice(e, _dp(w))
+    return np.array(list(e), dtype=np.int64).reshape(9, 2), w
+
+
+def local_keff(kappa_leaf, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64):
+    """Local problems of Section 3 on one periodic square patch; Eq. 17.
+
+    Returns dict(keff=[xx, xy, yx, yy], ubar=[u1x, u1y, u2x, u2y], steps=[s1, s2], converged=n).
+    """
+    k = np.ascontiguousarray(kappa_leaf, dtype=np.float64)
+    s = k.shape[0]
+    assert k.shape == (s, s)
+    keff = np.empty(4)
+    ub = np.empty(4)
+    st = (C.c_long * 2)()
+    nconv = _L().orc_local_keff(s, _dp(k), float(tau), float(nu), float(eps), float(g_const),
+                                float(tol), int(max_steps), int(check_every), _dp(keff), _dp(ub), st)
+    return dict(keff=keff, ubar=ub, steps=[st[0], st[1]], converged=int(nconv))
+
+
+def block_average(a, r):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    ny, nx = a.shape
+    out = np.empty((ny // r, nx // r))
+    _L().orc_block_average(nx, ny, r, _dp(a), _dp(out))
+    return out
+
+
+def steady_state_dense(problem: Problem) -> np.ndarray:
+    """Brute-force steady state for tiny grids (<= 8x8).
+
+    One oracle step is linear in f (the force enters as rho G and rho is a sum
+    of f), so f' = A f. The steady state is the null vector of I - A with the
+    mass of the rest state r (mass is conserved, which makes I - A singular).
+    Writing f = r + delta: (I - A) delta = A r - r with sum(delta) = 0. A is
+    recovered column by column from the step (A e_i = step(r + e_i) - step(r))
+    and the system is solved densely with the mass row (least squares, numpy).
+    This is a different algorithm from time stepping: it does not iterate.
+    """
+    n = problem.nx * problem.ny * Q
+    if n > 9 * 64:
+        raise ValueError("dense steady state is for grids of at most 64 cells")
+    r = problem.rest()
+    sr = problem.step(r).ravel()
+    A = np.empty((n, n))
+    for i in range(n):
+        e = r.ravel().copy()
+        e[i] += 1.0
+        A[:, i] = problem.step(e.reshape(r.shape)).ravel() - sr
+    M = np.vstack([np.eye(n) - A, np.ones((1, n))])
+    rhs = np.concatenate([sr - r.ravel(), [0.0]])
+    delta, *_ = np.linalg.lstsq(M, rhs, rcond=None)
+    return r + delta.reshape(r.shape)

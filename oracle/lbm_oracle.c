@@ -1,0 +1,368 @@
+/*
+ * lbm_oracle.c -- FP64 CPU oracle of the upscaled lattice Boltzmann method.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file restates, slowly and in plain loops, what
+ * the paper's method computes, so that the CUDA library can be checked against
+ * it. Only the tests, the package smoke check and the benchmark's CPU baseline
+ * load it. It shares no code, header or constant table with the CUDA path, and
+ * the CUDA path never calls it.
+ *
+ * What it follows (Li & Brown, "Upscaled Lattice Boltzmann Method for
+ * Simulations of Flows in Heterogeneous Porous Media"):
+ *   - D2Q9 lattice: e_alpha and w_alpha as defined in Section 2 (theta formulas).
+ *   - Simplified Shan-Chen evolution, Section 2.2:
+ *       rho = sum_a f_a, j = sum_a e_a f_a
+ *       u    = (j + dt/2 eps rho G) / (rho (1 + eps dt nu / (2 kappa)))    Eq. 6
+ *              (valid for the Shan-Chen model, Section 2.2 below Eq. 15)
+ *       u_eq = 2 tau u + (1 - 2 tau) j / rho                                 Eq. 16
+ *       f_eq = w rho (1 + e.u_eq / c_s^2)                                    Eq. 2
+ *       f(x + e dt, t + dt) = f + (f_eq - f) / tau                           Eq. 13
+ *   - Tensor permeability (Eq. 18): f_m = -eps nu K*^-1 u + eps G, so that
+ *       rho u = (I + dt/2 eps nu K*^-1)^-1 (j + dt/2 eps rho G)            (Eq. 15 + Eq. 18)
+ *   - Local problems (Section 3): periodic subdomain, G1 = (G, 0) and
+ *     G2 = (0, G), volume-averaged velocity, and Eq. 17 for K*.
+ *
+ * Lattice units throughout: dx = dt = 1, c = 1, c_s^2 = 1/3, rho0 = 1.
+ * Layout: f[(y * nx + x) * 9 + a] (array of structures).
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - initial state is rest, f = w rho0;
+ *   - walls (when requested) are half-way bounce-back links at y = -1/2 and
+ *     y = ny - 1/2; the paper itself uses periodic boundaries;
+ *   - the averaged velocity is the flow velocity of Eq. 15 (half-force included),
+ *     arithmetic mean over the cells;
+ *   - nu = 0 or eps = 0 means no drag at all (then kappa is not used).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 9
+
+typedef struct {
+    int nx, ny;
+    double tau, nu, eps;
+    int walls;               /* 0: periodic in x and y; 1: bounce-back walls in y */
+    double gx, gy;           /* constant body force, used when gfield == NULL */
+    const double *kappa;     /* [ny][nx] scalar permeability (may be +inf), or NULL */
+    const double *ktensor;   /* [ny][nx][4] (xx, xy, yx, yy), used when kappa == NULL */
+    const double *gfield;    /* [2][ny][nx] body force, or NULL */
+} orc_problem;
+
+/* D2Q9 velocities and weights, built from the angle definitions of Section 2. */
+static int E[Q][2];
+static double W[Q];
+static int OPP[Q];
+static int lattice_ready = 0;
+
+static void lattice_init(void)
+{
+    if (lattice_ready) return;
+    const double pi = 3.14159265358979323846;
+    E[0][0] = 0; E[0][1] = 0; W[0] = 4.0 / 9.0;
+    for (int a = 1; a <= 4; ++a) {
+        double th = (a - 1) * pi / 2.0;
+        E[a][0] = (int)lround(cos(th));
+        E[a][1] = (int)lround(sin(th));
+        W[a] = 1.0 / 9.0;
+    }
+    for (int a = 5; a <= 8; ++a) {
+        double th = (a - 5) * pi / 2.0 + pi / 4.0;
+        E[a][0] = (int)lround(sqrt(2.0) * cos(th));
+        E[a][1] = (int)lround(sqrt(2.0) * sin(th));
+        W[a] = 1.0 / 36.0;
+    }
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b)
+            if (E[b][0] == -E[a][0] && E[b][1] == -E[a][1]) OPP[a] = b;
+    lattice_ready = 1;
+}
+
+void orc_lattice(int *e_out /* [9][2] */, double *w_out /* [9] */)
+{
+    lattice_init();
+    for (int a = 0; a < Q; ++a) {
+        e_out[2 * a] = E[a][0];
+        e_out[2 * a + 1] = E[a][1];
+        w_out[a] = W[a];
+    }
+}
+
+static void force_at(const orc_problem *p, long c, double *Gx, double *Gy)
+{
+    if (p->gfield) {
+        long n = (long)p->nx * p->ny;
+        *Gx = p->gfield[c];
+        *Gy = p->gfield[n + c];
+    } else {
+        *Gx = p->gx;
+        *Gy = p->gy;
+    }
+}
+
+/*
+ * Flow velocity of one cell from its (pre-collision) distributions:
+ * Eq. 15 with f_m from Eq. 5 (scalar kappa, solved explicitly as Eq. 6) or
+ * from Eq. 18 (tensor K*, a 2x2 solve). Also returns rho and j.
+ */
+static void cell_velocity(const orc_problem *p, long c, const double *fc,
+                          double *rho_o, double *jx_o, double *jy_o,
+                          double *ux_o, double *uy_o)
+{
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int a = 0; a < Q; ++a) {
+        rho += fc[a];
+        jx += E[a][0] * fc[a];
+        jy += E[a][1] * fc[a];
+    }
+    double Gx, Gy;
+    force_at(p, c, &Gx, &Gy);
+    const double dt = 1.0;
+    double ux, uy;
+    if (p->eps * p->nu == 0.0) {
+        /* no drag: u = (j + dt/2 eps rho G) / rho */
+        ux = (jx + 0.5 * dt * p->eps * rho * Gx) / rho;
+        uy = (jy + 0.5 * dt * p->eps * rho * Gy) / rho;
+    } else if (p->kappa) {
+        double kap = p->kappa[c];
+        double denom = rho * (1.0 + p->eps * dt * p->nu / (2.0 * kap));   /* Eq. 6 */
+        ux = (jx + 0.5 * dt * p->eps * rho * Gx) / denom;
+        uy = (jy + 0.5 * dt * p->eps * rho * Gy) / denom;
+    } else {
+        /* Eq. 18 in Eq. 15: (I + dt/2 eps nu K*^-1) rho u = j + dt/2 eps rho G */
+        const double *k = p->ktensor + 4 * c;
+        double det = k[0] * k[3] - k[1] * k[2];
+        double ixx = k[3] / det, ixy = -k[1] / det, iyx = -k[2] / det, iyy = k[0] / det;
+        double h = 0.5 * dt * p->eps * p->nu;
+        double bxx = 1.0 + h * ixx, bxy = h * ixy, byx = h * iyx, byy = 1.0 + h * iyy;
+        double rx = jx + 0.5 * dt * p->eps * rho * Gx;
+        double ry = jy + 0.5 * dt * p->eps * rho * Gy;
+        double bdet = bxx * byy - bxy * byx;
+        double rux = (byy * rx - bxy * ry) / bdet;
+        double ruy = (-byx * rx + bxx * ry) / bdet;
+        ux = rux / rho;
+        uy = ruy / rho;
+    }
+    *rho_o = rho; *jx_o = jx; *jy_o = jy;
+    *ux_o = ux; *uy_o = uy;
+}
+
+void orc_init_rest(const orc_problem *p, double *f)
+{
+    lattice_init();
+    long n = (long)p->nx * p->ny;
+    for (long c = 0; c < n; ++c)
+        for (int a = 0; a < Q; ++a) f[c * Q + a] = W[a] * 1.0;
+}
+
+/* rho, u, v of the state f (Eq. 15); any output pointer may be NULL. */
+void orc_velocity(const orc_problem *p, const double *f, double *rho, double *u, double *v)
+{
+    lattice_init();
+    long n = (long)p->nx * p->ny;
+    for (long c = 0; c < n; ++c) {
+        double r, jx, jy, ux, uy;
+        cell_velocity(p, c, f + c * Q, &r, &jx, &jy, &ux, &uy);
+        if (rho) rho[c] = r;
+        if (u) u[c] = ux;
+        if (v) v[c] = uy;
+    }
+}
+
+/* One time step f -> fnew: collide (Eqs. 6, 16, 2, 13), then stream along e_a. */
+void orc_step(const orc_problem *p, const double *f, double *fnew)
+{
+    lattice_init();
+    const int nx = p->nx, ny = p->ny;
+    const double tau = p->tau, cs2 = 1.0 / 3.0;
+#pragma omp parallel for schedule(static) if ((long)nx * ny >= 16384)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            long c = (long)y * nx + x;
+            const double *fc = f + c * Q;
+            double rho, jx, jy, ux, uy;
+            cell_velocity(p, c, fc, &rho, &jx, &jy, &ux, &uy);
+            double uex = 2.0 * tau * ux + (1.0 - 2.0 * tau) * jx / rho;     /* Eq. 16 */
+            double uey = 2.0 * tau * uy + (1.0 - 2.0 * tau) * jy / rho;
+            for (int a = 0; a < Q; ++a) {
+                double eu = E[a][0] * uex + E[a][1] * uey;
+                double feq = W[a] * rho * (1.0 + eu / cs2);                 /* Eq. 2 */
+                double fpost = fc[a] + (feq - fc[a]) / tau;                 /* Eq. 13 */
+                int xd = x + E[a][0];
+                int yd = y + E[a][1];
+                xd = (xd + nx) % nx;
+                if (p->walls && (yd < 0 || yd >= ny)) {
+                    /* half-way bounce-back: the particle returns to its own cell reversed */
+                    fnew[c * Q + OPP[a]] = fpost;
+                } else {
+                    yd = (yd + ny) % ny;
+                    fnew[((long)yd * nx + xd) * Q + a] = fpost;
+                }
+            }
+        }
+    }
+}
+
+static double max_abs_diff_uv(long n, const double *u0, const double *v0,
+                              const double *u1, const double *v1, double *umax)
+{
+    double dm = 0.0, m = 0.0;
+    for (long c = 0; c < n; ++c) {
+        double du = fabs(u1[c] - u0[c]), dv = fabs(v1[c] - v0[c]);
+        if (du > dm) dm = du;
+        if (dv > dm) dm = dv;
+        if (fabs(u1[c]) > m) m = fabs(u1[c]);
+        if (fabs(v1[c]) > m) m = fabs(v1[c]);
+    }
+    *umax = m;
+    return dm;
+}
+
+/*
+ * Time stepping from the state in f (updated in place) for at most max_steps.
+ * Every check_every steps (when > 0) the change of the flow velocity between
+ * the last two steps is measured: resid = max|u^n - u^(n-1)| / max|u^n|
+ * (max over cells and both components). Stops when tol > 0 and resid <= tol.
+ * Returns the number of steps taken; *resid_out gets the last residual (or -1).
+ */
+long orc_run(const orc_problem *p, double *f, long max_steps, double tol, int check_every,
+             double *resid_out, int *converged)
+{
+    lattice_init();
+    long n = (long)p->nx * p->ny;
+    double *g = (double *)malloc(sizeof(double) * n * Q);
+    double *u0 = NULL, *v0 = NULL, *u1 = NULL, *v1 = NULL;
+    if (check_every > 0) {
+        u0 = (double *)malloc(sizeof(double) * n);
+        v0 = (double *)malloc(sizeof(double) * n);
+        u1 = (double *)malloc(sizeof(double) * n);
+        v1 = (double *)malloc(sizeof(double) * n);
+    }
+    double resid = -1.0;
+    int conv = 0;
+    long s = 0;
+    /* u0/v0 hold u(f^(s-1)) whenever s is a check step (s % check_every == 0) */
+    if (check_every == 1) orc_velocity(p, f, NULL, u0, v0);
+    while (s < max_steps) {
+        orc_step(p, f, g);
+        memcpy(f, g, sizeof(double) * n * Q);
+        ++s;
+        if (check_every > 0) {
+            if (s % check_every == 0) {
+                double um;
+                orc_velocity(p, f, NULL, u1, v1);
+                double d = max_abs_diff_uv(n, u0, v0, u1, v1, &um);
+                resid = um > 0.0 ? d / um : d;
+                if (tol > 0.0 && resid <= tol) { conv = 1; break; }
+            }
+            if ((s + 1) % check_every == 0) orc_velocity(p, f, NULL, u0, v0);
+        }
+    }
+    free(g); free(u0); free(v0); free(u1); free(v1);
+    if (resid_out) *resid_out = resid;
+    if (converged) *converged = conv;
+    return s;
+}
+
+/* Volume average (arithmetic mean over cells) of the flow velocity, Section 3. */
+void orc_mean_velocity(const orc_problem *p, const double *f, double out[2])
+{
+    lattice_init();
+    long n = (long)p->nx * p->ny;
+    double su = 0.0, sv = 0.0;
+    for (long c = 0; c < n; ++c) {
+        double r, jx, jy, ux, uy;
+        cell_velocity(p, c, f + c * Q, &r, &jx, &jy, &ux, &uy);
+        su += ux;
+        sv += uy;
+    }
+    out[0] = su / n;
+    out[1] = sv / n;
+}
+
+/*
+ * Steps f (in place) until the volume-averaged flow velocity settles: every
+ * check_every steps, |ubar_d(n) - ubar_d(n - k)| <= tol * k * |ubar_d(n)| on
+ * component d (0: x, 1: y). tol <= 0 runs exactly max_steps. Returns the
+ * steps taken; *converged tells whether the test passed; ubar gets the final mean.
+ */
+long orc_run_mean_steady(const orc_problem *p, double *f, int d, double tol, long max_steps,
+                         int check_every, double ubar[2], int *converged)
+{
+    lattice_init();
+    long n = (long)p->nx * p->ny;
+    double *g = (double *)malloc(sizeof(double) * n * Q);
+    double prev = 0.0, m[2] = {0.0, 0.0};
+    long st = 0;
+    int conv = 0;
+    while (st < max_steps) {
+        orc_step(p, f, g);
+        memcpy(f, g, sizeof(double) * n * Q);
+        ++st;
+        if (check_every > 0 && st % check_every == 0) {
+            orc_mean_velocity(p, f, m);
+            double cur = m[d];
+            if (tol > 0.0 && st > check_every &&
+                fabs(cur - prev) <= tol * check_every * fabs(cur)) {
+                conv = 1;
+                break;
+            }
+            prev = cur;
+        }
+    }
+    orc_mean_velocity(p, f, ubar);
+    free(g);
+    if (converged) *converged = conv;
+    return st;
+}
+
+/*
+ * One local problem (Section 3): the s x s permeability patch `kappa_leaf`
+ * (row-major) with periodic closure, driven by G1 = (gconst, 0) and then
+ * G2 = (0, gconst), each from rest until the volume-averaged velocity settles
+ * (orc_run_mean_steady on the driven component).
+ * Eq. 17 then gives K* = nu / gconst * [[ubar1_x, ubar2_x], [ubar1_y, ubar2_y]].
+ * keff = (xx, xy, yx, yy); ubar = (ubar1_x, ubar1_y, ubar2_x, ubar2_y);
+ * steps[d] = steps taken per drive; returns the number of drives that converged.
+ */
+int orc_local_keff(int s, const double *kappa_leaf, double tau, double nu, double eps,
+                   double gconst, double tol, long max_steps, int check_every,
+                   double keff[4], double ubar[4], long steps[2])
+{
+    lattice_init();
+    orc_problem p;
+    memset(&p, 0, sizeof p);
+    p.nx = s; p.ny = s; p.tau = tau; p.nu = nu; p.eps = eps;
+    p.walls = 0; p.kappa = kappa_leaf;
+    long n = (long)s * s;
+    double *f = (double *)malloc(sizeof(double) * n * Q);
+    int nconv = 0;
+    for (int d = 0; d < 2; ++d) {
+        p.gx = d == 0 ? gconst : 0.0;
+        p.gy = d == 0 ? 0.0 : gconst;
+        orc_init_rest(&p, f);
+        int conv = 0;
+        steps[d] = orc_run_mean_steady(&p, f, d, tol, max_steps, check_every, ubar + 2 * d, &conv);
+        nconv += conv;
+    }
+    /* Eq. 17: columns are the two drives, rows the velocity components */
+    keff[0] = nu / gconst * ubar[0];   /* K*_xx = nu/G ubar1 . (1,0) */
+    keff[1] = nu / gconst * ubar[2];   /* K*_xy = nu/G ubar2 . (1,0) */
+    keff[2] = nu / gconst * ubar[1];   /* K*_yx = nu/G ubar1 . (0,1) */
+    keff[3] = nu / gconst * ubar[3];   /* K*_yy = nu/G ubar2 . (0,1) */
+    free(f);
+    return nconv;
+}
+
+/* Mean of a [ny][nx] field over r x r blocks -> [ny/r][nx/r] (fine-to-coarse comparison). */
+void orc_block_average(int nx, int ny, int r, const double *a, double *out)
+{
+    int cx = nx / r, cy = ny / r;
+    for (int J = 0; J < cy; ++J)
+        for (int I = 0; I < cx; ++I) {
+            double s = 0.0;
+            for (int y = J * r; y < (J + 1) * r; ++y)
+                for (int x = I * r; x < (I + 1) * r; ++x) s += a[(long)y * nx + x];
+            out[(long)J * cx + I] = s / ((double)r * r);
+        }
+}
