@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the fine-grid D2Q9 step (FP32 deviation storage) on one GB300.
+
+Workload: 4096 x 4096 periodic lattice, log-normal permeability K = 1e-2 exp(2 Z)
+(Z: Gaussian random field, correlation length 32 cells, seed 2), tau = 0.6,
+nu = nu_eff, eps = 1, G = (1e-6, 0), synthetic and seeded. One bench step is one
+`lbm_step` call of 1000 lattice time steps with the FP64 residual check every
+64 steps (the whole fine-grid hot path: fused stream+collide, moments,
+residual and flux reductions), replayed as CUDA graphs. The state (2 x 604 MB)
+is far larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+the same workload instead (bounded sample per step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 MLUPS (%HBM roofline); K_eff patches/s: surrogate vs batched LBM at stated err"
+N = 4096
+TAU = 0.6
+NU = (TAU - 0.5) / 3.0
+G = (1e-6, 0.0)
+LBM_STEPS_PER_STEP = 1000
+CHECK_EVERY = 64
+BYTES_PER_LUP = {"f32": 76, "f16": 40, "f64": 152}
+WORKLOAD = (f"D2Q9 fine grid {N}x{N} periodic, log-normal K (sigma_logK=2, ell=32, seed 2), "
+            f"tau={TAU}, nu=nu_eff, G=(1e-6,0)")
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+            else:
+                torch.cuda.set_device(local)
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_kappa() -> np.ndarray:
+    import synth
+    return synth.lognormal_kappa(N, N, 32.0, 2.0, seed=2).astype(np.float32)
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d.get("hbm_gbs"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def traffic_from_profile(kernel_src: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    p = os.path.join(ROOT, "profiles", "step_f32_4096_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if d.get("step_cu_sha256") != h:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def oracle_rate(kap: np.ndarray, steps: int) -> tuple[float, int, float]:
+    """MLUPS of the FP64 oracle on the same lattice for `steps` steps (all host cores)."""
+    import oracle
+    p = oracle.Problem(TAU, NU, 1.0, kappa=kap.astype(np.float64), g=G)
+    f = p.rest()
+    t0 = time.perf_counter()
+    p.run(f, steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return N * N * steps / dt / 1e6, cores, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    kap = make_kappa()
+    import oracle
+    oracle.build()
+    p = oracle.Problem(TAU, NU, 1.0, kappa=kap.astype(np.float64), g=G)
+    f = p.rest()
+    for _ in range(args.warmup):
+        p.run(f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p.run(f, 1)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = N * N * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded log-normal permeability field)",
+        "config": {"workload": WORKLOAD + "; FP64 CPU oracle, one lattice step per bench step",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} lattice steps of the full {N}x{N} lattice"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_1312_0195_gb300 as lbm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    storage = {"f32": lbm.LBM_F32, "f16": lbm.LBM_F16, "f64": lbm.LBM_F64}[args.storage]
+    kap_np = make_kappa()
+    kap = torch.from_numpy(kap_np).to(dev)
+    p = lbm.Params(nx=N, ny=N, tau=TAU, nu=NU, eps=1.0, gx=G[0], gy=G[1], storage=storage)
+    grid = lbm.Grid(p, kap)
+
+    for _ in range(args.warmup):
+        grid.step(LBM_STEPS_PER_STEP, 0.0, CHECK_EVERY)
+    torch.cuda.synchronize()
+    barrier(ws)
+    l0 = lbm.lbm_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            grid.step(LBM_STEPS_PER_STEP, 0.0, CHECK_EVERY)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = lbm.lbm_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms, ws)
+    lups = float(N) * N * LBM_STEPS_PER_STEP * args.steps * ws
+    value = lups / (ms_max * 1e-3) / 1e6
+
+    # roofline of the dominant kernel: plain fused steps only, timed on the grid's stream
+    nplain = 500
+    grid.step(nplain, 0.0, 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    grid.step(nplain, 0.0, 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_launch = e0.elapsed_time(e1) * 1e-3 / nplain
+    bytes_launch = BYTES_PER_LUP[args.storage] * float(N) * N
+    peaks = measured_peaks()
+    achieved = bytes_launch / t_launch / 1e9
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_1312_0195_gb300", "csrc", "step.cu")) \
+        if args.storage == "f32" else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": peaks["source"], "kernel": f"step_kernel<{args.storage}>",
+                "algorithmic_bytes_per_lup": BYTES_PER_LUP[args.storage],
+                "launch_ms": t_launch * 1e3}
+    grid.close()
+
+    # end to end through the public API with host buffers: H2D kappa, create, step, D2H u and v
+    kap_host = torch.from_numpy(kap_np).pin_memory()
+    u_host = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    v_host = torch.empty((N, N), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        kd = kap_host.to(dev, non_blocking=True)
+        with lbm.Grid(p, kd) as g2:
+            g2.step(LBM_STEPS_PER_STEP, 0.0, CHECK_EVERY)
+            _, u, v = g2.fields()
+            u_host.copy_(u, non_blocking=True)
+            v_host.copy_(v, non_blocking=True)
+            torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, ws)
+    e2e = {"value": float(N) * N * LBM_STEPS_PER_STEP * e2e_steps * ws / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": int(kap_host.numel() * 4),
+           "d2h_bytes_per_step": int(u_host.numel() * 4 + v_host.numel() * 4),
+           "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, cores, dt = oracle_rate(kap_np, args.cpu_steps)
+        cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_steps} lattice steps of the full {N}x{N} lattice ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+            "data": "synthetic (seeded log-normal permeability field)",
+            "config": {"workload": WORKLOAD + f"; {args.storage.upper()} deviation storage",
+                       "lattice_steps_per_step": LBM_STEPS_PER_STEP, "check_every": CHECK_EVERY,
+                       "l2": "state 1.2 GB >> 129 MB L2 (no flush needed)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"])
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

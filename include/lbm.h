@@ -1,0 +1,141 @@
+/*
+ * lbm.h -- C ABI of the GB300 upscaled lattice Boltzmann library (liblbm.so).
+ *
+ * The library steps the D2Q9 simplified Shan-Chen lattice Boltzmann scheme for
+ * Brinkman/Darcy flow in heterogeneous porous media (Li & Brown, "Upscaled
+ * Lattice Boltzmann Method for Simulations of Flows in Heterogeneous Porous
+ * Media", Section 2.2), solves the local problems that give the effective
+ * permeability tensor K* of each subdomain (Section 3, Eq. 17), and runs the
+ * coarse upscaled simulation with K* (Section 3, Eq. 18; Section 4.3).
+ *
+ * Units. Everything is in lattice units: dx = dt = 1, c = 1, c_s^2 = 1/3 and
+ * rho0 = 1. tau sets nu_eff = (tau - 1/2) / 3 (Section 2.1). nu is the Darcy
+ * viscosity of the drag term (Eq. 5), independent of nu_eff; kappa is the
+ * permeability in cells^2; G is the body force per unit mass.
+ *
+ * Conventions shared by every call.
+ *   - Arrays are row-major [ny][nx] (x fastest). Array arguments named *_dev
+ *     are DEVICE pointers owned by the caller; the library never frees them.
+ *     Passing a host pointer where a device pointer is expected returns
+ *     LBM_EINVAL. Only the opaque handles (lbm_grid) own device memory.
+ *   - `cuda_stream` is a cudaStream_t (NULL: the legacy default stream). Work is
+ *     ordered on that stream; every call synchronises the stream before it
+ *     returns, so outputs are ready when it returns LBM_OK.
+ *   - Every call returns an lbm_status. On failure lbm_last_error() returns a
+ *     thread-local message. LBM_EINVAL is returned before any device work when
+ *     the arguments can be checked on the host; device-resident inputs (kappa)
+ *     are validated by a kernel and reported as LBM_EINVAL as well.
+ *   - The library uses one GPU: the current CUDA device at the call.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* invalid argument (nothing was launched or changed)          */
+    LBM_ENOMEM = 2,     /* device or pinned host allocation failed                     */
+    LBM_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error)     */
+    LBM_ENOTCONV = 4,   /* stopping tolerance not met within max_steps (results valid) */
+    LBM_ETIMEOUT = 5    /* a bounded device-side wait gave up (results not valid)      */
+} lbm_status;
+
+typedef enum {
+    LBM_F32 = 0,        /* distributions stored as FP32 deviations g = f - w rho0     */
+    LBM_F16 = 1,        /* FP16 deviations scaled by a power of two S, FP32 arithmetic */
+    LBM_F64 = 2         /* FP64 deviations and FP64 arithmetic                        */
+} lbm_storage;
+
+typedef enum {
+    LBM_BC_PERIODIC = 0,  /* periodic in x and y (the paper's choice, Section 3)       */
+    LBM_BC_WALLS_Y = 1    /* periodic in x; half-way bounce-back walls at y = -1/2 and
+                             y = ny - 1/2 (no-slip channel walls)                      */
+} lbm_bc;
+
+typedef struct {
+    int32_t nx, ny;       /* lattice size in cells, each >= 1                          */
+    double  tau;          /* BGK relaxation time, tau >= 1/2; nu_eff = (tau - 1/2)/3    */
+    double  nu;           /* Darcy viscosity in f_m = -(eps nu / kappa) u + eps G (Eq. 5);
+                             a negative value selects nu = nu_eff                       */
+    double  eps;          /* porosity epsilon, >= 0                                     */
+    double  gx, gy;       /* constant body force, used when no force field is given     */
+    int32_t bc;           /* lbm_bc                                                     */
+    int32_t storage;      /* lbm_storage                                                */
+    double  scale;        /* LBM_F16 only: power-of-two storage scale S; 0 picks S from
+                             the largest finite kappa, |G| and nu                        */
+} lbm_params;
+
+/* Thread-local description of the last failure of any call in this thread. */
+const char *lbm_last_error(void);
+
+/* Number of kernels this library has launched in this process (graph launches
+ * count each kernel node). Lets a caller check that the device path ran. */
+int64_t lbm_launch_count(void);
+
+/* ------------------------------------------------------------------ grids ---
+ * A grid is one lattice with its permeability and force, stepped by the
+ * simplified Shan-Chen scheme of Section 2.2:
+ *   rho = sum_a f_a, j = sum_a e_a f_a,
+ *   u = (j + eps rho G / 2) / (rho (1 + eps nu / (2 kappa)))      (Eq. 6, Eq. 15)
+ *   u_eq = 2 tau u + (1 - 2 tau) j / rho                            (Eq. 16)
+ *   f_eq = w_a rho (1 + e_a . u_eq / c_s^2)                        (Eq. 2)
+ *   f_a(x + e_a, t + 1) = f_a + (f_eq - f_a) / tau                  (Eq. 13)
+ * starting from rest (f = w_a rho0). */
+typedef struct lbm_grid lbm_grid;
+
+/* Creates a grid. kappa_dev: float [ny][nx] permeability, each >= 0 (0 blocks the
+ * cell completely, +inf means no drag); NaN or negative values give LBM_EINVAL.
+ * g_field_dev: NULL for the constant (gx, gy), else float [2][ny][nx] (x plane,
+ * then y plane). Both are read during the call only (the grid keeps its own
+ * derived copy). On success *out owns two distribution buffers of
+ * 9 * nx * ny elements of the storage type plus per-cell coefficients. */
+lbm_status lbm_grid_create(const lbm_params *p, const float *kappa_dev, const float *g_field_dev,
+                           void *cuda_stream, lbm_grid **out);
+
+/* Frees a grid and everything it owns. NULL is accepted. */
+lbm_status lbm_grid_destroy(lbm_grid *g);
+
+/* Advances the grid by up to max_steps time steps (fused pull-stream + collide,
+ * replayed as CUDA graphs). With check_every = k > 0, after every step count t
+ * that is a multiple of k (counted from grid creation) the residual
+ *   r = max_x,i |u_i^t - u_i^(t-1)| / max_x,i |u_i^t|
+ * is computed in FP64; when tol_rel > 0 and r <= tol_rel the call stops and
+ * returns LBM_OK. tol_rel <= 0 runs exactly max_steps and returns LBM_OK.
+ * If tol_rel > 0 and the test never passes, returns LBM_ENOTCONV (the state is
+ * valid). steps_done (may be NULL) receives the steps taken by this call;
+ * residual (may be NULL) the last residual computed in this call, or -1. */
+lbm_status lbm_step(lbm_grid *g, int64_t max_steps, double tol_rel, int32_t check_every,
+                    int64_t *steps_done, double *residual);
+
+/* Density and flow velocity (Eq. 15) of the current state into caller-owned
+ * float [ny][nx] device arrays; any of the three may be NULL. */
+lbm_status lbm_get_fields(lbm_grid *g, float *rho_dev, float *u_dev, float *v_dev);
+
+/* Volume average of the flow velocity over all cells (Section 3), reduced in
+ * FP64 in a fixed order (bitwise reproducible). out_mean_uv is HOST memory. */
+lbm_status lbm_mean_velocity(lbm_grid *g, double out_mean_uv[2]);
+
+/* Total steps taken since creation (host value). */
+int64_t lbm_grid_steps(const lbm_grid *g);
+
+/* Checkpoint: copies the grid's state (its current distribution buffer, storage
+ * type, 9 * nx * ny elements in [9][ny][nx] order, deviations from w_a rho0,
+ * multiplied by the FP16 scale for LBM_F16) to or from caller-owned DEVICE
+ * memory of lbm_grid_state_bytes(g) bytes, together with the step count. */
+int64_t lbm_grid_state_bytes(const lbm_grid *g);
+lbm_status lbm_grid_save_state(lbm_grid *g, void *state_dev, int64_t *steps);
+lbm_status lbm_grid_load_state(lbm_grid *g, const void *state_dev, int64_t steps);
+
+/* Storage scale S in use (1 for LBM_F32 / LBM_F64). */
+double lbm_grid_scale(const lbm_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,185 @@
+"""GB300 upscaled lattice Boltzmann library: Python binding of ``liblbm.so``.
+
+The functions named ``lbm_*`` mirror the C ABI of ``include/lbm.h`` one to
+one; they only marshal arguments (torch CUDA tensors -> device pointers, the
+current torch stream -> ``cuda_stream``). ``Grid`` is a small convenience
+wrapper over the same calls. Nothing here computes any part of the method:
+every step runs in the library's CUDA kernels, and importing this package
+fails when the library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+from . import _abi
+from ._abi import (LBM_BC_PERIODIC, LBM_BC_WALLS_Y, LBM_ECUDA, LBM_EINVAL, LBM_ENOMEM,  # noqa: F401
+                   LBM_ENOTCONV, LBM_ETIMEOUT, LBM_F16, LBM_F32, LBM_F64, LBM_OK)
+
+_abi.lib()   # fail loudly at import when the CUDA library is absent
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_abi.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int, allow=(LBM_OK,)) -> int:
+    if status not in allow:
+        raise LbmError(status, lbm_last_error())
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (None -> NULL). Host tensors are passed as
+    host pointers on purpose, so the library can reject them with LBM_EINVAL."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        # without a device the library rejects the call before using the stream
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class Params:
+    nx: int
+    ny: int
+    tau: float
+    nu: float = -1.0
+    eps: float = 1.0
+    gx: float = 0.0
+    gy: float = 0.0
+    bc: int = LBM_BC_PERIODIC
+    storage: int = LBM_F32
+    scale: float = 0.0
+
+    def c(self) -> _abi.lbm_params:
+        return _abi.lbm_params(int(self.nx), int(self.ny), float(self.tau), float(self.nu), float(self.eps),
+                               float(self.gx), float(self.gy), int(self.bc), int(self.storage), float(self.scale))
+
+
+# ----------------------------------------------------------------- C ABI mirror
+
+def lbm_last_error() -> str:
+    return (_abi.lib().lbm_last_error() or b"").decode()
+
+
+def lbm_launch_count() -> int:
+    return int(_abi.lib().lbm_launch_count())
+
+
+def lbm_grid_create(params: Params, kappa, g_field=None, stream=None) -> C.c_void_p:
+    out = C.c_void_p()
+    p = params.c()
+    _check(_abi.lib().lbm_grid_create(C.byref(p), _ptr(kappa), _ptr(g_field), _stream(stream), C.byref(out)))
+    return out
+
+
+def lbm_grid_destroy(grid) -> None:
+    _check(_abi.lib().lbm_grid_destroy(grid))
+
+
+def lbm_step(grid, max_steps: int, tol_rel: float = 0.0, check_every: int = 0):
+    """Returns (status, steps_done, residual); raises except for LBM_OK / LBM_ENOTCONV."""
+    steps = C.c_int64(0)
+    res = C.c_double(-1.0)
+    st = _check(_abi.lib().lbm_step(grid, int(max_steps), float(tol_rel), int(check_every),
+                                    C.byref(steps), C.byref(res)), allow=(LBM_OK, LBM_ENOTCONV))
+    return st, int(steps.value), float(res.value)
+
+
+def lbm_get_fields(grid, rho=None, u=None, v=None) -> None:
+    _check(_abi.lib().lbm_get_fields(grid, _ptr(rho), _ptr(u), _ptr(v)))
+
+
+def lbm_mean_velocity(grid):
+    out = (C.c_double * 2)()
+    _check(_abi.lib().lbm_mean_velocity(grid, out))
+    return float(out[0]), float(out[1])
+
+
+def lbm_grid_steps(grid) -> int:
+    return int(_abi.lib().lbm_grid_steps(grid))
+
+
+def lbm_grid_state_bytes(grid) -> int:
+    return int(_abi.lib().lbm_grid_state_bytes(grid))
+
+
+def lbm_grid_save_state(grid, state) -> int:
+    steps = C.c_int64(0)
+    _check(_abi.lib().lbm_grid_save_state(grid, _ptr(state), C.byref(steps)))
+    return int(steps.value)
+
+
+def lbm_grid_load_state(grid, state, steps: int) -> None:
+    _check(_abi.lib().lbm_grid_load_state(grid, _ptr(state), int(steps)))
+
+
+def lbm_grid_scale(grid) -> float:
+    return float(_abi.lib().lbm_grid_scale(grid))
+
+
+# ------------------------------------------------------------------ convenience
+
+class Grid:
+    """Owning wrapper: ``Grid(params, kappa_cuda_f32[, g_field])``."""
+
+    def __init__(self, params: Params, kappa, g_field=None, stream=None):
+        self.params = params
+        self.stream = stream
+        self.handle = lbm_grid_create(params, kappa, g_field, stream)
+
+    def step(self, max_steps: int, tol_rel: float = 0.0, check_every: int = 0):
+        st, n, r = lbm_step(self.handle, max_steps, tol_rel, check_every)
+        return n, r, st == LBM_OK
+
+    def fields(self):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        shape = (self.params.ny, self.params.nx)
+        rho = torch.empty(shape, dtype=torch.float32, device=dev)
+        u = torch.empty_like(rho)
+        v = torch.empty_like(rho)
+        lbm_get_fields(self.handle, rho, u, v)
+        return rho, u, v
+
+    def mean_velocity(self):
+        return lbm_mean_velocity(self.handle)
+
+    @property
+    def steps(self) -> int:
+        return lbm_grid_steps(self.handle)
+
+    @property
+    def scale(self) -> float:
+        return lbm_grid_scale(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lbm_grid_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

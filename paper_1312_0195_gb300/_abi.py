@@ -1,0 +1,78 @@
+"""ctypes declarations of include/lbm.h (argument marshalling only).
+
+Loads the in-tree ``liblbm.so``. There is no fallback: if the library is
+missing or cannot be loaded, importing the package raises, and every step of
+the method runs in the library's CUDA kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTCONV, LBM_ETIMEOUT = range(6)
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ENOTCONV",
+                5: "LBM_ETIMEOUT"}
+LBM_F32, LBM_F16, LBM_F64 = 0, 1, 2
+LBM_BC_PERIODIC, LBM_BC_WALLS_Y = 0, 1
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32),
+                ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
+                ("gx", C.c_double), ("gy", C.c_double),
+                ("bc", C.c_int32), ("storage", C.c_int32),
+                ("scale", C.c_double)]
+
+
+class lbm_leaf(C.Structure):
+    _fields_ = [("x0", C.c_int32), ("y0", C.c_int32), ("size", C.c_int32)]
+
+
+_P = C.c_void_p
+_I32 = C.c_int32
+_I64 = C.c_int64
+_D = C.c_double
+_PP = C.POINTER(lbm_params)
+
+# name -> (restype, argtypes); every entry is declared in include/lbm.h
+SIGNATURES = {
+    "lbm_last_error": (C.c_char_p, []),
+    "lbm_launch_count": (_I64, []),
+    "lbm_grid_create": (C.c_int, [_PP, _P, _P, _P, C.POINTER(_P)]),
+    "lbm_grid_destroy": (C.c_int, [_P]),
+    "lbm_step": (C.c_int, [_P, _I64, _D, _I32, C.POINTER(_I64), C.POINTER(_D)]),
+    "lbm_get_fields": (C.c_int, [_P, _P, _P, _P]),
+    "lbm_mean_velocity": (C.c_int, [_P, C.POINTER(_D)]),
+    "lbm_grid_steps": (_I64, [_P]),
+    "lbm_grid_state_bytes": (_I64, [_P]),
+    "lbm_grid_save_state": (C.c_int, [_P, _P, C.POINTER(_I64)]),
+    "lbm_grid_load_state": (C.c_int, [_P, _P, _I64]),
+    "lbm_grid_scale": (_D, [_P]),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded liblbm.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"` "
+                "(needs nvcc); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return sorted(SIGNATURES)

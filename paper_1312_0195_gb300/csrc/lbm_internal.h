@@ -1,0 +1,77 @@
+// lbm_internal.h -- declarations shared by the library's translation units.
+// Nothing here is part of the public ABI (see include/lbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// D2Q9 velocity set, ordered as in Section 2 of the paper:
+// 0 rest, 1..4 axis directions at angles (a-1) pi/2, 5..8 diagonals at (a-5) pi/2 + pi/4.
+constexpr int Q = 9;
+__host__ __device__ constexpr int ex(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
+__host__ __device__ constexpr int ey(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5); }
+
+enum CoefMode { COEF_SCALAR = 0, COEF_TENSOR = 1 };
+
+// Everything one launch of the fused step (or the moment/check pass) needs.
+// src/dst are the storage-type planes [9][plane]; coefficient and force planes
+// use CT (float for FP32/FP16 storage, double for FP64).
+template <typename T, typename CT>
+struct StepArgs {
+    int nx, ny;
+    int64_t plane;        // elements between consecutive population planes
+    CT omega;             // 1 / tau
+    CT two_tau;           // 2 tau             (Eq. 16)
+    CT one_m_two_tau;     // 1 - 2 tau         (Eq. 16)
+    CT half_eps;          // eps dt / 2        (Eq. 6)
+    CT gx, gy;            // constant force when gfield == nullptr
+    CT rho0;              // rest density in storage units (the FP16 scale S, else 1)
+    const T *src;         // post-collision state of the previous step
+    T *dst;
+    const CT *coef;       // COEF_SCALAR: d [plane]; COEF_TENSOR: M [4][plane]
+    const CT *gfield;     // [2][plane] or nullptr
+};
+
+// Moments / residual pass: reads the current (and optionally previous) state.
+template <typename T, typename CT>
+struct MomArgs {
+    StepArgs<T, CT> s;    // s.src = current state; dst unused
+    const T *prev;        // previous state (nullptr: no residual)
+    CT inv_scale;         // 1 / S
+    float *rho, *u, *v;   // optional field outputs [ny][nx]
+    double *partials;     // [gridDim.x][4]: max|du|, max|u|, sum u, sum v
+};
+
+struct GridLaunch {
+    int step_blocks;      // persistent grid for the fused step
+    int step_threads;
+    int mom_blocks;
+    int mom_threads;
+};
+
+// ---- launchers (step.cu) -----------------------------------------------------
+// storage: lbm_storage; coef_mode: CoefMode. All return cudaGetLastError().
+cudaError_t launch_step(int storage, int coef_mode, bool gfield, bool walls, const void *args,
+                        const GridLaunch &L, cudaStream_t st);
+cudaError_t launch_moments(int storage, int coef_mode, bool gfield, bool walls, const void *args,
+                           const GridLaunch &L, cudaStream_t st);
+cudaError_t launch_reduce_partials(const double *partials, int n, double *out4, cudaStream_t st);
+cudaError_t launch_coef_scalar(int storage, const float *kappa, void *coef, int64_t n, int64_t plane,
+                               double eps_nu, unsigned *flags, unsigned *kmax_bits, cudaStream_t st);
+cudaError_t launch_coef_tensor(int storage, const double *kstar, void *coef, int64_t n, int64_t plane,
+                               double c, unsigned *flags, cudaStream_t st);
+cudaError_t launch_copy_force(int storage, const float *g, void *dst, int64_t n, int64_t plane,
+                              double scale_unused, cudaStream_t st);
+int step_vec(int storage, int nx);   // cells per thread used for this storage and row length
+int step_blocks_per_sm(int storage, int coef_mode, bool gfield, bool walls, int nx, int threads);
+
+// ---- launch counter (lbm_api.cu) ----------------------------------------------
+void count_launches(int64_t n);
+
+}  // namespace lbm

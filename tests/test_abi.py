@@ -1,0 +1,88 @@
+"""The C ABI: the library loads, exports every function include/lbm.h declares,
+and rejects invalid arguments on the host (no device work, no GPU needed)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    names = set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1312_0195_gb300 import _abi
+    return _abi.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("lbm_grid_create", "lbm_grid_destroy", "lbm_step", "lbm_get_fields",
+                     "lbm_mean_velocity", "lbm_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1312_0195_gb300 import _abi
+    for name in _declared_functions():
+        assert hasattr(lib, name), f"{name} declared in lbm.h but not exported"
+        assert name in _abi.SIGNATURES, f"{name} has no Python binding"
+
+
+def _params(**kw):
+    from paper_1312_0195_gb300 import _abi
+    base = dict(nx=16, ny=8, tau=1.0, nu=-1.0, eps=1.0, gx=1e-6, gy=0.0, bc=0, storage=0, scale=0.0)
+    base.update(kw)
+    return _abi.lbm_params(**base)
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(tau=0.49), dict(tau=float("nan")),
+                                 dict(eps=-0.1), dict(gx=float("inf")), dict(bc=7), dict(storage=3),
+                                 dict(scale=3.0), dict(scale=-1.0), dict(nu=float("nan"))])
+def test_create_rejects_bad_params(lib, bad):
+    out = C.c_void_p(123)
+    p = _params(**bad)
+    st = lib.lbm_grid_create(C.byref(p), None, None, None, C.byref(out))
+    assert st == 1   # LBM_EINVAL
+    assert out.value is None
+    assert len(lib.lbm_last_error()) > 0
+
+
+def test_create_rejects_null_and_host_pointers(lib):
+    import numpy as np
+    out = C.c_void_p()
+    p = _params()
+    assert lib.lbm_grid_create(None, None, None, None, C.byref(out)) == 1
+    assert lib.lbm_grid_create(C.byref(p), None, None, None, C.byref(out)) == 1
+    host = np.ones(16 * 8, dtype=np.float32)
+    assert lib.lbm_grid_create(C.byref(p), host.ctypes.data, None, None, C.byref(out)) == 1
+    assert b"device pointer" in lib.lbm_last_error()
+
+
+def test_calls_on_null_grid_are_einval(lib):
+    steps = C.c_int64(5)
+    res = C.c_double(0.0)
+    assert lib.lbm_step(None, 10, 0.0, 0, C.byref(steps), C.byref(res)) == 1
+    assert steps.value == 0 and res.value == -1.0
+    assert lib.lbm_get_fields(None, None, None, None) == 1
+    out = (C.c_double * 2)()
+    assert lib.lbm_mean_velocity(None, out) == 1
+    assert lib.lbm_grid_destroy(None) == 0
+    assert lib.lbm_grid_steps(None) == -1
+
+
+def test_python_binding_raises_typed_error():
+    import paper_1312_0195_gb300 as lbm
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_grid_create(lbm.Params(nx=0, ny=4, tau=1.0), None)
+    assert ei.value.status == lbm.LBM_EINVAL
