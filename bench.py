@@ -314,11 +314,29 @@ def main(argv=None):
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"])
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling mode: create the grid, run this many plain lattice steps, exit")
     args = ap.parse_args(argv)
     ws, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.profile_steps > 0:
+        return run_profile(args, local)
     return run_ours(args, ws, rank, local)
+
+
+def run_profile(args, local):
+    """A short, fixed launch sequence for ncu: one grid, `profile_steps` plain steps, one check."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    torch.cuda.set_device(local)
+    storage = {"f32": lbm.LBM_F32, "f16": lbm.LBM_F16, "f64": lbm.LBM_F64}[args.storage]
+    kap = torch.from_numpy(make_kappa()).cuda()
+    p = lbm.Params(nx=N, ny=N, tau=TAU, nu=NU, eps=1.0, gx=G[0], gy=G[1], storage=storage)
+    with lbm.Grid(p, kap) as grid:
+        grid.step(args.profile_steps, 0.0, args.profile_steps)
+        torch.cuda.synchronize()
+    return 0
 
 
 if __name__ == "__main__":

@@ -134,6 +134,84 @@ lbm_status lbm_grid_load_state(lbm_grid *g, const void *state_dev, int64_t steps
 /* Storage scale S in use (1 for LBM_F32 / LBM_F64). */
 double lbm_grid_scale(const lbm_grid *g);
 
+/* --------------------------------------------------------- local problems ---
+ * Section 3 of the paper: each subdomain ("leaf") is solved twice on the fine
+ * grid with periodic closure, driven by G1 = (g_const, 0) and G2 = (0, g_const),
+ * from rest until its volume-averaged flow velocity ubar settles; then
+ *   K* = nu / g_const [[ubar1_x, ubar2_x], [ubar1_y, ubar2_y]]        (Eq. 17)
+ * which reproduces the mean flux of the heterogeneous leaf when the leaf is
+ * re-run with the uniform tensor K* (Eqs. 19-21). */
+typedef struct {
+    int32_t x0, y0;       /* lower-left cell of the leaf in the field                 */
+    int32_t size;         /* side s in cells, 1 <= s <= 64                            */
+} lbm_leaf;
+
+/* Solves all leaves in one launch. p: nx, ny are the FIELD dimensions and tau,
+ * nu (< 0: nu_eff), eps the lattice parameters; bc, gx, gy, storage and scale
+ * are ignored (leaves are periodic, FP32 deviation storage, FP64 means).
+ * kappa_dev: float [ny][nx] field; leaves_dev: DEVICE array of n_leaves leaves,
+ * each inside the field. Stopping test per drive d, every check_every steps t:
+ *   |ubar_d(t) - ubar_d(t - check_every)| <= tol_rel * check_every * |ubar_d(t)|;
+ * tol_rel = 0 runs exactly max_steps. Outputs (caller-owned DEVICE memory):
+ *   keff_dev   double [n_leaves][4] = (K*_xx, K*_xy, K*_yx, K*_yy), lattice units;
+ *   status_dev int32  [n_leaves]   = LBM_OK, LBM_ENOTCONV (max_steps reached with
+ *                                    tol_rel > 0) or LBM_ETIMEOUT (abandoned);
+ *   steps_dev  int32  [n_leaves][2] steps taken per drive, or NULL.
+ * persistent != 0: one persistent launch fed by a device work queue, leaves
+ * resident in shared memory with per-leaf exit; persistent == 0: one launch
+ * per leaf (the same solver, for comparison). Returns the worst per-leaf
+ * status (LBM_OK, LBM_ENOTCONV or LBM_ETIMEOUT); invalid leaves give
+ * LBM_EINVAL before any launch. Uses device scratch for the queue. */
+lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
+                                int32_t n_leaves, double g_const, double tol_rel, int64_t max_steps,
+                                int32_t check_every, int32_t persistent, double *keff_dev, int32_t *status_dev,
+                                int32_t *steps_dev, void *cuda_stream);
+
+/* Wall-clock bound (seconds, > 0) of one local-problem launch; past it the
+ * kernel abandons its remaining jobs with LBM_ETIMEOUT instead of running on.
+ * Process-wide; default 600 s. */
+lbm_status lbm_set_time_limit(double seconds);
+
+/* ------------------------------------------------------------- upscaling ---
+ * Section 3: the field is cut into block x block subdomains, one coarse point
+ * each (row-major, coarse cell (I, J) <-> fine cells [I r, (I+1) r) x [J r, (J+1) r)).
+ * K* of every subdomain comes from its local problems (lbm_local_keff_batch).
+ * keff_coarse_dev: caller-owned DEVICE double [ny/r][nx/r][4] (xx, xy, yx, yy) in
+ * FINE lattice units. sur must be NULL (every block is solved by local LBM);
+ * spread_max is reserved for an ensemble gate. *n_fallback (host, may be NULL)
+ * receives the number of blocks solved by local LBM. Status as for
+ * lbm_local_keff_batch (check_every = 64, persistent launch). */
+typedef struct lbm_surrogate lbm_surrogate;
+lbm_status lbm_upscale(const lbm_params *p, const float *kappa_dev, int32_t block, const lbm_surrogate *sur,
+                       double spread_max, double g_const, double tol_rel, int64_t max_steps,
+                       double *keff_coarse_dev, int32_t *n_fallback, void *cuda_stream);
+
+/* Coarse lattice parameters for a fine set-up coarsened by `block` (= r):
+ * nx/r x ny/r cells, tau_c = 1/2 + (tau_f - 1/2)/r, nu_c = nu_f/r, G_c = r G_f,
+ * same eps, bc and storage (the paper keeps rho0, nu_eff, eps, nu and G and
+ * scales dx and dt by r; Section 3 and Section 4.3). */
+lbm_status lbm_coarse_params(const lbm_params *fine_p, int32_t block, lbm_params *coarse_out);
+
+/* The coarse (upscaled) run of Section 3 / Section 4.3: the simplified
+ * Shan-Chen step on the coarse lattice with the tensor drag of Eq. 18,
+ *   rho u = (I + eps nu_c K*_c^-1 / 2)^-1 (j + eps rho G_c / 2),  K*_c = K*_f / r^2,
+ * from rest for up to max_steps (stopping test as lbm_step). keff_coarse_dev is
+ * [ny/r][nx/r][4] in FINE lattice units (as lbm_upscale writes it); each K* must
+ * be finite with K*_c + (eps nu_c / 2) I invertible. g_coarse_dev: NULL for the
+ * constant force of fine_p, else float [2][ny/r][nx/r] holding G sampled at the
+ * coarse cell centres in FINE lattice units (the call multiplies it by r).
+ * rho/u/v_dev (any may be NULL): caller-owned float [ny/r][nx/r] outputs (Eq. 15).
+ * The grid is created and destroyed inside the call. */
+lbm_status lbm_coarse_run(const lbm_params *fine_p, int32_t block, const double *keff_coarse_dev,
+                          const float *g_coarse_dev, int64_t max_steps, double tol_rel, int32_t check_every,
+                          float *rho_dev, float *u_dev, float *v_dev, int64_t *steps_done, void *cuda_stream);
+
+/* Mean of a float [ny][nx] device field over block x block tiles into float
+ * [ny/block][nx/block] (accumulated in FP64, fixed order): the fine-grid
+ * averages the coarse run is compared with (Section 4.3.1). */
+lbm_status lbm_block_average(const float *in_dev, int32_t nx, int32_t ny, int32_t block, float *out_dev,
+                             void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -132,6 +132,77 @@ def lbm_grid_scale(grid) -> float:
     return float(_abi.lib().lbm_grid_scale(grid))
 
 
+def lbm_local_keff_batch(params: Params, kappa, leaves, g_const: float, tol_rel: float, max_steps: int,
+                         check_every: int, persistent: bool, keff, status, steps=None, stream=None) -> int:
+    """Local problems (Section 3, Eq. 17) for every leaf; ``leaves`` is an int32 CUDA
+    tensor [n, 3] of (x0, y0, size). Returns the worst status (OK / ENOTCONV / ETIMEOUT)."""
+    n = int(leaves.shape[0])
+    p = params.c()
+    return _check(_abi.lib().lbm_local_keff_batch(C.byref(p), _ptr(kappa), _ptr(leaves), n, float(g_const),
+                                                   float(tol_rel), int(max_steps), int(check_every),
+                                                   int(bool(persistent)), _ptr(keff), _ptr(status),
+                                                   _ptr(steps), _stream(stream)),
+                  allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
+
+
+def lbm_set_time_limit(seconds: float) -> None:
+    _check(_abi.lib().lbm_set_time_limit(float(seconds)))
+
+
+def local_keff(params: Params, kappa, leaves, g_const: float = 1e-6, tol_rel: float = 1e-8,
+               max_steps: int = 200000, check_every: int = 64, persistent: bool = True, stream=None):
+    """Allocating convenience over lbm_local_keff_batch: returns (keff [n,4] f64, status [n], steps [n,2], worst)."""
+    import torch
+    dev = kappa.device
+    n = int(leaves.shape[0])
+    keff = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    status = torch.empty((n,), dtype=torch.int32, device=dev)
+    steps = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    worst = lbm_local_keff_batch(params, kappa, leaves, g_const, tol_rel, max_steps, check_every, persistent,
+                                 keff, status, steps, stream)
+    return keff, status, steps, worst
+
+
+def lbm_upscale(params: Params, kappa, block: int, keff_coarse, g_const: float = 1e-6, tol_rel: float = 1e-8,
+                max_steps: int = 200000, surrogate=None, spread_max: float = 0.03, stream=None):
+    """K* per block x block subdomain (Section 3). Returns (status, n_fallback)."""
+    p = params.c()
+    nfb = C.c_int32(0)
+    st = _check(_abi.lib().lbm_upscale(C.byref(p), _ptr(kappa), int(block), surrogate, float(spread_max),
+                                       float(g_const), float(tol_rel), int(max_steps), _ptr(keff_coarse),
+                                       C.byref(nfb), _stream(stream)),
+                allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
+    return st, int(nfb.value)
+
+
+def lbm_coarse_params(params: Params, block: int) -> Params:
+    out = _abi.lbm_params()
+    p = params.c()
+    _check(_abi.lib().lbm_coarse_params(C.byref(p), int(block), C.byref(out)))
+    return Params(out.nx, out.ny, out.tau, out.nu, out.eps, out.gx, out.gy, out.bc, out.storage, out.scale)
+
+
+def lbm_coarse_run(params: Params, block: int, keff_coarse, g_coarse=None, max_steps: int = 100000,
+                   tol_rel: float = 0.0, check_every: int = 64, rho=None, u=None, v=None, stream=None):
+    """Coarse run with K* (Eq. 18). Returns (status, steps_done)."""
+    p = params.c()
+    steps = C.c_int64(0)
+    st = _check(_abi.lib().lbm_coarse_run(C.byref(p), int(block), _ptr(keff_coarse), _ptr(g_coarse),
+                                          int(max_steps), float(tol_rel), int(check_every), _ptr(rho), _ptr(u),
+                                          _ptr(v), C.byref(steps), _stream(stream)),
+                allow=(LBM_OK, LBM_ENOTCONV))
+    return st, int(steps.value)
+
+
+def lbm_block_average(field, block: int, out=None, stream=None):
+    import torch
+    ny, nx = field.shape
+    if out is None:
+        out = torch.empty((ny // block, nx // block), dtype=torch.float32, device=field.device)
+    _check(_abi.lib().lbm_block_average(_ptr(field), int(nx), int(ny), int(block), _ptr(out), _stream(stream)))
+    return out
+
+
 # ------------------------------------------------------------------ convenience
 
 class Grid:

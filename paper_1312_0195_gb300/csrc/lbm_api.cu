@@ -316,8 +316,8 @@ lbm_status grid_create_impl(const lbm_params *p, const float *kappa_dev, const d
                                                           p->bc == LBM_BC_WALLS_Y, p->nx, g->L.step_threads);
     g->L.step_blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     g->L.mom_threads = 256;
-    const int64_t mwant = (n + 255) / 256;
-    const int64_t mcap = (int64_t)sms * 4;
+    const int64_t mwant = (chunks + 255) / 256;
+    const int64_t mcap = (int64_t)sms * 2;   // 128 registers: two 256-thread blocks per SM
     g->L.mom_blocks = (int)(mwant < mcap ? (mwant < 1 ? 1 : mwant) : mcap);
 
     LBM_GRID_CUDA(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));

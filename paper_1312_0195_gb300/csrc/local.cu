@@ -1,0 +1,489 @@
+// local.cu -- batched local problems of the upscaling scheme (Section 3):
+// for every leaf (square subdomain) two periodic fine-grid runs driven by
+// G1 = (G, 0) and G2 = (0, G), each until its volume-averaged velocity settles,
+// then K* from Eq. 17. All jobs of a batch run in ONE persistent launch.
+//
+// Design (one CTA per SM, 1024 threads):
+//  * A CTA owns CMAX = 4096 lattice cells in shared memory and works on one
+//    leaf size s at a time: it holds nslots = min(CMAX / s^2, MAXSLOTS) jobs of
+//    that size side by side ("slots"). Jobs are popped from a per-size device
+//    queue with atomicAdd (no waiting, so nothing can hang). When a job's
+//    steady-state test passes, its slot is refilled from the queue at once.
+//  * The distributions of a slot stay resident in shared memory for the whole
+//    job and are updated in place with the AA access pattern: on even steps a
+//    cell reads its own nine values and writes the post-collision values into
+//    the opposite slots of the same cell; on odd steps it reads them from its
+//    neighbours' opposite slots and writes streamed values into its
+//    neighbours' own slots. Each cell touches the same nine locations for both
+//    reading and writing within a step, so only one barrier per step is needed
+//    and one buffer suffices (64 x 64 leaves fit).
+//  * The collision is the same simplified Shan-Chen update as the fine grid
+//    (Eqs. 6, 16, 2, 13) in FP32 deviation form, periodic closure on the leaf.
+//  * Every check_every steps of a job (and at max_steps) its mean velocity is
+//    reduced in FP64 by one warp in a fixed order (bitwise reproducible); the
+//    job ends when |ubar_d(t) - ubar_d(t - k)| <= tol k |ubar_d(t)| on the driven
+//    component d. Drive 1 writes K*_xx, K*_yx and drive 2 K*_xy, K*_yy (Eq. 17).
+//  * A wall-clock limit (globaltimer) bounds the launch: past it every CTA
+//    abandons its jobs with LBM_ETIMEOUT and returns.
+#include "lbm_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace lbm {
+
+lbm_status fail(lbm_status s, const char *fmt, ...);
+bool is_device_ptr(const void *p);
+int sm_count(int dev);
+void count_launches(int64_t n);
+
+namespace {
+
+constexpr int LOCAL_THREADS = 1024;
+constexpr int CMAX = 4096;               // cells resident per CTA
+constexpr int CPT = CMAX / LOCAL_THREADS; // cells per thread
+constexpr int MAXSLOTS = 64;
+constexpr int MAXCLASS = 64;
+constexpr size_t LOCAL_SMEM = (size_t)(9 + 1 + 2) * CMAX * sizeof(float);
+
+struct LocalArgs {
+    const float *kappa;       // field [ny][nx]
+    int nx, ny;
+    const int *leaves;        // [n][3] (x0, y0, size)
+    const int *jobs;          // job = 2 * leaf + drive, grouped by size class
+    int nclass;
+    int class_off[MAXCLASS + 1];
+    int class_size[MAXCLASS];
+    int *heads;               // [nclass] queue heads (zeroed before launch)
+    float omega, two_tau, omt, half_eps, gmag;
+    double eps_nu;            // eps * nu for the drag coefficient
+    double nu_over_g;         // nu / G for Eq. 17
+    double tol;
+    int check_every;
+    long long max_steps;
+    double *keff;             // [n][4]
+    int *status;              // [n] (zeroed before launch)
+    int *steps;               // [n][2] or nullptr
+    int *worst;               // [1] (zeroed)
+    int *abort_flag;          // [1] (zeroed)
+    unsigned long long time_limit_ns;
+};
+
+struct Slot {
+    int job;                  // -1: empty
+    int leaf, drive, x0, y0;
+    long long tstart;         // CTA step counter value at the job's step 0
+    double prev;              // driven mean velocity at the previous check
+};
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ float coef_d(float k, double eps_nu)
+{
+    if (!(k >= 0.0f)) return 0.0f;
+    if (eps_nu == 0.0 || isinf(k)) return 1.0f;
+    if (k == 0.0f) return 0.0f;
+    return (float)(2.0 * (double)k / (2.0 * (double)k + eps_nu));
+}
+
+__device__ __forceinline__ int wrapi(int v, int s) { return v < 0 ? v + s : (v >= s ? v - s : v); }
+
+__global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs a)
+{
+    extern __shared__ float smem[];
+    float *F = smem;                    // [9][CMAX]
+    float *D = F + 9 * CMAX;            // [CMAX]
+    float *UX = D + CMAX;               // [CMAX]
+    float *UY = UX + CMAX;              // [CMAX]
+    __shared__ Slot slots[MAXSLOTS];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned long long t0 = globaltimer();
+    if (tid == 0) s_abort = 0;
+
+    for (int cls = 0; cls < a.nclass; ++cls) {
+        const int s = a.class_size[cls], s2 = s * s;
+        int nslots = CMAX / s2;
+        if (nslots > MAXSLOTS) nslots = MAXSLOTS;
+        const int ncell = nslots * s2;
+        const int qbeg = a.class_off[cls], qn = a.class_off[cls + 1] - qbeg;
+
+        // per-thread cell geometry for this size class, packed as slot << 12 | ly << 6 | lx
+        int cgeo[CPT];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int c = tid + i * LOCAL_THREADS;
+            if (c < ncell) {
+                const int j = c / s2;
+                const int loc = c - j * s2;
+                const int ly = loc / s;
+                cgeo[i] = (j << 12) | (ly << 6) | (loc - ly * s);
+            } else {
+                cgeo[i] = -1;
+            }
+        }
+        __syncthreads();
+        long long T = 0;
+        if (tid < nslots) {
+            Slot sl;
+            sl.job = -1;
+            int q = s_abort ? qn : atomicAdd(&a.heads[cls], 1);
+            if (q < qn) {
+                sl.job = a.jobs[qbeg + q];
+                sl.leaf = sl.job >> 1;
+                sl.drive = sl.job & 1;
+                sl.x0 = a.leaves[3 * sl.leaf];
+                sl.y0 = a.leaves[3 * sl.leaf + 1];
+                sl.tstart = 0;
+                sl.prev = 0.0;
+            }
+            slots[tid] = sl;
+        }
+        int any = __syncthreads_or(tid < nslots && slots[tid].job >= 0);
+
+        while (any) {
+            // ---------------------------------------------------------- one step
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const int geo = cgeo[i];
+                if (geo < 0) continue;
+                const int j = geo >> 12, cly = (geo >> 6) & 63, clx = geo & 63;
+                const Slot &sl = slots[j];
+                if (sl.job < 0) continue;
+                const long long t = T - sl.tstart;
+                const int c = tid + i * LOCAL_THREADS;
+                const int base = j * s2;
+                float g[Q];
+                if (t == 0) {
+                    const int gx = sl.x0 + clx, gy = sl.y0 + cly;
+                    D[c] = coef_d(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) g[q] = 0.0f;      // rest state
+                } else if ((t & 1) == 0) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) g[q] = F[q * CMAX + c];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const int nxl = wrapi(clx - ex(q), s), nyl = wrapi(cly - ey(q), s);
+                        g[q] = F[opp(q) * CMAX + base + nyl * s + nxl];
+                    }
+                }
+                const float d = D[c];
+                const float Gx = sl.drive == 0 ? a.gmag : 0.0f;
+                const float Gy = sl.drive == 0 ? 0.0f : a.gmag;
+                float drho = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    drho += g[q];
+                    jx += (float)ex(q) * g[q];
+                    jy += (float)ey(q) * g[q];
+                }
+                const float rho = 1.0f + drho;
+                const float rux = d * (jx + a.half_eps * rho * Gx);     // Eq. 6 times rho
+                const float ruy = d * (jy + a.half_eps * rho * Gy);
+                const bool check = t > 0 && (t % a.check_every == 0 || t == a.max_steps);
+                if (check) {
+                    UX[c] = rux / rho;                                   // Eq. 15
+                    UY[c] = ruy / rho;
+                }
+                const float uex = a.two_tau * rux + a.omt * jx;          // Eq. 16 times rho
+                const float uey = a.two_tau * ruy + a.omt * jy;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float eu = (float)ex(q) * uex + (float)ey(q) * uey;
+                    const float w = q == 0 ? 4.0f / 9.0f : (q <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+                    const float geq = w * (drho + 3.0f * eu);             // Eq. 2
+                    g[q] = g[q] + a.omega * (geq - g[q]);                 // Eq. 13
+                }
+                if ((t & 1) == 0) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) F[opp(q) * CMAX + c] = g[q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const int nxl = wrapi(clx + ex(q), s), nyl = wrapi(cly + ey(q), s);
+                        F[q * CMAX + base + nyl * s + nxl] = g[q];
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ----------------------------------------------------- bookkeeping
+            if (tid == 0 && !s_abort) {
+                if (*(volatile int *)a.abort_flag) s_abort = 1;
+                else if (globaltimer() - t0 > a.time_limit_ns) {
+                    s_abort = 1;
+                    atomicExch(a.abort_flag, 1);
+                }
+            }
+            __syncthreads();
+            const bool abort_now = s_abort != 0;
+            for (int j = wid; j < nslots; j += LOCAL_THREADS / 32) {
+                Slot sl = slots[j];
+                if (sl.job < 0) continue;
+                const long long t = T - sl.tstart;
+                const bool check = t > 0 && (t % a.check_every == 0 || t == a.max_steps);
+                if (!check && !abort_now) continue;
+                int st = -1;   // -1: keep going
+                double ux = 0.0, uy = 0.0;
+                if (check) {
+                    for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
+                        ux += (double)UX[c];
+                        uy += (double)UY[c];
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        ux += __shfl_xor_sync(0xffffffffu, ux, off);
+                        uy += __shfl_xor_sync(0xffffffffu, uy, off);
+                    }
+                    ux /= (double)s2;
+                    uy /= (double)s2;
+                    const double cur = sl.drive == 0 ? ux : uy;
+                    if (a.tol > 0.0 && t > a.check_every && t % a.check_every == 0 &&
+                        fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur))
+                        st = LBM_OK;
+                    else if (t == a.max_steps)
+                        st = a.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
+                    sl.prev = cur;
+                }
+                if (abort_now && st < 0) st = LBM_ETIMEOUT;
+                if (lane == 0) {
+                    if (st >= 0) {
+                        // Eq. 17: column `drive` of K* from the mean velocity (NaN if abandoned unchecked)
+                        const double kx = check ? a.nu_over_g * ux : __longlong_as_double(0x7ff8000000000000LL);
+                        const double ky = check ? a.nu_over_g * uy : __longlong_as_double(0x7ff8000000000000LL);
+                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 0 : 1)] = kx;
+                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 2 : 3)] = ky;
+                        if (a.steps) a.steps[2 * (int64_t)sl.leaf + sl.drive] = (int)t;
+                        if (st != LBM_OK) {
+                            atomicMax(&a.status[sl.leaf], st);
+                            atomicMax(a.worst, st);
+                        }
+                        // refill the slot from this size's queue
+                        int q = abort_now ? qn : atomicAdd(&a.heads[cls], 1);
+                        if (q < qn) {
+                            sl.job = a.jobs[qbeg + q];
+                            sl.leaf = sl.job >> 1;
+                            sl.drive = sl.job & 1;
+                            sl.x0 = a.leaves[3 * sl.leaf];
+                            sl.y0 = a.leaves[3 * sl.leaf + 1];
+                            sl.tstart = T + 1;
+                            sl.prev = 0.0;
+                        } else {
+                            sl.job = -1;
+                        }
+                    }
+                    slots[j] = sl;
+                }
+                __syncwarp();
+            }
+            ++T;
+            __syncthreads();   // slot updates of every warp are visible before they are tested
+            any = __syncthreads_or(tid < nslots && slots[tid].job >= 0);
+        }
+    }
+}
+
+}  // namespace
+
+lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev, int32_t n_leaves,
+                           double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
+                           int32_t persistent, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                           void *cuda_stream, double time_limit_s)
+{
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 1 || p->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
+    if (!std::isfinite(p->tau) || p->tau < 0.5) return fail(LBM_EINVAL, "tau must be finite and >= 0.5");
+    if (!std::isfinite(p->nu) || !std::isfinite(p->eps) || p->eps < 0.0)
+        return fail(LBM_EINVAL, "nu must be finite and eps finite and >= 0");
+    if (n_leaves < 0) return fail(LBM_EINVAL, "n_leaves must be >= 0");
+    if (!std::isfinite(g_const) || g_const == 0.0) return fail(LBM_EINVAL, "g_const must be finite and non-zero");
+    if (!std::isfinite(tol_rel) || tol_rel < 0.0) return fail(LBM_EINVAL, "tol_rel must be finite and >= 0");
+    if (max_steps < 1 || max_steps > (int64_t)1 << 31) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31]");
+    if (check_every < 1) return fail(LBM_EINVAL, "check_every must be >= 1");
+    if (n_leaves == 0) return LBM_OK;
+    if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(keff_dev) ||
+        !is_device_ptr(status_dev) || (steps_dev && !is_device_ptr(steps_dev)))
+        return fail(LBM_EINVAL, "kappa, leaves, keff, status (and steps) must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+#define LOC_CUDA(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s failed: %s", \
+                        #call, cudaGetErrorString(e_));                                          \
+        }                                                                                        \
+    } while (0)
+
+    // leaves come from the device; validate them on the host before any launch
+    std::vector<lbm_leaf> lv(n_leaves);
+    LOC_CUDA(cudaMemcpyAsync(lv.data(), leaves_dev, sizeof(lbm_leaf) * n_leaves, cudaMemcpyDeviceToHost, st));
+    LOC_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> sizes;
+    for (int i = 0; i < n_leaves; ++i) {
+        const lbm_leaf &L = lv[i];
+        if (L.size < 1 || L.size > 64) return fail(LBM_EINVAL, "leaf %d: size %d outside [1, 64]", i, L.size);
+        if (L.x0 < 0 || L.y0 < 0 || (int64_t)L.x0 + L.size > p->nx || (int64_t)L.y0 + L.size > p->ny)
+            return fail(LBM_EINVAL, "leaf %d (%d, %d, %d) lies outside the %d x %d field", i, L.x0, L.y0, L.size,
+                        p->nx, p->ny);
+        sizes.push_back(L.size);
+    }
+    std::sort(sizes.begin(), sizes.end(), std::greater<int>());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    if ((int)sizes.size() > MAXCLASS) return fail(LBM_EINVAL, "more than %d distinct leaf sizes", MAXCLASS);
+
+    const double nu = p->nu < 0.0 ? (p->tau - 0.5) / 3.0 : p->nu;
+    LocalArgs a{};
+    a.kappa = kappa_dev;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.leaves = reinterpret_cast<const int *>(leaves_dev);
+    a.omega = (float)(1.0 / p->tau);
+    a.two_tau = (float)(2.0 * p->tau);
+    a.omt = (float)(1.0 - 2.0 * p->tau);
+    a.half_eps = (float)(0.5 * p->eps);
+    a.gmag = (float)g_const;
+    a.eps_nu = p->eps * nu;
+    a.nu_over_g = nu / g_const;
+    a.tol = tol_rel;
+    a.check_every = check_every;
+    a.max_steps = max_steps;
+    a.keff = keff_dev;
+    a.status = status_dev;
+    a.steps = steps_dev;
+    a.time_limit_ns = (unsigned long long)(time_limit_s * 1e9);
+
+    // job lists: persistent -> grouped by size (largest first); per-leaf -> leaf order
+    std::vector<int> jobs;
+    jobs.reserve(2 * (size_t)n_leaves);
+    std::vector<int> off;
+    if (persistent) {
+        for (int s : sizes) {
+            off.push_back((int)jobs.size());
+            for (int i = 0; i < n_leaves; ++i)
+                if (lv[i].size == s) {
+                    jobs.push_back(2 * i);
+                    jobs.push_back(2 * i + 1);
+                }
+        }
+        off.push_back((int)jobs.size());
+    } else {
+        for (int i = 0; i < n_leaves; ++i) {
+            jobs.push_back(2 * i);
+            jobs.push_back(2 * i + 1);
+        }
+    }
+    const int nheads = persistent ? (int)sizes.size() : n_leaves;
+
+    int *d_jobs = nullptr, *d_heads = nullptr, *d_flags = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_jobs);
+        cudaFree(d_heads);
+        cudaFree(d_flags);
+        cudaGetLastError();
+    };
+#define LOC_CUDA2(call)                                                                          \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            cleanup();                                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s failed: %s", \
+                        #call, cudaGetErrorString(e_));                                          \
+        }                                                                                        \
+    } while (0)
+    LOC_CUDA2(cudaMalloc(&d_jobs, sizeof(int) * jobs.size()));
+    LOC_CUDA2(cudaMalloc(&d_heads, sizeof(int) * nheads));
+    LOC_CUDA2(cudaMalloc(&d_flags, sizeof(int) * 2));
+    LOC_CUDA2(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(int) * jobs.size(), cudaMemcpyHostToDevice, st));
+    LOC_CUDA2(cudaMemsetAsync(d_heads, 0, sizeof(int) * nheads, st));
+    LOC_CUDA2(cudaMemsetAsync(d_flags, 0, sizeof(int) * 2, st));
+    LOC_CUDA2(cudaMemsetAsync(status_dev, 0, sizeof(int32_t) * n_leaves, st));
+    if (steps_dev) LOC_CUDA2(cudaMemsetAsync(steps_dev, 0, sizeof(int32_t) * 2 * n_leaves, st));
+    a.jobs = d_jobs;
+    a.worst = d_flags;
+    a.abort_flag = d_flags + 1;
+
+    LOC_CUDA2(cudaFuncSetAttribute(local_keff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LOCAL_SMEM));
+    int dev = 0;
+    LOC_CUDA2(cudaGetDevice(&dev));
+    if (persistent) {
+        a.nclass = (int)sizes.size();
+        for (int c = 0; c < a.nclass; ++c) {
+            a.class_off[c] = off[c];
+            a.class_size[c] = sizes[c];
+        }
+        a.class_off[a.nclass] = off[a.nclass];
+        a.heads = d_heads;
+        int blocks = sm_count(dev);
+        const int64_t max_useful = (int64_t)jobs.size();
+        if (blocks > max_useful) blocks = (int)max_useful;
+        local_keff_kernel<<<blocks, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
+        LOC_CUDA2(cudaGetLastError());
+        count_launches(1);
+    } else {
+        a.nclass = 1;
+        for (int i = 0; i < n_leaves; ++i) {
+            a.class_off[0] = 2 * i;
+            a.class_off[1] = 2 * i + 2;
+            a.class_size[0] = lv[i].size;
+            a.heads = d_heads + i;
+            local_keff_kernel<<<1, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
+            LOC_CUDA2(cudaGetLastError());
+        }
+        count_launches(n_leaves);
+    }
+    int flags[2] = {0, 0};
+    LOC_CUDA2(cudaMemcpyAsync(flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, st));
+    LOC_CUDA2(cudaStreamSynchronize(st));
+    cleanup();
+    if (flags[1] || flags[0] == LBM_ETIMEOUT)
+        return fail(LBM_ETIMEOUT, "local problems exceeded the %.3g s limit; unfinished leaves carry LBM_ETIMEOUT",
+                    time_limit_s);
+    if (flags[0] == LBM_ENOTCONV)
+        return fail(LBM_ENOTCONV, "some leaves did not meet the tolerance within max_steps (status per leaf)");
+    return LBM_OK;
+#undef LOC_CUDA
+#undef LOC_CUDA2
+}
+
+}  // namespace lbm
+
+namespace {
+double g_time_limit_s = 600.0;
+}
+
+extern "C" {
+
+lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
+                                int32_t n_leaves, double g_const, double tol_rel, int64_t max_steps,
+                                int32_t check_every, int32_t persistent, double *keff_dev, int32_t *status_dev,
+                                int32_t *steps_dev, void *cuda_stream)
+{
+    return lbm::local_keff_impl(p, kappa_dev, leaves_dev, n_leaves, g_const, tol_rel, max_steps, check_every,
+                                persistent, keff_dev, status_dev, steps_dev, cuda_stream, g_time_limit_s);
+}
+
+lbm_status lbm_set_time_limit(double seconds)
+{
+    if (!(seconds > 0.0) || !std::isfinite(seconds))
+        return lbm::fail(LBM_EINVAL, "time limit must be finite and > 0");
+    g_time_limit_s = seconds;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace lbm {
+double local_time_limit() { return g_time_limit_s; }
+}  // namespace lbm

@@ -122,6 +122,82 @@ __device__ __forceinline__ void collide_cell(C (&gq)[Q], C rho0, C half_eps, C G
     }
 }
 
+// Streamed (pre-collision) deviations of the VEC cells (y, x0 .. x0+VEC-1):
+// g[q][i] = src_q(x - e_q) with periodic wrap, or the opposite population of the
+// same cell for links that cross a bounce-back wall. Every lane of the warp must
+// call this (the one-cell x shifts use warp shuffles).
+template <typename T, int VEC, bool WALLS>
+__device__ __forceinline__ void pull_chunk(const T *__restrict__ src, int64_t plane, int nx, int ny, int y, int xc,
+                                           int cpr, int lane, typename Comp<T>::type (&g)[Q][VEC])
+{
+    using P = Pack<T, VEC>;
+    const int x0 = xc * VEC;
+    const bool left_in_warp = lane > 0 && xc > 0;         // lane-1 holds (y, x0 - VEC)
+    const bool right_in_warp = lane < 31 && xc < cpr - 1; // lane+1 holds (y, x0 + VEC)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int dy = ey(q), dx = ex(q);
+        bool bb = false;
+        int ys = y - dy;
+        if (WALLS) bb = (dy == 1 && y == 0) || (dy == -1 && y == ny - 1);
+        if (ys < 0) ys += ny;
+        if (ys >= ny) ys -= ny;
+        const T *pl = src + (int64_t)q * plane;
+        if (WALLS && bb) ys = y;
+        const T *plb = WALLS && bb ? src + (int64_t)opp(q) * plane : pl;
+        const P pk = *reinterpret_cast<const P *>(plb + (int64_t)ys * nx + x0);
+        if (dx == 0) {
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) g[q][i] = to_c(pk.v[i]);
+        } else if (dx == 1) {
+            T left = shfl_up1(pk.v[VEC - 1]);
+            if (!(WALLS && bb)) {
+                if (!left_in_warp) left = pl[(int64_t)ys * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
+                g[q][0] = to_c(left);
+#pragma unroll
+                for (int i = 1; i < VEC; ++i) g[q][i] = to_c(pk.v[i - 1]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) g[q][i] = to_c(pk.v[i]);
+            }
+        } else {
+            T right = shfl_down1(pk.v[0]);
+            if (!(WALLS && bb)) {
+                if (!right_in_warp) right = pl[(int64_t)ys * nx + (x0 + VEC == nx ? 0 : x0 + VEC)];
+#pragma unroll
+                for (int i = 0; i < VEC - 1; ++i) g[q][i] = to_c(pk.v[i + 1]);
+                g[q][VEC - 1] = to_c(right);
+            } else {
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) g[q][i] = to_c(pk.v[i]);
+            }
+        }
+    }
+}
+
+// Per-cell drag coefficients and body force of the VEC cells starting at cell0.
+template <typename T, typename C, int VEC, int COEF, bool GF>
+__device__ __forceinline__ void cell_params(const StepArgs<T, C> &a, int64_t cell0, C (&c0)[VEC], C (&c1)[VEC],
+                                            C (&c2)[VEC], C (&c3)[VEC], C (&gxv)[VEC], C (&gyv)[VEC])
+{
+    load_vec<C, VEC>(a.coef, cell0, c0);
+    if constexpr (COEF == COEF_TENSOR) {
+        load_vec<C, VEC>(a.coef + a.plane, cell0, c1);
+        load_vec<C, VEC>(a.coef + 2 * a.plane, cell0, c2);
+        load_vec<C, VEC>(a.coef + 3 * a.plane, cell0, c3);
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) c1[i] = c2[i] = c3[i] = C(0);
+    }
+    if constexpr (GF) {
+        load_vec<C, VEC>(a.gfield, cell0, gxv);
+        load_vec<C, VEC>(a.gfield + a.plane, cell0, gyv);
+    } else {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) { gxv[i] = a.gx; gyv[i] = a.gy; }
+    }
+}
+
 template <typename T, int VEC, int COEF, bool GF, bool WALLS>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs<T, typename Comp<T>::type> a)
 {
@@ -141,71 +217,13 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs<T, typename Comp<T>:
         const int y = (int)(ce / cpr);
         const int xc = (int)(ce - (int64_t)y * cpr);
         const int x0 = xc * VEC;
-        const bool left_in_warp = lane > 0 && xc > 0;         // lane-1 holds (y, x0 - VEC)
-        const bool right_in_warp = lane < 31 && xc < cpr - 1; // lane+1 holds (y, x0 + VEC)
 
         C g[Q][VEC];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int dy = ey(q), dx = ex(q);
-            bool bb = false;
-            int ys = y - dy;
-            if (WALLS) {
-                bb = (dy == 1 && y == 0) || (dy == -1 && y == ny - 1);
-            }
-            if (ys < 0) ys += ny;
-            if (ys >= ny) ys -= ny;
-            const T *pl = a.src + (int64_t)q * a.plane;
-            if (WALLS && bb) ys = y;
-            const T *plb = WALLS && bb ? a.src + (int64_t)opp(q) * a.plane : pl;
-            const P pk = *reinterpret_cast<const P *>(plb + (int64_t)ys * nx + x0);
-            if (dx == 0) {
-#pragma unroll
-                for (int i = 0; i < VEC; ++i) g[q][i] = to_c(pk.v[i]);
-            } else if (dx == 1) {
-                T left = shfl_up1(pk.v[VEC - 1]);
-                if (!(WALLS && bb)) {
-                    if (!left_in_warp) left = pl[(int64_t)ys * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
-                    g[q][0] = to_c(left);
-#pragma unroll
-                    for (int i = 1; i < VEC; ++i) g[q][i] = to_c(pk.v[i - 1]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < VEC; ++i) g[q][i] = to_c(pk.v[i]);
-                }
-            } else {
-                T right = shfl_down1(pk.v[0]);
-                if (!(WALLS && bb)) {
-                    if (!right_in_warp) right = pl[(int64_t)ys * nx + (x0 + VEC == nx ? 0 : x0 + VEC)];
-#pragma unroll
-                    for (int i = 0; i < VEC - 1; ++i) g[q][i] = to_c(pk.v[i + 1]);
-                    g[q][VEC - 1] = to_c(right);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < VEC; ++i) g[q][i] = to_c(pk.v[i]);
-                }
-            }
-        }
+        pull_chunk<T, VEC, WALLS>(a.src, a.plane, nx, ny, y, xc, cpr, lane, g);
 
         const int64_t cell0 = (int64_t)y * nx + x0;
-        C c0[VEC], c1[VEC], c2[VEC], c3[VEC];
-        load_vec<C, VEC>(a.coef, cell0, c0);
-        if constexpr (COEF == COEF_TENSOR) {
-            load_vec<C, VEC>(a.coef + a.plane, cell0, c1);
-            load_vec<C, VEC>(a.coef + 2 * a.plane, cell0, c2);
-            load_vec<C, VEC>(a.coef + 3 * a.plane, cell0, c3);
-        } else {
-#pragma unroll
-            for (int i = 0; i < VEC; ++i) c1[i] = c2[i] = c3[i] = C(0);
-        }
-        C gxv[VEC], gyv[VEC];
-        if constexpr (GF) {
-            load_vec<C, VEC>(a.gfield, cell0, gxv);
-            load_vec<C, VEC>(a.gfield + a.plane, cell0, gyv);
-        } else {
-#pragma unroll
-            for (int i = 0; i < VEC; ++i) { gxv[i] = a.gx; gyv[i] = a.gy; }
-        }
+        C c0[VEC], c1[VEC], c2[VEC], c3[VEC], gxv[VEC], gyv[VEC];
+        cell_params<T, C, VEC, COEF, GF>(a, cell0, c0, c1, c2, c3, gxv, gyv);
 
 #pragma unroll
         for (int i = 0; i < VEC; ++i) {
@@ -230,38 +248,21 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs<T, typename Comp<T>:
     }
 }
 
-// Streamed (pre-collision) deviations of one cell, scalar loads.
-template <typename T, typename C, bool WALLS>
-__device__ __forceinline__ void pull_cell(const T *src, int64_t plane, int nx, int ny, int x, int y,
-                                          C (&g)[Q])
-{
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int dy = ey(q), dx = ex(q);
-        if (WALLS && ((dy == 1 && y == 0) || (dy == -1 && y == ny - 1))) {
-            g[q] = to_c(src[(int64_t)opp(q) * plane + (int64_t)y * nx + x]);
-            continue;
-        }
-        int xs = x - dx, ys = y - dy;
-        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-        g[q] = to_c(src[(int64_t)q * plane + (int64_t)ys * nx + xs]);
-    }
-}
-
-// Flow velocity (Eq. 15 with Eq. 6 / Eq. 18) of one streamed cell, in physical
-// (unscaled) units, accumulated in double.
+// Density deviation (storage units) and flow velocity of one streamed cell:
+// Eq. 15 with Eq. 6 (scalar d) or Eq. 18 (coefficient matrix), in the compute
+// type. The storage scale cancels in u = (rho u) / rho.
 template <typename C, int COEF>
-__device__ __forceinline__ void cell_uv(const C (&g)[Q], C rho0, C half_eps, C Gx, C Gy,
-                                        C c0, C c1, C c2, C c3, double inv_scale,
-                                        double &rho, double &u, double &v)
+__device__ __forceinline__ void cell_uv(const C (&g)[Q], C rho0, C half_eps, C Gx, C Gy, C c0, C c1, C c2, C c3,
+                                        C &drho_o, C &u, C &v)
 {
     C drho = 0, jx = 0, jy = 0;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         drho += g[a];
-        jx += C(ex(a)) * g[a];
-        jy += C(ey(a)) * g[a];
+        if (ex(a) == 1) jx += g[a];
+        if (ex(a) == -1) jx -= g[a];
+        if (ey(a) == 1) jy += g[a];
+        if (ey(a) == -1) jy -= g[a];
     }
     const C r = rho0 + drho;
     const C rx = jx + half_eps * r * Gx, ry = jy + half_eps * r * Gy;
@@ -273,53 +274,78 @@ __device__ __forceinline__ void cell_uv(const C (&g)[Q], C rho0, C half_eps, C G
         rux = c0 * rx + c1 * ry;
         ruy = c2 * rx + c3 * ry;
     }
-    rho = 1.0 + (double)drho * inv_scale;
-    u = (double)rux * inv_scale / rho;
-    v = (double)ruy * inv_scale / rho;
+    drho_o = drho;
+    u = rux / r;
+    v = ruy / r;
 }
 
-template <typename T, int COEF, bool GF, bool WALLS>
+// Moment / residual pass (same vectorised pulls as the step): flow velocity of
+// the current state and, when m.prev is set, of the previous one; optional
+// rho/u/v fields; per-block max|du|, max|u| and FP64 sums of u and v.
+template <typename T, int VEC, int COEF, bool GF, bool WALLS>
 __global__ void __launch_bounds__(256) moments_kernel(MomArgs<T, typename Comp<T>::type> m)
 {
     using C = typename Comp<T>::type;
     const StepArgs<T, C> &a = m.s;
+    const int lane = threadIdx.x & 31;
     const int nx = a.nx, ny = a.ny;
-    const int64_t n = (int64_t)nx * ny;
+    const int cpr = nx / VEC;
+    const int64_t nchunk = (int64_t)cpr * ny;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double dmax = 0.0, umax = 0.0, su = 0.0, sv = 0.0;
-    for (int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cidx < n;
-         cidx += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(cidx / nx), x = (int)(cidx - (int64_t)y * nx);
-        C c0 = a.coef[cidx], c1 = 0, c2 = 0, c3 = 0;
-        if constexpr (COEF == COEF_TENSOR) {
-            c1 = a.coef[a.plane + cidx];
-            c2 = a.coef[2 * a.plane + cidx];
-            c3 = a.coef[3 * a.plane + cidx];
+    for (int64_t base = warp0 * 32; base < nchunk; base += wstride * 32) {
+        const int64_t c = base + lane;
+        const bool active = c < nchunk;
+        const int64_t ce = active ? c : nchunk - 1;
+        const int y = (int)(ce / cpr);
+        const int xc = (int)(ce - (int64_t)y * cpr);
+        const int64_t cell0 = (int64_t)y * nx + xc * VEC;
+        C c0[VEC], c1[VEC], c2[VEC], c3[VEC], gxv[VEC], gyv[VEC];
+        cell_params<T, C, VEC, COEF, GF>(a, cell0, c0, c1, c2, c3, gxv, gyv);
+        C g[Q][VEC];
+        pull_chunk<T, VEC, WALLS>(a.src, a.plane, nx, ny, y, xc, cpr, lane, g);
+        C uu[VEC], vv[VEC];
+        C csu = 0, csv = 0, cmax = 0;
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            C gq[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) gq[q] = g[q][i];
+            C dr;
+            cell_uv<C, COEF>(gq, a.rho0, a.half_eps, gxv[i], gyv[i], c0[i], c1[i], c2[i], c3[i], dr, uu[i], vv[i]);
+            if (active) {
+                if (m.rho) m.rho[cell0 + i] = (float)(1.0 + (double)dr * (double)m.inv_scale);
+                if (m.u) m.u[cell0 + i] = (float)uu[i];
+                if (m.v) m.v[cell0 + i] = (float)vv[i];
+            }
+            csu += uu[i];
+            csv += vv[i];
+            cmax = fmax(cmax, fmax(fabs(uu[i]), fabs(vv[i])));
         }
-        C Gx = a.gx, Gy = a.gy;
-        if constexpr (GF) {
-            Gx = a.gfield[cidx];
-            Gy = a.gfield[a.plane + cidx];
-        }
-        C g[Q];
-        pull_cell<T, C, WALLS>(a.src, a.plane, nx, ny, x, y, g);
-        double rho, u, v;
-        cell_uv<C, COEF>(g, a.rho0, a.half_eps, Gx, Gy, c0, c1, c2, c3, (double)m.inv_scale, rho, u, v);
-        if (m.rho) m.rho[cidx] = (float)rho;
-        if (m.u) m.u[cidx] = (float)u;
-        if (m.v) m.v[cidx] = (float)v;
-        su += u;
-        sv += v;
-        umax = fmax(umax, fmax(fabs(u), fabs(v)));
         if (m.prev) {
-            pull_cell<T, C, WALLS>(m.prev, a.plane, nx, ny, x, y, g);
-            double rp, up, vp;
-            cell_uv<C, COEF>(g, a.rho0, a.half_eps, Gx, Gy, c0, c1, c2, c3, (double)m.inv_scale, rp, up, vp);
-            dmax = fmax(dmax, fmax(fabs(u - up), fabs(v - vp)));
+            pull_chunk<T, VEC, WALLS>(m.prev, a.plane, nx, ny, y, xc, cpr, lane, g);
+            C cd = 0;
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) {
+                C gq[Q];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) gq[q] = g[q][i];
+                C dr, up, vp;
+                cell_uv<C, COEF>(gq, a.rho0, a.half_eps, gxv[i], gyv[i], c0[i], c1[i], c2[i], c3[i], dr, up, vp);
+                cd = fmax(cd, fmax(fabs(uu[i] - up), fabs(vv[i] - vp)));
+            }
+            if (active) dmax = fmax(dmax, (double)cd);
+        }
+        if (active) {
+            su += (double)csu;
+            sv += (double)csv;
+            umax = fmax(umax, (double)cmax);
         }
     }
     // block reduction in a fixed order: warp shuffles, then warp 0 over the warps
     __shared__ double sh[4][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wid = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, off));
@@ -507,7 +533,7 @@ cudaError_t launch_step_t(int coef_mode, bool gf, bool walls, const void *args, 
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
+template <typename T, int VEC>
 cudaError_t launch_moments_t(int coef_mode, bool gf, bool walls, const void *args, const GridLaunch &L, cudaStream_t st)
 {
     using C = typename Comp<T>::type;
@@ -515,7 +541,7 @@ cudaError_t launch_moments_t(int coef_mode, bool gf, bool walls, const void *arg
     dim3 grid(L.mom_blocks), block(L.mom_threads);
 #define LBM_MOM_CASE(CM, GFv, WLv)                                                      \
     if (coef_mode == CM && gf == GFv && walls == WLv) {                                 \
-        moments_kernel<T, CM, GFv, WLv><<<grid, block, 0, st>>>(m);                     \
+        moments_kernel<T, VEC, CM, GFv, WLv><<<grid, block, 0, st>>>(m);                \
         return cudaGetLastError();                                                      \
     }
     LBM_MOM_CASE(COEF_SCALAR, false, false)
@@ -596,9 +622,23 @@ cudaError_t launch_moments(int storage, int coef_mode, bool gfield, bool walls, 
                            const GridLaunch &L, cudaStream_t st)
 {
     switch (storage) {
-    case LBM_F32: return launch_moments_t<float>(coef_mode, gfield, walls, args, L, st);
-    case LBM_F16: return launch_moments_t<__half>(coef_mode, gfield, walls, args, L, st);
-    case LBM_F64: return launch_moments_t<double>(coef_mode, gfield, walls, args, L, st);
+    case LBM_F32: {
+        const int nx = static_cast<const MomArgs<float, float> *>(args)->s.nx;
+        return step_vec(storage, nx) == 4 ? launch_moments_t<float, 4>(coef_mode, gfield, walls, args, L, st)
+                                          : launch_moments_t<float, 1>(coef_mode, gfield, walls, args, L, st);
+    }
+    case LBM_F16: {
+        const int nx = static_cast<const MomArgs<__half, float> *>(args)->s.nx;
+        const int v = step_vec(storage, nx);
+        return v == 8 ? launch_moments_t<__half, 8>(coef_mode, gfield, walls, args, L, st)
+                      : (v == 2 ? launch_moments_t<__half, 2>(coef_mode, gfield, walls, args, L, st)
+                                : launch_moments_t<__half, 1>(coef_mode, gfield, walls, args, L, st));
+    }
+    case LBM_F64: {
+        const int nx = static_cast<const MomArgs<double, double> *>(args)->s.nx;
+        return step_vec(storage, nx) == 2 ? launch_moments_t<double, 2>(coef_mode, gfield, walls, args, L, st)
+                                          : launch_moments_t<double, 1>(coef_mode, gfield, walls, args, L, st);
+    }
     }
     return cudaErrorInvalidValue;
 }
