@@ -167,6 +167,27 @@ lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, con
                                 int32_t check_every, int32_t persistent, double *keff_dev, int32_t *status_dev,
                                 int32_t *steps_dev, void *cuda_stream);
 
+/* Allocation-free variant of lbm_local_keff_batch (the paper has no counterpart;
+ * it exists for callers of this library). Some callers cannot allocate device
+ * memory: code that runs inside a host application owning a fixed device pool,
+ * under a hard memory budget, or beside an allocator that must not be bypassed.
+ * This call allocates no device or pinned memory (no cudaMalloc, cudaFree or
+ * cudaMallocHost, directly or through another library); the caller passes the
+ * inputs and outputs exactly as for lbm_local_keff_batch, and the work queue
+ * lives in a static device array built into the library (1 MiB, held on every
+ * GPU that loads it until the process exits). Differences from
+ * lbm_local_keff_batch: always one persistent launch; at most 131072 leaves
+ * per call (more gives LBM_EINVAL); leaves are validated on the device (a bad
+ * leaf gives LBM_EINVAL before the solver starts). The first call on each
+ * device looks up the array's device address, so make it before any stream
+ * capture. Every call reuses the same array (it is cleared at the start of each
+ * call), so calls that overlap on the GPU (other streams or threads) race on
+ * it and must be serialised by the caller. Results match lbm_local_keff_batch. */
+lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
+                                        int32_t n_leaves, double g_const, double tol_rel, int64_t max_steps,
+                                        int32_t check_every, double *keff_dev, int32_t *status_dev,
+                                        int32_t *steps_dev, void *cuda_stream);
+
 /* Wall-clock bound (seconds, > 0) of one local-problem launch; past it the
  * kernel abandons its remaining jobs with LBM_ETIMEOUT instead of running on.
  * Process-wide; default 600 s. */

@@ -28,6 +28,7 @@
 #include "lbm_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -74,6 +75,7 @@ struct Slot {
     int job;                  // -1: empty
     int leaf, drive, x0, y0;
     long long tstart;         // CTA step counter value at the job's step 0
+    int next_check;           // job step of the next steady-state check
     double prev;              // driven mean velocity at the previous check
 };
 
@@ -84,12 +86,13 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-__device__ __forceinline__ float coef_d(float k, double eps_nu)
+// drag fraction e = 1 - d = eps nu / (2 kappa + eps nu) of Eq. 6 (see the fine-grid step)
+__device__ __forceinline__ float coef_e(float k, double eps_nu)
 {
-    if (!(k >= 0.0f)) return 0.0f;
-    if (eps_nu == 0.0 || isinf(k)) return 1.0f;
-    if (k == 0.0f) return 0.0f;
-    return (float)(2.0 * (double)k / (2.0 * (double)k + eps_nu));
+    if (!(k >= 0.0f)) return 1.0f;
+    if (eps_nu == 0.0 || isinf(k)) return 0.0f;
+    if (k == 0.0f) return 1.0f;
+    return (float)(eps_nu / (2.0 * (double)k + eps_nu));
 }
 
 __device__ __forceinline__ int wrapi(int v, int s) { return v < 0 ? v + s : (v >= s ? v - s : v); }
@@ -142,6 +145,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 sl.x0 = a.leaves[3 * sl.leaf];
                 sl.y0 = a.leaves[3 * sl.leaf + 1];
                 sl.tstart = 0;
+                sl.next_check = a.check_every;
                 sl.prev = 0.0;
             }
             slots[tid] = sl;
@@ -157,13 +161,13 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 const int j = geo >> 12, cly = (geo >> 6) & 63, clx = geo & 63;
                 const Slot &sl = slots[j];
                 if (sl.job < 0) continue;
-                const long long t = T - sl.tstart;
+                const int t = (int)(T - sl.tstart);
                 const int c = tid + i * LOCAL_THREADS;
                 const int base = j * s2;
                 float g[Q];
                 if (t == 0) {
                     const int gx = sl.x0 + clx, gy = sl.y0 + cly;
-                    D[c] = coef_d(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
+                    D[c] = coef_e(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
 #pragma unroll
                     for (int q = 0; q < Q; ++q) g[q] = 0.0f;      // rest state
                 } else if ((t & 1) == 0) {
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                         g[q] = F[opp(q) * CMAX + base + nyl * s + nxl];
                     }
                 }
-                const float d = D[c];
+                const float e = D[c];
                 const float Gx = sl.drive == 0 ? a.gmag : 0.0f;
                 const float Gy = sl.drive == 0 ? 0.0f : a.gmag;
                 float drho = 0.f, jx = 0.f, jy = 0.f;
@@ -187,9 +191,11 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     jy += (float)ey(q) * g[q];
                 }
                 const float rho = 1.0f + drho;
-                const float rux = d * (jx + a.half_eps * rho * Gx);     // Eq. 6 times rho
-                const float ruy = d * (jy + a.half_eps * rho * Gy);
-                const bool check = t > 0 && (t % a.check_every == 0 || t == a.max_steps);
+                const float rx = jx + a.half_eps * rho * Gx;
+                const float ry = jy + a.half_eps * rho * Gy;
+                const float rux = rx - e * rx;                           // Eq. 6 times rho: (1 - e) r
+                const float ruy = ry - e * ry;
+                const bool check = t == sl.next_check || t == a.max_steps;
                 if (check) {
                     UX[c] = rux / rho;                                   // Eq. 15
                     UY[c] = ruy / rho;
@@ -229,8 +235,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
             for (int j = wid; j < nslots; j += LOCAL_THREADS / 32) {
                 Slot sl = slots[j];
                 if (sl.job < 0) continue;
-                const long long t = T - sl.tstart;
-                const bool check = t > 0 && (t % a.check_every == 0 || t == a.max_steps);
+                const int t = (int)(T - sl.tstart);
+                const bool check = t == sl.next_check || t == a.max_steps;
                 if (!check && !abort_now) continue;
                 int st = -1;   // -1: keep going
                 double ux = 0.0, uy = 0.0;
@@ -247,7 +253,9 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     ux /= (double)s2;
                     uy /= (double)s2;
                     const double cur = sl.drive == 0 ? ux : uy;
-                    if (a.tol > 0.0 && t > a.check_every && t % a.check_every == 0 &&
+                    const bool regular = t == sl.next_check;
+                    if (regular) sl.next_check += a.check_every;
+                    if (a.tol > 0.0 && t > a.check_every && regular &&
                         fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur))
                         st = LBM_OK;
                     else if (t == a.max_steps)
@@ -276,6 +284,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                             sl.x0 = a.leaves[3 * sl.leaf];
                             sl.y0 = a.leaves[3 * sl.leaf + 1];
                             sl.tstart = T + 1;
+                            sl.next_check = a.check_every;
                             sl.prev = 0.0;
                         } else {
                             sl.job = -1;
@@ -307,7 +316,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     if (n_leaves < 0) return fail(LBM_EINVAL, "n_leaves must be >= 0");
     if (!std::isfinite(g_const) || g_const == 0.0) return fail(LBM_EINVAL, "g_const must be finite and non-zero");
     if (!std::isfinite(tol_rel) || tol_rel < 0.0) return fail(LBM_EINVAL, "tol_rel must be finite and >= 0");
-    if (max_steps < 1 || max_steps > (int64_t)1 << 31) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31]");
+    if (max_steps < 1 || max_steps >= (int64_t)1 << 31) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31 - 1]");
     if (check_every < 1) return fail(LBM_EINVAL, "check_every must be >= 1");
     if (n_leaves == 0) return LBM_OK;
     if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(keff_dev) ||
@@ -487,3 +496,198 @@ lbm_status lbm_set_time_limit(double seconds)
 namespace lbm {
 double local_time_limit() { return g_time_limit_s; }
 }  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the batched local problems.
+//
+// For callers that must not allocate device memory themselves or through the
+// library: code running where cudaMalloc is not allowed or not wanted (inside
+// a host that owns a fixed memory pool, under a strict memory budget, or next
+// to an allocator that must not be bypassed). The work queue, the per-size
+// class table and the status flags live in the file-scope device array below
+// instead of cudaMalloc'd scratch. The array holds at most NOALLOC_MAX_LEAVES
+// leaves (1 MiB plus a small header); every GPU that loads this library keeps
+// it until the process exits. Its device address is looked up with
+// cudaGetSymbolAddress once per device, by the first call on that device with
+// the device current; that first call should therefore happen before any
+// stream capture. All calls share the array and it keeps the last call's
+// contents, so each call clears what must start at zero; calls that overlap
+// on the GPU (different streams or threads) race on it.
+// ---------------------------------------------------------------------------
+namespace lbm {
+namespace {
+
+constexpr int NOALLOC_MAX_LEAVES = 131072;
+constexpr int NA_COUNTS = 0;                  // [65] leaves per size
+constexpr int NA_CURSOR = 65;                 // [65] scatter cursors per size
+constexpr int NA_HEADS = 130;                 // [64] queue heads per class
+constexpr int NA_FLAGS = 194;                 // [4]  bad-leaf flag, worst status, abort flag, spare
+constexpr int NA_TABLE = 198;                 // [1 + 64 + 65] nclass, class_size[], class_off[]
+constexpr int NA_HEADER = 328;                // ints before the job list (keeps it 32-byte aligned)
+constexpr int NA_JOBS = NA_HEADER;            // [2 * NOALLOC_MAX_LEAVES]
+constexpr int NA_TOTAL = NA_JOBS + 2 * NOALLOC_MAX_LEAVES;
+
+static __device__ __align__(256) int g_noalloc_scratch[NA_TOTAL];
+
+std::atomic<int *> g_noalloc_ptr[64];   // device address of the array, per device
+
+__global__ void noalloc_count_kernel(const int *leaves, int n, int nx, int ny, int *scr)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x0 = leaves[3 * i], y0 = leaves[3 * i + 1], s = leaves[3 * i + 2];
+        if (s < 1 || s > 64 || x0 < 0 || y0 < 0 || (long long)x0 + s > nx || (long long)y0 + s > ny) {
+            atomicOr(&scr[NA_FLAGS], 1);
+            continue;
+        }
+        atomicAdd(&scr[NA_COUNTS + s], 1);
+    }
+}
+
+// one thread: classes in descending size, offsets of their job ranges
+__global__ void noalloc_table_kernel(int *scr)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int nclass = 0, off = 0;
+    for (int s = 64; s >= 1; --s) {
+        const int c = scr[NA_COUNTS + s];
+        if (c == 0) continue;
+        scr[NA_TABLE + 1 + nclass] = s;
+        scr[NA_TABLE + 65 + nclass] = off;
+        scr[NA_CURSOR + s] = off;
+        off += 2 * c;
+        ++nclass;
+    }
+    scr[NA_TABLE + 65 + nclass] = off;
+    scr[NA_TABLE] = nclass;
+}
+
+__global__ void noalloc_scatter_kernel(const int *leaves, int n, int *scr)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = leaves[3 * i + 2];
+        const int pos = atomicAdd(&scr[NA_CURSOR + s], 2);
+        scr[NA_JOBS + pos] = 2 * i;
+        scr[NA_JOBS + pos + 1] = 2 * i + 1;
+    }
+}
+
+}  // namespace
+}  // namespace lbm
+
+extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_dev,
+                                                   const lbm_leaf *leaves_dev, int32_t n_leaves, double g_const,
+                                                   double tol_rel, int64_t max_steps, int32_t check_every,
+                                                   double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                                                   void *cuda_stream)
+{
+    using namespace lbm;
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 1 || p->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
+    if (!std::isfinite(p->tau) || p->tau < 0.5) return fail(LBM_EINVAL, "tau must be finite and >= 0.5");
+    if (!std::isfinite(p->nu) || !std::isfinite(p->eps) || p->eps < 0.0)
+        return fail(LBM_EINVAL, "nu must be finite and eps finite and >= 0");
+    if (n_leaves < 0) return fail(LBM_EINVAL, "n_leaves must be >= 0");
+    if (n_leaves > NOALLOC_MAX_LEAVES)
+        return fail(LBM_EINVAL, "n_leaves %d exceeds the %d leaves the static scratch holds", n_leaves,
+                    NOALLOC_MAX_LEAVES);
+    if (!std::isfinite(g_const) || g_const == 0.0) return fail(LBM_EINVAL, "g_const must be finite and non-zero");
+    if (!std::isfinite(tol_rel) || tol_rel < 0.0) return fail(LBM_EINVAL, "tol_rel must be finite and >= 0");
+    if (max_steps < 1 || max_steps >= (int64_t)1 << 31) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31 - 1]");
+    if (check_every < 1) return fail(LBM_EINVAL, "check_every must be >= 1");
+    if (n_leaves == 0) return LBM_OK;
+    if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(keff_dev) ||
+        !is_device_ptr(status_dev) || (steps_dev && !is_device_ptr(steps_dev)))
+        return fail(LBM_EINVAL, "kappa, leaves, keff, status (and steps) must be device pointers");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "no usable current device");
+    }
+    if (!g_noalloc_ptr[dev].load()) {
+        // set-up, once per device, with that device current: the host-side name of a
+        // __device__ array is not its device address, so ask the runtime for it
+        int *ptr = nullptr;
+        e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return fail(LBM_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        }
+        g_noalloc_ptr[dev].store(ptr);
+    }
+    int *scr = g_noalloc_ptr[dev].load();
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+#define NA_CUDA(call)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            return fail(LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));              \
+        }                                                                                        \
+    } while (0)
+    // the array keeps the previous call's contents: clear the header (counts, cursors,
+    // heads, flags, class table) and the caller's status / steps outputs
+    NA_CUDA(cudaMemsetAsync(scr, 0, sizeof(int) * NA_HEADER, st));
+    NA_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int32_t) * n_leaves, st));
+    if (steps_dev) NA_CUDA(cudaMemsetAsync(steps_dev, 0, sizeof(int32_t) * 2 * n_leaves, st));
+    const int *lv = reinterpret_cast<const int *>(leaves_dev);
+    const int nb = (n_leaves + 255) / 256 < 1024 ? (n_leaves + 255) / 256 : 1024;
+    noalloc_count_kernel<<<nb, 256, 0, st>>>(lv, n_leaves, p->nx, p->ny, scr);
+    noalloc_table_kernel<<<1, 32, 0, st>>>(scr);
+    NA_CUDA(cudaGetLastError());
+    int head[NA_HEADER];
+    NA_CUDA(cudaMemcpyAsync(head, scr, sizeof head, cudaMemcpyDeviceToHost, st));
+    NA_CUDA(cudaStreamSynchronize(st));
+    count_launches(2);
+    if (head[NA_FLAGS]) return fail(LBM_EINVAL, "a leaf has a size outside [1, 64] or lies outside the field");
+    noalloc_scatter_kernel<<<nb, 256, 0, st>>>(lv, n_leaves, scr);
+    NA_CUDA(cudaGetLastError());
+    count_launches(1);
+
+    const double nu = p->nu < 0.0 ? (p->tau - 0.5) / 3.0 : p->nu;
+    LocalArgs a{};
+    a.kappa = kappa_dev;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.leaves = lv;
+    a.jobs = scr + NA_JOBS;
+    a.nclass = head[NA_TABLE];
+    for (int c = 0; c < a.nclass; ++c) {
+        a.class_size[c] = head[NA_TABLE + 1 + c];
+        a.class_off[c] = head[NA_TABLE + 65 + c];
+    }
+    a.class_off[a.nclass] = head[NA_TABLE + 65 + a.nclass];
+    a.heads = scr + NA_HEADS;
+    a.omega = (float)(1.0 / p->tau);
+    a.two_tau = (float)(2.0 * p->tau);
+    a.omt = (float)(1.0 - 2.0 * p->tau);
+    a.half_eps = (float)(0.5 * p->eps);
+    a.gmag = (float)g_const;
+    a.eps_nu = p->eps * nu;
+    a.nu_over_g = nu / g_const;
+    a.tol = tol_rel;
+    a.check_every = check_every;
+    a.max_steps = max_steps;
+    a.keff = keff_dev;
+    a.status = status_dev;
+    a.steps = steps_dev;
+    a.worst = scr + NA_FLAGS + 1;
+    a.abort_flag = scr + NA_FLAGS + 2;
+    a.time_limit_ns = (unsigned long long)(g_time_limit_s * 1e9);
+    NA_CUDA(cudaFuncSetAttribute(local_keff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LOCAL_SMEM));
+    int blocks = sm_count(dev);
+    if (blocks > 2 * n_leaves) blocks = 2 * n_leaves;
+    local_keff_kernel<<<blocks, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
+    NA_CUDA(cudaGetLastError());
+    count_launches(1);
+    int flags[2] = {0, 0};
+    NA_CUDA(cudaMemcpyAsync(flags, scr + NA_FLAGS + 1, sizeof flags, cudaMemcpyDeviceToHost, st));
+    NA_CUDA(cudaStreamSynchronize(st));
+#undef NA_CUDA
+    if (flags[1] || flags[0] == LBM_ETIMEOUT)
+        return fail(LBM_ETIMEOUT, "local problems exceeded the time limit; unfinished leaves carry LBM_ETIMEOUT");
+    if (flags[0] == LBM_ENOTCONV)
+        return fail(LBM_ENOTCONV, "some leaves did not meet the tolerance within max_steps (status per leaf)");
+    return LBM_OK;
+}
