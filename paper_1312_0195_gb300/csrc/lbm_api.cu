@@ -7,7 +7,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 
@@ -246,6 +248,103 @@ static lbm_status get_graph(lbm_grid *g, int n, int parity, int check, cudaGraph
     return LBM_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Picks the fused step's launch shape (threads per block, resident blocks per SM,
+// cells per thread) by timing candidates on the grid itself right after
+// creation, then resets the state to rest. The choice is cached per lattice
+// shape and variant for the whole process. Results do not depend on the launch
+// shape (every cell's arithmetic and every reduction order are fixed), so
+// tuning never changes answers. LBM_AUTOTUNE=0 disables it.
+struct TuneKey {
+    int nx, ny, storage, coef, gf, walls;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(nx, ny, storage, coef, gf, walls) < std::tie(o.nx, o.ny, o.storage, o.coef, o.gf, o.walls);
+    }
+};
+static std::map<TuneKey, GridLaunch> g_tuned;
+static std::mutex g_tune_mu;
+
+static lbm_status autotune(lbm_grid *g)
+{
+    const char *env = std::getenv("LBM_AUTOTUNE");
+    if (env && env[0] == '0') return LBM_OK;
+    const int64_t n = (int64_t)g->p.nx * g->p.ny;
+    if (n < ((int64_t)1 << 20)) return LBM_OK;      // small lattices are launch-bound: keep the default
+    const bool walls = g->p.bc == LBM_BC_WALLS_Y;
+    const TuneKey key{g->p.nx, g->p.ny, g->p.storage, g->coef_mode, g->has_g, walls};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            g->L.step_blocks = it->second.step_blocks;
+            g->L.step_threads = it->second.step_threads;
+            g->L.step_vec = it->second.step_vec;
+            return LBM_OK;
+        }
+    }
+    const int sms = sm_count(g->dev);
+    // cells-per-thread candidates: the default for this storage and row length, and the wider pack
+    const int dvec = step_vec(g->p.storage, g->p.nx);
+    const int wide = g->p.storage == LBM_F32 ? 8 : (g->p.storage == LBM_F16 ? 2 : dvec);
+    const int vecs[2] = {dvec, step_vec_ok(g->p.storage, g->p.nx, wide) ? wide : dvec};
+    GridLaunch best = g->L;
+    float best_ms = -1.0f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LBM_CUDA(cudaEventCreate(&e0));
+    LBM_CUDA(cudaEventCreate(&e1));
+    const int warm = 2, timed = 8;
+    for (int vi = 0; vi < 2; ++vi) {
+        const int vec = vecs[vi];
+        if (vi == 1 && vec == vecs[0]) break;
+        for (int threads : {128, 256, 512}) {
+            const int occ = step_blocks_per_sm(g->p.storage, g->coef_mode, g->has_g, walls, g->p.nx, threads, vec);
+            const int64_t chunks = n / vec;
+            const int64_t want = (chunks + threads - 1) / threads;
+            for (int bpsm : {occ, occ > 1 ? occ / 2 : 0}) {
+                if (bpsm < 1) continue;
+                const int64_t cap = (int64_t)sms * bpsm;
+                GridLaunch L = g->L;
+                L.step_threads = threads;
+                L.step_vec = vec;
+                L.step_blocks = (int)(want < cap ? want : cap);
+                g->L = L;
+                cudaError_t err = cudaSuccess;
+                for (int i = 0; i < warm && err == cudaSuccess; ++i) { err = enqueue_step(g, g->cur, g->stream); g->cur ^= 1; }
+                cudaEventRecord(e0, g->stream);
+                for (int i = 0; i < timed && err == cudaSuccess; ++i) { err = enqueue_step(g, g->cur, g->stream); g->cur ^= 1; }
+                cudaEventRecord(e1, g->stream);
+                count_launches(warm + timed);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (err != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                if (best_ms < 0.0f || ms < best_ms) {
+                    best_ms = ms;
+                    best = L;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->L.step_blocks = best.step_blocks;
+    g->L.step_threads = best.step_threads;
+    g->L.step_vec = best.step_vec;
+    // back to rest: zero deviations in both buffers
+    const size_t bytes = 9 * g->plane * storage_bytes(g->p.storage);
+    LBM_CUDA(cudaMemsetAsync(g->buf[0], 0, bytes, g->stream));
+    LBM_CUDA(cudaMemsetAsync(g->buf[1], 0, bytes, g->stream));
+    LBM_CUDA(cudaStreamSynchronize(g->stream));
+    g->cur = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = g->L;
+    return LBM_OK;
+}
+
 static void free_grid(lbm_grid *g)
 {
     if (!g) return;
@@ -311,6 +410,7 @@ lbm_status grid_create_impl(const lbm_params *p, const float *kappa_dev, const d
     const int vec = step_vec(p->storage, p->nx);
     const int64_t chunks = n / vec;
     g->L.step_threads = 256;
+    g->L.step_vec = 0;
     const int64_t want = (chunks + g->L.step_threads - 1) / g->L.step_threads;
     const int64_t cap = (int64_t)sms * step_blocks_per_sm(p->storage, g->coef_mode, g->has_g,
                                                           p->bc == LBM_BC_WALLS_Y, p->nx, g->L.step_threads);
@@ -375,6 +475,8 @@ lbm_status grid_create_impl(const lbm_params *p, const float *kappa_dev, const d
             g->S = std::ldexp(1.0, e2);
         }
     }
+    s = autotune(g);
+    if (s != LBM_OK) return bail(s);
     *out = g;
     return LBM_OK;
 #undef LBM_GRID_CUDA
@@ -423,7 +525,7 @@ lbm_status lbm_step(lbm_grid *g, int64_t max_steps, double tol_rel, int32_t chec
     const int CHUNK = 1024;
     int64_t left = max_steps, done = 0;
     double resid = -1.0;
-    bool converged = false;
+    bool converged = false, checked = false;
     while (left > 0) {
         int64_t n = left < CHUNK ? left : CHUNK;
         int check = 0;
@@ -445,16 +547,23 @@ lbm_status lbm_step(lbm_grid *g, int64_t max_steps, double tol_rel, int32_t chec
         left -= n;
         if (n & 1) g->cur = 1 - g->cur;
         if (check) {
-            LBM_CUDA(cudaStreamSynchronize(g->stream));
-            const double dmax = g->h_result[0], umax = g->h_result[1];
-            resid = umax > 0.0 ? dmax / umax : dmax;
-            if (tol_rel > 0.0 && resid <= tol_rel) {
-                converged = true;
-                break;
+            checked = true;
+            if (tol_rel > 0.0) {      // the stop test needs the value now; otherwise read it at the end
+                LBM_CUDA(cudaStreamSynchronize(g->stream));
+                const double dmax = g->h_result[0], umax = g->h_result[1];
+                resid = umax > 0.0 ? dmax / umax : dmax;
+                if (resid <= tol_rel) {
+                    converged = true;
+                    break;
+                }
             }
         }
     }
     LBM_CUDA(cudaStreamSynchronize(g->stream));
+    if (checked && tol_rel <= 0.0) {
+        const double dmax = g->h_result[0], umax = g->h_result[1];
+        resid = umax > 0.0 ? dmax / umax : dmax;
+    }
     if (steps_done) *steps_done = done;
     if (residual) *residual = resid;
     if (tol_rel > 0.0 && !converged)

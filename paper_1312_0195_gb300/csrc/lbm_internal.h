@@ -34,7 +34,7 @@ struct StepArgs {
     CT rho0;              // rest density in storage units (the FP16 scale S, else 1)
     const T *src;         // post-collision state of the previous step
     T *dst;
-    const CT *coef;       // COEF_SCALAR: d [plane]; COEF_TENSOR: M [4][plane]
+    const CT *coef;       // COEF_SCALAR: e [plane] (rho u = (1 - e) r); COEF_TENSOR: E [4][plane] (rho u = (I - E) r)
     const CT *gfield;     // [2][plane] or nullptr
 };
 
@@ -50,7 +50,8 @@ struct MomArgs {
 
 struct GridLaunch {
     int step_blocks;      // persistent grid for the fused step
-    int step_threads;
+    int step_threads;     // threads per block (<= 512)
+    int step_vec;         // cells per thread (0: the default for the storage and row length)
     int mom_blocks;
     int mom_threads;
 };
@@ -69,7 +70,8 @@ cudaError_t launch_coef_tensor(int storage, const double *kstar, void *coef, int
 cudaError_t launch_copy_force(int storage, const float *g, void *dst, int64_t n, int64_t plane,
                               double scale_unused, cudaStream_t st);
 int step_vec(int storage, int nx);   // cells per thread used for this storage and row length
-int step_blocks_per_sm(int storage, int coef_mode, bool gfield, bool walls, int nx, int threads);
+int step_blocks_per_sm(int storage, int coef_mode, bool gfield, bool walls, int nx, int threads, int vec = 0);
+bool step_vec_ok(int storage, int nx, int vec);   // is this cells-per-thread variant built and usable
 
 // ---- launch counter (lbm_api.cu) ----------------------------------------------
 void count_launches(int64_t n);

@@ -5,12 +5,12 @@
 // Storage. Distributions live as deviations g_a = f_a - w_a rho0 in nine SoA
 // planes [9][plane], x fastest. Every quantity of the step is linear in f (the
 // force enters as rho G and rho is a sum of f), so in deviation form
-//   drho = sum g,  j = sum e g,  rho = rho0 + drho
-//   rho u    = d (j + eps rho G / 2)                    (Eq. 6 times rho)
+//   drho = sum_a g_a,  j = sum_a e_a g_a,  rho = rho0 + drho
+//   rho u    = (1 - e) r,  r = j + eps rho G / 2       (Eq. 6 times rho)
 //   rho u_eq = 2 tau (rho u) + (1 - 2 tau) j            (Eq. 16 times rho)
 //   g_eq     = w (drho + 3 e . rho u_eq)                (Eq. 2 minus w rho0)
 //   g*       = g + (g_eq - g) / tau                     (Eq. 13)
-// with d = 1 / (1 + eps nu / (2 kappa)) precomputed per cell. No division by
+// with the drag fraction e = 1 - 1/(1 + eps nu / (2 kappa)) precomputed per cell. No division by
 // rho happens inside the step. Scaling every g by S (FP16 storage) is exact if
 // rho0 is replaced by S in the force term, which is what `rho0` carries.
 //
@@ -101,12 +101,12 @@ __device__ __forceinline__ void collide_cell(C (&gq)[Q], C rho0, C half_eps, C G
     const C rx = jx + half_eps * rho * Gx;
     const C ry = jy + half_eps * rho * Gy;
     C rux, ruy;
-    if constexpr (COEF == COEF_SCALAR) {
-        rux = c0 * rx;
-        ruy = c0 * ry;
-    } else {
-        rux = c0 * rx + c1 * ry;
-        ruy = c2 * rx + c3 * ry;
+    if constexpr (COEF == COEF_SCALAR) {          // rho u = (1 - e) r, written so that e << 1 keeps its digits
+        rux = rx - c0 * rx;
+        ruy = ry - c0 * ry;
+    } else {                                      // rho u = (I - E) r
+        rux = rx - (c0 * rx + c1 * ry);
+        ruy = ry - (c2 * rx + c3 * ry);
     }
     const C uex = two_tau * rux + omt * jx;   // rho u_eq, Eq. 16
     const C uey = two_tau * ruy + omt * jy;
@@ -199,7 +199,7 @@ __device__ __forceinline__ void cell_params(const StepArgs<T, C> &a, int64_t cel
 }
 
 template <typename T, int VEC, int COEF, bool GF, bool WALLS>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs<T, typename Comp<T>::type> a)
+__global__ void __launch_bounds__(512) step_kernel(StepArgs<T, typename Comp<T>::type> a)
 {
     using C = typename Comp<T>::type;
     using P = Pack<T, VEC>;
@@ -268,11 +268,11 @@ __device__ __forceinline__ void cell_uv(const C (&g)[Q], C rho0, C half_eps, C G
     const C rx = jx + half_eps * r * Gx, ry = jy + half_eps * r * Gy;
     C rux, ruy;
     if constexpr (COEF == COEF_SCALAR) {
-        rux = c0 * rx;
-        ruy = c0 * ry;
+        rux = rx - c0 * rx;
+        ruy = ry - c0 * ry;
     } else {
-        rux = c0 * rx + c1 * ry;
-        ruy = c2 * rx + c3 * ry;
+        rux = rx - (c0 * rx + c1 * ry);
+        ruy = ry - (c2 * rx + c3 * ry);
     }
     drho_o = drho;
     u = rux / r;
@@ -414,9 +414,12 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const double *part
     }
 }
 
-// d = 1 / (1 + eps nu / (2 kappa)) = 2 kappa / (2 kappa + eps nu), evaluated in
-// double; kappa = +inf (or eps nu = 0) gives 1, kappa = 0 gives 0. flags bit 0
-// is set for a negative or NaN kappa. kmax_bits collects the largest finite
+// Drag fraction e = 1 - d with d = 1 / (1 + eps nu / (2 kappa)) of Eq. 6, i.e.
+// e = eps nu / (2 kappa + eps nu), evaluated in double; kappa = +inf (or
+// eps nu = 0) gives 0, kappa = 0 gives 1. The step forms rho u = r - e r: storing
+// e rather than d keeps full relative precision when the drag is weak (d -> 1),
+// where FP32 d alone would leave 1 - d with only a few digits. flags bit 0 is set
+// for a negative or NaN kappa. kmax_bits collects the largest finite
 // kappa (the bit pattern of a non-negative float orders like an unsigned int).
 template <typename CT>
 __global__ void __launch_bounds__(256) coef_scalar_kernel(const float *kappa, CT *d, int64_t n, double eps_nu,
@@ -427,10 +430,10 @@ __global__ void __launch_bounds__(256) coef_scalar_kernel(const float *kappa, CT
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float k = kappa[i];
         double dd;
-        if (!(k >= 0.0f)) { bad = 1u; dd = 0.0; }
-        else if (eps_nu == 0.0 || isinf(k)) dd = 1.0;
-        else if (k == 0.0f) dd = 0.0;
-        else dd = 2.0 * (double)k / (2.0 * (double)k + eps_nu);
+        if (!(k >= 0.0f)) { bad = 1u; dd = 1.0; }
+        else if (eps_nu == 0.0 || isinf(k)) dd = 0.0;
+        else if (k == 0.0f) dd = 1.0;
+        else dd = eps_nu / (2.0 * (double)k + eps_nu);
         d[i] = (CT)dd;
         if (k >= 0.0f && !isinf(k)) local_max = max(local_max, __float_as_uint(k));
     }
@@ -446,15 +449,16 @@ __global__ void __launch_bounds__(256) coef_scalar_kernel(const float *kappa, CT
 }
 
 // Coarse-grid coefficient for a tensor K* (Eq. 18 in Eq. 15):
-// rho u = (I + c K*^-1)^-1 (j + eps rho G / 2) = (K* + c I)^-1 K* (j + ...), c = eps nu / 2.
-// kstar is [n][4] (xx, xy, yx, yy); the coefficient is stored as 4 planes.
+// rho u = (I + c K*^-1)^-1 r = (K* + c I)^-1 K* r = (I - E) r with E = c (K* + c I)^-1,
+// c = eps nu / 2, r = j + eps rho G / 2. E (the drag part, like e of the scalar
+// case) is stored as 4 planes; kstar is [n][4] (xx, xy, yx, yy).
 template <typename CT>
 __global__ void __launch_bounds__(256) coef_tensor_kernel(const double *kstar, CT *m, int64_t n, int64_t plane,
                                                           double c, unsigned *flags)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double kxx = kstar[4 * i], kxy = kstar[4 * i + 1], kyx = kstar[4 * i + 2], kyy = kstar[4 * i + 3];
-        double mxx = 1.0, mxy = 0.0, myx = 0.0, myy = 1.0;
+        double mxx = 0.0, mxy = 0.0, myx = 0.0, myy = 0.0;
         if (!(isfinite(kxx) && isfinite(kxy) && isfinite(kyx) && isfinite(kyy))) {
             atomicOr(flags, 1u);
         } else if (c != 0.0) {
@@ -463,11 +467,10 @@ __global__ void __launch_bounds__(256) coef_tensor_kernel(const double *kstar, C
             if (!(fabs(det) > 0.0)) {
                 atomicOr(flags, 2u);
             } else {
-                const double ixx = ayy / det, ixy = -axy / det, iyx = -ayx / det, iyy = axx / det;
-                mxx = ixx * kxx + ixy * kyx;
-                mxy = ixx * kxy + ixy * kyy;
-                myx = iyx * kxx + iyy * kyx;
-                myy = iyx * kxy + iyy * kyy;
+                mxx = c * ayy / det;
+                mxy = -c * axy / det;
+                myx = -c * ayx / det;
+                myy = c * axx / det;
             }
         }
         m[i] = (CT)mxx;
@@ -574,13 +577,25 @@ int step_vec(int storage, int nx)
     return 1;
 }
 
-int step_blocks_per_sm(int storage, int coef_mode, bool gfield, bool walls, int nx, int threads)
+bool step_vec_ok(int storage, int nx, int vec)
 {
-    const int v = step_vec(storage, nx);
+    if (vec <= 0 || nx % vec) return false;
+    switch (storage) {
+    case LBM_F32: return vec == 1 || vec == 4 || vec == 8;
+    case LBM_F16: return vec == 1 || vec == 2 || vec == 8;
+    case LBM_F64: return vec == 1 || vec == 2;
+    }
+    return false;
+}
+
+int step_blocks_per_sm(int storage, int coef_mode, bool gfield, bool walls, int nx, int threads, int vec)
+{
+    const int v = vec > 0 ? vec : step_vec(storage, nx);
     switch (storage) {
     case LBM_F32:
-        return v == 4 ? occupancy_t<float, 4>(coef_mode, gfield, walls, threads)
-                      : occupancy_t<float, 1>(coef_mode, gfield, walls, threads);
+        return v == 8 ? occupancy_t<float, 8>(coef_mode, gfield, walls, threads)
+                      : (v == 4 ? occupancy_t<float, 4>(coef_mode, gfield, walls, threads)
+                                : occupancy_t<float, 1>(coef_mode, gfield, walls, threads));
     case LBM_F16:
         return v == 8 ? occupancy_t<__half, 8>(coef_mode, gfield, walls, threads)
                       : (v == 2 ? occupancy_t<__half, 2>(coef_mode, gfield, walls, threads)
@@ -599,20 +614,23 @@ cudaError_t launch_step(int storage, int coef_mode, bool gfield, bool walls, con
     switch (storage) {
     case LBM_F32: {
         nx = static_cast<const StepArgs<float, float> *>(args)->nx;
-        return step_vec(storage, nx) == 4 ? launch_step_t<float, 4>(coef_mode, gfield, walls, args, L, st)
-                                          : launch_step_t<float, 1>(coef_mode, gfield, walls, args, L, st);
+        const int v = step_vec_ok(storage, nx, L.step_vec) ? L.step_vec : step_vec(storage, nx);
+        return v == 8 ? launch_step_t<float, 8>(coef_mode, gfield, walls, args, L, st)
+                      : (v == 4 ? launch_step_t<float, 4>(coef_mode, gfield, walls, args, L, st)
+                                : launch_step_t<float, 1>(coef_mode, gfield, walls, args, L, st));
     }
     case LBM_F16: {
         nx = static_cast<const StepArgs<__half, float> *>(args)->nx;
-        const int v = step_vec(storage, nx);
+        const int v = step_vec_ok(storage, nx, L.step_vec) ? L.step_vec : step_vec(storage, nx);
         return v == 8 ? launch_step_t<__half, 8>(coef_mode, gfield, walls, args, L, st)
                       : (v == 2 ? launch_step_t<__half, 2>(coef_mode, gfield, walls, args, L, st)
                                 : launch_step_t<__half, 1>(coef_mode, gfield, walls, args, L, st));
     }
     case LBM_F64: {
         nx = static_cast<const StepArgs<double, double> *>(args)->nx;
-        return step_vec(storage, nx) == 2 ? launch_step_t<double, 2>(coef_mode, gfield, walls, args, L, st)
-                                          : launch_step_t<double, 1>(coef_mode, gfield, walls, args, L, st);
+        const int v = step_vec_ok(storage, nx, L.step_vec) ? L.step_vec : step_vec(storage, nx);
+        return v == 2 ? launch_step_t<double, 2>(coef_mode, gfield, walls, args, L, st)
+                      : launch_step_t<double, 1>(coef_mode, gfield, walls, args, L, st);
     }
     }
     return cudaErrorInvalidValue;

@@ -109,16 +109,28 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def _iso(kappa_blocks):
+    """[40, 40] scalar block permeability as an isotropic K* tensor field."""
+    import torch
+    k = np.zeros((40, 40, 4))
+    k[..., 0] = kappa_blocks
+    k[..., 3] = kappa_blocks
+    return torch.from_numpy(k).cuda()
+
+
 def test_fiveblock_darcy_upscaled_run_follows_fine_run():
     """Section 4.3.1 (E5): 400^2 fine grid, Eq. 23, G = (sin pi x, sin pi y), tau = 0.5; K* of every
-    10x10 block by local LBM; 40^2 coarse run; compared at the same physical time."""
+    10x10 block by local LBM; 40^2 coarse run; compared near steady state (3e6 fine steps = 6
+    time constants of the slowest pressure mode, 3e5 coarse steps, the same physical time).
+    The coarse run with K* must follow the block-averaged fine run, and do so better than a
+    coarse run with the naive block-mean permeability."""
     import torch
     lbm = _lbm()
     ex = synth.paper_experiment("E5_fine")
     kap = ex["kappa"].astype(np.float32)
     p = lbm.Params(nx=400, ny=400, tau=ex["tau"], nu=ex["nu"], eps=ex["eps"])
     keff = torch.empty((40, 40, 4), dtype=torch.float64, device="cuda")
-    st, _ = lbm.lbm_upscale(p, _t(kap), 10, keff, 5e-7, 1e-10, 400000)
+    st, _ = lbm.lbm_upscale(p, _t(kap), 10, keff, 5e-7, 1e-9, 400000)
     assert st == 0
     k = keff.cpu().numpy() / ex["k_const"]
     mask = synth.fiveblock_coarse_kappa_eq24(40, 1.0, 0.0) == 1.0           # the five K = K_const blocks
@@ -127,17 +139,21 @@ def test_fiveblock_darcy_upscaled_run_follows_fine_run():
     assert abs(np.mean(0.5 * (sin_blocks[:, 0] + sin_blocks[:, 3])) - 8.485) < 1e-3
     gfine = ex["gfield"].astype(np.float32)
     gco = synth.sinusoidal_g_field(40, synth.LatticeUnits(0.0025, 2.5e-5).force(1.0))   # fine lattice units
-    fine_steps = 200000
+    fine_steps = 3000000
     rf, uf, vf = _fine_fields(lbm, p, kap, gfine, fine_steps)
-    rc, uc, vc = _coarse(lbm, p, keff, gco, fine_steps // 10)
+    _, uc, vc = _coarse(lbm, p, keff, gco, fine_steps // 10)
+    naive = ex["kappa"].reshape(40, 10, 40, 10).mean(axis=(1, 3))           # arithmetic block mean of kappa
+    _, un, vn = _coarse(lbm, p, _iso(naive), gco, fine_steps // 10)
     eu, ev = _rel(uc, uf), _rel(vc, vf)
-    print(f"E5 coarse vs block-averaged fine: rel L2 u {eu:.3e}, v {ev:.3e}")
+    en = _rel(un, uf)
+    print(f"E5 coarse vs block-averaged fine: rel L2 u {eu:.3e}, v {ev:.3e}; naive block mean: u {en:.3e}")
     assert eu < 0.05 and ev < 0.05
+    assert eu < en
 
 
 def test_fiveblock_brinkman_kstar_beats_kstar_err():
     """Section 4.3.2 (E6): with nu_eff > 0 the local problems must use the same nu_eff; K*err computed
-    with nu_eff = 0 (the paper's 8.485 vs 7.367) makes the coarse run deviate visibly."""
+    with nu_eff = 0 (the paper's 8.485 against 7.367) makes the coarse run deviate visibly."""
     import torch
     lbm = _lbm()
     ex = synth.paper_experiment("E6_fine")
@@ -146,17 +162,19 @@ def test_fiveblock_brinkman_kstar_beats_kstar_err():
     p_err = lbm.Params(nx=400, ny=400, tau=0.5, nu=ex["nu"], eps=ex["eps"])
     keff = torch.empty((40, 40, 4), dtype=torch.float64, device="cuda")
     keff_err = torch.empty_like(keff)
-    lbm.lbm_upscale(p, _t(kap), 10, keff, 5e-7, 1e-10, 1000000)
-    lbm.lbm_upscale(p_err, _t(kap), 10, keff_err, 5e-7, 1e-10, 1000000)
+    # the slow momentum modes of these weak-drag leaves need the tighter test (see the stop-rule reading)
+    lbm.lbm_upscale(p, _t(kap), 10, keff, 5e-7, 1e-9, 2000000)
+    lbm.lbm_upscale(p_err, _t(kap), 10, keff_err, 5e-7, 1e-9, 2000000)
     k = keff.cpu().numpy() / ex["k_const"]
     ke = keff_err.cpu().numpy() / ex["k_const"]
     mask = synth.fiveblock_coarse_kappa_eq24(40, 1.0, 0.0) == 1.0
     s_k = np.mean(0.5 * (k[~mask][:, 0] + k[~mask][:, 3]))
     s_e = np.mean(0.5 * (ke[~mask][:, 0] + ke[~mask][:, 3]))
-    assert abs(s_k - 7.367) < 2e-3 and abs(s_e - 8.485) < 2e-3
+    print(f"E6 K*/K_const {s_k:.5f} (paper 7.367), K*err/K_const {s_e:.5f} (paper 8.485)")
+    assert abs(s_k - 7.367) < 1.5e-3 and abs(s_e - 8.485) < 1.5e-3
     gfine = ex["gfield"].astype(np.float32)
     gco = synth.sinusoidal_g_field(40, synth.LatticeUnits(0.0025, 2.5e-5).force(1.0))   # fine lattice units
-    fine_steps = 60000
+    fine_steps = 100000
     rf, uf, vf = _fine_fields(lbm, p, kap, gfine, fine_steps)
     _, uc, vc = _coarse(lbm, p, keff, gco, fine_steps // 10)
     _, ue, ve = _coarse(lbm, p, keff_err, gco, fine_steps // 10)
