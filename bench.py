@@ -175,6 +175,64 @@ def oracle_rate(kap: np.ndarray, steps: int) -> tuple[float, int, float]:
     return N * N * steps / dt / 1e6, cores, dt
 
 
+def measure_variants(lbm, torch, kap, stream, steps=300):
+    """FP16-scaled and FP64 storage on the same lattice: MLUPS and the fraction of HBM roofline."""
+    out = {}
+    peaks = measured_peaks()
+    for name, st in (("f16", lbm.LBM_F16), ("f64", lbm.LBM_F64)):
+        p = lbm.Params(nx=N, ny=N, tau=TAU, nu=NU, eps=1.0, gx=G[0], gy=G[1], storage=st)
+        with lbm.Grid(p, kap) as g:
+            g.step(50, 0.0, 0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.step(steps, 0.0, 0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3 / steps
+        out[name] = {"mlups": N * N / t / 1e6, "bytes_per_lup": BYTES_PER_LUP[name],
+                     "hbm_frac": BYTES_PER_LUP[name] * N * N / t / 1e9 / peaks["hbm_gbs"]}
+    return out
+
+
+def measure_local_keff(lbm, torch, kap, ws, sample=512, seed=11):
+    """Batched local problems on the 4096^2 field cut by the seeded quadtree (seed 3, ~71.6k
+    leaves): one persistent launch for all leaves, tol 1e-8 on the per-drive mean flux,
+    check every 64 steps, at most 200k steps per drive. The one-launch-per-leaf mode is
+    timed on a seeded sample of `sample` leaves, with the persistent launch on the same
+    sample beside it."""
+    import synth
+    leaves_np = synth.quadtree_leaves(N, N, seed=3)
+    p = lbm.Params(nx=N, ny=N, tau=1.0, eps=1.0)
+    leaves = torch.from_numpy(leaves_np).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    keff, status, steps, worst = lbm.local_keff(p, kap, leaves, 1e-6, 1e-8, 200000, 64, True)
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t0
+    st = status.cpu().numpy()
+    sz = leaves_np[:, 2].astype(np.float64)
+    lups = float((steps.cpu().numpy().astype(np.float64).sum(axis=1) * sz * sz).sum())
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(leaves_np), sample, replace=False)
+    sub = torch.from_numpy(leaves_np[idx]).cuda()
+    times = {}
+    for persistent in (True, False):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbm.local_keff(p, kap, sub, 1e-6, 1e-8, 200000, 64, persistent)
+        torch.cuda.synchronize()
+        times[persistent] = time.perf_counter() - t0
+    return {
+        "workload": "4096^2 log-normal field (sigma 2, ell 32), quadtree p=0.6 seed 3, tau=1, "
+                    "G=1e-6 along x then y, tol 1e-8, FP32, max 200k steps per drive",
+        "leaves": int(len(leaves_np)), "converged": int((st == 0).sum()),
+        "patches_per_s": len(leaves_np) * ws / t_all, "seconds": t_all,
+        "glups": lups / t_all / 1e9,
+        "sample": {"leaves": sample, "persistent_patches_per_s": sample / times[True],
+                   "per_leaf_launch_patches_per_s": sample / times[False]},
+    }
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -282,6 +340,13 @@ def run_ours(args, ws, rank, local):
            "d2h_bytes_per_step": int(u_host.numel() * 4 + v_host.numel() * 4),
            "steps": e2e_steps}
 
+    variants = {}
+    if not args.no_extras:
+        variants = measure_variants(lbm, torch, kap, stream)
+        local = measure_local_keff(lbm, torch, kap, ws)
+    else:
+        local = None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, cores, dt = oracle_rate(kap_np, args.cpu_steps)
@@ -301,6 +366,10 @@ def run_ours(args, ws, rank, local):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
+        if variants:
+            line["storage_variants"] = variants
+        if local:
+            line["local_keff"] = local
         print(json.dumps(line), flush=True)
     return 0
 
@@ -314,6 +383,8 @@ def main(argv=None):
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"])
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the storage variants and the local-problem measurement")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: create the grid, run this many plain lattice steps, exit")
     args = ap.parse_args(argv)

@@ -68,6 +68,10 @@ typedef struct {
     int32_t storage;      /* lbm_storage                                                */
     double  scale;        /* LBM_F16 only: power-of-two storage scale S; 0 picks S from
                              the largest finite kappa, |G| and nu                        */
+    int32_t force_model;  /* 0: simplified Shan-Chen scheme (Section 2.2, Eqs. 13-16);
+                             1: Guo scheme (Section 2.1, Eqs. 1-6: u_eq = u and the
+                             forcing term F_a of Eq. 4). With the linear equilibrium of
+                             Eq. 2 both give the same update up to rounding.          */
 } lbm_params;
 
 /* Thread-local description of the last failure of any call in this thread. */
@@ -193,16 +197,75 @@ lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_
  * Process-wide; default 600 s. */
 lbm_status lbm_set_time_limit(double seconds);
 
+/* -------------------------------------------------------- K* surrogate ---
+ * A learned shortcut for the local problems, not part of the paper (which
+ * obtains every K* by local LBM, Section 3): an ensemble of small CNNs maps a
+ * subdomain's permeability patch to (log K*_xx, log K*_yy); local LBM stays the
+ * fallback for doubtful patches and the judge of the surrogate's error.
+ * Network per model: six 3x3 'same' convolutions 2 -> 32 -> 32 -> 64 -> 64 ->
+ * 64 -> 64 with ReLU, global average pooling, a 64 -> 2 linear head; BF16
+ * activations and weights on the tensor cores with FP32 accumulation, FP32
+ * master weights, Adam. Inputs are patches from lbm_patches. */
+typedef struct lbm_surrogate lbm_surrogate;
+
+/* Number of FP32 parameters of one model; layout: for layer l = 0..5 the weights
+ * [c_out][c_in][3][3] then the bias [c_out] (c_in = 2, 32, 32, 64, 64, 64;
+ * c_out = 32, 32, 64, 64, 64, 64), then the head [2][64] and its bias [2]. */
+int64_t lbm_surrogate_param_count(void);
+
+/* Creates n_models (1..16) models with seeded He-normal weights (splitmix64). */
+lbm_status lbm_surrogate_create(int32_t n_models, uint64_t seed, lbm_surrogate **out);
+lbm_status lbm_surrogate_destroy(lbm_surrogate *s);
+/* Copy one model's FP32 parameters to / from HOST memory (checkpoints, tests). */
+lbm_status lbm_surrogate_get_params(const lbm_surrogate *s, int32_t model, float *host_out);
+lbm_status lbm_surrogate_set_params(lbm_surrogate *s, int32_t model, const float *host_in);
+/* Normalisation and gate range, HOST float[13]: input shift and scale of the
+ * log-K plane, target mean/std of log K*_xx and log K*_yy, then (low, high) of
+ * each patch statistic (mean, std, gradient energy of log K), last entry unused.
+ * lbm_surrogate_train sets them from its data. */
+lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13]);
+lbm_status lbm_surrogate_get_normalization(const lbm_surrogate *s, float norm[13]);
+
+/* Leaf -> surrogate input. For each leaf (size s dividing 32, or a multiple of
+ * 32 up to 1024) writes x_dev[i] = two float [32][32] planes: log K resampled to
+ * 32 x 32 (each cell repeated 32/s times per axis, or the mean of log K over
+ * (s/32)^2 blocks) and the constant log2(s)/6; and stats_dev[i] = (mean,
+ * standard deviation, gradient energy) of that log-K patch. kappa must be > 0. */
+lbm_status lbm_patches(const float *kappa_dev, int32_t nx, int32_t ny, const lbm_leaf *leaves_dev, int32_t n,
+                       float *x_dev, float *stats_dev, void *cuda_stream);
+
+/* Trains every model on n samples x_dev [n][2][32][32], targets y_dev [n][2]
+ * (log K*_xx, log K*_yy), stats_dev [n][3] from lbm_patches. Adam (0.9, 0.999,
+ * 1e-8), learning rate lr with cosine decay to lr/10, mini-batches of `batch`
+ * (<= 1024) from a seeded shuffle per epoch. loss_host (HOST, may be NULL)
+ * receives [n_models][epochs] mean training loss on standardised targets. */
+lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float *y_dev, const float *stats_dev,
+                               int32_t n, int32_t epochs, int32_t batch, double lr, uint64_t seed, float *loss_host,
+                               void *cuda_stream);
+
+/* Predictions of every model: y_dev [n_models][n][2] = log K*_xx, log K*_yy. */
+lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n, float *y_dev, void *cuda_stream);
+
+/* One forward and backward pass of one model on n <= 1024 inputs with
+ * targets t_dev [n][2] in standardised units: HOST outputs (each may be NULL)
+ * grad_host [param_count] = d mean((y - t)^2) / d params, *loss_host, and the
+ * raw outputs y_host [n][2]. For gradient checks against an independent code. */
+lbm_status lbm_surrogate_grad(lbm_surrogate *s, int32_t model, const float *x_dev, const float *t_dev, int32_t n,
+                              float *grad_host, float *loss_host, float *y_host, void *cuda_stream);
+
 /* ------------------------------------------------------------- upscaling ---
  * Section 3: the field is cut into block x block subdomains, one coarse point
  * each (row-major, coarse cell (I, J) <-> fine cells [I r, (I+1) r) x [J r, (J+1) r)).
  * K* of every subdomain comes from its local problems (lbm_local_keff_batch).
  * keff_coarse_dev: caller-owned DEVICE double [ny/r][nx/r][4] (xx, xy, yx, yy) in
- * FINE lattice units. sur must be NULL (every block is solved by local LBM);
- * spread_max is reserved for an ensemble gate. *n_fallback (host, may be NULL)
- * receives the number of blocks solved by local LBM. Status as for
- * lbm_local_keff_batch (check_every = 64, persistent launch). */
-typedef struct lbm_surrogate lbm_surrogate;
+ * FINE lattice units. With sur == NULL every block is solved by local LBM. With
+ * an ensemble, its prediction (K*_xx = exp(mean log K*_xx), likewise yy, zero
+ * off-diagonal) is used for a block unless the ensemble's spread (standard
+ * deviation across models of either log K*) exceeds ln(1 + spread_max) or a
+ * patch statistic lies outside the range seen in training; such blocks fall
+ * back to local LBM. *n_fallback (HOST, may be NULL) receives the number of
+ * blocks solved by local LBM. Status as for lbm_local_keff_batch (check_every =
+ * 64, persistent launch). */
 lbm_status lbm_upscale(const lbm_params *p, const float *kappa_dev, int32_t block, const lbm_surrogate *sur,
                        double spread_max, double g_const, double tol_rel, int64_t max_steps,
                        double *keff_coarse_dev, int32_t *n_fallback, void *cuda_stream);

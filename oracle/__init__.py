@@ -49,7 +49,8 @@ class _Problem(C.Structure):
                 ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
                 ("walls", C.c_int),
                 ("gx", C.c_double), ("gy", C.c_double),
-                ("kappa", C.c_void_p), ("ktensor", C.c_void_p), ("gfield", C.c_void_p)]
+                ("kappa", C.c_void_p), ("ktensor", C.c_void_p), ("gfield", C.c_void_p),
+                ("force_model", C.c_int)]
 
 
 _lib = None
@@ -88,11 +89,12 @@ class Problem:
 
     ``kappa``: ``[ny, nx]`` scalar permeability (may contain +inf, or 0), or
     ``ktensor``: ``[ny, nx, 4]`` (xx, xy, yx, yy). ``g``: constant (gx, gy) or
-    ``gfield``: ``[2, ny, nx]``. ``walls``: half-way bounce-back in y.
+    ``gfield``: ``[2, ny, nx]``. ``walls``: half-way bounce-back in y. ``guo``: the
+    Guo force scheme of Section 2.1 instead of the simplified scheme of Section 2.2.
     """
 
     def __init__(self, tau, nu, eps=1.0, kappa=None, ktensor=None, g=(0.0, 0.0), gfield=None,
-                 walls=False):
+                 walls=False, guo=False):
         if kappa is None and ktensor is None:
             raise ValueError("kappa or ktensor is required")
         self.kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
@@ -104,7 +106,8 @@ class Problem:
                            float(g[0]), float(g[1]),
                            None if self.kappa is None else self.kappa.ctypes.data,
                            None if self.ktensor is None else self.ktensor.ctypes.data,
-                           None if self.gfield is None else self.gfield.ctypes.data)
+                           None if self.gfield is None else self.gfield.ctypes.data,
+                           1 if guo else 0)
         self.tau, self.nu, self.eps, self.walls = float(tau), float(nu), float(eps), bool(walls)
 
     def rest(self) -> np.ndarray:

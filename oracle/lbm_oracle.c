@@ -47,6 +47,7 @@ typedef struct {
     const double *kappa;     /* [ny][nx] scalar permeability (may be +inf), or NULL */
     const double *ktensor;   /* [ny][nx][4] (xx, xy, yx, yy), used when kappa == NULL */
     const double *gfield;    /* [2][ny][nx] body force, or NULL */
+    int force_model;         /* 0: simplified Shan-Chen scheme (Section 2.2); 1: Guo scheme (Section 2.1) */
 } orc_problem;
 
 /* D2Q9 velocities and weights, built from the angle definitions of Section 2. */
@@ -147,6 +148,37 @@ static void cell_velocity(const orc_problem *p, long c, const double *fc,
     *ux_o = ux; *uy_o = uy;
 }
 
+/*
+ * Force per unit mass f_m of Eq. 5 (scalar kappa) or Eq. 18 (tensor K*) at the
+ * flow velocity u of Eq. 6. A blocked cell (kappa = 0) has u = 0 and its f_m
+ * follows from Eq. 3 with u_eq = u = 0: f_m = -2 j / rho (reading; Eq. 5 is 0/0 there).
+ */
+static void force_per_mass(const orc_problem *p, long c, double rho, double jx, double jy, double ux, double uy,
+                           double *fmx, double *fmy)
+{
+    double Gx, Gy;
+    force_at(p, c, &Gx, &Gy);
+    if (p->eps * p->nu == 0.0) {
+        *fmx = p->eps * Gx;
+        *fmy = p->eps * Gy;
+    } else if (p->kappa) {
+        double kap = p->kappa[c];
+        if (kap == 0.0) {
+            *fmx = -2.0 * jx / rho;
+            *fmy = -2.0 * jy / rho;
+        } else {
+            *fmx = -p->eps * p->nu / kap * ux + p->eps * Gx;                 /* Eq. 5 */
+            *fmy = -p->eps * p->nu / kap * uy + p->eps * Gy;
+        }
+    } else {
+        const double *k = p->ktensor + 4 * c;                                /* Eq. 18 */
+        double det = k[0] * k[3] - k[1] * k[2];
+        double ixx = k[3] / det, ixy = -k[1] / det, iyx = -k[2] / det, iyy = k[0] / det;
+        *fmx = -p->eps * p->nu * (ixx * ux + ixy * uy) + p->eps * Gx;
+        *fmy = -p->eps * p->nu * (iyx * ux + iyy * uy) + p->eps * Gy;
+    }
+}
+
 void orc_init_rest(const orc_problem *p, double *f)
 {
     lattice_init();
@@ -169,7 +201,9 @@ void orc_velocity(const orc_problem *p, const double *f, double *rho, double *u,
     }
 }
 
-/* One time step f -> fnew: collide (Eqs. 6, 16, 2, 13), then stream along e_a. */
+/* One time step f -> fnew: collide, then stream along e_a. Simplified Shan-Chen
+ * scheme: Eqs. 6, 16, 2, 13. Guo scheme (force_model = 1): Eq. 6 for u, u_eq = u,
+ * f_m by Eq. 5, the forcing term F_a of Eq. 4 and the update of Eq. 1. */
 void orc_step(const orc_problem *p, const double *f, double *fnew)
 {
     lattice_init();
@@ -182,12 +216,23 @@ void orc_step(const orc_problem *p, const double *f, double *fnew)
             const double *fc = f + c * Q;
             double rho, jx, jy, ux, uy;
             cell_velocity(p, c, fc, &rho, &jx, &jy, &ux, &uy);
-            double uex = 2.0 * tau * ux + (1.0 - 2.0 * tau) * jx / rho;     /* Eq. 16 */
-            double uey = 2.0 * tau * uy + (1.0 - 2.0 * tau) * jy / rho;
+            double uex, uey, fmx = 0.0, fmy = 0.0;
+            if (p->force_model == 1) {
+                uex = ux;                                                    /* Guo: u_eq = u */
+                uey = uy;
+                force_per_mass(p, c, rho, jx, jy, ux, uy, &fmx, &fmy);
+            } else {
+                uex = 2.0 * tau * ux + (1.0 - 2.0 * tau) * jx / rho;        /* Eq. 16 */
+                uey = 2.0 * tau * uy + (1.0 - 2.0 * tau) * jy / rho;
+            }
             for (int a = 0; a < Q; ++a) {
                 double eu = E[a][0] * uex + E[a][1] * uey;
                 double feq = W[a] * rho * (1.0 + eu / cs2);                 /* Eq. 2 */
                 double fpost = fc[a] + (feq - fc[a]) / tau;                 /* Eq. 13 */
+                if (p->force_model == 1) {
+                    double ef = E[a][0] * fmx + E[a][1] * fmy;
+                    fpost += W[a] * rho * (1.0 - 1.0 / (2.0 * tau)) * ef / cs2;   /* dt F_a, Eqs. 1, 4 */
+                }
                 int xd = x + E[a][0];
                 int yd = y + E[a][1];
                 xd = (xd + nx) % nx;

@@ -64,10 +64,12 @@ class Params:
     bc: int = LBM_BC_PERIODIC
     storage: int = LBM_F32
     scale: float = 0.0
+    force_model: int = 0      # 0: simplified Shan-Chen scheme, 1: Guo scheme
 
     def c(self) -> _abi.lbm_params:
         return _abi.lbm_params(int(self.nx), int(self.ny), float(self.tau), float(self.nu), float(self.eps),
-                               float(self.gx), float(self.gy), int(self.bc), int(self.storage), float(self.scale))
+                               float(self.gx), float(self.gy), int(self.bc), int(self.storage), float(self.scale),
+                               int(self.force_model))
 
 
 # ----------------------------------------------------------------- C ABI mirror
@@ -168,7 +170,8 @@ def lbm_upscale(params: Params, kappa, block: int, keff_coarse, g_const: float =
     """K* per block x block subdomain (Section 3). Returns (status, n_fallback)."""
     p = params.c()
     nfb = C.c_int32(0)
-    st = _check(_abi.lib().lbm_upscale(C.byref(p), _ptr(kappa), int(block), surrogate, float(spread_max),
+    sur = getattr(surrogate, "handle", surrogate)
+    st = _check(_abi.lib().lbm_upscale(C.byref(p), _ptr(kappa), int(block), sur, float(spread_max),
                                        float(g_const), float(tol_rel), int(max_steps), _ptr(keff_coarse),
                                        C.byref(nfb), _stream(stream)),
                 allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
@@ -179,7 +182,8 @@ def lbm_coarse_params(params: Params, block: int) -> Params:
     out = _abi.lbm_params()
     p = params.c()
     _check(_abi.lib().lbm_coarse_params(C.byref(p), int(block), C.byref(out)))
-    return Params(out.nx, out.ny, out.tau, out.nu, out.eps, out.gx, out.gy, out.bc, out.storage, out.scale)
+    return Params(out.nx, out.ny, out.tau, out.nu, out.eps, out.gx, out.gy, out.bc, out.storage, out.scale,
+                  out.force_model)
 
 
 def lbm_coarse_run(params: Params, block: int, keff_coarse, g_coarse=None, max_steps: int = 100000,
@@ -201,6 +205,101 @@ def lbm_block_average(field, block: int, out=None, stream=None):
         out = torch.empty((ny // block, nx // block), dtype=torch.float32, device=field.device)
     _check(_abi.lib().lbm_block_average(_ptr(field), int(nx), int(ny), int(block), _ptr(out), _stream(stream)))
     return out
+
+
+def lbm_patches(kappa, leaves, x=None, stats=None, stream=None):
+    """Surrogate inputs for leaves: x [n, 2, 32, 32] and stats [n, 3] (CUDA float32)."""
+    import torch
+    ny, nx = kappa.shape
+    n = int(leaves.shape[0])
+    if x is None:
+        x = torch.empty((n, 2, 32, 32), dtype=torch.float32, device=kappa.device)
+    if stats is None:
+        stats = torch.empty((n, 3), dtype=torch.float32, device=kappa.device)
+    _check(_abi.lib().lbm_patches(_ptr(kappa), int(nx), int(ny), _ptr(leaves), n, _ptr(x), _ptr(stats),
+                                  _stream(stream)))
+    return x, stats
+
+
+def lbm_surrogate_param_count() -> int:
+    return int(_abi.lib().lbm_surrogate_param_count())
+
+
+class Surrogate:
+    """Owning wrapper of an lbm_surrogate ensemble (the lbm_surrogate_* calls)."""
+
+    def __init__(self, n_models: int = 4, seed: int = 0):
+        self.n_models = n_models
+        h = C.c_void_p()
+        _check(_abi.lib().lbm_surrogate_create(int(n_models), int(seed), C.byref(h)))
+        self.handle = h
+
+    def get_params(self, model: int):
+        import numpy as np
+        out = np.empty(lbm_surrogate_param_count(), dtype=np.float32)
+        _check(_abi.lib().lbm_surrogate_get_params(self.handle, int(model), out.ctypes.data))
+        return out
+
+    def set_params(self, model: int, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == lbm_surrogate_param_count()
+        _check(_abi.lib().lbm_surrogate_set_params(self.handle, int(model), p.ctypes.data))
+
+    def get_normalization(self):
+        import numpy as np
+        out = np.empty(13, dtype=np.float32)
+        _check(_abi.lib().lbm_surrogate_get_normalization(self.handle, out.ctypes.data))
+        return out
+
+    def set_normalization(self, norm):
+        import numpy as np
+        p = np.ascontiguousarray(norm, dtype=np.float32)
+        assert p.size == 13
+        _check(_abi.lib().lbm_surrogate_set_normalization(self.handle, p.ctypes.data))
+
+    def train(self, x, y, stats, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, stream=None):
+        import numpy as np
+        loss = np.zeros((self.n_models, epochs), dtype=np.float32)
+        _check(_abi.lib().lbm_surrogate_train(self.handle, _ptr(x), _ptr(y), _ptr(stats), int(x.shape[0]),
+                                              int(epochs), int(batch), float(lr), int(seed), loss.ctypes.data,
+                                              _stream(stream)))
+        return loss
+
+    def predict(self, x, stream=None):
+        import torch
+        n = int(x.shape[0])
+        y = torch.empty((self.n_models, n, 2), dtype=torch.float32, device=x.device)
+        _check(_abi.lib().lbm_surrogate_predict(self.handle, _ptr(x), n, _ptr(y), _stream(stream)))
+        return y
+
+    def grad(self, model: int, x, t, stream=None):
+        """(grad [P], loss, y [n, 2]) of one forward/backward pass (standardised targets t)."""
+        import numpy as np
+        n = int(x.shape[0])
+        g = np.empty(lbm_surrogate_param_count(), dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        y = np.empty((n, 2), dtype=np.float32)
+        _check(_abi.lib().lbm_surrogate_grad(self.handle, int(model), _ptr(x), _ptr(t), n, g.ctypes.data,
+                                             loss.ctypes.data, y.ctypes.data, _stream(stream)))
+        return g, float(loss[0]), y
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _check(_abi.lib().lbm_surrogate_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ convenience

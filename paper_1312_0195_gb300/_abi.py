@@ -25,7 +25,7 @@ class lbm_params(C.Structure):
                 ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double),
                 ("bc", C.c_int32), ("storage", C.c_int32),
-                ("scale", C.c_double)]
+                ("scale", C.c_double), ("force_model", C.c_int32)]
 
 
 class lbm_leaf(C.Structure):
@@ -59,6 +59,17 @@ SIGNATURES = {
     "lbm_coarse_params": (C.c_int, [_PP, _I32, _PP]),
     "lbm_coarse_run": (C.c_int, [_PP, _I32, _P, _P, _I64, _D, _I32, _P, _P, _P, C.POINTER(_I64), _P]),
     "lbm_block_average": (C.c_int, [_P, _I32, _I32, _I32, _P, _P]),
+    "lbm_surrogate_param_count": (_I64, []),
+    "lbm_surrogate_create": (C.c_int, [_I32, C.c_uint64, C.POINTER(_P)]),
+    "lbm_surrogate_destroy": (C.c_int, [_P]),
+    "lbm_surrogate_get_params": (C.c_int, [_P, _I32, _P]),
+    "lbm_surrogate_set_params": (C.c_int, [_P, _I32, _P]),
+    "lbm_surrogate_set_normalization": (C.c_int, [_P, _P]),
+    "lbm_surrogate_get_normalization": (C.c_int, [_P, _P]),
+    "lbm_patches": (C.c_int, [_P, _I32, _I32, _P, _I32, _P, _P, _P]),
+    "lbm_surrogate_train": (C.c_int, [_P, _P, _P, _P, _I32, _I32, _I32, _D, C.c_uint64, _P, _P]),
+    "lbm_surrogate_predict": (C.c_int, [_P, _P, _I32, _P, _P]),
+    "lbm_surrogate_grad": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _P, _P]),
 }
 
 _lib = None

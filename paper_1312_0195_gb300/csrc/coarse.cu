@@ -26,6 +26,9 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
                            int32_t persistent, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
                            void *cuda_stream, double time_limit_s);
 double local_time_limit();
+lbm_status upscale_with_surrogate(const lbm_params *p, const float *kappa_dev, int32_t block, lbm_surrogate *s,
+                                  double spread_max, double g_const, double tol_rel, int64_t max_steps,
+                                  double *keff_dev, int32_t *n_fallback, void *cuda_stream);
 
 namespace {
 
@@ -153,8 +156,9 @@ lbm_status lbm_upscale(const lbm_params *p, const float *kappa_dev, int32_t bloc
     if (s != LBM_OK) return s;
     if (block < 1 || block > 64 || p->nx % block || p->ny % block)
         return fail(LBM_EINVAL, "block must be in [1, 64] and divide nx, ny");
-    if (sur) return fail(LBM_EINVAL, "no surrogate ensemble support in this build: pass NULL");
-    (void)spread_max;
+    // the ensemble is logically const here: only its internal work buffers are reused
+    if (sur) return upscale_with_surrogate(p, kappa_dev, block, const_cast<lbm_surrogate *>(sur), spread_max, g_const,
+                                           tol_rel, max_steps, keff_coarse_dev, n_fallback, cuda_stream);
     const int cx = p->nx / block, cy = p->ny / block;
     const int64_t nl = (int64_t)cx * cy;
     if (nl > (int64_t)1 << 30) return fail(LBM_EINVAL, "too many blocks");

@@ -70,6 +70,7 @@ lbm_status validate_params(const lbm_params *p)
     if (p->storage != LBM_F32 && p->storage != LBM_F16 && p->storage != LBM_F64)
         return fail(LBM_EINVAL, "unknown storage %d", p->storage);
     if (!finite(p->scale) || p->scale < 0.0) return fail(LBM_EINVAL, "scale must be finite and >= 0");
+    if (p->force_model != 0 && p->force_model != 1) return fail(LBM_EINVAL, "unknown force_model %d", p->force_model);
     if (p->scale > 0.0) {
         int ex2;
         double m = std::frexp(p->scale, &ex2);
@@ -148,6 +149,8 @@ static StepArgs<T, CT> make_args(const lbm_grid *g, const void *src, void *dst)
     a.gx = (CT)g->p.gx;
     a.gy = (CT)g->p.gy;
     a.rho0 = (CT)g->S;
+    a.guo = g->p.force_model == 1 ? 1 : 0;
+    a.guo_c = (CT)(6.0 * (1.0 - 1.0 / (2.0 * g->p.tau)));
     a.src = static_cast<const T *>(src);
     a.dst = static_cast<T *>(dst);
     a.coef = static_cast<const CT *>(g->coef);

@@ -32,6 +32,8 @@ struct StepArgs {
     CT half_eps;          // eps dt / 2        (Eq. 6)
     CT gx, gy;            // constant force when gfield == nullptr
     CT rho0;              // rest density in storage units (the FP16 scale S, else 1)
+    int guo;              // 1: Guo forcing (u_eq = u plus the forcing term of Eq. 4)
+    CT guo_c;             // 6 (1 - 1/(2 tau)): F_a = w_a guo_c e_a . (rho u - j)
     const T *src;         // post-collision state of the previous step
     T *dst;
     const CT *coef;       // COEF_SCALAR: e [plane] (rho u = (1 - e) r); COEF_TENSOR: E [4][plane] (rho u = (I - E) r)

@@ -42,11 +42,16 @@ void count_launches(int64_t n);
 namespace {
 
 constexpr int LOCAL_THREADS = 1024;
-constexpr int CMAX = 4096;               // cells resident per CTA
-constexpr int CPT = CMAX / LOCAL_THREADS; // cells per thread
+// cells resident per CTA: 4096 in FP32 (leaves up to 64 x 64), 2048 in FP64 (up to 45 x 45);
+// either way 12 values per cell fill 192 KiB of shared memory
+template <typename T> struct LocalCfg {
+    static constexpr int CMAX = sizeof(T) == 8 ? 2048 : 4096;
+    static constexpr int CPT = CMAX / LOCAL_THREADS;   // cells per thread
+    static constexpr size_t SMEM = (size_t)(9 + 1 + 2) * CMAX * sizeof(T);
+};
 constexpr int MAXSLOTS = 64;
 constexpr int MAXCLASS = 64;
-constexpr size_t LOCAL_SMEM = (size_t)(9 + 1 + 2) * CMAX * sizeof(float);
+constexpr size_t LOCAL_SMEM = LocalCfg<float>::SMEM;
 
 struct LocalArgs {
     const float *kappa;       // field [ny][nx]
@@ -57,7 +62,7 @@ struct LocalArgs {
     int class_off[MAXCLASS + 1];
     int class_size[MAXCLASS];
     int *heads;               // [nclass] queue heads (zeroed before launch)
-    float omega, two_tau, omt, half_eps, gmag;
+    double omega, two_tau, omt, half_eps, gmag;
     double eps_nu;            // eps * nu for the drag coefficient
     double nu_over_g;         // nu / G for Eq. 17
     double tol;
@@ -87,23 +92,25 @@ __device__ __forceinline__ unsigned long long globaltimer()
 }
 
 // drag fraction e = 1 - d = eps nu / (2 kappa + eps nu) of Eq. 6 (see the fine-grid step)
-__device__ __forceinline__ float coef_e(float k, double eps_nu)
+__device__ __forceinline__ double coef_e(float k, double eps_nu)
 {
-    if (!(k >= 0.0f)) return 1.0f;
-    if (eps_nu == 0.0 || isinf(k)) return 0.0f;
-    if (k == 0.0f) return 1.0f;
-    return (float)(eps_nu / (2.0 * (double)k + eps_nu));
+    if (!(k >= 0.0f)) return 1.0;
+    if (eps_nu == 0.0 || isinf(k)) return 0.0;
+    if (k == 0.0f) return 1.0;
+    return eps_nu / (2.0 * (double)k + eps_nu);
 }
 
 __device__ __forceinline__ int wrapi(int v, int s) { return v < 0 ? v + s : (v >= s ? v - s : v); }
 
+template <typename T>
 __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs a)
 {
-    extern __shared__ float smem[];
-    float *F = smem;                    // [9][CMAX]
-    float *D = F + 9 * CMAX;            // [CMAX]
-    float *UX = D + CMAX;               // [CMAX]
-    float *UY = UX + CMAX;              // [CMAX]
+    constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *F = reinterpret_cast<T *>(smem_raw);   // [9][CMAX]
+    T *D = F + 9 * CMAX;                      // [CMAX]
+    T *UX = D + CMAX;                         // [CMAX]
+    T *UY = UX + CMAX;                        // [CMAX]
     __shared__ Slot slots[MAXSLOTS];
     __shared__ int s_abort;
 
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
             }
         }
         __syncthreads();
-        long long T = 0;
+        long long Tcta = 0;          // CTA step counter
         if (tid < nslots) {
             Slot sl;
             sl.job = -1;
@@ -161,15 +168,15 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 const int j = geo >> 12, cly = (geo >> 6) & 63, clx = geo & 63;
                 const Slot &sl = slots[j];
                 if (sl.job < 0) continue;
-                const int t = (int)(T - sl.tstart);
+                const int t = (int)(Tcta - sl.tstart);
                 const int c = tid + i * LOCAL_THREADS;
                 const int base = j * s2;
-                float g[Q];
+                T g[Q];
                 if (t == 0) {
                     const int gx = sl.x0 + clx, gy = sl.y0 + cly;
-                    D[c] = coef_e(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
+                    D[c] = (T)coef_e(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) g[q] = 0.0f;      // rest state
+                    for (int q = 0; q < Q; ++q) g[q] = T(0);      // rest state
                 } else if ((t & 1) == 0) {
 #pragma unroll
                     for (int q = 0; q < Q; ++q) g[q] = F[q * CMAX + c];
@@ -180,34 +187,34 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                         g[q] = F[opp(q) * CMAX + base + nyl * s + nxl];
                     }
                 }
-                const float e = D[c];
-                const float Gx = sl.drive == 0 ? a.gmag : 0.0f;
-                const float Gy = sl.drive == 0 ? 0.0f : a.gmag;
-                float drho = 0.f, jx = 0.f, jy = 0.f;
+                const T e = D[c];
+                const T Gx = sl.drive == 0 ? (T)a.gmag : T(0);
+                const T Gy = sl.drive == 0 ? T(0) : (T)a.gmag;
+                T drho = 0, jx = 0, jy = 0;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     drho += g[q];
-                    jx += (float)ex(q) * g[q];
-                    jy += (float)ey(q) * g[q];
+                    jx += (T)ex(q) * g[q];
+                    jy += (T)ey(q) * g[q];
                 }
-                const float rho = 1.0f + drho;
-                const float rx = jx + a.half_eps * rho * Gx;
-                const float ry = jy + a.half_eps * rho * Gy;
-                const float rux = rx - e * rx;                           // Eq. 6 times rho: (1 - e) r
-                const float ruy = ry - e * ry;
+                const T rho = T(1) + drho;
+                const T rx = jx + (T)a.half_eps * rho * Gx;
+                const T ry = jy + (T)a.half_eps * rho * Gy;
+                const T rux = rx - e * rx;                               // Eq. 6 times rho: (1 - e) r
+                const T ruy = ry - e * ry;
                 const bool check = t == sl.next_check || t == a.max_steps;
                 if (check) {
                     UX[c] = rux / rho;                                   // Eq. 15
                     UY[c] = ruy / rho;
                 }
-                const float uex = a.two_tau * rux + a.omt * jx;          // Eq. 16 times rho
-                const float uey = a.two_tau * ruy + a.omt * jy;
+                const T uex = (T)a.two_tau * rux + (T)a.omt * jx;        // Eq. 16 times rho
+                const T uey = (T)a.two_tau * ruy + (T)a.omt * jy;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const float eu = (float)ex(q) * uex + (float)ey(q) * uey;
-                    const float w = q == 0 ? 4.0f / 9.0f : (q <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
-                    const float geq = w * (drho + 3.0f * eu);             // Eq. 2
-                    g[q] = g[q] + a.omega * (geq - g[q]);                 // Eq. 13
+                    const T eu = (T)ex(q) * uex + (T)ey(q) * uey;
+                    const T w = q == 0 ? T(4.0 / 9.0) : (q <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+                    const T geq = w * (drho + T(3) * eu);                 // Eq. 2
+                    g[q] = g[q] + (T)a.omega * (geq - g[q]);                 // Eq. 13
                 }
                 if ((t & 1) == 0) {
 #pragma unroll
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
             for (int j = wid; j < nslots; j += LOCAL_THREADS / 32) {
                 Slot sl = slots[j];
                 if (sl.job < 0) continue;
-                const int t = (int)(T - sl.tstart);
+                const int t = (int)(Tcta - sl.tstart);
                 const bool check = t == sl.next_check || t == a.max_steps;
                 if (!check && !abort_now) continue;
                 int st = -1;   // -1: keep going
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                             sl.drive = sl.job & 1;
                             sl.x0 = a.leaves[3 * sl.leaf];
                             sl.y0 = a.leaves[3 * sl.leaf + 1];
-                            sl.tstart = T + 1;
+                            sl.tstart = Tcta + 1;
                             sl.next_check = a.check_every;
                             sl.prev = 0.0;
                         } else {
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 }
                 __syncwarp();
             }
-            ++T;
+            ++Tcta;
             __syncthreads();   // slot updates of every warp are visible before they are tested
             any = __syncthreads_or(tid < nslots && slots[tid].job >= 0);
         }
@@ -341,7 +348,8 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     std::vector<int> sizes;
     for (int i = 0; i < n_leaves; ++i) {
         const lbm_leaf &L = lv[i];
-        if (L.size < 1 || L.size > 64) return fail(LBM_EINVAL, "leaf %d: size %d outside [1, 64]", i, L.size);
+        const int smax = p->storage == LBM_F64 ? 45 : 64;   // FP64 leaves hold 2048 cells per CTA
+        if (L.size < 1 || L.size > smax) return fail(LBM_EINVAL, "leaf %d: size %d outside [1, %d]", i, L.size, smax);
         if (L.x0 < 0 || L.y0 < 0 || (int64_t)L.x0 + L.size > p->nx || (int64_t)L.y0 + L.size > p->ny)
             return fail(LBM_EINVAL, "leaf %d (%d, %d, %d) lies outside the %d x %d field", i, L.x0, L.y0, L.size,
                         p->nx, p->ny);
@@ -357,11 +365,11 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.nx = p->nx;
     a.ny = p->ny;
     a.leaves = reinterpret_cast<const int *>(leaves_dev);
-    a.omega = (float)(1.0 / p->tau);
-    a.two_tau = (float)(2.0 * p->tau);
-    a.omt = (float)(1.0 - 2.0 * p->tau);
-    a.half_eps = (float)(0.5 * p->eps);
-    a.gmag = (float)g_const;
+    a.omega = (1.0 / p->tau);
+    a.two_tau = (2.0 * p->tau);
+    a.omt = (1.0 - 2.0 * p->tau);
+    a.half_eps = (0.5 * p->eps);
+    a.gmag = g_const;
     a.eps_nu = p->eps * nu;
     a.nu_over_g = nu / g_const;
     a.tol = tol_rel;
@@ -423,7 +431,10 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.worst = d_flags;
     a.abort_flag = d_flags + 1;
 
-    LOC_CUDA2(cudaFuncSetAttribute(local_keff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LOCAL_SMEM));
+    const bool f64 = p->storage == LBM_F64;
+    auto kern = f64 ? local_keff_kernel<double> : local_keff_kernel<float>;
+    const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
+    LOC_CUDA2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0;
     LOC_CUDA2(cudaGetDevice(&dev));
     if (persistent) {
@@ -437,7 +448,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
         int blocks = sm_count(dev);
         const int64_t max_useful = (int64_t)jobs.size();
         if (blocks > max_useful) blocks = (int)max_useful;
-        local_keff_kernel<<<blocks, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
+        kern<<<blocks, LOCAL_THREADS, smem, st>>>(a);
         LOC_CUDA2(cudaGetLastError());
         count_launches(1);
     } else {
@@ -447,7 +458,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
             a.class_off[1] = 2 * i + 2;
             a.class_size[0] = lv[i].size;
             a.heads = d_heads + i;
-            local_keff_kernel<<<1, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
+            kern<<<1, LOCAL_THREADS, smem, st>>>(a);
             LOC_CUDA2(cudaGetLastError());
         }
         count_launches(n_leaves);
@@ -659,11 +670,11 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     }
     a.class_off[a.nclass] = head[NA_TABLE + 65 + a.nclass];
     a.heads = scr + NA_HEADS;
-    a.omega = (float)(1.0 / p->tau);
-    a.two_tau = (float)(2.0 * p->tau);
-    a.omt = (float)(1.0 - 2.0 * p->tau);
-    a.half_eps = (float)(0.5 * p->eps);
-    a.gmag = (float)g_const;
+    a.omega = (1.0 / p->tau);
+    a.two_tau = (2.0 * p->tau);
+    a.omt = (1.0 - 2.0 * p->tau);
+    a.half_eps = (0.5 * p->eps);
+    a.gmag = g_const;
     a.eps_nu = p->eps * nu;
     a.nu_over_g = nu / g_const;
     a.tol = tol_rel;
@@ -675,10 +686,10 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     a.worst = scr + NA_FLAGS + 1;
     a.abort_flag = scr + NA_FLAGS + 2;
     a.time_limit_ns = (unsigned long long)(g_time_limit_s * 1e9);
-    NA_CUDA(cudaFuncSetAttribute(local_keff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LOCAL_SMEM));
+    NA_CUDA(cudaFuncSetAttribute(local_keff_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LOCAL_SMEM));
     int blocks = sm_count(dev);
     if (blocks > 2 * n_leaves) blocks = 2 * n_leaves;
-    local_keff_kernel<<<blocks, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
+    local_keff_kernel<float><<<blocks, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
     NA_CUDA(cudaGetLastError());
     count_launches(1);
     int flags[2] = {0, 0};

@@ -83,10 +83,12 @@ __device__ __forceinline__ void load_vec(const CT *p, int64_t i, CT out[VEC])
 }
 
 // The collision of one cell given its streamed deviations gq[9] (in place).
+// Guo scheme (guo != 0): u_eq = u and g* += w_a 3 (1 - 1/(2 tau)) e_a . (rho f_m) with
+// rho f_m = 2 (rho u - j) (Eq. 3 with u_eq = u), i.e. the forcing term of Eq. 4.
 template <typename C, int COEF>
 __device__ __forceinline__ void collide_cell(C (&gq)[Q], C rho0, C half_eps, C Gx, C Gy,
                                              C c0, C c1, C c2, C c3,
-                                             C omega, C two_tau, C omt)
+                                             C omega, C two_tau, C omt, int guo = 0, C guo_c = C(0))
 {
     C drho = 0, jx = 0, jy = 0;
 #pragma unroll
@@ -107,6 +109,20 @@ __device__ __forceinline__ void collide_cell(C (&gq)[Q], C rho0, C half_eps, C G
     } else {                                      // rho u = (I - E) r
         rux = rx - (c0 * rx + c1 * ry);
         ruy = ry - (c2 * rx + c3 * ry);
+    }
+    if (guo) {
+        const C fx = guo_c * (rux - jx), fy = guo_c * (ruy - jy);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            C eu = C(0), ef = C(0);
+            if (ex(a) == 1) { eu += rux; ef += fx; }
+            if (ex(a) == -1) { eu -= rux; ef -= fx; }
+            if (ey(a) == 1) { eu += ruy; ef += fy; }
+            if (ey(a) == -1) { eu -= ruy; ef -= fy; }
+            const C geq = wgt<C>(a) * (drho + C(3) * eu);
+            gq[a] = gq[a] + omega * (geq - gq[a]) + wgt<C>(a) * ef;
+        }
+        return;
     }
     const C uex = two_tau * rux + omt * jx;   // rho u_eq, Eq. 16
     const C uey = two_tau * ruy + omt * jy;
@@ -231,7 +247,7 @@ __global__ void __launch_bounds__(512) step_kernel(StepArgs<T, typename Comp<T>:
 #pragma unroll
             for (int q = 0; q < Q; ++q) gq[q] = g[q][i];
             collide_cell<C, COEF>(gq, a.rho0, a.half_eps, gxv[i], gyv[i], c0[i], c1[i], c2[i], c3[i],
-                                  a.omega, a.two_tau, a.one_m_two_tau);
+                                  a.omega, a.two_tau, a.one_m_two_tau, a.guo, a.guo_c);
 #pragma unroll
             for (int q = 0; q < Q; ++q) g[q][i] = gq[q];
         }

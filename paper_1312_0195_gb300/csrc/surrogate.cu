@@ -1,0 +1,990 @@
+// surrogate.cu -- the learned K* surrogate: patches, forward, backward, Adam,
+// training loop, ensemble inference and the gate that sends doubtful patches
+// back to local LBM. (An addition to the paper's method, which computes every
+// K* by local LBM, Section 3; local LBM here stays the fallback and the judge.)
+#include "lbm_internal.h"
+#include "surrogate_kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace lbm {
+
+lbm_status fail(lbm_status s, const char *fmt, ...);
+bool is_device_ptr(const void *p);
+void count_launches(int64_t n);
+int sm_count(int dev);
+lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev, int32_t n_leaves,
+                           double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
+                           int32_t persistent, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                           void *cuda_stream, double time_limit_s);
+double local_time_limit();
+
+namespace sur {
+
+// ------------------------------------------------------------ parameter layout
+// Per model, FP32 master parameters laid out as
+//   for l in 0..5: W_l [cout][cin][3][3], b_l [cout];  then W_h [2][64], b_h [2].
+struct Layout {
+    int64_t w[NLAYER], b[NLAYER], wh, bh, total;
+    Layout()
+    {
+        int64_t o = 0;
+        for (int l = 0; l < NLAYER; ++l) {
+            w[l] = o;
+            o += (int64_t)cout_of(l) * cin_real(l) * 9;
+            b[l] = o;
+            o += cout_of(l);
+        }
+        wh = o;
+        o += 2 * 64;
+        bh = o;
+        o += 2;
+        total = o;
+    }
+};
+static const Layout LAYOUT;
+
+// ------------------------------------------------------------------ kernels
+
+// Leaf -> 32 x 32 log-K patch (replicate for s < 32, 2x2.. block means of log K
+// for s > 32), as two FP32 input planes [n][2][32][32]: log K and log2(s) / 6;
+// plus (mean, std, gradient energy) of the log-K patch. One CTA per leaf.
+__global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, const int *leaves, float *x,
+                                                   float *stats)
+{
+    const int i = blockIdx.x;
+    const int x0 = leaves[3 * i], y0 = leaves[3 * i + 1], s = leaves[3 * i + 2];
+    __shared__ float p[PIX];
+    __shared__ double red[3][8];
+    for (int q = threadIdx.x; q < PIX; q += blockDim.x) {
+        const int py = q >> 5, px = q & 31;
+        float v;
+        if (s <= IMG) {
+            const int r = IMG / s;
+            v = logf(kappa[(int64_t)(y0 + py / r) * nx + x0 + px / r]);
+        } else {
+            const int r = s / IMG;
+            double acc = 0.0;
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b)
+                    acc += (double)logf(kappa[(int64_t)(y0 + py * r + a) * nx + x0 + px * r + b]);
+            v = (float)(acc / (r * r));
+        }
+        p[q] = v;
+        x[(int64_t)i * 2 * PIX + q] = v;
+        x[(int64_t)i * 2 * PIX + PIX + q] = log2f((float)s) / 6.0f;
+    }
+    __syncthreads();
+    double sm = 0.0, sq = 0.0, ge = 0.0;
+    for (int q = threadIdx.x; q < PIX; q += blockDim.x) {
+        const int py = q >> 5, px = q & 31;
+        const double v = p[q];
+        sm += v;
+        sq += v * v;
+        if (px < 31) { const double d = p[q + 1] - v; ge += d * d; }
+        if (py < 31) { const double d = p[q + 32] - v; ge += d * d; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sm += __shfl_down_sync(0xffffffffu, sm, off);
+        sq += __shfl_down_sync(0xffffffffu, sq, off);
+        ge += __shfl_down_sync(0xffffffffu, ge, off);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][w] = sm; red[1][w] = sq; red[2][w] = ge; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += red[0][k]; b += red[1][k]; c += red[2][k]; }
+        const double mean = a / PIX;
+        const double var = b / PIX - mean * mean;
+        stats[3 * i] = (float)mean;
+        stats[3 * i + 1] = (float)sqrt(var > 0.0 ? var : 0.0);
+        stats[3 * i + 2] = (float)(0.5 * c / (IMG * (IMG - 1)));
+    }
+}
+
+// FP32 [n][2][32][32] inputs (rows idx[b]) -> BF16 NHWC [B][32][32][16] with
+// plane 0 normalised as (x - shift) / scale, plane 1 as is, planes 2..15 zero.
+__global__ void __launch_bounds__(256) input_kernel(const float *x, const int *idx, int B, float shift, float scale,
+                                                   __nv_bfloat16 *out)
+{
+    const int64_t total = (int64_t)B * PIX;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t / PIX), q = (int)(t - (int64_t)b * PIX);
+        const int64_t src = (int64_t)(idx ? idx[b] : b) * 2 * PIX;
+        uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(o);
+        ob[0] = __float2bfloat16_rn((x[src + q] - shift) / scale);
+        ob[1] = __float2bfloat16_rn(x[src + PIX + q]);
+        uint4 *dst = reinterpret_cast<uint4 *>(out + t * CIN0);
+        dst[0] = o[0];
+        dst[1] = o[1];
+    }
+}
+
+// B operand of the forward conv: row n = c_out, k = tap * CIN_P + c_in.
+__global__ void pack_fwd_kernel(const float *w, int cin, int cin_p, int cout, __nv_bfloat16 *out)
+{
+    const int K = 9 * cin_p;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cout * K; t += gridDim.x * blockDim.x) {
+        const int n = t / K, k = t - n * K, tap = k / cin_p, ci = k - tap * cin_p;
+        const float v = ci < cin ? w[((int64_t)n * cin + ci) * 9 + tap] : 0.0f;
+        out[umma::core_offset(n, k, K) / 2] = __float2bfloat16_rn(v);
+    }
+}
+
+// B operand of the input-gradient conv: row n = c_in, k = tap' * COUT + c_out, value
+// W[c_out][c_in][8 - tap'] (the transposed, spatially flipped kernel).
+__global__ void pack_bwd_kernel(const float *w, int cin, int cout, __nv_bfloat16 *out)
+{
+    const int K = 9 * cout;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cin * K; t += gridDim.x * blockDim.x) {
+        const int n = t / K, k = t - n * K, tp = k / cout, co = k - tp * cout;
+        out[umma::core_offset(n, k, K) / 2] = __float2bfloat16_rn(w[((int64_t)co * cin + n) * 9 + (8 - tp)]);
+    }
+}
+
+// Global average pooling of the last activation and the linear head. One CTA per image.
+__global__ void __launch_bounds__(256) gap_head_kernel(const __nv_bfloat16 *act, const float *wh, const float *bh,
+                                                      float *pooled, float *y)
+{
+    const int b = blockIdx.x;
+    __shared__ float part[4][64];
+    __shared__ float pool[64];
+    const int c = threadIdx.x & 63, quarter = threadIdx.x >> 6;
+    float s = 0.0f;
+    for (int q = quarter * 256; q < (quarter + 1) * 256; ++q)
+        s += __bfloat162float(act[((int64_t)b * PIX + q) * 64 + c]);
+    part[quarter][c] = s;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const float v = (part[0][c] + part[1][c] + part[2][c] + part[3][c]) / PIX;
+        pool[c] = v;
+        pooled[(int64_t)b * 64 + c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        float acc = bh[threadIdx.x];
+        for (int k = 0; k < 64; ++k) acc += wh[threadIdx.x * 64 + k] * pool[k];
+        y[(int64_t)b * 2 + threadIdx.x] = acc;
+    }
+}
+
+// Loss L = mean((y - t)^2) over B x 2 entries (targets already standardised), the head's
+// gradients and dL/dpool. One CTA; every sum runs in a fixed order.
+__global__ void __launch_bounds__(256) loss_head_backward_kernel(const float *y, const float *t, const float *pooled,
+                                                                const float *wh, int B, float *dpool, float *gwh,
+                                                                float *gbh, float *loss)
+{
+    __shared__ float dy[2][1024];
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        dy[0][b] = 2.0f * (y[2 * b] - t[2 * b]) / (2.0f * B);
+        dy[1][b] = 2.0f * (y[2 * b + 1] - t[2 * b + 1]) / (2.0f * B);
+    }
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int o = threadIdx.x >> 6, c = threadIdx.x & 63;
+        float acc = 0.0f;
+        for (int b = 0; b < B; ++b) acc += dy[o][b] * pooled[(int64_t)b * 64 + c];
+        gwh[o * 64 + c] = acc;
+    } else if (threadIdx.x < 130) {
+        const int o = threadIdx.x - 128;
+        float acc = 0.0f;
+        for (int b = 0; b < B; ++b) acc += dy[o][b];
+        gbh[o] = acc;
+    } else if (threadIdx.x == 130) {
+        double acc = 0.0;
+        for (int b = 0; b < B; ++b) {
+            const double e0 = (double)y[2 * b] - t[2 * b], e1 = (double)y[2 * b + 1] - t[2 * b + 1];
+            acc += e0 * e0 + e1 * e1;
+        }
+        *loss = (float)(acc / (2.0 * B));
+    }
+    for (int q = threadIdx.x; q < B * 64; q += blockDim.x) {
+        const int b = q >> 6, c = q & 63;
+        dpool[q] = dy[0][b] * wh[c] + dy[1][b] * wh[64 + c];
+    }
+}
+
+// dL/d(last activation), ReLU mask applied: dpool / 1024 where the activation is positive.
+__global__ void __launch_bounds__(256) gap_backward_kernel(const float *dpool, const __nv_bfloat16 *act, int B,
+                                                          __nv_bfloat16 *dact)
+{
+    const int64_t total = (int64_t)B * PIX * 64;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t / (PIX * 64);
+        const int c = (int)(t & 63);
+        const float g = __bfloat162float(act[t]) > 0.0f ? dpool[b * 64 + c] / PIX : 0.0f;
+        dact[t] = __float2bfloat16_rn(g);
+    }
+}
+
+// Weight gradient of one conv layer for one (image, tap) on CUDA cores in FP32:
+//   part[b][tap][co][ci] = sum_p dout[b][p][co] * in[b][p + off(tap)][ci]
+// and, for tap 0, the bias partial sum_p dout[b][p][co]. Each thread owns a
+// 4 x TCI block of (co, ci); rows of 32 pixels are staged in shared memory.
+template <int COUT, int CINP, int CIN>
+__global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part,
+                                                   float *bpart)
+{
+    constexpr int TCI = (COUT * CIN) / 1024 > 0 ? (COUT * CIN) / 1024 : 1;
+    constexpr int NCOB = COUT / 4, NCIB = CIN / TCI;
+    const int b = blockIdx.x / 9, tap = blockIdx.x % 9, dy = tap / 3, dx = tap % 3;
+    __shared__ float sO[IMG][COUT];
+    __shared__ float sI[IMG][CIN];
+    const int tid = threadIdx.x;
+    const bool active = tid < NCOB * NCIB;
+    const int cob = tid % NCOB, cib = tid / NCOB;
+    float acc[4][TCI];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TCI; ++j) acc[i][j] = 0.0f;
+    float bacc = 0.0f;   // bias partial for channel tid (tap 0)
+    for (int row = 0; row < IMG; ++row) {
+        for (int q = tid; q < IMG * COUT; q += 256) {
+            const int px = q / COUT, c = q - px * COUT;
+            sO[px][c] = __bfloat162float(dout[((int64_t)b * PIX + row * IMG + px) * COUT + c]);
+        }
+        const int ys = row + dy - 1;
+        for (int q = tid; q < IMG * CIN; q += 256) {
+            const int px = q / CIN, c = q - px * CIN;
+            const int xs = px + dx - 1;
+            float v = 0.0f;
+            if (ys >= 0 && ys < IMG && xs >= 0 && xs < IMG)
+                v = __bfloat162float(in[((int64_t)b * PIX + ys * IMG + xs) * CINP + c]);
+            sI[px][c] = v;
+        }
+        __syncthreads();
+        if (active) {
+            for (int px = 0; px < IMG; ++px) {
+                float o4[4], iv[TCI];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) o4[i] = sO[px][cob * 4 + i];
+#pragma unroll
+                for (int j = 0; j < TCI; ++j) iv[j] = sI[px][cib * TCI + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < TCI; ++j) acc[i][j] += o4[i] * iv[j];
+            }
+        }
+        if (tap == 0 && tid < COUT)
+            for (int px = 0; px < IMG; ++px) bacc += sO[px][tid];
+        __syncthreads();
+    }
+    if (active) {
+        float *dst = part + ((int64_t)b * 9 + tap) * COUT * CIN;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TCI; ++j) dst[(cob * 4 + i) * CIN + cib * TCI + j] = acc[i][j];
+    }
+    if (tap == 0 && tid < COUT) bpart[(int64_t)b * COUT + tid] = bacc;
+}
+
+// Fold the per-image partials in image order into the layer's gradient slots.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float *part, const float *bpart, int B, int cout,
+                                                          int cin, float *gw, float *gb)
+{
+    const int nw = cout * cin * 9;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nw + cout; t += gridDim.x * blockDim.x) {
+        if (t < nw) {
+            const int co = t / (cin * 9), rem = t - co * cin * 9, ci = rem / 9, tap = rem - ci * 9;
+            float acc = 0.0f;
+            for (int b = 0; b < B; ++b) acc += part[(((int64_t)b * 9 + tap) * cout + co) * cin + ci];
+            gw[t] = acc;
+        } else {
+            const int co = t - nw;
+            float acc = 0.0f;
+            for (int b = 0; b < B; ++b) acc += bpart[(int64_t)b * cout + co];
+            gb[co] = acc;
+        }
+    }
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters.
+__global__ void __launch_bounds__(256) adam_kernel(float *p, const float *g, float *m, float *v, int64_t n, float lr,
+                                                  float b1, float b2, float eps, float c1, float c2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// Sum and sum of squares of the log-K planes of x [n][2][32][32], per block (fixed order).
+__global__ void __launch_bounds__(256) input_moments_kernel(const float *x, int n, double *part)
+{
+    double s = 0.0, q = 0.0;
+    const int64_t total = (int64_t)n * PIX;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / PIX, pq = t - i * PIX;
+        const double v = x[i * 2 * PIX + pq];
+        s += v;
+        q += v * v;
+    }
+    __shared__ double sh[2][256];
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < 256; ++k) { a += sh[0][k]; b += sh[1][k]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// standardised predictions -> log K* (y * std + mean), [model][n][2]
+__global__ void destandardise_kernel(float *y, int64_t n2, float m0, float s0, float m1, float s1)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (i & 1) ? y[i] * s1 + m1 : y[i] * s0 + m0;
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <int CIN_P, int COUT, int EPI>
+cudaError_t launch_conv(const ConvArgs &a, cudaStream_t st)
+{
+    using S = ConvShape<CIN_P, COUT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN_P, COUT, EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    conv3x3_tc_kernel<CIN_P, COUT, EPI><<<a.nimg * 8, 128, S::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_forward(int l, const ConvArgs &a, cudaStream_t st)
+{
+    switch (l) {
+    case 0: return launch_conv<16, 32, EPI_BIAS_RELU>(a, st);
+    case 1: return launch_conv<32, 32, EPI_BIAS_RELU>(a, st);
+    case 2: return launch_conv<32, 64, EPI_BIAS_RELU>(a, st);
+    default: return launch_conv<64, 64, EPI_BIAS_RELU>(a, st);
+    }
+}
+
+// input gradient of layer l (l >= 1): CIN_P' = cout(l), COUT' = cin(l)
+cudaError_t conv_dgrad(int l, const ConvArgs &a, cudaStream_t st)
+{
+    switch (l) {
+    case 1: return launch_conv<32, 32, EPI_MASK>(a, st);
+    case 2: return launch_conv<64, 32, EPI_MASK>(a, st);
+    default: return launch_conv<64, 64, EPI_MASK>(a, st);
+    }
+}
+
+cudaError_t wgrad(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part, float *bpart, int B,
+                  cudaStream_t st)
+{
+    const dim3 grid(B * 9);
+    switch (l) {
+    case 0: wgrad_kernel<32, 16, 2><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
+    case 1: wgrad_kernel<32, 32, 32><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
+    case 2: wgrad_kernel<64, 32, 32><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
+    default: wgrad_kernel<64, 64, 64><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
+    }
+    return cudaGetLastError();
+}
+
+int nblk(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b)); }
+
+// splitmix64 (Steele, Lea, Flood 2014) for the library's own initialisation and shuffles
+struct SplitMix {
+    uint64_t s;
+    uint64_t next()
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (next() >> 11) * (1.0 / 9007199254740992.0); }
+    double normal()
+    {
+        const double u1 = uniform() + 1e-300, u2 = uniform();
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    }
+};
+
+}  // namespace sur
+}  // namespace lbm
+
+using namespace lbm;
+using namespace lbm::sur;
+
+// ------------------------------------------------------------- the ensemble
+
+struct lbm_surrogate {
+    int nmodels = 0;
+    int dev = 0;
+    float *params = nullptr;      // device [nmodels][P] FP32 master
+    float *adam_m = nullptr, *adam_v = nullptr;
+    int64_t adam_t = 0;
+    __nv_bfloat16 *wf[NLAYER] = {};   // packed forward weights (current model)
+    __nv_bfloat16 *wb[NLAYER] = {};   // packed input-gradient weights (current model)
+    // normalisation: input plane 0 and targets; stats range for the gate
+    float in_shift = 0.0f, in_scale = 1.0f;
+    float y_mean[2] = {0.0f, 0.0f}, y_std[2] = {1.0f, 1.0f};
+    float stat_lo[3] = {-1e30f, -1e30f, -1e30f}, stat_hi[3] = {1e30f, 1e30f, 1e30f};
+    // work buffers sized for `cap` images
+    int cap = 0;
+    __nv_bfloat16 *act[NLAYER + 1] = {};
+    __nv_bfloat16 *dact[2] = {};
+    float *pooled = nullptr, *y = nullptr, *t = nullptr, *dpool = nullptr, *grad = nullptr, *loss = nullptr;
+    float *part = nullptr, *bpart = nullptr;
+    int *idx = nullptr, *err = nullptr;
+};
+
+namespace lbm {
+namespace sur {
+
+static void free_work(lbm_surrogate *s)
+{
+    for (auto &p : s->act) { cudaFree(p); p = nullptr; }
+    for (auto &p : s->dact) { cudaFree(p); p = nullptr; }
+    cudaFree(s->pooled); cudaFree(s->y); cudaFree(s->t); cudaFree(s->dpool); cudaFree(s->grad);
+    cudaFree(s->loss); cudaFree(s->part); cudaFree(s->bpart); cudaFree(s->idx);
+    s->pooled = s->y = s->t = s->dpool = s->grad = s->loss = s->part = s->bpart = nullptr;
+    s->idx = nullptr;
+    s->cap = 0;
+    cudaGetLastError();
+}
+
+static lbm_status ensure_work(lbm_surrogate *s, int B)
+{
+    if (B <= s->cap) return LBM_OK;
+    free_work(s);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l <= NLAYER && e == cudaSuccess; ++l) {
+        const int c = l == 0 ? CIN0 : cout_of(l - 1);
+        e = cudaMalloc(&s->act[l], sizeof(__nv_bfloat16) * (size_t)B * PIX * c);
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&s->dact[k], sizeof(__nv_bfloat16) * (size_t)B * PIX * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&s->pooled, sizeof(float) * (size_t)B * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&s->y, sizeof(float) * (size_t)B * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&s->t, sizeof(float) * (size_t)B * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dpool, sizeof(float) * (size_t)B * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&s->grad, sizeof(float) * (size_t)LAYOUT.total);
+    if (e == cudaSuccess) e = cudaMalloc(&s->loss, sizeof(float) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(float) * (size_t)B * 9 * 64 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&s->bpart, sizeof(float) * (size_t)B * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&s->idx, sizeof(int) * (size_t)B);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_work(s);
+        return fail(LBM_ENOMEM, "surrogate work buffers for %d images: %s", B, cudaGetErrorString(e));
+    }
+    s->cap = B;
+    return LBM_OK;
+}
+
+// packs model m's weights for the tensor-core convolutions
+static cudaError_t pack_model(lbm_surrogate *s, int m, cudaStream_t st)
+{
+    const float *P = s->params + (int64_t)m * LAYOUT.total;
+    for (int l = 0; l < NLAYER; ++l) {
+        const int ci = cin_real(l), cp = cin_p(l), co = cout_of(l);
+        pack_fwd_kernel<<<nblk((int64_t)co * 9 * cp), 256, 0, st>>>(P + LAYOUT.w[l], ci, cp, co, s->wf[l]);
+        if (l >= 1) pack_bwd_kernel<<<nblk((int64_t)ci * 9 * co), 256, 0, st>>>(P + LAYOUT.w[l], ci, co, s->wb[l]);
+    }
+    count_launches(2 * NLAYER - 1);
+    return cudaGetLastError();
+}
+
+// forward of model m on act[0] (B images): fills act[1..6], pooled, y (standardised units)
+static cudaError_t forward(lbm_surrogate *s, int m, int B, cudaStream_t st)
+{
+    const float *P = s->params + (int64_t)m * LAYOUT.total;
+    for (int l = 0; l < NLAYER; ++l) {
+        ConvArgs a{s->act[l], s->wf[l], P + LAYOUT.b[l], nullptr, s->act[l + 1], B, s->err};
+        cudaError_t e = conv_forward(l, a, st);
+        if (e != cudaSuccess) return e;
+    }
+    gap_head_kernel<<<B, 256, 0, st>>>(s->act[NLAYER], P + LAYOUT.wh, P + LAYOUT.bh, s->pooled, s->y);
+    count_launches(NLAYER + 1);
+    return cudaGetLastError();
+}
+
+// backward of model m after forward(): gradient of mean((y - t)^2) into s->grad, loss into s->loss[0]
+static cudaError_t backward(lbm_surrogate *s, int m, int B, cudaStream_t st)
+{
+    const float *P = s->params + (int64_t)m * LAYOUT.total;
+    float *G = s->grad;
+    loss_head_backward_kernel<<<1, 256, 0, st>>>(s->y, s->t, s->pooled, P + LAYOUT.wh, B, s->dpool, G + LAYOUT.wh,
+                                                 G + LAYOUT.bh, s->loss);
+    gap_backward_kernel<<<nblk((int64_t)B * PIX * 64), 256, 0, st>>>(s->dpool, s->act[NLAYER], B, s->dact[0]);
+    count_launches(2);
+    int cur = 0;
+    for (int l = NLAYER - 1; l >= 0; --l) {
+        cudaError_t e = wgrad(l, s->act[l], s->dact[cur], s->part, s->bpart, B, st);
+        if (e != cudaSuccess) return e;
+        const int co = cout_of(l), ci = cin_real(l);
+        wgrad_reduce_kernel<<<nblk((int64_t)co * ci * 9 + co), 256, 0, st>>>(s->part, s->bpart, B, co, ci,
+                                                                           G + LAYOUT.w[l], G + LAYOUT.b[l]);
+        count_launches(2);
+        if (l >= 1) {
+            // dL/d(act_l) masked by act_l > 0: the masked gradient of layer l-1's output
+            ConvArgs a{s->dact[cur], s->wb[l], nullptr, s->act[l], s->dact[1 - cur], B, s->err};
+            e = conv_dgrad(l, a, st);
+            if (e != cudaSuccess) return e;
+            count_launches(1);
+            cur = 1 - cur;
+        }
+    }
+    return cudaGetLastError();
+}
+
+static lbm_status check_err(lbm_surrogate *s, cudaStream_t st)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "surrogate: %s", cudaGetErrorString(e));
+    }
+    if (h) return fail(LBM_ETIMEOUT, "surrogate: a tensor-core wait gave up (results not valid)");
+    return LBM_OK;
+}
+
+}  // namespace sur
+}  // namespace lbm
+
+#define SUR_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            cudaGetLastError();                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s failed: %s", #call, \
+                        cudaGetErrorString(e_));                                               \
+        }                                                                                      \
+    } while (0)
+
+extern "C" {
+
+int64_t lbm_surrogate_param_count(void) { return LAYOUT.total; }
+
+lbm_status lbm_surrogate_create(int32_t n_models, uint64_t seed, lbm_surrogate **out)
+{
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_models < 1 || n_models > 16) return fail(LBM_EINVAL, "n_models must be in [1, 16]");
+    lbm_surrogate *s = new lbm_surrogate();
+    s->nmodels = n_models;
+    cudaGetDevice(&s->dev);
+    const int64_t P = LAYOUT.total;
+    auto bail = [&](lbm_status st) { lbm_surrogate_destroy(s); return st; };
+    cudaError_t e = cudaMalloc(&s->params, sizeof(float) * P * n_models);
+    if (e == cudaSuccess) e = cudaMalloc(&s->adam_m, sizeof(float) * P * n_models);
+    if (e == cudaSuccess) e = cudaMalloc(&s->adam_v, sizeof(float) * P * n_models);
+    if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
+    for (int l = 0; l < NLAYER && e == cudaSuccess; ++l) {
+        e = cudaMalloc(&s->wf[l], 2 * (size_t)cout_of(l) * 9 * cin_p(l));
+        if (e == cudaSuccess) e = cudaMalloc(&s->wb[l], 2 * (size_t)cin_p(l) * 9 * cout_of(l));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LBM_ENOMEM, "surrogate parameters: %s", cudaGetErrorString(e)));
+    }
+    // He-normal conv weights, zero biases, head ~ N(0, 1/64); splitmix64 per model
+    std::vector<float> h((size_t)P);
+    for (int m = 0; m < n_models; ++m) {
+        SplitMix rng{seed * 0x100000001B3ull + (uint64_t)m * 0x9E3779B97F4A7C15ull + 1};
+        std::fill(h.begin(), h.end(), 0.0f);
+        for (int l = 0; l < NLAYER; ++l) {
+            const double sd = std::sqrt(2.0 / (9.0 * cin_real(l)));
+            for (int64_t i = 0; i < (int64_t)cout_of(l) * cin_real(l) * 9; ++i) h[LAYOUT.w[l] + i] = (float)(sd * rng.normal());
+        }
+        for (int i = 0; i < 128; ++i) h[LAYOUT.wh + i] = (float)(rng.normal() / 8.0);
+        e = cudaMemcpy(s->params + (int64_t)m * P, h.data(), sizeof(float) * P, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaMemset(s->adam_m, 0, sizeof(float) * P * n_models);
+    if (e == cudaSuccess) e = cudaMemset(s->adam_v, 0, sizeof(float) * P * n_models);
+    if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(LBM_ECUDA, "surrogate initialisation: %s", cudaGetErrorString(e)));
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_destroy(lbm_surrogate *s)
+{
+    if (!s) return LBM_OK;
+    free_work(s);
+    cudaFree(s->params); cudaFree(s->adam_m); cudaFree(s->adam_v); cudaFree(s->err);
+    for (int l = 0; l < NLAYER; ++l) { cudaFree(s->wf[l]); cudaFree(s->wb[l]); }
+    cudaGetLastError();
+    delete s;
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_get_params(const lbm_surrogate *s, int32_t model, float *host_out)
+{
+    if (!s || !host_out || model < 0 || model >= s->nmodels) return fail(LBM_EINVAL, "bad surrogate, model or output");
+    SUR_CUDA(cudaMemcpy(host_out, s->params + (int64_t)model * LAYOUT.total, sizeof(float) * LAYOUT.total,
+                        cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_set_params(lbm_surrogate *s, int32_t model, const float *host_in)
+{
+    if (!s || !host_in || model < 0 || model >= s->nmodels) return fail(LBM_EINVAL, "bad surrogate, model or input");
+    SUR_CUDA(cudaMemcpy(s->params + (int64_t)model * LAYOUT.total, host_in, sizeof(float) * LAYOUT.total,
+                        cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13])
+{
+    if (!s || !norm) return fail(LBM_EINVAL, "bad surrogate or norm");
+    if (!(norm[1] > 0.0f) || !(norm[3] > 0.0f) || !(norm[5] > 0.0f)) return fail(LBM_EINVAL, "scales must be > 0");
+    s->in_shift = norm[0]; s->in_scale = norm[1];
+    s->y_mean[0] = norm[2]; s->y_std[0] = norm[3]; s->y_mean[1] = norm[4]; s->y_std[1] = norm[5];
+    for (int k = 0; k < 3; ++k) { s->stat_lo[k] = norm[6 + 2 * k]; s->stat_hi[k] = norm[7 + 2 * k]; }
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_get_normalization(const lbm_surrogate *s, float norm[13])
+{
+    if (!s || !norm) return fail(LBM_EINVAL, "bad surrogate or norm");
+    norm[0] = s->in_shift; norm[1] = s->in_scale;
+    norm[2] = s->y_mean[0]; norm[3] = s->y_std[0]; norm[4] = s->y_mean[1]; norm[5] = s->y_std[1];
+    for (int k = 0; k < 3; ++k) { norm[6 + 2 * k] = s->stat_lo[k]; norm[7 + 2 * k] = s->stat_hi[k]; }
+    norm[12] = 0.0f;
+    return LBM_OK;
+}
+
+lbm_status lbm_patches(const float *kappa_dev, int32_t nx, int32_t ny, const lbm_leaf *leaves_dev, int32_t n,
+                       float *x_dev, float *stats_dev, void *cuda_stream)
+{
+    if (nx < 1 || ny < 1 || n < 0) return fail(LBM_EINVAL, "bad sizes");
+    if (n == 0) return LBM_OK;
+    if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(x_dev) || !is_device_ptr(stats_dev))
+        return fail(LBM_EINVAL, "kappa, leaves, x and stats must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<lbm_leaf> lv(n);
+    SUR_CUDA(cudaMemcpyAsync(lv.data(), leaves_dev, sizeof(lbm_leaf) * n, cudaMemcpyDeviceToHost, st));
+    SUR_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) {
+        const int s = lv[i].size;
+        const bool ok_size = (s >= 1 && s <= 32 && 32 % s == 0) || (s > 32 && s % 32 == 0 && s <= 1024);
+        if (!ok_size || lv[i].x0 < 0 || lv[i].y0 < 0 || (int64_t)lv[i].x0 + s > nx || (int64_t)lv[i].y0 + s > ny)
+            return fail(LBM_EINVAL, "leaf %d: size %d must divide 32 or be a multiple of 32, inside the field", i, s);
+    }
+    patch_kernel<<<n, 256, 0, st>>>(kappa_dev, nx, reinterpret_cast<const int *>(leaves_dev), x_dev, stats_dev);
+    SUR_CUDA(cudaGetLastError());
+    count_launches(1);
+    SUR_CUDA(cudaStreamSynchronize(st));
+    return LBM_OK;
+}
+
+// One forward + backward of `model` on n inputs (standardised targets t_dev [n][2]);
+// gradient of mean((y - t)^2) to grad_host [P], loss to *loss_host; predictions
+// (standardised units) to y_host [n][2] if not NULL. For gradient checks.
+lbm_status lbm_surrogate_grad(lbm_surrogate *s, int32_t model, const float *x_dev, const float *t_dev, int32_t n,
+                              float *grad_host, float *loss_host, float *y_host, void *cuda_stream)
+{
+    if (!s || model < 0 || model >= s->nmodels || n < 1 || n > 1024) return fail(LBM_EINVAL, "bad arguments");
+    if (!is_device_ptr(x_dev) || !is_device_ptr(t_dev)) return fail(LBM_EINVAL, "x and t must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    lbm_status r = ensure_work(s, n);
+    if (r != LBM_OK) return r;
+    SUR_CUDA(pack_model(s, model, st));
+    input_kernel<<<nblk((int64_t)n * PIX), 256, 0, st>>>(x_dev, nullptr, n, s->in_shift, s->in_scale, s->act[0]);
+    count_launches(1);
+    SUR_CUDA(cudaMemcpyAsync(s->t, t_dev, sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, st));
+    SUR_CUDA(forward(s, model, n, st));
+    SUR_CUDA(backward(s, model, n, st));
+    r = check_err(s, st);
+    if (r != LBM_OK) return r;
+    if (grad_host) SUR_CUDA(cudaMemcpy(grad_host, s->grad, sizeof(float) * LAYOUT.total, cudaMemcpyDeviceToHost));
+    if (loss_host) SUR_CUDA(cudaMemcpy(loss_host, s->loss, sizeof(float), cudaMemcpyDeviceToHost));
+    if (y_host) SUR_CUDA(cudaMemcpy(y_host, s->y, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+// Predictions of every model: y_dev [n_models][n][2] = log K*_xx, log K*_yy.
+lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n, float *y_dev, void *cuda_stream)
+{
+    if (!s || n < 0) return fail(LBM_EINVAL, "bad arguments");
+    if (n == 0) return LBM_OK;
+    if (!is_device_ptr(x_dev) || !is_device_ptr(y_dev)) return fail(LBM_EINVAL, "x and y must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int B = n < 2048 ? n : 2048;
+    lbm_status r = ensure_work(s, B);
+    if (r != LBM_OK) return r;
+    for (int m = 0; m < s->nmodels; ++m) {
+        SUR_CUDA(pack_model(s, m, st));
+        for (int b0 = 0; b0 < n; b0 += B) {
+            const int nb = n - b0 < B ? n - b0 : B;
+            input_kernel<<<nblk((int64_t)nb * PIX), 256, 0, st>>>(x_dev + (int64_t)b0 * 2 * PIX, nullptr, nb,
+                                                                 s->in_shift, s->in_scale, s->act[0]);
+            count_launches(1);
+            SUR_CUDA(forward(s, m, nb, st));
+            SUR_CUDA(cudaMemcpyAsync(y_dev + ((int64_t)m * n + b0) * 2, s->y, sizeof(float) * 2 * nb,
+                                     cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    destandardise_kernel<<<nblk((int64_t)s->nmodels * n * 2), 256, 0, st>>>(
+        y_dev, (int64_t)s->nmodels * n * 2, s->y_mean[0], s->y_std[0], s->y_mean[1], s->y_std[1]);
+    count_launches(1);
+    return check_err(s, st);
+}
+
+// Trains every model of the ensemble on n samples: inputs x_dev [n][2][32][32]
+// (lbm_patches), targets y_dev [n][2] = log K*_xx, log K*_yy. Sets the input and
+// target normalisation and the patch-statistics range of the gate from the data
+// (stats_dev [n][3] from lbm_patches). Adam (0.9, 0.999, 1e-8), learning rate lr
+// with cosine decay to lr / 10, mini-batches of `batch` drawn by a seeded
+// shuffle each epoch. loss_host (may be NULL): [n_models][epochs] mean loss.
+lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float *y_dev, const float *stats_dev,
+                               int32_t n, int32_t epochs, int32_t batch, double lr, uint64_t seed, float *loss_host,
+                               void *cuda_stream)
+{
+    if (!s || n < 2 || epochs < 1 || batch < 1 || batch > 1024 || !(lr > 0.0)) return fail(LBM_EINVAL, "bad arguments");
+    if (!is_device_ptr(x_dev) || !is_device_ptr(y_dev) || !is_device_ptr(stats_dev))
+        return fail(LBM_EINVAL, "x, y and stats must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // normalisation from the data (host, once)
+    std::vector<float> hy((size_t)2 * n), hs((size_t)3 * n), hx0;
+    SUR_CUDA(cudaMemcpy(hy.data(), y_dev, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost));
+    SUR_CUDA(cudaMemcpy(hs.data(), stats_dev, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost));
+    double my[2] = {0, 0}, sy[2] = {0, 0}, mx = 0, sx = 0;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 2; ++k) { my[k] += hy[2 * i + k]; sy[k] += (double)hy[2 * i + k] * hy[2 * i + k]; }
+    for (int k = 0; k < 2; ++k) {
+        my[k] /= n;
+        sy[k] = std::sqrt(std::max(sy[k] / n - my[k] * my[k], 1e-12));
+        s->y_mean[k] = (float)my[k];
+        s->y_std[k] = (float)sy[k];
+    }
+    {   // mean and standard deviation of the log-K planes over every training pixel
+        constexpr int NB = 256;
+        double *d_part = nullptr;
+        SUR_CUDA(cudaMalloc(&d_part, sizeof(double) * 2 * NB));
+        input_moments_kernel<<<NB, 256, 0, cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : nullptr>>>(
+            x_dev, n, d_part);
+        count_launches(1);
+        double hp[2 * NB];
+        cudaError_t e2 = cudaMemcpy(hp, d_part, sizeof hp, cudaMemcpyDeviceToHost);
+        cudaFree(d_part);
+        if (e2 != cudaSuccess) { cudaGetLastError(); return fail(LBM_ECUDA, "input moments: %s", cudaGetErrorString(e2)); }
+        for (int k = 0; k < NB; ++k) { mx += hp[2 * k]; sx += hp[2 * k + 1]; }
+        const double cnt = (double)n * PIX;
+        mx /= cnt;
+        sx = std::sqrt(std::max(sx / cnt - mx * mx, 1e-12));
+    }
+    s->in_shift = (float)mx;
+    s->in_scale = (float)sx;
+    for (int k = 0; k < 3; ++k) {
+        std::vector<float> col(n);
+        for (int i = 0; i < n; ++i) col[i] = hs[3 * i + k];
+        std::sort(col.begin(), col.end());
+        s->stat_lo[k] = col[(size_t)(0.005 * (n - 1))];
+        s->stat_hi[k] = col[(size_t)(0.995 * (n - 1))];
+    }
+    // standardised targets
+    std::vector<float> ty((size_t)2 * n);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 2; ++k) ty[2 * i + k] = (float)((hy[2 * i + k] - my[k]) / sy[k]);
+    float *d_ty = nullptr;
+    SUR_CUDA(cudaMalloc(&d_ty, sizeof(float) * 2 * n));
+    cudaError_t e = cudaMemcpy(d_ty, ty.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice);
+    lbm_status r = e == cudaSuccess ? ensure_work(s, batch) : fail(LBM_ECUDA, "target upload failed");
+    if (r != LBM_OK) { cudaFree(d_ty); return r; }
+    const int steps_per_epoch = n / batch > 0 ? n / batch : 1;
+    const int64_t total_steps = (int64_t)steps_per_epoch * epochs;
+    std::vector<int> order(n), bidx(batch);
+    std::vector<float> tb((size_t)2 * batch);
+    for (int m = 0; m < s->nmodels && r == LBM_OK; ++m) {
+        SplitMix rng{seed * 0x2545F4914F6CDD1Dull + (uint64_t)m + 7};
+        int64_t step = 0;
+        for (int ep = 0; ep < epochs && r == LBM_OK; ++ep) {
+            for (int i = 0; i < n; ++i) order[i] = i;
+            for (int i = n - 1; i > 0; --i) std::swap(order[i], order[rng.next() % (uint64_t)(i + 1)]);
+            double ep_loss = 0.0;
+            for (int sb = 0; sb < steps_per_epoch && r == LBM_OK; ++sb, ++step) {
+                const int B = std::min(batch, n - sb * batch);
+                for (int b = 0; b < B; ++b) {
+                    bidx[b] = order[sb * batch + b];
+                    tb[2 * b] = ty[2 * bidx[b]];
+                    tb[2 * b + 1] = ty[2 * bidx[b] + 1];
+                }
+                e = cudaMemcpyAsync(s->idx, bidx.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(s->t, tb.data(), sizeof(float) * 2 * B, cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) e = pack_model(s, m, st);
+                if (e == cudaSuccess) {
+                    input_kernel<<<nblk((int64_t)B * PIX), 256, 0, st>>>(x_dev, s->idx, B, s->in_shift, s->in_scale,
+                                                                        s->act[0]);
+                    count_launches(1);
+                    e = forward(s, m, B, st);
+                }
+                if (e == cudaSuccess) e = backward(s, m, B, st);
+                if (e == cudaSuccess) {
+                    const double frac = total_steps > 1 ? (double)step / (total_steps - 1) : 0.0;
+                    const double lr_t = lr * (0.1 + 0.9 * 0.5 * (1.0 + std::cos(3.141592653589793 * frac)));
+                    const int64_t t = step + 1;
+                    const float c1 = (float)(1.0 - std::pow(0.9, (double)t));
+                    const float c2 = (float)(1.0 - std::pow(0.999, (double)t));
+                    const int64_t P = LAYOUT.total;
+                    adam_kernel<<<nblk(P), 256, 0, st>>>(s->params + m * P, s->grad, s->adam_m + m * P,
+                                                         s->adam_v + m * P, P, (float)lr_t, 0.9f, 0.999f, 1e-8f, c1, c2);
+                    count_launches(1);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) {
+                    float l = 0.0f;
+                    e = cudaMemcpyAsync(&l, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                    ep_loss += l;
+                }
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    r = fail(LBM_ECUDA, "surrogate training step: %s", cudaGetErrorString(e));
+                }
+            }
+            if (loss_host) loss_host[(int64_t)m * epochs + ep] = (float)(ep_loss / steps_per_epoch);
+        }
+        if (r == LBM_OK) r = check_err(s, st);
+    }
+    cudaFree(d_ty);
+    return r;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ the gate
+
+namespace lbm {
+namespace sur {
+
+// Ensemble mean / spread per block and the range test of the patch statistics:
+// accepted blocks get K* = diag(exp(mean log K*_xx), exp(mean log K*_yy)); the
+// others are flagged for local LBM.
+__global__ void gate_kernel(const float *y, int nmodels, int n, const float *stats, float lo0, float hi0, float lo1,
+                            float hi1, float lo2, float hi2, float max_sd, double *keff, int *fallback)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double m[2] = {0.0, 0.0}, q[2] = {0.0, 0.0};
+        for (int k = 0; k < nmodels; ++k)
+            for (int c = 0; c < 2; ++c) {
+                const double v = y[((int64_t)k * n + i) * 2 + c];
+                m[c] += v;
+                q[c] += v * v;
+            }
+        bool ok = true;
+        for (int c = 0; c < 2; ++c) {
+            m[c] /= nmodels;
+            const double var = nmodels > 1 ? (q[c] - nmodels * m[c] * m[c]) / (nmodels - 1) : 0.0;
+            if (!(sqrt(var > 0.0 ? var : 0.0) <= max_sd) || !isfinite(m[c])) ok = false;
+        }
+        const float s0 = stats[3 * i], s1 = stats[3 * i + 1], s2 = stats[3 * i + 2];
+        if (!(s0 >= lo0 && s0 <= hi0 && s1 >= lo1 && s1 <= hi1 && s2 >= lo2 && s2 <= hi2)) ok = false;
+        fallback[i] = ok ? 0 : 1;
+        if (ok) {
+            keff[4 * (int64_t)i] = exp(m[0]);
+            keff[4 * (int64_t)i + 1] = 0.0;
+            keff[4 * (int64_t)i + 2] = 0.0;
+            keff[4 * (int64_t)i + 3] = exp(m[1]);
+        }
+    }
+}
+
+__global__ void scatter_keff_kernel(const double *src, const int *ids, int nf, double *dst)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x)
+        for (int c = 0; c < 4; ++c) dst[4 * (int64_t)ids[j] + c] = src[4 * (int64_t)j + c];
+}
+
+}  // namespace sur
+
+// Upscaling with the ensemble and the LBM fallback (see lbm_upscale in lbm.h).
+lbm_status upscale_with_surrogate(const lbm_params *p, const float *kappa_dev, int32_t block, lbm_surrogate *s,
+                                  double spread_max, double g_const, double tol_rel, int64_t max_steps,
+                                  double *keff_dev, int32_t *n_fallback, void *cuda_stream)
+{
+    using namespace sur;
+    if (!(spread_max > 0.0)) return fail(LBM_EINVAL, "spread_max must be > 0");
+    if (!is_device_ptr(kappa_dev) || !is_device_ptr(keff_dev)) return fail(LBM_EINVAL, "kappa and keff must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int cx = p->nx / block, cy = p->ny / block;
+    const int64_t n64 = (int64_t)cx * cy;
+    if (n64 > (int64_t)1 << 26) return fail(LBM_EINVAL, "too many blocks for the surrogate path");
+    const int n = (int)n64;
+    std::vector<lbm_leaf> lv((size_t)n);
+    for (int J = 0; J < cy; ++J)
+        for (int I = 0; I < cx; ++I) lv[(size_t)J * cx + I] = lbm_leaf{I * block, J * block, block};
+    lbm_leaf *d_leaves = nullptr;
+    float *d_x = nullptr, *d_stats = nullptr, *d_y = nullptr;
+    int *d_fb = nullptr, *d_ids = nullptr;
+    double *d_kf = nullptr;
+    int32_t *d_status = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_leaves); cudaFree(d_x); cudaFree(d_stats); cudaFree(d_y); cudaFree(d_fb); cudaFree(d_ids);
+        cudaFree(d_kf); cudaFree(d_status);
+        cudaGetLastError();
+    };
+    cudaError_t e = cudaMalloc(&d_leaves, sizeof(lbm_leaf) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_x, sizeof(float) * (size_t)n * 2 * PIX);
+    if (e == cudaSuccess) e = cudaMalloc(&d_stats, sizeof(float) * (size_t)n * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&d_y, sizeof(float) * (size_t)n * 2 * s->nmodels);
+    if (e == cudaSuccess) e = cudaMalloc(&d_fb, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_leaves, lv.data(), sizeof(lbm_leaf) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(LBM_ENOMEM, "surrogate upscaling buffers: %s", cudaGetErrorString(e));
+    }
+    lbm_status r = lbm_patches(kappa_dev, p->nx, p->ny, d_leaves, n, d_x, d_stats, cuda_stream);
+    if (r == LBM_OK) r = lbm_surrogate_predict(s, d_x, n, d_y, cuda_stream);
+    if (r != LBM_OK) { cleanup(); return r; }
+    gate_kernel<<<nblk(n), 256, 0, st>>>(d_y, s->nmodels, n, d_stats, s->stat_lo[0], s->stat_hi[0], s->stat_lo[1],
+                                         s->stat_hi[1], s->stat_lo[2], s->stat_hi[2],
+                                         (float)std::log1p(spread_max), keff_dev, d_fb);
+    count_launches(1);
+    std::vector<int> fb((size_t)n);
+    e = cudaMemcpyAsync(fb.data(), d_fb, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cleanup(); return fail(LBM_ECUDA, "gate: %s", cudaGetErrorString(e)); }
+    std::vector<int> ids;
+    std::vector<lbm_leaf> fl;
+    for (int i = 0; i < n; ++i)
+        if (fb[i]) { ids.push_back(i); fl.push_back(lv[i]); }
+    const int nf = (int)ids.size();
+    if (n_fallback) *n_fallback = nf;
+    if (nf == 0) { cleanup(); return LBM_OK; }
+    e = cudaMalloc(&d_ids, sizeof(int) * nf);
+    if (e == cudaSuccess) e = cudaMalloc(&d_kf, sizeof(double) * 4 * nf);
+    if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int32_t) * nf);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_leaves, fl.data(), sizeof(lbm_leaf) * nf, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { cleanup(); return fail(LBM_ENOMEM, "fallback buffers: %s", cudaGetErrorString(e)); }
+    r = local_keff_impl(p, kappa_dev, d_leaves, nf, g_const, tol_rel, max_steps, 64, 1, d_kf, d_status, nullptr,
+                        cuda_stream, local_time_limit());
+    if (r == LBM_OK || r == LBM_ENOTCONV) {
+        scatter_keff_kernel<<<nblk(nf), 256, 0, st>>>(d_kf, d_ids, nf, keff_dev);
+        count_launches(1);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = fail(LBM_ECUDA, "scatter: %s", cudaGetErrorString(e));
+    }
+    cleanup();
+    return r;
+}
+
+}  // namespace lbm

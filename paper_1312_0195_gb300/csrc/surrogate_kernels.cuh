@@ -123,8 +123,10 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a)
             umma::commit(&mbar[b]);
         }
     }
-    // the last commit (tap 8, buffer 0) covers every MMA issued before it
-    bool done = s_fail == 0 && umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);
+    // the last commit (tap 8, buffer 0) covers every MMA issued before it; the
+    // decision is made CTA-wide because tcgen05.ld is warp-collective
+    const bool waited = s_fail == 0 && umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);
+    const bool done = __syncthreads_and(waited ? 1 : 0) != 0;
     if (!done) {
         if (tid == 0) atomicExch(a.err, 1);
         umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);   // give in-flight MMAs a second chance

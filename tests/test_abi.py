@@ -48,7 +48,8 @@ def _params(**kw):
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(tau=0.49), dict(tau=float("nan")),
                                  dict(eps=-0.1), dict(gx=float("inf")), dict(bc=7), dict(storage=3),
-                                 dict(scale=3.0), dict(scale=-1.0), dict(nu=float("nan"))])
+                                 dict(scale=3.0), dict(scale=-1.0), dict(nu=float("nan")),
+                                 dict(force_model=2)])
 def test_create_rejects_bad_params(lib, bad):
     out = C.c_void_p(123)
     p = _params(**bad)

@@ -162,16 +162,19 @@ def test_fiveblock_brinkman_kstar_beats_kstar_err():
     p_err = lbm.Params(nx=400, ny=400, tau=0.5, nu=ex["nu"], eps=ex["eps"])
     keff = torch.empty((40, 40, 4), dtype=torch.float64, device="cuda")
     keff_err = torch.empty_like(keff)
-    # the slow momentum modes of these weak-drag leaves need the tighter test (see the stop-rule reading)
-    lbm.lbm_upscale(p, _t(kap), 10, keff, 5e-7, 1e-9, 2000000)
-    lbm.lbm_upscale(p_err, _t(kap), 10, keff_err, 5e-7, 1e-9, 2000000)
+    # weak drag at tau ~ 1/2: per-step momentum increments are ~1e-5 of the momentum, below what FP32
+    # storage resolves over 10^6 steps, so these local problems run on the FP64 local solver
+    p64 = lbm.Params(nx=400, ny=400, tau=ex["tau"], nu=ex["nu"], eps=ex["eps"], storage=lbm.LBM_F64)
+    p64_err = lbm.Params(nx=400, ny=400, tau=0.5, nu=ex["nu"], eps=ex["eps"], storage=lbm.LBM_F64)
+    lbm.lbm_upscale(p64, _t(kap), 10, keff, 5e-7, 1e-10, 2000000)
+    lbm.lbm_upscale(p64_err, _t(kap), 10, keff_err, 5e-7, 1e-10, 2000000)
     k = keff.cpu().numpy() / ex["k_const"]
     ke = keff_err.cpu().numpy() / ex["k_const"]
     mask = synth.fiveblock_coarse_kappa_eq24(40, 1.0, 0.0) == 1.0
     s_k = np.mean(0.5 * (k[~mask][:, 0] + k[~mask][:, 3]))
     s_e = np.mean(0.5 * (ke[~mask][:, 0] + ke[~mask][:, 3]))
     print(f"E6 K*/K_const {s_k:.5f} (paper 7.367), K*err/K_const {s_e:.5f} (paper 8.485)")
-    assert abs(s_k - 7.367) < 1.5e-3 and abs(s_e - 8.485) < 1.5e-3
+    assert abs(s_k - 7.367) < 1e-3 and abs(s_e - 8.485) < 1e-3
     gfine = ex["gfield"].astype(np.float32)
     gco = synth.sinusoidal_g_field(40, synth.LatticeUnits(0.0025, 2.5e-5).force(1.0))   # fine lattice units
     fine_steps = 100000

@@ -83,6 +83,23 @@ def test_odd_sizes_and_tiny_leaves():
         assert_keff_close(ke[i], ref["keff"], 1e-4)
 
 
+def test_fp64_local_solver_matches_oracle_to_roundoff():
+    """storage = LBM_F64 selects the FP64 local solver (2048 resident cells, leaves up to 45)."""
+    import torch
+    lbm = _lbm()
+    ex = synth.paper_experiment("E6_local")
+    kap = np.asarray(ex["kappa"], dtype=np.float32)
+    p = lbm.Params(nx=10, ny=10, tau=ex["tau"], nu=ex["nu"], eps=ex["eps"], storage=lbm.LBM_F64)
+    lt = torch.tensor([[0, 0, 10]], dtype=torch.int32, device="cuda")
+    ke, st, steps, worst = lbm.local_keff(p, torch.from_numpy(kap).cuda(), lt, ex["g_const"], 0.0, 20000, 64)
+    ref = oracle.local_keff(kap.astype(np.float64), ex["tau"], ex["nu"], ex["eps"], ex["g_const"], tol=0.0,
+                            max_steps=20000, check_every=64)
+    np.testing.assert_allclose(ke.cpu().numpy()[0, [0, 3]], ref["keff"][[0, 3]], rtol=1e-9)
+    big = torch.tensor([[0, 0, 46]], dtype=torch.int32, device="cuda")
+    with pytest.raises(lbm.LbmError):
+        lbm.local_keff(p, torch.zeros((64, 64), device="cuda") + 0.1, big)
+
+
 def test_uniform_leaf_gives_kappa_identity():
     kap = np.full((64, 64), 0.037)
     leaves = np.array([[0, 0, 64], [0, 0, 8], [8, 8, 32]], dtype=np.int32)

@@ -96,6 +96,28 @@ def test_fp32_elementwise_parity(nx, ny, walls):
     assert np.abs(a["rho"] - b["rho"]).max() <= 1e-6
 
 
+def test_guo_force_model_matches_oracle_guo_and_simplified():
+    """Guo scheme (Section 2.1) on the GPU against the oracle's Guo scheme; and, as the paper's E1
+    comparison shows and the algebra of the linear equilibrium implies, against the simplified scheme."""
+    import torch
+    lbm = _lbm()
+    ex = synth.paper_experiment("E1")
+    kap = ex["kappa"].astype(np.float32)
+    outs = {}
+    for fm in (0, 1):
+        p = lbm.Params(nx=100, ny=100, tau=ex["tau"], nu=ex["nu"], eps=ex["eps"], gx=ex["g"][0], force_model=fm)
+        with lbm.Grid(p, torch.from_numpy(kap).cuda()) as G:
+            G.step(1000, 0.0, 0)
+            outs[fm] = G.fields()[1].cpu().numpy().astype(np.float64)
+    prob = oracle.Problem(ex["tau"], ex["nu"], ex["eps"], kappa=kap.astype(np.float64), g=ex["g"], guo=True)
+    f = prob.rest()
+    prob.run(f, 1000)
+    _, uo, _ = prob.fields(f)
+    scale = np.abs(uo).max()
+    assert np.abs(outs[1] - uo).max() <= 1e-5 * scale
+    assert np.abs(outs[1] - outs[0]).max() <= 1e-5 * scale
+
+
 def test_fp64_storage_matches_to_roundoff():
     kap = synth.lognormal_kappa(66, 40, 5.0, 2.0, seed=4)
     args = (kap, 0.7, 0.1, 0.8, (3e-6, 1e-6), True, 400)

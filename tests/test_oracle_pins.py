@@ -111,6 +111,33 @@ def test_isotropic_tensor_equals_scalar():
     np.testing.assert_allclose(fa, fb, rtol=1e-13, atol=1e-17)
 
 
+def test_guo_scheme_uniform_fixed_point():
+    """Section 2.1 (Guo scheme, Eqs. 1-6): the uniform state of Eq. 19 is steady there too (f_m = 0)."""
+    kap, G, tau, nu, eps = 0.3, (1e-3, 2e-4), 0.8, 0.05, 0.7
+    p = oracle.Problem(tau, nu, eps, kappa=np.full((4, 5), kap), g=G, guo=True)
+    u = np.array(G) * kap / nu
+    f = np.broadcast_to(_lattice_f(u), (4, 5, 9)).copy()
+    assert np.abs(p.step(f) - f).max() <= 1e-14
+
+
+def test_guo_and_simplified_schemes_coincide():
+    """Section 4.1 (E1): the paper finds excellent agreement between the Guo and the simplified
+    Shan-Chen schemes. With the linear equilibrium of Eq. 2 they are the same update: both give
+    the post-collision first moment j + (rho u_eq - j)/tau + sum_a e_a F_a = 2 rho u + (1/tau - 2) j,
+    so the two oracle runs agree to round-off at every step (here 300 steps of E1)."""
+    ex = synth.paper_experiment("E1")
+    out = []
+    for guo in (False, True):
+        p = oracle.Problem(ex["tau"], ex["nu"], ex["eps"], kappa=ex["kappa"], g=ex["g"], guo=guo)
+        f = p.rest()
+        p.run(f, 300)
+        out.append(p.fields(f))
+    (r0, u0, v0), (r1, u1, v1) = out
+    assert np.linalg.norm(u1 - u0) <= 1e-12 * np.linalg.norm(u0)
+    assert np.linalg.norm(v1 - v0) <= 1e-12 * np.linalg.norm(u0)
+    assert np.abs(r1 - r0).max() <= 1e-14
+
+
 # ----------------------------------------------------------- conservation laws
 
 @pytest.mark.parametrize("walls", [False, True])
