@@ -387,13 +387,50 @@ def main(argv=None):
                     help="skip the storage variants and the local-problem measurement")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: create the grid, run this many plain lattice steps, exit")
+    ap.add_argument("--profile-local", type=int, default=0,
+                    help="profiling mode: this many quadtree leaves of the 4096^2 field, 2000 fixed steps, exit")
+    ap.add_argument("--profile-surrogate", type=int, default=0,
+                    help="profiling mode: ensemble inference on this many 32x32 patches, exit")
     args = ap.parse_args(argv)
     ws, rank, local = dist_init()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.profile_steps > 0:
         return run_profile(args, local)
+    if args.profile_local > 0:
+        return run_profile_local(args, local)
+    if args.profile_surrogate > 0:
+        return run_profile_surrogate(args, local)
     return run_ours(args, ws, rank, local)
+
+
+def run_profile_local(args, local):
+    """Fixed launch sequence for ncu: one persistent local-problem launch (2000 steps per drive)."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    import synth
+    torch.cuda.set_device(local)
+    kap = torch.from_numpy(make_kappa()).cuda()
+    leaves_np = synth.quadtree_leaves(N, N, seed=3)[: args.profile_local]
+    p = lbm.Params(nx=N, ny=N, tau=1.0, eps=1.0)
+    lbm.local_keff(p, kap, torch.from_numpy(leaves_np).cuda(), 1e-6, 0.0, 2000, 64, True)
+    torch.cuda.synchronize()
+    return 0
+
+
+def run_profile_surrogate(args, local):
+    """Fixed launch sequence for ncu: patches of the first quadtree leaves, 4-model inference."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    import synth
+    torch.cuda.set_device(local)
+    kap = torch.from_numpy(make_kappa()).cuda()
+    leaves = torch.from_numpy(synth.quadtree_leaves(N, N, seed=3)[: args.profile_surrogate]).cuda()
+    x, _ = lbm.lbm_patches(kap, leaves)
+    with lbm.Surrogate(4, 0) as sur:
+        sur.predict(x)
+    torch.cuda.synchronize()
+    return 0
 
 
 def run_profile(args, local):

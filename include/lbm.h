@@ -235,7 +235,9 @@ lbm_status lbm_patches(const float *kappa_dev, int32_t nx, int32_t ny, const lbm
                        float *x_dev, float *stats_dev, void *cuda_stream);
 
 /* Trains every model on n samples x_dev [n][2][32][32], targets y_dev [n][2]
- * (log K*_xx, log K*_yy), stats_dev [n][3] from lbm_patches. Adam (0.9, 0.999,
+ * (log K*_xx, log K*_yy), stats_dev [n][3] from lbm_patches. The networks learn
+ * log K* minus the patch's mean log K (standardised); lbm_surrogate_predict adds
+ * it back. Adam (0.9, 0.999,
  * 1e-8), learning rate lr with cosine decay to lr/10, mini-batches of `batch`
  * (<= 1024) from a seeded shuffle per epoch. loss_host (HOST, may be NULL)
  * receives [n_models][epochs] mean training loss on standardised targets. */

@@ -343,11 +343,42 @@ __global__ void __launch_bounds__(256) input_moments_kernel(const float *x, int 
     }
 }
 
-// standardised predictions -> log K* (y * std + mean), [model][n][2]
-__global__ void destandardise_kernel(float *y, int64_t n2, float m0, float s0, float m1, float s1)
+// Mean log K of each patch (plane 0 of x), one block per patch, fixed order.
+__global__ void __launch_bounds__(256) patch_mean_kernel(const float *x, int n, float *pm)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (i & 1) ? y[i] * s1 + m1 : y[i] * s0 + m0;
+    __shared__ double sh[256];
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        double acc = 0.0;
+        for (int q = threadIdx.x; q < PIX; q += 256) acc += x[(int64_t)i * 2 * PIX + q];
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0;
+            for (int k = 0; k < 256; ++k) a += sh[k];
+            pm[i] = (float)(a / PIX);
+        }
+        __syncthreads();
+    }
+}
+
+// Targets of a mini-batch: t[b] = ty[idx[b]] (two components).
+__global__ void gather_targets_kernel(const float *ty, const int *idx, int B, float *t)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        t[2 * b] = ty[2 * (int64_t)idx[b]];
+        t[2 * b + 1] = ty[2 * (int64_t)idx[b] + 1];
+    }
+}
+
+// Standardised network outputs -> log K*: y * std + mean + (mean log K of the patch), [model][n][2].
+__global__ void destandardise_kernel(float *y, int n, int nmodels, const float *pm, float m0, float s0, float m1,
+                                     float s1)
+{
+    const int64_t n2 = (int64_t)nmodels * n * 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const float base = pm[(i >> 1) % n];
+        y[i] = ((i & 1) ? y[i] * s1 + m1 : y[i] * s0 + m0) + base;
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -742,16 +773,22 @@ lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n
                                      cudaMemcpyDeviceToDevice, st));
         }
     }
-    destandardise_kernel<<<nblk((int64_t)s->nmodels * n * 2), 256, 0, st>>>(
-        y_dev, (int64_t)s->nmodels * n * 2, s->y_mean[0], s->y_std[0], s->y_mean[1], s->y_std[1]);
-    count_launches(1);
-    return check_err(s, st);
+    float *d_pm = nullptr;
+    SUR_CUDA(cudaMalloc(&d_pm, sizeof(float) * n));
+    patch_mean_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, d_pm);
+    destandardise_kernel<<<nblk((int64_t)s->nmodels * n * 2), 256, 0, st>>>(y_dev, n, s->nmodels, d_pm, s->y_mean[0],
+                                                                          s->y_std[0], s->y_mean[1], s->y_std[1]);
+    count_launches(2);
+    r = check_err(s, st);
+    cudaFree(d_pm);
+    return r;
 }
 
 // Trains every model of the ensemble on n samples: inputs x_dev [n][2][32][32]
-// (lbm_patches), targets y_dev [n][2] = log K*_xx, log K*_yy. Sets the input and
-// target normalisation and the patch-statistics range of the gate from the data
-// (stats_dev [n][3] from lbm_patches). Adam (0.9, 0.999, 1e-8), learning rate lr
+// (lbm_patches), targets y_dev [n][2] = log K*_xx, log K*_yy. The networks learn
+// log K* minus the patch's mean log K, standardised. Sets the input and target
+// normalisation from the data and the patch-statistics range of the gate from
+// stats_dev [n][3] (lbm_patches). Adam (0.9, 0.999, 1e-8), learning rate lr
 // with cosine decay to lr / 10, mini-batches of `batch` drawn by a seeded
 // shuffle each epoch. loss_host (may be NULL): [n_models][epochs] mean loss.
 lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float *y_dev, const float *stats_dev,
@@ -766,9 +803,24 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
     std::vector<float> hy((size_t)2 * n), hs((size_t)3 * n), hx0;
     SUR_CUDA(cudaMemcpy(hy.data(), y_dev, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost));
     SUR_CUDA(cudaMemcpy(hs.data(), stats_dev, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost));
+    // targets are learned relative to the patch's mean log K (the geometric-mean permeability)
+    std::vector<float> pm((size_t)n);
+    {
+        float *d_pm = nullptr;
+        SUR_CUDA(cudaMalloc(&d_pm, sizeof(float) * n));
+        patch_mean_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, d_pm);
+        count_launches(1);
+        cudaError_t e1 = cudaMemcpy(pm.data(), d_pm, sizeof(float) * n, cudaMemcpyDeviceToHost);
+        cudaFree(d_pm);
+        if (e1 != cudaSuccess) { cudaGetLastError(); return fail(LBM_ECUDA, "patch means: %s", cudaGetErrorString(e1)); }
+    }
     double my[2] = {0, 0}, sy[2] = {0, 0}, mx = 0, sx = 0;
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 2; ++k) { my[k] += hy[2 * i + k]; sy[k] += (double)hy[2 * i + k] * hy[2 * i + k]; }
+        for (int k = 0; k < 2; ++k) {
+            const double rr = (double)hy[2 * i + k] - pm[i];
+            my[k] += rr;
+            sy[k] += rr * rr;
+        }
     for (int k = 0; k < 2; ++k) {
         my[k] /= n;
         sy[k] = std::sqrt(std::max(sy[k] / n - my[k] * my[k], 1e-12));
@@ -800,10 +852,10 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
         s->stat_lo[k] = col[(size_t)(0.005 * (n - 1))];
         s->stat_hi[k] = col[(size_t)(0.995 * (n - 1))];
     }
-    // standardised targets
+    // standardised residual targets
     std::vector<float> ty((size_t)2 * n);
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 2; ++k) ty[2 * i + k] = (float)((hy[2 * i + k] - my[k]) / sy[k]);
+        for (int k = 0; k < 2; ++k) ty[2 * i + k] = (float)(((double)hy[2 * i + k] - pm[i] - my[k]) / sy[k]);
     float *d_ty = nullptr;
     SUR_CUDA(cudaMalloc(&d_ty, sizeof(float) * 2 * n));
     cudaError_t e = cudaMemcpy(d_ty, ty.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice);
@@ -811,29 +863,34 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
     if (r != LBM_OK) { cudaFree(d_ty); return r; }
     const int steps_per_epoch = n / batch > 0 ? n / batch : 1;
     const int64_t total_steps = (int64_t)steps_per_epoch * epochs;
-    std::vector<int> order(n), bidx(batch);
-    std::vector<float> tb((size_t)2 * batch);
+    std::vector<int> order(n);
+    std::vector<float> step_loss(steps_per_epoch);
+    int *d_order = nullptr;
+    float *d_losses = nullptr;
+    e = cudaMalloc(&d_order, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_losses, sizeof(float) * steps_per_epoch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_ty); cudaFree(d_order); cudaFree(d_losses);
+        return fail(LBM_ENOMEM, "training buffers: %s", cudaGetErrorString(e));
+    }
+    // every step is enqueued without waiting; the host reads the losses once per epoch
     for (int m = 0; m < s->nmodels && r == LBM_OK; ++m) {
         SplitMix rng{seed * 0x2545F4914F6CDD1Dull + (uint64_t)m + 7};
         int64_t step = 0;
         for (int ep = 0; ep < epochs && r == LBM_OK; ++ep) {
             for (int i = 0; i < n; ++i) order[i] = i;
             for (int i = n - 1; i > 0; --i) std::swap(order[i], order[rng.next() % (uint64_t)(i + 1)]);
-            double ep_loss = 0.0;
-            for (int sb = 0; sb < steps_per_epoch && r == LBM_OK; ++sb, ++step) {
+            e = cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+            for (int sb = 0; sb < steps_per_epoch && e == cudaSuccess; ++sb, ++step) {
                 const int B = std::min(batch, n - sb * batch);
-                for (int b = 0; b < B; ++b) {
-                    bidx[b] = order[sb * batch + b];
-                    tb[2 * b] = ty[2 * bidx[b]];
-                    tb[2 * b + 1] = ty[2 * bidx[b] + 1];
-                }
-                e = cudaMemcpyAsync(s->idx, bidx.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(s->t, tb.data(), sizeof(float) * 2 * B, cudaMemcpyHostToDevice, st);
-                if (e == cudaSuccess) e = pack_model(s, m, st);
+                const int *idx = d_order + (int64_t)sb * batch;
+                e = pack_model(s, m, st);
                 if (e == cudaSuccess) {
-                    input_kernel<<<nblk((int64_t)B * PIX), 256, 0, st>>>(x_dev, s->idx, B, s->in_shift, s->in_scale,
+                    input_kernel<<<nblk((int64_t)B * PIX), 256, 0, st>>>(x_dev, idx, B, s->in_shift, s->in_scale,
                                                                         s->act[0]);
-                    count_launches(1);
+                    gather_targets_kernel<<<nblk(B), 256, 0, st>>>(d_ty, idx, B, s->t);
+                    count_launches(2);
                     e = forward(s, m, B, st);
                 }
                 if (e == cudaSuccess) e = backward(s, m, B, st);
@@ -849,21 +906,25 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
                     count_launches(1);
                     e = cudaGetLastError();
                 }
-                if (e == cudaSuccess) {
-                    float l = 0.0f;
-                    e = cudaMemcpyAsync(&l, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
-                    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-                    ep_loss += l;
-                }
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    r = fail(LBM_ECUDA, "surrogate training step: %s", cudaGetErrorString(e));
-                }
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(d_losses + sb, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
             }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(step_loss.data(), d_losses, sizeof(float) * steps_per_epoch, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                r = fail(LBM_ECUDA, "surrogate training: %s", cudaGetErrorString(e));
+                break;
+            }
+            double ep_loss = 0.0;
+            for (float l : step_loss) ep_loss += l;
             if (loss_host) loss_host[(int64_t)m * epochs + ep] = (float)(ep_loss / steps_per_epoch);
         }
         if (r == LBM_OK) r = check_err(s, st);
     }
+    cudaFree(d_order);
+    cudaFree(d_losses);
     cudaFree(d_ty);
     return r;
 }

@@ -115,7 +115,9 @@ def test_guo_force_model_matches_oracle_guo_and_simplified():
     _, uo, _ = prob.fields(f)
     scale = np.abs(uo).max()
     assert np.abs(outs[1] - uo).max() <= 1e-5 * scale
-    assert np.abs(outs[1] - outs[0]).max() <= 1e-5 * scale
+    # two FP32 runs with different arithmetic: each is within 1e-5 of the oracle; E1's drag is weak
+    # (1 - d ~ 1e-4), where FP32 rounding of the momentum weighs most, so allow the sum of both
+    assert np.abs(outs[1] - outs[0]).max() <= 3e-5 * scale
 
 
 def test_fp64_storage_matches_to_roundoff():
@@ -215,6 +217,48 @@ def test_full_size_4096_sampled_against_oracle_windows():
         assert abs(v[y, x] - vo[h, h]) <= 1e-5 * max(scale, abs(vo[h, h])) + 1e-12
         assert abs(rho[y, x] - ro[h, h]) <= 1e-6
     # mass is conserved at full size up to FP32 rounding of the deviations (~1e-13 each)
+    assert abs(total_drho) / (N * N) < 1e-14
+
+
+def test_full_size_16384_channelised_sampled():
+    """16384^2 channelised field (seed 5, contrast 1e4, eps 1, tau 1, G = (1e-6, 0)): the largest
+    fine lattice of the workloads (19.3 GB of FP32 state), sampled against oracle windows after
+    n steps, plus mass conservation on the raw state."""
+    import torch
+    lbm = _lbm()
+    n = 8
+    N = 16384
+    kap = synth.channel_kappa(N, N, seed=5)
+    tau, nu, eps, g = 1.0, 1.0 / 6.0, 1.0, (1e-6, 0.0)
+    p = lbm.Params(nx=N, ny=N, tau=tau, nu=nu, eps=eps, gx=g[0], gy=g[1])
+    kt = torch.from_numpy(kap).cuda()
+    rng = np.random.default_rng(3)
+    # half the samples on channel cells, half anywhere
+    ys, xs = np.nonzero(kap[::97, ::89] > 1e-3)
+    chan = [(int(xs[i] * 89), int(ys[i] * 97)) for i in rng.choice(len(xs), 6, replace=False)]
+    pts = chan + [tuple(int(v) for v in rng.integers(0, N, 2)) for _ in range(6)] + [(0, 0), (N - 1, N - 1)]
+    with lbm.Grid(p, kt) as G:
+        del kt
+        G.step(n, 0.0, 0)
+        rho, u, v = G.fields()
+        vals = [(float(u[y, x]), float(v[y, x]), float(rho[y, x])) for (x, y) in pts]
+        del rho, u, v
+        full = torch.empty(lbm.lbm_grid_state_bytes(G.handle), dtype=torch.uint8, device="cuda")
+        lbm.lbm_grid_save_state(G.handle, full)
+        total_drho = float(full[: full.numel() // 2].view(torch.float32).sum(dtype=torch.float64))
+        del full
+    W = 2 * n + 9
+    h = W // 2
+    for (x, y), (ug, vg, rg) in zip(pts, vals):
+        win = synth.crop_periodic(kap, x - h, y - h, W, W).astype(np.float64)
+        pr = oracle.Problem(tau, nu, eps, kappa=win, g=g)
+        f = pr.rest()
+        pr.run(f, n)
+        ro, uo, vo = pr.fields(f)
+        scale = max(abs(uo[h, h]), abs(vo[h, h]), 1e-30)
+        assert abs(ug - uo[h, h]) <= 1e-5 * scale + 1e-14
+        assert abs(vg - vo[h, h]) <= 1e-5 * scale + 1e-14
+        assert abs(rg - ro[h, h]) <= 1e-6
     assert abs(total_drho) / (N * N) < 1e-14
 
 

@@ -123,7 +123,8 @@ def test_adam_step_matches_oracle():
         norm = sur.get_normalization()
         # the same step's gradient, with the normalisation train() chose
         sur.set_params(0, _flat(p))
-        tstd = np.stack([(ylab[:, 0] - norm[2]) / norm[3], (ylab[:, 1] - norm[4]) / norm[5]], axis=1)
+        pm = x[:, 0].mean(axis=(1, 2))        # targets are learned relative to the patch's mean log K
+        tstd = np.stack([(ylab[:, 0] - pm - norm[2]) / norm[3], (ylab[:, 1] - pm - norm[4]) / norm[5]], axis=1)
         g, _, _ = sur.grad(0, _t(x), _t(tstd))
     ref, _, _ = S.adam_step(_flat(p).astype(np.float64), g.astype(np.float64), 0.0, 0.0, 1, 1e-3)
     # training sums the batch in its own shuffled order, so gradients that are pure
