@@ -233,6 +233,98 @@ def measure_local_keff(lbm, torch, kap, ws, sample=512, seed=11):
     }
 
 
+def _surrogate_set(nfields, seed0, side=256):
+    """Seeded log-normal fields (sigma ~ U[0.5, 3], ell ~ U[2, 16]) stacked along y, with quadtree leaves."""
+    import synth
+    rng = np.random.default_rng(seed0)
+    ks, leaves = [], []
+    for f in range(nfields):
+        sigma, ell = rng.uniform(0.5, 3.0), rng.uniform(2.0, 16.0)
+        ks.append(synth.lognormal_kappa(side, side, ell, sigma, seed=seed0 * 10000 + f).astype(np.float32))
+        lv = synth.quadtree_leaves(side, side, seed=seed0 * 10000 + f)
+        lv[:, 1] += f * side
+        leaves.append(lv)
+    return np.concatenate(ks, axis=0), np.concatenate(leaves, axis=0)
+
+
+def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, spread_max=0.03):
+    """The learned K* surrogate against the batched local LBM on held-out patches.
+
+    Labels: local LBM (FP32, tau = 1, G = 1e-6, tol 1e-8, persistent launch). The ensemble of
+    4 CNNs is trained on the training patches; on held-out fields it predicts every patch,
+    the gate (spread <= ln(1 + spread_max), statistics in the training range) accepts some,
+    the rest fall back to local LBM. Reports patches/s of LBM alone, of ensemble inference
+    with the gate, and end to end (inference + gate + LBM on the rejected patches), and the
+    relative K* error of accepted predictions against their LBM labels."""
+    def label(kap, leaves):
+        p = lbm.Params(nx=kap.shape[1], ny=kap.shape[0], tau=1.0, eps=1.0)
+        kt, lt = torch.from_numpy(kap).cuda(), torch.from_numpy(leaves).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke, st, _, _ = lbm.local_keff(p, kt, lt, 1e-6, 1e-8, 200000, 64, True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        x, stats = lbm.lbm_patches(kt, lt)
+        y = torch.log(torch.stack([ke[:, 0], ke[:, 3]], dim=1)).float()
+        return kt, lt, p, x, stats, y, st, dt
+
+    ktr, ltr = _surrogate_set(train_fields, 10)
+    kte, lte = _surrogate_set(test_fields, 1000)
+    _, _, _, xtr, str_, ytr, sttr, _ = label(ktr, ltr)
+    kt, lt, p, xte, ste, yte, stte, t_lbm = label(kte, lte)
+    ok = sttr == 0
+    sur = lbm.Surrogate(4, 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sur.train(xtr[ok], ytr[ok], str_[ok], epochs=epochs, batch=256, lr=2e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n = len(lte)
+    # inference + gate alone
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, stats = lbm.lbm_patches(kt, lt)
+    pred = sur.predict(x)
+    sd = pred.std(dim=0).max(dim=1).values
+    norm = sur.get_normalization()
+    in_range = torch.ones(n, dtype=torch.bool, device="cuda")
+    for k in range(3):
+        in_range &= (stats[:, k] >= float(norm[6 + 2 * k])) & (stats[:, k] <= float(norm[7 + 2 * k]))
+    accept = (sd <= float(np.log1p(spread_max))) & in_range
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    # end to end: inference + gate + local LBM on the rejected leaves
+    rej = torch.nonzero(~accept).flatten()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if rej.numel():
+        lbm.local_keff(p, kt, lt[rej].contiguous(), 1e-6, 1e-8, 200000, 64, True)
+    torch.cuda.synchronize()
+    t_fb = time.perf_counter() - t0
+    good = (stte == 0)
+    rel = (torch.exp(pred.mean(dim=0)) / torch.exp(yte) - 1.0).abs()
+    acc = (accept & good)
+    rel_acc = rel[acc].flatten().cpu().numpy()
+    rel_all = rel[good].flatten().cpu().numpy()
+    flops = 4 * 2 * 1024 * 9 * (2 * 32 + 32 * 32 + 32 * 64 + 3 * 64 * 64)      # ensemble, per patch
+    sur.close()
+    return {
+        "workload": f"{train_fields} training / {test_fields} held-out 256^2 log-normal fields (sigma U[0.5,3], "
+                    "ell U[2,16]), quadtree leaves 8-64, labels by local LBM tol 1e-8; ensemble of 4, "
+                    f"gate: spread <= {spread_max:.0%} and statistics in the training range",
+        "train_patches": int(ok.sum()), "test_patches": n, "epochs": epochs, "train_seconds": t_train,
+        "lbm_patches_per_s": n / t_lbm,
+        "surrogate_patches_per_s": n / t_inf,
+        "end_to_end_patches_per_s": n / (t_inf + t_fb),
+        "speedup_end_to_end": (n / (t_inf + t_fb)) / (n / t_lbm),
+        "accepted_fraction": float(acc.float().mean()),
+        "accepted_rel_err_median": float(np.median(rel_acc)) if rel_acc.size else None,
+        "accepted_rel_err_p99": float(np.percentile(rel_acc, 99)) if rel_acc.size else None,
+        "all_rel_err_median": float(np.median(rel_all)), "all_rel_err_p99": float(np.percentile(rel_all, 99)),
+        "inference_tflops": flops * n / t_inf / 1e12,
+    }
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -341,11 +433,12 @@ def run_ours(args, ws, rank, local):
            "steps": e2e_steps}
 
     variants = {}
+    local = surrogate = None
     if not args.no_extras:
         variants = measure_variants(lbm, torch, kap, stream)
         local = measure_local_keff(lbm, torch, kap, ws)
-    else:
-        local = None
+        if not args.no_surrogate:
+            surrogate = measure_surrogate(lbm, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -370,6 +463,8 @@ def run_ours(args, ws, rank, local):
             line["storage_variants"] = variants
         if local:
             line["local_keff"] = local
+        if surrogate:
+            line["surrogate"] = surrogate
         print(json.dumps(line), flush=True)
     return 0
 
@@ -384,7 +479,8 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the storage variants and the local-problem measurement")
+                    help="skip the storage variants, the local-problem and the surrogate measurements")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: create the grid, run this many plain lattice steps, exit")
     ap.add_argument("--profile-local", type=int, default=0,

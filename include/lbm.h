@@ -127,10 +127,15 @@ lbm_status lbm_mean_velocity(lbm_grid *g, double out_mean_uv[2]);
 /* Total steps taken since creation (host value). */
 int64_t lbm_grid_steps(const lbm_grid *g);
 
-/* Checkpoint: copies the grid's state (its current distribution buffer, storage
- * type, 9 * nx * ny elements in [9][ny][nx] order, deviations from w_a rho0,
- * multiplied by the FP16 scale for LBM_F16) to or from caller-owned DEVICE
- * memory of lbm_grid_state_bytes(g) bytes, together with the step count. */
+/* Checkpoint: copies the grid's state to or from caller-owned DEVICE memory of
+ * lbm_grid_state_bytes(g) bytes, together with the step count. The state is
+ * both distribution buffers, the current one first (the previous one is kept so
+ * that the convergence test after a restart compares the same two states as an
+ * uninterrupted run). Each buffer holds 9 planes of the storage type, plane a at
+ * offset a * plane where plane = nx * ny rounded up to a multiple of 64, cell
+ * (x, y) at y * nx + x; the values are deviations from w_a rho0, multiplied by
+ * the FP16 scale for LBM_F16. The layout is opaque to callers that only save and
+ * load it on grids created with the same parameters. */
 int64_t lbm_grid_state_bytes(const lbm_grid *g);
 lbm_status lbm_grid_save_state(lbm_grid *g, void *state_dev, int64_t *steps);
 lbm_status lbm_grid_load_state(lbm_grid *g, const void *state_dev, int64_t steps);

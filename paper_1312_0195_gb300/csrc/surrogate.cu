@@ -387,14 +387,24 @@ template <int CIN_P, int COUT, int EPI>
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t st)
 {
     using S = ConvShape<CIN_P, COUT>;
-    static bool attr = false;
-    if (!attr) {
+    static int resident = 0;     // CTAs per SM for this instantiation (persistent grid)
+    static int sms = 0;
+    if (!resident) {
         cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN_P, COUT, EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv3x3_tc_kernel<CIN_P, COUT, EPI>, CONV_THREADS,
+                                                          S::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        sms = sm_count(dev);
+        resident = nb < 1 ? 1 : nb;
     }
-    conv3x3_tc_kernel<CIN_P, COUT, EPI><<<a.nimg * 8, 128, S::SMEM, st>>>(a);
+    const int64_t ntiles = (int64_t)a.nimg * 8;
+    const int64_t cap = (int64_t)sms * resident;
+    conv3x3_tc_kernel<CIN_P, COUT, EPI><<<(int)(ntiles < cap ? ntiles : cap), CONV_THREADS, S::SMEM, st>>>(a);
     return cudaGetLastError();
 }
 

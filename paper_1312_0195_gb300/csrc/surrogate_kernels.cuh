@@ -56,12 +56,16 @@ struct ConvShape {
     static constexpr uint32_t TMEM_COLS = COUT < 32 ? 32 : COUT;
 };
 
+constexpr int CONV_THREADS = 256;          // 8 warps: all gather; warps w and w+4 share TMEM lanes
+
 template <int CIN_P, int COUT, int EPI>
-__global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a)
+__global__ void __launch_bounds__(CONV_THREADS) conv3x3_tc_kernel(ConvArgs a)
 {
     using S = ConvShape<CIN_P, COUT>;
     constexpr int KB = CIN_P;                       // K-block = one tap, all input channels
+    constexpr int KG = KB / 8;                      // core matrices along K per tap
     constexpr uint32_t IDESC = umma::idesc_bf16_f32(128, COUT);
+    constexpr int HALF = COUT / 2;                  // TMEM columns read by each warpgroup
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
     uint8_t *sA[2] = {smem + S::B_BYTES, smem + S::B_BYTES + S::A_BYTES};
@@ -71,13 +75,13 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a)
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int img = blockIdx.x >> 3, rb = blockIdx.x & 7;   // 8 blocks of 4 rows per image
+    const int ntiles = a.nimg * 8;                 // tile = 4 rows (128 pixels) of one image
 
-    // resident weights (already in the core-matrix layout) and bias
-    for (uint32_t i = tid; i < S::B_BYTES / 16; i += 128)
+    // resident weights (already in the core-matrix layout) and bias, loaded once per CTA
+    for (uint32_t i = tid; i < S::B_BYTES / 16; i += CONV_THREADS)
         reinterpret_cast<uint4 *>(sB)[i] = reinterpret_cast<const uint4 *>(a.wpack)[i];
     if (EPI == EPI_BIAS_RELU)
-        for (int i = tid; i < COUT; i += 128) s_bias[i] = a.bias[i];
+        for (int i = tid; i < COUT; i += CONV_THREADS) s_bias[i] = a.bias[i];
     if (tid == 0) {
         umma::mbar_init(&mbar[0], 1);
         umma::mbar_init(&mbar[1], 1);
@@ -91,53 +95,64 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a)
     const uint32_t tmem = s_taddr;
 
     uint32_t phase[2] = {0u, 0u};
-    for (int kb = 0; kb < 9; ++kb) {
-        const int b = kb & 1;
-        if (kb >= 2) {                               // the MMAs of tap kb-2 read this buffer
-            if (!umma::mbar_wait_bounded(&mbar[b], phase[b], WAIT_LIMIT)) s_fail = 1;
-            phase[b] ^= 1u;
-            __syncthreads();
-            if (s_fail) break;
-        }
-        const int dy = kb / 3, dx = kb % 3;
-        uint8_t *dst = sA[b];
-        for (int i = tid; i < 128 * (KB / 8); i += 128) {
-            const int r = i / (KB / 8), g = i - r * (KB / 8);      // pixel row r of the tile, 8-channel group g
-            const int y = rb * 4 + (r >> 5) + dy - 1, x = (r & 31) + dx - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (y >= 0 && y < IMG && x >= 0 && x < IMG)
-                v = *reinterpret_cast<const uint4 *>(a.in + ((int64_t)(img * IMG + y) * IMG + x) * CIN_P + g * 8);
-            *reinterpret_cast<uint4 *>(dst + umma::core_offset(r, g * 8, KB)) = v;
-        }
-        umma::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            umma::fence_after();
-#pragma unroll
-            for (int kk = 0; kk < KB / 16; ++kk) {
-                const uint64_t ad = umma::desc(umma::smem_addr(dst) + kk * 256, 128, (KB / 8) * 128);
-                const uint64_t bd = umma::desc(umma::smem_addr(sB) + ((kb * KB + kk * 16) / 8) * 128, 128,
-                                               (S::K / 8) * 128);
-                umma::mma_bf16(tmem, ad, bd, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+    int issued[2] = {0, 0};                        // commits on each barrier not yet waited for
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int img = tile >> 3, rb = tile & 7;
+        for (int kb = 0; kb < 9; ++kb) {
+            const int b = kb & 1;
+            if (issued[b]) {                       // earlier MMAs read this buffer
+                if (!umma::mbar_wait_bounded(&mbar[b], phase[b], WAIT_LIMIT)) s_fail = 1;
+                phase[b] ^= 1u;
+                issued[b] = 0;
+                __syncthreads();
+                if (s_fail) break;
             }
-            umma::commit(&mbar[b]);
+            const int dy = kb / 3, dx = kb % 3;
+            uint8_t *dst = sA[b];
+            // eight consecutive threads fill one 128-byte core matrix (8 pixels x 16 bytes)
+            for (int i = tid; i < 128 * KG; i += CONV_THREADS) {
+                const int cm = i >> 3, rr = i & 7;
+                const int rg = cm / KG, g = cm - rg * KG;
+                const int r = rg * 8 + rr;
+                const int y = rb * 4 + (r >> 5) + dy - 1, x = (r & 31) + dx - 1;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (y >= 0 && y < IMG && x >= 0 && x < IMG)
+                    v = *reinterpret_cast<const uint4 *>(a.in + ((int64_t)(img * IMG + y) * IMG + x) * CIN_P + g * 8);
+                *reinterpret_cast<uint4 *>(dst + (uint32_t)rg * (KG * 128) + g * 128 + rr * 16) = v;
+            }
+            umma::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                umma::fence_after();
+#pragma unroll
+                for (int kk = 0; kk < KB / 16; ++kk) {
+                    const uint64_t ad = umma::desc(umma::smem_addr(dst) + kk * 256, 128, KG * 128);
+                    const uint64_t bd = umma::desc(umma::smem_addr(sB) + ((kb * KB + kk * 16) / 8) * 128, 128,
+                                                   (S::K / 8) * 128);
+                    umma::mma_bf16(tmem, ad, bd, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+                }
+                umma::commit(&mbar[b]);
+            }
+            issued[b] = 1;
         }
-    }
-    // the last commit (tap 8, buffer 0) covers every MMA issued before it; the
-    // decision is made CTA-wide because tcgen05.ld is warp-collective
-    const bool waited = s_fail == 0 && umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);
-    const bool done = __syncthreads_and(waited ? 1 : 0) != 0;
-    if (!done) {
-        if (tid == 0) atomicExch(a.err, 1);
-        umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);   // give in-flight MMAs a second chance
-    } else {
+        if (s_fail) break;
+        // the last commit of the tile (tap 8, buffer 0) covers every MMA issued before it;
+        // the decision is made CTA-wide because tcgen05.ld is warp-collective
+        const bool waited = umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);
+        phase[0] ^= 1u;
+        issued[0] = 0;
+        if (!__syncthreads_and(waited ? 1 : 0)) {
+            s_fail = 1;
+            break;
+        }
         umma::fence_after();
-        const int y = rb * 4 + warp, x = lane;                       // this thread's pixel = TMEM lane 32 w + lane
+        const int wq = warp & 3, half = warp >> 2;    // TMEM lane quarter, column half
+        const int y = rb * 4 + wq, x = lane;           // this thread's pixel = TMEM lane 32 wq + lane
         const int64_t pix = (int64_t)(img * IMG + y) * IMG + x;
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
+        for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 16) {
             float v[16];
-            umma::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            umma::tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c0, v);
             if (EPI == EPI_BIAS_RELU) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.0f);
@@ -160,6 +175,15 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a)
             op[0] = o[0];
             op[1] = o[1];
         }
+        // the next tile's first MMA overwrites the accumulator: every read must be done
+        umma::fence_before();
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) atomicExch(a.err, 1);
+        // give in-flight MMAs a chance to finish before the accumulator is released
+        if (issued[0]) umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);
+        if (issued[1]) umma::mbar_wait_bounded(&mbar[1], phase[1], WAIT_LIMIT);
     }
     umma::fence_before();
     __syncthreads();
