@@ -280,17 +280,21 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, s
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     n = len(lte)
-    # inference + gate alone
+    norm = sur.get_normalization()
+
+    def infer_and_gate(leaves):
+        x, stats = lbm.lbm_patches(kt, leaves)
+        pred = sur.predict(x)
+        sd = pred.std(dim=0).max(dim=1).values
+        in_range = torch.ones(len(leaves), dtype=torch.bool, device="cuda")
+        for k in range(3):
+            in_range &= (stats[:, k] >= float(norm[6 + 2 * k])) & (stats[:, k] <= float(norm[7 + 2 * k]))
+        return pred, (sd <= float(np.log1p(spread_max))) & in_range
+
+    infer_and_gate(lt)                                   # warm-up: work buffers, launch set-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x, stats = lbm.lbm_patches(kt, lt)
-    pred = sur.predict(x)
-    sd = pred.std(dim=0).max(dim=1).values
-    norm = sur.get_normalization()
-    in_range = torch.ones(n, dtype=torch.bool, device="cuda")
-    for k in range(3):
-        in_range &= (stats[:, k] >= float(norm[6 + 2 * k])) & (stats[:, k] <= float(norm[7 + 2 * k]))
-    accept = (sd <= float(np.log1p(spread_max))) & in_range
+    pred, accept = infer_and_gate(lt)
     torch.cuda.synchronize()
     t_inf = time.perf_counter() - t0
     # end to end: inference + gate + local LBM on the rejected leaves
@@ -487,8 +491,14 @@ def main(argv=None):
                     help="profiling mode: this many quadtree leaves of the 4096^2 field, 2000 fixed steps, exit")
     ap.add_argument("--profile-surrogate", type=int, default=0,
                     help="profiling mode: ensemble inference on this many 32x32 patches, exit")
+    ap.add_argument("--pipeline", type=int, default=0,
+                    help="run the whole upscaled method on an n^2 channelised field (e.g. 16384) and exit")
+    ap.add_argument("--pipeline-steps", type=int, default=20000, help="fine steps of --pipeline")
+    ap.add_argument("--pipeline-epochs", type=int, default=10, help="surrogate training epochs of --pipeline")
     args = ap.parse_args(argv)
     ws, rank, local = dist_init()
+    if args.pipeline > 0:
+        return run_pipeline(args, local)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.profile_steps > 0:
@@ -498,6 +508,83 @@ def main(argv=None):
     if args.profile_surrogate > 0:
         return run_profile_surrogate(args, local)
     return run_ours(args, ws, rank, local)
+
+
+def run_pipeline(args, local):
+    """The whole upscaled method on an n^2 channelised field (default 16384^2, r = 16).
+
+    Fine run (FP32, tau = 1, nu = nu_eff, eps = 1, G = (1e-6, 0)) for `steps` steps; K* of every r x r
+    block (Eq. 17) by local LBM alone and by the surrogate ensemble with local-LBM fallback (trained
+    on the r x r blocks of a 4096^2 channelised field of another seed); coarse runs (Eq. 18, tensor
+    K*, scaled parameters) for steps / r steps, the same physical time; relative L2 error of the
+    coarse velocity against the r x r block average of the fine velocity. Prints one JSON line."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    import synth
+    torch.cuda.set_device(local)
+    n, r, steps = args.pipeline, 16, args.pipeline_steps
+    out = {"workload": f"{n}^2 channelised (seed 5, K 1e-2 / 1e-6), r = {r}, fine {steps} steps, "
+                       f"coarse {steps // r} steps", "n": n, "block": r}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        return res, time.perf_counter() - t0
+
+    p = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, gx=1e-6, gy=0.0)
+    kt = torch.from_numpy(synth.channel_kappa(n, n, seed=5)).cuda()
+    with lbm.Grid(p, kt) as G:
+        _, t = timed(lambda: G.step(steps, 0.0, 0))
+        out["fine_seconds"] = t
+        out["fine_mlups"] = n * n * steps / t / 1e6
+        rho, u, v = G.fields()
+        del rho
+        ub, vb = lbm.lbm_block_average(u, r), lbm.lbm_block_average(v, r)
+        del u, v
+    # surrogate for r x r channelised blocks, trained on another seed's field
+    m = 4096
+    ktr = torch.from_numpy(synth.channel_kappa(m, m, seed=6)).cuda()
+    ltr = torch.from_numpy(synth.uniform_leaves(m, m, r)).cuda()
+    ptr = lbm.Params(nx=m, ny=m, tau=1.0, eps=1.0)
+    (ke, st, _, _), t_lab = timed(lambda: lbm.local_keff(ptr, ktr, ltr, 1e-6, 1e-8, 200000, 64, True))
+    x, stats = lbm.lbm_patches(ktr, ltr)
+    ok = st == 0
+    y = torch.log(torch.stack([ke[:, 0], ke[:, 3]], dim=1)).float()
+    sur = lbm.Surrogate(4, 3)
+    _, t_train = timed(lambda: sur.train(x[ok], y[ok], stats[ok], epochs=args.pipeline_epochs, batch=256,
+                                         lr=2e-3, seed=1))
+    out["surrogate_training"] = {"patches": int(ok.sum()), "label_seconds": t_lab, "train_seconds": t_train,
+                                 "epochs": args.pipeline_epochs}
+    del ktr, ltr, x, stats, ke, st, y
+    nb = n // r
+    keff = {k: torch.empty((nb, nb, 4), dtype=torch.float64, device="cuda") for k in ("lbm", "surrogate")}
+    (st_l, _), t_l = timed(lambda: lbm.lbm_upscale(p, kt, r, keff["lbm"], 1e-6, 1e-8, 200000))
+    (st_s, nfb), t_s = timed(lambda: lbm.lbm_upscale(p, kt, r, keff["surrogate"], 1e-6, 1e-8, 200000,
+                                                     surrogate=sur, spread_max=0.03))
+    sur.close()
+    kl, ks = keff["lbm"], keff["surrogate"]
+    rel = torch.stack([(ks[..., 0] / kl[..., 0] - 1).abs(), (ks[..., 3] / kl[..., 3] - 1).abs()]).flatten()
+    rel = rel.cpu().numpy()
+    out["upscale"] = {
+        "blocks": nb * nb,
+        "lbm_seconds": t_l, "lbm_blocks_per_s": nb * nb / t_l, "lbm_status": st_l,
+        "surrogate_seconds": t_s, "surrogate_blocks_per_s": nb * nb / t_s, "surrogate_status": st_s,
+        "fallback_fraction": nfb / (nb * nb),
+        "kstar_rel_err_vs_lbm_median": float(np.median(rel)), "kstar_rel_err_vs_lbm_p99": float(np.percentile(rel, 99)),
+    }
+    pc = lbm.lbm_coarse_params(p, r)
+    out["coarse_params"] = {"tau": pc.tau, "nu": pc.nu, "gx": pc.gx}
+    den = float(torch.sqrt((ub.double() ** 2 + vb.double() ** 2).sum()))
+    for name in ("lbm", "surrogate"):
+        uc = torch.empty((nb, nb), dtype=torch.float32, device="cuda")
+        vc, rc = torch.empty_like(uc), torch.empty_like(uc)
+        (_, done), t = timed(lambda: lbm.lbm_coarse_run(p, r, keff[name], None, steps // r, 0.0, 64, rc, uc, vc))
+        num = float(torch.sqrt(((uc.double() - ub.double()) ** 2 + (vc.double() - vb.double()) ** 2).sum()))
+        out[f"coarse_{name}"] = {"steps": done, "seconds": t, "rel_l2_vs_fine": num / den}
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_profile_local(args, local):

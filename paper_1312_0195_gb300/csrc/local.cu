@@ -63,6 +63,8 @@ struct LocalArgs {
     int class_size[MAXCLASS];
     int *heads;               // [nclass] queue heads (zeroed before launch)
     double omega, two_tau, omt, half_eps, gmag;
+    float kf[9];              // collision constants (K_*) in FP32 and FP64, set by cell_consts()
+    double kd[9];
     double eps_nu;            // eps * nu for the drag coefficient
     double nu_over_g;         // nu / G for Eq. 17
     double tol;
@@ -79,8 +81,6 @@ struct LocalArgs {
 struct Slot {
     int job;                  // -1: empty
     int leaf, drive, x0, y0;
-    long long tstart;         // CTA step counter value at the job's step 0
-    int next_check;           // job step of the next steady-state check
     double prev;              // driven mean velocity at the previous check
 };
 
@@ -100,7 +100,68 @@ __device__ __forceinline__ double coef_e(float k, double eps_nu)
     return eps_nu / (2.0 * (double)k + eps_nu);
 }
 
-__device__ __forceinline__ int wrapi(int v, int s) { return v < 0 ? v + s : (v >= s ? v - s : v); }
+// Per-slot values every cell reads each step, packed for one 16-byte shared load.
+struct SlotHot {
+    int tstart;       // CTA step counter at the job's step 0 (differences taken modulo 2^32)
+    int next_check;   // job step of the next steady-state check
+    int flags;        // bit 0: active, bit 1: driven along y
+    int pad;
+};
+
+// Collision constants (host-computed in the storage precision, so the FMAs read them from the
+// constant bank): 1 - omega; omega w_a for the three weight classes; 3 omega w_a for the
+// momentum terms; Eq. 16's 2 tau and 1 - 2 tau; eps G / 2.
+enum { K_OM1, K_A0, K_A9, K_A36, K_B9, K_B36, K_TWO_TAU, K_OMT, K_HG, K_N };
+
+void cell_consts(LocalArgs &a)
+{
+    const double w = a.omega;
+    const double k[K_N] = {1.0 - w,  4.0 * w / 9.0, w / 9.0, w / 36.0, w / 3.0,
+                           w / 12.0, a.two_tau,     a.omt,   a.half_eps * a.gmag};
+    for (int i = 0; i < K_N; ++i) {
+        a.kd[i] = k[i];
+        a.kf[i] = (float)k[i];
+    }
+}
+
+template <typename T> __device__ __forceinline__ T kc(const LocalArgs &a, int i);
+template <> __device__ __forceinline__ float kc<float>(const LocalArgs &a, int i) { return a.kf[i]; }
+template <> __device__ __forceinline__ double kc<double>(const LocalArgs &a, int i) { return a.kd[i]; }
+
+// Eqs. 6, 16, 2 and 13 for one cell in deviation form with the D2Q9 sums written out (a product
+// with a zero velocity component is not free in IEEE arithmetic): moments, r = j + eps rho G / 2,
+// rho u = (1 - e) r, rho u_eq = 2 tau rho u + (1 - 2 tau) j, then
+// g <- (1 - omega) g + omega w_a (drho + 3 e_a . rho u_eq). Returns rho u and rho.
+template <typename T>
+__device__ __forceinline__ void collide_d2q9(T (&g)[Q], T e, T hgx, T hgy, const LocalArgs &a, T &rux, T &ruy,
+                                             T &rho)
+{
+    const T s13 = g[1] + g[3], s24 = g[2] + g[4], s57 = g[5] + g[7], s68 = g[6] + g[8];
+    const T drho = g[0] + ((s13 + s24) + (s57 + s68));
+    const T d57 = g[5] - g[7], d86 = g[8] - g[6];
+    const T jx = (g[1] - g[3]) + (d57 + d86);
+    const T jy = (g[2] - g[4]) + (d57 - d86);
+    rho = T(1) + drho;
+    const T rx = fma(hgx, rho, jx), ry = fma(hgy, rho, jy);
+    rux = fma(-e, rx, rx);
+    ruy = fma(-e, ry, ry);
+    const T uex = fma(kc<T>(a, K_TWO_TAU), rux, kc<T>(a, K_OMT) * jx);
+    const T uey = fma(kc<T>(a, K_TWO_TAU), ruy, kc<T>(a, K_OMT) * jy);
+    const T om1 = kc<T>(a, K_OM1);
+    const T a9 = kc<T>(a, K_A9) * drho, a36 = kc<T>(a, K_A36) * drho;
+    const T bx9 = kc<T>(a, K_B9) * uex, by9 = kc<T>(a, K_B9) * uey;
+    const T bx36 = kc<T>(a, K_B36) * uex, by36 = kc<T>(a, K_B36) * uey;
+    g[0] = fma(om1, g[0], kc<T>(a, K_A0) * drho);
+    g[1] = fma(om1, g[1], a9 + bx9);
+    g[3] = fma(om1, g[3], a9 - bx9);
+    g[2] = fma(om1, g[2], a9 + by9);
+    g[4] = fma(om1, g[4], a9 - by9);
+    const T p = a36 + bx36, m = a36 - bx36;
+    g[5] = fma(om1, g[5], p + by36);
+    g[8] = fma(om1, g[8], p - by36);
+    g[6] = fma(om1, g[6], m + by36);
+    g[7] = fma(om1, g[7], m - by36);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs a)
@@ -108,14 +169,18 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
     constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *F = reinterpret_cast<T *>(smem_raw);   // [9][CMAX]
-    T *D = F + 9 * CMAX;                      // [CMAX]
+    T *D = F + 9 * CMAX;                      // [CMAX] drag fraction e of each cell
     T *UX = D + CMAX;                         // [CMAX]
     T *UY = UX + CMAX;                        // [CMAX]
     __shared__ Slot slots[MAXSLOTS];
+    __shared__ int4 hot[MAXSLOTS];            // SlotHot
     __shared__ int s_abort;
+    __shared__ unsigned s_event;              // CTA step of the next check of any slot
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned long long t0 = globaltimer();
+    const int max_steps = (int)a.max_steps;
+    const T hg = kc<T>(a, K_HG);
     if (tid == 0) s_abort = 0;
 
     for (int cls = 0; cls < a.nclass; ++cls) {
@@ -140,7 +205,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
             }
         }
         __syncthreads();
-        long long Tcta = 0;          // CTA step counter
+        unsigned Tcta = 0;           // CTA step counter
         if (tid < nslots) {
             Slot sl;
             sl.job = -1;
@@ -151,13 +216,13 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 sl.drive = sl.job & 1;
                 sl.x0 = a.leaves[3 * sl.leaf];
                 sl.y0 = a.leaves[3 * sl.leaf + 1];
-                sl.tstart = 0;
-                sl.next_check = a.check_every;
                 sl.prev = 0.0;
             }
             slots[tid] = sl;
+            hot[tid] = make_int4(0, a.check_every, sl.job >= 0 ? 1 | (sl.drive << 1) : 0, 0);
         }
-        int any = __syncthreads_or(tid < nslots && slots[tid].job >= 0);
+        if (tid == 0) s_event = (unsigned)min(a.check_every, max_steps);
+        int any = __syncthreads_or(tid < nslots && hot[tid].z);
 
         while (any) {
             // ---------------------------------------------------------- one step
@@ -166,14 +231,16 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 const int geo = cgeo[i];
                 if (geo < 0) continue;
                 const int j = geo >> 12, cly = (geo >> 6) & 63, clx = geo & 63;
-                const Slot &sl = slots[j];
-                if (sl.job < 0) continue;
-                const int t = (int)(Tcta - sl.tstart);
+                const int4 h = hot[j];
+                if (!(h.z & 1)) continue;
+                const int t = (int)(Tcta - (unsigned)h.x);
                 const int c = tid + i * LOCAL_THREADS;
-                const int base = j * s2;
                 T g[Q];
+                // odd steps: the 8 neighbours with periodic closure on the leaf; cell x - e_a is
+                // read for population a and cell x + e_a written, so each index serves both
+                int n1 = 0, n2 = 0, n3 = 0, n4 = 0, n5 = 0, n6 = 0, n7 = 0, n8 = 0;
                 if (t == 0) {
-                    const int gx = sl.x0 + clx, gy = sl.y0 + cly;
+                    const int gx = slots[j].x0 + clx, gy = slots[j].y0 + cly;
                     D[c] = (T)coef_e(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
 #pragma unroll
                     for (int q = 0; q < Q; ++q) g[q] = T(0);      // rest state
@@ -181,129 +248,133 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
 #pragma unroll
                     for (int q = 0; q < Q; ++q) g[q] = F[q * CMAX + c];
                 } else {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        const int nxl = wrapi(clx - ex(q), s), nyl = wrapi(cly - ey(q), s);
-                        g[q] = F[opp(q) * CMAX + base + nyl * s + nxl];
-                    }
+                    const int row = c - clx;                                  // cell (0, cly) of the slot
+                    const int xm = (clx == 0 ? s : clx) - 1, xp = clx + 1 == s ? 0 : clx + 1;
+                    const int rm = cly == 0 ? row + s2 - s : row - s;        // row y - 1
+                    const int rp = cly + 1 == s ? row - s2 + s : row + s;    // row y + 1
+                    n1 = row + xp; n3 = row + xm; n2 = rp + clx; n4 = rm + clx;     // x + e_a for a = 1..4
+                    n5 = rp + xp; n6 = rp + xm; n7 = rm + xm; n8 = rm + xp;         // a = 5..8
+                    g[0] = F[c];
+                    g[1] = F[3 * CMAX + n3]; g[3] = F[1 * CMAX + n1];
+                    g[2] = F[4 * CMAX + n4]; g[4] = F[2 * CMAX + n2];
+                    g[5] = F[7 * CMAX + n7]; g[7] = F[5 * CMAX + n5];
+                    g[6] = F[8 * CMAX + n8]; g[8] = F[6 * CMAX + n6];
                 }
                 const T e = D[c];
-                const T Gx = sl.drive == 0 ? (T)a.gmag : T(0);
-                const T Gy = sl.drive == 0 ? T(0) : (T)a.gmag;
-                T drho = 0, jx = 0, jy = 0;
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    drho += g[q];
-                    jx += (T)ex(q) * g[q];
-                    jy += (T)ey(q) * g[q];
-                }
-                const T rho = T(1) + drho;
-                const T rx = jx + (T)a.half_eps * rho * Gx;
-                const T ry = jy + (T)a.half_eps * rho * Gy;
-                const T rux = rx - e * rx;                               // Eq. 6 times rho: (1 - e) r
-                const T ruy = ry - e * ry;
-                const bool check = t == sl.next_check || t == a.max_steps;
-                if (check) {
+                const bool along_y = (h.z & 2) != 0;
+                T rux, ruy, rho;
+                collide_d2q9<T>(g, e, along_y ? T(0) : hg, along_y ? hg : T(0), a, rux, ruy, rho);
+                if (t == h.y || t == max_steps) {
                     UX[c] = rux / rho;                                   // Eq. 15
                     UY[c] = ruy / rho;
-                }
-                const T uex = (T)a.two_tau * rux + (T)a.omt * jx;        // Eq. 16 times rho
-                const T uey = (T)a.two_tau * ruy + (T)a.omt * jy;
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const T eu = (T)ex(q) * uex + (T)ey(q) * uey;
-                    const T w = q == 0 ? T(4.0 / 9.0) : (q <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
-                    const T geq = w * (drho + T(3) * eu);                 // Eq. 2
-                    g[q] = g[q] + (T)a.omega * (geq - g[q]);                 // Eq. 13
                 }
                 if ((t & 1) == 0) {
 #pragma unroll
                     for (int q = 0; q < Q; ++q) F[opp(q) * CMAX + c] = g[q];
                 } else {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        const int nxl = wrapi(clx + ex(q), s), nyl = wrapi(cly + ey(q), s);
-                        F[q * CMAX + base + nyl * s + nxl] = g[q];
-                    }
+                    F[c] = g[0];
+                    F[1 * CMAX + n1] = g[1]; F[3 * CMAX + n3] = g[3];
+                    F[2 * CMAX + n2] = g[2]; F[4 * CMAX + n4] = g[4];
+                    F[5 * CMAX + n5] = g[5]; F[7 * CMAX + n7] = g[7];
+                    F[6 * CMAX + n6] = g[6]; F[8 * CMAX + n8] = g[8];
                 }
             }
             __syncthreads();
 
-            // ----------------------------------------------------- bookkeeping
-            if (tid == 0 && !s_abort) {
-                if (*(volatile int *)a.abort_flag) s_abort = 1;
-                else if (globaltimer() - t0 > a.time_limit_ns) {
-                    s_abort = 1;
-                    atomicExch(a.abort_flag, 1);
+            // ------------------------------------- bookkeeping, only at check steps
+            // (and every 256 steps for the wall-clock limit); s_event is uniform
+            if (Tcta == s_event || (Tcta & 255u) == 255u) {
+                if (tid == 0 && !s_abort) {
+                    if (*(volatile int *)a.abort_flag) s_abort = 1;
+                    else if (globaltimer() - t0 > a.time_limit_ns) {
+                        s_abort = 1;
+                        atomicExch(a.abort_flag, 1);
+                    }
                 }
-            }
-            __syncthreads();
-            const bool abort_now = s_abort != 0;
-            for (int j = wid; j < nslots; j += LOCAL_THREADS / 32) {
-                Slot sl = slots[j];
-                if (sl.job < 0) continue;
-                const int t = (int)(Tcta - sl.tstart);
-                const bool check = t == sl.next_check || t == a.max_steps;
-                if (!check && !abort_now) continue;
-                int st = -1;   // -1: keep going
-                double ux = 0.0, uy = 0.0;
-                if (check) {
-                    for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
-                        ux += (double)UX[c];
-                        uy += (double)UY[c];
+                __syncthreads();
+                const bool abort_now = s_abort != 0;
+                for (int j = wid; j < nslots; j += LOCAL_THREADS / 32) {
+                    int4 h = hot[j];
+                    if (!(h.z & 1)) continue;
+                    Slot sl = slots[j];
+                    const int t = (int)(Tcta - (unsigned)h.x);
+                    const bool check = t == h.y || t == max_steps;
+                    if (!check && !abort_now) continue;
+                    int st = -1;   // -1: keep going
+                    double ux = 0.0, uy = 0.0;
+                    if (check) {
+                        for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
+                            ux += (double)UX[c];
+                            uy += (double)UY[c];
+                        }
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            ux += __shfl_xor_sync(0xffffffffu, ux, off);
+                            uy += __shfl_xor_sync(0xffffffffu, uy, off);
+                        }
+                        ux /= (double)s2;
+                        uy /= (double)s2;
+                        const double cur = sl.drive == 0 ? ux : uy;
+                        const bool regular = t == h.y;
+                        if (regular) h.y += a.check_every;
+                        if (a.tol > 0.0 && t > a.check_every && regular &&
+                            fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur))
+                            st = LBM_OK;
+                        else if (t == max_steps)
+                            st = a.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
+                        sl.prev = cur;
+                    }
+                    if (abort_now && st < 0) st = LBM_ETIMEOUT;
+                    if (lane == 0) {
+                        if (st >= 0) {
+                            // Eq. 17: column `drive` of K* from the mean velocity (NaN if abandoned unchecked)
+                            const double kx = check ? a.nu_over_g * ux : __longlong_as_double(0x7ff8000000000000LL);
+                            const double ky = check ? a.nu_over_g * uy : __longlong_as_double(0x7ff8000000000000LL);
+                            a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 0 : 1)] = kx;
+                            a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 2 : 3)] = ky;
+                            if (a.steps) a.steps[2 * (int64_t)sl.leaf + sl.drive] = t;
+                            if (st != LBM_OK) {
+                                atomicMax(&a.status[sl.leaf], st);
+                                atomicMax(a.worst, st);
+                            }
+                            // refill the slot from this size's queue
+                            int q = abort_now ? qn : atomicAdd(&a.heads[cls], 1);
+                            if (q < qn) {
+                                sl.job = a.jobs[qbeg + q];
+                                sl.leaf = sl.job >> 1;
+                                sl.drive = sl.job & 1;
+                                sl.x0 = a.leaves[3 * sl.leaf];
+                                sl.y0 = a.leaves[3 * sl.leaf + 1];
+                                sl.prev = 0.0;
+                                h = make_int4((int)(Tcta + 1u), a.check_every, 1 | (sl.drive << 1), 0);
+                            } else {
+                                sl.job = -1;
+                                h.z = 0;
+                            }
+                        }
+                        slots[j] = sl;
+                        hot[j] = h;
+                    }
+                    __syncwarp();
+                }
+                __syncthreads();   // slot updates of every warp are visible before they are read
+                // next event: the earliest step at which an active slot reaches min(next check, max_steps)
+                if (wid == 0) {
+                    unsigned best = 0xffffffffu;
+                    for (int j = lane; j < nslots; j += 32) {
+                        const int4 h = hot[j];
+                        if (h.z & 1) {
+                            const int t = (int)(Tcta - (unsigned)h.x);
+                            best = min(best, (unsigned)(min(h.y, max_steps) - t));
+                        }
                     }
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        ux += __shfl_xor_sync(0xffffffffu, ux, off);
-                        uy += __shfl_xor_sync(0xffffffffu, uy, off);
-                    }
-                    ux /= (double)s2;
-                    uy /= (double)s2;
-                    const double cur = sl.drive == 0 ? ux : uy;
-                    const bool regular = t == sl.next_check;
-                    if (regular) sl.next_check += a.check_every;
-                    if (a.tol > 0.0 && t > a.check_every && regular &&
-                        fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur))
-                        st = LBM_OK;
-                    else if (t == a.max_steps)
-                        st = a.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
-                    sl.prev = cur;
+                    for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
+                    if (lane == 0) s_event = Tcta + best;
                 }
-                if (abort_now && st < 0) st = LBM_ETIMEOUT;
-                if (lane == 0) {
-                    if (st >= 0) {
-                        // Eq. 17: column `drive` of K* from the mean velocity (NaN if abandoned unchecked)
-                        const double kx = check ? a.nu_over_g * ux : __longlong_as_double(0x7ff8000000000000LL);
-                        const double ky = check ? a.nu_over_g * uy : __longlong_as_double(0x7ff8000000000000LL);
-                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 0 : 1)] = kx;
-                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 2 : 3)] = ky;
-                        if (a.steps) a.steps[2 * (int64_t)sl.leaf + sl.drive] = (int)t;
-                        if (st != LBM_OK) {
-                            atomicMax(&a.status[sl.leaf], st);
-                            atomicMax(a.worst, st);
-                        }
-                        // refill the slot from this size's queue
-                        int q = abort_now ? qn : atomicAdd(&a.heads[cls], 1);
-                        if (q < qn) {
-                            sl.job = a.jobs[qbeg + q];
-                            sl.leaf = sl.job >> 1;
-                            sl.drive = sl.job & 1;
-                            sl.x0 = a.leaves[3 * sl.leaf];
-                            sl.y0 = a.leaves[3 * sl.leaf + 1];
-                            sl.tstart = Tcta + 1;
-                            sl.next_check = a.check_every;
-                            sl.prev = 0.0;
-                        } else {
-                            sl.job = -1;
-                        }
-                    }
-                    slots[j] = sl;
-                }
-                __syncwarp();
+                any = __syncthreads_or(tid < nslots && (hot[tid].z & 1));
             }
             ++Tcta;
-            __syncthreads();   // slot updates of every warp are visible before they are tested
-            any = __syncthreads_or(tid < nslots && slots[tid].job >= 0);
         }
     }
 }
@@ -370,6 +441,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.omt = (1.0 - 2.0 * p->tau);
     a.half_eps = (0.5 * p->eps);
     a.gmag = g_const;
+    cell_consts(a);
     a.eps_nu = p->eps * nu;
     a.nu_over_g = nu / g_const;
     a.tol = tol_rel;
@@ -675,6 +747,7 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     a.omt = (1.0 - 2.0 * p->tau);
     a.half_eps = (0.5 * p->eps);
     a.gmag = g_const;
+    cell_consts(a);
     a.eps_nu = p->eps * nu;
     a.nu_over_g = nu / g_const;
     a.tol = tol_rel;

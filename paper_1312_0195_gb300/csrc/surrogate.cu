@@ -5,6 +5,8 @@
 #include "lbm_internal.h"
 #include "surrogate_kernels.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -106,8 +108,8 @@ __global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, 
     }
 }
 
-// FP32 [n][2][32][32] inputs (rows idx[b]) -> BF16 NHWC [B][32][32][16] with
-// plane 0 normalised as (x - shift) / scale, plane 1 as is, planes 2..15 zero.
+// FP32 [n][2][32][32] inputs (rows idx[b]) -> BF16 16-channel activation (act_at layout) with
+// channel 0 normalised as (x - shift) / scale, channel 1 as is, channels 2..15 zero.
 __global__ void __launch_bounds__(256) input_kernel(const float *x, const int *idx, int B, float shift, float scale,
                                                    __nv_bfloat16 *out)
 {
@@ -119,9 +121,8 @@ __global__ void __launch_bounds__(256) input_kernel(const float *x, const int *i
         __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(o);
         ob[0] = __float2bfloat16_rn((x[src + q] - shift) / scale);
         ob[1] = __float2bfloat16_rn(x[src + PIX + q]);
-        uint4 *dst = reinterpret_cast<uint4 *>(out + t * CIN0);
-        dst[0] = o[0];
-        dst[1] = o[1];
+        *reinterpret_cast<uint4 *>(out + act_at(b, q, 0, CIN0)) = o[0];
+        *reinterpret_cast<uint4 *>(out + act_at(b, q, 8, CIN0)) = o[1];
     }
 }
 
@@ -147,29 +148,34 @@ __global__ void pack_bwd_kernel(const float *w, int cin, int cout, __nv_bfloat16
     }
 }
 
-// Global average pooling of the last activation and the linear head. One CTA per image.
+// Global average pooling of the last activation and the linear head. One CTA per image;
+// thread t reads elements t, t + 256, ... of each 8-channel plane (always channel t % 8), and
+// the 32 partial sums of a channel are folded in a fixed order.
 __global__ void __launch_bounds__(256) gap_head_kernel(const __nv_bfloat16 *act, const float *wh, const float *bh,
                                                       float *pooled, float *y)
 {
-    const int b = blockIdx.x;
-    __shared__ float part[4][64];
+    const int b = blockIdx.x, t = threadIdx.x;
+    __shared__ float part[32][64];
     __shared__ float pool[64];
-    const int c = threadIdx.x & 63, quarter = threadIdx.x >> 6;
-    float s = 0.0f;
-    for (int q = quarter * 256; q < (quarter + 1) * 256; ++q)
-        s += __bfloat162float(act[((int64_t)b * PIX + q) * 64 + c]);
-    part[quarter][c] = s;
-    __syncthreads();
-    if (threadIdx.x < 64) {
-        const float v = (part[0][c] + part[1][c] + part[2][c] + part[3][c]) / PIX;
-        pool[c] = v;
-        pooled[(int64_t)b * 64 + c] = v;
+    for (int g = 0; g < 8; ++g) {
+        const __nv_bfloat16 *plane = act + act_at(b, 0, 8 * g, 64);
+        float s = 0.0f;
+        for (int e = t; e < PIX * 8; e += 256) s += __bfloat162float(plane[e]);
+        part[t >> 3][8 * g + (t & 7)] = s;
     }
     __syncthreads();
-    if (threadIdx.x < 2) {
-        float acc = bh[threadIdx.x];
-        for (int k = 0; k < 64; ++k) acc += wh[threadIdx.x * 64 + k] * pool[k];
-        y[(int64_t)b * 2 + threadIdx.x] = acc;
+    if (t < 64) {
+        float v = 0.0f;
+        for (int k = 0; k < 32; ++k) v += part[k][t];
+        v /= PIX;
+        pool[t] = v;
+        pooled[(int64_t)b * 64 + t] = v;
+    }
+    __syncthreads();
+    if (t < 2) {
+        float acc = bh[t];
+        for (int k = 0; k < 64; ++k) acc += wh[t * 64 + k] * pool[k];
+        y[(int64_t)b * 2 + t] = acc;
     }
 }
 
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(256) gap_backward_kernel(const float *dpool, c
     const int64_t total = (int64_t)B * PIX * 64;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = t / (PIX * 64);
-        const int c = (int)(t & 63);
+        const int c = (int)((t / (PIX * 8)) & 7) * 8 + (int)(t & 7);      // act_at layout
         const float g = __bfloat162float(act[t]) > 0.0f ? dpool[b * 64 + c] / PIX : 0.0f;
         dact[t] = __float2bfloat16_rn(g);
     }
@@ -245,17 +251,19 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16 *in, con
         for (int j = 0; j < TCI; ++j) acc[i][j] = 0.0f;
     float bacc = 0.0f;   // bias partial for channel tid (tap 0)
     for (int row = 0; row < IMG; ++row) {
+        // q -> (8-channel group, pixel, channel in group): consecutive threads read a plane's row
         for (int q = tid; q < IMG * COUT; q += 256) {
-            const int px = q / COUT, c = q - px * COUT;
-            sO[px][c] = __bfloat162float(dout[((int64_t)b * PIX + row * IMG + px) * COUT + c]);
+            const int px = (q >> 3) & (IMG - 1), c = (q >> 8) * 8 + (q & 7);
+            sO[px][c] = __bfloat162float(dout[act_at(b, row * IMG + px, c, COUT)]);
         }
         const int ys = row + dy - 1;
         for (int q = tid; q < IMG * CIN; q += 256) {
-            const int px = q / CIN, c = q - px * CIN;
+            const int px = CIN >= 8 ? (q >> 3) & (IMG - 1) : q / CIN;
+            const int c = CIN >= 8 ? (q >> 8) * 8 + (q & 7) : q - px * CIN;
             const int xs = px + dx - 1;
             float v = 0.0f;
             if (ys >= 0 && ys < IMG && xs >= 0 && xs < IMG)
-                v = __bfloat162float(in[((int64_t)b * PIX + ys * IMG + xs) * CINP + c]);
+                v = __bfloat162float(in[act_at(b, ys * IMG + xs, c, CINP)]);
             sI[px][c] = v;
         }
         __syncthreads();
@@ -383,6 +391,38 @@ __global__ void destandardise_kernel(float *y, int n, int nmodels, const float *
 
 // ---------------------------------------------------------------- launchers
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time libcuda dependency)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map over BF16 activations in channel-group planes [nimg][cin_p/8][32][32][8], seen as 4-D
+// (8 channels, 32 columns, 32 rows, nimg * cin_p / 8 planes): boxes of 8 channels x 34 columns x 18 rows
+// of one plane (a half-image tile with its one-pixel halo); out-of-range pixels read as zero.
+static cudaError_t encode_halo_map(CUtensorMap *map, const __nv_bfloat16 *act, int cin_p, int nimg)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {8, IMG, IMG, (cuuint64_t)nimg * (cin_p / 8)};
+    const cuuint64_t strides[3] = {8 * 2, (cuuint64_t)IMG * 8 * 2, (cuuint64_t)PIX * 8 * 2};
+    const cuuint32_t box[4] = {8, HALO_W, HALO_H, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(act), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CIN_P, int COUT, int EPI>
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t st)
 {
@@ -390,21 +430,29 @@ cudaError_t launch_conv(const ConvArgs &a, cudaStream_t st)
     static int resident = 0;     // CTAs per SM for this instantiation (persistent grid)
     static int sms = 0;
     if (!resident) {
-        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN_P, COUT, EPI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        if ((int)S::SMEM > optin) return cudaErrorInvalidConfiguration;
+        e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN_P, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)S::SMEM);
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv3x3_tc_kernel<CIN_P, COUT, EPI>, CONV_THREADS,
                                                           S::SMEM);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
+        // co-resident CTAs share the SM's 512 TMEM columns
+        const int tmem_fit = 512 / (int)S::TMEM_COLS;
         sms = sm_count(dev);
-        resident = nb < 1 ? 1 : nb;
+        resident = std::max(1, std::min(nb, tmem_fit));
     }
-    const int64_t ntiles = (int64_t)a.nimg * 8;
+    CUtensorMap map;
+    cudaError_t e = encode_halo_map(&map, a.in, CIN_P, a.nimg);
+    if (e != cudaSuccess) return e;
+    const int64_t nitems = (int64_t)a.nimg * 2;
     const int64_t cap = (int64_t)sms * resident;
-    conv3x3_tc_kernel<CIN_P, COUT, EPI><<<(int)(ntiles < cap ? ntiles : cap), CONV_THREADS, S::SMEM, st>>>(a);
+    conv3x3_tc_kernel<CIN_P, COUT, EPI><<<(int)(nitems < cap ? nitems : cap), CONV_THREADS, S::SMEM, st>>>(map, a);
     return cudaGetLastError();
 }
 

@@ -5,21 +5,30 @@
 //
 // Network: six 3x3 'same' convolutions 2(->16 padded) -> 32 -> 32 -> 64 -> 64 ->
 // 64 -> 64 with ReLU, global average pooling over the 32 x 32 patch, a linear
-// head to 2 outputs. Activations are BF16 NHWC [B][32][32][C]; FP32 master
-// weights; accumulation in FP32.
+// head to 2 outputs. Activations are BF16 in channel-group planes
+// [B][C/8][32][32][8] (act_at below); FP32 master weights; accumulation in FP32.
 //
-//  * conv3x3_tc_kernel: implicit GEMM on the tensor cores (tcgen05, TMEM). One
-//    CTA = 128 output pixels (4 rows of one image) x all output channels; the
-//    9 taps are the 9 K-blocks (K-block = all input channels of one tap). The
-//    weights of the layer stay resident in shared memory; the im2col tile of a
-//    tap is gathered by all 128 threads into a double buffer while the previous
-//    tap's MMAs run. Used for the forward pass (epilogue: bias + ReLU) and for
-//    the input gradient (flipped, transposed weights; epilogue: ReLU mask).
+//  * conv3x3_tc_kernel: implicit GEMM on the tensor cores (tcgen05, TMEM, TMA)
+//    without an im2col copy. A work item is half an image (16 rows x 32
+//    columns = 512 output pixels). TMA loads the item's input with a one-pixel
+//    zero halo (18 x 34 pixels) into shared memory, one box per 8-channel
+//    plane (rows of 34 x 16 contiguous bytes in global memory), so in shared
+//    memory a pixel's 8 channels are 16 contiguous bytes and a row of 8 pixels
+//    is one 128-byte core matrix. The A operand of a tap (dy, dx) for
+//    an M-tile of 16 rows x 8 columns is then just a descriptor into that
+//    halo tile: start at (dy, 8 m + dx), 8-row groups one padded image row
+//    (544 B) apart, K groups one plane apart. The 9 taps x CIN/16 K-steps of
+//    the 4 M-tiles accumulate into TMEM; the layer's weights stay resident in
+//    shared memory. Warp-specialised and double-buffered: warp 0 issues the
+//    TMA loads, warp 1 the MMAs, warps 2-5 drain the other TMEM buffer
+//    (epilogue: bias + ReLU for the forward pass, ReLU mask for the input
+//    gradient, which runs with flipped, transposed weights).
 //  * wgrad_kernel: weight gradient per (image, tap) on CUDA cores in FP32,
 //    written as per-image partials and folded in a fixed order (deterministic).
 #pragma once
 
 #include "sm100_umma.cuh"
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 namespace lbm {
@@ -35,47 +44,66 @@ __host__ __device__ constexpr int cout_of(int l) { return l <= 1 ? 32 : 64; }
 
 enum Epi { EPI_BIAS_RELU = 0, EPI_MASK = 1 };
 
+// Element (image b, pixel p, channel c) of a C-channel activation: channel-group planes
+// [B][C/8][32][32][8], so one 8-channel plane of an image is 16 KB contiguous.
+__host__ __device__ __forceinline__ int64_t act_at(int64_t b, int p, int c, int C)
+{
+    return ((b * (C >> 3) + (c >> 3)) * PIX + p) * 8 + (c & 7);
+}
+
 struct ConvArgs {
-    const __nv_bfloat16 *in;     // [B][32][32][CIN_P]
+    const __nv_bfloat16 *in;     // [B][CIN_P/8][32][32][8] (read through the tensor map)
     const __nv_bfloat16 *wpack;  // B operand, core-matrix layout, [COUT rows][9 * CIN_P]
     const float *bias;           // [COUT] (EPI_BIAS_RELU)
-    const __nv_bfloat16 *mask;   // [B][32][32][COUT] (EPI_MASK): output *= (mask > 0)
-    __nv_bfloat16 *out;          // [B][32][32][COUT]
+    const __nv_bfloat16 *mask;   // [B][COUT/8][32][32][8] (EPI_MASK): output *= (mask > 0)
+    __nv_bfloat16 *out;          // [B][COUT/8][32][32][8]
     int nimg;
     int *err;                    // set to 1 if a bounded wait gave up
 };
 
 constexpr uint32_t WAIT_LIMIT = 1u << 24;   // polls before a wait gives up (~0.1-1 s)
 
+constexpr int HALF_ROWS = IMG / 2;                            // output rows per work item
+constexpr int HALO_W = IMG + 2;                               // 34 padded columns
+constexpr int HALO_H = HALF_ROWS + 2;                         // 18 padded rows
+constexpr uint32_t PLANE_TX = HALO_W * HALO_H * 16;           // 9792 bytes per 8-channel TMA box
+constexpr uint32_t PLANE = (PLANE_TX + 127u) / 128u * 128u;   // planes start 128-byte aligned
+constexpr uint32_t CTRL = 512;                                // barriers, TMEM address, flag, bias
+constexpr int CONV_THREADS = 192;                             // TMA warp, MMA warp, 4 epilogue warps
+
 template <int CIN_P, int COUT>
 struct ConvShape {
+    static constexpr int NG = CIN_P / 8;                      // 8-channel planes per tile
     static constexpr int K = 9 * CIN_P;
     static constexpr uint32_t B_BYTES = (uint32_t)COUT * K * 2;
-    static constexpr uint32_t A_BYTES = 128u * CIN_P * 2;
-    static constexpr uint32_t SMEM = B_BYTES + 2 * A_BYTES;
-    static constexpr uint32_t TMEM_COLS = COUT < 32 ? 32 : COUT;
+    static constexpr uint32_t A_BYTES = NG * PLANE;
+    static constexpr uint32_t SMEM = CTRL + B_BYTES + 2 * A_BYTES + 128;   // + runtime alignment
+    static constexpr uint32_t TMEM_COLS = 2 * 4 * COUT;       // 2 buffers x 4 M-tiles x COUT columns
+    static_assert(B_BYTES % 128 == 0, "weight block keeps the tiles 128-byte aligned");
+    static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two >= 32");
 };
 
-constexpr int CONV_THREADS = 256;          // 8 warps: all gather; warps w and w+4 share TMEM lanes
-
 template <int CIN_P, int COUT, int EPI>
-__global__ void __launch_bounds__(CONV_THREADS) conv3x3_tc_kernel(ConvArgs a)
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a)
 {
     using S = ConvShape<CIN_P, COUT>;
-    constexpr int KB = CIN_P;                       // K-block = one tap, all input channels
-    constexpr int KG = KB / 8;                      // core matrices along K per tap
+    constexpr int KSTEPS = CIN_P / 16;
     constexpr uint32_t IDESC = umma::idesc_bf16_f32(128, COUT);
-    constexpr int HALF = COUT / 2;                  // TMEM columns read by each warpgroup
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *sB = smem;
-    uint8_t *sA[2] = {smem + S::B_BYTES, smem + S::B_BYTES + S::A_BYTES};
-    __shared__ uint64_t mbar[2];
-    __shared__ uint32_t s_taddr;
-    __shared__ float s_bias[COUT];
-    __shared__ int s_fail;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((128u - (umma::smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);      // [2] input tile landed (TMA bytes)
+    uint64_t *empty = full + 2;                               // [2] MMAs finished reading the tile
+    uint64_t *tfull = full + 4;                               // [2] accumulators complete
+    uint64_t *tempty = full + 6;                              // [2] accumulators drained
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem + 64);
+    volatile int *s_fail = reinterpret_cast<volatile int *>(smem + 68);
+    float *s_bias = reinterpret_cast<float *>(smem + 128);
+    uint8_t *sB = smem + CTRL;
+    uint8_t *sA = sB + S::B_BYTES;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ntiles = a.nimg * 8;                 // tile = 4 rows (128 pixels) of one image
+    const int nitems = a.nimg * 2;
 
     // resident weights (already in the core-matrix layout) and bias, loaded once per CTA
     for (uint32_t i = tid; i < S::B_BYTES / 16; i += CONV_THREADS)
@@ -83,111 +111,148 @@ __global__ void __launch_bounds__(CONV_THREADS) conv3x3_tc_kernel(ConvArgs a)
     if (EPI == EPI_BIAS_RELU)
         for (int i = tid; i < COUT; i += CONV_THREADS) s_bias[i] = a.bias[i];
     if (tid == 0) {
-        umma::mbar_init(&mbar[0], 1);
-        umma::mbar_init(&mbar[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            umma::mbar_init(&full[i], 1);
+            umma::mbar_init(&empty[i], 1);
+            umma::mbar_init(&tfull[i], 1);
+            umma::mbar_init(&tempty[i], 4);
+        }
         umma::fence_mbar_init();
-        s_fail = 0;
+        *s_fail = 0;
+        umma::prefetch_tmap(&tmap);
     }
-    if (warp == 0) umma::tmem_alloc(&s_taddr, S::TMEM_COLS);
+    if (warp == 1) umma::tmem_alloc(s_taddr, S::TMEM_COLS);
+    umma::fence_proxy_async();                 // weights: generic stores, tensor-core reads
     umma::fence_before();
     __syncthreads();
     umma::fence_after();
-    const uint32_t tmem = s_taddr;
+    const uint32_t tmem = *s_taddr;
 
-    uint32_t phase[2] = {0u, 0u};
-    int issued[2] = {0, 0};                        // commits on each barrier not yet waited for
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int img = tile >> 3, rb = tile & 7;
-        for (int kb = 0; kb < 9; ++kb) {
-            const int b = kb & 1;
-            if (issued[b]) {                       // earlier MMAs read this buffer
-                if (!umma::mbar_wait_bounded(&mbar[b], phase[b], WAIT_LIMIT)) s_fail = 1;
-                phase[b] ^= 1u;
-                issued[b] = 0;
-                __syncthreads();
-                if (s_fail) break;
+    if (warp == 0) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int k = 0;
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
+                const int b = k & 1;
+                if (k >= 2 && !umma::mbar_wait_bounded(&empty[b], ((k >> 1) - 1) & 1, WAIT_LIMIT)) {
+                    *s_fail = 1;
+                    break;
+                }
+                if (*s_fail) break;
+                const int img = item >> 1, y0 = (item & 1) * HALF_ROWS;
+                uint8_t *dst = sA + b * S::A_BYTES;
+                umma::mbar_arrive_expect_tx(&full[b], S::NG * PLANE_TX);
+#pragma unroll
+                for (int g = 0; g < S::NG; ++g)
+                    umma::tma_load_4d(dst + g * PLANE, &tmap, &full[b], 0, -1, y0 - 1, img * S::NG + g);
             }
-            const int dy = kb / 3, dx = kb % 3;
-            uint8_t *dst = sA[b];
-            // eight consecutive threads fill one 128-byte core matrix (8 pixels x 16 bytes)
-            for (int i = tid; i < 128 * KG; i += CONV_THREADS) {
-                const int cm = i >> 3, rr = i & 7;
-                const int rg = cm / KG, g = cm - rg * KG;
-                const int r = rg * 8 + rr;
-                const int y = rb * 4 + (r >> 5) + dy - 1, x = (r & 31) + dx - 1;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (y >= 0 && y < IMG && x >= 0 && x < IMG)
-                    v = *reinterpret_cast<const uint4 *>(a.in + ((int64_t)(img * IMG + y) * IMG + x) * CIN_P + g * 8);
-                *reinterpret_cast<uint4 *>(dst + (uint32_t)rg * (KG * 128) + g * 128 + rr * 16) = v;
-            }
-            umma::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
+            if (*s_fail)     // loads already issued land before shared memory is released
+                for (int kk = k - 2 < 0 ? 0 : k - 2; kk < k; ++kk)
+                    umma::mbar_wait_bounded(&full[kk & 1], (kk >> 1) & 1, WAIT_LIMIT);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t b_base = umma::smem_addr(sB);
+            int k = 0;
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
+                const int b = k & 1;
+                if (!umma::mbar_wait_bounded(&full[b], (k >> 1) & 1, WAIT_LIMIT) ||
+                    (k >= 2 && !umma::mbar_wait_bounded(&tempty[b], ((k >> 1) - 1) & 1, WAIT_LIMIT))) {
+                    *s_fail = 1;
+                    break;
+                }
+                if (*s_fail) break;
                 umma::fence_after();
+                const uint32_t a_base = umma::smem_addr(sA + b * S::A_BYTES);
+#pragma unroll 1
+                for (int m = 0; m < 4; ++m) {
+                    const uint32_t d = tmem + (uint32_t)((b * 4 + m) * COUT);
 #pragma unroll
-                for (int kk = 0; kk < KB / 16; ++kk) {
-                    const uint64_t ad = umma::desc(umma::smem_addr(dst) + kk * 256, 128, KG * 128);
-                    const uint64_t bd = umma::desc(umma::smem_addr(sB) + ((kb * KB + kk * 16) / 8) * 128, 128,
-                                                   (S::K / 8) * 128);
-                    umma::mma_bf16(tmem, ad, bd, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+                        for (int c = 0; c < KSTEPS; ++c) {
+                            const uint64_t ad = umma::desc(a_base + 2u * c * PLANE +
+                                                               (uint32_t)(dy * HALO_W + 8 * m + dx) * 16u,
+                                                           PLANE, HALO_W * 16);
+                            const uint64_t bd = umma::desc(b_base + ((tap * CIN_P + c * 16) / 8) * 128, 128,
+                                                           (S::K / 8) * 128);
+                            umma::mma_bf16(d, ad, bd, IDESC, (tap > 0 || c > 0) ? 1u : 0u);
+                        }
+                    }
                 }
-                umma::commit(&mbar[b]);
+                umma::commit(&empty[b]);
+                umma::commit(&tfull[b]);
             }
-            issued[b] = 1;
+            // the last commits land before TMEM and shared memory are released
+            for (int kk = k - 2 < 0 ? 0 : k - 2; kk < k; ++kk)
+                umma::mbar_wait_bounded(&empty[kk & 1], (kk >> 1) & 1, WAIT_LIMIT);
         }
-        if (s_fail) break;
-        // the last commit of the tile (tap 8, buffer 0) covers every MMA issued before it;
-        // the decision is made CTA-wide because tcgen05.ld is warp-collective
-        const bool waited = umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);
-        phase[0] ^= 1u;
-        issued[0] = 0;
-        if (!__syncthreads_and(waited ? 1 : 0)) {
-            s_fail = 1;
-            break;
-        }
-        umma::fence_after();
-        const int wq = warp & 3, half = warp >> 2;    // TMEM lane quarter, column half
-        const int y = rb * 4 + wq, x = lane;           // this thread's pixel = TMEM lane 32 wq + lane
-        const int64_t pix = (int64_t)(img * IMG + y) * IMG + x;
+    } else {
+        // ---------------------------------------------------------------- epilogue, warps 2-5
+        const int q = warp & 3;                 // TMEM lane quarter this warp may read
+        int k = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
+            const int b = k & 1;
+            const bool ok = umma::mbar_wait_bounded(&tfull[b], (k >> 1) & 1, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, ok)) {   // tcgen05.ld is warp-collective
+                *s_fail = 1;
+                break;
+            }
+            umma::fence_after();
+            // TMEM lane 32 q + lane = M row: output row 4 q + lane / 8 of the half, column 8 m + lane % 8
+            const int img = item >> 1, y = (item & 1) * HALF_ROWS + 4 * q + (lane >> 3);
+#pragma unroll 1
+            for (int m = 0; m < 4; ++m) {
+                const int pix = y * IMG + 8 * m + (lane & 7);
+                uint32_t acc[COUT / 16][16];
 #pragma unroll
-        for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 16) {
-            float v[16];
-            umma::tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c0, v);
-            if (EPI == EPI_BIAS_RELU) {
+                for (int c = 0; c < COUT / 16; ++c)
+                    umma::tmem_ld16_async(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((b * 4 + m) * COUT + 16 * c),
+                                          acc[c]);
+                umma::tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.0f);
-            } else {
-                const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + pix * COUT + c0);
-                const uint4 m0 = mp[0], m1 = mp[1];
-                const __nv_bfloat16 *mb0 = reinterpret_cast<const __nv_bfloat16 *>(&m0);
-                const __nv_bfloat16 *mb1 = reinterpret_cast<const __nv_bfloat16 *>(&m1);
+                for (int c = 0; c < COUT / 16; ++c) umma::tmem_hold(acc[c]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (!(__bfloat162float(mb0[j]) > 0.0f)) v[j] = 0.0f;
-                    if (!(__bfloat162float(mb1[j]) > 0.0f)) v[8 + j] = 0.0f;
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(acc[c0 / 16][j]);
+                    if (EPI == EPI_BIAS_RELU) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j] + s_bias[c0 + j], 0.0f);
+                    } else {
+                        const uint4 m0 = *reinterpret_cast<const uint4 *>(a.mask + act_at(img, pix, c0, COUT));
+                        const uint4 m1 = *reinterpret_cast<const uint4 *>(a.mask + act_at(img, pix, c0 + 8, COUT));
+                        const __nv_bfloat16 *mb0 = reinterpret_cast<const __nv_bfloat16 *>(&m0);
+                        const __nv_bfloat16 *mb1 = reinterpret_cast<const __nv_bfloat16 *>(&m1);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (!(__bfloat162float(mb0[j]) > 0.0f)) v[j] = 0.0f;
+                            if (!(__bfloat162float(mb1[j]) > 0.0f)) v[8 + j] = 0.0f;
+                        }
+                    }
+                    uint4 o[2];
+                    __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(o);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) ob[j] = __float2bfloat16_rn(v[j]);
+                    *reinterpret_cast<uint4 *>(a.out + act_at(img, pix, c0, COUT)) = o[0];
+                    *reinterpret_cast<uint4 *>(a.out + act_at(img, pix, c0 + 8, COUT)) = o[1];
                 }
             }
-            uint4 o[2];
-            __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(o);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) ob[j] = __float2bfloat16_rn(v[j]);
-            uint4 *op = reinterpret_cast<uint4 *>(a.out + pix * COUT + c0);
-            op[0] = o[0];
-            op[1] = o[1];
+            umma::fence_before();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive(&tempty[b]);
         }
-        // the next tile's first MMA overwrites the accumulator: every read must be done
-        umma::fence_before();
-        __syncthreads();
-    }
-    if (s_fail) {
-        if (tid == 0) atomicExch(a.err, 1);
-        // give in-flight MMAs a chance to finish before the accumulator is released
-        if (issued[0]) umma::mbar_wait_bounded(&mbar[0], phase[0], WAIT_LIMIT);
-        if (issued[1]) umma::mbar_wait_bounded(&mbar[1], phase[1], WAIT_LIMIT);
     }
     umma::fence_before();
     __syncthreads();
-    if (warp == 0) umma::tmem_dealloc(tmem, S::TMEM_COLS);
+    if (tid == 0 && *s_fail) atomicExch(a.err, 1);
+    if (warp == 1) {
+        umma::fence_after();
+        umma::tmem_dealloc(tmem, S::TMEM_COLS);
+    }
 }
 
 }  // namespace sur

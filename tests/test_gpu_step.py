@@ -254,16 +254,21 @@ def test_full_size_16384_channelised_sampled():
         del full
     W = 2 * n + 9
     h = W // 2
-    for (x, y), (ug, vg, rg) in zip(pts, vals):
+    ref = []
+    for (x, y) in pts:
         win = synth.crop_periodic(kap, x - h, y - h, W, W).astype(np.float64)
         pr = oracle.Problem(tau, nu, eps, kappa=win, g=g)
         f = pr.rest()
         pr.run(f, n)
         ro, uo, vo = pr.fields(f)
-        scale = max(abs(uo[h, h]), abs(vo[h, h]), 1e-30)
-        assert abs(ug - uo[h, h]) <= 1e-5 * scale + 1e-14
-        assert abs(vg - vo[h, h]) <= 1e-5 * scale + 1e-14
-        assert abs(rg - ro[h, h]) <= 1e-6
+        ref.append((uo[h, h], vo[h, h], ro[h, h]))
+    # FP32 rounding of the stored deviations is absolute, set by the largest velocities of the
+    # field (the channels), not by the 1e4-times slower matrix cells: floor 1e-6 of that scale
+    umax = max(max(abs(uo), abs(vo)) for uo, vo, _ in ref)
+    for (ug, vg, rg), (uo, vo, ro) in zip(vals, ref):
+        assert abs(ug - uo) <= 1e-5 * abs(uo) + 1e-6 * umax
+        assert abs(vg - vo) <= 1e-5 * abs(vo) + 1e-6 * umax
+        assert abs(rg - ro) <= 1e-6
     assert abs(total_drho) / (N * N) < 1e-14
 
 
