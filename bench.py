@@ -79,6 +79,17 @@ def max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def make_kappa() -> np.ndarray:
     import synth
     return synth.lognormal_kappa(N, N, 32.0, 2.0, seed=2).astype(np.float32)
@@ -194,24 +205,80 @@ def measure_variants(lbm, torch, kap, stream, steps=300):
     return out
 
 
-def measure_local_keff(lbm, torch, kap, ws, sample=512, seed=11):
+def _oracle_leaf(args):
+    """One local problem by the FP64 oracle (process-pool worker)."""
+    import oracle
+    patch, tol = args
+    oracle.local_keff(patch, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=tol, max_steps=200000)
+    return 0
+
+
+def _oracle_forward(args):
+    """Ensemble forward of one patch by the FP64 surrogate oracle (process-pool worker)."""
+    from oracle import surrogate as osur
+    x, n_models = args
+    for m in range(n_models):
+        osur.forward(osur.init_params(m), x[None])
+    return 0
+
+
+def measure_cpu_oracles(kap_np, leaf_sample=64, patch_sample=32, seed=12):
+    """Oracle rates for the two other units of the metric, on the host cores (a spawn-started
+    process pool, one process per core, each running the oracle as it stands):
+    local K* (both drives, tol 1e-8) on a seeded sample of the quadtree leaves of the bench
+    field, and the 4-model surrogate forward on a seeded sample of their patches."""
+    import multiprocessing as mp
+    import synth
+    from oracle import surrogate as osur
+    leaves = synth.quadtree_leaves(N, N, seed=3)
+    rng = np.random.default_rng(seed)
+    pick = leaves[rng.choice(len(leaves), leaf_sample, replace=False)]
+    patches = [np.array(kap_np[y:y + s, x:x + s], dtype=np.float64) for x, y, s in pick]
+    xs = [osur.make_input(osur.resample_patch(np.log(p)), p.shape[0], 0.0, 1.0) for p in patches[:patch_sample]]
+    workers = os.cpu_count() or 1
+    out = {}
+    with mp.get_context("spawn").Pool(workers) as pool:
+        pool.map(_oracle_leaf, [(patches[0], 1e-8)] * workers)          # start-up outside the timing
+        t0 = time.perf_counter()
+        pool.map(_oracle_leaf, [(p, 1e-8) for p in patches], chunksize=1)
+        dt = time.perf_counter() - t0
+        out["local_keff"] = {"value": leaf_sample / dt, "unit": "patches/s", "cores": workers, "kind": "oracle",
+                             "sample": f"{leaf_sample} seeded quadtree leaves of the bench field, tol 1e-8 "
+                                       f"({dt:.1f} s)"}
+        t0 = time.perf_counter()
+        pool.map(_oracle_forward, [(x, 4) for x in xs], chunksize=1)
+        dt = time.perf_counter() - t0
+        out["surrogate_forward"] = {"value": len(xs) / dt, "unit": "patches/s", "cores": workers,
+                                    "kind": "oracle",
+                                    "sample": f"4-model FP64 forward of {len(xs)} of those leaves' patches ({dt:.1f} s)"}
+    return out
+
+
+def measure_local_keff(lbm, torch, kap, ws, rank=0, sample=512, seed=11):
     """Batched local problems on the 4096^2 field cut by the seeded quadtree (seed 3, ~71.6k
     leaves): one persistent launch for all leaves, tol 1e-8 on the per-drive mean flux,
-    check every 64 steps, at most 200k steps per drive. The one-launch-per-leaf mode is
-    timed on a seeded sample of `sample` leaves, with the persistent launch on the same
-    sample beside it."""
+    check every 64 steps, at most 200k steps per drive. With several ranks each solves its
+    contiguous, work-balanced share of the leaves (no exchange) and the rate is all leaves
+    over the slowest rank's time. The one-launch-per-leaf mode is timed on a seeded sample of
+    `sample` leaves, with the persistent launch on the same sample beside it."""
     import synth
-    leaves_np = synth.quadtree_leaves(N, N, seed=3)
+    from paper_1312_0195_gb300.shard import leaf_shard
+    all_leaves = synth.quadtree_leaves(N, N, seed=3)
+    lo, hi = leaf_shard(all_leaves[:, 2], rank, ws)
+    leaves_np = all_leaves[lo:hi]
     p = lbm.Params(nx=N, ny=N, tau=1.0, eps=1.0)
     leaves = torch.from_numpy(leaves_np).cuda()
+    barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     keff, status, steps, worst = lbm.local_keff(p, kap, leaves, 1e-6, 1e-8, 200000, 64, True)
     torch.cuda.synchronize()
-    t_all = time.perf_counter() - t0
+    t_all = max_over_ranks(time.perf_counter() - t0, ws)
     st = status.cpu().numpy()
     sz = leaves_np[:, 2].astype(np.float64)
     lups = float((steps.cpu().numpy().astype(np.float64).sum(axis=1) * sz * sz).sum())
+    lups = sum_over_ranks(lups, ws)
+    converged = int(sum_over_ranks(float((st == 0).sum()), ws))
     rng = np.random.default_rng(seed)
     idx = rng.choice(len(leaves_np), sample, replace=False)
     sub = torch.from_numpy(leaves_np[idx]).cuda()
@@ -225,8 +292,8 @@ def measure_local_keff(lbm, torch, kap, ws, sample=512, seed=11):
     return {
         "workload": "4096^2 log-normal field (sigma 2, ell 32), quadtree p=0.6 seed 3, tau=1, "
                     "G=1e-6 along x then y, tol 1e-8, FP32, max 200k steps per drive",
-        "leaves": int(len(leaves_np)), "converged": int((st == 0).sum()),
-        "patches_per_s": len(leaves_np) * ws / t_all, "seconds": t_all,
+        "leaves": int(len(all_leaves)), "converged": converged, "ranks": ws,
+        "patches_per_s": len(all_leaves) / t_all, "seconds": t_all,
         "glups": lups / t_all / 1e9,
         "sample": {"leaves": sample, "persistent_patches_per_s": sample / times[True],
                    "per_leaf_launch_patches_per_s": sample / times[False]},
@@ -440,7 +507,7 @@ def run_ours(args, ws, rank, local):
     local = surrogate = None
     if not args.no_extras:
         variants = measure_variants(lbm, torch, kap, stream)
-        local = measure_local_keff(lbm, torch, kap, ws)
+        local = measure_local_keff(lbm, torch, kap, ws, rank)
         if not args.no_surrogate:
             surrogate = measure_surrogate(lbm, torch)
 
@@ -449,6 +516,8 @@ def run_ours(args, ws, rank, local):
         rate, cores, dt = oracle_rate(kap_np, args.cpu_steps)
         cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_steps} lattice steps of the full {N}x{N} lattice ({dt:.1f} s)"}
+        if not args.no_extras:
+            cpu["other_units"] = measure_cpu_oracles(kap_np)
 
     if rank == 0:
         line = {

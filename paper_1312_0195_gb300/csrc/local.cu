@@ -63,8 +63,8 @@ struct LocalArgs {
     int class_size[MAXCLASS];
     int *heads;               // [nclass] queue heads (zeroed before launch)
     double omega, two_tau, omt, half_eps, gmag;
-    float kf[9];              // collision constants (K_*) in FP32 and FP64, set by cell_consts()
-    double kd[9];
+    float kf[4];              // collision constants (K_*) in FP32 and FP64, set by cell_consts()
+    double kd[4];
     double eps_nu;            // eps * nu for the drag coefficient
     double nu_over_g;         // nu / G for Eq. 17
     double tol;
@@ -109,15 +109,12 @@ struct SlotHot {
 };
 
 // Collision constants (host-computed in the storage precision, so the FMAs read them from the
-// constant bank): 1 - omega; omega w_a for the three weight classes; 3 omega w_a for the
-// momentum terms; Eq. 16's 2 tau and 1 - 2 tau; eps G / 2.
-enum { K_OM1, K_A0, K_A9, K_A36, K_B9, K_B36, K_TWO_TAU, K_OMT, K_HG, K_N };
+// constant bank): omega, Eq. 16's 2 tau and 1 - 2 tau, and eps G / 2.
+enum { K_OMEGA, K_TWO_TAU, K_OMT, K_HG, K_N };
 
 void cell_consts(LocalArgs &a)
 {
-    const double w = a.omega;
-    const double k[K_N] = {1.0 - w,  4.0 * w / 9.0, w / 9.0, w / 36.0, w / 3.0,
-                           w / 12.0, a.two_tau,     a.omt,   a.half_eps * a.gmag};
+    const double k[K_N] = {a.omega, a.two_tau, a.omt, a.half_eps * a.gmag};
     for (int i = 0; i < K_N; ++i) {
         a.kd[i] = k[i];
         a.kf[i] = (float)k[i];
@@ -130,8 +127,10 @@ template <> __device__ __forceinline__ double kc<double>(const LocalArgs &a, int
 
 // Eqs. 6, 16, 2 and 13 for one cell in deviation form with the D2Q9 sums written out (a product
 // with a zero velocity component is not free in IEEE arithmetic): moments, r = j + eps rho G / 2,
-// rho u = (1 - e) r, rho u_eq = 2 tau rho u + (1 - 2 tau) j, then
-// g <- (1 - omega) g + omega w_a (drho + 3 e_a . rho u_eq). Returns rho u and rho.
+// rho u = (1 - e) r, rho u_eq = 2 tau rho u + (1 - 2 tau) j, g_eq = w_a (drho + 3 e_a . rho u_eq),
+// and BGK as g + omega (g_eq - g): the difference is formed first, so the rounding of the update
+// stays at the size of the non-equilibrium part (FP32 solves in the Darcy regime depend on it).
+// Returns rho u and rho.
 template <typename T>
 __device__ __forceinline__ void collide_d2q9(T (&g)[Q], T e, T hgx, T hgy, const LocalArgs &a, T &rux, T &ruy,
                                              T &rho)
@@ -147,20 +146,18 @@ __device__ __forceinline__ void collide_d2q9(T (&g)[Q], T e, T hgx, T hgy, const
     ruy = fma(-e, ry, ry);
     const T uex = fma(kc<T>(a, K_TWO_TAU), rux, kc<T>(a, K_OMT) * jx);
     const T uey = fma(kc<T>(a, K_TWO_TAU), ruy, kc<T>(a, K_OMT) * jy);
-    const T om1 = kc<T>(a, K_OM1);
-    const T a9 = kc<T>(a, K_A9) * drho, a36 = kc<T>(a, K_A36) * drho;
-    const T bx9 = kc<T>(a, K_B9) * uex, by9 = kc<T>(a, K_B9) * uey;
-    const T bx36 = kc<T>(a, K_B36) * uex, by36 = kc<T>(a, K_B36) * uey;
-    g[0] = fma(om1, g[0], kc<T>(a, K_A0) * drho);
-    g[1] = fma(om1, g[1], a9 + bx9);
-    g[3] = fma(om1, g[3], a9 - bx9);
-    g[2] = fma(om1, g[2], a9 + by9);
-    g[4] = fma(om1, g[4], a9 - by9);
-    const T p = a36 + bx36, m = a36 - bx36;
-    g[5] = fma(om1, g[5], p + by36);
-    g[8] = fma(om1, g[8], p - by36);
-    g[6] = fma(om1, g[6], m + by36);
-    g[7] = fma(om1, g[7], m - by36);
+    const T om = kc<T>(a, K_OMEGA);
+    const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+    const T tx = T(3) * uex, ty = T(3) * uey, sp = tx + ty, sm = tx - ty;
+    g[0] = fma(om, T(4.0 / 9.0) * drho - g[0], g[0]);
+    g[1] = fma(om, w1 * (drho + tx) - g[1], g[1]);
+    g[3] = fma(om, w1 * (drho - tx) - g[3], g[3]);
+    g[2] = fma(om, w1 * (drho + ty) - g[2], g[2]);
+    g[4] = fma(om, w1 * (drho - ty) - g[4], g[4]);
+    g[5] = fma(om, w2 * (drho + sp) - g[5], g[5]);
+    g[7] = fma(om, w2 * (drho - sp) - g[7], g[7]);
+    g[8] = fma(om, w2 * (drho + sm) - g[8], g[8]);
+    g[6] = fma(om, w2 * (drho - sm) - g[6], g[6]);
 }
 
 template <typename T>

@@ -294,6 +294,168 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16 *in, con
     if (tap == 0 && tid < COUT) bpart[(int64_t)b * COUT + tid] = bacc;
 }
 
+// ------------------------------------------------ weight gradient on the tensor cores (layers 1..5)
+// dW[tap][co][ci] = sum over pixels p of dout[p][co] * in[p + off(tap)][ci] as warp-level BF16 MMAs
+// (mma.sync m16n8k16, FP32 accumulate). A work item is a quarter image (8 rows x 32 columns);
+// cp.async stages its dout tile and its input tile with a one-pixel zero halo in shared memory as
+// 8-channel planes (16 bytes per pixel), double-buffered. ldmatrix.trans turns 8 pixels x 8
+// channels into fragments: A = dout^T (16 co x 16 pixels), B = shifted input (16 pixels x 8 ci),
+// and a tap is just another row address. Each warp owns one 16-channel co tile and NJ 8-channel ci
+// tiles for all 9 taps; a CTA accumulates its items in registers and writes one partial, and
+// wgrad_reduce_kernel folds the partials in CTA order (deterministic). The warps of the first ci
+// group also sum their A fragments: the bias gradient.
+constexpr int WG_THREADS = 256;
+constexpr int WG_ROWS = 8;                                    // output rows per work item
+constexpr int WG_HW = IMG + 2, WG_HH = WG_ROWS + 2;           // input tile with halo: 10 x 34 pixels
+constexpr uint32_t WG_IPLANE = WG_HH * WG_HW * 16;            // bytes per 8-channel input plane
+constexpr uint32_t WG_OPLANE = WG_ROWS * IMG * 16;            // bytes per 8-channel dout plane
+
+template <int COUT, int CIN>
+struct WgShape {
+    static constexpr int CT = COUT / 16, NT = CIN / 8, NJ = CT * NT / 8;
+    static constexpr uint32_t STAGE = (CIN / 8) * WG_IPLANE + (COUT / 8) * WG_OPLANE;
+    static constexpr uint32_t SMEM = 2 * STAGE;
+    static_assert((CT * NT) % 8 == 0 && NJ >= 1 && (NJ == 1 || NJ % 2 == 0), "8 warps share the tiles evenly");
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(saddr), "l"(g), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t saddr, uint32_t (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(saddr));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t saddr, uint32_t (&r)[2])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(saddr));
+}
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float bf16x2_sum(uint32_t v)
+{
+    return __uint_as_float(v << 16) + __uint_as_float(v & 0xffff0000u);
+}
+
+template <int COUT, int CIN>
+__global__ void __launch_bounds__(WG_THREADS, 1) wgrad_mma_kernel(const __nv_bfloat16 *in, const __nv_bfloat16 *dout,
+                                                                 int nimg, float *part, float *bpart)
+{
+    using W = WgShape<COUT, CIN>;
+    constexpr int CT = W::CT, NJ = W::NJ, IPI = IMG / WG_ROWS;
+    extern __shared__ __align__(128) uint8_t wsm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ct = warp % CT, j0 = (warp / CT) * NJ;        // co tile and first ci tile of this warp
+    const int mat = lane >> 3, row = lane & 7;               // ldmatrix: matrix and row this lane addresses
+    const int nitems = nimg * IPI;
+
+    float acc[9][NJ][4];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[t][j][q] = 0.0f;
+    float bsum0 = 0.0f, bsum1 = 0.0f;                        // bias partials of co = 16 ct + g, + 8
+
+    auto load = [&](int item, int buf) {
+        const int img = item / IPI, y0 = (item - img * IPI) * WG_ROWS;
+        const uint32_t ibase = umma::smem_addr(wsm + buf * W::STAGE);
+        for (int i = tid; i < (CIN / 8) * WG_HH * WG_HW; i += WG_THREADS) {
+            const int g = i / (WG_HH * WG_HW), rem = i - g * (WG_HH * WG_HW);
+            const int r = rem / WG_HW, c = rem - r * WG_HW;
+            const int y = y0 - 1 + r, x = c - 1;
+            const bool ok = y >= 0 && y < IMG && x >= 0 && x < IMG;
+            cp_async16(ibase + g * WG_IPLANE + rem * 16, ok ? in + act_at(img, y * IMG + x, 8 * g, CIN) : in,
+                       ok ? 16u : 0u);
+        }
+        const uint32_t obase = ibase + (CIN / 8) * WG_IPLANE;
+        for (int i = tid; i < (COUT / 8) * WG_ROWS * IMG; i += WG_THREADS) {
+            const int g = i / (WG_ROWS * IMG), pp = i - g * (WG_ROWS * IMG);
+            cp_async16(obase + g * WG_OPLANE + pp * 16, dout + act_at(img, y0 * IMG + pp, 8 * g, COUT), 16u);
+        }
+    };
+
+    int k = 0;
+    if ((int)blockIdx.x < nitems) load(blockIdx.x, 0);
+    cp_async_commit();
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
+        if (item + (int)gridDim.x < nitems) load(item + gridDim.x, (k + 1) & 1);
+        cp_async_commit();                                   // one group per iteration, possibly empty
+        cp_async_wait<1>();                                  // this item's tiles have landed
+        __syncthreads();
+        const uint32_t ib = umma::smem_addr(wsm + (k & 1) * W::STAGE);
+        const uint32_t ob = ib + (CIN / 8) * WG_IPLANE;
+#pragma unroll 1
+        for (int r = 0; r < WG_ROWS; ++r) {
+#pragma unroll
+            for (int x0 = 0; x0 < IMG; x0 += 16) {
+                // A: (co 0-7, px 0-7), (co 8-15, px 0-7), (co 0-7, px 8-15), (co 8-15, px 8-15)
+                uint32_t a[4];
+                ldsm_x4_t(ob + (2 * ct + (mat & 1)) * WG_OPLANE + (r * IMG + x0 + (mat >> 1) * 8 + row) * 16, a);
+                if (warp < CT) {
+                    bsum0 += bf16x2_sum(a[0]) + bf16x2_sum(a[2]);
+                    bsum1 += bf16x2_sum(a[1]) + bf16x2_sum(a[3]);
+                }
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const uint32_t prow = (uint32_t)(((r + dy) * WG_HW + x0 + dx) * 16);
+                    if constexpr (NJ == 1) {
+                        uint32_t b[2];    // (ci tile j0, px 0-7), (j0, px 8-15)
+                        ldsm_x2_t(ib + j0 * WG_IPLANE + prow + ((mat & 1) * 8 + row) * 16, b);
+                        mma_16816(acc[tap][0], a, b[0], b[1]);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < NJ; jj += 2) {
+                            uint32_t b[4];    // (j, px 0-7), (j, px 8-15), (j + 1, px 0-7), (j + 1, px 8-15)
+                            ldsm_x4_t(ib + (j0 + jj + (mat >> 1)) * WG_IPLANE + prow + ((mat & 1) * 8 + row) * 16, b);
+                            mma_16816(acc[tap][jj], a, b[0], b[1]);
+                            mma_16816(acc[tap][jj + 1], a, b[2], b[3]);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();                                     // buffer k & 1 is refilled next iteration
+    }
+    cp_async_wait<0>();
+    // partial [tap][co][ci] of this CTA; thread (g, t4) holds rows g, g + 8 and columns 2 t4, 2 t4 + 1 of each tile
+    const int g = lane >> 2, t4 = lane & 3;
+    float *dst = part + (int64_t)blockIdx.x * 9 * COUT * CIN;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj) {
+            const int co = ct * 16 + g, ci = (j0 + jj) * 8 + 2 * t4;
+            float *d0 = dst + ((int64_t)tap * COUT + co) * CIN + ci;
+            float *d1 = d0 + 8 * CIN;
+            d0[0] = acc[tap][jj][0];
+            d0[1] = acc[tap][jj][1];
+            d1[0] = acc[tap][jj][2];
+            d1[1] = acc[tap][jj][3];
+        }
+    if (warp < CT) {
+        bsum0 += __shfl_xor_sync(0xffffffffu, bsum0, 1);
+        bsum1 += __shfl_xor_sync(0xffffffffu, bsum1, 1);
+        bsum0 += __shfl_xor_sync(0xffffffffu, bsum0, 2);
+        bsum1 += __shfl_xor_sync(0xffffffffu, bsum1, 2);
+        if (t4 == 0) {
+            bpart[(int64_t)blockIdx.x * COUT + ct * 16 + g] = bsum0;
+            bpart[(int64_t)blockIdx.x * COUT + ct * 16 + g + 8] = bsum1;
+        }
+    }
+}
+
 // Fold the per-image partials in image order into the layer's gradient slots.
 __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float *part, const float *bpart, int B, int cout,
                                                           int cin, float *gw, float *gb)
@@ -476,17 +638,39 @@ cudaError_t conv_dgrad(int l, const ConvArgs &a, cudaStream_t st)
     }
 }
 
-cudaError_t wgrad(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part, float *bpart, int B,
-                  cudaStream_t st)
+template <int COUT, int CIN>
+static cudaError_t launch_wgrad_mma(const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part, float *bpart,
+                                    int B, int *nparts, cudaStream_t st)
 {
-    const dim3 grid(B * 9);
-    switch (l) {
-    case 0: wgrad_kernel<32, 16, 2><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
-    case 1: wgrad_kernel<32, 32, 32><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
-    case 2: wgrad_kernel<64, 32, 32><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
-    default: wgrad_kernel<64, 64, 64><<<grid, 256, 0, st>>>(in, dout, part, bpart); break;
+    using W = WgShape<COUT, CIN>;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const cudaError_t e = cudaFuncSetAttribute(wgrad_mma_kernel<COUT, CIN>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::SMEM);
+        if (e != cudaSuccess) return e;
+        sms = sm_count(dev);
     }
+    const int grid = B < sms ? B : sms;          // partial buffers hold B slices
+    wgrad_mma_kernel<COUT, CIN><<<grid, WG_THREADS, W::SMEM, st>>>(in, dout, B, part, bpart);
+    *nparts = grid;
     return cudaGetLastError();
+}
+
+// Weight and bias gradient partials of layer l; *nparts partials of [9][cout][cin] (+ [cout]) to fold.
+cudaError_t wgrad(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part, float *bpart, int B,
+                  int *nparts, cudaStream_t st)
+{
+    switch (l) {
+    case 0:
+        wgrad_kernel<32, 16, 2><<<dim3(B * 9), 256, 0, st>>>(in, dout, part, bpart);
+        *nparts = B;
+        return cudaGetLastError();
+    case 1: return launch_wgrad_mma<32, 32>(in, dout, part, bpart, B, nparts, st);
+    case 2: return launch_wgrad_mma<64, 32>(in, dout, part, bpart, B, nparts, st);
+    default: return launch_wgrad_mma<64, 64>(in, dout, part, bpart, B, nparts, st);
+    }
 }
 
 int nblk(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b)); }
@@ -619,10 +803,11 @@ static cudaError_t backward(lbm_surrogate *s, int m, int B, cudaStream_t st)
     count_launches(2);
     int cur = 0;
     for (int l = NLAYER - 1; l >= 0; --l) {
-        cudaError_t e = wgrad(l, s->act[l], s->dact[cur], s->part, s->bpart, B, st);
+        int nparts = 0;
+        cudaError_t e = wgrad(l, s->act[l], s->dact[cur], s->part, s->bpart, B, &nparts, st);
         if (e != cudaSuccess) return e;
         const int co = cout_of(l), ci = cin_real(l);
-        wgrad_reduce_kernel<<<nblk((int64_t)co * ci * 9 + co), 256, 0, st>>>(s->part, s->bpart, B, co, ci,
+        wgrad_reduce_kernel<<<nblk((int64_t)co * ci * 9 + co), 256, 0, st>>>(s->part, s->bpart, nparts, co, ci,
                                                                            G + LAYOUT.w[l], G + LAYOUT.b[l]);
         count_launches(2);
         if (l >= 1) {
