@@ -564,6 +564,8 @@ def main(argv=None):
                     help="run the whole upscaled method on an n^2 channelised field (e.g. 16384) and exit")
     ap.add_argument("--pipeline-steps", type=int, default=20000, help="fine steps of --pipeline")
     ap.add_argument("--pipeline-epochs", type=int, default=10, help="surrogate training epochs of --pipeline")
+    ap.add_argument("--pipeline-margins", default="0,4",
+                    help="oversampling margins of the local-LBM upscaling runs of --pipeline")
     args = ap.parse_args(argv)
     ws, rank, local = dist_init()
     if args.pipeline > 0:
@@ -583,8 +585,9 @@ def run_pipeline(args, local):
     """The whole upscaled method on an n^2 channelised field (default 16384^2, r = 16).
 
     Fine run (FP32, tau = 1, nu = nu_eff, eps = 1, G = (1e-6, 0)) for `steps` steps; K* of every r x r
-    block (Eq. 17) by local LBM alone and by the surrogate ensemble with local-LBM fallback (trained
-    on the r x r blocks of a 4096^2 channelised field of another seed); coarse runs (Eq. 18, tensor
+    block (Eq. 17) by the surrogate ensemble with local-LBM fallback (trained on the r x r blocks of
+    a 4096^2 channelised field of another seed) and by local LBM alone for each oversampling margin
+    of --pipeline-margins (0: the paper's plain local problems); coarse runs (Eq. 18, tensor
     K*, scaled parameters) for steps / r steps, the same physical time; relative L2 error of the
     coarse velocity against the r x r block average of the fine velocity. Prints one JSON line."""
     import torch
@@ -628,25 +631,28 @@ def run_pipeline(args, local):
                                  "epochs": args.pipeline_epochs}
     del ktr, ltr, x, stats, ke, st, y
     nb = n // r
-    keff = {k: torch.empty((nb, nb, 4), dtype=torch.float64, device="cuda") for k in ("lbm", "surrogate")}
-    (st_l, _), t_l = timed(lambda: lbm.lbm_upscale(p, kt, r, keff["lbm"], 1e-6, 1e-8, 200000))
+    margins = [int(v) for v in args.pipeline_margins.split(",")]
+    keff = {"surrogate": torch.empty((nb, nb, 4), dtype=torch.float64, device="cuda")}
     (st_s, nfb), t_s = timed(lambda: lbm.lbm_upscale(p, kt, r, keff["surrogate"], 1e-6, 1e-8, 200000,
                                                      surrogate=sur, spread_max=0.03))
     sur.close()
-    kl, ks = keff["lbm"], keff["surrogate"]
-    rel = torch.stack([(ks[..., 0] / kl[..., 0] - 1).abs(), (ks[..., 3] / kl[..., 3] - 1).abs()]).flatten()
-    rel = rel.cpu().numpy()
-    out["upscale"] = {
-        "blocks": nb * nb,
-        "lbm_seconds": t_l, "lbm_blocks_per_s": nb * nb / t_l, "lbm_status": st_l,
-        "surrogate_seconds": t_s, "surrogate_blocks_per_s": nb * nb / t_s, "surrogate_status": st_s,
-        "fallback_fraction": nfb / (nb * nb),
-        "kstar_rel_err_vs_lbm_median": float(np.median(rel)), "kstar_rel_err_vs_lbm_p99": float(np.percentile(rel, 99)),
-    }
+    out["upscale"] = {"blocks": nb * nb, "surrogate_seconds": t_s, "surrogate_blocks_per_s": nb * nb / t_s,
+                      "surrogate_status": st_s, "fallback_fraction": nfb / (nb * nb)}
+    for m in margins:
+        keff[f"lbm_m{m}"] = torch.empty((nb, nb, 4), dtype=torch.float64, device="cuda")
+        pm = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, gx=1e-6, gy=0.0, margin=m)
+        (st_l, _), t_l = timed(lambda: lbm.lbm_upscale(pm, kt, r, keff[f"lbm_m{m}"], 1e-6, 1e-8, 200000))
+        out["upscale"][f"lbm_margin{m}"] = {"seconds": t_l, "blocks_per_s": nb * nb / t_l, "status": st_l}
+    if 0 in margins:
+        kl, ks = keff["lbm_m0"], keff["surrogate"]
+        rel = torch.stack([(ks[..., 0] / kl[..., 0] - 1).abs(), (ks[..., 3] / kl[..., 3] - 1).abs()]).flatten()
+        rel = rel.cpu().numpy()
+        out["upscale"]["surrogate_kstar_rel_err_vs_lbm_median"] = float(np.median(rel))
+        out["upscale"]["surrogate_kstar_rel_err_vs_lbm_p99"] = float(np.percentile(rel, 99))
     pc = lbm.lbm_coarse_params(p, r)
     out["coarse_params"] = {"tau": pc.tau, "nu": pc.nu, "gx": pc.gx}
     den = float(torch.sqrt((ub.double() ** 2 + vb.double() ** 2).sum()))
-    for name in ("lbm", "surrogate"):
+    for name in keff:
         uc = torch.empty((nb, nb), dtype=torch.float32, device="cuda")
         vc, rc = torch.empty_like(uc), torch.empty_like(uc)
         (_, done), t = timed(lambda: lbm.lbm_coarse_run(p, r, keff[name], None, steps // r, 0.0, 64, rc, uc, vc))

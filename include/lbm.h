@@ -72,6 +72,13 @@ typedef struct {
                              1: Guo scheme (Section 2.1, Eqs. 1-6: u_eq = u and the
                              forcing term F_a of Eq. 4). With the linear equilibrium of
                              Eq. 2 both give the same update up to rounding.          */
+    int32_t margin;       /* local problems (lbm_local_keff_batch, lbm_upscale): oversampling
+                             margin m >= 0 in cells, the treatment the Conclusions name for
+                             channelised, high-contrast media. Each leaf's problem is solved
+                             on the leaf grown by m cells on every side (taken from the field
+                             with periodic wrap) with periodic closure, and the stop test and
+                             Eq. 17 average the inner leaf only. 0 is the plain local problem
+                             of Section 3. Ignored by the grid calls.                    */
 } lbm_params;
 
 /* Thread-local description of the last failure of any call in this thread. */
@@ -186,8 +193,9 @@ lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, con
  * lives in a static device array built into the library (1 MiB, held on every
  * GPU that loads it until the process exits). Differences from
  * lbm_local_keff_batch: always one persistent launch; at most 131072 leaves
- * per call (more gives LBM_EINVAL); leaves are validated on the device (a bad
- * leaf gives LBM_EINVAL before the solver starts). The first call on each
+ * per call (more gives LBM_EINVAL); p->margin must be 0 (plain local
+ * problems); leaves are validated on the device (a bad leaf gives LBM_EINVAL
+ * before the solver starts). The first call on each
  * device looks up the array's device address, so make it before any stream
  * capture. Every call reuses the same array (it is cleared at the start of each
  * call), so calls that overlap on the GPU (other streams or threads) race on

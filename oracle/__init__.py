@@ -72,6 +72,10 @@ def _L():
                                         C.c_double, C.c_double, C.c_long, C.c_int,
                                         dp, dp, C.POINTER(C.c_long)]
         _lib.orc_local_keff.restype = C.c_int
+        _lib.orc_local_keff_os.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_double, C.c_long, C.c_int,
+                                           dp, dp, C.POINTER(C.c_long)]
+        _lib.orc_local_keff_os.restype = C.c_int
         _lib.orc_run_mean_steady.argtypes = [C.POINTER(_Problem), dp, C.c_int, C.c_double, C.c_long,
                                              C.c_int, dp, C.POINTER(C.c_int)]
         _lib.orc_run_mean_steady.restype = C.c_long
@@ -165,19 +169,26 @@ def lattice():
     return np.array(list(e), dtype=np.int64).reshape(9, 2), w
 
 
-def local_keff(kappa_leaf, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64):
+def local_keff(kappa_leaf, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64, margin=0):
     """Local problems of Section 3 on one periodic square patch; Eq. 17.
 
+    margin > 0: the patch is the leaf with `margin` cells on every side (oversampling, the
+    treatment the Conclusions name for channelised media); the stop test and Eq. 17 use the
+    mean velocity over the inner leaf only (orc_local_keff_os).
     Returns dict(keff=[xx, xy, yx, yy], ubar=[u1x, u1y, u2x, u2y], steps=[s1, s2], converged=n).
     """
     k = np.ascontiguousarray(kappa_leaf, dtype=np.float64)
     s = k.shape[0]
-    assert k.shape == (s, s)
+    assert k.shape == (s, s) and 0 <= margin and s - 2 * margin >= 1
     keff = np.empty(4)
     ub = np.empty(4)
     st = (C.c_long * 2)()
-    nconv = _L().orc_local_keff(s, _dp(k), float(tau), float(nu), float(eps), float(g_const),
-                                float(tol), int(max_steps), int(check_every), _dp(keff), _dp(ub), st)
+    if margin == 0:
+        nconv = _L().orc_local_keff(s, _dp(k), float(tau), float(nu), float(eps), float(g_const),
+                                    float(tol), int(max_steps), int(check_every), _dp(keff), _dp(ub), st)
+    else:
+        nconv = _L().orc_local_keff_os(s, int(margin), _dp(k), float(tau), float(nu), float(eps), float(g_const),
+                                       float(tol), int(max_steps), int(check_every), _dp(keff), _dp(ub), st)
     return dict(keff=keff, ubar=ub, steps=[st[0], st[1]], converged=int(nconv))
 
 

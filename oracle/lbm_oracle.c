@@ -399,6 +399,76 @@ int orc_local_keff(int s, const double *kappa_leaf, double tau, double nu, doubl
     return nconv;
 }
 
+/*
+ * Oversampled local problem (the treatment named in the Conclusions for high-contrast,
+ * channelised media): the leaf's s x s block is embedded in an se x se patch
+ * (se = s + 2 margin, the block in the middle) which is solved with periodic closure
+ * exactly as in orc_local_keff; the stop test and Eq. 17 use the mean velocity over
+ * the inner s x s window only. margin = 0 is orc_local_keff.
+ */
+static void mean_velocity_window(const orc_problem *p, const double *f, int x0, int y0, int w, double out[2])
+{
+    double su = 0.0, sv = 0.0;
+    for (int y = y0; y < y0 + w; ++y)
+        for (int x = x0; x < x0 + w; ++x) {
+            long c = (long)y * p->nx + x;
+            double r, jx, jy, ux, uy;
+            cell_velocity(p, c, f + c * Q, &r, &jx, &jy, &ux, &uy);
+            su += ux;
+            sv += uy;
+        }
+    out[0] = su / ((double)w * w);
+    out[1] = sv / ((double)w * w);
+}
+
+int orc_local_keff_os(int se, int margin, const double *kappa_ext, double tau, double nu, double eps,
+                      double gconst, double tol, long max_steps, int check_every,
+                      double keff[4], double ubar[4], long steps[2])
+{
+    lattice_init();
+    const int s = se - 2 * margin;
+    if (margin < 0 || s < 1) return -1;
+    orc_problem p;
+    memset(&p, 0, sizeof p);
+    p.nx = se; p.ny = se; p.tau = tau; p.nu = nu; p.eps = eps;
+    p.walls = 0; p.kappa = kappa_ext;
+    long n = (long)se * se;
+    double *f = (double *)malloc(sizeof(double) * n * Q);
+    double *g = (double *)malloc(sizeof(double) * n * Q);
+    int nconv = 0;
+    for (int d = 0; d < 2; ++d) {
+        p.gx = d == 0 ? gconst : 0.0;
+        p.gy = d == 0 ? 0.0 : gconst;
+        orc_init_rest(&p, f);
+        double prev = 0.0, m[2];
+        long st = 0;
+        int conv = 0;
+        while (st < max_steps) {
+            orc_step(&p, f, g);
+            memcpy(f, g, sizeof(double) * n * Q);
+            ++st;
+            if (check_every > 0 && st % check_every == 0) {
+                mean_velocity_window(&p, f, margin, margin, s, m);
+                if (tol > 0.0 && st > check_every && fabs(m[d] - prev) <= tol * check_every * fabs(m[d])) {
+                    conv = 1;
+                    break;
+                }
+                prev = m[d];
+            }
+        }
+        mean_velocity_window(&p, f, margin, margin, s, ubar + 2 * d);
+        steps[d] = st;
+        nconv += conv;
+    }
+    keff[0] = nu / gconst * ubar[0];   /* Eq. 17 on the inner window, as in orc_local_keff */
+    keff[1] = nu / gconst * ubar[2];
+    keff[2] = nu / gconst * ubar[1];
+    keff[3] = nu / gconst * ubar[3];
+    free(f);
+    free(g);
+    return nconv;
+}
+
 /* Mean of a [ny][nx] field over r x r blocks -> [ny/r][nx/r] (fine-to-coarse comparison). */
 void orc_block_average(int nx, int ny, int r, const double *a, double *out)
 {

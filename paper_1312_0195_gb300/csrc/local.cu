@@ -56,6 +56,7 @@ constexpr size_t LOCAL_SMEM = LocalCfg<float>::SMEM;
 struct LocalArgs {
     const float *kappa;       // field [ny][nx]
     int nx, ny;
+    int margin;               // oversampling margin: a job's patch is its leaf grown by margin cells
     const int *leaves;        // [n][3] (x0, y0, size)
     const int *jobs;          // job = 2 * leaf + drive, grouped by size class
     int nclass;
@@ -211,8 +212,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 sl.job = a.jobs[qbeg + q];
                 sl.leaf = sl.job >> 1;
                 sl.drive = sl.job & 1;
-                sl.x0 = a.leaves[3 * sl.leaf];
-                sl.y0 = a.leaves[3 * sl.leaf + 1];
+                sl.x0 = a.leaves[3 * sl.leaf] - a.margin;
+                sl.y0 = a.leaves[3 * sl.leaf + 1] - a.margin;
                 sl.prev = 0.0;
             }
             slots[tid] = sl;
@@ -237,7 +238,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 // read for population a and cell x + e_a written, so each index serves both
                 int n1 = 0, n2 = 0, n3 = 0, n4 = 0, n5 = 0, n6 = 0, n7 = 0, n8 = 0;
                 if (t == 0) {
-                    const int gx = slots[j].x0 + clx, gy = slots[j].y0 + cly;
+                    // patch origin may lie outside the field when oversampling: periodic wrap
+                    int gx = slots[j].x0 + clx, gy = slots[j].y0 + cly;
+                    gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
+                    gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
                     D[c] = (T)coef_e(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
 #pragma unroll
                     for (int q = 0; q < Q; ++q) g[q] = T(0);      // rest state
@@ -300,17 +304,23 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     int st = -1;   // -1: keep going
                     double ux = 0.0, uy = 0.0;
                     if (check) {
+                        // mean over the leaf: all s2 cells, or the inner window when oversampling
+                        const int m = a.margin, hi = s - m;
                         for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
-                            ux += (double)UX[c];
-                            uy += (double)UY[c];
+                            const int loc = c - j * s2, ly = loc / s, lx = loc - ly * s;
+                            if (m == 0 || (lx >= m && lx < hi && ly >= m && ly < hi)) {
+                                ux += (double)UX[c];
+                                uy += (double)UY[c];
+                            }
                         }
 #pragma unroll
                         for (int off = 16; off > 0; off >>= 1) {
                             ux += __shfl_xor_sync(0xffffffffu, ux, off);
                             uy += __shfl_xor_sync(0xffffffffu, uy, off);
                         }
-                        ux /= (double)s2;
-                        uy /= (double)s2;
+                        const double inner = (double)(s - 2 * a.margin) * (double)(s - 2 * a.margin);
+                        ux /= inner;
+                        uy /= inner;
                         const double cur = sl.drive == 0 ? ux : uy;
                         const bool regular = t == h.y;
                         if (regular) h.y += a.check_every;
@@ -340,8 +350,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                                 sl.job = a.jobs[qbeg + q];
                                 sl.leaf = sl.job >> 1;
                                 sl.drive = sl.job & 1;
-                                sl.x0 = a.leaves[3 * sl.leaf];
-                                sl.y0 = a.leaves[3 * sl.leaf + 1];
+                                sl.x0 = a.leaves[3 * sl.leaf] - a.margin;
+                                sl.y0 = a.leaves[3 * sl.leaf + 1] - a.margin;
                                 sl.prev = 0.0;
                                 h = make_int4((int)(Tcta + 1u), a.check_every, 1 | (sl.drive << 1), 0);
                             } else {
@@ -413,15 +423,19 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     std::vector<lbm_leaf> lv(n_leaves);
     LOC_CUDA(cudaMemcpyAsync(lv.data(), leaves_dev, sizeof(lbm_leaf) * n_leaves, cudaMemcpyDeviceToHost, st));
     LOC_CUDA(cudaStreamSynchronize(st));
+    const int m = p->margin;
+    if (m < 0 || m > 32 || m >= p->nx || m >= p->ny)
+        return fail(LBM_EINVAL, "margin %d outside [0, 32] or not below the field size", m);
     std::vector<int> sizes;
     for (int i = 0; i < n_leaves; ++i) {
         const lbm_leaf &L = lv[i];
         const int smax = p->storage == LBM_F64 ? 45 : 64;   // FP64 leaves hold 2048 cells per CTA
-        if (L.size < 1 || L.size > smax) return fail(LBM_EINVAL, "leaf %d: size %d outside [1, %d]", i, L.size, smax);
+        if (L.size < 1 || L.size + 2 * m > smax)
+            return fail(LBM_EINVAL, "leaf %d: size %d (+ 2 x margin %d) outside [1, %d]", i, L.size, m, smax);
         if (L.x0 < 0 || L.y0 < 0 || (int64_t)L.x0 + L.size > p->nx || (int64_t)L.y0 + L.size > p->ny)
             return fail(LBM_EINVAL, "leaf %d (%d, %d, %d) lies outside the %d x %d field", i, L.x0, L.y0, L.size,
                         p->nx, p->ny);
-        sizes.push_back(L.size);
+        sizes.push_back(L.size + 2 * m);
     }
     std::sort(sizes.begin(), sizes.end(), std::greater<int>());
     sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
@@ -432,6 +446,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.kappa = kappa_dev;
     a.nx = p->nx;
     a.ny = p->ny;
+    a.margin = m;
     a.leaves = reinterpret_cast<const int *>(leaves_dev);
     a.omega = (1.0 / p->tau);
     a.two_tau = (2.0 * p->tau);
@@ -457,7 +472,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
         for (int s : sizes) {
             off.push_back((int)jobs.size());
             for (int i = 0; i < n_leaves; ++i)
-                if (lv[i].size == s) {
+                if (lv[i].size + 2 * m == s) {
                     jobs.push_back(2 * i);
                     jobs.push_back(2 * i + 1);
                 }
@@ -525,7 +540,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
         for (int i = 0; i < n_leaves; ++i) {
             a.class_off[0] = 2 * i;
             a.class_off[1] = 2 * i + 2;
-            a.class_size[0] = lv[i].size;
+            a.class_size[0] = lv[i].size + 2 * m;
             a.heads = d_heads + i;
             kern<<<1, LOCAL_THREADS, smem, st>>>(a);
             LOC_CUDA2(cudaGetLastError());
@@ -667,6 +682,7 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     if (!std::isfinite(p->nu) || !std::isfinite(p->eps) || p->eps < 0.0)
         return fail(LBM_EINVAL, "nu must be finite and eps finite and >= 0");
     if (n_leaves < 0) return fail(LBM_EINVAL, "n_leaves must be >= 0");
+    if (p->margin != 0) return fail(LBM_EINVAL, "the allocation-free entry point solves plain local problems (margin 0)");
     if (n_leaves > NOALLOC_MAX_LEAVES)
         return fail(LBM_EINVAL, "n_leaves %d exceeds the %d leaves the static scratch holds", n_leaves,
                     NOALLOC_MAX_LEAVES);
@@ -730,6 +746,7 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     a.kappa = kappa_dev;
     a.nx = p->nx;
     a.ny = p->ny;
+    a.margin = 0;
     a.leaves = lv;
     a.jobs = scr + NA_JOBS;
     a.nclass = head[NA_TABLE];

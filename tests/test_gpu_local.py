@@ -183,3 +183,57 @@ def test_invalid_leaves_rejected():
         with pytest.raises(lbm.LbmError) as ei:
             lbm.local_keff(p, kap, lt)
         assert ei.value.status == lbm.LBM_EINVAL
+
+
+# ------------------------------------------------- oversampled local problems (Conclusions)
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_oversampled_leaves_match_oracle(storage):
+    """margin > 0: each leaf's problem is solved on the leaf grown by `margin` cells (periodic wrap
+    at the field edge) and K* averages the inner leaf. Leaves at the field corners exercise the
+    wrap; fixed step counts make the comparison step for step."""
+    import torch
+    lbm = _lbm()
+    kap = synth.lognormal_kappa(48, 40, 4.0, 1.5, seed=41).astype(np.float32)
+    leaves = np.array([[0, 0, 8], [40, 32, 8], [16, 8, 16], [4, 24, 12], [32, 0, 8]], dtype=np.int32)
+    for margin in (3, 8):
+        p = lbm.Params(nx=48, ny=40, tau=1.0, nu=1.0 / 6.0, eps=1.0, storage=storage, margin=margin)
+        ke, st, steps, _ = lbm.local_keff(p, torch.from_numpy(kap).cuda(), torch.from_numpy(leaves).cuda(), 1e-6,
+                                          0.0, 1500, 64)
+        ke = ke.cpu().numpy()
+        for i, (x0, y0, s) in enumerate(leaves):
+            ext = synth.crop_periodic(kap, x0 - margin, y0 - margin, s + 2 * margin, s + 2 * margin)
+            ref = oracle.local_keff(ext.astype(np.float64), 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=0.0, max_steps=1500,
+                                    margin=margin)["keff"]
+            scale = max(abs(ref[0]), abs(ref[3]))
+            tol = 1e-9 if storage == 2 else 2e-5
+            np.testing.assert_allclose(ke[i], ref, rtol=0, atol=tol * scale)
+
+
+def test_oversampling_inner_window_on_parallel_layers():
+    """The GPU counterpart of the oracle pin: parallel layers at tau = 1/2 with margin columns of
+    a third permeability; the oversampled K*_yy is the mean over the inner leaf's columns."""
+    import torch
+    lbm = _lbm()
+    ex = synth.paper_experiment("E3", ratio=10.0, ny=1)
+    k1, k2 = float(ex["kappa"][0, 0]), float(ex["kappa"][0, 10])
+    cols = np.array([5.0 * k2] * 10 + [k1] * 10 + [k2] * 10 + [5.0 * k2] * 10, dtype=np.float32)
+    kap = np.tile(cols, (40, 1))
+    p = lbm.Params(nx=40, ny=40, tau=ex["tau"], nu=ex["nu"], eps=ex["eps"], storage=lbm.LBM_F64, margin=10)
+    lt = torch.tensor([[10, 10, 20]], dtype=torch.int32, device="cuda")
+    ke, st, _, _ = lbm.local_keff(p, torch.from_numpy(kap).cuda(), lt, 1e-6, 1e-11, 20000, 64)
+    kyy = float(ke[0, 3])
+    inner = 0.5 * (float(np.float32(k1)) + float(np.float32(k2)))
+    assert abs(kyy - inner) <= 2e-6 * inner
+
+
+def test_oversampling_limits_are_rejected():
+    import torch
+    lbm = _lbm()
+    kap = torch.full((64, 64), 0.01, device="cuda")
+    lt = torch.tensor([[0, 0, 64]], dtype=torch.int32, device="cuda")
+    for margin in (-1, 33):
+        with pytest.raises(lbm.LbmError):
+            lbm.local_keff(lbm.Params(nx=64, ny=64, tau=1.0, margin=margin), kap, lt)
+    with pytest.raises(lbm.LbmError):          # 64 + 2 x 1 cells do not fit the resident patch
+        lbm.local_keff(lbm.Params(nx=64, ny=64, tau=1.0, margin=1), kap, lt)

@@ -440,3 +440,39 @@ def test_block_average_matches_reshape_mean():
     a = RNG.standard_normal((40, 60))
     np.testing.assert_allclose(oracle.block_average(a, 10), a.reshape(4, 10, 6, 10).mean(axis=(1, 3)),
                                rtol=1e-14, atol=1e-15)
+
+
+# ------------------------------------------------- oversampled local problems (Conclusions)
+
+def test_oversampling_of_a_periodic_block_is_the_plain_local_problem():
+    """A block embedded in copies of itself (margin = one block) evolves cell for cell like the
+    periodic block alone, so the inner-window K* equals the plain local K* exactly."""
+    blk = synth.lognormal_kappa(10, 10, 2.0, 1.0, seed=31)
+    plain = oracle.local_keff(blk, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-9, max_steps=100000)
+    os_ = oracle.local_keff(np.tile(blk, (3, 3)), 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-9, max_steps=100000, margin=10)
+    assert plain["steps"] == os_["steps"]
+    np.testing.assert_array_equal(plain["keff"], os_["keff"])
+
+
+def test_oversampling_averages_the_inner_window_only():
+    """Parallel layers at tau = 1/2 (Darcy, Table 2 setting): K*_yy is the arithmetic mean of
+    kappa over the columns averaged. With margin columns of a third permeability, the
+    oversampled K*_yy is the mean over the inner leaf's columns, not over the whole patch."""
+    ex = synth.paper_experiment("E3", ratio=10.0, ny=1)
+    k1, k2 = float(ex["kappa"][0, 0]), float(ex["kappa"][0, 10])
+    k3 = 5.0 * k2
+    cols = np.array([k3] * 10 + [k1] * 10 + [k2] * 10 + [k3] * 10)
+    patch = np.tile(cols, (40, 1))
+    r = oracle.local_keff(patch, ex["tau"], ex["nu"], ex["eps"], 1e-6, tol=1e-11, max_steps=20000, margin=10)
+    kyy_inner = 0.5 * (k1 + k2)
+    assert abs(r["keff"][3] - kyy_inner) <= 2e-6 * kyy_inner
+    full = oracle.local_keff(patch, ex["tau"], ex["nu"], ex["eps"], 1e-6, tol=1e-11, max_steps=20000)
+    assert abs(full["keff"][3] - cols.mean()) <= 2e-6 * cols.mean()
+    assert abs(full["keff"][3] - r["keff"][3]) > 0.5 * kyy_inner
+
+
+def test_oversampling_uniform_patch_gives_kappa():
+    """Eq. 19 with any margin: a uniform patch gives K* = kappa I."""
+    r = oracle.local_keff(np.full((18, 18), 3e-3), 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-12, max_steps=100000, margin=5)
+    np.testing.assert_allclose(r["keff"][[0, 3]], 3e-3, rtol=1e-9)
+    assert abs(r["keff"][1]) < 1e-15 and abs(r["keff"][2]) < 1e-15
