@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lbm3d_oracle.c")]
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 
 Q = 9
@@ -36,10 +37,10 @@ def build(force: bool = False) -> str:
     alt = os.environ.get("LBM_ORACLE_LIB")
     if alt:
         return alt
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -81,11 +82,72 @@ def _L():
         _lib.orc_run_mean_steady.restype = C.c_long
         _lib.orc_block_average.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
         _lib.orc_lattice.argtypes = [C.POINTER(C.c_int), dp]
+        _lib.orc3_lattice.argtypes = [C.POINTER(C.c_int), dp]
+        _lib.orc3_init_rest.argtypes = [C.POINTER(_Problem3), dp]
+        _lib.orc3_step.argtypes = [C.POINTER(_Problem3), dp, dp]
+        _lib.orc3_run.argtypes = [C.POINTER(_Problem3), dp, C.c_long]
+        _lib.orc3_fields.argtypes = [C.POINTER(_Problem3), dp, dp, dp, dp, dp]
+        _lib.orc3_mean_velocity.argtypes = [C.POINTER(_Problem3), dp, dp]
     return _lib
 
 
 def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _Problem3(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
+                ("gx", C.c_double), ("gy", C.c_double), ("gz", C.c_double),
+                ("kappa", C.c_void_p)]
+
+
+Q3 = 19
+
+
+def lattice3():
+    """D3Q19 velocities [19, 3] and weights [19] as the oracle builds them."""
+    e = (C.c_int * (Q3 * 3))()
+    w = np.empty(Q3)
+    _L().orc3_lattice(e, _dp(w))
+    return np.array(list(e), dtype=np.int64).reshape(Q3, 3), w
+
+
+class Problem3D:
+    """A periodic D3Q19 problem (Section 2's scheme in three dimensions): ``kappa`` [nz, ny, nx]
+    (may contain +inf or 0), constant body force ``g`` = (gx, gy, gz)."""
+
+    def __init__(self, tau, nu, eps=1.0, kappa=None, g=(0.0, 0.0, 0.0)):
+        self.kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        self.nz, self.ny, self.nx = (int(v) for v in self.kappa.shape)
+        self._s = _Problem3(self.nx, self.ny, self.nz, float(tau), float(nu), float(eps),
+                            float(g[0]), float(g[1]), float(g[2]), self.kappa.ctypes.data)
+
+    def rest(self) -> np.ndarray:
+        f = np.empty((self.nz, self.ny, self.nx, Q3))
+        _L().orc3_init_rest(C.byref(self._s), _dp(f))
+        return f
+
+    def step(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.empty_like(f)
+        _L().orc3_step(C.byref(self._s), _dp(f), _dp(out))
+        return out
+
+    def run(self, f: np.ndarray, steps: int) -> None:
+        assert f.flags.c_contiguous and f.dtype == np.float64
+        _L().orc3_run(C.byref(self._s), _dp(f), int(steps))
+
+    def fields(self, f: np.ndarray):
+        """(rho, u, v, w) of every cell, each [nz, ny, nx]."""
+        out = [np.empty((self.nz, self.ny, self.nx)) for _ in range(4)]
+        _L().orc3_fields(C.byref(self._s), _dp(f), *(_dp(o) for o in out))
+        return tuple(out)
+
+    def mean_velocity(self, f: np.ndarray) -> np.ndarray:
+        m = np.empty(3)
+        _L().orc3_mean_velocity(C.byref(self._s), _dp(f), _dp(m))
+        return m
 
 
 class Problem:

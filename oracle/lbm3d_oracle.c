@@ -1,0 +1,161 @@
+/*
+ * lbm3d_oracle.c -- FP64 CPU oracle of the D3Q19 form of the method.
+ *
+ * TEST INFRASTRUCTURE ONLY, like lbm_oracle.c: plain loops restating what the
+ * method computes, loaded only by the tests, the package smoke check and the
+ * benchmark's CPU baseline; it shares nothing with the CUDA path.
+ *
+ * Section 2 states the scheme on D2Q9 and notes that it carries over to three
+ * dimensions unchanged. The three-dimensional lattice used here is D3Q19: the
+ * rest velocity, the 6 face neighbours and the 12 edge neighbours of the cubic
+ * lattice, with weights 1/3, 1/18 and 1/36 and c_s^2 = 1/3 (the weights are the
+ * unique ones for these shells with sum w = 1, sum w e e = c_s^2 I and an
+ * isotropic fourth moment). The update is the one of Section 2.2 with vectors of
+ * three components:
+ *     rho = sum_a f_a, j = sum_a e_a f_a
+ *     u    = (j + eps rho G / 2) / (rho (1 + eps nu / (2 kappa)))          Eq. 6
+ *     u_eq = 2 tau u + (1 - 2 tau) j / rho                                  Eq. 16
+ *     f_eq = w rho (1 + e.u_eq / c_s^2)                                     Eq. 2
+ *     f(x + e, t + 1) = f + (f_eq - f) / tau                                Eq. 13
+ * Periodic in x, y and z; rest initial state (f = w rho0, rho0 = 1).
+ * Layout: f[((z * ny + y) * nx + x) * 19 + a].
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q3 19
+
+typedef struct {
+    int nx, ny, nz;
+    double tau, nu, eps;
+    double gx, gy, gz;        /* constant body force */
+    const double *kappa;      /* [nz][ny][nx] permeability (may be +inf) */
+} orc3_problem;
+
+static int E3[Q3][3];
+static double W3[Q3];
+static int ready3 = 0;
+
+/* The 19 vectors of {-1, 0, 1}^3 with at most two non-zero components, weighted by shell. */
+static void lattice3_init(void)
+{
+    if (ready3) return;
+    int a = 0;
+    for (int shell = 0; shell <= 2; ++shell)
+        for (int z = -1; z <= 1; ++z)
+            for (int y = -1; y <= 1; ++y)
+                for (int x = -1; x <= 1; ++x)
+                    if (x * x + y * y + z * z == shell) {
+                        E3[a][0] = x; E3[a][1] = y; E3[a][2] = z;
+                        W3[a] = shell == 0 ? 1.0 / 3.0 : (shell == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+                        ++a;
+                    }
+    ready3 = 1;
+}
+
+void orc3_lattice(int *e_out /* [19][3] */, double *w_out /* [19] */)
+{
+    lattice3_init();
+    for (int a = 0; a < Q3; ++a) {
+        for (int k = 0; k < 3; ++k) e_out[3 * a + k] = E3[a][k];
+        w_out[a] = W3[a];
+    }
+}
+
+/* Eq. 6 for one cell: rho, j and the flow velocity u (Eq. 15). */
+static void cell3(const orc3_problem *p, long c, const double *fc, double *rho_o, double j[3], double u[3])
+{
+    double rho = 0.0;
+    j[0] = j[1] = j[2] = 0.0;
+    for (int a = 0; a < Q3; ++a) {
+        rho += fc[a];
+        for (int k = 0; k < 3; ++k) j[k] += E3[a][k] * fc[a];
+    }
+    const double G[3] = {p->gx, p->gy, p->gz};
+    double drag = 0.0;                           /* eps nu / (2 kappa) */
+    if (p->eps != 0.0 && p->nu != 0.0) {
+        const double k = p->kappa[c];
+        drag = isinf(k) ? 0.0 : (k == 0.0 ? INFINITY : p->eps * p->nu / (2.0 * k));
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double r = j[k] + 0.5 * p->eps * rho * G[k];
+        u[k] = isinf(drag) ? 0.0 : r / (rho * (1.0 + drag));
+    }
+    *rho_o = rho;
+}
+
+void orc3_init_rest(const orc3_problem *p, double *f)
+{
+    lattice3_init();
+    const long n = (long)p->nx * p->ny * p->nz;
+    for (long c = 0; c < n; ++c)
+        for (int a = 0; a < Q3; ++a) f[c * Q3 + a] = W3[a];
+}
+
+/* One step f -> out: collide every cell (Eqs. 6, 16, 2, 13), then stream along e_a
+ * with periodic wrap. The stored state is the streamed, pre-collision one, as in
+ * the two-dimensional oracle. */
+void orc3_step(const orc3_problem *p, const double *f, double *out)
+{
+    lattice3_init();
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const double tau = p->tau;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const long c = ((long)z * ny + y) * nx + x;
+                const double *fc = f + c * Q3;
+                double rho, j[3], u[3];
+                cell3(p, c, fc, &rho, j, u);
+                double ueq[3];
+                for (int k = 0; k < 3; ++k) ueq[k] = 2.0 * tau * u[k] + (1.0 - 2.0 * tau) * j[k] / rho;
+                for (int a = 0; a < Q3; ++a) {
+                    const double eu = E3[a][0] * ueq[0] + E3[a][1] * ueq[1] + E3[a][2] * ueq[2];
+                    const double feq = W3[a] * rho * (1.0 + 3.0 * eu);
+                    const int xd = (x + E3[a][0] + nx) % nx, yd = (y + E3[a][1] + ny) % ny,
+                              zd = (z + E3[a][2] + nz) % nz;
+                    out[(((long)zd * ny + yd) * nx + xd) * Q3 + a] = fc[a] + (feq - fc[a]) / tau;
+                }
+            }
+}
+
+void orc3_run(const orc3_problem *p, double *f, long steps)
+{
+    const long n = (long)p->nx * p->ny * p->nz;
+    double *g = (double *)malloc(sizeof(double) * n * Q3);
+    for (long s = 0; s < steps; ++s) {
+        orc3_step(p, f, g);
+        memcpy(f, g, sizeof(double) * n * Q3);
+    }
+    free(g);
+}
+
+/* Density and flow velocity (Eq. 15) of every cell; any output may be NULL. */
+void orc3_fields(const orc3_problem *p, const double *f, double *rho, double *u, double *v, double *w)
+{
+    lattice3_init();
+    const long n = (long)p->nx * p->ny * p->nz;
+    for (long c = 0; c < n; ++c) {
+        double r, j[3], uc[3];
+        cell3(p, c, f + c * Q3, &r, j, uc);
+        if (rho) rho[c] = r;
+        if (u) u[c] = uc[0];
+        if (v) v[c] = uc[1];
+        if (w) w[c] = uc[2];
+    }
+}
+
+/* Volume average of the flow velocity (arithmetic mean over cells). */
+void orc3_mean_velocity(const orc3_problem *p, const double *f, double out[3])
+{
+    lattice3_init();
+    const long n = (long)p->nx * p->ny * p->nz;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long c = 0; c < n; ++c) {
+        double r, j[3], uc[3];
+        cell3(p, c, f + c * Q3, &r, j, uc);
+        for (int k = 0; k < 3; ++k) s[k] += uc[k];
+    }
+    for (int k = 0; k < 3; ++k) out[k] = s[k] / n;
+}

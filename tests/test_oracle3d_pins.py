@@ -1,0 +1,123 @@
+"""Pins of the D3Q19 oracle (Section 2's scheme in three dimensions) against what the lattice and
+the mathematics fix: the lattice moments, the exact reduction to the (already pinned) D2Q9
+oracle for fields invariant along any one axis, the uniform fixed point (Eq. 19), the uniform
+transient, and mass conservation."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def test_d3q19_lattice_moments():
+    e, w = oracle.lattice3()
+    assert len({tuple(v) for v in e}) == 19 and (np.abs(e).sum(axis=1) <= 2).all()
+    assert {tuple(v) for v in e} == {tuple(-v) for v in e}
+    assert abs(w.sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(w @ e, 0.0, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("a,ai,aj->ij", w, e, e), np.eye(3) / 3.0, atol=1e-16)
+    d = np.eye(3)
+    iso = (np.einsum("ij,kl->ijkl", d, d) + np.einsum("ik,jl->ijkl", d, d) + np.einsum("il,jk->ijkl", d, d)) / 9.0
+    np.testing.assert_allclose(np.einsum("a,ai,aj,ak,al->ijkl", w, e, e, e, e), iso, atol=1e-16)
+
+
+def _run2d(k2, tau, nu, eps, g2, steps):
+    p = oracle.Problem(tau, nu, eps, kappa=k2, g=g2)
+    f = p.rest()
+    p.run(f, steps)
+    return p.fields(f)
+
+
+def _run3d(k3, tau, nu, eps, g3, steps):
+    p = oracle.Problem3D(tau, nu, eps, kappa=k3, g=g3)
+    f = p.rest()
+    p.run(f, steps)
+    return p.fields(f)
+
+
+@pytest.mark.parametrize("axis", ["z", "x", "y"])
+def test_field_invariant_along_an_axis_reduces_to_d2q9(axis):
+    """Summed over e along the invariant axis, the D3Q19 weights are the D2Q9 weights (4/9, 1/9,
+    1/36), the equilibrium is linear in e . u and streaming along that axis moves nothing, so a
+    field invariant along one axis, with no force along it, evolves like the D2Q9 problem on the
+    other two axes: same rho and in-plane velocity, zero velocity along the axis."""
+    k2 = synth.lognormal_kappa(12, 9, 2.5, 1.5, seed=51)          # [9][12]: 2-D (y, x)
+    tau, nu, eps, steps = 0.8, 0.1, 0.9, 150
+    g2 = (2e-6, -1.3e-6)
+    r2, u2, v2 = _run2d(k2, tau, nu, eps, g2, steps)
+    n = 3
+    if axis == "z":       # 3-D (x, y) = 2-D (x, y)
+        k3 = np.broadcast_to(k2[None, :, :], (n, 9, 12))
+        r3, a3, b3, c3 = _run3d(k3, tau, nu, eps, (g2[0], g2[1], 0.0), steps)
+        r3, a3, b3, c3 = (t[1] for t in (r3, a3, b3, c3))
+    elif axis == "x":     # 3-D (y, z) = 2-D (x, y): kappa[z][y][x] = k2[z][y]
+        k3 = np.broadcast_to(k2[:, :, None], (9, 12, n))
+        r3, c3, a3, b3 = _run3d(k3, tau, nu, eps, (0.0, g2[0], g2[1]), steps)
+        r3, a3, b3, c3 = (t[:, :, 1] for t in (r3, a3, b3, c3))
+    else:                 # 3-D (x, z) = 2-D (x, y): kappa[z][y][x] = k2[z][x]
+        k3 = np.broadcast_to(k2[:, None, :], (9, n, 12))
+        r3, a3, c3, b3 = _run3d(k3, tau, nu, eps, (g2[0], 0.0, g2[1]), steps)
+        r3, a3, b3, c3 = (t[:, 1, :] for t in (r3, a3, b3, c3))
+    # both oracles store full f (~0.05 per population) while u ~ 1e-7: velocities agree to the
+    # cancellation floor, ~1e-16 absolute (1e-9 of the velocity scale); a wrong weight, velocity or
+    # stream direction shows up at order one
+    scale = max(np.abs(u2).max(), np.abs(v2).max())
+    np.testing.assert_allclose(r3, r2, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(a3, u2, rtol=0, atol=2e-9 * scale)
+    np.testing.assert_allclose(b3, v2, rtol=0, atol=2e-9 * scale)
+    assert np.abs(c3).max() <= 2e-9 * scale
+
+
+def test_uniform_fixed_point_eq19_in_3d():
+    """Eq. 19 in three dimensions: with uniform kappa, f_a = w_a rho0 (1 + 3 e_a . kappa G / nu)
+    is a fixed point of the step."""
+    e, w = oracle.lattice3()
+    kap, nu, eps, tau = 3e-3, 0.05, 0.8, 0.7
+    G = np.array([1e-6, -2e-6, 0.5e-6])
+    p = oracle.Problem3D(tau, nu, eps, kappa=np.full((4, 3, 5), kap), g=G)
+    u = kap * G / nu
+    f = np.broadcast_to(w * (1.0 + 3.0 * (e @ u)), (4, 3, 5, 19)).copy()
+    np.testing.assert_allclose(p.step(f), f, rtol=0, atol=1e-16)
+    _, uu, vv, ww = p.fields(f)
+    # j ~ 1e-7 is a sum of populations ~0.05 (the oracle stores full f): ~1e-15 absolute
+    np.testing.assert_allclose([uu.mean(), vv.mean(), ww.mean()], u, rtol=0, atol=1e-14)
+
+
+def test_uniform_transient_closed_form_in_3d():
+    """Uniform state from rest: j' = (2 d - 1) j + d eps rho G with d = 1 / (1 + eps nu / (2 kappa))
+    (any lattice; only the moments enter), and u = d (j + eps rho G / 2) / rho."""
+    kap, nu, eps, tau = 2e-2, 0.1, 0.9, 0.6
+    G = np.array([3e-6, 1e-6, -2e-6])
+    p = oracle.Problem3D(tau, nu, eps, kappa=np.full((2, 3, 4), kap), g=G)
+    f = p.rest()
+    d = 1.0 / (1.0 + eps * nu / (2.0 * kap))
+    j = np.zeros(3)
+    for n in range(1, 40):
+        f = p.step(f)
+        j = (2 * d - 1) * j + d * eps * G
+        _, uu, vv, ww = p.fields(f)
+        np.testing.assert_allclose([uu[0, 0, 0], vv[0, 0, 0], ww[0, 0, 0]], d * (j + 0.5 * eps * G),
+                                   rtol=0, atol=1e-15)         # cancellation in j, as above
+
+
+def test_mass_conservation_and_symmetry_in_3d():
+    rng = np.random.default_rng(52)
+    kap = np.exp(rng.normal(-4.0, 1.5, (5, 6, 7)))
+    kap[1, 2, 3] = 0.0
+    kap[3, 1, 4] = np.inf
+    p = oracle.Problem3D(0.9, 0.1, 0.8, kappa=kap, g=(1e-6, 2e-6, -1e-6))
+    f = p.rest()
+    p.run(f, 120)
+    rho, u, v, w = p.fields(f)
+    assert abs(rho.sum() - rho.size) <= 1e-12 * rho.size
+    assert u[1, 2, 3] == 0.0 and v[1, 2, 3] == 0.0 and w[1, 2, 3] == 0.0   # blocked cell
+    # mirror z -> -z (with gz -> -gz) mirrors the flow
+    pm = oracle.Problem3D(0.9, 0.1, 0.8, kappa=kap[::-1].copy(), g=(1e-6, 2e-6, 1e-6))
+    fm = pm.rest()
+    pm.run(fm, 120)
+    _, um, vm, wm = pm.fields(fm)
+    s = np.abs(u).max()
+    np.testing.assert_allclose(um[::-1], u, atol=1e-12 * s)
+    np.testing.assert_allclose(wm[::-1], -w, atol=1e-12 * s)

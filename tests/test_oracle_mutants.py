@@ -3,7 +3,8 @@
 Each mutant is the oracle source with one textual change (a dropped 1/2, a sign
 in Eq. 16, a wrong velocity component in Eq. 17, a wrong bounce-back direction,
 a wrong lattice weight, streaming against e_a), compiled to a temporary library
-and run against a fast subset of ``test_oracle_pins.py`` in a subprocess. The
+and run against a fast subset of ``test_oracle_pins.py`` in a subprocess (the
+D3Q19 mutants against ``test_oracle3d_pins.py``). The
 subset must FAIL for every mutant. Mistakes are only ever planted on the CPU,
 in the oracle.
 """
@@ -16,6 +17,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lbm_oracle.c")
+SRC3 = os.path.join(ROOT, "oracle", "lbm3d_oracle.c")
 
 FAST_PINS = ("lattice_moments or eq19 or transient_closed_form or mass_conservation or "
              "magic_tau or hydrostatic or uniform_patch or symmetries or (table1 and 10-) or flux_conservation")
@@ -34,30 +36,62 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
-    src = open(SRC).read()
-    for old, new in MUTANTS[name]:
+# mistakes in the D3Q19 oracle, run against its own pins
+MUTANTS3 = {
+    "d3q19_edge_weight": [("(shell == 1 ? 1.0 / 18.0 : 1.0 / 36.0)", "(shell == 1 ? 1.0 / 18.0 : 1.0 / 18.0)")],
+    "d3q19_stream_against_e": [("const int xd = (x + E3[a][0] + nx) % nx, yd = (y + E3[a][1] + ny) % ny,",
+                                "const int xd = (x - E3[a][0] + nx) % nx, yd = (y - E3[a][1] + ny) % ny,")],
+    "d3q19_eq16_sign": [("(1.0 - 2.0 * tau) * j[k] / rho", "(1.0 + 2.0 * tau) * j[k] / rho")],
+    "d3q19_force_half_dropped": [("j[k] + 0.5 * p->eps * rho * G[k]", "j[k] + 1.0 * p->eps * rho * G[k]")],
+}
+
+
+def _build(tmp_path, src2, src3, name):
+    c2, c3 = tmp_path / f"{name}.c", tmp_path / f"{name}3d.c"
+    c2.write_text(src2)
+    c3.write_text(src3)
+    so = tmp_path / f"lib{name}.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", str(so), str(c2), str(c3), "-lm"])
+    return so
+
+
+def _pins(so, pins_file, expr, stop_first=True):
+    env = dict(os.environ, LBM_ORACLE_LIB=str(so))
+    args = [sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", os.path.join(ROOT, "tests", pins_file)]
+    if stop_first:
+        args.insert(4, "-x")
+    if expr:
+        args += ["-k", expr]
+    return subprocess.run(args, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def _mutate(src, changes):
+    for old, new in changes:
         assert old in src, f"mutation anchor not found: {old!r}"
         src = src.replace(old, new)
-    c = tmp_path / "mutant.c"
-    c.write_text(src)
-    so = tmp_path / "libmutant.so"
-    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", str(so), str(c), "-lm"])
-    env = dict(os.environ, LBM_ORACLE_LIB=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", FAST_PINS],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return src
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    so = _build(tmp_path, _mutate(open(SRC).read(), MUTANTS[name]), open(SRC3).read(), "mutant")
+    r = _pins(so, "test_oracle_pins.py", FAST_PINS)
+    assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS3))
+def test_3d_pins_catch_mutant(name, tmp_path):
+    so = _build(tmp_path, open(SRC).read(), _mutate(open(SRC3).read(), MUTANTS3[name]), "mutant")
+    r = _pins(so, "test_oracle3d_pins.py", None)
     assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
 
 
 def test_unmutated_copy_passes(tmp_path):
     """The same harness with no mutation passes (so failures above come from the mutations)."""
-    so = tmp_path / "libsame.so"
-    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", str(so), SRC, "-lm"])
-    env = dict(os.environ, LBM_ORACLE_LIB=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", FAST_PINS],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    so = _build(tmp_path, open(SRC).read(), open(SRC3).read(), "same")
+    r = _pins(so, "test_oracle_pins.py", FAST_PINS, stop_first=False)
+    assert r.returncode == 0, r.stdout[-3000:]
+    r = _pins(so, "test_oracle3d_pins.py", None, stop_first=False)
     assert r.returncode == 0, r.stdout[-3000:]
