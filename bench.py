@@ -205,6 +205,29 @@ def measure_variants(lbm, torch, kap, stream, steps=300):
     return out
 
 
+def measure_d3q19(lbm, torch, n=256, steps=200):
+    """The scheme on the D3Q19 lattice (Section 2 in three dimensions): n^3 periodic box,
+    log-normal K (sigma 2, ell 8, seed 7), tau = 0.6, nu = nu_eff, G = (1e-6, 0, 0); MLUPS and the
+    fraction of the measured HBM bandwidth at 19 x 2 x 4 + 4 = 156 B/LUP (FP32), 308 B/LUP (FP64)."""
+    import synth
+    kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
+    peaks = measured_peaks()
+    out = {"workload": f"D3Q19 {n}^3 periodic, log-normal K (sigma 2, ell 8, seed 7), tau 0.6, nu = nu_eff, "
+                       "G = (1e-6, 0, 0)"}
+    for name, st, bpl, k in (("f32", lbm.LBM_F32, 156, steps), ("f64", lbm.LBM_F64, 308, steps // 4)):
+        p = lbm.Params3D(nx=n, ny=n, nz=n, tau=TAU, nu=NU, eps=1.0, gx=1e-6, storage=st)
+        with lbm.Grid3D(p, kap) as g:
+            g.step(10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.step(k)
+            torch.cuda.synchronize()
+            t = (time.perf_counter() - t0) / k
+        out[name] = {"mlups": n ** 3 / t / 1e6, "bytes_per_lup": bpl,
+                     "hbm_frac": bpl * n ** 3 / t / 1e9 / peaks["hbm_gbs"]}
+    return out
+
+
 def _oracle_leaf(args):
     """One local problem by the FP64 oracle (process-pool worker)."""
     import oracle
@@ -504,9 +527,10 @@ def run_ours(args, ws, rank, local):
            "steps": e2e_steps}
 
     variants = {}
-    local = surrogate = None
+    local = surrogate = d3 = None
     if not args.no_extras:
         variants = measure_variants(lbm, torch, kap, stream)
+        d3 = measure_d3q19(lbm, torch)
         local = measure_local_keff(lbm, torch, kap, ws, rank)
         if not args.no_surrogate:
             surrogate = measure_surrogate(lbm, torch)
@@ -538,6 +562,8 @@ def run_ours(args, ws, rank, local):
             line["local_keff"] = local
         if surrogate:
             line["surrogate"] = surrogate
+        if d3:
+            line["d3q19"] = d3
         print(json.dumps(line), flush=True)
     return 0
 
@@ -558,6 +584,8 @@ def main(argv=None):
                     help="profiling mode: create the grid, run this many plain lattice steps, exit")
     ap.add_argument("--profile-local", type=int, default=0,
                     help="profiling mode: this many quadtree leaves of the 4096^2 field, 2000 fixed steps, exit")
+    ap.add_argument("--profile-3d", type=int, default=0,
+                    help="profiling mode: this many cells per side of a D3Q19 box, 8 steps, exit")
     ap.add_argument("--profile-surrogate", type=int, default=0,
                     help="profiling mode: ensemble inference on this many 32x32 patches, exit")
     ap.add_argument("--pipeline", type=int, default=0,
@@ -578,6 +606,8 @@ def main(argv=None):
         return run_profile_local(args, local)
     if args.profile_surrogate > 0:
         return run_profile_surrogate(args, local)
+    if args.profile_3d > 0:
+        return run_profile_3d(args, local)
     return run_ours(args, ws, rank, local)
 
 
@@ -672,6 +702,20 @@ def run_profile_local(args, local):
     leaves_np = synth.quadtree_leaves(N, N, seed=3)[: args.profile_local]
     p = lbm.Params(nx=N, ny=N, tau=1.0, eps=1.0)
     lbm.local_keff(p, kap, torch.from_numpy(leaves_np).cuda(), 1e-6, 0.0, 2000, 64, True)
+    torch.cuda.synchronize()
+    return 0
+
+
+def run_profile_3d(args, local):
+    """Fixed launch sequence for ncu: one D3Q19 box of profile_3d^3 cells, 8 FP32 steps."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    import synth
+    torch.cuda.set_device(local)
+    n = args.profile_3d
+    kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
+    with lbm.Grid3D(lbm.Params3D(nx=n, ny=n, nz=n, tau=TAU, nu=NU, eps=1.0, gx=1e-6), kap) as g:
+        g.step(8)
     torch.cuda.synchronize()
     return 0
 

@@ -311,6 +311,34 @@ lbm_status lbm_coarse_run(const lbm_params *fine_p, int32_t block, const double 
 lbm_status lbm_block_average(const float *in_dev, int32_t nx, int32_t ny, int32_t block, float *out_dev,
                              void *cuda_stream);
 
+/* ------------------------------------------------------ 3-D grids (D3Q19) ---
+ * Section 2 uses the D3Q19 lattice for three-dimensional problems with the
+ * algorithms unchanged. These calls step the scheme on it (rest, 6 face and 12 edge velocities,
+ * weights 1/3, 1/18, 1/36, c_s^2 = 1/3) with the same update as the 2-D grid
+ * (Eqs. 6, 16, 2, 13 with three-component vectors), periodic in x, y and z,
+ * constant body force, scalar permeability, from rest. Arrays are [nz][ny][nx]
+ * (x fastest), caller-owned device memory. */
+typedef struct {
+    int32_t nx, ny, nz;   /* lattice size, each >= 1; ny, nz <= 65535                   */
+    double  tau, nu, eps; /* as in lbm_params (nu < 0 selects nu_eff)                  */
+    double  gx, gy, gz;   /* constant body force                                        */
+    int32_t storage;      /* LBM_F32 or LBM_F64 deviation storage                      */
+} lbm3d_params;
+typedef struct lbm3d_grid lbm3d_grid;
+
+/* Creates a 3-D grid: two distribution buffers of 19 planes of the storage type
+ * and the per-cell drag fraction; kappa_dev float [nz][ny][nx] is read during the
+ * call only (>= 0, +inf allowed; NaN or negative give LBM_EINVAL). */
+lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void *cuda_stream, lbm3d_grid **out);
+lbm_status lbm3d_grid_destroy(lbm3d_grid *g);
+/* Advances the grid by `steps` time steps (fused pull-stream + collide). */
+lbm_status lbm3d_step(lbm3d_grid *g, int64_t steps);
+/* Density and flow velocity (Eq. 15) into caller-owned float [nz][ny][nx] device
+ * arrays; any of the four may be NULL. */
+lbm_status lbm3d_get_fields(lbm3d_grid *g, float *rho_dev, float *u_dev, float *v_dev, float *w_dev);
+/* Volume average of the flow velocity, FP64 in a fixed order; HOST out[3]. */
+lbm_status lbm3d_mean_velocity(lbm3d_grid *g, double out_mean_uvw[3]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,12 +5,12 @@
  * method computes, loaded only by the tests, the package smoke check and the
  * benchmark's CPU baseline; it shares nothing with the CUDA path.
  *
- * Section 2 states the scheme on D2Q9 and notes that it carries over to three
- * dimensions unchanged. The three-dimensional lattice used here is D3Q19: the
- * rest velocity, the 6 face neighbours and the 12 edge neighbours of the cubic
- * lattice, with weights 1/3, 1/18 and 1/36 and c_s^2 = 1/3 (the weights are the
- * unique ones for these shells with sum w = 1, sum w e e = c_s^2 I and an
- * isotropic fourth moment). The update is the one of Section 2.2 with vectors of
+ * Section 2 uses D3Q19 for three-dimensional problems with the algorithms
+ * unchanged, without listing its velocities and weights. They are taken here as
+ * the rest velocity, the 6 face neighbours and the 12 edge neighbours of the
+ * cubic lattice, with weights 1/3, 1/18 and 1/36 and c_s^2 = 1/3 (the unique
+ * weights for these shells with sum w = 1, sum w e e = c_s^2 I and an isotropic
+ * fourth moment). The update is the one of Section 2.2 with vectors of
  * three components:
  *     rho = sum_a f_a, j = sum_a e_a f_a
  *     u    = (j + eps rho G / 2) / (rho (1 + eps nu / (2 kappa)))          Eq. 6

@@ -354,3 +354,87 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- D3Q19 grids
+
+@dataclass
+class Params3D:
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    nu: float = -1.0
+    eps: float = 1.0
+    gx: float = 0.0
+    gy: float = 0.0
+    gz: float = 0.0
+    storage: int = LBM_F32
+
+    def c(self) -> _abi.lbm3d_params:
+        return _abi.lbm3d_params(int(self.nx), int(self.ny), int(self.nz), float(self.tau), float(self.nu),
+                                 float(self.eps), float(self.gx), float(self.gy), float(self.gz), int(self.storage))
+
+
+def lbm3d_grid_create(params: Params3D, kappa, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    p = params.c()
+    _check(_abi.lib().lbm3d_grid_create(C.byref(p), _ptr(kappa), _stream(stream), C.byref(h)))
+    return h
+
+
+def lbm3d_grid_destroy(grid) -> None:
+    _check(_abi.lib().lbm3d_grid_destroy(grid))
+
+
+def lbm3d_step(grid, steps: int) -> None:
+    _check(_abi.lib().lbm3d_step(grid, int(steps)))
+
+
+def lbm3d_get_fields(grid, rho=None, u=None, v=None, w=None) -> None:
+    _check(_abi.lib().lbm3d_get_fields(grid, _ptr(rho), _ptr(u), _ptr(v), _ptr(w)))
+
+
+def lbm3d_mean_velocity(grid):
+    out = (C.c_double * 3)()
+    _check(_abi.lib().lbm3d_mean_velocity(grid, out))
+    return tuple(out)
+
+
+class Grid3D:
+    """Owning wrapper of a D3Q19 grid: ``Grid3D(params3d, kappa_cuda_f32 [nz, ny, nx])``."""
+
+    def __init__(self, params: Params3D, kappa, stream=None):
+        self.params = params
+        self.handle = lbm3d_grid_create(params, kappa, stream)
+
+    def step(self, steps: int) -> None:
+        lbm3d_step(self.handle, steps)
+
+    def fields(self):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        shape = (self.params.nz, self.params.ny, self.params.nx)
+        out = [torch.empty(shape, dtype=torch.float32, device=dev) for _ in range(4)]
+        lbm3d_get_fields(self.handle, *out)
+        return tuple(out)
+
+    def mean_velocity(self):
+        return lbm3d_mean_velocity(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lbm3d_grid_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -28,6 +28,13 @@ class lbm_params(C.Structure):
                 ("scale", C.c_double), ("force_model", C.c_int32), ("margin", C.c_int32)]
 
 
+class lbm3d_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
+                ("gx", C.c_double), ("gy", C.c_double), ("gz", C.c_double),
+                ("storage", C.c_int32)]
+
+
 class lbm_leaf(C.Structure):
     _fields_ = [("x0", C.c_int32), ("y0", C.c_int32), ("size", C.c_int32)]
 
@@ -57,6 +64,11 @@ SIGNATURES = {
     "lbm_local_keff_batch_noalloc": (C.c_int, [_PP, _P, _P, _I32, _D, _D, _I64, _I32, _P, _P, _P, _P]),
     "lbm_upscale": (C.c_int, [_PP, _P, _I32, _P, _D, _D, _D, _I64, _P, C.POINTER(_I32), _P]),
     "lbm_coarse_params": (C.c_int, [_PP, _I32, _PP]),
+    "lbm3d_grid_create": (C.c_int, [C.POINTER(lbm3d_params), _P, _P, C.POINTER(_P)]),
+    "lbm3d_grid_destroy": (C.c_int, [_P]),
+    "lbm3d_step": (C.c_int, [_P, _I64]),
+    "lbm3d_get_fields": (C.c_int, [_P, _P, _P, _P, _P]),
+    "lbm3d_mean_velocity": (C.c_int, [_P, C.POINTER(_D)]),
     "lbm_coarse_run": (C.c_int, [_PP, _I32, _P, _P, _I64, _D, _I32, _P, _P, _P, C.POINTER(_I64), _P]),
     "lbm_block_average": (C.c_int, [_P, _I32, _I32, _I32, _P, _P]),
     "lbm_surrogate_param_count": (_I64, []),

@@ -9,6 +9,7 @@ inputs from here, so the two implementations always see identical inputs.
 from .fields import (  # noqa: F401
     gaussian_random_field,
     lognormal_kappa,
+    lognormal_kappa3d,
     quadtree_leaves,
     uniform_leaves,
     channel_kappa,

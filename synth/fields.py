@@ -50,6 +50,24 @@ def lognormal_kappa(nx: int, ny: int, ell: float, sigma: float, seed: int,
     return k0 * np.exp(sigma * gaussian_random_field(nx, ny, ell, seed))
 
 
+def lognormal_kappa3d(nx: int, ny: int, nz: int, ell: float, sigma: float, seed: int,
+                      k0: float = 1e-2) -> np.ndarray:
+    """Three-dimensional log-normal permeability ``[nz, ny, nx]`` (float32): the recipe of
+    ``gaussian_random_field`` (white noise from PCG64(seed), spectral filter of
+    ``exp(-r^2 / (2 ell^2))``, standardised) on a periodic box, then ``k0 exp(sigma Z)``."""
+    rng = _rng(seed)
+    white = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    k2 = (2.0 * np.pi * np.fft.fftfreq(nz))[:, None, None] ** 2 + \
+        (2.0 * np.pi * np.fft.fftfreq(ny))[None, :, None] ** 2 + \
+        (2.0 * np.pi * np.fft.rfftfreq(nx))[None, None, :] ** 2
+    z = np.fft.irfftn(np.fft.rfftn(white) * np.sqrt(np.exp(-0.5 * ell * ell * k2)), s=(nz, ny, nx))
+    z -= z.mean()
+    sd = z.std()
+    if sd == 0.0:
+        raise ValueError("degenerate random field (zero variance)")
+    return (k0 * np.exp(sigma * z / sd)).astype(np.float32)
+
+
 def quadtree_leaves(nx: int, ny: int, seed: int, root: int = 64, min_size: int = 8,
                     p_split: float = 0.6) -> np.ndarray:
     """Seeded quadtree over ``root``-sized tiles; returns int32 ``[n, 3]`` of (x0, y0, size).

@@ -1,4 +1,4 @@
-"""Pins of the D3Q19 oracle (Section 2's scheme in three dimensions) against what the lattice and
+"""Pins of the D3Q19 oracle (Section 2's scheme on the D3Q19 lattice) against what the lattice and
 the mathematics fix: the lattice moments, the exact reduction to the (already pinned) D2Q9
 oracle for fields invariant along any one axis, the uniform fixed point (Eq. 19), the uniform
 transient, and mass conservation."""
