@@ -351,17 +351,17 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, s
         kt, lt = torch.from_numpy(kap).cuda(), torch.from_numpy(leaves).cuda()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ke, st, _, _ = lbm.local_keff(p, kt, lt, 1e-6, 1e-8, 200000, 64, True)
+        ke, st, steps, _ = lbm.local_keff(p, kt, lt, 1e-6, 1e-8, 200000, 64, True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         x, stats = lbm.lbm_patches(kt, lt)
         y = torch.log(torch.stack([ke[:, 0], ke[:, 3]], dim=1)).float()
-        return kt, lt, p, x, stats, y, st, dt
+        return kt, lt, p, x, stats, y, st, dt, steps.cpu().numpy().astype(np.float64)
 
     ktr, ltr = _surrogate_set(train_fields, 10)
     kte, lte = _surrogate_set(test_fields, 1000)
-    _, _, _, xtr, str_, ytr, sttr, _ = label(ktr, ltr)
-    kt, lt, p, xte, ste, yte, stte, t_lbm = label(kte, lte)
+    _, _, _, xtr, str_, ytr, sttr, _, _ = label(ktr, ltr)
+    kt, lt, p, xte, ste, yte, stte, t_lbm, steps_te = label(kte, lte)
     ok = sttr == 0
     sur = lbm.Surrogate(4, 3)
     torch.cuda.synchronize()
@@ -401,6 +401,29 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, s
     rel_acc = rel[acc].flatten().cpu().numpy()
     rel_all = rel[good].flatten().cpu().numpy()
     flops = 4 * 2 * 1024 * 9 * (2 * 32 + 32 * 32 + 32 * 64 + 3 * 64 * 64)      # ensemble, per patch
+    # the tighter gate (spread <= 2 %) on the same predictions, with its own LBM fallback
+    sd = pred.std(dim=0).max(dim=1).values
+    accept2 = accept & (sd <= float(np.log1p(0.02)))
+    rej2 = torch.nonzero(~accept2).flatten()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if rej2.numel():
+        lbm.local_keff(p, kt, lt[rej2].contiguous(), 1e-6, 1e-8, 200000, 64, True)
+    torch.cuda.synchronize()
+    t_fb2 = time.perf_counter() - t0
+    acc2 = (accept2 & good)
+    rel_acc2 = rel[acc2].flatten().cpu().numpy()
+    # where the LBM time goes, by leaf size (cost = cells x steps of both drives)
+    sz = lte[:, 2]
+    cost = sz.astype(np.float64) ** 2 * steps_te.sum(axis=1)
+    acc_np, rel_np, good_np = acc.cpu().numpy(), rel.max(dim=1).values.cpu().numpy(), good.cpu().numpy()
+    by_size = {}
+    for size in (8, 16, 32, 64):
+        sel = sz == size
+        if sel.any():
+            by_size[str(size)] = {"leaves": int(sel.sum()), "lbm_cost_share": float(cost[sel].sum() / cost.sum()),
+                                  "accepted": float(acc_np[sel].mean()),
+                                  "median_rel_err": float(np.median(rel_np[sel & good_np]))}
     sur.close()
     return {
         "workload": f"{train_fields} training / {test_fields} held-out 256^2 log-normal fields (sigma U[0.5,3], "
@@ -416,6 +439,11 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, s
         "accepted_rel_err_p99": float(np.percentile(rel_acc, 99)) if rel_acc.size else None,
         "all_rel_err_median": float(np.median(rel_all)), "all_rel_err_p99": float(np.percentile(rel_all, 99)),
         "inference_tflops": flops * n / t_inf / 1e12,
+        "gate_2pct": {"accepted_fraction": float(acc2.float().mean()),
+                      "accepted_rel_err_median": float(np.median(rel_acc2)) if rel_acc2.size else None,
+                      "accepted_rel_err_p99": float(np.percentile(rel_acc2, 99)) if rel_acc2.size else None,
+                      "end_to_end_patches_per_s": n / (t_inf + t_fb2)},
+        "by_leaf_size": by_size,
     }
 
 
