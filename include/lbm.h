@@ -214,7 +214,7 @@ lbm_status lbm_set_time_limit(double seconds);
  * A learned shortcut for the local problems, not part of the paper (which
  * obtains every K* by local LBM, Section 3): an ensemble of small CNNs maps a
  * subdomain's permeability patch to (log K*_xx, log K*_yy); local LBM stays the
- * fallback for doubtful patches and the judge of the surrogate's error.
+ * fallback for doubtful patches and the arbiter of the surrogate's error.
  * Network per model: six 3x3 'same' convolutions 2 -> 32 -> 32 -> 64 -> 64 ->
  * 64 -> 64 with ReLU, global average pooling, a 64 -> 2 linear head; BF16
  * activations and weights on the tensor cores with FP32 accumulation, FP32

@@ -2,7 +2,7 @@
 
 The surrogate is an addition to the paper's method (the paper obtains every K*
 from local LBM runs, Section 3). It maps a subdomain's permeability patch to
-log K*_xx and log K*_yy; local LBM stays its fallback and the judge of its error.
+log K*_xx and log K*_yy; local LBM stays its fallback and the arbiter of its error.
 This module restates what the library's kernels compute, plainly and in FP64,
 so they can be checked: direct 3x3 'same' convolutions (one matmul per tap),
 ReLU, global average pooling, a linear head, the backward pass of all of it,

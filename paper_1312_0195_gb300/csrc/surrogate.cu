@@ -1,7 +1,7 @@
 // surrogate.cu -- the learned K* surrogate: patches, forward, backward, Adam,
 // training loop, ensemble inference and the gate that sends doubtful patches
 // back to local LBM. (An addition to the paper's method, which computes every
-// K* by local LBM, Section 3; local LBM here stays the fallback and the judge.)
+// K* by local LBM, Section 3; local LBM here stays the fallback and the arbiter.)
 #include "lbm_internal.h"
 #include "surrogate_kernels.cuh"
 

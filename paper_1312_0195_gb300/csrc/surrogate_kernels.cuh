@@ -1,7 +1,7 @@
 // surrogate_kernels.cuh -- kernels of the learned K* surrogate (an addition to
 // the paper's method: the paper gets every K* from local LBM, Section 3; here a
 // small CNN predicts log K*_xx and log K*_yy from the subdomain's permeability
-// patch and local LBM remains the fallback and the judge of its error).
+// patch and local LBM remains the fallback and the arbiter of its error).
 //
 // Network: six 3x3 'same' convolutions 2(->16 padded) -> 32 -> 32 -> 64 -> 64 ->
 // 64 -> 64 with ReLU, global average pooling over the 32 x 32 patch, a linear

@@ -2,7 +2,7 @@
 and the paper's own K* values reproduced by the GPU solver.
 
 The GPU solver stores FP32 deviations and reduces the means in FP64; the bar is
-1e-4 relative on K* (spec tolerance). Off-diagonal entries are compared
+1e-4 relative on K*, the FP32 accuracy bar of the path. Off-diagonal entries are compared
 relative to sqrt(K*_xx K*_yy), the scale of the tensor.
 """
 

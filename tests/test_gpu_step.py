@@ -1,7 +1,7 @@
 """GPU parity of the fused step (liblbm.so through the C ABI) against the FP64 oracle.
 
-Tolerances. The spec bar is 1e-4 relative L2 on steady velocity for the
-FP32 path. Element-wise checks early in a run use |gpu - oracle| <= 1e-5 max|u|:
+Tolerances. The FP32 path must reach 1e-4 relative L2 on steady velocity.
+Element-wise checks early in a run use |gpu - oracle| <= 1e-5 max|u|:
 FP32 deviation storage rounds each population to ~6e-8 of its own size and a
 cell's velocity sums nine of them, so a few hundred steps stay far below that.
 FP64 storage must agree to ~1e-11 (only summation order differs). FP16 storage
