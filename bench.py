@@ -226,6 +226,78 @@ def measure_storage_error(lbm, torch, kap_np, crop=512, steps=1000):
     return out
 
 
+def measure_d3q19(lbm, torch, n=256, steps=200):
+    """The scheme on the D3Q19 lattice (Section 2 in three dimensions): n^3 periodic box,
+    log-normal K (sigma 2, ell 8, seed 7), tau = 0.6, nu = nu_eff, G = (1e-6, 0, 0); MLUPS and the
+    fraction of the measured HBM bandwidth at 19 x 2 x 4 + 4 = 156 B/LUP (FP32), 308 B/LUP (FP64)."""
+    import synth
+    kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
+    peaks = measured_peaks()
+    out = {"workload": f"D3Q19 {n}^3 periodic, log-normal K (sigma 2, ell 8, seed 7), tau 0.6, nu = nu_eff, "
+                       "G = (1e-6, 0, 0)"}
+    for name, st, bpl, k in (("f32", lbm.LBM_F32, 156, steps), ("f64", lbm.LBM_F64, 308, steps // 4)):
+        p = lbm.Params3D(nx=n, ny=n, nz=n, tau=TAU, nu=NU, eps=1.0, gx=1e-6, storage=st)
+        with lbm.Grid3D(p, kap) as g:
+            g.step(10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.step(k)
+            torch.cuda.synchronize()
+            t = (time.perf_counter() - t0) / k
+        out[name] = {"mlups": n ** 3 / t / 1e6, "bytes_per_lup": bpl,
+                     "hbm_frac": bpl * n ** 3 / t / 1e9 / peaks["hbm_gbs"]}
+    return out
+
+
+def _oracle_leaf(args):
+    """One local problem by the FP64 oracle (process-pool worker)."""
+    import oracle
+    patch, tol = args
+    oracle.local_keff(patch, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=tol, max_steps=200000)
+    return 0
+
+
+def _oracle_forward(args):
+    """Ensemble forward of one patch by the FP64 surrogate oracle (process-pool worker)."""
+    from oracle import surrogate as osur
+    x, n_models = args
+    for m in range(n_models):
+        osur.forward(osur.init_params(m), x[None])
+    return 0
+
+
+def measure_cpu_oracles(kap_np, leaf_sample=64, patch_sample=32, seed=12):
+    """Oracle rates for the two other units of the metric, on the host cores (a spawn-started
+    process pool, one process per core, each running the oracle as it stands):
+    local K* (both drives, tol 1e-8) on a seeded sample of the quadtree leaves of the bench
+    field, and the 4-model surrogate forward on a seeded sample of their patches."""
+    import multiprocessing as mp
+    import synth
+    from oracle import surrogate as osur
+    leaves = synth.quadtree_leaves(N, N, seed=3)
+    rng = np.random.default_rng(seed)
+    pick = leaves[rng.choice(len(leaves), leaf_sample, replace=False)]
+    patches = [np.array(kap_np[y:y + s, x:x + s], dtype=np.float64) for x, y, s in pick]
+    xs = [osur.make_input(osur.resample_patch(np.log(p)), p.shape[0], 0.0, 1.0) for p in patches[:patch_sample]]
+    workers = os.cpu_count() or 1
+    out = {}
+    with mp.get_context("spawn").Pool(workers) as pool:
+        pool.map(_oracle_leaf, [(patches[0], 1e-8)] * workers)          # start-up outside the timing
+        t0 = time.perf_counter()
+        pool.map(_oracle_leaf, [(p, 1e-8) for p in patches], chunksize=1)
+        dt = time.perf_counter() - t0
+        out["local_keff"] = {"value": leaf_sample / dt, "unit": "patches/s", "cores": workers, "kind": "oracle",
+                             "sample": f"{leaf_sample} seeded quadtree leaves of the bench field, tol 1e-8 "
+                                       f"({dt:.1f} s)"}
+        t0 = time.perf_counter()
+        pool.map(_oracle_forward, [(x, 4) for x in xs], chunksize=1)
+        dt = time.perf_counter() - t0
+        out["surrogate_forward"] = {"value": len(xs) / dt, "unit": "patches/s", "cores": workers,
+                                    "kind": "oracle",
+                                    "sample": f"4-model FP64 forward of {len(xs)} of those leaves' patches ({dt:.1f} s)"}
+    return out
+
+
 def measure_local_keff(lbm, torch, kap, ws, rank=0, sample=512, seed=11):
     """Batched local problems on the 4096^2 field cut by the seeded quadtree (seed 3, ~71.6k
     leaves): one persistent launch for all leaves, tol 1e-8 on the per-drive mean flux,
