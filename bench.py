@@ -635,6 +635,8 @@ def main(argv=None):
                     help="profiling mode: create the grid, run this many plain lattice steps, exit")
     ap.add_argument("--profile-local", type=int, default=0,
                     help="profiling mode: this many quadtree leaves of the 4096^2 field, 2000 fixed steps, exit")
+    ap.add_argument("--profile-train", type=int, default=0,
+                    help="profiling mode: one surrogate training step (one model) on this many patches, exit")
     ap.add_argument("--profile-3d", type=int, default=0,
                     help="profiling mode: this many cells per side of a D3Q19 box, 8 steps, exit")
     ap.add_argument("--profile-surrogate", type=int, default=0,
@@ -659,6 +661,8 @@ def main(argv=None):
         return run_profile_surrogate(args, local)
     if args.profile_3d > 0:
         return run_profile_3d(args, local)
+    if args.profile_train > 0:
+        return run_profile_train(args, local)
     return run_ours(args, ws, rank, local)
 
 
@@ -753,6 +757,24 @@ def run_profile_local(args, local):
     leaves_np = synth.quadtree_leaves(N, N, seed=3)[: args.profile_local]
     p = lbm.Params(nx=N, ny=N, tau=1.0, eps=1.0)
     lbm.local_keff(p, kap, torch.from_numpy(leaves_np).cuda(), 1e-6, 0.0, 2000, 64, True)
+    torch.cuda.synchronize()
+    return 0
+
+
+def run_profile_train(args, local):
+    """Fixed launch sequence for ncu: one training step of one model (forward, backward, Adam) on the
+    patches of the first quadtree leaves of the bench field, with seeded targets."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    import synth
+    torch.cuda.set_device(local)
+    n = args.profile_train
+    kap = torch.from_numpy(make_kappa()).cuda()
+    leaves = torch.from_numpy(synth.quadtree_leaves(N, N, seed=3)[:n]).cuda()
+    x, stats = lbm.lbm_patches(kap, leaves)
+    y = torch.from_numpy(np.random.default_rng(5).normal(-4.0, 1.0, (n, 2)).astype(np.float32)).cuda()
+    with lbm.Surrogate(1, 0) as sur:
+        sur.train(x, y, stats, epochs=1, batch=n, lr=1e-3, seed=0)
     torch.cuda.synchronize()
     return 0
 
