@@ -358,7 +358,7 @@ def _surrogate_set(nfields, seed0, side=256):
     return np.concatenate(ks, axis=0), np.concatenate(leaves, axis=0)
 
 
-def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, spread_max=0.03):
+def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=20, spread_max=0.03):
     """The learned K* surrogate against the batched local LBM on held-out patches.
 
     Labels: local LBM (FP32, tau = 1, G = 1e-6, tol 1e-8, persistent launch). The ensemble of
@@ -422,18 +422,25 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, s
     rel_acc = rel[acc].flatten().cpu().numpy()
     rel_all = rel[good].flatten().cpu().numpy()
     flops = 4 * 2 * 1024 * 9 * (2 * 32 + 32 * 32 + 32 * 64 + 3 * 64 * 64)      # ensemble, per patch
-    # the tighter gate (spread <= 2 %) on the same predictions, with its own LBM fallback
+    # tighter gates on the same predictions, each with its own LBM fallback
     sd = pred.std(dim=0).max(dim=1).values
-    accept2 = accept & (sd <= float(np.log1p(0.02)))
-    rej2 = torch.nonzero(~accept2).flatten()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    if rej2.numel():
-        lbm.local_keff(p, kt, lt[rej2].contiguous(), 1e-6, 1e-8, 200000, 64, True)
-    torch.cuda.synchronize()
-    t_fb2 = time.perf_counter() - t0
-    acc2 = (accept2 & good)
-    rel_acc2 = rel[acc2].flatten().cpu().numpy()
+    tighter = {}
+    for thr in (0.01, 0.02):
+        acc_t = accept & (sd <= float(np.log1p(thr)))
+        rej_t = torch.nonzero(~acc_t).flatten()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if rej_t.numel():
+            lbm.local_keff(p, kt, lt[rej_t].contiguous(), 1e-6, 1e-8, 200000, 64, True)
+        torch.cuda.synchronize()
+        t_fb_t = time.perf_counter() - t0
+        rel_t = rel[acc_t & good].flatten().cpu().numpy()
+        tighter[f"gate_{int(round(thr * 100))}pct"] = {
+            "accepted_fraction": float((acc_t & good).float().mean()),
+            "accepted_rel_err_median": float(np.median(rel_t)) if rel_t.size else None,
+            "accepted_rel_err_p99": float(np.percentile(rel_t, 99)) if rel_t.size else None,
+            "end_to_end_patches_per_s": n / (t_inf + t_fb_t),
+            "speedup_end_to_end": (n / (t_inf + t_fb_t)) / (n / t_lbm)}
     # where the LBM time goes, by leaf size (cost = cells x steps of both drives)
     sz = lte[:, 2]
     cost = sz.astype(np.float64) ** 2 * steps_te.sum(axis=1)
@@ -449,6 +456,7 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, s
     return {
         "workload": f"{train_fields} training / {test_fields} held-out 256^2 log-normal fields (sigma U[0.5,3], "
                     "ell U[2,16]), quadtree leaves 8-64, labels by local LBM tol 1e-8; ensemble of 4, "
+                    "target (log K* - c) / w on the layered-medium bounds (mode 2), "
                     f"gate: spread <= {spread_max:.0%} and statistics in the training range",
         "train_patches": int(ok.sum()), "test_patches": n, "epochs": epochs, "train_seconds": t_train,
         "lbm_patches_per_s": n / t_lbm,
@@ -460,10 +468,7 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=10, s
         "accepted_rel_err_p99": float(np.percentile(rel_acc, 99)) if rel_acc.size else None,
         "all_rel_err_median": float(np.median(rel_all)), "all_rel_err_p99": float(np.percentile(rel_all, 99)),
         "inference_tflops": flops * n / t_inf / 1e12,
-        "gate_2pct": {"accepted_fraction": float(acc2.float().mean()),
-                      "accepted_rel_err_median": float(np.median(rel_acc2)) if rel_acc2.size else None,
-                      "accepted_rel_err_p99": float(np.percentile(rel_acc2, 99)) if rel_acc2.size else None,
-                      "end_to_end_patches_per_s": n / (t_inf + t_fb2)},
+        **tighter,
         "by_leaf_size": by_size,
     }
 

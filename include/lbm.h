@@ -234,9 +234,14 @@ lbm_status lbm_surrogate_get_params(const lbm_surrogate *s, int32_t model, float
 lbm_status lbm_surrogate_set_params(lbm_surrogate *s, int32_t model, const float *host_in);
 /* Normalisation and gate range, HOST float[13]: input shift and scale of the
  * log-K plane, target mean/std of log K*_xx and log K*_yy, then (low, high) of
- * each patch statistic (mean, std, gradient energy of log K), last entry unused.
- * lbm_surrogate_train sets them from its data. */
-lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13]);
+ * each patch statistic (mean, std, gradient energy of log K), then the target
+ * mode: the networks learn (log K* - c) / w per component with, per patch,
+ * 0: c = mean log K, w = 1; 1: c = midpoint of the log layered-medium bounds
+ * of the 32 x 32 plane (rows as parallel series tubes below, columns as series
+ * parallel slabs above), w = 1; 2: that midpoint and w = half the log width
+ * (at least 0.05). lbm_surrogate_train sets every entry but the mode from its
+ * data and keeps the mode set before it (2 for a new ensemble). */
+lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13]);   /* mode not 0-2: EINVAL */
 lbm_status lbm_surrogate_get_normalization(const lbm_surrogate *s, float norm[13]);
 
 /* Leaf -> surrogate input. For each leaf (size s dividing 32, or a multiple of

@@ -513,19 +513,64 @@ __global__ void __launch_bounds__(256) input_moments_kernel(const float *x, int 
     }
 }
 
-// Mean log K of each patch (plane 0 of x), one block per patch, fixed order.
-__global__ void __launch_bounds__(256) patch_mean_kernel(const float *x, int n, float *pm)
+// Per-patch target base for the two components, cw[i] = (c_xx, w_xx, c_yy, w_yy): the network learns
+// (log K* - c) / w. Mode 0: c = mean log K of the patch, w = 1. Modes 1 and 2 centre on the
+// layered-medium bounds of the 32 x 32 plane (for flow along x, rows as parallel series tubes give
+// A_y(H_x K) below and columns as series parallel slabs give H_x(A_y K) above; the same with x and y
+// swapped for K*_yy): c = the midpoint of the log bounds, and w = 1 (mode 1) or half the log width,
+// at least 0.05 (mode 2). One block per patch, FP64 sums in a fixed order.
+__global__ void __launch_bounds__(256) patch_base_kernel(const float *x, int n, int mode, float4 *cw)
 {
-    __shared__ double sh[256];
+    __shared__ double K[IMG][IMG + 1];
+    __shared__ double rowK[IMG], rowI[IMG], colK[IMG], colI[IMG];
+    __shared__ double lsum;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        double acc = 0.0;
-        for (int q = threadIdx.x; q < PIX; q += 256) acc += x[(int64_t)i * 2 * PIX + q];
-        sh[threadIdx.x] = acc;
+        const float *p = x + (int64_t)i * 2 * PIX;
+        for (int q = threadIdx.x; q < PIX; q += 256) K[q / IMG][q % IMG] = (double)p[q];   // log K for now
         __syncthreads();
         if (threadIdx.x == 0) {
             double a = 0.0;
-            for (int k = 0; k < 256; ++k) a += sh[k];
-            pm[i] = (float)(a / PIX);
+            for (int r = 0; r < IMG; ++r)
+                for (int c = 0; c < IMG; ++c) a += K[r][c];
+            lsum = a;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < PIX; q += 256) K[q / IMG][q % IMG] = exp(K[q / IMG][q % IMG]);
+        __syncthreads();
+        if (threadIdx.x < IMG) {
+            const int r = threadIdx.x;
+            double sk = 0.0, si = 0.0;
+            for (int c = 0; c < IMG; ++c) { sk += K[r][c]; si += 1.0 / K[r][c]; }
+            rowK[r] = sk;
+            rowI[r] = si;
+        } else if (threadIdx.x < 2 * IMG) {
+            const int c = threadIdx.x - IMG;
+            double sk = 0.0, si = 0.0;
+            for (int r = 0; r < IMG; ++r) { sk += K[r][c]; si += 1.0 / K[r][c]; }
+            colK[c] = sk;
+            colI[c] = si;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float4 o;
+            if (mode == 0) {
+                const float m = (float)(lsum / PIX);
+                o = make_float4(m, 1.0f, m, 1.0f);
+            } else {
+                double ahx = 0.0, hax = 0.0, ahy = 0.0, hay = 0.0;
+                for (int k = 0; k < IMG; ++k) {
+                    ahx += IMG / rowI[k];          // H_x of row k
+                    hax += IMG / colK[k];          // 1 / A_y of column k
+                    ahy += IMG / colI[k];          // H_y of column k
+                    hay += IMG / rowK[k];          // 1 / A_x of row k
+                }
+                const double lox = log(ahx / IMG), hix = log(IMG / hax);
+                const double loy = log(ahy / IMG), hiy = log(IMG / hay);
+                const float wx = mode == 2 ? (float)fmax(0.5 * (hix - lox), 0.05) : 1.0f;
+                const float wy = mode == 2 ? (float)fmax(0.5 * (hiy - loy), 0.05) : 1.0f;
+                o = make_float4((float)(0.5 * (lox + hix)), wx, (float)(0.5 * (loy + hiy)), wy);
+            }
+            cw[i] = o;
         }
         __syncthreads();
     }
@@ -540,14 +585,14 @@ __global__ void gather_targets_kernel(const float *ty, const int *idx, int B, fl
     }
 }
 
-// Standardised network outputs -> log K*: y * std + mean + (mean log K of the patch), [model][n][2].
-__global__ void destandardise_kernel(float *y, int n, int nmodels, const float *pm, float m0, float s0, float m1,
+// Standardised network outputs -> log K*: c + w (y * std + mean) per component, [model][n][2].
+__global__ void destandardise_kernel(float *y, int n, int nmodels, const float4 *cw, float m0, float s0, float m1,
                                      float s1)
 {
     const int64_t n2 = (int64_t)nmodels * n * 2;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-        const float base = pm[(i >> 1) % n];
-        y[i] = ((i & 1) ? y[i] * s1 + m1 : y[i] * s0 + m0) + base;
+        const float4 b = cw[(i >> 1) % n];
+        y[i] = (i & 1) ? b.z + b.w * (y[i] * s1 + m1) : b.x + b.y * (y[i] * s0 + m0);
     }
 }
 
@@ -713,6 +758,7 @@ struct lbm_surrogate {
     float in_shift = 0.0f, in_scale = 1.0f;
     float y_mean[2] = {0.0f, 0.0f}, y_std[2] = {1.0f, 1.0f};
     float stat_lo[3] = {-1e30f, -1e30f, -1e30f}, stat_hi[3] = {1e30f, 1e30f, 1e30f};
+    int target_mode = 2;          // patch_base_kernel: 0 mean log K, 1 bound midpoint, 2 midpoint and width
     // work buffers sized for `cap` images
     int cap = 0;
     __nv_bfloat16 *act[NLAYER + 1] = {};
@@ -931,7 +977,10 @@ lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13
     if (!(norm[1] > 0.0f) || !(norm[3] > 0.0f) || !(norm[5] > 0.0f)) return fail(LBM_EINVAL, "scales must be > 0");
     s->in_shift = norm[0]; s->in_scale = norm[1];
     s->y_mean[0] = norm[2]; s->y_std[0] = norm[3]; s->y_mean[1] = norm[4]; s->y_std[1] = norm[5];
+    const int mode = (int)norm[12];
+    if (!(norm[12] == (float)mode) || mode < 0 || mode > 2) return fail(LBM_EINVAL, "target mode must be 0, 1 or 2");
     for (int k = 0; k < 3; ++k) { s->stat_lo[k] = norm[6 + 2 * k]; s->stat_hi[k] = norm[7 + 2 * k]; }
+    s->target_mode = mode;
     return LBM_OK;
 }
 
@@ -941,7 +990,7 @@ lbm_status lbm_surrogate_get_normalization(const lbm_surrogate *s, float norm[13
     norm[0] = s->in_shift; norm[1] = s->in_scale;
     norm[2] = s->y_mean[0]; norm[3] = s->y_std[0]; norm[4] = s->y_mean[1]; norm[5] = s->y_std[1];
     for (int k = 0; k < 3; ++k) { norm[6 + 2 * k] = s->stat_lo[k]; norm[7 + 2 * k] = s->stat_hi[k]; }
-    norm[12] = 0.0f;
+    norm[12] = (float)s->target_mode;
     return LBM_OK;
 }
 
@@ -1016,20 +1065,21 @@ lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n
                                      cudaMemcpyDeviceToDevice, st));
         }
     }
-    float *d_pm = nullptr;
-    SUR_CUDA(cudaMalloc(&d_pm, sizeof(float) * n));
-    patch_mean_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, d_pm);
-    destandardise_kernel<<<nblk((int64_t)s->nmodels * n * 2), 256, 0, st>>>(y_dev, n, s->nmodels, d_pm, s->y_mean[0],
+    float4 *d_cw = nullptr;
+    SUR_CUDA(cudaMalloc(&d_cw, sizeof(float4) * n));
+    patch_base_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, s->target_mode, d_cw);
+    destandardise_kernel<<<nblk((int64_t)s->nmodels * n * 2), 256, 0, st>>>(y_dev, n, s->nmodels, d_cw, s->y_mean[0],
                                                                           s->y_std[0], s->y_mean[1], s->y_std[1]);
     count_launches(2);
     r = check_err(s, st);
-    cudaFree(d_pm);
+    cudaFree(d_cw);
     return r;
 }
 
 // Trains every model of the ensemble on n samples: inputs x_dev [n][2][32][32]
 // (lbm_patches), targets y_dev [n][2] = log K*_xx, log K*_yy. The networks learn
-// log K* minus the patch's mean log K, standardised. Sets the input and target
+// (log K* - c) / w, standardised, with the per-patch base (c, w) of the target
+// mode (patch_base_kernel; mode 2 unless set before training). Sets the input and target
 // normalisation from the data and the patch-statistics range of the gate from
 // stats_dev [n][3] (lbm_patches). Adam (0.9, 0.999, 1e-8), learning rate lr
 // with cosine decay to lr / 10, mini-batches of `batch` drawn by a seeded
@@ -1046,21 +1096,24 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
     std::vector<float> hy((size_t)2 * n), hs((size_t)3 * n), hx0;
     SUR_CUDA(cudaMemcpy(hy.data(), y_dev, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost));
     SUR_CUDA(cudaMemcpy(hs.data(), stats_dev, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost));
-    // targets are learned relative to the patch's mean log K (the geometric-mean permeability)
-    std::vector<float> pm((size_t)n);
+    // targets are learned relative to a per-patch base (c, w) (patch_base_kernel, target_mode)
+    std::vector<float> cw((size_t)4 * n);
     {
-        float *d_pm = nullptr;
-        SUR_CUDA(cudaMalloc(&d_pm, sizeof(float) * n));
-        patch_mean_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, d_pm);
+        float4 *d_cw = nullptr;
+        SUR_CUDA(cudaMalloc(&d_cw, sizeof(float4) * n));
+        patch_base_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, s->target_mode, d_cw);
         count_launches(1);
-        cudaError_t e1 = cudaMemcpy(pm.data(), d_pm, sizeof(float) * n, cudaMemcpyDeviceToHost);
-        cudaFree(d_pm);
-        if (e1 != cudaSuccess) { cudaGetLastError(); return fail(LBM_ECUDA, "patch means: %s", cudaGetErrorString(e1)); }
+        cudaError_t e1 = cudaMemcpy(cw.data(), d_cw, sizeof(float4) * n, cudaMemcpyDeviceToHost);
+        cudaFree(d_cw);
+        if (e1 != cudaSuccess) { cudaGetLastError(); return fail(LBM_ECUDA, "patch bases: %s", cudaGetErrorString(e1)); }
     }
+    auto resid = [&](int i, int k) {   // (log K* - c) / w
+        return ((double)hy[2 * i + k] - cw[4 * i + 2 * k]) / cw[4 * i + 2 * k + 1];
+    };
     double my[2] = {0, 0}, sy[2] = {0, 0}, mx = 0, sx = 0;
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < 2; ++k) {
-            const double rr = (double)hy[2 * i + k] - pm[i];
+            const double rr = resid(i, k);
             my[k] += rr;
             sy[k] += rr * rr;
         }
@@ -1098,7 +1151,7 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
     // standardised residual targets
     std::vector<float> ty((size_t)2 * n);
     for (int i = 0; i < n; ++i)
-        for (int k = 0; k < 2; ++k) ty[2 * i + k] = (float)(((double)hy[2 * i + k] - pm[i] - my[k]) / sy[k]);
+        for (int k = 0; k < 2; ++k) ty[2 * i + k] = (float)((resid(i, k) - my[k]) / sy[k]);
     float *d_ty = nullptr;
     SUR_CUDA(cudaMalloc(&d_ty, sizeof(float) * 2 * n));
     cudaError_t e = cudaMemcpy(d_ty, ty.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice);

@@ -118,6 +118,9 @@ def test_adam_step_matches_oracle():
     stats = np.stack([S.patch_stats(x[i, 0].astype(np.float64)) for i in range(n)]).astype(np.float32)
     with lbm.Surrogate(1, 0) as sur:
         sur.set_params(0, _flat(p))
+        norm0 = sur.get_normalization()
+        norm0[12] = 0                          # targets relative to the patch's mean log K (rebuilt below)
+        sur.set_normalization(norm0)
         sur.train(_t(x), _t(ylab), _t(stats), epochs=1, batch=n, lr=1e-3, seed=0)
         p1 = sur.get_params(0)
         norm = sur.get_normalization()
@@ -159,6 +162,10 @@ def test_training_fits_a_smooth_target():
     y = np.stack([x[:, 0].mean(axis=(1, 2)), x[:, 0].std(axis=(1, 2)) + 0.3 * x[:, 1, 0, 0]], axis=1)
     stats = np.zeros((n, 3), dtype=np.float32)
     with lbm.Surrogate(2, 1) as sur:
+        norm = sur.get_normalization()
+        assert norm[12] == 2                          # a new ensemble learns the bound-normalised target
+        norm[12] = 0                                  # mechanics only: the plain mean-log-K base
+        sur.set_normalization(norm)
         loss = sur.train(_t(x), _t(y), _t(stats), epochs=30, batch=64, lr=2e-3, seed=1)
         pred = sur.predict(_t(x)).cpu().numpy()
     print("training loss per epoch (model 0):", loss[0][::5])
@@ -194,3 +201,41 @@ def test_gate_routes_blocks():
     np.testing.assert_allclose(ks[:, 0], np.exp(pred[:, :, 0].mean(axis=0)), rtol=1e-5)
     np.testing.assert_allclose(ks[:, 3], np.exp(pred[:, :, 1].mean(axis=0)), rtol=1e-5)
     assert (ks[:, 1] == 0).all() and (ks[:, 2] == 0).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_target_base_modes(mode):
+    """With every weight zero and target mean 0 the network contributes nothing, so the prediction is
+    the per-patch base c of the target mode. Mode 0: mean log K. Modes 1 and 2: the midpoint of the
+    layered-medium bounds, which for a patch of layers across x collapse to the harmonic mean of the
+    layers for K*_xx and their arithmetic mean for K*_yy (Tables 1 and 2 in the Darcy limit)."""
+    import torch
+    lbm = _lbm()
+    rng = np.random.default_rng(81)
+    layers = np.exp(rng.uniform(-6.0, 0.0, 32))                    # K varies along x only
+    logk = [np.tile(np.log(layers), (32, 1)), rng.normal(-3.0, 1.2, (32, 32))]
+    x = np.zeros((2, 2, 32, 32), dtype=np.float32)
+    for i, lk in enumerate(logk):
+        x[i, 0] = lk
+        x[i, 1] = 5.0 / 6.0
+    with lbm.Surrogate(1, 0) as sur:
+        sur.set_params(0, np.zeros(lbm.lbm_surrogate_param_count(), dtype=np.float32))
+        norm = np.array([0, 1, 0, 1, 0, 1, -1e30, 1e30, -1e30, 1e30, -1e30, 1e30, mode], dtype=np.float32)
+        sur.set_normalization(norm)
+        y = sur.predict(torch.from_numpy(x).cuda()).cpu().numpy()[0]
+    for i, lk in enumerate(logk):
+        k = np.exp(lk.astype(np.float32).astype(np.float64))
+        if mode == 0:
+            cx = cy = lk.astype(np.float32).astype(np.float64).mean()
+        else:
+            lox = np.log((1.0 / (1.0 / k).mean(axis=1)).mean())        # rows (series along x) in parallel
+            hix = np.log(1.0 / (1.0 / k.mean(axis=0)).mean())          # columns (parallel) in series
+            loy = np.log((1.0 / (1.0 / k).mean(axis=0)).mean())
+            hiy = np.log(1.0 / (1.0 / k.mean(axis=1)).mean())
+            cx, cy = 0.5 * (lox + hix), 0.5 * (loy + hiy)
+        np.testing.assert_allclose(y[i], [cx, cy], rtol=0, atol=2e-5)
+    if mode:
+        np.testing.assert_allclose(y[0, 0], np.log(1.0 / (1.0 / layers.astype(np.float32)).mean()), atol=2e-5)
+        np.testing.assert_allclose(y[0, 1], np.log(layers.astype(np.float32).mean()), atol=2e-5)
+    with lbm.Surrogate(1, 0) as sur, pytest.raises(lbm.LbmError):
+        sur.set_normalization(np.array([0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 3], dtype=np.float32))
