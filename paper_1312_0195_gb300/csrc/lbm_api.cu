@@ -272,6 +272,7 @@ static lbm_status autotune(lbm_grid *g)
 {
     const char *env = std::getenv("LBM_AUTOTUNE");
     if (env && env[0] == '0') return LBM_OK;
+    if (std::getenv("LBM_STEP_VEC")) return LBM_OK;      // a variant was chosen explicitly
     const int64_t n = (int64_t)g->p.nx * g->p.ny;
     if (n < ((int64_t)1 << 20)) return LBM_OK;      // small lattices are launch-bound: keep the default
     const bool walls = g->p.bc == LBM_BC_WALLS_Y;
@@ -287,19 +288,23 @@ static lbm_status autotune(lbm_grid *g)
         }
     }
     const int sms = sm_count(g->dev);
-    // cells-per-thread candidates: the default for this storage and row length, and the wider pack
+    // cells-per-thread candidates: the default for this storage and row length, then the other
+    // built packs (FP32: 8; FP16: 4 and 2, fewer registers and more resident warps)
     const int dvec = step_vec(g->p.storage, g->p.nx);
-    const int wide = g->p.storage == LBM_F32 ? 8 : (g->p.storage == LBM_F16 ? 2 : dvec);
-    const int vecs[2] = {dvec, step_vec_ok(g->p.storage, g->p.nx, wide) ? wide : dvec};
+    int vecs[3] = {dvec, 0, 0};
+    int nvec = 1;
+    const int others[2] = {g->p.storage == LBM_F32 ? 8 : (g->p.storage == LBM_F16 ? 4 : 0),
+                           g->p.storage == LBM_F16 ? 2 : 0};
+    for (int o : others)
+        if (o && o != dvec && step_vec_ok(g->p.storage, g->p.nx, o)) vecs[nvec++] = o;
     GridLaunch best = g->L;
     float best_ms = -1.0f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     LBM_CUDA(cudaEventCreate(&e0));
     LBM_CUDA(cudaEventCreate(&e1));
     const int warm = 2, timed = 8;
-    for (int vi = 0; vi < 2; ++vi) {
+    for (int vi = 0; vi < nvec; ++vi) {
         const int vec = vecs[vi];
-        if (vi == 1 && vec == vecs[0]) break;
         for (int threads : {128, 256, 512}) {
             const int occ = step_blocks_per_sm(g->p.storage, g->coef_mode, g->has_g, walls, g->p.nx, threads, vec);
             const int64_t chunks = n / vec;
@@ -418,6 +423,18 @@ lbm_status grid_create_impl(const lbm_params *p, const float *kappa_dev, const d
     const int64_t cap = (int64_t)sms * step_blocks_per_sm(p->storage, g->coef_mode, g->has_g,
                                                           p->bc == LBM_BC_WALLS_Y, p->nx, g->L.step_threads);
     g->L.step_blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    // LBM_STEP_VEC=v selects another built cells-per-thread variant of the step (the arithmetic per
+    // cell is the same in every variant) and turns the autotuner off for this grid
+    if (const char *ev = std::getenv("LBM_STEP_VEC")) {
+        const int v = std::atoi(ev);
+        if (step_vec_ok(p->storage, p->nx, v)) {
+            g->L.step_vec = v;
+            const int64_t w2 = (n / v + g->L.step_threads - 1) / g->L.step_threads;
+            const int64_t c2 = (int64_t)sms * step_blocks_per_sm(p->storage, g->coef_mode, g->has_g,
+                                                                 p->bc == LBM_BC_WALLS_Y, p->nx, g->L.step_threads, v);
+            g->L.step_blocks = (int)(w2 < c2 ? (w2 < 1 ? 1 : w2) : c2);
+        }
+    }
     g->L.mom_threads = 256;
     const int64_t mwant = (chunks + 255) / 256;
     const int64_t mcap = (int64_t)sms * 2;   // 128 registers: two 256-thread blocks per SM

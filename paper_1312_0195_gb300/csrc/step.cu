@@ -598,7 +598,7 @@ bool step_vec_ok(int storage, int nx, int vec)
     if (vec <= 0 || nx % vec) return false;
     switch (storage) {
     case LBM_F32: return vec == 1 || vec == 4 || vec == 8;
-    case LBM_F16: return vec == 1 || vec == 2 || vec == 8;
+    case LBM_F16: return vec == 1 || vec == 2 || vec == 4 || vec == 8;
     case LBM_F64: return vec == 1 || vec == 2;
     }
     return false;
@@ -614,8 +614,9 @@ int step_blocks_per_sm(int storage, int coef_mode, bool gfield, bool walls, int 
                                 : occupancy_t<float, 1>(coef_mode, gfield, walls, threads));
     case LBM_F16:
         return v == 8 ? occupancy_t<__half, 8>(coef_mode, gfield, walls, threads)
+                      : (v == 4 ? occupancy_t<__half, 4>(coef_mode, gfield, walls, threads)
                       : (v == 2 ? occupancy_t<__half, 2>(coef_mode, gfield, walls, threads)
-                                : occupancy_t<__half, 1>(coef_mode, gfield, walls, threads));
+                                : occupancy_t<__half, 1>(coef_mode, gfield, walls, threads)));
     case LBM_F64:
         return v == 2 ? occupancy_t<double, 2>(coef_mode, gfield, walls, threads)
                       : occupancy_t<double, 1>(coef_mode, gfield, walls, threads);
@@ -639,8 +640,9 @@ cudaError_t launch_step(int storage, int coef_mode, bool gfield, bool walls, con
         nx = static_cast<const StepArgs<__half, float> *>(args)->nx;
         const int v = step_vec_ok(storage, nx, L.step_vec) ? L.step_vec : step_vec(storage, nx);
         return v == 8 ? launch_step_t<__half, 8>(coef_mode, gfield, walls, args, L, st)
+                      : (v == 4 ? launch_step_t<__half, 4>(coef_mode, gfield, walls, args, L, st)
                       : (v == 2 ? launch_step_t<__half, 2>(coef_mode, gfield, walls, args, L, st)
-                                : launch_step_t<__half, 1>(coef_mode, gfield, walls, args, L, st));
+                                : launch_step_t<__half, 1>(coef_mode, gfield, walls, args, L, st)));
     }
     case LBM_F64: {
         nx = static_cast<const StepArgs<double, double> *>(args)->nx;

@@ -326,3 +326,26 @@ def test_mean_velocity_bitwise_repeatable_and_checkpoint():
     with lbm.Grid(p, kt) as B:
         B.step(100, 0.0, 0)
         assert B.mean_velocity() == m1
+
+
+@pytest.mark.parametrize("storage,vecs", [(0, (1, 4, 8)), (1, (1, 2, 4, 8)), (2, (1, 2))])
+def test_every_cells_per_thread_variant_agrees_bitwise(storage, vecs, monkeypatch):
+    """The step is built for several cells-per-thread packs per storage type (the autotuner picks
+    one per lattice); each cell's arithmetic is the same in all of them, so the states agree bit for
+    bit, with walls and periodic rows alike."""
+    import torch
+    lbm = _lbm()
+    kap = synth.lognormal_kappa(256, 96, 6.0, 1.5, seed=91).astype(np.float32)
+    for walls in (False, True):
+        states = {}
+        for v in vecs:
+            monkeypatch.setenv("LBM_STEP_VEC", str(v))
+            p = lbm.Params(nx=256, ny=96, tau=0.7, nu=0.05, eps=0.9, gx=2e-6, gy=-1e-6, storage=storage,
+                           bc=lbm.LBM_BC_WALLS_Y if walls else lbm.LBM_BC_PERIODIC)
+            with lbm.Grid(p, torch.from_numpy(kap).cuda()) as G:
+                G.step(150, 0.0, 0)
+                st = torch.empty(lbm.lbm_grid_state_bytes(G.handle), dtype=torch.uint8, device="cuda")
+                lbm.lbm_grid_save_state(G.handle, st)
+                states[v] = st.cpu().numpy()
+        for v in vecs[1:]:
+            np.testing.assert_array_equal(states[v], states[vecs[0]])
