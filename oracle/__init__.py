@@ -88,6 +88,9 @@ def _L():
         _lib.orc3_run.argtypes = [C.POINTER(_Problem3), dp, C.c_long]
         _lib.orc3_fields.argtypes = [C.POINTER(_Problem3), dp, dp, dp, dp, dp]
         _lib.orc3_mean_velocity.argtypes = [C.POINTER(_Problem3), dp, dp]
+        _lib.orc3_local_keff.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_long, C.c_int, dp, C.POINTER(C.c_long)]
+        _lib.orc3_local_keff.restype = C.c_int
     return _lib
 
 
@@ -148,6 +151,20 @@ class Problem3D:
         m = np.empty(3)
         _L().orc3_mean_velocity(C.byref(self._s), _dp(f), _dp(m))
         return m
+
+
+def local_keff3(kappa_cube, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64):
+    """Three-dimensional local problem on one periodic s^3 cube (D3Q19), drives along x, y, z;
+    Eq. 17 in 3-D. Returns dict(keff=[3][3] (K*_ij, i velocity component, j drive), steps=[3],
+    converged=n)."""
+    k = np.ascontiguousarray(kappa_cube, dtype=np.float64)
+    s = k.shape[0]
+    assert k.shape == (s, s, s)
+    keff = np.empty(9)
+    st = (C.c_long * 3)()
+    nconv = _L().orc3_local_keff(s, _dp(k), float(tau), float(nu), float(eps), float(g_const), float(tol),
+                                 int(max_steps), int(check_every), _dp(keff), st)
+    return dict(keff=keff.reshape(3, 3), steps=[st[0], st[1], st[2]], converged=int(nconv))
 
 
 class Problem:

@@ -159,3 +159,56 @@ void orc3_mean_velocity(const orc3_problem *p, const double *f, double out[3])
     }
     for (int k = 0; k < 3; ++k) out[k] = s[k] / n;
 }
+
+/*
+ * One three-dimensional local problem (Section 3 with the D3Q19 lattice): the
+ * s x s x s permeability cube `kappa_cube` ([z][y][x]) with periodic closure,
+ * driven along x, y and z in turn by a body force of magnitude gconst, each from
+ * rest until the driven component of the volume-averaged velocity settles:
+ * every check_every steps n, |ubar_d(n) - ubar_d(n - k)| <= tol k |ubar_d(n)|
+ * (tol <= 0 runs exactly max_steps). Eq. 17 in three dimensions: column d of K*
+ * is nu / gconst times the mean velocity of drive d, so K*[i][d] = nu ubar_d,i / G.
+ * keff [3][3] row-major (K*_ij, i the velocity component, j the drive);
+ * steps[d] per drive; returns the number of drives that converged.
+ */
+int orc3_local_keff(int s, const double *kappa_cube, double tau, double nu, double eps, double gconst,
+                    double tol, long max_steps, int check_every, double keff[9], long steps[3])
+{
+    lattice3_init();
+    orc3_problem p;
+    memset(&p, 0, sizeof p);
+    p.nx = s; p.ny = s; p.nz = s; p.tau = tau; p.nu = nu; p.eps = eps; p.kappa = kappa_cube;
+    const long n = (long)s * s * s;
+    double *f = (double *)malloc(sizeof(double) * n * Q3);
+    double *g = (double *)malloc(sizeof(double) * n * Q3);
+    int nconv = 0;
+    for (int d = 0; d < 3; ++d) {
+        p.gx = d == 0 ? gconst : 0.0;
+        p.gy = d == 1 ? gconst : 0.0;
+        p.gz = d == 2 ? gconst : 0.0;
+        orc3_init_rest(&p, f);
+        double prev = 0.0, m[3];
+        long st = 0;
+        int conv = 0;
+        while (st < max_steps) {
+            orc3_step(&p, f, g);
+            memcpy(f, g, sizeof(double) * n * Q3);
+            ++st;
+            if (check_every > 0 && st % check_every == 0) {
+                orc3_mean_velocity(&p, f, m);
+                if (tol > 0.0 && st > check_every && fabs(m[d] - prev) <= tol * check_every * fabs(m[d])) {
+                    conv = 1;
+                    break;
+                }
+                prev = m[d];
+            }
+        }
+        orc3_mean_velocity(&p, f, m);
+        for (int i = 0; i < 3; ++i) keff[3 * i + d] = nu / gconst * m[i];
+        steps[d] = st;
+        nconv += conv;
+    }
+    free(f);
+    free(g);
+    return nconv;
+}

@@ -121,3 +121,49 @@ def test_mass_conservation_and_symmetry_in_3d():
     s = np.abs(u).max()
     np.testing.assert_allclose(um[::-1], u, atol=1e-12 * s)
     np.testing.assert_allclose(wm[::-1], -w, atol=1e-12 * s)
+
+
+# ------------------------------------------------- three-dimensional local problems (Eq. 17)
+
+def test_local_keff3_uniform_cube_is_kappa_identity():
+    r = oracle.local_keff3(np.full((5, 5, 5), 2e-3), 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-12, max_steps=100000)
+    np.testing.assert_allclose(np.diag(r["keff"]), 2e-3, rtol=1e-9)
+    # off-diagonals are rounding only: the cancellation floor of full-f storage, ~1e-10 of K*
+    assert np.abs(r["keff"] - np.diag(np.diag(r["keff"]))).max() < 1e-9 * 2e-3
+
+
+def test_local_keff3_of_a_z_invariant_cube_is_the_2d_local_keff():
+    """The exact D3Q19 -> D2Q9 reduction of a field invariant along z: the xy block of K* is the
+    2-D local K* of the slice (same stop rule, same step counts) and nothing couples to z."""
+    k2 = synth.lognormal_kappa(6, 6, 2.0, 1.2, seed=55)
+    r3 = oracle.local_keff3(np.broadcast_to(k2[None], (6, 6, 6)).copy(), 1.0, 1.0 / 6.0, 1.0, 1e-6,
+                            tol=1e-9, max_steps=100000)
+    r2 = oracle.local_keff(k2, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-9, max_steps=100000)
+    k2d = np.array([[r2["keff"][0], r2["keff"][1]], [r2["keff"][2], r2["keff"][3]]])
+    assert r3["steps"][:2] == r2["steps"]
+    np.testing.assert_allclose(r3["keff"][:2, :2], k2d, rtol=0, atol=1e-9 * np.abs(k2d).max())
+    assert np.abs(r3["keff"][2, :2]).max() < 1e-9 * np.abs(k2d).max()    # rounding floor, as above
+    assert np.abs(r3["keff"][:2, 2]).max() < 1e-9 * np.abs(k2d).max()
+
+
+def test_local_keff3_axis_permutation():
+    """Relabelling the axes of the cube (x, y, z) -> (y, z, x) permutes K* the same way."""
+    rng = np.random.default_rng(56)
+    k = np.exp(rng.normal(-5.0, 1.0, (4, 4, 4)))
+    a = oracle.local_keff3(k, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-11, max_steps=100000)["keff"]
+    # new field K'[z'][y'][x'] with x' = y, y' = z, z' = x: K'[x][z][y] = K[z][y][x]
+    kp = np.transpose(k, (2, 0, 1)).copy()
+    b = oracle.local_keff3(kp, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-11, max_steps=100000)["keff"]
+    P = np.array([[0, 1, 0], [0, 0, 1], [1, 0, 0]])        # new axis i is old axis perm[i]
+    np.testing.assert_allclose(b, P @ a @ P.T, rtol=1e-7, atol=1e-9 * np.abs(a).max())
+
+
+def test_local_keff3_parallel_layers_darcy_arithmetic_mean():
+    """Table 2's setting in three dimensions: kappa varies along x in two bands, tau = 1/2 (Darcy);
+    driven along y or z the flow sees the layers in parallel: K*_yy = K*_zz = arithmetic mean."""
+    ex = synth.paper_experiment("E3", ratio=10.0, ny=1)
+    k1, k2 = float(ex["kappa"][0, 0]), float(ex["kappa"][0, 10])
+    cube = np.broadcast_to(np.array([k1] * 4 + [k2] * 4)[None, None, :], (8, 8, 8)).copy()
+    r = oracle.local_keff3(cube, ex["tau"], ex["nu"], ex["eps"], 1e-6, tol=1e-11, max_steps=20000)
+    mean = 0.5 * (k1 + k2)
+    assert abs(r["keff"][1, 1] - mean) <= 2e-6 * mean and abs(r["keff"][2, 2] - mean) <= 2e-6 * mean

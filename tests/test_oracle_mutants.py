@@ -43,6 +43,8 @@ MUTANTS3 = {
                                 "const int xd = (x - E3[a][0] + nx) % nx, yd = (y - E3[a][1] + ny) % ny,")],
     "d3q19_eq16_sign": [("(1.0 - 2.0 * tau) * j[k] / rho", "(1.0 + 2.0 * tau) * j[k] / rho")],
     "d3q19_force_half_dropped": [("j[k] + 0.5 * p->eps * rho * G[k]", "j[k] + 1.0 * p->eps * rho * G[k]")],
+    "d3q19_local_drive_axes": [("        p.gy = d == 1 ? gconst : 0.0;\n        p.gz = d == 2 ? gconst : 0.0;",
+                                "        p.gy = d == 2 ? gconst : 0.0;\n        p.gz = d == 1 ? gconst : 0.0;")],
 }
 
 
