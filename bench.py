@@ -246,6 +246,20 @@ def measure_d3q19(lbm, torch, n=256, steps=200):
             t = (time.perf_counter() - t0) / k
         out[name] = {"mlups": n ** 3 / t / 1e6, "bytes_per_lup": bpl,
                      "hbm_frac": bpl * n ** 3 / t / 1e9 / peaks["hbm_gbs"]}
+    # three-dimensional local problems (Eq. 17 in 3-D): every 16^3 cube of the box, three drives
+    b = 16
+    leaves = torch.tensor([(x, y, z, b) for z in range(0, n, b) for y in range(0, n, b) for x in range(0, n, b)],
+                          dtype=torch.int32, device="cuda")
+    p = lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    keff, status, lsteps, _ = lbm.local_keff3(p, kap, leaves, 1e-6, 1e-8, 200000, 64)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    lups = float(lsteps.double().sum()) * b ** 3
+    out["local_keff"] = {"workload": f"all {leaves.shape[0]} cubes of {b}^3, tau 1, G 1e-6 along x, y, z, tol 1e-8",
+                         "patches_per_s": leaves.shape[0] / t, "seconds": t, "glups": lups / t / 1e9,
+                         "converged": int((status == 0).sum())}
     return out
 
 

@@ -344,6 +344,30 @@ lbm_status lbm3d_get_fields(lbm3d_grid *g, float *rho_dev, float *u_dev, float *
 /* Volume average of the flow velocity, FP64 in a fixed order; HOST out[3]. */
 lbm_status lbm3d_mean_velocity(lbm3d_grid *g, double out_mean_uvw[3]);
 
+/* Three-dimensional local problems (Section 3 with the D3Q19 lattice). For each
+ * cubic leaf (x0, y0, z0, size) of the field kappa_dev [nz][ny][nx] (p->nx, ny,
+ * nz are the field size; tau, nu, eps, storage as for a 3-D grid, the force is
+ * ignored) three periodic runs from rest, driven by g_const along x, y and z,
+ * each until its volume-averaged velocity settles: every check_every steps t,
+ * |ubar_d(t) - ubar_d(t - check_every)| <= tol_rel * check_every * |ubar_d(t)|
+ * on the driven component d (tol_rel = 0 runs exactly max_steps). Eq. 17 in 3-D
+ * gives column d of K*: K*_id = nu ubar_d,i / g_const. Outputs (caller-owned
+ * DEVICE memory): keff_dev double [n][3][3] (row i = velocity component, column
+ * d = drive), status_dev int32 [n] (LBM_OK, LBM_ENOTCONV, or LBM_ETIMEOUT when
+ * the lbm_set_time_limit bound ran out first; keff then not valid), steps_dev
+ * int32 [n][3] or NULL. Cubes that fit the shared memory of a thread-block
+ * cluster of at most 16 CTAs (up to 32 cells wide in FP32, 16 in FP64) run one
+ * job per cluster entirely on chip; larger cubes run with their 3 n jobs stacked
+ * in device memory (allocated and freed by the call); the environment variable
+ * LBM_LOCAL3_GLOBAL=1 sends every size that second way. Returns the worst
+ * status; leaves outside the field or with size outside [1, 256] give
+ * LBM_EINVAL. */
+typedef struct { int32_t x0, y0, z0, size; } lbm3d_leaf;
+lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev, const lbm3d_leaf *leaves_dev,
+                                  int32_t n_leaves, double g_const, double tol_rel, int64_t max_steps,
+                                  int32_t check_every, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                                  void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -401,6 +401,30 @@ def lbm3d_mean_velocity(grid):
     return tuple(out)
 
 
+def lbm3d_local_keff_batch(params: Params3D, kappa, leaves, g_const: float, tol_rel: float, max_steps: int,
+                           check_every: int, keff, status, steps=None, stream=None) -> int:
+    p = params.c()
+    return _check(_abi.lib().lbm3d_local_keff_batch(C.byref(p), _ptr(kappa), _ptr(leaves), int(leaves.shape[0]),
+                                                    float(g_const), float(tol_rel), int(max_steps), int(check_every),
+                                                    _ptr(keff), _ptr(status), _ptr(steps), _stream(stream)),
+                  allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
+
+
+def local_keff3(params: Params3D, kappa, leaves, g_const: float = 1e-6, tol_rel: float = 1e-8,
+                max_steps: int = 200000, check_every: int = 64, stream=None):
+    """Allocating convenience over lbm3d_local_keff_batch: leaves int32 [n, 4] (x0, y0, z0, size);
+    returns (keff [n, 3, 3] f64, status [n], steps [n, 3], worst)."""
+    import torch
+    dev = kappa.device
+    n = int(leaves.shape[0])
+    keff = torch.empty((n, 3, 3), dtype=torch.float64, device=dev)
+    status = torch.empty((n,), dtype=torch.int32, device=dev)
+    steps = torch.empty((n, 3), dtype=torch.int32, device=dev)
+    worst = lbm3d_local_keff_batch(params, kappa, leaves, g_const, tol_rel, max_steps, check_every, keff, status,
+                                   steps, stream)
+    return keff, status, steps, worst
+
+
 class Grid3D:
     """Owning wrapper of a D3Q19 grid: ``Grid3D(params3d, kappa_cuda_f32 [nz, ny, nx])``."""
 

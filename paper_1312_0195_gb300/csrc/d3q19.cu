@@ -11,13 +11,19 @@
 // coalesced. HBM-bound: 19 x 4 x 2 + 4 = 156 bytes per lattice update in FP32.
 #include "lbm_internal.h"
 
+
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <vector>
 
 namespace lbm {
 
 lbm_status fail(lbm_status s, const char *fmt, ...);
 bool is_device_ptr(const void *p);
 void count_launches(int64_t n);
+double local_time_limit();
 
 namespace {
 
@@ -241,6 +247,530 @@ __global__ void __launch_bounds__(256) coef3d_kernel(const float *kappa, T *coef
     if (bad) atomicOr(flags, 1u);
 }
 
+// ------------------------------------------------------------------------
+// Three-dimensional local problems (Section 3 on the D3Q19 lattice): job j is leaf
+// j / 3 driven along axis j % 3, an s^3 periodic cube stored as the j-th block of s^3
+// cells in every population plane. All jobs of one leaf size step together; a job
+// that has met the stop rule is skipped.
+template <typename T>
+struct Local3Args {
+    const T *src;
+    T *dst;
+    const T *coef;          // e per cell of every job
+    const int *list;        // [blocks along y] the jobs still running
+    int s;
+    int64_t s3, plane;
+    T omega, two_tau, omt, hg;   // hg = eps G / 2 along the job's drive axis
+};
+
+// Neighbours within cube `job` (periodic on the cube): base offset folded into the z row.
+__device__ __forceinline__ Nbr cube_neighbours(int x, int y, int z, int s, int64_t base)
+{
+    Nbr n;
+    const int64_t pz = (int64_t)s * s;
+    n.x[0] = x == 0 ? s - 1 : x - 1;
+    n.x[1] = x;
+    n.x[2] = x + 1 == s ? 0 : x + 1;
+    n.y[0] = (int64_t)(y == 0 ? s - 1 : y - 1) * s;
+    n.y[1] = (int64_t)y * s;
+    n.y[2] = (int64_t)(y + 1 == s ? 0 : y + 1) * s;
+    n.z[0] = base + (z == 0 ? s - 1 : z - 1) * pz;
+    n.z[1] = base + z * pz;
+    n.z[2] = base + (z + 1 == s ? 0 : z + 1) * pz;
+    return n;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) local3d_step_kernel(Local3Args<T> a)
+{
+    const int job = a.list[blockIdx.y];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.s3) return;
+    const int s = a.s;
+    const int x = (int)(c % s), yz = (int)(c / s), y = yz % s, z = yz / s;
+    const int64_t base = (int64_t)job * a.s3;
+    const T *__restrict__ src = a.src;
+    T *__restrict__ dst = a.dst;
+    const Nbr nb = cube_neighbours(x, y, z, s, base);
+    T g[Q19];
+    pull19(src, a.plane, nb, g);
+    const T e = __ldg(a.coef + base + c);
+    const int d = job % 3;
+    T drho, jx, jy, jz;
+    moments19(g, drho, jx, jy, jz);
+    const T rho = T(1) + drho;
+    const T rx = d == 0 ? fma(a.hg, rho, jx) : jx;
+    const T ry = d == 1 ? fma(a.hg, rho, jy) : jy;
+    const T rz = d == 2 ? fma(a.hg, rho, jz) : jz;
+    const T rux = fma(-e, rx, rx), ruy = fma(-e, ry, ry), ruz = fma(-e, rz, rz);
+    const T u3x = T(3) * fma(a.two_tau, rux, a.omt * jx);
+    const T u3y = T(3) * fma(a.two_tau, ruy, a.omt * jy);
+    const T u3z = T(3) * fma(a.two_tau, ruz, a.omt * jz);
+    relax_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(g, drho, u3x, u3y, u3z, a.omega);
+#pragma unroll
+    for (int q = 0; q < Q19; ++q) dst[q * a.plane + base + c] = g[q];
+}
+
+struct Check3 {
+    int t, k, regular;      // steps done, check interval, t is a multiple of k
+    int64_t max_steps;
+    double tol, nu_over_g;
+    int *active;
+    double *prev;           // [njobs] driven mean velocity at the previous regular check
+    const int *job_leaf;    // [njobs] leaf index of the job
+    double *keff;           // [n][9]
+    int *status, *steps;    // [n], [n][3] or nullptr
+    int *nactive;
+};
+
+// One block per job: mean flow velocity over the cube (pulled state, Eq. 15) in FP64 in a
+// fixed order, then the stop rule on the driven component; a finished job writes column d of K*.
+template <typename T>
+__global__ void __launch_bounds__(256) local3d_check_kernel(Local3Args<T> a, Check3 ck)
+{
+    const int job = a.list[blockIdx.x];
+    const int s = a.s, d = job % 3;
+    const int64_t base = (int64_t)job * a.s3;
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int64_t c = threadIdx.x; c < a.s3; c += blockDim.x) {
+        const int x = (int)(c % s), yz = (int)(c / s), y = yz % s, z = yz / s;
+        const Nbr nb = cube_neighbours(x, y, z, s, base);
+        T g[Q19];
+        pull19(a.src, a.plane, nb, g);
+        const T e = a.coef[base + c];
+        T drho, jx, jy, jz;
+        moments19(g, drho, jx, jy, jz);
+        const T rho = T(1) + drho;
+        const T rx = d == 0 ? fma(a.hg, rho, jx) : jx;
+        const T ry = d == 1 ? fma(a.hg, rho, jy) : jy;
+        const T rz = d == 2 ? fma(a.hg, rho, jz) : jz;
+        m0 += (double)(fma(-e, rx, rx) / rho);
+        m1 += (double)(fma(-e, ry, ry) / rho);
+        m2 += (double)(fma(-e, rz, rz) / rho);
+    }
+    __shared__ double sh[3][256];
+    sh[0][threadIdx.x] = m0;
+    sh[1][threadIdx.x] = m1;
+    sh[2][threadIdx.x] = m2;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double m[3];
+    for (int q = 0; q < 3; ++q) m[q] = sh[q][0] / (double)a.s3;
+    const double cur = m[d];
+    int st = -1;
+    if (ck.regular) {
+        if (ck.tol > 0.0 && ck.t > ck.k && fabs(cur - ck.prev[job]) <= ck.tol * ck.k * fabs(cur)) st = LBM_OK;
+        ck.prev[job] = cur;
+    }
+    if (st < 0 && ck.t >= ck.max_steps) st = ck.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
+    if (st < 0) return;
+    const int leaf = ck.job_leaf[job];
+    for (int i = 0; i < 3; ++i) ck.keff[9 * (int64_t)leaf + 3 * i + d] = ck.nu_over_g * m[i];   // Eq. 17
+    if (ck.steps) ck.steps[3 * (int64_t)leaf + d] = ck.t;
+    if (st != LBM_OK) atomicMax(&ck.status[leaf], st);
+    ck.active[job] = 0;
+    atomicSub(ck.nactive, 1);
+}
+
+// Rebuilds the list of running jobs in job order: one block, each thread owns a contiguous
+// run of jobs, a block-wide exclusive scan of the counts gives the write offsets.
+__global__ void __launch_bounds__(1024) local3d_compact_kernel(const int *active, int njobs, int *list)
+{
+    __shared__ int cnt[1024];
+    const int per = (njobs + 1023) / 1024;
+    const int j0 = threadIdx.x * per, j1 = min(njobs, j0 + per);
+    int n = 0;
+    for (int j = j0; j < j1; ++j) n += active[j] != 0;
+    cnt[threadIdx.x] = n;
+    __syncthreads();
+    for (int h = 1; h < 1024; h <<= 1) {      // Hillis-Steele inclusive scan
+        const int v = threadIdx.x >= h ? cnt[threadIdx.x - h] : 0;
+        __syncthreads();
+        cnt[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int o = cnt[threadIdx.x] - n;
+    for (int j = j0; j < j1; ++j)
+        if (active[j]) list[o++] = j;
+}
+
+// ------------------------------------------------------------------------
+// Cluster-resident local problems. One job per thread-block cluster of C CTAs: the
+// s^3 cube is split along z into slabs of L = ceil(s / C) layers, CTA r holding
+// layers [r L, r L + L) of all 19 populations and of e in shared memory, so a job
+// never touches HBM after its first step. One copy of the populations is updated
+// in place with the AA pattern: a step of even type reads cell x's own slots and
+// writes each post-collision value to the opposite slot of x; a step of odd type
+// reads slot opp(a) of x - e_a and writes slot a of x + e_a. Either way a thread
+// touches only locations no other thread touches in that step, and after n steps
+// the streamed state is what the next step reads. Neighbours on a slab boundary
+// sit in a peer CTA and go through distributed shared memory; one cluster barrier
+// ends every step. The checks every k steps sum the flow velocity in FP64 per
+// thread, per warp by a fixed shuffle tree, per CTA in warp order and per
+// cluster in rank order, so every CTA takes the same stop decision.
+template <typename T>
+struct Clu3Args {
+    const float *kappa;
+    int nx, ny;
+    const int4 *leaves;     // all leaves of the call
+    const int *ids;         // [njobs / 3] leaf indices of this size
+    int njobs, s, L;
+    T omega, two_tau, omt, hg;
+    double eps_nu, nu_over_g, tol;
+    int k;
+    int64_t max_steps;
+    double *keff;
+    int *status, *steps;
+    unsigned long long *t_start;   // first globaltimer reading of the launch (0 before)
+    int *abort_flag;
+    unsigned long long time_limit_ns;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer3()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr __host__ __device__ int opp19(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
+// Distributed shared memory through 32-bit shared::cluster addresses
+__device__ __forceinline__ uint32_t cluster_addr(const void *own_smem, uint32_t rank)
+{
+    uint32_t d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(d) : "r"((uint32_t)__cvta_generic_to_shared(own_smem)), "r"(rank));
+    return d;
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_size()
+{
+    uint32_t n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
+}
+template <typename T> __device__ __forceinline__ T ld_cluster(uint32_t a);
+template <> __device__ __forceinline__ float ld_cluster<float>(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+template <> __device__ __forceinline__ double ld_cluster<double>(uint32_t a)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v));
+}
+
+// Per-cell geometry: cluster addresses of layers z - 1, z, z + 1 (in whichever CTA
+// holds them) and the wrapped x and y byte offsets within a layer.
+template <typename T>
+struct Cell3 {
+    uint32_t lz[3];
+    uint32_t xo[3], yo[3];
+    int c;                 // index within this CTA's slab
+    template <int A> __device__ __forceinline__ uint32_t from(uint32_t Pb) const   // slot opp(A) of x - e_A
+    {
+        return lz[1 - cz(A)] + opp19(A) * Pb + yo[1 - cy(A)] + xo[1 - cx(A)];
+    }
+    template <int A> __device__ __forceinline__ uint32_t to(uint32_t Pb) const     // slot A of x + e_A
+    {
+        return lz[1 + cz(A)] + A * Pb + yo[1 + cy(A)] + xo[1 + cx(A)];
+    }
+};
+
+template <bool ODD, int A, typename T>
+__device__ __forceinline__ void aa_read_one(const Cell3<T> &q, const T *own, int P, T (&g)[Q19])
+{
+    if (ODD) g[A] = ld_cluster<T>(q.template from<A>(P * (uint32_t)sizeof(T)));
+    else g[A] = own[A * P + q.c];
+}
+template <bool ODD, int A, typename T>
+__device__ __forceinline__ void aa_write_one(const Cell3<T> &q, T *own, int P, const T (&g)[Q19])
+{
+    if (ODD) st_cluster(q.template to<A>(P * (uint32_t)sizeof(T)), g[A]);
+    else own[opp19(A) * P + q.c] = g[A];
+}
+template <bool ODD, typename T, int... As>
+__device__ __forceinline__ void aa_read(const Cell3<T> &q, const T *own, int P, T (&g)[Q19])
+{
+    (aa_read_one<ODD, As>(q, own, P, g), ...);
+}
+template <bool ODD, typename T, int... As>
+__device__ __forceinline__ void aa_write(const Cell3<T> &q, T *own, int P, const T (&g)[Q19])
+{
+    (aa_write_one<ODD, As>(q, own, P, g), ...);
+}
+template <bool ODD, typename T>
+__device__ __forceinline__ void aa_read19(const Cell3<T> &q, const T *own, int P, T (&g)[Q19])
+{
+    aa_read<ODD, T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(q, own, P, g);
+}
+
+// moments of g plus the drag-reduced momentum (1 - e) r, r = j + hg rho along the drive axis d
+template <typename T>
+__device__ __forceinline__ void drag_momentum(const T (&g)[Q19], T e, T hg, int d, T &drho, T &jx, T &jy, T &jz,
+                                              T &rux, T &ruy, T &ruz)
+{
+    moments19(g, drho, jx, jy, jz);
+    const T rho = T(1) + drho;
+    const T rx = d == 0 ? fma(hg, rho, jx) : jx;
+    const T ry = d == 1 ? fma(hg, rho, jy) : jy;
+    const T rz = d == 2 ? fma(hg, rho, jz) : jz;
+    rux = fma(-e, rx, rx);
+    ruy = fma(-e, ry, ry);
+    ruz = fma(-e, rz, rz);
+}
+
+template <bool ODD, typename T>
+__device__ __forceinline__ void aa_step_cell(const Cell3<T> &q, T *own, int P, T e, const Clu3Args<T> &a, int d)
+{
+    T g[Q19];
+    aa_read19<ODD>(q, own, P, g);
+    T drho, jx, jy, jz, rux, ruy, ruz;
+    drag_momentum(g, e, a.hg, d, drho, jx, jy, jz, rux, ruy, ruz);
+    const T u3x = T(3) * fma(a.two_tau, rux, a.omt * jx);
+    const T u3y = T(3) * fma(a.two_tau, ruy, a.omt * jy);
+    const T u3z = T(3) * fma(a.two_tau, ruz, a.omt * jz);
+    relax_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(g, drho, u3x, u3y, u3z, a.omega);
+    aa_write<ODD, T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(q, own, P, g);
+}
+
+template <bool ODD, typename T>
+__device__ __forceinline__ void aa_velocity_cell(const Cell3<T> &q, const T *own, int P, T e, T hg, int d,
+                                                 double &m0, double &m1, double &m2)
+{
+    T g[Q19];
+    aa_read19<ODD>(q, own, P, g);
+    T drho, jx, jy, jz, rux, ruy, ruz;
+    drag_momentum(g, e, hg, d, drho, jx, jy, jz, rux, ruy, ruz);
+    const T rho = T(1) + drho;
+    m0 += (double)(rux / rho);
+    m1 += (double)(ruy / rho);
+    m2 += (double)(ruz / rho);
+}
+
+// cells per thread at most: a slab of P cells needs a block of at least P / CPT threads
+template <typename T> __host__ __device__ constexpr int clu3_cpt() { return sizeof(T) == 4 ? 4 : 2; }
+template <typename T> __host__ __device__ constexpr int clu3_threads() { return 512; }
+
+// Cell3 of the packed cell (zl << 16 | y << 8 | x) from the table of layer addresses
+template <typename T>
+__device__ __forceinline__ Cell3<T> cell3_of(int geo, int s, const uint32_t *zb, int z0)
+{
+    Cell3<T> q;
+    const int x = geo & 255, y = (geo >> 8) & 255, z = z0 + (geo >> 16);
+    const uint32_t E = sizeof(T);
+    q.c = ((geo >> 16) * s + y) * s + x;
+    q.xo[0] = (x == 0 ? s - 1 : x - 1) * E;
+    q.xo[1] = x * E;
+    q.xo[2] = (x + 1 == s ? 0 : x + 1) * E;
+    q.yo[0] = (y == 0 ? s - 1 : y - 1) * s * E;
+    q.yo[1] = y * s * E;
+    q.yo[2] = (y + 1 == s ? 0 : y + 1) * s * E;
+    q.lz[0] = zb[z == 0 ? s - 1 : z - 1];
+    q.lz[1] = zb[z];
+    q.lz[2] = zb[z + 1 == s ? 0 : z + 1];
+    return q;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(Clu3Args<T> a)
+{
+    constexpr int CLU3_CPT = clu3_cpt<T>();
+    const int C = (int)cluster_size();
+    const int r = (int)cluster_rank();
+    const int job = (int)(blockIdx.x / (unsigned)C);
+    const int leaf = a.ids[job / 3], d = job % 3;
+    const int s = a.s, s2 = s * s, L = a.L;
+    const int P = L * s2;                                   // cells of a full slab
+    const int z0 = r * L, Lr = max(0, min(L, s - z0));      // this CTA's layers
+    const int ncell = Lr * s2;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    extern __shared__ __align__(16) unsigned char clu3_smem[];
+    double *part = reinterpret_cast<double *>(clu3_smem);         // [4]: sums of u, abort
+    double *wred = part + 4;                                       // [32][3]
+    uint32_t *zb = reinterpret_cast<uint32_t *>(wred + 96);        // [32] layer z of the cube, any CTA
+    T *own = reinterpret_cast<T *>(wred + 96 + 16);                // [19][P] populations
+
+    for (int z = tid; z < s; z += nt) zb[z] = cluster_addr(own, z / L) + (uint32_t)((z % L) * s2 * sizeof(T));
+    // this thread's cells; e from the leaf's cube of kappa
+    const int4 Lf = a.leaves[leaf];
+    int geo[CLU3_CPT];
+    T ec[CLU3_CPT];
+#pragma unroll
+    for (int i = 0; i < CLU3_CPT; ++i) {
+        const int c = tid + i * nt;
+        geo[i] = -1;
+        ec[i] = T(0);
+        if (c >= ncell) continue;
+        const int x = c % s, yz = c / s, y = yz % s, zl = yz / s;
+        geo[i] = (zl << 16) | (y << 8) | x;
+        const float kv = a.kappa[((int64_t)(Lf.z + z0 + zl) * a.ny + (Lf.y + y)) * a.nx + (Lf.x + x)];
+        double e;
+        if (!(kv >= 0.0f)) e = 1.0;
+        else if (a.eps_nu == 0.0 || isinf(kv)) e = 0.0;
+        else if (kv == 0.0f) e = 1.0;
+        else e = a.eps_nu / (2.0 * (double)kv + a.eps_nu);
+        ec[i] = (T)e;
+#pragma unroll
+        for (int q = 0; q < Q19; ++q) own[q * P + c] = T(0);       // rest: every deviation zero
+    }
+    unsigned long long t0 = 0;
+    if (r == 0 && tid == 0) {
+        const unsigned long long now = globaltimer3();
+        const unsigned long long prev = atomicCAS(a.t_start, 0ull, now);
+        t0 = prev == 0ull ? now : prev;
+    }
+    cluster_sync_all();
+
+    const int lane = tid & 31, wid = tid >> 5;
+    double prev_u = 0.0;
+    int64_t t = 0;
+    for (;;) {
+        const int64_t nstep = min((int64_t)a.k, a.max_steps - t);
+        for (int64_t i = 0; i < nstep; ++i) {
+            const bool odd = ((t + i) & 1) != 0;
+#pragma unroll
+            for (int j = 0; j < CLU3_CPT; ++j) {
+                if (geo[j] < 0) continue;
+                int gj = geo[j];
+                asm volatile("" : "+r"(gj));     // keeps the addresses out of registers between steps
+                const Cell3<T> q = cell3_of<T>(gj, s, zb, z0);
+                if (odd) aa_step_cell<true>(q, own, P, ec[j], a, d);
+                else aa_step_cell<false>(q, own, P, ec[j], a, d);
+            }
+            cluster_sync_all();
+        }
+        t += nstep;
+
+        // mean flow velocity of the streamed state (Eq. 15), FP64 in a fixed order
+        double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+        const bool odd = (t & 1) != 0;
+#pragma unroll
+        for (int j = 0; j < CLU3_CPT; ++j) {
+            if (geo[j] < 0) continue;
+            int gj = geo[j];
+            asm volatile("" : "+r"(gj));
+            const Cell3<T> q = cell3_of<T>(gj, s, zb, z0);
+            if (odd) aa_velocity_cell<true>(q, own, P, ec[j], a.hg, d, m0, m1, m2);
+            else aa_velocity_cell<false>(q, own, P, ec[j], a.hg, d, m0, m1, m2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            m0 += __shfl_down_sync(0xffffffffu, m0, o);
+            m1 += __shfl_down_sync(0xffffffffu, m1, o);
+            m2 += __shfl_down_sync(0xffffffffu, m2, o);
+        }
+        if (lane == 0) {
+            wred[3 * wid] = m0;
+            wred[3 * wid + 1] = m1;
+            wred[3 * wid + 2] = m2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+            for (int w = 0; w < (nt + 31) / 32; ++w) {
+                u0 += wred[3 * w];
+                u1 += wred[3 * w + 1];
+                u2 += wred[3 * w + 2];
+            }
+            part[0] = u0;
+            part[1] = u1;
+            part[2] = u2;
+            part[3] = 0.0;
+            if (r == 0) {                 // rank 0 decides the wall-clock limit for the cluster
+                if (*(volatile int *)a.abort_flag) part[3] = 1.0;
+                else if (globaltimer3() - t0 > a.time_limit_ns) {
+                    part[3] = 1.0;
+                    atomicExch(a.abort_flag, 1);
+                }
+            }
+        }
+        cluster_sync_all();
+        double m[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < C; ++q) {
+            const uint32_t pq = cluster_addr(part, q);
+            m[0] += ld_cluster<double>(pq);
+            m[1] += ld_cluster<double>(pq + 8);
+            m[2] += ld_cluster<double>(pq + 16);
+        }
+        const bool abort_now = ld_cluster<double>(cluster_addr(part, 0) + 24) != 0.0;
+        const double inv = 1.0 / ((double)s2 * s);
+        for (int q = 0; q < 3; ++q) m[q] *= inv;
+        const double cur = m[d];
+        int st = -1;
+        if (t % a.k == 0) {
+            if (a.tol > 0.0 && t > a.k && fabs(cur - prev_u) <= a.tol * a.k * fabs(cur)) st = LBM_OK;
+            prev_u = cur;
+        }
+        if (st < 0 && t >= a.max_steps) st = a.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
+        if (st < 0 && abort_now) st = LBM_ETIMEOUT;
+        if (st >= 0) {
+            if (r == 0 && tid == 0) {
+                for (int i = 0; i < 3; ++i) a.keff[9 * (int64_t)leaf + 3 * i + d] = a.nu_over_g * m[i];   // Eq. 17
+                if (a.steps) a.steps[3 * (int64_t)leaf + d] = (int)t;
+                if (st != LBM_OK) atomicMax(&a.status[leaf], st);
+            }
+            break;
+        }
+    }
+    cluster_sync_all();     // no CTA leaves while a peer may still read its shared memory
+}
+
+// Shared memory of local3d_cluster_kernel for slabs of P cells
+inline size_t clu3_smem_bytes(int64_t P, size_t esz)
+{
+    return sizeof(double) * (4 + 96 + 16) + (size_t)P * Q19 * esz;
+}
+
+// e per cell of every job of a chunk: job j copies its leaf's cube of the field
+__global__ void __launch_bounds__(256) local3d_coef_kernel(const float *kappa, int nx, int ny, const int4 *leaves,
+                                                           const int *job_leaf, int s, int64_t s3, int njobs,
+                                                           double eps_nu, float *coef_f, double *coef_d)
+{
+    const int64_t total = (int64_t)njobs * s3;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int job = (int)(i / s3);
+        const int64_t c = i - (int64_t)job * s3;
+        const int x = (int)(c % s), yz = (int)(c / s), y = yz % s, z = yz / s;
+        const int4 L = leaves[job_leaf[job]];
+        const float k = kappa[((int64_t)(L.z + z) * ny + (L.y + y)) * nx + (L.x + x)];
+        double e;
+        if (!(k >= 0.0f)) e = 1.0;
+        else if (eps_nu == 0.0 || isinf(k)) e = 0.0;
+        else if (k == 0.0f) e = 1.0;
+        else e = eps_nu / (2.0 * (double)k + eps_nu);
+        if (coef_f) coef_f[i] = (float)e;
+        else coef_d[i] = e;
+    }
+}
+
 }  // namespace
 }  // namespace lbm
 
@@ -305,6 +835,106 @@ void free3(lbm3d_grid *g)
                         #call, cudaGetErrorString(e_));                                          \
         }                                                                                        \
     } while (0)
+
+}  // namespace
+
+namespace {
+
+// Runs every job of one leaf size on the cluster path. Returns LBM_EINVAL (nothing
+// launched) when the cube does not fit the shared memory of a cluster of at most 16
+// CTAs or the device cannot schedule such a cluster.
+lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const int4 *d_l4,
+                            const std::vector<int> &ids, int *d_ids, int sz, double nu, double g_const,
+                            double tol_rel, int64_t max_steps, int32_t check_every, int optin,
+                            unsigned long long *d_clock, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                            cudaStream_t st)
+{
+    const bool f64 = p->storage == LBM_F64;
+    const size_t esz = f64 ? 8 : 4;
+    const int NT = f64 ? clu3_threads<double>() : clu3_threads<float>();
+    const int CPT = f64 ? clu3_cpt<double>() : clu3_cpt<float>();
+    if (sz > 32) return LBM_EINVAL;
+    int C = 0, L = 0;
+    for (int c = 1; c <= 16 && c <= sz; c *= 2) {
+        const int l = (sz + c - 1) / c;
+        const int64_t P = (int64_t)l * sz * sz;
+        if (P <= (int64_t)CPT * NT && clu3_smem_bytes(P, esz) <= (size_t)optin) {
+            C = c;
+            L = l;
+            break;
+        }
+    }
+    if (C == 0) return LBM_EINVAL;
+    const int64_t P = (int64_t)L * sz * sz;
+    const size_t smem = clu3_smem_bytes(P, esz);
+    // enough threads for CPT cells each, whole warps
+    const int nt = (int)std::min<int64_t>(NT, ((P + CPT - 1) / CPT + 31) / 32 * 32);
+    const void *fn = f64 ? reinterpret_cast<const void *>(&local3d_cluster_kernel<double>)
+                         : reinterpret_cast<const void *>(&local3d_cluster_kernel<float>);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return LBM_EINVAL;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3((unsigned)nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return LBM_EINVAL;
+    }
+    const int n = (int)ids.size();
+    if (cudaMemcpyAsync(d_ids, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "copying the leaf list failed");
+    }
+    // launches of at most 2^31 - 1 CTAs, each a whole number of leaves
+    const int64_t leaves_per = std::max<int64_t>(1, (((int64_t)1 << 31) - 1) / (3 * (int64_t)C));
+    for (int64_t l0 = 0; l0 < n; l0 += leaves_per) {
+        const int nl = (int)std::min<int64_t>(leaves_per, n - l0);
+        cfg.gridDim = dim3((unsigned)(3 * (int64_t)nl * C));
+        cudaError_t e;
+        if (f64) {
+            Clu3Args<double> a{kappa_dev, p->nx, p->ny, d_l4, d_ids + l0, 3 * nl, sz, L, 1.0 / p->tau, 2.0 * p->tau,
+                               1.0 - 2.0 * p->tau, 0.5 * p->eps * g_const, p->eps * nu, nu / g_const, tol_rel,
+                               check_every, max_steps, keff_dev, status_dev, steps_dev, d_clock,
+                               reinterpret_cast<int *>(d_clock + 1),
+                               (unsigned long long)(local_time_limit() * 1e9)};
+            e = cudaLaunchKernelEx(&cfg, local3d_cluster_kernel<double>, a);
+        } else {
+            Clu3Args<float> a{kappa_dev, p->nx, p->ny, d_l4, d_ids + l0, 3 * nl, sz, L, (float)(1.0 / p->tau),
+                              (float)(2.0 * p->tau), (float)(1.0 - 2.0 * p->tau), (float)(0.5 * p->eps * g_const),
+                              p->eps * nu, nu / g_const, tol_rel, check_every, max_steps, keff_dev, status_dev,
+                              steps_dev, d_clock, reinterpret_cast<int *>(d_clock + 1),
+                              (unsigned long long)(local_time_limit() * 1e9)};
+            e = cudaLaunchKernelEx(&cfg, local3d_cluster_kernel<float>, a);
+        }
+        count_launches(1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ECUDA, "cluster launch failed: %s", cudaGetErrorString(e));
+        }
+    }
+    unsigned long long clk[2] = {0, 0};
+    if (cudaMemcpyAsync(clk, d_clock, sizeof(clk), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "local problems failed on the device");
+    }
+    if (reinterpret_cast<const int *>(&clk[1])[0])
+        return fail(LBM_ETIMEOUT, "local problems exceeded the time limit; unfinished leaves carry LBM_ETIMEOUT");
+    return LBM_OK;
+}
 
 }  // namespace
 
@@ -419,6 +1049,194 @@ lbm_status lbm3d_mean_velocity(lbm3d_grid *g, double out_mean_uvw[3])
     L3_CUDA(cudaMemcpyAsync(out_mean_uvw, g->mean, sizeof(double) * 3, cudaMemcpyDeviceToHost, g->st));
     L3_CUDA(cudaStreamSynchronize(g->st));
     return LBM_OK;
+}
+
+lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev, const lbm3d_leaf *leaves_dev,
+                                  int32_t n_leaves, double g_const, double tol_rel, int64_t max_steps,
+                                  int32_t check_every, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                                  void *cuda_stream)
+{
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBM_EINVAL, "nx, ny, nz must be >= 1");
+    if (!std::isfinite(p->tau) || p->tau < 0.5) return fail(LBM_EINVAL, "tau must be finite and >= 0.5");
+    if (!std::isfinite(p->nu) || !std::isfinite(p->eps) || p->eps < 0.0)
+        return fail(LBM_EINVAL, "nu must be finite and eps finite and >= 0");
+    if (p->storage != LBM_F32 && p->storage != LBM_F64) return fail(LBM_EINVAL, "storage must be LBM_F32 or LBM_F64");
+    if (n_leaves < 0) return fail(LBM_EINVAL, "n_leaves must be >= 0");
+    if (!std::isfinite(g_const) || g_const == 0.0) return fail(LBM_EINVAL, "g_const must be finite and non-zero");
+    if (!std::isfinite(tol_rel) || tol_rel < 0.0) return fail(LBM_EINVAL, "tol_rel must be finite and >= 0");
+    if (max_steps < 1 || max_steps >= ((int64_t)1 << 31)) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31 - 1]");
+    if (check_every < 1) return fail(LBM_EINVAL, "check_every must be >= 1");
+    if (n_leaves == 0) return LBM_OK;
+    if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(keff_dev) ||
+        !is_device_ptr(status_dev) || (steps_dev && !is_device_ptr(steps_dev)))
+        return fail(LBM_EINVAL, "kappa, leaves, keff, status (and steps) must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<lbm3d_leaf> lv(n_leaves);
+    L3_CUDA(cudaMemcpyAsync(lv.data(), leaves_dev, sizeof(lbm3d_leaf) * n_leaves, cudaMemcpyDeviceToHost, st));
+    L3_CUDA(cudaStreamSynchronize(st));
+    std::map<int, std::vector<int>> by_size;
+    for (int i = 0; i < n_leaves; ++i) {
+        const lbm3d_leaf &L = lv[i];
+        if (L.size < 1 || L.size > 256) return fail(LBM_EINVAL, "leaf %d: size %d outside [1, 256]", i, L.size);
+        if (L.x0 < 0 || L.y0 < 0 || L.z0 < 0 || (int64_t)L.x0 + L.size > p->nx || (int64_t)L.y0 + L.size > p->ny ||
+            (int64_t)L.z0 + L.size > p->nz)
+            return fail(LBM_EINVAL, "leaf %d (%d, %d, %d, %d) lies outside the field", i, L.x0, L.y0, L.z0, L.size);
+        by_size[L.size].push_back(i);
+    }
+    L3_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int32_t) * n_leaves, st));
+    if (steps_dev) L3_CUDA(cudaMemsetAsync(steps_dev, 0, sizeof(int32_t) * 3 * n_leaves, st));
+    const double nu = p->nu < 0.0 ? (p->tau - 0.5) / 3.0 : p->nu;
+    const bool f64 = p->storage == LBM_F64;
+    const size_t esz = f64 ? 8 : 4;
+    std::vector<int4> l4(n_leaves);
+    for (int i = 0; i < n_leaves; ++i) l4[i] = make_int4(lv[i].x0, lv[i].y0, lv[i].z0, lv[i].size);
+
+    // device scratch, sized for the largest chunk and freed on every exit
+    int4 *d_l4 = nullptr;
+    void *buf[2] = {nullptr, nullptr};
+    void *coef = nullptr;
+    int *d_active = nullptr, *d_list = nullptr, *d_jl = nullptr, *d_nact = nullptr, *d_ids = nullptr;
+    double *d_prev = nullptr;
+    unsigned long long *d_clock = nullptr;    // [0] launch start (globaltimer), [1] abort flag
+    auto release = [&]() {
+        cudaFree(d_l4); cudaFree(buf[0]); cudaFree(buf[1]); cudaFree(coef);
+        cudaFree(d_active); cudaFree(d_list); cudaFree(d_jl); cudaFree(d_nact); cudaFree(d_prev);
+        cudaFree(d_ids); cudaFree(d_clock);
+        cudaGetLastError();
+    };
+#define L3_CUDA2(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            release();                                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s failed: %s", \
+                        #call, cudaGetErrorString(e_));                                          \
+        }                                                                                        \
+    } while (0)
+    L3_CUDA2(cudaMalloc(&d_l4, sizeof(int4) * n_leaves));
+    L3_CUDA2(cudaMemcpyAsync(d_l4, l4.data(), sizeof(int4) * n_leaves, cudaMemcpyHostToDevice, st));
+    L3_CUDA2(cudaMalloc(&d_nact, sizeof(int)));
+    L3_CUDA2(cudaMalloc(&d_ids, sizeof(int) * n_leaves));
+    L3_CUDA2(cudaMalloc(&d_clock, 2 * sizeof(unsigned long long)));
+    L3_CUDA2(cudaMemsetAsync(d_clock, 0, 2 * sizeof(unsigned long long), st));
+    int dev = 0, optin = 0;
+    L3_CUDA2(cudaGetDevice(&dev));
+    L3_CUDA2(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const char *force_global = std::getenv("LBM_LOCAL3_GLOBAL");
+    const bool cluster_ok = !(force_global && force_global[0] == '1');
+    constexpr int64_t CELL_BUDGET = (int64_t)1 << 26;     // cells per chunk (10 GB of FP32 state)
+    int64_t cap_cells = 0, cap_jobs = 0;
+    for (const auto &kv : by_size) {
+        const int sz = kv.first;
+        const int64_t s3 = (int64_t)sz * sz * sz;
+        if (cluster_ok) {
+            const lbm_status cs = run_cluster_size(p, kappa_dev, d_l4, kv.second, d_ids, sz, nu, g_const, tol_rel,
+                                                   max_steps, check_every, optin, d_clock, keff_dev, status_dev,
+                                                   steps_dev, st);
+            // LBM_ETIMEOUT is in the leaves' status already; LBM_EINVAL: the cube does not fit, take the global path
+            if (cs == LBM_OK || cs == LBM_ETIMEOUT) continue;
+            if (cs != LBM_EINVAL) {
+                release();
+                return cs;
+            }
+        }
+        // jobs per chunk: a multiple of 3, so that a job's drive axis is its chunk index modulo 3
+        const int64_t per = std::max<int64_t>(3, std::min<int64_t>(65535, CELL_BUDGET / s3) / 3 * 3);
+        const std::vector<int> &ids = kv.second;
+        const int64_t njobs_all = 3 * (int64_t)ids.size();
+        for (int64_t j0 = 0; j0 < njobs_all; j0 += per) {
+            const int njobs = (int)std::min<int64_t>(per, njobs_all - j0);
+            const int64_t cells = (int64_t)njobs * s3, plane = (cells + 63) / 64 * 64;
+            if (plane > cap_cells || njobs > cap_jobs) {   // grow the scratch
+                cudaFree(buf[0]); cudaFree(buf[1]); cudaFree(coef); cudaFree(d_active); cudaFree(d_list);
+                cudaFree(d_jl); cudaFree(d_prev);
+                buf[0] = buf[1] = coef = nullptr;
+                d_active = d_list = d_jl = nullptr;
+                d_prev = nullptr;
+                cap_cells = std::max(cap_cells, plane);
+                cap_jobs = std::max<int64_t>(cap_jobs, njobs);
+                L3_CUDA2(cudaMalloc(&buf[0], Q19 * cap_cells * esz));
+                L3_CUDA2(cudaMalloc(&buf[1], Q19 * cap_cells * esz));
+                L3_CUDA2(cudaMalloc(&coef, cap_cells * esz));
+                L3_CUDA2(cudaMalloc(&d_active, sizeof(int) * cap_jobs));
+                L3_CUDA2(cudaMalloc(&d_list, sizeof(int) * cap_jobs));
+                L3_CUDA2(cudaMalloc(&d_jl, sizeof(int) * cap_jobs));
+                L3_CUDA2(cudaMalloc(&d_prev, sizeof(double) * cap_jobs));
+            }
+            std::vector<int> jl(njobs), act(njobs, 1), list(njobs);
+            for (int j = 0; j < njobs; ++j) {
+                jl[j] = ids[(size_t)((j0 + j) / 3)];
+                list[j] = j;
+            }
+            L3_CUDA2(cudaMemcpyAsync(d_list, list.data(), sizeof(int) * njobs, cudaMemcpyHostToDevice, st));
+            L3_CUDA2(cudaMemcpyAsync(d_jl, jl.data(), sizeof(int) * njobs, cudaMemcpyHostToDevice, st));
+            L3_CUDA2(cudaMemcpyAsync(d_active, act.data(), sizeof(int) * njobs, cudaMemcpyHostToDevice, st));
+            L3_CUDA2(cudaMemsetAsync(d_prev, 0, sizeof(double) * njobs, st));
+            L3_CUDA2(cudaMemsetAsync(buf[0], 0, Q19 * plane * esz, st));
+            L3_CUDA2(cudaMemsetAsync(buf[1], 0, Q19 * plane * esz, st));
+            int nact = njobs;
+            L3_CUDA2(cudaMemcpyAsync(d_nact, &nact, sizeof(int), cudaMemcpyHostToDevice, st));
+            const int nb = (int)std::min<int64_t>((cells + 255) / 256, 8192);
+            local3d_coef_kernel<<<nb, 256, 0, st>>>(kappa_dev, p->nx, p->ny, d_l4, d_jl, sz, s3, njobs, p->eps * nu,
+                                                    f64 ? nullptr : static_cast<float *>(coef),
+                                                    f64 ? static_cast<double *>(coef) : nullptr);
+            count_launches(1);
+            int cur = 0, nlist = njobs;    // blocks go to the nlist jobs of d_list only
+            int64_t t = 0;
+            while (t < max_steps && nact > 0) {
+                const int64_t nstep = std::min<int64_t>(check_every, max_steps - t);
+                const dim3 sgrid((unsigned)((s3 + 255) / 256), (unsigned)nlist);
+                for (int64_t i = 0; i < nstep; ++i) {
+                    if (f64) {
+                        Local3Args<double> a{static_cast<const double *>(buf[cur]), static_cast<double *>(buf[1 - cur]),
+                                             static_cast<const double *>(coef), d_list, sz, s3, plane,
+                                             1.0 / p->tau, 2.0 * p->tau, 1.0 - 2.0 * p->tau, 0.5 * p->eps * g_const};
+                        local3d_step_kernel<double><<<sgrid, 256, 0, st>>>(a);
+                    } else {
+                        Local3Args<float> a{static_cast<const float *>(buf[cur]), static_cast<float *>(buf[1 - cur]),
+                                            static_cast<const float *>(coef), d_list, sz, s3, plane,
+                                            (float)(1.0 / p->tau), (float)(2.0 * p->tau), (float)(1.0 - 2.0 * p->tau),
+                                            (float)(0.5 * p->eps * g_const)};
+                        local3d_step_kernel<float><<<sgrid, 256, 0, st>>>(a);
+                    }
+                    cur = 1 - cur;
+                }
+                t += nstep;
+                Check3 ck{(int)t, check_every, t % check_every == 0 ? 1 : 0, max_steps, tol_rel, nu / g_const,
+                          d_active, d_prev, d_jl, keff_dev, status_dev, steps_dev, d_nact};
+                if (f64) {
+                    Local3Args<double> a{static_cast<const double *>(buf[cur]), nullptr, static_cast<const double *>(coef),
+                                         d_list, sz, s3, plane, 1.0 / p->tau, 2.0 * p->tau, 1.0 - 2.0 * p->tau,
+                                         0.5 * p->eps * g_const};
+                    local3d_check_kernel<double><<<nlist, 256, 0, st>>>(a, ck);
+                } else {
+                    Local3Args<float> a{static_cast<const float *>(buf[cur]), nullptr, static_cast<const float *>(coef),
+                                        d_list, sz, s3, plane, (float)(1.0 / p->tau), (float)(2.0 * p->tau),
+                                        (float)(1.0 - 2.0 * p->tau), (float)(0.5 * p->eps * g_const)};
+                    local3d_check_kernel<float><<<nlist, 256, 0, st>>>(a, ck);
+                }
+                count_launches(nstep + 1);
+                L3_CUDA2(cudaGetLastError());
+                L3_CUDA2(cudaMemcpyAsync(&nact, d_nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+                L3_CUDA2(cudaStreamSynchronize(st));
+                if (nact > 0 && nact < nlist) {    // drop the finished jobs from the launch grid
+                    local3d_compact_kernel<<<1, 1024, 0, st>>>(d_active, njobs, d_list);
+                    count_launches(1);
+                    L3_CUDA2(cudaGetLastError());
+                    nlist = nact;
+                }
+            }
+        }
+    }
+    std::vector<int32_t> stat(n_leaves);
+    L3_CUDA2(cudaMemcpyAsync(stat.data(), status_dev, sizeof(int32_t) * n_leaves, cudaMemcpyDeviceToHost, st));
+    L3_CUDA2(cudaStreamSynchronize(st));
+    release();
+    int worst = LBM_OK;
+    for (int v : stat) worst = std::max(worst, v);
+    return (lbm_status)worst;
 }
 
 }  // extern "C"

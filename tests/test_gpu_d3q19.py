@@ -104,3 +104,104 @@ def test_d3q19_rejects_bad_input():
         lbm.Grid3D(lbm.Params3D(nx=4, ny=4, nz=4, tau=1.0), kap)
     with pytest.raises(lbm.LbmError):
         lbm.Grid3D(lbm.Params3D(nx=4, ny=4, nz=4, tau=0.4), torch.full((4, 4, 4), 0.01, device="cuda"))
+
+
+# ------------------------------------------------- three-dimensional local problems
+
+def gpu_keff3(kap, leaves, tau, nu, eps, g, tol, max_steps, storage=0, k=64):
+    import torch
+    lbm = _lbm()
+    nz, ny, nx = kap.shape
+    p = lbm.Params3D(nx=nx, ny=ny, nz=nz, tau=tau, nu=nu, eps=eps, storage=storage)
+    ke, st, steps, worst = lbm.local_keff3(p, torch.from_numpy(np.ascontiguousarray(kap, dtype=np.float32)).cuda(),
+                                           torch.from_numpy(np.asarray(leaves, dtype=np.int32)).cuda(), g, tol,
+                                           max_steps, k)
+    return ke.cpu().numpy(), st.cpu().numpy(), steps.cpu().numpy(), worst
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_local_keff3_matches_oracle(storage):
+    """Mixed cube sizes at fixed step counts (every drive the same number of steps on both sides)."""
+    kap = _field(12, 14, 16, seed=71)
+    leaves = [(0, 0, 0, 4), (8, 6, 4, 8), (3, 2, 1, 5), (12, 10, 8, 4), (0, 0, 0, 12)]
+    ke, st, steps, _ = gpu_keff3(kap, leaves, 1.0, 1.0 / 6.0, 1.0, 1e-6, 0.0, 600, storage)
+    assert (steps == 600).all() and (st == 0).all()
+    for i, (x0, y0, z0, s) in enumerate(leaves):
+        cube = kap[z0:z0 + s, y0:y0 + s, x0:x0 + s].astype(np.float64)
+        ref = oracle.local_keff3(cube, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=0.0, max_steps=600)["keff"]
+        scale = np.abs(np.diag(ref)).max()
+        tol = 1e-9 if storage == 2 else 1e-5
+        np.testing.assert_allclose(ke[i], ref, rtol=0, atol=tol * scale)
+
+
+def test_local_keff3_tolerance_stop_and_uniform_cube():
+    """The stop rule gives the oracle's step counts; a uniform cube gives kappa I (Eq. 19 in 3-D)."""
+    kap = _field(8, 8, 8, seed=72)
+    kap[:4, :4, :4] = 3e-3
+    leaves = [(0, 0, 0, 4), (0, 0, 0, 8)]
+    ke, st, steps, worst = gpu_keff3(kap, leaves, 1.0, 1.0 / 6.0, 1.0, 1e-6, 1e-7, 100000, storage=2)
+    # stopped at tol 1e-7 per 64 steps, the uniform cube is within 1e-6 of its steady kappa
+    np.testing.assert_allclose(np.diag(ke[0]), float(np.float32(3e-3)), rtol=1e-6)
+    for i, (x0, y0, z0, s) in enumerate(leaves):
+        ref = oracle.local_keff3(kap[z0:z0 + s, y0:y0 + s, x0:x0 + s].astype(np.float64), 1.0, 1.0 / 6.0, 1.0,
+                                 1e-6, tol=1e-7, max_steps=100000)
+        assert list(steps[i]) == ref["steps"]
+        np.testing.assert_allclose(ke[i], ref["keff"], rtol=0, atol=1e-9 * np.abs(ref["keff"]).max())
+    assert worst == 0 and (st == 0).all()
+
+
+def test_local_keff3_rejects_bad_leaves():
+    import torch
+    lbm = _lbm()
+    kap = torch.full((8, 8, 8), 0.01, device="cuda")
+    p = lbm.Params3D(nx=8, ny=8, nz=8, tau=1.0)
+    for bad in ([[4, 0, 0, 5]], [[0, 0, 0, 0]], [[-1, 0, 0, 2]]):
+        with pytest.raises(lbm.LbmError):
+            lbm.local_keff3(p, kap, torch.tensor(bad, dtype=torch.int32, device="cuda"))
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_local_keff3_cluster_slabs_match_oracle(storage):
+    """Cubes wider than one CTA's shared memory: 16 and 15 cells (two slabs in FP32, four in
+    FP64; 15 leaves the last slab one layer short) and 32 cells (sixteen slabs in FP32)."""
+    kap = _field(32, 32, 32, seed=73)
+    kap[20, 5, 17] = 0.0
+    leaves = [(0, 0, 0, 16), (16, 8, 3, 15), (0, 0, 0, 32)]
+    ke, st, steps, _ = gpu_keff3(kap, leaves, 0.8, 0.1, 0.9, 2e-6, 0.0, 300, storage)
+    assert (steps == 300).all() and (st == 0).all()
+    for i, (x0, y0, z0, s) in enumerate(leaves):
+        cube = kap[z0:z0 + s, y0:y0 + s, x0:x0 + s].astype(np.float64)
+        ref = oracle.local_keff3(cube, 0.8, 0.1, 0.9, 2e-6, tol=0.0, max_steps=300)["keff"]
+        scale = np.abs(np.diag(ref)).max()
+        np.testing.assert_allclose(ke[i], ref, rtol=0, atol=(1e-9 if storage == 2 else 1e-5) * scale)
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_local_keff3_cluster_and_global_paths_agree(storage, monkeypatch):
+    """The shared-memory (cluster) path and the HBM path take the same arithmetic per cell;
+    only the order of the FP64 velocity sums differs."""
+    kap = _field(16, 16, 16, seed=74)
+    leaves = [(0, 0, 0, 16), (4, 4, 4, 8), (1, 2, 3, 11), (0, 0, 0, 3)]
+    a = gpu_keff3(kap, leaves, 1.0, 1.0 / 6.0, 1.0, 1e-6, 0.0, 257, storage, k=16)
+    monkeypatch.setenv("LBM_LOCAL3_GLOBAL", "1")
+    b = gpu_keff3(kap, leaves, 1.0, 1.0 / 6.0, 1.0, 1e-6, 0.0, 257, storage, k=16)
+    assert (a[2] == 257).all() and (b[2] == 257).all()
+    scale = np.abs(np.diagonal(b[0], axis1=1, axis2=2)).max()
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-12 * scale)
+
+
+def test_local_keff3_time_limit_gives_etimeout():
+    """The launch's wall-clock bound on the cluster path: with a tiny limit every cluster
+    abandons its job at its next check and the host sees LBM_ETIMEOUT; the context stays usable."""
+    lbm = _lbm()
+    kap = _field(32, 32, 32, seed=75)
+    leaves = [(x, y, z, 16) for z in (0, 16) for y in (0, 16) for x in (0, 16)]
+    try:
+        lbm.lbm_set_time_limit(2e-4)
+        ke, st, steps, worst = gpu_keff3(kap, leaves, 1.0, 1.0 / 6.0, 1.0, 1e-6, 1e-14, 10_000_000)
+        assert worst == lbm.LBM_ETIMEOUT
+        assert (st == lbm.LBM_ETIMEOUT).all()
+    finally:
+        lbm.lbm_set_time_limit(600.0)
+    ke, st, steps, worst = gpu_keff3(kap, leaves[:2], 1.0, 1.0 / 6.0, 1.0, 1e-6, 0.0, 100)
+    assert worst == 0 and np.isfinite(ke).all()
