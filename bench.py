@@ -658,6 +658,8 @@ def main(argv=None):
                     help="profiling mode: one surrogate training step (one model) on this many patches, exit")
     ap.add_argument("--profile-3d", type=int, default=0,
                     help="profiling mode: this many cells per side of a D3Q19 box, 8 steps, exit")
+    ap.add_argument("--profile-local3d", type=int, default=0,
+                    help="profiling mode: this many 16^3 cubes of a 256^3 field, three drives, 512 fixed steps, exit")
     ap.add_argument("--profile-surrogate", type=int, default=0,
                     help="profiling mode: ensemble inference on this many 32x32 patches, exit")
     ap.add_argument("--pipeline", type=int, default=0,
@@ -680,6 +682,8 @@ def main(argv=None):
         return run_profile_surrogate(args, local)
     if args.profile_3d > 0:
         return run_profile_3d(args, local)
+    if args.profile_local3d > 0:
+        return run_profile_local3d(args, local)
     if args.profile_train > 0:
         return run_profile_train(args, local)
     return run_ours(args, ws, rank, local)
@@ -813,6 +817,22 @@ def run_profile_3d(args, local):
     kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
     with lbm.Grid3D(lbm.Params3D(nx=n, ny=n, nz=n, tau=TAU, nu=NU, eps=1.0, gx=1e-6), kap) as g:
         g.step(8)
+    torch.cuda.synchronize()
+    return 0
+
+
+def run_profile_local3d(args, local):
+    """Fixed launch sequence for ncu: the first profile_local3d 16^3 cubes of the 256^3 D3Q19 field of
+    the bench's d3q19 block, three drives each, 512 steps with no stopping test."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    import synth
+    torch.cuda.set_device(local)
+    n, b = 256, 16
+    kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
+    cubes = [(x, y, z, b) for z in range(0, n, b) for y in range(0, n, b) for x in range(0, n, b)]
+    leaves = torch.tensor(cubes[: args.profile_local3d], dtype=torch.int32, device="cuda")
+    lbm.local_keff3(lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0), kap, leaves, 1e-6, 0.0, 512, 64)
     torch.cuda.synchronize()
     return 0
 
