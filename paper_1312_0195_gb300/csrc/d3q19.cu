@@ -41,13 +41,6 @@ __host__ __device__ constexpr int cz(int a)
 {
     return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1 : ((a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0);
 }
-__host__ __device__ constexpr double w19(int a) { return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
-
-// a +/- v for a component c in {-1, 0, 1} known at compile time (no multiplication by 0 or 1)
-template <int C, typename T> __device__ __forceinline__ T addc(T acc, T v)
-{
-    return C == 1 ? acc + v : (C == -1 ? acc - v : acc);
-}
 
 template <typename T>
 struct Step3Args {
@@ -56,7 +49,7 @@ struct Step3Args {
     const T *coef;          // e per cell
     int nx, ny, nz;
     int64_t plane;          // elements per population plane
-    T omega, two_tau, omt, hgx, hgy, hgz;   // 1/tau, 2 tau, 1 - 2 tau, eps G / 2
+    T omega, k_ru, k_j, hgx, hgy, hgz;   // 1/tau, 6 tau, 3 (1 - 2 tau), eps G / 2
 };
 
 // Index of cell (x - e_x, y - e_y, z - e_z) from the wrapped neighbour offsets.
@@ -97,40 +90,70 @@ template <typename T> __device__ __forceinline__ void pull19(const T *src, int64
     pull_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(src, plane, nb, g);
 }
 
-template <int A, typename T> __device__ __forceinline__ void moment_one(const T (&g)[Q19], T &d, T &jx, T &jy, T &jz)
-{
-    d += g[A];
-    jx = addc<cx(A)>(jx, g[A]);
-    jy = addc<cy(A)>(jy, g[A]);
-    jz = addc<cz(A)>(jz, g[A]);
-}
-template <typename T, int... As>
-__device__ __forceinline__ void moments_all(const T (&g)[Q19], T &d, T &jx, T &jy, T &jz)
-{
-    (moment_one<As>(g, d, jx, jy, jz), ...);
-}
+// Moments through the nine opposite pairs (a, a + 1): s_p = g_a + g_{a+1} and
+// d_p = g_a - g_{a+1}. The pairs point along x, y, z, (x, y), (x, -y), (x, z),
+// (x, -z), (y, z) and (y, -z), which the asserts tie to the velocity table.
+static_assert(cx(1) == 1 && cy(3) == 1 && cz(5) == 1, "face pairs");
+static_assert(cx(7) == 1 && cy(7) == 1 && cx(9) == 1 && cy(9) == -1, "xy edge pairs");
+static_assert(cx(11) == 1 && cz(11) == 1 && cx(13) == 1 && cz(13) == -1, "xz edge pairs");
+static_assert(cy(15) == 1 && cz(15) == 1 && cy(17) == 1 && cz(17) == -1, "yz edge pairs");
+static_assert(cx(2) == -1 && cy(4) == -1 && cz(6) == -1 && cx(8) == -1 && cy(8) == -1 && cx(10) == -1 &&
+                  cy(10) == 1 && cx(12) == -1 && cz(12) == -1 && cx(14) == -1 && cz(14) == 1 && cy(16) == -1 &&
+                  cz(16) == -1 && cy(18) == -1 && cz(18) == 1,
+              "a + 1 is opposite to a");
+static_assert(cz(1) == 0 && cz(7) == 0 && cz(9) == 0 && cy(11) == 0 && cy(13) == 0 && cx(15) == 0 && cx(17) == 0,
+              "edge pairs lie in their planes");
+
 // drho = sum_a g_a and j = sum_a e_a g_a
-template <typename T> __device__ __forceinline__ void moments19(const T (&g)[Q19], T &d, T &jx, T &jy, T &jz)
+template <typename T> __device__ __forceinline__ void moments19(const T (&g)[Q19], T &drho, T &jx, T &jy, T &jz)
 {
-    d = T(0);
-    jx = jy = jz = T(0);
-    moments_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(g, d, jx, jy, jz);
+    T s[9], d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        s[p] = g[2 * p + 1] + g[2 * p + 2];
+        d[p] = g[2 * p + 1] - g[2 * p + 2];
+    }
+    drho = g[0] + ((((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]))) + s[8]);
+    jx = d[0] + ((d[3] + d[4]) + (d[5] + d[6]));
+    jy = d[1] + ((d[3] - d[4]) + (d[7] + d[8]));
+    jz = d[2] + ((d[5] - d[6]) + (d[7] - d[8]));
 }
 
-template <int A, typename T>
-__device__ __forceinline__ void relax_one(T (&g)[Q19], T drho, T ux, T uy, T uz, T om)
+// BGK (Eq. 13) in difference form for an opposite pair whose equilibria (Eq. 2) are
+// w drho +/- w eu: g + om (w drho - g +/- w eu), with wd = w drho.
+template <typename T> __device__ __forceinline__ void relax_pair(T &gp, T &gm, T wd, T w, T eu, T om)
 {
-    T eu = T(0);
-    eu = addc<cx(A)>(eu, ux);
-    eu = addc<cy(A)>(eu, uy);
-    eu = addc<cz(A)>(eu, uz);
-    const T geq = T(w19(A)) * (drho + eu);                // ux, uy, uz carry the factor 3 already
-    g[A] = fma(om, geq - g[A], g[A]);
+    gp = fma(om, fma(w, eu, wd - gp), gp);
+    gm = fma(om, fma(-w, eu, wd - gm), gm);
 }
-template <typename T, int... As>
-__device__ __forceinline__ void relax_all(T (&g)[Q19], T drho, T ux, T uy, T uz, T om)
+// All 19 populations; ux, uy, uz are 3 rho u_eq (Eq. 16 times 3), so e_a . u is the eu above.
+template <typename T> __device__ __forceinline__ void relax19(T (&g)[Q19], T drho, T ux, T uy, T uz, T om)
 {
-    (relax_one<As>(g, drho, ux, uy, uz, om), ...);
+    const T w0 = T(1.0 / 3.0), w1 = T(1.0 / 18.0), w2 = T(1.0 / 36.0);
+    const T d1 = w1 * drho, d2 = w2 * drho;
+    g[0] = fma(om, fma(w0, drho, -g[0]), g[0]);
+    relax_pair(g[1], g[2], d1, w1, ux, om);
+    relax_pair(g[3], g[4], d1, w1, uy, om);
+    relax_pair(g[5], g[6], d1, w1, uz, om);
+    relax_pair(g[7], g[8], d2, w2, ux + uy, om);
+    relax_pair(g[9], g[10], d2, w2, ux - uy, om);
+    relax_pair(g[11], g[12], d2, w2, ux + uz, om);
+    relax_pair(g[13], g[14], d2, w2, ux - uz, om);
+    relax_pair(g[15], g[16], d2, w2, uy + uz, om);
+    relax_pair(g[17], g[18], d2, w2, uy - uz, om);
+}
+
+// The whole collision of one cell: moments, r = j + (eps G / 2) rho, rho u = (1 - e) r
+// (Eq. 6 times rho), 3 rho u_eq = 6 tau rho u + 3 (1 - 2 tau) j (Eq. 16 times 3), relax.
+template <typename T>
+__device__ __forceinline__ void collide19(T (&g)[Q19], T e, T hgx, T hgy, T hgz, T k_ru, T k_j, T om)
+{
+    T drho, jx, jy, jz;
+    moments19(g, drho, jx, jy, jz);
+    const T rho = T(1) + drho;
+    const T rx = fma(hgx, rho, jx), ry = fma(hgy, rho, jy), rz = fma(hgz, rho, jz);
+    const T rux = fma(-e, rx, rx), ruy = fma(-e, ry, ry), ruz = fma(-e, rz, rz);
+    relax19(g, drho, fma(k_ru, rux, k_j * jx), fma(k_ru, ruy, k_j * jy), fma(k_ru, ruz, k_j * jz), om);
 }
 
 template <typename T>
@@ -145,16 +168,7 @@ __global__ void __launch_bounds__(256) step3d_kernel(Step3Args<T> a)
     pull19(src, a.plane, nb, g);
     const int64_t c = nb.z[1] + nb.y[1] + x;
     const T e = __ldg(a.coef + c);
-    T drho, jx, jy, jz;
-    moments19(g, drho, jx, jy, jz);
-    const T rho = T(1) + drho;
-    const T rx = fma(a.hgx, rho, jx), ry = fma(a.hgy, rho, jy), rz = fma(a.hgz, rho, jz);
-    const T rux = fma(-e, rx, rx), ruy = fma(-e, ry, ry), ruz = fma(-e, rz, rz);       // Eq. 6 times rho
-    // 3 rho u_eq (Eq. 16 times 3 rho), so that g_eq = w (drho + e . (3 rho u_eq))
-    const T u3x = T(3) * fma(a.two_tau, rux, a.omt * jx);
-    const T u3y = T(3) * fma(a.two_tau, ruy, a.omt * jy);
-    const T u3z = T(3) * fma(a.two_tau, ruz, a.omt * jz);
-    relax_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(g, drho, u3x, u3y, u3z, a.omega);
+    collide19(g, e, a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega);
 #pragma unroll
     for (int q = 0; q < Q19; ++q) dst[q * a.plane + c] = g[q];
 }
@@ -260,7 +274,7 @@ struct Local3Args {
     const int *list;        // [blocks along y] the jobs still running
     int s;
     int64_t s3, plane;
-    T omega, two_tau, omt, hg;   // hg = eps G / 2 along the job's drive axis
+    T omega, k_ru, k_j, hg;      // 1/tau, 6 tau, 3 (1 - 2 tau); hg = eps G / 2 along the job's drive axis
 };
 
 // Neighbours within cube `job` (periodic on the cube): base offset folded into the z row.
@@ -296,17 +310,7 @@ __global__ void __launch_bounds__(256) local3d_step_kernel(Local3Args<T> a)
     pull19(src, a.plane, nb, g);
     const T e = __ldg(a.coef + base + c);
     const int d = job % 3;
-    T drho, jx, jy, jz;
-    moments19(g, drho, jx, jy, jz);
-    const T rho = T(1) + drho;
-    const T rx = d == 0 ? fma(a.hg, rho, jx) : jx;
-    const T ry = d == 1 ? fma(a.hg, rho, jy) : jy;
-    const T rz = d == 2 ? fma(a.hg, rho, jz) : jz;
-    const T rux = fma(-e, rx, rx), ruy = fma(-e, ry, ry), ruz = fma(-e, rz, rz);
-    const T u3x = T(3) * fma(a.two_tau, rux, a.omt * jx);
-    const T u3y = T(3) * fma(a.two_tau, ruy, a.omt * jy);
-    const T u3z = T(3) * fma(a.two_tau, ruz, a.omt * jz);
-    relax_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(g, drho, u3x, u3y, u3z, a.omega);
+    collide19(g, e, d == 0 ? a.hg : T(0), d == 1 ? a.hg : T(0), d == 2 ? a.hg : T(0), a.k_ru, a.k_j, a.omega);
 #pragma unroll
     for (int q = 0; q < Q19; ++q) dst[q * a.plane + base + c] = g[q];
 }
@@ -420,7 +424,7 @@ struct Clu3Args {
     const int4 *leaves;     // all leaves of the call
     const int *ids;         // [njobs / 3] leaf indices of this size
     int njobs, s, L;
-    T omega, two_tau, omt, hg;
+    T omega, k_ru, k_j, hg;      // 1/tau, 6 tau, 3 (1 - 2 tau), eps G / 2
     double eps_nu, nu_over_g, tol;
     int k;
     int64_t max_steps;
@@ -503,32 +507,33 @@ struct Cell3 {
     }
 };
 
-template <bool ODD, int A, typename T>
-__device__ __forceinline__ void aa_read_one(const Cell3<T> &q, const T *own, int P, T (&g)[Q19])
+// PS is the slot stride in cells (compile time, so slot offsets are immediates)
+template <bool ODD, int PS, int A, typename T>
+__device__ __forceinline__ void aa_read_one(const Cell3<T> &q, const T *own, T (&g)[Q19])
 {
-    if (ODD) g[A] = ld_cluster<T>(q.template from<A>(P * (uint32_t)sizeof(T)));
-    else g[A] = own[A * P + q.c];
+    if (ODD) g[A] = ld_cluster<T>(q.template from<A>(PS * (uint32_t)sizeof(T)));
+    else g[A] = own[A * PS + q.c];
 }
-template <bool ODD, int A, typename T>
-__device__ __forceinline__ void aa_write_one(const Cell3<T> &q, T *own, int P, const T (&g)[Q19])
+template <bool ODD, int PS, int A, typename T>
+__device__ __forceinline__ void aa_write_one(const Cell3<T> &q, T *own, const T (&g)[Q19])
 {
-    if (ODD) st_cluster(q.template to<A>(P * (uint32_t)sizeof(T)), g[A]);
-    else own[opp19(A) * P + q.c] = g[A];
+    if (ODD) st_cluster(q.template to<A>(PS * (uint32_t)sizeof(T)), g[A]);
+    else own[opp19(A) * PS + q.c] = g[A];
 }
-template <bool ODD, typename T, int... As>
-__device__ __forceinline__ void aa_read(const Cell3<T> &q, const T *own, int P, T (&g)[Q19])
+template <bool ODD, int PS, typename T, int... As>
+__device__ __forceinline__ void aa_read(const Cell3<T> &q, const T *own, T (&g)[Q19])
 {
-    (aa_read_one<ODD, As>(q, own, P, g), ...);
+    (aa_read_one<ODD, PS, As>(q, own, g), ...);
 }
-template <bool ODD, typename T, int... As>
-__device__ __forceinline__ void aa_write(const Cell3<T> &q, T *own, int P, const T (&g)[Q19])
+template <bool ODD, int PS, typename T, int... As>
+__device__ __forceinline__ void aa_write(const Cell3<T> &q, T *own, const T (&g)[Q19])
 {
-    (aa_write_one<ODD, As>(q, own, P, g), ...);
+    (aa_write_one<ODD, PS, As>(q, own, g), ...);
 }
-template <bool ODD, typename T>
-__device__ __forceinline__ void aa_read19(const Cell3<T> &q, const T *own, int P, T (&g)[Q19])
+template <bool ODD, int PS, typename T>
+__device__ __forceinline__ void aa_read19(const Cell3<T> &q, const T *own, T (&g)[Q19])
 {
-    aa_read<ODD, T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(q, own, P, g);
+    aa_read<ODD, PS, T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(q, own, g);
 }
 
 // moments of g plus the drag-reduced momentum (1 - e) r, r = j + hg rho along the drive axis d
@@ -546,26 +551,21 @@ __device__ __forceinline__ void drag_momentum(const T (&g)[Q19], T e, T hg, int 
     ruz = fma(-e, rz, rz);
 }
 
-template <bool ODD, typename T>
-__device__ __forceinline__ void aa_step_cell(const Cell3<T> &q, T *own, int P, T e, const Clu3Args<T> &a, int d)
+template <bool ODD, int PS, typename T>
+__device__ __forceinline__ void aa_step_cell(const Cell3<T> &q, T *own, T e, const Clu3Args<T> &a, T hgx, T hgy, T hgz)
 {
     T g[Q19];
-    aa_read19<ODD>(q, own, P, g);
-    T drho, jx, jy, jz, rux, ruy, ruz;
-    drag_momentum(g, e, a.hg, d, drho, jx, jy, jz, rux, ruy, ruz);
-    const T u3x = T(3) * fma(a.two_tau, rux, a.omt * jx);
-    const T u3y = T(3) * fma(a.two_tau, ruy, a.omt * jy);
-    const T u3z = T(3) * fma(a.two_tau, ruz, a.omt * jz);
-    relax_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(g, drho, u3x, u3y, u3z, a.omega);
-    aa_write<ODD, T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(q, own, P, g);
+    aa_read19<ODD, PS>(q, own, g);
+    collide19(g, e, hgx, hgy, hgz, a.k_ru, a.k_j, a.omega);
+    aa_write<ODD, PS, T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(q, own, g);
 }
 
-template <bool ODD, typename T>
-__device__ __forceinline__ void aa_velocity_cell(const Cell3<T> &q, const T *own, int P, T e, T hg, int d,
+template <bool ODD, int PS, typename T>
+__device__ __forceinline__ void aa_velocity_cell(const Cell3<T> &q, const T *own, T e, T hg, int d,
                                                  double &m0, double &m1, double &m2)
 {
     T g[Q19];
-    aa_read19<ODD>(q, own, P, g);
+    aa_read19<ODD, PS>(q, own, g);
     T drho, jx, jy, jz, rux, ruy, ruz;
     drag_momentum(g, e, hg, d, drho, jx, jy, jz, rux, ruy, ruz);
     const T rho = T(1) + drho;
@@ -598,7 +598,7 @@ __device__ __forceinline__ Cell3<T> cell3_of(int geo, int s, const uint32_t *zb,
     return q;
 }
 
-template <typename T>
+template <typename T, int PS>
 __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(Clu3Args<T> a)
 {
     constexpr int CLU3_CPT = clu3_cpt<T>();
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
     const int job = (int)(blockIdx.x / (unsigned)C);
     const int leaf = a.ids[job / 3], d = job % 3;
     const int s = a.s, s2 = s * s, L = a.L;
-    const int P = L * s2;                                   // cells of a full slab
+    static_assert(PS % 32 == 0, "slot stride");
     const int z0 = r * L, Lr = max(0, min(L, s - z0));      // this CTA's layers
     const int ncell = Lr * s2;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
     double *part = reinterpret_cast<double *>(clu3_smem);         // [4]: sums of u, abort
     double *wred = part + 4;                                       // [32][3]
     uint32_t *zb = reinterpret_cast<uint32_t *>(wred + 96);        // [32] layer z of the cube, any CTA
-    T *own = reinterpret_cast<T *>(wred + 96 + 16);                // [19][P] populations
+    T *own = reinterpret_cast<T *>(wred + 96 + 16);                // [19][PS] populations, L s^2 <= PS used
 
     for (int z = tid; z < s; z += nt) zb[z] = cluster_addr(own, z / L) + (uint32_t)((z % L) * s2 * sizeof(T));
     // this thread's cells; e from the leaf's cube of kappa
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
         else e = a.eps_nu / (2.0 * (double)kv + a.eps_nu);
         ec[i] = (T)e;
 #pragma unroll
-        for (int q = 0; q < Q19; ++q) own[q * P + c] = T(0);       // rest: every deviation zero
+        for (int q = 0; q < Q19; ++q) own[q * PS + c] = T(0);      // rest: every deviation zero
     }
     unsigned long long t0 = 0;
     if (r == 0 && tid == 0) {
@@ -650,6 +650,7 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
     cluster_sync_all();
 
     const int lane = tid & 31, wid = tid >> 5;
+    const T hgx = d == 0 ? a.hg : T(0), hgy = d == 1 ? a.hg : T(0), hgz = d == 2 ? a.hg : T(0);
     double prev_u = 0.0;
     int64_t t = 0;
     for (;;) {
@@ -662,8 +663,8 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
                 int gj = geo[j];
                 asm volatile("" : "+r"(gj));     // keeps the addresses out of registers between steps
                 const Cell3<T> q = cell3_of<T>(gj, s, zb, z0);
-                if (odd) aa_step_cell<true>(q, own, P, ec[j], a, d);
-                else aa_step_cell<false>(q, own, P, ec[j], a, d);
+                if (odd) aa_step_cell<true, PS>(q, own, ec[j], a, hgx, hgy, hgz);
+                else aa_step_cell<false, PS>(q, own, ec[j], a, hgx, hgy, hgz);
             }
             cluster_sync_all();
         }
@@ -678,8 +679,8 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
             int gj = geo[j];
             asm volatile("" : "+r"(gj));
             const Cell3<T> q = cell3_of<T>(gj, s, zb, z0);
-            if (odd) aa_velocity_cell<true>(q, own, P, ec[j], a.hg, d, m0, m1, m2);
-            else aa_velocity_cell<false>(q, own, P, ec[j], a.hg, d, m0, m1, m2);
+            if (odd) aa_velocity_cell<true, PS>(q, own, ec[j], a.hg, d, m0, m1, m2);
+            else aa_velocity_cell<false, PS>(q, own, ec[j], a.hg, d, m0, m1, m2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -743,10 +744,25 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
     cluster_sync_all();     // no CTA leaves while a peer may still read its shared memory
 }
 
-// Shared memory of local3d_cluster_kernel for slabs of P cells
-inline size_t clu3_smem_bytes(int64_t P, size_t esz)
+// The compiled slot strides: FP32 up to 2048 cells per slab, FP64 up to 1024
+template <typename T>
+const void *clu3_kernel(int ps)
 {
-    return sizeof(double) * (4 + 96 + 16) + (size_t)P * Q19 * esz;
+    switch (ps) {
+    case 256: return reinterpret_cast<const void *>(&local3d_cluster_kernel<T, 256>);
+    case 512: return reinterpret_cast<const void *>(&local3d_cluster_kernel<T, 512>);
+    case 1024: return reinterpret_cast<const void *>(&local3d_cluster_kernel<T, 1024>);
+    case 2048:
+        if constexpr (sizeof(T) == 4) return reinterpret_cast<const void *>(&local3d_cluster_kernel<T, 2048>);
+        return nullptr;
+    default: return nullptr;
+    }
+}
+
+// Shared memory of local3d_cluster_kernel at slot stride PS
+inline size_t clu3_smem_bytes(int64_t PS, size_t esz)
+{
+    return sizeof(double) * (4 + 96 + 16) + (size_t)PS * Q19 * esz;
 }
 
 // e per cell of every job of a chunk: job j copies its leaf's cube of the field
@@ -803,8 +819,8 @@ Step3Args<T> args3(const lbm3d_grid *g, int src)
     a.nz = g->p.nz;
     a.plane = g->plane;
     a.omega = (T)(1.0 / g->p.tau);
-    a.two_tau = (T)(2.0 * g->p.tau);
-    a.omt = (T)(1.0 - 2.0 * g->p.tau);
+    a.k_ru = (T)(6.0 * g->p.tau);
+    a.k_j = (T)(3.0 * (1.0 - 2.0 * g->p.tau));
     a.hgx = (T)(0.5 * g->p.eps * g->p.gx);
     a.hgy = (T)(0.5 * g->p.eps * g->p.gy);
     a.hgz = (T)(0.5 * g->p.eps * g->p.gz);
@@ -854,23 +870,28 @@ lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const
     const int NT = f64 ? clu3_threads<double>() : clu3_threads<float>();
     const int CPT = f64 ? clu3_cpt<double>() : clu3_cpt<float>();
     if (sz > 32) return LBM_EINVAL;
-    int C = 0, L = 0;
-    for (int c = 1; c <= 16 && c <= sz; c *= 2) {
+    // the fewest CTAs whose slab of L s^2 cells fits a compiled slot stride PS
+    int C = 0, L = 0, PS = 0;
+    for (int c = 1; c <= 16 && c <= sz && C == 0; c *= 2) {
         const int l = (sz + c - 1) / c;
         const int64_t P = (int64_t)l * sz * sz;
-        if (P <= (int64_t)CPT * NT && clu3_smem_bytes(P, esz) <= (size_t)optin) {
-            C = c;
-            L = l;
-            break;
+        for (int ps : {256, 512, 1024, 2048}) {
+            if (P <= ps && P <= (int64_t)CPT * NT && clu3_smem_bytes(ps, esz) <= (size_t)optin &&
+                (!f64 || ps <= 1024)) {
+                C = c;
+                L = l;
+                PS = ps;
+                break;
+            }
         }
     }
     if (C == 0) return LBM_EINVAL;
     const int64_t P = (int64_t)L * sz * sz;
-    const size_t smem = clu3_smem_bytes(P, esz);
+    const size_t smem = clu3_smem_bytes(PS, esz);
     // enough threads for CPT cells each, whole warps
     const int nt = (int)std::min<int64_t>(NT, ((P + CPT - 1) / CPT + 31) / 32 * 32);
-    const void *fn = f64 ? reinterpret_cast<const void *>(&local3d_cluster_kernel<double>)
-                         : reinterpret_cast<const void *>(&local3d_cluster_kernel<float>);
+    const void *fn = f64 ? clu3_kernel<double>(PS) : clu3_kernel<float>(PS);
+    if (!fn) return LBM_EINVAL;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
         cudaGetLastError();
@@ -905,19 +926,21 @@ lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const
         cfg.gridDim = dim3((unsigned)(3 * (int64_t)nl * C));
         cudaError_t e;
         if (f64) {
-            Clu3Args<double> a{kappa_dev, p->nx, p->ny, d_l4, d_ids + l0, 3 * nl, sz, L, 1.0 / p->tau, 2.0 * p->tau,
-                               1.0 - 2.0 * p->tau, 0.5 * p->eps * g_const, p->eps * nu, nu / g_const, tol_rel,
+            Clu3Args<double> a{kappa_dev, p->nx, p->ny, d_l4, d_ids + l0, 3 * nl, sz, L, 1.0 / p->tau, 6.0 * p->tau,
+                               3.0 * (1.0 - 2.0 * p->tau), 0.5 * p->eps * g_const, p->eps * nu, nu / g_const, tol_rel,
                                check_every, max_steps, keff_dev, status_dev, steps_dev, d_clock,
                                reinterpret_cast<int *>(d_clock + 1),
                                (unsigned long long)(local_time_limit() * 1e9)};
-            e = cudaLaunchKernelEx(&cfg, local3d_cluster_kernel<double>, a);
+            void *args[] = {&a};
+            e = cudaLaunchKernelExC(&cfg, fn, args);
         } else {
             Clu3Args<float> a{kappa_dev, p->nx, p->ny, d_l4, d_ids + l0, 3 * nl, sz, L, (float)(1.0 / p->tau),
-                              (float)(2.0 * p->tau), (float)(1.0 - 2.0 * p->tau), (float)(0.5 * p->eps * g_const),
+                              (float)(6.0 * p->tau), (float)(3.0 * (1.0 - 2.0 * p->tau)), (float)(0.5 * p->eps * g_const),
                               p->eps * nu, nu / g_const, tol_rel, check_every, max_steps, keff_dev, status_dev,
                               steps_dev, d_clock, reinterpret_cast<int *>(d_clock + 1),
                               (unsigned long long)(local_time_limit() * 1e9)};
-            e = cudaLaunchKernelEx(&cfg, local3d_cluster_kernel<float>, a);
+            void *args[] = {&a};
+            e = cudaLaunchKernelExC(&cfg, fn, args);
         }
         count_launches(1);
         if (e != cudaSuccess) {
@@ -1192,12 +1215,12 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
                     if (f64) {
                         Local3Args<double> a{static_cast<const double *>(buf[cur]), static_cast<double *>(buf[1 - cur]),
                                              static_cast<const double *>(coef), d_list, sz, s3, plane,
-                                             1.0 / p->tau, 2.0 * p->tau, 1.0 - 2.0 * p->tau, 0.5 * p->eps * g_const};
+                                             1.0 / p->tau, 6.0 * p->tau, 3.0 * (1.0 - 2.0 * p->tau), 0.5 * p->eps * g_const};
                         local3d_step_kernel<double><<<sgrid, 256, 0, st>>>(a);
                     } else {
                         Local3Args<float> a{static_cast<const float *>(buf[cur]), static_cast<float *>(buf[1 - cur]),
                                             static_cast<const float *>(coef), d_list, sz, s3, plane,
-                                            (float)(1.0 / p->tau), (float)(2.0 * p->tau), (float)(1.0 - 2.0 * p->tau),
+                                            (float)(1.0 / p->tau), (float)(6.0 * p->tau), (float)(3.0 * (1.0 - 2.0 * p->tau)),
                                             (float)(0.5 * p->eps * g_const)};
                         local3d_step_kernel<float><<<sgrid, 256, 0, st>>>(a);
                     }
@@ -1208,7 +1231,7 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
                           d_active, d_prev, d_jl, keff_dev, status_dev, steps_dev, d_nact};
                 if (f64) {
                     Local3Args<double> a{static_cast<const double *>(buf[cur]), nullptr, static_cast<const double *>(coef),
-                                         d_list, sz, s3, plane, 1.0 / p->tau, 2.0 * p->tau, 1.0 - 2.0 * p->tau,
+                                         d_list, sz, s3, plane, 1.0 / p->tau, 6.0 * p->tau, 3.0 * (1.0 - 2.0 * p->tau),
                                          0.5 * p->eps * g_const};
                     local3d_check_kernel<double><<<nlist, 256, 0, st>>>(a, ck);
                 } else {
