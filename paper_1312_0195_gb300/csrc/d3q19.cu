@@ -126,21 +126,46 @@ template <typename T> __device__ __forceinline__ void relax_pair(T &gp, T &gm, T
     gp = fma(om, fma(w, eu, wd - gp), gp);
     gm = fma(om, fma(-w, eu, wd - gm), gm);
 }
+// FP32 pair in packed f32x2 instructions, lane by lane the operations of relax_pair:
+// fma(g, -1, wd) is wd - g rounded once, then fma(+/-w, eu, .) and fma(om, ., g).
+__device__ __forceinline__ void relax_pair2(float &gp, float &gm, float2 wd, float2 wpm, float eu, float2 om)
+{
+    const float2 g = make_float2(gp, gm);
+    const float2 t = __ffma2_rn(g, make_float2(-1.0f, -1.0f), wd);
+    const float2 r = __ffma2_rn(om, __ffma2_rn(wpm, make_float2(eu, eu), t), g);
+    gp = r.x;
+    gm = r.y;
+}
+
 // All 19 populations; ux, uy, uz are 3 rho u_eq (Eq. 16 times 3), so e_a . u is the eu above.
 template <typename T> __device__ __forceinline__ void relax19(T (&g)[Q19], T drho, T ux, T uy, T uz, T om)
 {
     const T w0 = T(1.0 / 3.0), w1 = T(1.0 / 18.0), w2 = T(1.0 / 36.0);
     const T d1 = w1 * drho, d2 = w2 * drho;
     g[0] = fma(om, fma(w0, drho, -g[0]), g[0]);
-    relax_pair(g[1], g[2], d1, w1, ux, om);
-    relax_pair(g[3], g[4], d1, w1, uy, om);
-    relax_pair(g[5], g[6], d1, w1, uz, om);
-    relax_pair(g[7], g[8], d2, w2, ux + uy, om);
-    relax_pair(g[9], g[10], d2, w2, ux - uy, om);
-    relax_pair(g[11], g[12], d2, w2, ux + uz, om);
-    relax_pair(g[13], g[14], d2, w2, ux - uz, om);
-    relax_pair(g[15], g[16], d2, w2, uy + uz, om);
-    relax_pair(g[17], g[18], d2, w2, uy - uz, om);
+    if constexpr (sizeof(T) == 4) {
+        const float2 o2 = make_float2(om, om), d12 = make_float2(d1, d1), d22 = make_float2(d2, d2);
+        const float2 w12 = make_float2(w1, -w1), w22 = make_float2(w2, -w2);
+        relax_pair2(g[1], g[2], d12, w12, ux, o2);
+        relax_pair2(g[3], g[4], d12, w12, uy, o2);
+        relax_pair2(g[5], g[6], d12, w12, uz, o2);
+        relax_pair2(g[7], g[8], d22, w22, ux + uy, o2);
+        relax_pair2(g[9], g[10], d22, w22, ux - uy, o2);
+        relax_pair2(g[11], g[12], d22, w22, ux + uz, o2);
+        relax_pair2(g[13], g[14], d22, w22, ux - uz, o2);
+        relax_pair2(g[15], g[16], d22, w22, uy + uz, o2);
+        relax_pair2(g[17], g[18], d22, w22, uy - uz, o2);
+    } else {
+        relax_pair(g[1], g[2], d1, w1, ux, om);
+        relax_pair(g[3], g[4], d1, w1, uy, om);
+        relax_pair(g[5], g[6], d1, w1, uz, om);
+        relax_pair(g[7], g[8], d2, w2, ux + uy, om);
+        relax_pair(g[9], g[10], d2, w2, ux - uy, om);
+        relax_pair(g[11], g[12], d2, w2, ux + uz, om);
+        relax_pair(g[13], g[14], d2, w2, ux - uz, om);
+        relax_pair(g[15], g[16], d2, w2, uy + uz, om);
+        relax_pair(g[17], g[18], d2, w2, uy - uz, om);
+    }
 }
 
 // The whole collision of one cell: moments, r = j + (eps G / 2) rho, rho u = (1 - e) r

@@ -205,3 +205,21 @@ def test_local_keff3_time_limit_gives_etimeout():
         lbm.lbm_set_time_limit(600.0)
     ke, st, steps, worst = gpu_keff3(kap, leaves[:2], 1.0, 1.0 / 6.0, 1.0, 1e-6, 0.0, 100)
     assert worst == 0 and np.isfinite(ke).all()
+
+
+def test_local_keff3_degenerate_and_large_cubes():
+    """Cubes of 1, 2 and 3 cells (every neighbour is the cell itself or a wrapped copy), a cube
+    of 36 (above the cluster limit, so on the HBM path) and an empty leaf list."""
+    kap = _field(36, 36, 40, seed=76)
+    leaves = [(5, 6, 7, 1), (0, 1, 2, 2), (30, 31, 32, 3), (2, 0, 0, 36)]
+    ke, st, steps, _ = gpu_keff3(kap, leaves, 0.9, 0.12, 0.8, 1e-6, 0.0, 200)
+    assert (steps == 200).all() and (st == 0).all()
+    for i, (x0, y0, z0, s) in enumerate(leaves):
+        cube = kap[z0:z0 + s, y0:y0 + s, x0:x0 + s].astype(np.float64)
+        ref = oracle.local_keff3(cube, 0.9, 0.12, 0.8, 1e-6, tol=0.0, max_steps=200)["keff"]
+        scale = np.abs(np.diag(ref)).max()
+        np.testing.assert_allclose(ke[i], ref, rtol=0, atol=1e-5 * scale)
+    # a single cell is a uniform cube: kappa on the diagonal, nothing off it (Eq. 19 in 3-D)
+    np.testing.assert_allclose(np.diag(ke[0]), kap[7, 6, 5], rtol=1e-3)
+    ke, st, steps, worst = gpu_keff3(kap, np.zeros((0, 4), np.int32), 0.9, 0.12, 0.8, 1e-6, 0.0, 200)
+    assert worst == 0 and ke.shape == (0, 3, 3)
