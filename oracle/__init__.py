@@ -102,7 +102,7 @@ class _Problem3(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double), ("gz", C.c_double),
-                ("kappa", C.c_void_p)]
+                ("kappa", C.c_void_p), ("ktensor", C.c_void_p)]
 
 
 Q3 = 19
@@ -118,13 +118,22 @@ def lattice3():
 
 class Problem3D:
     """A periodic D3Q19 problem (Section 2's scheme in three dimensions): ``kappa`` [nz, ny, nx]
-    (may contain +inf or 0), constant body force ``g`` = (gx, gy, gz)."""
+    (may contain +inf or 0), or ``ktensor`` [nz, ny, nx, 3, 3] (K*_ij per cell, the coarse run of
+    Eq. 18), constant body force ``g`` = (gx, gy, gz)."""
 
-    def __init__(self, tau, nu, eps=1.0, kappa=None, g=(0.0, 0.0, 0.0)):
-        self.kappa = np.ascontiguousarray(kappa, dtype=np.float64)
-        self.nz, self.ny, self.nx = (int(v) for v in self.kappa.shape)
+    def __init__(self, tau, nu, eps=1.0, kappa=None, g=(0.0, 0.0, 0.0), ktensor=None):
+        if (kappa is None) == (ktensor is None):
+            raise ValueError("exactly one of kappa and ktensor is required")
+        self.kappa = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
+        self.ktensor = None if ktensor is None else np.ascontiguousarray(ktensor, dtype=np.float64)
+        shape = self.kappa.shape if self.kappa is not None else self.ktensor.shape[:3]
+        if self.ktensor is not None:
+            assert self.ktensor.shape[3:] == (3, 3)
+        self.nz, self.ny, self.nx = (int(v) for v in shape)
         self._s = _Problem3(self.nx, self.ny, self.nz, float(tau), float(nu), float(eps),
-                            float(g[0]), float(g[1]), float(g[2]), self.kappa.ctypes.data)
+                            float(g[0]), float(g[1]), float(g[2]),
+                            None if self.kappa is None else self.kappa.ctypes.data,
+                            None if self.ktensor is None else self.ktensor.ctypes.data)
 
     def rest(self) -> np.ndarray:
         f = np.empty((self.nz, self.ny, self.nx, Q3))

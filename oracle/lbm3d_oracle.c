@@ -19,6 +19,9 @@
  *     f(x + e, t + 1) = f + (f_eq - f) / tau                                Eq. 13
  * Periodic in x, y and z; rest initial state (f = w rho0, rho0 = 1).
  * Layout: f[((z * ny + y) * nx + x) * 19 + a].
+ *
+ * With a tensor K* per cell instead of kappa (the coarse run, Eq. 18 in three
+ * dimensions) Eq. 6 becomes the 3x3 solve (I + eps nu / 2 K*^-1) rho u = j + eps rho G / 2.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -31,6 +34,7 @@ typedef struct {
     double tau, nu, eps;
     double gx, gy, gz;        /* constant body force */
     const double *kappa;      /* [nz][ny][nx] permeability (may be +inf) */
+    const double *ktensor;    /* [nz][ny][nx][9] K*_ij row-major, used when kappa == NULL */
 } orc3_problem;
 
 static int E3[Q3][3];
@@ -63,7 +67,20 @@ void orc3_lattice(int *e_out /* [19][3] */, double *w_out /* [19] */)
     }
 }
 
-/* Eq. 6 for one cell: rho, j and the flow velocity u (Eq. 15). */
+/* Inverse of the 3x3 matrix m (row-major) by cofactors: inv = adj(m) / det(m). */
+static void inv3(const double m[9], double inv[9])
+{
+    const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+    const double c10 = m[2] * m[7] - m[1] * m[8], c11 = m[0] * m[8] - m[2] * m[6], c12 = m[1] * m[6] - m[0] * m[7];
+    const double c20 = m[1] * m[5] - m[2] * m[4], c21 = m[2] * m[3] - m[0] * m[5], c22 = m[0] * m[4] - m[1] * m[3];
+    const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    /* adj(m) is the transpose of the cofactor matrix */
+    inv[0] = c00 / det; inv[1] = c10 / det; inv[2] = c20 / det;
+    inv[3] = c01 / det; inv[4] = c11 / det; inv[5] = c21 / det;
+    inv[6] = c02 / det; inv[7] = c12 / det; inv[8] = c22 / det;
+}
+
+/* Eq. 6 (or Eq. 18) for one cell: rho, j and the flow velocity u (Eq. 15). */
 static void cell3(const orc3_problem *p, long c, const double *fc, double *rho_o, double j[3], double u[3])
 {
     double rho = 0.0;
@@ -73,6 +90,24 @@ static void cell3(const orc3_problem *p, long c, const double *fc, double *rho_o
         for (int k = 0; k < 3; ++k) j[k] += E3[a][k] * fc[a];
     }
     const double G[3] = {p->gx, p->gy, p->gz};
+    *rho_o = rho;
+    if (!p->kappa) {
+        double r[3];
+        for (int k = 0; k < 3; ++k) r[k] = j[k] + 0.5 * p->eps * rho * G[k];
+        if (p->eps == 0.0 || p->nu == 0.0) {
+            for (int k = 0; k < 3; ++k) u[k] = r[k] / rho;
+            return;
+        }
+        /* Eq. 18: (I + h K*^-1) rho u = r, h = eps nu / 2 */
+        double Ki[9], B[9], Bi[9];
+        inv3(p->ktensor + 9 * c, Ki);
+        const double h = 0.5 * p->eps * p->nu;
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) B[3 * i + k] = (i == k ? 1.0 : 0.0) + h * Ki[3 * i + k];
+        inv3(B, Bi);
+        for (int i = 0; i < 3; ++i) u[i] = (Bi[3 * i] * r[0] + Bi[3 * i + 1] * r[1] + Bi[3 * i + 2] * r[2]) / rho;
+        return;
+    }
     double drag = 0.0;                           /* eps nu / (2 kappa) */
     if (p->eps != 0.0 && p->nu != 0.0) {
         const double k = p->kappa[c];
@@ -82,7 +117,6 @@ static void cell3(const orc3_problem *p, long c, const double *fc, double *rho_o
         const double r = j[k] + 0.5 * p->eps * rho * G[k];
         u[k] = isinf(drag) ? 0.0 : r / (rho * (1.0 + drag));
     }
-    *rho_o = rho;
 }
 
 void orc3_init_rest(const orc3_problem *p, double *f)

@@ -167,3 +167,99 @@ def test_local_keff3_parallel_layers_darcy_arithmetic_mean():
     r = oracle.local_keff3(cube, ex["tau"], ex["nu"], ex["eps"], 1e-6, tol=1e-11, max_steps=20000)
     mean = 0.5 * (k1 + k2)
     assert abs(r["keff"][1, 1] - mean) <= 2e-6 * mean and abs(r["keff"][2, 2] - mean) <= 2e-6 * mean
+
+
+# ------------------------------------------------------------------ tensor K* (Eq. 18 in 3-D)
+
+def _random_tensor_field(shape, seed):
+    """Per-cell K* with a dominant positive diagonal and small, non-symmetric off-diagonals."""
+    rng = np.random.default_rng(seed)
+    K = np.zeros(shape + (3, 3))
+    for i in range(3):
+        K[..., i, i] = 1e-2 * np.exp(0.8 * rng.standard_normal(shape))
+    off = 1.5e-3 * rng.standard_normal(shape + (3, 3))
+    off[..., [0, 1, 2], [0, 1, 2]] = 0.0
+    return K + off
+
+
+def test_tensor_diagonal_is_the_scalar_run():
+    """K* = kappa I in every cell is the scalar-kappa problem (Eq. 18 reduces to Eq. 6)."""
+    k = synth.lognormal_kappa3d(5, 4, 6, 2.0, 1.5, seed=81).astype(np.float64)
+    K = np.zeros(k.shape + (3, 3))
+    for i in range(3):
+        K[..., i, i] = k
+    g = (1.5e-6, -1e-6, 0.7e-6)
+    a = oracle.Problem3D(0.8, 0.1, 0.9, kappa=k, g=g)
+    b = oracle.Problem3D(0.8, 0.1, 0.9, ktensor=K, g=g)
+    fa, fb = a.rest(), b.rest()
+    a.run(fa, 120)
+    b.run(fb, 120)
+    ua, ub = a.fields(fa), b.fields(fb)
+    scale = max(np.abs(t).max() for t in ua[1:])
+    for x, y in zip(ua[1:], ub[1:]):
+        np.testing.assert_allclose(y, x, rtol=0, atol=1e-9 * scale)
+
+
+def test_tensor_uniform_fixed_point_is_k_g_over_nu():
+    """Eq. 18 with a uniform, non-symmetric K*: the uniform state f_a = w_a rho0 (1 + 3 e_a . u)
+    with u = K* G / nu is a fixed point (then u_eq = u and (eps nu / 2) K*^-1 u = eps G / 2), and
+    a run from rest converges to it. A transposed K* gives K*^T G and fails."""
+    K0 = np.array([[2.0, 0.3, 0.1], [0.2, 1.5, 0.4], [0.05, 0.25, 1.2]]) * 1e-2
+    nu, g = 0.1, np.array([1e-6, -2e-6, 0.5e-6])
+    K = np.broadcast_to(K0, (2, 3, 2, 3, 3)).copy()
+    p = oracle.Problem3D(1.0, nu, 0.7, ktensor=K, g=tuple(g))
+    u = K0 @ g / nu
+    e, w = oracle.lattice3()
+    f = np.broadcast_to(w * (1.0 + 3.0 * (e @ u)), (2, 3, 2, 19)).copy()
+    np.testing.assert_allclose(p.step(f), f, rtol=0, atol=2e-16)     # a few ulps of w_0 = 1/3
+    # u ~ 1e-7 is recovered from full f ~ 0.05: the cancellation floor is ~1e-9 relative
+    np.testing.assert_allclose(p.mean_velocity(f), u, rtol=2e-9)
+    f = p.rest()
+    p.run(f, 4000)
+    np.testing.assert_allclose(p.mean_velocity(f), u, rtol=1e-8)
+
+
+def test_tensor_z_invariant_reduces_to_the_2d_tensor_run():
+    """A z-invariant K* with no coupling to z (K_xz = K_yz = K_zx = K_zy = 0) and no force along z
+    evolves like the already pinned 2-D tensor run of its xy block (the exact D3Q19 -> D2Q9
+    reduction, now through Eq. 18)."""
+    K2 = _random_tensor_field((7, 8), seed=82)[..., :2, :2]
+    K3 = np.zeros((3, 7, 8, 3, 3))
+    K3[..., :2, :2] = K2[None]
+    K3[..., 2, 2] = 5e-3
+    tau, nu, eps, steps, g2 = 0.9, 0.08, 0.8, 150, (1.2e-6, -0.8e-6)
+    p2 = oracle.Problem(tau, nu, eps, ktensor=K2.reshape(7, 8, 4), g=g2)
+    f2 = p2.rest()
+    p2.run(f2, steps)
+    r2, u2, v2 = p2.fields(f2)
+    p3 = oracle.Problem3D(tau, nu, eps, ktensor=K3, g=(g2[0], g2[1], 0.0))
+    f3 = p3.rest()
+    p3.run(f3, steps)
+    r3, u3, v3, w3 = (t[1] for t in p3.fields(f3))
+    scale = max(np.abs(u2).max(), np.abs(v2).max())
+    np.testing.assert_allclose(r3, r2, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(u3, u2, rtol=0, atol=2e-9 * scale)
+    np.testing.assert_allclose(v3, v2, rtol=0, atol=2e-9 * scale)
+    assert np.abs(w3).max() <= 2e-9 * scale
+
+
+def test_tensor_axis_permutation():
+    """Relabelling the axes (x, y, z) -> (y, z, x) of the field, of K* (rows and columns) and of G
+    permutes the velocity field the same way."""
+    K = _random_tensor_field((4, 5, 6), seed=83)
+    g = (1e-6, 2e-6, -1.5e-6)
+    p = oracle.Problem3D(0.9, 0.1, 0.8, ktensor=K, g=g)
+    f = p.rest()
+    p.run(f, 80)
+    r, u, v, w = p.fields(f)
+    # new axes: x' = y, y' = z, z' = x; arrays [z'][y'][x'] = old [x][z][y]
+    perm = [1, 2, 0]                                  # new component i is old component perm[i]
+    Kp = np.transpose(K, (2, 0, 1, 3, 4))[..., perm, :][..., :, perm]
+    q = oracle.Problem3D(0.9, 0.1, 0.8, ktensor=Kp, g=tuple(g[i] for i in perm))
+    fq = q.rest()
+    q.run(fq, 80)
+    rq, uq, vq, wq = q.fields(fq)
+    scale = max(np.abs(t).max() for t in (u, v, w))
+    np.testing.assert_allclose(uq, np.transpose(v, (2, 0, 1)), rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(vq, np.transpose(w, (2, 0, 1)), rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(wq, np.transpose(u, (2, 0, 1)), rtol=0, atol=1e-9 * scale)

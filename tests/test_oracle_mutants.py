@@ -45,6 +45,12 @@ MUTANTS3 = {
     "d3q19_force_half_dropped": [("j[k] + 0.5 * p->eps * rho * G[k]", "j[k] + 1.0 * p->eps * rho * G[k]")],
     "d3q19_local_drive_axes": [("        p.gy = d == 1 ? gconst : 0.0;\n        p.gz = d == 2 ? gconst : 0.0;",
                                 "        p.gy = d == 2 ? gconst : 0.0;\n        p.gz = d == 1 ? gconst : 0.0;")],
+    # Eq. 18 applied transposed: rho u = B^-T r instead of B^-1 r
+    "d3q19_tensor_transposed": [("u[i] = (Bi[3 * i] * r[0] + Bi[3 * i + 1] * r[1] + Bi[3 * i + 2] * r[2]) / rho;",
+                                 "u[i] = (Bi[i] * r[0] + Bi[3 + i] * r[1] + Bi[6 + i] * r[2]) / rho;")],
+    # Eq. 18 with the drag term's factor 1/2 dropped: (I + eps nu K*^-1) rho u = r
+    "d3q19_tensor_drag_half": [("const double h = 0.5 * p->eps * p->nu;\n        for (int i = 0; i < 3; ++i)",
+                                "const double h = 1.0 * p->eps * p->nu;\n        for (int i = 0; i < 3; ++i)")],
 }
 
 
