@@ -344,6 +344,29 @@ lbm_status lbm3d_get_fields(lbm3d_grid *g, float *rho_dev, float *u_dev, float *
 /* Volume average of the flow velocity, FP64 in a fixed order; HOST out[3]. */
 lbm_status lbm3d_mean_velocity(lbm3d_grid *g, double out_mean_uvw[3]);
 
+/* Coarse-grid parameters for blocks of block^3 fine cells (Section 3 in 3-D: the
+ * same rho0, nu_eff, eps, nu and G in physical units with dx and dt scaled by
+ * r = block): nx, ny, nz / r, tau_c = 1/2 + (tau - 1/2) / r, nu_c = nu / r (nu < 0
+ * first becomes nu_eff), G_c = r G. nx, ny, nz must be multiples of block, else
+ * LBM_EINVAL. HOST in and out. */
+lbm_status lbm3d_coarse_params(const lbm3d_params *fine_p, int32_t block, lbm3d_params *coarse_out);
+/* Creates the coarse 3-D grid of the upscaled model (Eq. 18 in 3-D): parameters
+ * from lbm3d_coarse_params, and per coarse cell the tensor K* of
+ * keff_coarse_dev double [nz/r][ny/r][nx/r][3][3] (row i = velocity component,
+ * column j = drive, as lbm3d_local_keff_batch writes it, in FINE lattice units;
+ * divided by r^2 here). The step then uses rho u = (I + (eps nu / 2) K*^-1)^-1
+ * (j + eps rho G / 2), stored per cell as the 9 planes of E = (eps nu / 2)
+ * (K* + (eps nu / 2) I)^-1 (188 B per FP32 update). keff is read during the call
+ * only; non-finite entries or a singular K* + (eps nu / 2) I give LBM_EINVAL.
+ * Step, fields and mean velocity are the lbm3d_* calls above. */
+lbm_status lbm3d_coarse_grid_create(const lbm3d_params *fine_p, int32_t block, const double *keff_coarse_dev,
+                                    void *cuda_stream, lbm3d_grid **out);
+/* Mean of a float [nz][ny][nx] device field over block^3 cubes into float
+ * [nz/block][ny/block][nx/block] (FP64 accumulation, fixed order): the fine-grid
+ * averages a 3-D coarse run is compared with. Sizes must be multiples of block. */
+lbm_status lbm3d_block_average(const float *in_dev, int32_t nx, int32_t ny, int32_t nz, int32_t block,
+                               float *out_dev, void *cuda_stream);
+
 /* Three-dimensional local problems (Section 3 with the D3Q19 lattice). For each
  * cubic leaf (x0, y0, z0, size) of the field kappa_dev [nz][ny][nx] (p->nx, ny,
  * nz are the field size; tau, nu, eps, storage as for a 3-D grid, the force is

@@ -383,6 +383,31 @@ def lbm3d_grid_create(params: Params3D, kappa, stream=None) -> C.c_void_p:
     return h
 
 
+def lbm3d_coarse_params(params: Params3D, block: int) -> Params3D:
+    out = _abi.lbm3d_params()
+    p = params.c()
+    _check(_abi.lib().lbm3d_coarse_params(C.byref(p), int(block), C.byref(out)))
+    return Params3D(nx=out.nx, ny=out.ny, nz=out.nz, tau=out.tau, nu=out.nu, eps=out.eps, gx=out.gx, gy=out.gy,
+                    gz=out.gz, storage=out.storage)
+
+
+def lbm3d_coarse_grid_create(fine_params: Params3D, block: int, keff_coarse, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    p = fine_params.c()
+    _check(_abi.lib().lbm3d_coarse_grid_create(C.byref(p), int(block), _ptr(keff_coarse), _stream(stream), C.byref(h)))
+    return h
+
+
+def lbm3d_block_average(field, block: int, out=None, stream=None):
+    """Mean of a CUDA float32 [nz, ny, nx] field over block^3 cubes -> [nz/b, ny/b, nx/b]."""
+    import torch
+    nz, ny, nx = (int(v) for v in field.shape)
+    if out is None:
+        out = torch.empty((nz // block, ny // block, nx // block), dtype=torch.float32, device=field.device)
+    _check(_abi.lib().lbm3d_block_average(_ptr(field), nx, ny, nz, int(block), _ptr(out), _stream(stream)))
+    return out
+
+
 def lbm3d_grid_destroy(grid) -> None:
     _check(_abi.lib().lbm3d_grid_destroy(grid))
 
@@ -426,11 +451,17 @@ def local_keff3(params: Params3D, kappa, leaves, g_const: float = 1e-6, tol_rel:
 
 
 class Grid3D:
-    """Owning wrapper of a D3Q19 grid: ``Grid3D(params3d, kappa_cuda_f32 [nz, ny, nx])``."""
+    """Owning wrapper of a D3Q19 grid: ``Grid3D(params3d, kappa_cuda_f32 [nz, ny, nx])``, or the
+    coarse grid of the upscaled model: ``Grid3D.coarse(fine_params3d, block, keff [nz/b, ny/b, nx/b, 3, 3])``."""
 
-    def __init__(self, params: Params3D, kappa, stream=None):
+    def __init__(self, params: Params3D, kappa, stream=None, _handle=None):
         self.params = params
-        self.handle = lbm3d_grid_create(params, kappa, stream)
+        self.handle = _handle if _handle is not None else lbm3d_grid_create(params, kappa, stream)
+
+    @classmethod
+    def coarse(cls, fine_params: Params3D, block: int, keff_coarse, stream=None):
+        return cls(lbm3d_coarse_params(fine_params, block), None, stream,
+                   _handle=lbm3d_coarse_grid_create(fine_params, block, keff_coarse, stream))
 
     def step(self, steps: int) -> None:
         lbm3d_step(self.handle, steps)

@@ -46,9 +46,9 @@ template <typename T>
 struct Step3Args {
     const T *src;
     T *dst;
-    const T *coef;          // e per cell
+    const T *coef;          // e per cell, or the 9 planes E_ij of a tensor K* (E_ij at (3 i + j) plane)
     int nx, ny, nz;
-    int64_t plane;          // elements per population plane
+    int64_t plane;          // elements per population (and coefficient) plane
     T omega, k_ru, k_j, hgx, hgy, hgz;   // 1/tau, 6 tau, 3 (1 - 2 tau), eps G / 2
 };
 
@@ -181,7 +181,27 @@ __device__ __forceinline__ void collide19(T (&g)[Q19], T e, T hgx, T hgy, T hgz,
     relax19(g, drho, fma(k_ru, rux, k_j * jx), fma(k_ru, ruy, k_j * jy), fma(k_ru, ruz, k_j * jz), om);
 }
 
+// Coarse cell with a tensor K* (Eq. 18 in Eq. 15): rho u = (I + c K*^-1)^-1 r = r - E r with
+// E = c (K* + c I)^-1 and c = eps nu / 2 (for K* = kappa I, E = e I).
 template <typename T>
+__device__ __forceinline__ void drag_tensor(const T (&E)[9], T rx, T ry, T rz, T &rux, T &ruy, T &ruz)
+{
+    rux = rx - fma(E[0], rx, fma(E[1], ry, E[2] * rz));
+    ruy = ry - fma(E[3], rx, fma(E[4], ry, E[5] * rz));
+    ruz = rz - fma(E[6], rx, fma(E[7], ry, E[8] * rz));
+}
+template <typename T>
+__device__ __forceinline__ void collide19_tensor(T (&g)[Q19], const T (&E)[9], T hgx, T hgy, T hgz, T k_ru, T k_j,
+                                                 T om)
+{
+    T drho, jx, jy, jz, rux, ruy, ruz;
+    moments19(g, drho, jx, jy, jz);
+    const T rho = T(1) + drho;
+    drag_tensor(E, fma(hgx, rho, jx), fma(hgy, rho, jy), fma(hgz, rho, jz), rux, ruy, ruz);
+    relax19(g, drho, fma(k_ru, rux, k_j * jx), fma(k_ru, ruy, k_j * jy), fma(k_ru, ruz, k_j * jz), om);
+}
+
+template <typename T, bool TENSOR>
 __global__ void __launch_bounds__(256) step3d_kernel(Step3Args<T> a)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
@@ -192,14 +212,20 @@ __global__ void __launch_bounds__(256) step3d_kernel(Step3Args<T> a)
     T g[Q19];
     pull19(src, a.plane, nb, g);
     const int64_t c = nb.z[1] + nb.y[1] + x;
-    const T e = __ldg(a.coef + c);
-    collide19(g, e, a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega);
+    if constexpr (TENSOR) {
+        T E[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) E[k] = __ldg(a.coef + k * a.plane + c);
+        collide19_tensor(g, E, a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega);
+    } else {
+        collide19(g, __ldg(a.coef + c), a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega);
+    }
 #pragma unroll
     for (int q = 0; q < Q19; ++q) dst[q * a.plane + c] = g[q];
 }
 
 // Density and flow velocity (Eq. 15) of the streamed state, optional FP64 block sums of u.
-template <typename T>
+template <typename T, bool TENSOR>
 __global__ void __launch_bounds__(128) fields3d_kernel(Step3Args<T> a, float *rho_o, float *u_o, float *v_o,
                                                        float *w_o, double *partials)
 {
@@ -210,12 +236,23 @@ __global__ void __launch_bounds__(128) fields3d_kernel(Step3Args<T> a, float *rh
         T g[Q19];
         pull19(a.src, a.plane, nb, g);
         const int64_t c = nb.z[1] + nb.y[1] + x;
-        const T e = a.coef[c];
         T drho, jx, jy, jz;
         moments19(g, drho, jx, jy, jz);
         const T rho = T(1) + drho;
         const T rx = fma(a.hgx, rho, jx), ry = fma(a.hgy, rho, jy), rz = fma(a.hgz, rho, jz);
-        const T ux = fma(-e, rx, rx) / rho, uy = fma(-e, ry, ry) / rho, uz = fma(-e, rz, rz) / rho;
+        T rux, ruy, ruz;
+        if constexpr (TENSOR) {
+            T E[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) E[k] = a.coef[k * a.plane + c];
+            drag_tensor(E, rx, ry, rz, rux, ruy, ruz);
+        } else {
+            const T e = a.coef[c];
+            rux = fma(-e, rx, rx);
+            ruy = fma(-e, ry, ry);
+            ruz = fma(-e, rz, rz);
+        }
+        const T ux = rux / rho, uy = ruy / rho, uz = ruz / rho;
         if (rho_o) rho_o[c] = (float)rho;
         if (u_o) u_o[c] = (float)ux;
         if (v_o) v_o[c] = (float)uy;
@@ -284,6 +321,65 @@ __global__ void __launch_bounds__(256) coef3d_kernel(const float *kappa, T *coef
         coef[i] = (T)e;
     }
     if (bad) atomicOr(flags, 1u);
+}
+
+// E = c (K + c I)^-1 per coarse cell, K = scale keff (fine lattice units to coarse),
+// c = eps nu / 2, by cofactors; flags bit 0: keff not finite, bit 1: K + c I singular.
+template <typename T>
+__global__ void __launch_bounds__(256) coef3d_tensor_kernel(const double *keff, double scale, T *coef, int64_t n,
+                                                            int64_t plane, double c, unsigned *flags)
+{
+    unsigned bad = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double m[9], E[9];
+        bool finite = true;
+        for (int k = 0; k < 9; ++k) {
+            m[k] = scale * keff[9 * i + k] + (k % 4 == 0 ? c : 0.0);
+            finite = finite && isfinite(m[k]);
+        }
+        for (int k = 0; k < 9; ++k) E[k] = 0.0;
+        if (!finite) {
+            bad |= 1u;
+        } else if (c != 0.0) {
+            const double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8];
+            const double c02 = m[3] * m[7] - m[4] * m[6];
+            const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+            if (!(fabs(det) > 0.0)) {
+                bad |= 2u;
+            } else {
+                const double f = c / det;     // E = c adj(m) / det(m); adj is the transposed cofactor matrix
+                E[0] = f * c00;
+                E[1] = f * (m[2] * m[7] - m[1] * m[8]);
+                E[2] = f * (m[1] * m[5] - m[2] * m[4]);
+                E[3] = f * c01;
+                E[4] = f * (m[0] * m[8] - m[2] * m[6]);
+                E[5] = f * (m[2] * m[3] - m[0] * m[5]);
+                E[6] = f * c02;
+                E[7] = f * (m[1] * m[6] - m[0] * m[7]);
+                E[8] = f * (m[0] * m[4] - m[1] * m[3]);
+            }
+        }
+        for (int k = 0; k < 9; ++k) coef[k * plane + i] = (T)E[k];
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+// Mean of a float [nz][ny][nx] field over block^3 cubes, FP64 in a fixed order.
+__global__ void __launch_bounds__(256) block_average3_kernel(const float *in, int nx, int ny, int nz, int r,
+                                                             float *out)
+{
+    const int cx = nx / r, cy = ny / r, cz = nz / r;
+    const int64_t nb = (int64_t)cx * cy * cz;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(b % cx), J = (int)((b / cx) % cy), K = (int)(b / ((int64_t)cx * cy));
+        double s = 0.0;
+        for (int z = K * r; z < (K + 1) * r; ++z)
+            for (int y = J * r; y < (J + 1) * r; ++y) {
+                const float *row = in + ((int64_t)z * ny + y) * nx + (int64_t)I * r;
+                for (int x = 0; x < r; ++x) s += (double)row[x];
+            }
+        out[b] = (float)(s / ((double)r * r * r));
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -824,6 +920,7 @@ struct lbm3d_grid {
     double *partials = nullptr, *mean = nullptr;
     unsigned *flags = nullptr;
     int cur = 0;
+    int tensor = 0;         // coefficients are the 9 planes of E (coarse run with tensor K*)
     int64_t n = 0, plane = 0, nblocks = 0;
     size_t esz = 4;
 };
@@ -853,6 +950,18 @@ Step3Args<T> args3(const lbm3d_grid *g, int src)
 }
 
 dim3 grid3(const lbm3d_grid *g, int threads) { return dim3((g->p.nx + threads - 1) / threads, g->p.ny, g->p.nz); }
+
+void launch_fields3(const lbm3d_grid *g, float *rho, float *u, float *v, float *w, double *partials)
+{
+    const dim3 gr = grid3(g, 128);
+    if (g->esz == 8) {
+        if (g->tensor) fields3d_kernel<double, true><<<gr, 128, 0, g->st>>>(args3<double>(g, g->cur), rho, u, v, w, partials);
+        else fields3d_kernel<double, false><<<gr, 128, 0, g->st>>>(args3<double>(g, g->cur), rho, u, v, w, partials);
+    } else {
+        if (g->tensor) fields3d_kernel<float, true><<<gr, 128, 0, g->st>>>(args3<float>(g, g->cur), rho, u, v, w, partials);
+        else fields3d_kernel<float, false><<<gr, 128, 0, g->st>>>(args3<float>(g, g->cur), rho, u, v, w, partials);
+    }
+}
 
 void free3(lbm3d_grid *g)
 {
@@ -988,7 +1097,14 @@ lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const
 
 extern "C" {
 
-lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void *cuda_stream, lbm3d_grid **out)
+}  // extern "C"
+
+namespace {
+
+// A 3-D grid with per-cell scalar kappa (kappa_dev) or, for a coarse run, per-cell
+// tensor K* = kscale keff (keff_dev [n][9], row-major).
+lbm_status grid3_create_impl(const lbm3d_params *p, const float *kappa_dev, const double *keff_dev, double kscale,
+                             void *cuda_stream, lbm3d_grid **out)
 {
     if (!p || !out) return fail(LBM_EINVAL, "params and out must not be NULL");
     *out = nullptr;
@@ -1000,9 +1116,11 @@ lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void
     if (!std::isfinite(p->gx) || !std::isfinite(p->gy) || !std::isfinite(p->gz))
         return fail(LBM_EINVAL, "G must be finite");
     if (p->storage != LBM_F32 && p->storage != LBM_F64) return fail(LBM_EINVAL, "storage must be LBM_F32 or LBM_F64");
-    if (!is_device_ptr(kappa_dev)) return fail(LBM_EINVAL, "kappa_dev must be a device pointer");
+    if (keff_dev ? !is_device_ptr(keff_dev) : !is_device_ptr(kappa_dev))
+        return fail(LBM_EINVAL, keff_dev ? "keff_dev must be a device pointer" : "kappa_dev must be a device pointer");
     lbm3d_grid *g = new lbm3d_grid;
     g->p = *p;
+    g->tensor = keff_dev ? 1 : 0;
     cudaGetDevice(&g->dev);
     g->st = static_cast<cudaStream_t>(cuda_stream);
     g->n = (int64_t)p->nx * p->ny * p->nz;
@@ -1012,7 +1130,7 @@ lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void
     g->nblocks = (int64_t)gr.x * gr.y * gr.z;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&g->buf[k], Q19 * g->plane * g->esz);
-    if (e == cudaSuccess) e = cudaMalloc(&g->coef, g->n * g->esz);
+    if (e == cudaSuccess) e = cudaMalloc(&g->coef, (g->tensor ? 9 * g->plane : g->n) * g->esz);
     if (e == cudaSuccess) e = cudaMalloc(&g->partials, sizeof(double) * 3 * g->nblocks);
     if (e == cudaSuccess) e = cudaMalloc(&g->mean, sizeof(double) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&g->flags, sizeof(unsigned));
@@ -1026,10 +1144,21 @@ lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void
     }
     const double nu = p->nu < 0.0 ? (p->tau - 0.5) / 3.0 : p->nu;
     const int nb = (int)std::min<int64_t>((g->n + 255) / 256, 8192);
-    if (g->esz == 8)
-        coef3d_kernel<double><<<nb, 256, 0, g->st>>>(kappa_dev, static_cast<double *>(g->coef), g->n, p->eps * nu, g->flags);
-    else
-        coef3d_kernel<float><<<nb, 256, 0, g->st>>>(kappa_dev, static_cast<float *>(g->coef), g->n, p->eps * nu, g->flags);
+    if (g->tensor) {
+        if (g->esz == 8)
+            coef3d_tensor_kernel<double><<<nb, 256, 0, g->st>>>(keff_dev, kscale, static_cast<double *>(g->coef), g->n,
+                                                                g->plane, 0.5 * p->eps * nu, g->flags);
+        else
+            coef3d_tensor_kernel<float><<<nb, 256, 0, g->st>>>(keff_dev, kscale, static_cast<float *>(g->coef), g->n,
+                                                               g->plane, 0.5 * p->eps * nu, g->flags);
+    } else {
+        if (g->esz == 8)
+            coef3d_kernel<double><<<nb, 256, 0, g->st>>>(kappa_dev, static_cast<double *>(g->coef), g->n, p->eps * nu,
+                                                         g->flags);
+        else
+            coef3d_kernel<float><<<nb, 256, 0, g->st>>>(kappa_dev, static_cast<float *>(g->coef), g->n, p->eps * nu,
+                                                        g->flags);
+    }
     count_launches(1);
     unsigned flags = 0;
     e = cudaGetLastError();
@@ -1041,9 +1170,67 @@ lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void
     }
     if (flags) {
         free3(g);
-        return fail(LBM_EINVAL, "kappa holds NaN or negative values");
+        if (!keff_dev) return fail(LBM_EINVAL, "kappa holds NaN or negative values");
+        return fail(LBM_EINVAL, (flags & 1u) ? "keff holds non-finite values" : "K* + (eps nu / 2) I is singular");
     }
     *out = g;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void *cuda_stream, lbm3d_grid **out)
+{
+    return grid3_create_impl(p, kappa_dev, nullptr, 1.0, cuda_stream, out);
+}
+
+lbm_status lbm3d_coarse_params(const lbm3d_params *fine_p, int32_t block, lbm3d_params *coarse_out)
+{
+    if (!fine_p || !coarse_out) return fail(LBM_EINVAL, "params and out must not be NULL");
+    if (block < 1 || fine_p->nx % block || fine_p->ny % block || fine_p->nz % block)
+        return fail(LBM_EINVAL, "nx, ny, nz must be multiples of block %d", block);
+    if (!std::isfinite(fine_p->tau) || fine_p->tau < 0.5) return fail(LBM_EINVAL, "tau must be finite and >= 0.5");
+    const double r = block;
+    lbm3d_params c = *fine_p;
+    c.nx = fine_p->nx / block;
+    c.ny = fine_p->ny / block;
+    c.nz = fine_p->nz / block;
+    c.tau = 0.5 + (fine_p->tau - 0.5) / r;
+    c.nu = (fine_p->nu < 0.0 ? (fine_p->tau - 0.5) / 3.0 : fine_p->nu) / r;
+    c.gx = fine_p->gx * r;
+    c.gy = fine_p->gy * r;
+    c.gz = fine_p->gz * r;
+    *coarse_out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm3d_coarse_grid_create(const lbm3d_params *fine_p, int32_t block, const double *keff_coarse_dev,
+                                    void *cuda_stream, lbm3d_grid **out)
+{
+    if (out) *out = nullptr;
+    lbm3d_params c;
+    lbm_status s = lbm3d_coarse_params(fine_p, block, &c);
+    if (s != LBM_OK) return s;
+    if (!keff_coarse_dev) return fail(LBM_EINVAL, "keff_coarse_dev is NULL");
+    return grid3_create_impl(&c, nullptr, keff_coarse_dev, 1.0 / ((double)block * block), cuda_stream, out);
+}
+
+lbm_status lbm3d_block_average(const float *in_dev, int32_t nx, int32_t ny, int32_t nz, int32_t block,
+                               float *out_dev, void *cuda_stream)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || block < 1 || nx % block || ny % block || nz % block)
+        return fail(LBM_EINVAL, "nx, ny, nz must be positive multiples of block");
+    if (!is_device_ptr(in_dev) || !is_device_ptr(out_dev)) return fail(LBM_EINVAL, "in/out must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t nb = (int64_t)(nx / block) * (ny / block) * (nz / block);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
+    block_average3_kernel<<<blocks, 256, 0, st>>>(in_dev, nx, ny, nz, block, out_dev);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "3-D block average: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 
@@ -1059,8 +1246,13 @@ lbm_status lbm3d_step(lbm3d_grid *g, int64_t steps)
     if (steps < 0) return fail(LBM_EINVAL, "steps must be >= 0");
     const dim3 gr = grid3(g, 256);
     for (int64_t s = 0; s < steps; ++s) {
-        if (g->esz == 8) step3d_kernel<double><<<gr, 256, 0, g->st>>>(args3<double>(g, g->cur));
-        else step3d_kernel<float><<<gr, 256, 0, g->st>>>(args3<float>(g, g->cur));
+        if (g->esz == 8) {
+            if (g->tensor) step3d_kernel<double, true><<<gr, 256, 0, g->st>>>(args3<double>(g, g->cur));
+            else step3d_kernel<double, false><<<gr, 256, 0, g->st>>>(args3<double>(g, g->cur));
+        } else {
+            if (g->tensor) step3d_kernel<float, true><<<gr, 256, 0, g->st>>>(args3<float>(g, g->cur));
+            else step3d_kernel<float, false><<<gr, 256, 0, g->st>>>(args3<float>(g, g->cur));
+        }
         g->cur = 1 - g->cur;
     }
     count_launches(steps);
@@ -1074,10 +1266,7 @@ lbm_status lbm3d_get_fields(lbm3d_grid *g, float *rho_dev, float *u_dev, float *
     if (!g) return fail(LBM_EINVAL, "grid is NULL");
     for (const float *q : {rho_dev, u_dev, v_dev, w_dev})
         if (q && !is_device_ptr(q)) return fail(LBM_EINVAL, "field outputs must be device pointers");
-    if (g->esz == 8)
-        fields3d_kernel<double><<<grid3(g, 128), 128, 0, g->st>>>(args3<double>(g, g->cur), rho_dev, u_dev, v_dev, w_dev, nullptr);
-    else
-        fields3d_kernel<float><<<grid3(g, 128), 128, 0, g->st>>>(args3<float>(g, g->cur), rho_dev, u_dev, v_dev, w_dev, nullptr);
+    launch_fields3(g, rho_dev, u_dev, v_dev, w_dev, nullptr);
     count_launches(1);
     L3_CUDA(cudaGetLastError());
     L3_CUDA(cudaStreamSynchronize(g->st));
@@ -1087,10 +1276,7 @@ lbm_status lbm3d_get_fields(lbm3d_grid *g, float *rho_dev, float *u_dev, float *
 lbm_status lbm3d_mean_velocity(lbm3d_grid *g, double out_mean_uvw[3])
 {
     if (!g || !out_mean_uvw) return fail(LBM_EINVAL, "grid and out must not be NULL");
-    if (g->esz == 8)
-        fields3d_kernel<double><<<grid3(g, 128), 128, 0, g->st>>>(args3<double>(g, g->cur), nullptr, nullptr, nullptr, nullptr, g->partials);
-    else
-        fields3d_kernel<float><<<grid3(g, 128), 128, 0, g->st>>>(args3<float>(g, g->cur), nullptr, nullptr, nullptr, nullptr, g->partials);
+    launch_fields3(g, nullptr, nullptr, nullptr, nullptr, g->partials);
     reduce3_kernel<<<1, 1024, 0, g->st>>>(g->partials, g->nblocks, 1.0 / (double)g->n, g->mean);
     count_launches(2);
     L3_CUDA(cudaGetLastError());
