@@ -667,6 +667,7 @@ def main(argv=None):
     ap.add_argument("--pipeline3d", type=int, default=0,
                     help="run the upscaled method in 3-D (D3Q19) on an n^3 log-normal field (e.g. 256) and exit")
     ap.add_argument("--pipeline-steps", type=int, default=20000, help="fine steps of --pipeline / --pipeline3d")
+    ap.add_argument("--pipeline-sigma", type=float, default=2.0, help="log-permeability sigma of --pipeline3d")
     ap.add_argument("--pipeline-epochs", type=int, default=10, help="surrogate training epochs of --pipeline")
     ap.add_argument("--pipeline-margins", default="0,4",
                     help="oversampling margins of the local-LBM upscaling runs of --pipeline")
@@ -780,8 +781,8 @@ def run_pipeline(args, local):
 
 
 def run_pipeline3d(args, local):
-    """The upscaled method in three dimensions on an n^3 log-normal field (sigma 2, ell 8, seed 7;
-    default n = 256, r = 16): fine D3Q19 run (FP32, tau = 1, nu = nu_eff, eps = 1, G = (1e-6, 0, 0))
+    """The upscaled method in three dimensions on an n^3 log-normal field (sigma 2 by default, ell 8,
+    seed 7; default n = 256, r = 16): fine D3Q19 run (FP32, tau = 1, nu = nu_eff, eps = 1, G = (1e-6, 0, 0))
     for `steps` steps; K* of every r^3 block by the 3-D local problems (three drives, tol 1e-8);
     coarse run with the tensor K* (Eq. 18 in 3-D, scaled parameters) for steps / r steps, the same
     physical time, and then 16 times longer; relative L2 error of the coarse velocity against the
@@ -792,7 +793,8 @@ def run_pipeline3d(args, local):
     torch.cuda.set_device(local)
     n, r, steps = args.pipeline3d, 16, args.pipeline_steps
     nb = n // r
-    out = {"workload": f"{n}^3 log-normal (sigma 2, ell 8, seed 7), r = {r}, fine {steps} steps, "
+    sig = args.pipeline_sigma
+    out = {"workload": f"{n}^3 log-normal (sigma {sig:g}, ell 8, seed 7), r = {r}, fine {steps} steps, "
                        f"coarse {steps // r} steps", "n": n, "block": r}
 
     def timed(fn):
@@ -803,7 +805,7 @@ def run_pipeline3d(args, local):
         return res, time.perf_counter() - t0
 
     p = lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0, gx=1e-6)
-    kt = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
+    kt = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, sig, seed=7)).cuda()
     with lbm.Grid3D(p, kt) as G:
         _, t = timed(lambda: G.step(steps))
         out["fine_seconds"] = t
@@ -822,6 +824,7 @@ def run_pipeline3d(args, local):
     asym = (kc - kc.transpose(-1, -2)).abs().amax(dim=(-1, -2)) / kc.diagonal(dim1=-2, dim2=-1).abs().amax(dim=-1)
     out["upscale"]["kstar_asymmetry_median"] = float(asym.median())
     den = float(torch.sqrt(sum((a ** 2).sum() for a in avg)))
+    out["fine_mean_velocity"] = [float(a.mean()) for a in avg]
     with lbm.Grid3D.coarse(p, r, kc) as Cg:
         pc = Cg.params
         out["coarse_params"] = {"tau": pc.tau, "nu": pc.nu, "gx": pc.gx}
@@ -831,7 +834,8 @@ def run_pipeline3d(args, local):
             done += k
             _, uc, vc, wc = Cg.fields()
             num = float(torch.sqrt(sum(((c.double() - a) ** 2).sum() for c, a in zip((uc, vc, wc), avg))))
-            out[f"coarse_{name}"] = {"steps": done, "seconds": t, "rel_l2_vs_fine": num / den}
+            out[f"coarse_{name}"] = {"steps": done, "seconds": t, "rel_l2_vs_fine": num / den,
+                                     "mean_velocity": [float(c.double().mean()) for c in (uc, vc, wc)]}
     print(json.dumps(out), flush=True)
     return 0
 
