@@ -223,3 +223,24 @@ def test_local_keff3_degenerate_and_large_cubes():
     np.testing.assert_allclose(np.diag(ke[0]), kap[7, 6, 5], rtol=1e-3)
     ke, st, steps, worst = gpu_keff3(kap, np.zeros((0, 4), np.int32), 0.9, 0.12, 0.8, 1e-6, 0.0, 200)
     assert worst == 0 and ke.shape == (0, 3, 3)
+
+
+def test_local_keff3_full_size_sampled():
+    """The benchmarked launch: all 4096 cubes of 16^3 of the 256^3 log-normal field in one call
+    (clusters of two CTAs), a fixed 300 steps; seeded sample cubes against the oracle."""
+    import torch
+    lbm = _lbm()
+    n, b = 256, 16
+    kap = synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)
+    cubes = [(x, y, z, b) for z in range(0, n, b) for y in range(0, n, b) for x in range(0, n, b)]
+    p = lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0)
+    ke, st, steps, _ = lbm.local_keff3(p, torch.from_numpy(kap).cuda(),
+                                       torch.tensor(cubes, dtype=torch.int32, device="cuda"), 1e-6, 0.0, 300, 64)
+    ke, steps = ke.cpu().numpy(), steps.cpu().numpy()
+    assert (steps == 300).all() and (st.cpu().numpy() == 0).all()
+    rng = np.random.default_rng(77)
+    for i in list(rng.choice(len(cubes), 5, replace=False)) + [0, len(cubes) - 1]:
+        x0, y0, z0, s = cubes[i]
+        ref = oracle.local_keff3(kap[z0:z0 + s, y0:y0 + s, x0:x0 + s].astype(np.float64), 1.0, 1.0 / 6.0, 1.0,
+                                 1e-6, tol=0.0, max_steps=300)["keff"]
+        np.testing.assert_allclose(ke[i], ref, rtol=0, atol=1e-5 * np.abs(np.diag(ref)).max())
