@@ -91,6 +91,9 @@ def _L():
         _lib.orc3_local_keff.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                          C.c_double, C.c_long, C.c_int, dp, C.POINTER(C.c_long)]
         _lib.orc3_local_keff.restype = C.c_int
+        _lib.orc3_local_keff_os.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                            C.c_double, C.c_long, C.c_int, dp, C.POINTER(C.c_long)]
+        _lib.orc3_local_keff_os.restype = C.c_int
     return _lib
 
 
@@ -162,18 +165,33 @@ class Problem3D:
         return m
 
 
-def local_keff3(kappa_cube, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64):
+def local_keff3(kappa_cube, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64, margin=0):
     """Three-dimensional local problem on one periodic s^3 cube (D3Q19), drives along x, y, z;
-    Eq. 17 in 3-D. Returns dict(keff=[3][3] (K*_ij, i velocity component, j drive), steps=[3],
-    converged=n)."""
+    Eq. 17 in 3-D. margin > 0: the cube is the leaf grown by `margin` cells on every side
+    (oversampling) and the mean velocity is taken over the inner leaf (orc3_local_keff_os).
+    Returns dict(keff=[3][3] (K*_ij, i velocity component, j drive), steps=[3], converged=n)."""
     k = np.ascontiguousarray(kappa_cube, dtype=np.float64)
     s = k.shape[0]
-    assert k.shape == (s, s, s)
+    assert k.shape == (s, s, s) and 0 <= margin and s - 2 * margin >= 1
     keff = np.empty(9)
     st = (C.c_long * 3)()
-    nconv = _L().orc3_local_keff(s, _dp(k), float(tau), float(nu), float(eps), float(g_const), float(tol),
-                                 int(max_steps), int(check_every), _dp(keff), st)
+    if margin == 0:
+        nconv = _L().orc3_local_keff(s, _dp(k), float(tau), float(nu), float(eps), float(g_const), float(tol),
+                                     int(max_steps), int(check_every), _dp(keff), st)
+    else:
+        nconv = _L().orc3_local_keff_os(s, int(margin), _dp(k), float(tau), float(nu), float(eps), float(g_const),
+                                        float(tol), int(max_steps), int(check_every), _dp(keff), st)
     return dict(keff=keff.reshape(3, 3), steps=[st[0], st[1], st[2]], converged=int(nconv))
+
+
+def grown_cube(field, x0, y0, z0, s, margin):
+    """The leaf (x0, y0, z0, s) of a [nz, ny, nx] field grown by `margin` on every side, wrapping
+    periodically at the field's edges."""
+    nz, ny, nx = field.shape
+    zi = (np.arange(z0 - margin, z0 + s + margin) % nz)[:, None, None]
+    yi = (np.arange(y0 - margin, y0 + s + margin) % ny)[None, :, None]
+    xi = (np.arange(x0 - margin, x0 + s + margin) % nx)[None, None, :]
+    return field[zi, yi, xi]
 
 
 class Problem:

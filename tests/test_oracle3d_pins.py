@@ -263,3 +263,41 @@ def test_tensor_axis_permutation():
     np.testing.assert_allclose(uq, np.transpose(v, (2, 0, 1)), rtol=0, atol=1e-9 * scale)
     np.testing.assert_allclose(vq, np.transpose(w, (2, 0, 1)), rtol=0, atol=1e-9 * scale)
     np.testing.assert_allclose(wq, np.transpose(u, (2, 0, 1)), rtol=0, atol=1e-9 * scale)
+
+
+# ------------------------------------------------------- oversampled 3-D local problems
+
+def test_oversampled_local3_periodic_embedding_is_exact():
+    """A field that is periodic with the leaf's period: the cube grown by half a period on every
+    side is two periods wide, its periodic solution is the leaf's solution repeated, and the
+    inner-window mean equals the plain local problem's mean (up to summation order)."""
+    s, m = 4, 2
+    cube = synth.lognormal_kappa3d(s, s, s, 1.5, 1.5, seed=84).astype(np.float64)
+    field = np.tile(cube, (3, 3, 3))
+    grown = oracle.grown_cube(field, s, s, s, s, m)
+    a = oracle.local_keff3(cube, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=0.0, max_steps=300)
+    b = oracle.local_keff3(grown, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=0.0, max_steps=300, margin=m)
+    np.testing.assert_allclose(b["keff"], a["keff"], rtol=0, atol=1e-12 * np.abs(a["keff"]).max())
+
+
+def test_oversampled_local3_uniform_and_inner_layers():
+    """A uniform grown cube gives kappa I. Parallel layers in the Darcy setting of Table 2
+    (tau = 1/2, E3's nu and kappa ratio 10): bands of kappa_1 and kappa_2 across the inner leaf
+    and margin bands of a third permeability. Drives along y and z see parallel layers, so
+    K*_yy = K*_zz is the arithmetic mean over the columns averaged: the inner leaf's with
+    oversampling, the whole cube's without."""
+    s, m = 4, 2
+    se = s + 2 * m
+    r = oracle.local_keff3(np.full((se, se, se), 3e-3), 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-10, max_steps=100000,
+                           margin=m)
+    np.testing.assert_allclose(np.diag(r["keff"]), 3e-3, rtol=1e-6)
+    ex = synth.paper_experiment("E3", ratio=10.0, ny=1)
+    k1, k2 = float(ex["kappa"][0, 0]), float(ex["kappa"][0, 10])
+    cols = np.array([5.0 * k2] * m + [k1] * 2 + [k2] * 2 + [5.0 * k2] * m)
+    kap = np.broadcast_to(cols[None, None, :], (se, se, se)).copy()
+    r = oracle.local_keff3(kap, ex["tau"], ex["nu"], ex["eps"], 1e-6, tol=1e-11, max_steps=20000, margin=m)
+    inner = 0.5 * (k1 + k2)
+    np.testing.assert_allclose([r["keff"][1, 1], r["keff"][2, 2]], inner, rtol=2e-6)
+    full = oracle.local_keff3(kap, ex["tau"], ex["nu"], ex["eps"], 1e-6, tol=1e-11, max_steps=20000)
+    np.testing.assert_allclose([full["keff"][1, 1], full["keff"][2, 2]], cols.mean(), rtol=2e-6)
+    assert abs(full["keff"][1, 1] - inner) > 0.5 * inner

@@ -48,6 +48,11 @@ MUTANTS3 = {
     # Eq. 18 applied transposed: rho u = B^-T r instead of B^-1 r
     "d3q19_tensor_transposed": [("u[i] = (Bi[3 * i] * r[0] + Bi[3 * i + 1] * r[1] + Bi[3 * i + 2] * r[2]) / rho;",
                                  "u[i] = (Bi[i] * r[0] + Bi[3 + i] * r[1] + Bi[6 + i] * r[2]) / rho;")],
+    # oversampling with the mean over the grown cube's corner instead of the inner leaf
+    "d3q19_oversampled_window_origin": [("orc3_mean_velocity_window(&p, f, margin, margin, margin, s, m);\n                if",
+                                         "orc3_mean_velocity_window(&p, f, 0, 0, 0, s, m);\n                if"),
+                                        ("        orc3_mean_velocity_window(&p, f, margin, margin, margin, s, m);\n        for",
+                                         "        orc3_mean_velocity_window(&p, f, 0, 0, 0, s, m);\n        for")],
     # Eq. 18 with the drag term's factor 1/2 dropped: (I + eps nu K*^-1) rho u = r
     "d3q19_tensor_drag_half": [("const double h = 0.5 * p->eps * p->nu;\n        for (int i = 0; i < 3; ++i)",
                                 "const double h = 1.0 * p->eps * p->nu;\n        for (int i = 0; i < 3; ++i)")],
