@@ -783,10 +783,11 @@ def run_pipeline(args, local):
 def run_pipeline3d(args, local):
     """The upscaled method in three dimensions on an n^3 log-normal field (sigma 2 by default, ell 8,
     seed 7; default n = 256, r = 16): fine D3Q19 run (FP32, tau = 1, nu = nu_eff, eps = 1, G = (1e-6, 0, 0))
-    for `steps` steps; K* of every r^3 block by the 3-D local problems (three drives, tol 1e-8);
-    coarse run with the tensor K* (Eq. 18 in 3-D, scaled parameters) for steps / r steps, the same
-    physical time, and then 16 times longer; relative L2 error of the coarse velocity against the
-    r^3 block average of the fine velocity. Prints one JSON line."""
+    for `steps` steps; K* of every r^3 block by the 3-D local problems (three drives, tol 1e-8) for
+    each oversampling margin of --pipeline-margins; coarse run with the tensor K* (Eq. 18 in 3-D,
+    scaled parameters) for steps / r steps, the same physical time, and then 16 times longer;
+    relative L2 error of the coarse velocity against the r^3 block average of the fine velocity.
+    Prints one JSON line."""
     import torch
     import paper_1312_0195_gb300 as lbm
     import synth
@@ -815,27 +816,29 @@ def run_pipeline3d(args, local):
         del u, v, w
     leaves = torch.tensor([(x, y, z, r) for z in range(0, n, r) for y in range(0, n, r) for x in range(0, n, r)],
                           dtype=torch.int32, device="cuda")
-    (keff, st, lsteps, _), t = timed(lambda: lbm.local_keff3(p, kt, leaves, 1e-6, 1e-8, 200000, 64))
-    st = st.cpu().numpy()
-    out["upscale"] = {"blocks": nb ** 3, "seconds": t, "blocks_per_s": nb ** 3 / t,
-                      "converged": int((st == 0).sum()),
-                      "glups": float(lsteps.double().sum()) * r ** 3 / t / 1e9}
-    kc = keff.reshape(nb, nb, nb, 3, 3)
-    asym = (kc - kc.transpose(-1, -2)).abs().amax(dim=(-1, -2)) / kc.diagonal(dim1=-2, dim2=-1).abs().amax(dim=-1)
-    out["upscale"]["kstar_asymmetry_median"] = float(asym.median())
     den = float(torch.sqrt(sum((a ** 2).sum() for a in avg)))
     out["fine_mean_velocity"] = [float(a.mean()) for a in avg]
-    with lbm.Grid3D.coarse(p, r, kc) as Cg:
-        pc = Cg.params
-        out["coarse_params"] = {"tau": pc.tau, "nu": pc.nu, "gx": pc.gx}
-        done = 0
-        for name, k in (("same_time", steps // r), ("16x_longer", 15 * (steps // r))):
-            _, t = timed(lambda: Cg.step(k))
-            done += k
-            _, uc, vc, wc = Cg.fields()
-            num = float(torch.sqrt(sum(((c.double() - a) ** 2).sum() for c, a in zip((uc, vc, wc), avg))))
-            out[f"coarse_{name}"] = {"steps": done, "seconds": t, "rel_l2_vs_fine": num / den,
-                                     "mean_velocity": [float(c.double().mean()) for c in (uc, vc, wc)]}
+    for m in (int(v) for v in args.pipeline_margins.split(",")):
+        pm = lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0, gx=1e-6, margin=m)
+        (keff, st, lsteps, _), t = timed(lambda: lbm.local_keff3(pm, kt, leaves, 1e-6, 1e-8, 200000, 64))
+        st = st.cpu().numpy()
+        res = {"blocks": nb ** 3, "seconds": t, "blocks_per_s": nb ** 3 / t, "converged": int((st == 0).sum()),
+               "glups": float(lsteps.double().sum()) * (r + 2 * m) ** 3 / t / 1e9}
+        kc = keff.reshape(nb, nb, nb, 3, 3)
+        asym = (kc - kc.transpose(-1, -2)).abs().amax(dim=(-1, -2)) / kc.diagonal(dim1=-2, dim2=-1).abs().amax(dim=-1)
+        res["kstar_asymmetry_median"] = float(asym.median())
+        with lbm.Grid3D.coarse(p, r, kc) as Cg:
+            pc = Cg.params
+            out["coarse_params"] = {"tau": pc.tau, "nu": pc.nu, "gx": pc.gx}
+            done = 0
+            for name, k in (("same_time", steps // r), ("16x_longer", 15 * (steps // r))):
+                _, t = timed(lambda: Cg.step(k))
+                done += k
+                _, uc, vc, wc = Cg.fields()
+                num = float(torch.sqrt(sum(((c.double() - a) ** 2).sum() for c, a in zip((uc, vc, wc), avg))))
+                res[f"coarse_{name}"] = {"steps": done, "seconds": t, "rel_l2_vs_fine": num / den,
+                                         "mean_velocity": [float(c.double().mean()) for c in (uc, vc, wc)]}
+        out[f"margin{m}"] = res
     print(json.dumps(out), flush=True)
     return 0
 

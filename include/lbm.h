@@ -328,6 +328,8 @@ typedef struct {
     double  tau, nu, eps; /* as in lbm_params (nu < 0 selects nu_eff)                  */
     double  gx, gy, gz;   /* constant body force                                        */
     int32_t storage;      /* LBM_F32 or LBM_F64 deviation storage                      */
+    int32_t margin;       /* lbm3d_local_keff_batch only: oversampling margin m in     */
+                          /* [0, 32] (0: plain local problems); grids ignore it        */
 } lbm3d_params;
 typedef struct lbm3d_grid lbm3d_grid;
 
@@ -382,8 +384,11 @@ lbm_status lbm3d_block_average(const float *in_dev, int32_t nx, int32_t ny, int3
  * cluster of at most 16 CTAs (up to 32 cells wide in FP32, 16 in FP64) run one
  * job per cluster entirely on chip; larger cubes run with their 3 n jobs stacked
  * in device memory (allocated and freed by the call); the environment variable
- * LBM_LOCAL3_GLOBAL=1 sends every size that second way. Returns the worst
- * status; leaves outside the field or with size outside [1, 256] give
+ * LBM_LOCAL3_GLOBAL=1 sends every size that second way. With p->margin = m > 0
+ * (oversampling) each run is on the leaf grown by m cells on every side, cut from
+ * the field with periodic wrap at its edges, and the stop test and Eq. 17 use the
+ * mean over the inner leaf only. Returns the worst status; leaves outside the
+ * field, size + 2 m outside [1, 256] or m outside [0, min(32, nx, ny, nz)] give
  * LBM_EINVAL. */
 typedef struct { int32_t x0, y0, z0, size; } lbm3d_leaf;
 lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev, const lbm3d_leaf *leaves_dev,

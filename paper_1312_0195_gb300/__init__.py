@@ -370,10 +370,12 @@ class Params3D:
     gy: float = 0.0
     gz: float = 0.0
     storage: int = LBM_F32
+    margin: int = 0           # oversampling margin of the 3-D local problems
 
     def c(self) -> _abi.lbm3d_params:
         return _abi.lbm3d_params(int(self.nx), int(self.ny), int(self.nz), float(self.tau), float(self.nu),
-                                 float(self.eps), float(self.gx), float(self.gy), float(self.gz), int(self.storage))
+                                 float(self.eps), float(self.gx), float(self.gy), float(self.gz), int(self.storage),
+                                 int(self.margin))
 
 
 def lbm3d_grid_create(params: Params3D, kappa, stream=None) -> C.c_void_p:
@@ -388,7 +390,7 @@ def lbm3d_coarse_params(params: Params3D, block: int) -> Params3D:
     p = params.c()
     _check(_abi.lib().lbm3d_coarse_params(C.byref(p), int(block), C.byref(out)))
     return Params3D(nx=out.nx, ny=out.ny, nz=out.nz, tau=out.tau, nu=out.nu, eps=out.eps, gx=out.gx, gy=out.gy,
-                    gz=out.gz, storage=out.storage)
+                    gz=out.gz, storage=out.storage, margin=out.margin)
 
 
 def lbm3d_coarse_grid_create(fine_params: Params3D, block: int, keff_coarse, stream=None) -> C.c_void_p:

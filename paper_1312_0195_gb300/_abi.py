@@ -32,7 +32,7 @@ class lbm3d_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double), ("gz", C.c_double),
-                ("storage", C.c_int32)]
+                ("storage", C.c_int32), ("margin", C.c_int32)]
 
 
 class lbm3d_leaf(C.Structure):

@@ -393,7 +393,7 @@ struct Local3Args {
     T *dst;
     const T *coef;          // e per cell of every job
     const int *list;        // [blocks along y] the jobs still running
-    int s;
+    int s, m;               // side of the simulated cube (leaf + 2 margin), margin
     int64_t s3, plane;
     T omega, k_ru, k_j, hg;      // 1/tau, 6 tau, 3 (1 - 2 tau); hg = eps G / 2 along the job's drive axis
 };
@@ -457,8 +457,10 @@ __global__ void __launch_bounds__(256) local3d_check_kernel(Local3Args<T> a, Che
     const int s = a.s, d = job % 3;
     const int64_t base = (int64_t)job * a.s3;
     double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    const int lo = a.m, hi = s - a.m;       // the inner leaf of an oversampled cube
     for (int64_t c = threadIdx.x; c < a.s3; c += blockDim.x) {
         const int x = (int)(c % s), yz = (int)(c / s), y = yz % s, z = yz / s;
+        if (x < lo || x >= hi || y < lo || y >= hi || z < lo || z >= hi) continue;
         const Nbr nb = cube_neighbours(x, y, z, s, base);
         T g[Q19];
         pull19(a.src, a.plane, nb, g);
@@ -485,7 +487,8 @@ __global__ void __launch_bounds__(256) local3d_check_kernel(Local3Args<T> a, Che
     }
     if (threadIdx.x != 0) return;
     double m[3];
-    for (int q = 0; q < 3; ++q) m[q] = sh[q][0] / (double)a.s3;
+    const double sl = s - 2 * a.m;
+    for (int q = 0; q < 3; ++q) m[q] = sh[q][0] / (sl * sl * sl);
     const double cur = m[d];
     int st = -1;
     if (ck.regular) {
@@ -541,10 +544,11 @@ __global__ void __launch_bounds__(1024) local3d_compact_kernel(const int *active
 template <typename T>
 struct Clu3Args {
     const float *kappa;
-    int nx, ny;
+    int nx, ny, nz;
     const int4 *leaves;     // all leaves of the call
     const int *ids;         // [njobs / 3] leaf indices of this size
-    int njobs, s, L;
+    int njobs, s, L;        // s: side of the simulated cube (leaf + 2 margin)
+    int m;                  // oversampling margin: the mean is over the inner (s - 2 m)^3 leaf
     T omega, k_ru, k_j, hg;      // 1/tau, 6 tau, 3 (1 - 2 tau), eps G / 2
     double eps_nu, nu_over_g, tol;
     int k;
@@ -699,14 +703,18 @@ __device__ __forceinline__ void aa_velocity_cell(const Cell3<T> &q, const T *own
 template <typename T> __host__ __device__ constexpr int clu3_cpt() { return sizeof(T) == 4 ? 4 : 2; }
 template <typename T> __host__ __device__ constexpr int clu3_threads() { return 512; }
 
-// Cell3 of the packed cell (zl << 16 | y << 8 | x) from the table of layer addresses
+// Packed cell: zl << 16 | y << 8 | x, plus CLU3_IN when the cell lies in the inner leaf of an
+// oversampled cube (every cell without a margin)
+constexpr int CLU3_IN = 1 << 30;
+
+// Cell3 of a packed cell from the table of layer addresses
 template <typename T>
 __device__ __forceinline__ Cell3<T> cell3_of(int geo, int s, const uint32_t *zb, int z0)
 {
     Cell3<T> q;
-    const int x = geo & 255, y = (geo >> 8) & 255, z = z0 + (geo >> 16);
+    const int x = geo & 255, y = (geo >> 8) & 255, zl = (geo >> 16) & 255, z = z0 + zl;
     const uint32_t E = sizeof(T);
-    q.c = ((geo >> 16) * s + y) * s + x;
+    q.c = (zl * s + y) * s + x;
     q.xo[0] = (x == 0 ? s - 1 : x - 1) * E;
     q.xo[1] = x * E;
     q.xo[2] = (x + 1 == s ? 0 : x + 1) * E;
@@ -750,9 +758,16 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
         geo[i] = -1;
         ec[i] = T(0);
         if (c >= ncell) continue;
-        const int x = c % s, yz = c / s, y = yz % s, zl = yz / s;
-        geo[i] = (zl << 16) | (y << 8) | x;
-        const float kv = a.kappa[((int64_t)(Lf.z + z0 + zl) * a.ny + (Lf.y + y)) * a.nx + (Lf.x + x)];
+        const int x = c % s, yz = c / s, y = yz % s, zl = yz / s, z = z0 + zl;
+        const int sl = s - 2 * a.m;
+        const bool in = x >= a.m && x < a.m + sl && y >= a.m && y < a.m + sl && z >= a.m && z < a.m + sl;
+        geo[i] = (zl << 16) | (y << 8) | x | (in ? CLU3_IN : 0);
+        // the grown cube starts margin cells before the leaf, wrapping at the field's edges
+        int gx = Lf.x - a.m + x, gy = Lf.y - a.m + y, gz = Lf.z - a.m + z;
+        gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
+        gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
+        gz = gz < 0 ? gz + a.nz : (gz >= a.nz ? gz - a.nz : gz);
+        const float kv = a.kappa[((int64_t)gz * a.ny + gy) * a.nx + gx];
         double e;
         if (!(kv >= 0.0f)) e = 1.0;
         else if (a.eps_nu == 0.0 || isinf(kv)) e = 0.0;
@@ -796,7 +811,7 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
         const bool odd = (t & 1) != 0;
 #pragma unroll
         for (int j = 0; j < CLU3_CPT; ++j) {
-            if (geo[j] < 0) continue;
+            if (geo[j] < 0 || !(geo[j] & CLU3_IN)) continue;
             int gj = geo[j];
             asm volatile("" : "+r"(gj));
             const Cell3<T> q = cell3_of<T>(gj, s, zb, z0);
@@ -843,7 +858,7 @@ __global__ void __launch_bounds__(clu3_threads<T>(), 1) local3d_cluster_kernel(C
             m[2] += ld_cluster<double>(pq + 16);
         }
         const bool abort_now = ld_cluster<double>(cluster_addr(part, 0) + 24) != 0.0;
-        const double inv = 1.0 / ((double)s2 * s);
+        const double sl = s - 2 * a.m, inv = 1.0 / (sl * sl * sl);
         for (int q = 0; q < 3; ++q) m[q] *= inv;
         const double cur = m[d];
         int st = -1;
@@ -887,9 +902,10 @@ inline size_t clu3_smem_bytes(int64_t PS, size_t esz)
 }
 
 // e per cell of every job of a chunk: job j copies its leaf's cube of the field
-__global__ void __launch_bounds__(256) local3d_coef_kernel(const float *kappa, int nx, int ny, const int4 *leaves,
-                                                           const int *job_leaf, int s, int64_t s3, int njobs,
-                                                           double eps_nu, float *coef_f, double *coef_d)
+__global__ void __launch_bounds__(256) local3d_coef_kernel(const float *kappa, int nx, int ny, int nz,
+                                                           const int4 *leaves, const int *job_leaf, int s, int m,
+                                                           int64_t s3, int njobs, double eps_nu, float *coef_f,
+                                                           double *coef_d)
 {
     const int64_t total = (int64_t)njobs * s3;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -897,7 +913,11 @@ __global__ void __launch_bounds__(256) local3d_coef_kernel(const float *kappa, i
         const int64_t c = i - (int64_t)job * s3;
         const int x = (int)(c % s), yz = (int)(c / s), y = yz % s, z = yz / s;
         const int4 L = leaves[job_leaf[job]];
-        const float k = kappa[((int64_t)(L.z + z) * ny + (L.y + y)) * nx + (L.x + x)];
+        int gx = L.x - m + x, gy = L.y - m + y, gz = L.z - m + z;      // grown cube, periodic field
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+        gz = gz < 0 ? gz + nz : (gz >= nz ? gz - nz : gz);
+        const float k = kappa[((int64_t)gz * ny + gy) * nx + gx];
         double e;
         if (!(k >= 0.0f)) e = 1.0;
         else if (eps_nu == 0.0 || isinf(k)) e = 0.0;
@@ -994,7 +1014,7 @@ namespace {
 // launched) when the cube does not fit the shared memory of a cluster of at most 16
 // CTAs or the device cannot schedule such a cluster.
 lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const int4 *d_l4,
-                            const std::vector<int> &ids, int *d_ids, int sz, double nu, double g_const,
+                            const std::vector<int> &ids, int *d_ids, int sz, int m, double nu, double g_const,
                             double tol_rel, int64_t max_steps, int32_t check_every, int optin,
                             unsigned long long *d_clock, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
                             cudaStream_t st)
@@ -1060,7 +1080,7 @@ lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const
         cfg.gridDim = dim3((unsigned)(3 * (int64_t)nl * C));
         cudaError_t e;
         if (f64) {
-            Clu3Args<double> a{kappa_dev, p->nx, p->ny, d_l4, d_ids + l0, 3 * nl, sz, L, 1.0 / p->tau, 6.0 * p->tau,
+            Clu3Args<double> a{kappa_dev, p->nx, p->ny, p->nz, d_l4, d_ids + l0, 3 * nl, sz, L, m, 1.0 / p->tau, 6.0 * p->tau,
                                3.0 * (1.0 - 2.0 * p->tau), 0.5 * p->eps * g_const, p->eps * nu, nu / g_const, tol_rel,
                                check_every, max_steps, keff_dev, status_dev, steps_dev, d_clock,
                                reinterpret_cast<int *>(d_clock + 1),
@@ -1068,7 +1088,7 @@ lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const
             void *args[] = {&a};
             e = cudaLaunchKernelExC(&cfg, fn, args);
         } else {
-            Clu3Args<float> a{kappa_dev, p->nx, p->ny, d_l4, d_ids + l0, 3 * nl, sz, L, (float)(1.0 / p->tau),
+            Clu3Args<float> a{kappa_dev, p->nx, p->ny, p->nz, d_l4, d_ids + l0, 3 * nl, sz, L, m, (float)(1.0 / p->tau),
                               (float)(6.0 * p->tau), (float)(3.0 * (1.0 - 2.0 * p->tau)), (float)(0.5 * p->eps * g_const),
                               p->eps * nu, nu / g_const, tol_rel, check_every, max_steps, keff_dev, status_dev,
                               steps_dev, d_clock, reinterpret_cast<int *>(d_clock + 1),
@@ -1309,14 +1329,18 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
     std::vector<lbm3d_leaf> lv(n_leaves);
     L3_CUDA(cudaMemcpyAsync(lv.data(), leaves_dev, sizeof(lbm3d_leaf) * n_leaves, cudaMemcpyDeviceToHost, st));
     L3_CUDA(cudaStreamSynchronize(st));
-    std::map<int, std::vector<int>> by_size;
+    const int m = p->margin;
+    if (m < 0 || m > 32 || m > p->nx || m > p->ny || m > p->nz)
+        return fail(LBM_EINVAL, "margin %d must be in [0, 32] and at most nx, ny, nz", m);
+    std::map<int, std::vector<int>> by_size;       // by the side of the simulated cube, size + 2 margin
     for (int i = 0; i < n_leaves; ++i) {
         const lbm3d_leaf &L = lv[i];
         if (L.size < 1 || L.size > 256) return fail(LBM_EINVAL, "leaf %d: size %d outside [1, 256]", i, L.size);
         if (L.x0 < 0 || L.y0 < 0 || L.z0 < 0 || (int64_t)L.x0 + L.size > p->nx || (int64_t)L.y0 + L.size > p->ny ||
             (int64_t)L.z0 + L.size > p->nz)
             return fail(LBM_EINVAL, "leaf %d (%d, %d, %d, %d) lies outside the field", i, L.x0, L.y0, L.z0, L.size);
-        by_size[L.size].push_back(i);
+        if (L.size + 2 * m > 256) return fail(LBM_EINVAL, "leaf %d: size + 2 margin exceeds 256", i);
+        by_size[L.size + 2 * m].push_back(i);
     }
     L3_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int32_t) * n_leaves, st));
     if (steps_dev) L3_CUDA(cudaMemsetAsync(steps_dev, 0, sizeof(int32_t) * 3 * n_leaves, st));
@@ -1366,7 +1390,7 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
         const int sz = kv.first;
         const int64_t s3 = (int64_t)sz * sz * sz;
         if (cluster_ok) {
-            const lbm_status cs = run_cluster_size(p, kappa_dev, d_l4, kv.second, d_ids, sz, nu, g_const, tol_rel,
+            const lbm_status cs = run_cluster_size(p, kappa_dev, d_l4, kv.second, d_ids, sz, m, nu, g_const, tol_rel,
                                                    max_steps, check_every, optin, d_clock, keff_dev, status_dev,
                                                    steps_dev, st);
             // LBM_ETIMEOUT is in the leaves' status already; LBM_EINVAL: the cube does not fit, take the global path
@@ -1413,7 +1437,7 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
             int nact = njobs;
             L3_CUDA2(cudaMemcpyAsync(d_nact, &nact, sizeof(int), cudaMemcpyHostToDevice, st));
             const int nb = (int)std::min<int64_t>((cells + 255) / 256, 8192);
-            local3d_coef_kernel<<<nb, 256, 0, st>>>(kappa_dev, p->nx, p->ny, d_l4, d_jl, sz, s3, njobs, p->eps * nu,
+            local3d_coef_kernel<<<nb, 256, 0, st>>>(kappa_dev, p->nx, p->ny, p->nz, d_l4, d_jl, sz, m, s3, njobs, p->eps * nu,
                                                     f64 ? nullptr : static_cast<float *>(coef),
                                                     f64 ? static_cast<double *>(coef) : nullptr);
             count_launches(1);
@@ -1425,12 +1449,12 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
                 for (int64_t i = 0; i < nstep; ++i) {
                     if (f64) {
                         Local3Args<double> a{static_cast<const double *>(buf[cur]), static_cast<double *>(buf[1 - cur]),
-                                             static_cast<const double *>(coef), d_list, sz, s3, plane,
+                                             static_cast<const double *>(coef), d_list, sz, m, s3, plane,
                                              1.0 / p->tau, 6.0 * p->tau, 3.0 * (1.0 - 2.0 * p->tau), 0.5 * p->eps * g_const};
                         local3d_step_kernel<double><<<sgrid, 256, 0, st>>>(a);
                     } else {
                         Local3Args<float> a{static_cast<const float *>(buf[cur]), static_cast<float *>(buf[1 - cur]),
-                                            static_cast<const float *>(coef), d_list, sz, s3, plane,
+                                            static_cast<const float *>(coef), d_list, sz, m, s3, plane,
                                             (float)(1.0 / p->tau), (float)(6.0 * p->tau), (float)(3.0 * (1.0 - 2.0 * p->tau)),
                                             (float)(0.5 * p->eps * g_const)};
                         local3d_step_kernel<float><<<sgrid, 256, 0, st>>>(a);
@@ -1442,13 +1466,13 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
                           d_active, d_prev, d_jl, keff_dev, status_dev, steps_dev, d_nact};
                 if (f64) {
                     Local3Args<double> a{static_cast<const double *>(buf[cur]), nullptr, static_cast<const double *>(coef),
-                                         d_list, sz, s3, plane, 1.0 / p->tau, 6.0 * p->tau, 3.0 * (1.0 - 2.0 * p->tau),
+                                         d_list, sz, m, s3, plane, 1.0 / p->tau, 6.0 * p->tau, 3.0 * (1.0 - 2.0 * p->tau),
                                          0.5 * p->eps * g_const};
                     local3d_check_kernel<double><<<nlist, 256, 0, st>>>(a, ck);
                 } else {
                     Local3Args<float> a{static_cast<const float *>(buf[cur]), nullptr, static_cast<const float *>(coef),
-                                        d_list, sz, s3, plane, (float)(1.0 / p->tau), (float)(2.0 * p->tau),
-                                        (float)(1.0 - 2.0 * p->tau), (float)(0.5 * p->eps * g_const)};
+                                        d_list, sz, m, s3, plane, (float)(1.0 / p->tau), (float)(6.0 * p->tau),
+                                        (float)(3.0 * (1.0 - 2.0 * p->tau)), (float)(0.5 * p->eps * g_const)};
                     local3d_check_kernel<float><<<nlist, 256, 0, st>>>(a, ck);
                 }
                 count_launches(nstep + 1);

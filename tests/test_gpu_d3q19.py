@@ -244,3 +244,38 @@ def test_local_keff3_full_size_sampled():
         ref = oracle.local_keff3(kap[z0:z0 + s, y0:y0 + s, x0:x0 + s].astype(np.float64), 1.0, 1.0 / 6.0, 1.0,
                                  1e-6, tol=0.0, max_steps=300)["keff"]
         np.testing.assert_allclose(ke[i], ref, rtol=0, atol=1e-5 * np.abs(np.diag(ref)).max())
+
+
+@pytest.mark.parametrize("storage,force_global", [(0, False), (2, False), (0, True)])
+def test_local_keff3_oversampled_matches_oracle(storage, force_global, monkeypatch):
+    """Oversampling (margin m): leaves grown by m cells on every side, cut from the field with
+    periodic wrap (leaves at the field's edges wrap), inner-window mean; the cluster path and,
+    forced, the HBM path against the oracle's oversampled problem."""
+    import torch
+    lbm = _lbm()
+    if force_global:
+        monkeypatch.setenv("LBM_LOCAL3_GLOBAL", "1")
+    kap = _field(20, 18, 22, seed=78)
+    leaves = [(0, 0, 0, 8), (14, 10, 12, 8), (5, 6, 7, 4), (18, 14, 16, 4)]
+    for m in (2, 3):
+        nz, ny, nx = kap.shape
+        p = lbm.Params3D(nx=nx, ny=ny, nz=nz, tau=1.0, nu=1.0 / 6.0, eps=1.0, storage=storage, margin=m)
+        ke, st, steps, _ = lbm.local_keff3(p, torch.from_numpy(kap).cuda(),
+                                           torch.tensor(leaves, dtype=torch.int32, device="cuda"), 1e-6, 0.0, 300, 64)
+        ke = ke.cpu().numpy()
+        assert (steps.cpu().numpy() == 300).all() and (st.cpu().numpy() == 0).all()
+        for i, (x0, y0, z0, s) in enumerate(leaves):
+            grown = oracle.grown_cube(kap.astype(np.float64), x0, y0, z0, s, m)
+            ref = oracle.local_keff3(grown, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=0.0, max_steps=300, margin=m)["keff"]
+            tol = 1e-9 if storage == 2 else 1e-5
+            np.testing.assert_allclose(ke[i], ref, rtol=0, atol=tol * np.abs(np.diag(ref)).max())
+
+
+def test_local_keff3_margin_limits_are_rejected():
+    import torch
+    lbm = _lbm()
+    kap = torch.full((8, 8, 8), 0.01, device="cuda")
+    lv = torch.tensor([[0, 0, 0, 4]], dtype=torch.int32, device="cuda")
+    for m in (33, 9, -1):
+        with pytest.raises(lbm.LbmError):
+            lbm.local_keff3(lbm.Params3D(nx=8, ny=8, nz=8, tau=1.0, margin=m), kap, lv)
