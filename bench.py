@@ -260,6 +260,33 @@ def measure_d3q19(lbm, torch, n=256, steps=200):
     out["local_keff"] = {"workload": f"all {leaves.shape[0]} cubes of {b}^3, tau 1, G 1e-6 along x, y, z, tol 1e-8",
                          "patches_per_s": leaves.shape[0] / t, "seconds": t, "glups": lups / t / 1e9,
                          "converged": int((status == 0).sum())}
+    # the upscaled model on the same box (Eq. 18 in 3-D): fine run at tau 1 for 20k steps against the
+    # coarse run with those K* for 1250 steps (the same physical time), block-averaged velocity
+    fine_steps, nb = 20000, n // b
+    pf = lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0, gx=1e-6)
+    with lbm.Grid3D(pf, kap) as G:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.step(fine_steps)
+        torch.cuda.synchronize()
+        t_fine = time.perf_counter() - t0
+        _, u, v, w = G.fields()
+        avg = [lbm.lbm3d_block_average(f, b).double() for f in (u, v, w)]
+        del u, v, w
+    with lbm.Grid3D.coarse(pf, b, keff.reshape(nb, nb, nb, 3, 3)) as C:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        C.step(fine_steps // b)
+        torch.cuda.synchronize()
+        t_coarse = time.perf_counter() - t0
+        _, uc, vc, wc = C.fields()
+    num = sum(((c.double() - a) ** 2).sum() for c, a in zip((uc, vc, wc), avg))
+    out["upscaled"] = {"workload": f"fine {n}^3 tau 1, G (1e-6, 0, 0), {fine_steps} steps; coarse {nb}^3 with the "
+                                   f"local K* above, {fine_steps // b} steps",
+                       "fine_seconds": t_fine, "fine_mlups": n ** 3 * fine_steps / t_fine / 1e6,
+                       "coarse_seconds": t_coarse,
+                       "rel_l2_vs_fine": float(torch.sqrt(num / sum((a ** 2).sum() for a in avg))),
+                       "coarse_over_fine_mean_u": float(uc.double().mean() / avg[0].mean())}
     return out
 
 
@@ -268,6 +295,14 @@ def _oracle_leaf(args):
     import oracle
     patch, tol = args
     oracle.local_keff(patch, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=tol, max_steps=200000)
+    return 0
+
+
+def _oracle_cube(args):
+    """One three-dimensional local problem (three drives) by the FP64 oracle (process-pool worker)."""
+    import oracle
+    cube, tol, max_steps = args
+    oracle.local_keff3(cube, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=tol, max_steps=max_steps)
     return 0
 
 
@@ -280,11 +315,13 @@ def _oracle_forward(args):
     return 0
 
 
-def measure_cpu_oracles(kap_np, leaf_sample=64, patch_sample=32, seed=12):
-    """Oracle rates for the two other units of the metric, on the host cores (a spawn-started
+def measure_cpu_oracles(kap_np, leaf_sample=64, patch_sample=32, cube_sample=16, seed=12):
+    """Oracle rates for the other units of the bench, on the host cores (a spawn-started
     process pool, one process per core, each running the oracle as it stands):
     local K* (both drives, tol 1e-8) on a seeded sample of the quadtree leaves of the bench
-    field, and the 4-model surrogate forward on a seeded sample of their patches."""
+    field, the 4-model surrogate forward on a seeded sample of their patches, and 3-D local
+    problems (three drives, 1024 steps each) on a seeded sample of the 16^3 cubes of the d3q19
+    block's field, as lattice updates per second."""
     import multiprocessing as mp
     import synth
     from oracle import surrogate as osur
@@ -294,6 +331,11 @@ def measure_cpu_oracles(kap_np, leaf_sample=64, patch_sample=32, seed=12):
     patches = [np.array(kap_np[y:y + s, x:x + s], dtype=np.float64) for x, y, s in pick]
     xs = [osur.make_input(osur.resample_patch(np.log(p)), p.shape[0], 0.0, 1.0) for p in patches[:patch_sample]]
     workers = os.cpu_count() or 1
+    k3 = synth.lognormal_kappa3d(256, 256, 256, 8.0, 2.0, seed=7)
+    corners = rng.choice(16 ** 3, cube_sample, replace=False)
+    cubes = [np.array(k3[16 * (i // 256):16 * (i // 256) + 16, 16 * (i // 16 % 16):16 * (i // 16 % 16) + 16,
+                         16 * (i % 16):16 * (i % 16) + 16], dtype=np.float64) for i in corners]
+    del k3
     out = {}
     with mp.get_context("spawn").Pool(workers) as pool:
         pool.map(_oracle_leaf, [(patches[0], 1e-8)] * workers)          # start-up outside the timing
@@ -309,6 +351,15 @@ def measure_cpu_oracles(kap_np, leaf_sample=64, patch_sample=32, seed=12):
         out["surrogate_forward"] = {"value": len(xs) / dt, "unit": "patches/s", "cores": workers,
                                     "kind": "oracle",
                                     "sample": f"4-model FP64 forward of {len(xs)} of those leaves' patches ({dt:.1f} s)"}
+        # fixed steps, so the sample's time is bounded; the unit is lattice updates (the GPU block
+        # reports both cubes/s to tol 1e-8 and GLUPS)
+        t0 = time.perf_counter()
+        pool.map(_oracle_cube, [(c, 0.0, 1024) for c in cubes], chunksize=1)
+        dt = time.perf_counter() - t0
+        out["local_keff3"] = {"value": len(cubes) * 3 * 1024 * 16 ** 3 / dt / 1e6, "unit": "MLUPS",
+                              "cores": workers, "kind": "oracle",
+                              "sample": f"{len(cubes)} seeded 16^3 cubes of the d3q19 block's 256^3 field, three "
+                                        f"drives of 1024 steps each ({dt:.1f} s)"}
     return out
 
 
