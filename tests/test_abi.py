@@ -15,7 +15,7 @@ def _declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"//[^\n]*", "", src)
-    names = set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
+    names = set(re.findall(r"\b(lbm(?:3d)?_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
 
 
@@ -28,7 +28,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("lbm_grid_create", "lbm_grid_destroy", "lbm_step", "lbm_get_fields",
-                     "lbm_mean_velocity", "lbm_last_error"):
+                     "lbm_mean_velocity", "lbm_last_error", "lbm3d_grid_create", "lbm3d_local_keff_batch",
+                     "lbm3d_coarse_grid_create", "lbm3d_block_average"):
         assert required in names
 
 
@@ -87,3 +88,39 @@ def test_python_binding_raises_typed_error():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_grid_create(lbm.Params(nx=0, ny=4, tau=1.0), None)
     assert ei.value.status == lbm.LBM_EINVAL
+
+
+def _params3(**kw):
+    from paper_1312_0195_gb300 import _abi
+    base = dict(nx=8, ny=8, nz=8, tau=1.0, nu=-1.0, eps=1.0, gx=0.0, gy=0.0, gz=0.0, storage=0, margin=0)
+    base.update(kw)
+    return _abi.lbm3d_params(**base)
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(nz=70000), dict(tau=0.3), dict(eps=-1.0), dict(storage=1),
+                                 dict(gz=float("nan"))])
+def test_3d_create_rejects_bad_params(lib, bad):
+    h = C.c_void_p()
+    assert lib.lbm3d_grid_create(C.byref(_params3(**bad)), None, None, C.byref(h)) == 1
+    assert not h.value
+
+
+def test_3d_host_side_validation(lib):
+    """The 3-D calls reject invalid sizes, parameters and host pointers before any device work."""
+    from paper_1312_0195_gb300 import _abi
+    p = _params3()
+    out = _abi.lbm3d_params()
+    assert lib.lbm3d_coarse_params(C.byref(p), 3, C.byref(out)) == 1           # 8 is not a multiple of 3
+    assert lib.lbm3d_coarse_params(C.byref(p), 4, C.byref(out)) == 0
+    assert (out.nx, out.ny, out.nz) == (2, 2, 2) and abs(out.tau - 0.625) < 1e-15 and abs(out.nu - 1.0 / 24) < 1e-15
+    h = C.c_void_p()
+    assert lib.lbm3d_coarse_grid_create(C.byref(p), 4, None, None, C.byref(h)) == 1
+    assert lib.lbm3d_block_average(None, 8, 8, 8, 3, None, None) == 1
+    host = (C.c_float * 512)()
+    assert lib.lbm3d_block_average(host, 8, 8, 8, 4, host, None) == 1              # host pointers
+    args = (None, None, 1, 1e-6, 1e-8, 1000, 64, None, None, None, None)
+    assert lib.lbm3d_local_keff_batch(C.byref(p), *args) == 1                      # host/NULL pointers
+    assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, -1, 1e-6, 1e-8, 1000, 64, None, None, None, None) == 1
+    assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 1, 0.0, 1e-8, 1000, 64, None, None, None, None) == 1
+    assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 1, 1e-6, 1e-8, 0, 64, None, None, None, None) == 1
+    assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 0, 1e-6, 1e-8, 1000, 64, None, None, None, None) == 0
