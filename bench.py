@@ -229,13 +229,15 @@ def measure_storage_error(lbm, torch, kap_np, crop=512, steps=1000):
 def measure_d3q19(lbm, torch, n=256, steps=200):
     """The scheme on the D3Q19 lattice (Section 2 in three dimensions): n^3 periodic box,
     log-normal K (sigma 2, ell 8, seed 7), tau = 0.6, nu = nu_eff, G = (1e-6, 0, 0); MLUPS and the
-    fraction of the measured HBM bandwidth at 19 x 2 x 4 + 4 = 156 B/LUP (FP32), 308 B/LUP (FP64)."""
+    fraction of the measured HBM bandwidth at 19 x 2 x 4 + 4 = 156 B/LUP (FP32), 80 B/LUP (FP16
+    scaled storage), 308 B/LUP (FP64)."""
     import synth
     kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
     peaks = measured_peaks()
     out = {"workload": f"D3Q19 {n}^3 periodic, log-normal K (sigma 2, ell 8, seed 7), tau 0.6, nu = nu_eff, "
                        "G = (1e-6, 0, 0)"}
-    for name, st, bpl, k in (("f32", lbm.LBM_F32, 156, steps), ("f64", lbm.LBM_F64, 308, steps // 4)):
+    for name, st, bpl, k in (("f32", lbm.LBM_F32, 156, steps), ("f16", lbm.LBM_F16, 80, steps),
+                             ("f64", lbm.LBM_F64, 308, steps // 4)):
         p = lbm.Params3D(nx=n, ny=n, nz=n, tau=TAU, nu=NU, eps=1.0, gx=1e-6, storage=st)
         with lbm.Grid3D(p, kap) as g:
             g.step(10)

@@ -327,7 +327,9 @@ typedef struct {
     int32_t nx, ny, nz;   /* lattice size, each >= 1; ny, nz <= 65535                   */
     double  tau, nu, eps; /* as in lbm_params (nu < 0 selects nu_eff)                  */
     double  gx, gy, gz;   /* constant body force                                        */
-    int32_t storage;      /* LBM_F32 or LBM_F64 deviation storage                      */
+    int32_t storage;      /* LBM_F32, LBM_F64, or LBM_F16 (scalar-kappa grids only:   */
+                          /* deviations scaled by an automatic power of two S with    */
+                          /* S max|g| near 2^12, FP32 arithmetic, 80 B per update)    */
     int32_t margin;       /* lbm3d_local_keff_batch only: oversampling margin m in     */
                           /* [0, 32] (0: plain local problems); grids ignore it        */
 } lbm3d_params;

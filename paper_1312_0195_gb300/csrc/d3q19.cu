@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <vector>
 
@@ -42,14 +43,25 @@ __host__ __device__ constexpr int cz(int a)
     return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1 : ((a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0);
 }
 
+// Storage type T and compute type: FP16 storage (scaled deviations) computes in FP32.
+template <typename T> struct Comp3 { using type = T; };
+template <> struct Comp3<__half> { using type = float; };
+__device__ __forceinline__ float to_comp(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_comp(float v) { return v; }
+__device__ __forceinline__ double to_comp(double v) { return v; }
+template <typename T, typename C> __device__ __forceinline__ T from_comp(C v) { return (T)v; }
+template <> __device__ __forceinline__ __half from_comp<__half, float>(float v) { return __float2half_rn(v); }
+
 template <typename T>
 struct Step3Args {
+    using C = typename Comp3<T>::type;
     const T *src;
     T *dst;
-    const T *coef;          // e per cell, or the 9 planes E_ij of a tensor K* (E_ij at (3 i + j) plane)
+    const C *coef;          // e per cell, or the 9 planes E_ij of a tensor K* (E_ij at (3 i + j) plane)
     int nx, ny, nz;
     int64_t plane;          // elements per population (and coefficient) plane
-    T omega, k_ru, k_j, hgx, hgy, hgz;   // 1/tau, 6 tau, 3 (1 - 2 tau), eps G / 2
+    C omega, k_ru, k_j, hgx, hgy, hgz;   // 1/tau, 6 tau, 3 (1 - 2 tau), eps G / 2
+    C rho0, inv_scale;      // the storage scale S: populations are S g, so rho = S + S drho
 };
 
 // Index of cell (x - e_x, y - e_y, z - e_z) from the wrapped neighbour offsets.
@@ -75,19 +87,20 @@ __device__ __forceinline__ Nbr neighbours(int x, int y, int z, int nx, int ny, i
     return n;
 }
 
-template <int A, typename T>
-__device__ __forceinline__ void pull_one(const T *__restrict__ src, int64_t plane, const Nbr &nb, T (&g)[Q19])
+template <int A, typename T, typename C>
+__device__ __forceinline__ void pull_one(const T *__restrict__ src, int64_t plane, const Nbr &nb, C (&g)[Q19])
 {
-    g[A] = __ldg(src + A * plane + nb.template from<A>());
+    g[A] = to_comp(__ldg(src + A * plane + nb.template from<A>()));
 }
-template <typename T, int... As>
-__device__ __forceinline__ void pull_all(const T *src, int64_t plane, const Nbr &nb, T (&g)[Q19])
+template <typename T, typename C, int... As>
+__device__ __forceinline__ void pull_all(const T *src, int64_t plane, const Nbr &nb, C (&g)[Q19])
 {
     (pull_one<As>(src, plane, nb, g), ...);
 }
-template <typename T> __device__ __forceinline__ void pull19(const T *src, int64_t plane, const Nbr &nb, T (&g)[Q19])
+template <typename T, typename C>
+__device__ __forceinline__ void pull19(const T *src, int64_t plane, const Nbr &nb, C (&g)[Q19])
 {
-    pull_all<T, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(src, plane, nb, g);
+    pull_all<T, C, 0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>(src, plane, nb, g);
 }
 
 // Moments through the nine opposite pairs (a, a + 1): s_p = g_a + g_{a+1} and
@@ -171,11 +184,11 @@ template <typename T> __device__ __forceinline__ void relax19(T (&g)[Q19], T drh
 // The whole collision of one cell: moments, r = j + (eps G / 2) rho, rho u = (1 - e) r
 // (Eq. 6 times rho), 3 rho u_eq = 6 tau rho u + 3 (1 - 2 tau) j (Eq. 16 times 3), relax.
 template <typename T>
-__device__ __forceinline__ void collide19(T (&g)[Q19], T e, T hgx, T hgy, T hgz, T k_ru, T k_j, T om)
+__device__ __forceinline__ void collide19(T (&g)[Q19], T e, T hgx, T hgy, T hgz, T k_ru, T k_j, T om, T rho0 = T(1))
 {
     T drho, jx, jy, jz;
     moments19(g, drho, jx, jy, jz);
-    const T rho = T(1) + drho;
+    const T rho = rho0 + drho;
     const T rx = fma(hgx, rho, jx), ry = fma(hgy, rho, jy), rz = fma(hgz, rho, jz);
     const T rux = fma(-e, rx, rx), ruy = fma(-e, ry, ry), ruz = fma(-e, rz, rz);
     relax19(g, drho, fma(k_ru, rux, k_j * jx), fma(k_ru, ruy, k_j * jy), fma(k_ru, ruz, k_j * jz), om);
@@ -192,11 +205,11 @@ __device__ __forceinline__ void drag_tensor(const T (&E)[9], T rx, T ry, T rz, T
 }
 template <typename T>
 __device__ __forceinline__ void collide19_tensor(T (&g)[Q19], const T (&E)[9], T hgx, T hgy, T hgz, T k_ru, T k_j,
-                                                 T om)
+                                                 T om, T rho0 = T(1))
 {
     T drho, jx, jy, jz, rux, ruy, ruz;
     moments19(g, drho, jx, jy, jz);
-    const T rho = T(1) + drho;
+    const T rho = rho0 + drho;
     drag_tensor(E, fma(hgx, rho, jx), fma(hgy, rho, jy), fma(hgz, rho, jz), rux, ruy, ruz);
     relax19(g, drho, fma(k_ru, rux, k_j * jx), fma(k_ru, ruy, k_j * jy), fma(k_ru, ruz, k_j * jz), om);
 }
@@ -204,24 +217,25 @@ __device__ __forceinline__ void collide19_tensor(T (&g)[Q19], const T (&E)[9], T
 template <typename T, bool TENSOR>
 __global__ void __launch_bounds__(256) step3d_kernel(Step3Args<T> a)
 {
+    using C = typename Comp3<T>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= a.nx) return;
     const T *__restrict__ src = a.src;
     T *__restrict__ dst = a.dst;
     const Nbr nb = neighbours(x, y, z, a.nx, a.ny, a.nz);
-    T g[Q19];
+    C g[Q19];
     pull19(src, a.plane, nb, g);
     const int64_t c = nb.z[1] + nb.y[1] + x;
     if constexpr (TENSOR) {
-        T E[9];
+        C E[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) E[k] = __ldg(a.coef + k * a.plane + c);
-        collide19_tensor(g, E, a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega);
+        collide19_tensor(g, E, a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega, a.rho0);
     } else {
-        collide19(g, __ldg(a.coef + c), a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega);
+        collide19(g, __ldg(a.coef + c), a.hgx, a.hgy, a.hgz, a.k_ru, a.k_j, a.omega, a.rho0);
     }
 #pragma unroll
-    for (int q = 0; q < Q19; ++q) dst[q * a.plane + c] = g[q];
+    for (int q = 0; q < Q19; ++q) dst[q * a.plane + c] = from_comp<T>(g[q]);
 }
 
 // Density and flow velocity (Eq. 15) of the streamed state, optional FP64 block sums of u.
@@ -229,31 +243,32 @@ template <typename T, bool TENSOR>
 __global__ void __launch_bounds__(128) fields3d_kernel(Step3Args<T> a, float *rho_o, float *u_o, float *v_o,
                                                        float *w_o, double *partials)
 {
+    using C = typename Comp3<T>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     double su = 0.0, sv = 0.0, sw = 0.0;
     if (x < a.nx) {
         const Nbr nb = neighbours(x, y, z, a.nx, a.ny, a.nz);
-        T g[Q19];
+        C g[Q19];
         pull19(a.src, a.plane, nb, g);
         const int64_t c = nb.z[1] + nb.y[1] + x;
-        T drho, jx, jy, jz;
+        C drho, jx, jy, jz;
         moments19(g, drho, jx, jy, jz);
-        const T rho = T(1) + drho;
-        const T rx = fma(a.hgx, rho, jx), ry = fma(a.hgy, rho, jy), rz = fma(a.hgz, rho, jz);
-        T rux, ruy, ruz;
+        const C rho = a.rho0 + drho;        // scaled by S, which cancels in u = rho u / rho
+        const C rx = fma(a.hgx, rho, jx), ry = fma(a.hgy, rho, jy), rz = fma(a.hgz, rho, jz);
+        C rux, ruy, ruz;
         if constexpr (TENSOR) {
-            T E[9];
+            C E[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) E[k] = a.coef[k * a.plane + c];
             drag_tensor(E, rx, ry, rz, rux, ruy, ruz);
         } else {
-            const T e = a.coef[c];
+            const C e = a.coef[c];
             rux = fma(-e, rx, rx);
             ruy = fma(-e, ry, ry);
             ruz = fma(-e, rz, rz);
         }
-        const T ux = rux / rho, uy = ruy / rho, uz = ruz / rho;
-        if (rho_o) rho_o[c] = (float)rho;
+        const C ux = rux / rho, uy = ruy / rho, uz = ruz / rho;
+        if (rho_o) rho_o[c] = (float)fma(drho, a.inv_scale, C(1));
         if (u_o) u_o[c] = (float)ux;
         if (v_o) v_o[c] = (float)uy;
         if (w_o) w_o[c] = (float)uz;
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(1024) reduce3_kernel(const double *partials, i
 template <typename T>
 __global__ void __launch_bounds__(256) coef3d_kernel(const float *kappa, T *coef, int64_t n, double eps_nu, unsigned *flags)
 {
-    unsigned bad = 0u;
+    unsigned bad = 0u, kmax = 0u;    // kmax: bits of the largest finite kappa (ordered like the floats, all >= 0)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float k = kappa[i];
         double e;
@@ -318,9 +333,11 @@ __global__ void __launch_bounds__(256) coef3d_kernel(const float *kappa, T *coef
         else if (eps_nu == 0.0 || isinf(k)) e = 0.0;
         else if (k == 0.0f) e = 1.0;
         else e = eps_nu / (2.0 * (double)k + eps_nu);
+        if (k >= 0.0f && !isinf(k)) kmax = max(kmax, __float_as_uint(k));
         coef[i] = (T)e;
     }
     if (bad) atomicOr(flags, 1u);
+    if (kmax) atomicMax(flags + 1, kmax);
 }
 
 // E = c (K + c I)^-1 per coarse cell, K = scale keff (fine lattice units to coarse),
@@ -941,6 +958,7 @@ struct lbm3d_grid {
     unsigned *flags = nullptr;
     int cur = 0;
     int tensor = 0;         // coefficients are the 9 planes of E (coarse run with tensor K*)
+    double S = 1.0;         // FP16 storage: populations are stored as S g
     int64_t n = 0, plane = 0, nblocks = 0;
     size_t esz = 4;
 };
@@ -952,20 +970,23 @@ namespace {
 template <typename T>
 Step3Args<T> args3(const lbm3d_grid *g, int src)
 {
+    using C = typename Comp3<T>::type;
     Step3Args<T> a;
     a.src = static_cast<const T *>(g->buf[src]);
     a.dst = static_cast<T *>(g->buf[1 - src]);
-    a.coef = static_cast<const T *>(g->coef);
+    a.coef = static_cast<const C *>(g->coef);
     a.nx = g->p.nx;
     a.ny = g->p.ny;
     a.nz = g->p.nz;
     a.plane = g->plane;
-    a.omega = (T)(1.0 / g->p.tau);
-    a.k_ru = (T)(6.0 * g->p.tau);
-    a.k_j = (T)(3.0 * (1.0 - 2.0 * g->p.tau));
-    a.hgx = (T)(0.5 * g->p.eps * g->p.gx);
-    a.hgy = (T)(0.5 * g->p.eps * g->p.gy);
-    a.hgz = (T)(0.5 * g->p.eps * g->p.gz);
+    a.omega = (C)(1.0 / g->p.tau);
+    a.k_ru = (C)(6.0 * g->p.tau);
+    a.k_j = (C)(3.0 * (1.0 - 2.0 * g->p.tau));
+    a.hgx = (C)(0.5 * g->p.eps * g->p.gx);
+    a.hgy = (C)(0.5 * g->p.eps * g->p.gy);
+    a.hgz = (C)(0.5 * g->p.eps * g->p.gz);
+    a.rho0 = (C)g->S;
+    a.inv_scale = (C)(1.0 / g->S);
     return a;
 }
 
@@ -974,7 +995,9 @@ dim3 grid3(const lbm3d_grid *g, int threads) { return dim3((g->p.nx + threads - 
 void launch_fields3(const lbm3d_grid *g, float *rho, float *u, float *v, float *w, double *partials)
 {
     const dim3 gr = grid3(g, 128);
-    if (g->esz == 8) {
+    if (g->esz == 2) {
+        fields3d_kernel<__half, false><<<gr, 128, 0, g->st>>>(args3<__half>(g, g->cur), rho, u, v, w, partials);
+    } else if (g->esz == 8) {
         if (g->tensor) fields3d_kernel<double, true><<<gr, 128, 0, g->st>>>(args3<double>(g, g->cur), rho, u, v, w, partials);
         else fields3d_kernel<double, false><<<gr, 128, 0, g->st>>>(args3<double>(g, g->cur), rho, u, v, w, partials);
     } else {
@@ -1135,7 +1158,8 @@ lbm_status grid3_create_impl(const lbm3d_params *p, const float *kappa_dev, cons
         return fail(LBM_EINVAL, "nu must be finite and eps finite and >= 0");
     if (!std::isfinite(p->gx) || !std::isfinite(p->gy) || !std::isfinite(p->gz))
         return fail(LBM_EINVAL, "G must be finite");
-    if (p->storage != LBM_F32 && p->storage != LBM_F64) return fail(LBM_EINVAL, "storage must be LBM_F32 or LBM_F64");
+    if (p->storage != LBM_F32 && p->storage != LBM_F64 && !(p->storage == LBM_F16 && !keff_dev))
+        return fail(LBM_EINVAL, "storage must be LBM_F32, LBM_F16 (scalar kappa only) or LBM_F64");
     if (keff_dev ? !is_device_ptr(keff_dev) : !is_device_ptr(kappa_dev))
         return fail(LBM_EINVAL, keff_dev ? "keff_dev must be a device pointer" : "kappa_dev must be a device pointer");
     lbm3d_grid *g = new lbm3d_grid;
@@ -1145,17 +1169,18 @@ lbm_status grid3_create_impl(const lbm3d_params *p, const float *kappa_dev, cons
     g->st = static_cast<cudaStream_t>(cuda_stream);
     g->n = (int64_t)p->nx * p->ny * p->nz;
     g->plane = (g->n + 63) / 64 * 64;
-    g->esz = p->storage == LBM_F64 ? 8 : 4;
+    g->esz = p->storage == LBM_F64 ? 8 : (p->storage == LBM_F16 ? 2 : 4);
+    const size_t csz = g->esz == 8 ? 8 : 4;        // coefficients in the compute type
     const dim3 gr = grid3(g, 128);
     g->nblocks = (int64_t)gr.x * gr.y * gr.z;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&g->buf[k], Q19 * g->plane * g->esz);
-    if (e == cudaSuccess) e = cudaMalloc(&g->coef, (g->tensor ? 9 * g->plane : g->n) * g->esz);
+    if (e == cudaSuccess) e = cudaMalloc(&g->coef, (g->tensor ? 9 * g->plane : g->n) * csz);
     if (e == cudaSuccess) e = cudaMalloc(&g->partials, sizeof(double) * 3 * g->nblocks);
     if (e == cudaSuccess) e = cudaMalloc(&g->mean, sizeof(double) * 3);
-    if (e == cudaSuccess) e = cudaMalloc(&g->flags, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&g->flags, 2 * sizeof(unsigned));
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(g->buf[k], 0, Q19 * g->plane * g->esz, g->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->flags, 0, sizeof(unsigned), g->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->flags, 0, 2 * sizeof(unsigned), g->st);
     if (e != cudaSuccess) {
         free3(g);
         cudaGetLastError();
@@ -1180,18 +1205,31 @@ lbm_status grid3_create_impl(const lbm3d_params *p, const float *kappa_dev, cons
                                                         g->flags);
     }
     count_launches(1);
-    unsigned flags = 0;
+    unsigned hflags[2] = {0u, 0u};
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, g->flags, sizeof flags, cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, g->flags, sizeof hflags, cudaMemcpyDeviceToHost, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) {
         free3(g);
         return fail(LBM_ECUDA, "3-D coefficient pass: %s", cudaGetErrorString(e));
     }
+    const unsigned flags = hflags[0];
     if (flags) {
         free3(g);
         if (!keff_dev) return fail(LBM_EINVAL, "kappa holds NaN or negative values");
         return fail(LBM_EINVAL, (flags & 1u) ? "keff holds non-finite values" : "K* + (eps nu / 2) I is singular");
+    }
+    if (g->esz == 2) {
+        // FP16 keeps 11 bits: store S g with S = 2^k placing the largest expected deviation,
+        // ~ 3 w u_max with u_max ~ kappa_max |G| / nu, near 2^12 (headroom below the FP16 maximum)
+        float kmax;
+        std::memcpy(&kmax, &hflags[1], sizeof kmax);
+        const double gmag = std::fabs(p->gx) + std::fabs(p->gy) + std::fabs(p->gz);
+        double umax = (nu > 0.0 && kmax > 0.0f) ? (double)kmax * gmag / nu : gmag * 1e3;
+        if (!(umax > 0.0)) umax = 1e-3;
+        if (umax > 0.1) umax = 0.1;
+        const int e2 = std::max(0, std::min(60, (int)std::floor(std::log2(4096.0 / umax))));
+        g->S = std::ldexp(1.0, e2);
     }
     *out = g;
     return LBM_OK;
@@ -1266,7 +1304,9 @@ lbm_status lbm3d_step(lbm3d_grid *g, int64_t steps)
     if (steps < 0) return fail(LBM_EINVAL, "steps must be >= 0");
     const dim3 gr = grid3(g, 256);
     for (int64_t s = 0; s < steps; ++s) {
-        if (g->esz == 8) {
+        if (g->esz == 2) {
+            step3d_kernel<__half, false><<<gr, 256, 0, g->st>>>(args3<__half>(g, g->cur));
+        } else if (g->esz == 8) {
             if (g->tensor) step3d_kernel<double, true><<<gr, 256, 0, g->st>>>(args3<double>(g, g->cur));
             else step3d_kernel<double, false><<<gr, 256, 0, g->st>>>(args3<double>(g, g->cur));
         } else {

@@ -97,7 +97,7 @@ def _params3(**kw):
     return _abi.lbm3d_params(**base)
 
 
-@pytest.mark.parametrize("bad", [dict(nx=0), dict(nz=70000), dict(tau=0.3), dict(eps=-1.0), dict(storage=1),
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(nz=70000), dict(tau=0.3), dict(eps=-1.0), dict(storage=3),
                                  dict(gz=float("nan"))])
 def test_3d_create_rejects_bad_params(lib, bad):
     h = C.c_void_p()
