@@ -187,11 +187,13 @@ def oracle_rate(kap: np.ndarray, steps: int) -> tuple[float, int, float]:
 
 
 def measure_variants(lbm, torch, kap, stream, steps=300):
-    """FP16-scaled and FP64 storage on the same lattice: MLUPS and the fraction of HBM roofline."""
+    """FP16-scaled and FP64 storage on the same lattice, and FP32 at the workload's other tau (1.0,
+    nu = nu_eff = 1/6): MLUPS and the fraction of HBM roofline."""
     out = {}
     peaks = measured_peaks()
-    for name, st in (("f16", lbm.LBM_F16), ("f64", lbm.LBM_F64)):
-        p = lbm.Params(nx=N, ny=N, tau=TAU, nu=NU, eps=1.0, gx=G[0], gy=G[1], storage=st)
+    for name, st, tau, key in (("f16", lbm.LBM_F16, TAU, "f16"), ("f64", lbm.LBM_F64, TAU, "f64"),
+                               ("f32_tau1", lbm.LBM_F32, 1.0, "f32")):
+        p = lbm.Params(nx=N, ny=N, tau=tau, nu=-1.0, eps=1.0, gx=G[0], gy=G[1], storage=st)   # nu = nu_eff
         with lbm.Grid(p, kap) as g:
             g.step(50, 0.0, 0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -200,8 +202,8 @@ def measure_variants(lbm, torch, kap, stream, steps=300):
             e1.record(stream)
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) * 1e-3 / steps
-        out[name] = {"mlups": N * N / t / 1e6, "bytes_per_lup": BYTES_PER_LUP[name],
-                     "hbm_frac": BYTES_PER_LUP[name] * N * N / t / 1e9 / peaks["hbm_gbs"]}
+        out[name] = {"mlups": N * N / t / 1e6, "bytes_per_lup": BYTES_PER_LUP[key],
+                     "hbm_frac": BYTES_PER_LUP[key] * N * N / t / 1e9 / peaks["hbm_gbs"]}
     return out
 
 
