@@ -1069,7 +1069,8 @@ lbm_status run_cluster_size(const lbm3d_params *p, const float *kappa_dev, const
     const int nt = (int)std::min<int64_t>(NT, ((P + CPT - 1) / CPT + 31) / 32 * 32);
     const void *fn = f64 ? clu3_kernel<double>(PS) : clu3_kernel<float>(PS);
     if (!fn) return LBM_EINVAL;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    // the opt-in maximum, not this launch's size: a concurrent call with a larger cube stays valid
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
         (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
         cudaGetLastError();
         return LBM_EINVAL;
