@@ -321,8 +321,9 @@ lbm_status lbm_block_average(const float *in_dev, int32_t nx, int32_t ny, int32_
  * algorithms unchanged. These calls step the scheme on it (rest, 6 face and 12 edge velocities,
  * weights 1/3, 1/18, 1/36, c_s^2 = 1/3) with the same update as the 2-D grid
  * (Eqs. 6, 16, 2, 13 with three-component vectors), periodic in x, y and z,
- * constant body force, scalar permeability, from rest. Arrays are [nz][ny][nx]
- * (x fastest), caller-owned device memory. */
+ * constant body force, scalar permeability (a tensor K* per cell for the coarse
+ * grid below), from rest. Arrays are [nz][ny][nx] (x fastest), caller-owned
+ * device memory. */
 typedef struct {
     int32_t nx, ny, nz;   /* lattice size, each >= 1; ny, nz <= 65535                   */
     double  tau, nu, eps; /* as in lbm_params (nu < 0 selects nu_eff)                  */
@@ -373,8 +374,8 @@ lbm_status lbm3d_block_average(const float *in_dev, int32_t nx, int32_t ny, int3
 
 /* Three-dimensional local problems (Section 3 with the D3Q19 lattice). For each
  * cubic leaf (x0, y0, z0, size) of the field kappa_dev [nz][ny][nx] (p->nx, ny,
- * nz are the field size; tau, nu, eps, storage as for a 3-D grid, the force is
- * ignored) three periodic runs from rest, driven by g_const along x, y and z,
+ * nz are the field size; tau, nu, eps as for a 3-D grid; storage LBM_F32 or
+ * LBM_F64; the force is ignored) three periodic runs from rest, driven by g_const along x, y and z,
  * each until its volume-averaged velocity settles: every check_every steps t,
  * |ubar_d(t) - ubar_d(t - check_every)| <= tol_rel * check_every * |ubar_d(t)|
  * on the driven component d (tol_rel = 0 runs exactly max_steps). Eq. 17 in 3-D
@@ -383,7 +384,7 @@ lbm_status lbm3d_block_average(const float *in_dev, int32_t nx, int32_t ny, int3
  * d = drive), status_dev int32 [n] (LBM_OK, LBM_ENOTCONV, or LBM_ETIMEOUT when
  * the lbm_set_time_limit bound ran out first; keff then not valid), steps_dev
  * int32 [n][3] or NULL. Cubes that fit the shared memory of a thread-block
- * cluster of at most 16 CTAs (up to 32 cells wide in FP32, 16 in FP64) run one
+ * cluster of at most 16 CTAs (up to 32 cells wide in FP32, 22 in FP64) run one
  * job per cluster entirely on chip; larger cubes run with their 3 n jobs stacked
  * in device memory (allocated and freed by the call); the environment variable
  * LBM_LOCAL3_GLOBAL=1 sends every size that second way. With p->margin = m > 0
