@@ -228,11 +228,14 @@ def measure_storage_error(lbm, torch, kap_np, crop=512, steps=1000):
     return out
 
 
-def measure_d3q19(lbm, torch, n=256, steps=200):
+def measure_d3q19(lbm, torch, n=256, steps=200, ws=1, rank=0):
     """The scheme on the D3Q19 lattice (Section 2 in three dimensions): n^3 periodic box,
     log-normal K (sigma 2, ell 8, seed 7), tau = 0.6, nu = nu_eff, G = (1e-6, 0, 0); MLUPS and the
     fraction of the measured HBM bandwidth at 19 x 2 x 4 + 4 = 156 B/LUP (FP32), 80 B/LUP (FP16
-    scaled storage), 308 B/LUP (FP64)."""
+    scaled storage), 308 B/LUP (FP64). The 3-D local problems on the 16^3 cubes of the box are
+    sharded across ranks like the 2-D ones (contiguous, work-balanced ranges, no exchange; rate =
+    all cubes over the slowest rank's time); the upscaled model, which needs every cube's K*, runs
+    on a single rank only."""
     import synth
     kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 8.0, 2.0, seed=7)).cuda()
     peaks = measured_peaks()
@@ -252,18 +255,23 @@ def measure_d3q19(lbm, torch, n=256, steps=200):
                      "hbm_frac": bpl * n ** 3 / t / 1e9 / peaks["hbm_gbs"]}
     # three-dimensional local problems (Eq. 17 in 3-D): every 16^3 cube of the box, three drives
     b = 16
-    leaves = torch.tensor([(x, y, z, b) for z in range(0, n, b) for y in range(0, n, b) for x in range(0, n, b)],
-                          dtype=torch.int32, device="cuda")
+    from paper_1312_0195_gb300.shard import leaf_shard
+    cubes = [(x, y, z, b) for z in range(0, n, b) for y in range(0, n, b) for x in range(0, n, b)]
+    lo, hi = leaf_shard(np.full(len(cubes), b), rank, ws)
+    leaves = torch.tensor(cubes[lo:hi], dtype=torch.int32, device="cuda").reshape(-1, 4)
     p = lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0)
+    barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     keff, status, lsteps, _ = lbm.local_keff3(p, kap, leaves, 1e-6, 1e-8, 200000, 64)
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    lups = float(lsteps.double().sum()) * b ** 3
-    out["local_keff"] = {"workload": f"all {leaves.shape[0]} cubes of {b}^3, tau 1, G 1e-6 along x, y, z, tol 1e-8",
-                         "patches_per_s": leaves.shape[0] / t, "seconds": t, "glups": lups / t / 1e9,
-                         "converged": int((status == 0).sum())}
+    t = max_over_ranks(time.perf_counter() - t0, ws)
+    lups = sum_over_ranks(float(lsteps.double().sum()) * b ** 3, ws)
+    out["local_keff"] = {"workload": f"all {len(cubes)} cubes of {b}^3, tau 1, G 1e-6 along x, y, z, tol 1e-8",
+                         "patches_per_s": len(cubes) / t, "seconds": t, "glups": lups / t / 1e9, "ranks": ws,
+                         "converged": int(sum_over_ranks(float((status == 0).sum()), ws))}
+    if ws > 1:
+        return out
     # the upscaled model on the same box (Eq. 18 in 3-D): fine run at tau 1 for 20k steps against the
     # coarse run with those K* for 1250 steps (the same physical time), block-averaged velocity
     fine_steps, nb = 20000, n // b
@@ -655,7 +663,7 @@ def run_ours(args, ws, rank, local):
         variants = measure_variants(lbm, torch, kap, stream)
         if rank == 0:
             variants["error_vs_oracle"] = measure_storage_error(lbm, torch, kap_np)
-        d3 = measure_d3q19(lbm, torch)
+        d3 = measure_d3q19(lbm, torch, ws=ws, rank=rank)
         local = measure_local_keff(lbm, torch, kap, ws, rank)
         if not args.no_surrogate:
             surrogate = measure_surrogate(lbm, torch)

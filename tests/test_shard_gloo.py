@@ -58,6 +58,23 @@ def _solve(kap, leaves):
     return out
 
 
+def _cubes():
+    """3-D local problems as the bench shards them: equal cubes of a small log-normal box."""
+    import synth
+    k3 = synth.lognormal_kappa3d(8, 8, 8, 2.0, 1.0, seed=23)
+    return k3, [(x, y, z, 4) for z in (0, 4) for y in (0, 4) for x in (0, 4)]
+
+
+def _solve3(k3, cubes):
+    import oracle
+    out = []
+    for x0, y0, z0, s in cubes:
+        r = oracle.local_keff3(k3[z0:z0 + s, y0:y0 + s, x0:x0 + s].astype(np.float64), 1.0, 1.0 / 6.0, 1.0, 1e-6,
+                               tol=1e-8, max_steps=20000)
+        out.append([float(v) for v in r["keff"].ravel()])
+    return out
+
+
 def _rank_main(rank, world, port, out_path):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
@@ -67,11 +84,14 @@ def _rank_main(rank, world, port, out_path):
     kap, leaves = _field_and_leaves()
     lo, hi = leaf_shard(leaves[:, 2], rank, world)
     mine = _solve(kap, leaves[lo:hi])                    # no exchange while solving
+    k3, cubes = _cubes()
+    lo3, hi3 = leaf_shard(np.full(len(cubes), 4), rank, world)
+    mine3 = _solve3(k3, cubes[lo3:hi3])
     bench.barrier(ws)
     t_max = bench.max_over_ranks(float(rank + 1), ws)
     n_sum = bench.sum_over_ranks(float(hi - lo), ws)
     gathered = [None] * world
-    dist.all_gather_object(gathered, (lo, hi, mine))     # off the hot path: results to rank 0
+    dist.all_gather_object(gathered, (lo, hi, mine, lo3, hi3, mine3))   # off the hot path: results to rank 0
     if rank == 0:
         with open(out_path, "w") as fh:
             json.dump({"t_max": t_max, "n_sum": n_sum, "parts": gathered}, fh)
@@ -89,3 +109,7 @@ def test_two_gloo_ranks_solve_their_shards_like_one_process(tmp_path):
     assert parts[0][0] == 0 and parts[-1][1] == len(leaves) and parts[0][1] == parts[1][0]
     sharded = [k for p in parts for k in p[2]]
     assert sharded == _solve(kap, leaves)                # bitwise: same problems, same arithmetic
+    k3, cubes = _cubes()
+    parts3 = sorted(((p[3], p[4], p[5]) for p in res["parts"]), key=lambda p: p[0])
+    assert parts3[0][0] == 0 and parts3[-1][1] == len(cubes) and parts3[0][1] == parts3[1][0]
+    assert [k for p in parts3 for k in p[2]] == _solve3(k3, cubes)
