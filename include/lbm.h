@@ -394,6 +394,16 @@ lbm_status lbm3d_block_average(const float *in_dev, int32_t nx, int32_t ny, int3
  * field, size + 2 m outside [1, 256] or m outside [0, min(32, nx, ny, nz)] give
  * LBM_EINVAL. */
 typedef struct { int32_t x0, y0, z0, size; } lbm3d_leaf;
+/* The upscaling step in 3-D: K* of every block^3 block of the field (one cubic
+ * leaf per coarse cell, three drives, check every 64 steps, p->margin as
+ * above) into keff_coarse_dev double [nz/r][ny/r][nx/r][3][3], fine lattice
+ * units, the layout lbm3d_coarse_grid_create reads. n_notconv (HOST, may be
+ * NULL) receives the number of blocks whose status is not LBM_OK. nx, ny, nz
+ * must be multiples of block; returns the worst status, as
+ * lbm3d_local_keff_batch. Allocates and frees the leaf list and the status. */
+lbm_status lbm3d_upscale(const lbm3d_params *p, const float *kappa_dev, int32_t block, double g_const,
+                         double tol_rel, int64_t max_steps, double *keff_coarse_dev, int32_t *n_notconv,
+                         void *cuda_stream);
 lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev, const lbm3d_leaf *leaves_dev,
                                   int32_t n_leaves, double g_const, double tol_rel, int64_t max_steps,
                                   int32_t check_every, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,

@@ -452,6 +452,22 @@ def local_keff3(params: Params3D, kappa, leaves, g_const: float = 1e-6, tol_rel:
     return keff, status, steps, worst
 
 
+def lbm3d_upscale(params: Params3D, kappa, block: int, g_const: float = 1e-6, tol_rel: float = 1e-8,
+                  max_steps: int = 200000, keff_coarse=None, stream=None):
+    """K* of every block^3 block (3-D local problems, params.margin for oversampling) as a CUDA
+    float64 tensor [nz/b, ny/b, nx/b, 3, 3] in fine lattice units; returns (keff, n_notconv, status)."""
+    import torch
+    if keff_coarse is None:
+        keff_coarse = torch.empty((params.nz // block, params.ny // block, params.nx // block, 3, 3),
+                                  dtype=torch.float64, device=kappa.device)
+    p = params.c()
+    nnc = _abi._I32(0)
+    st = _check(_abi.lib().lbm3d_upscale(C.byref(p), _ptr(kappa), int(block), float(g_const), float(tol_rel),
+                                         int(max_steps), _ptr(keff_coarse), C.byref(nnc), _stream(stream)),
+                allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
+    return keff_coarse, int(nnc.value), st
+
+
 class Grid3D:
     """Owning wrapper of a D3Q19 grid: ``Grid3D(params3d, kappa_cuda_f32 [nz, ny, nx])``, or the
     coarse grid of the upscaled model: ``Grid3D.coarse(fine_params3d, block, keff [nz/b, ny/b, nx/b, 3, 3])``."""

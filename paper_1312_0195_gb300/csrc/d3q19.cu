@@ -13,7 +13,9 @@
 
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -1536,6 +1538,53 @@ lbm_status lbm3d_local_keff_batch(const lbm3d_params *p, const float *kappa_dev,
     int worst = LBM_OK;
     for (int v : stat) worst = std::max(worst, v);
     return (lbm_status)worst;
+}
+
+lbm_status lbm3d_upscale(const lbm3d_params *p, const float *kappa_dev, int32_t block, double g_const,
+                         double tol_rel, int64_t max_steps, double *keff_coarse_dev, int32_t *n_notconv,
+                         void *cuda_stream)
+{
+    if (n_notconv) *n_notconv = 0;
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (block < 1 || p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx % block || p->ny % block || p->nz % block)
+        return fail(LBM_EINVAL, "nx, ny, nz must be positive multiples of block %d", block);
+    if (block > 256) return fail(LBM_EINVAL, "block must be at most 256");
+    if (!keff_coarse_dev || !is_device_ptr(keff_coarse_dev)) return fail(LBM_EINVAL, "keff_coarse_dev must be a device pointer");
+    const int bx = p->nx / block, by = p->ny / block, bz = p->nz / block;
+    const int64_t n = (int64_t)bx * by * bz;
+    if (n > INT32_MAX) return fail(LBM_EINVAL, "too many blocks");
+    // one cubic leaf per coarse cell, in the coarse grid's [z][y][x] order, so keff lands in place
+    std::vector<lbm3d_leaf> lv((size_t)n);
+    for (int z = 0, i = 0; z < bz; ++z)
+        for (int y = 0; y < by; ++y)
+            for (int x = 0; x < bx; ++x, ++i) lv[i] = lbm3d_leaf{x * block, y * block, z * block, block};
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    lbm3d_leaf *d_leaves = nullptr;
+    int32_t *d_status = nullptr;
+    cudaError_t e = cudaMalloc(&d_leaves, sizeof(lbm3d_leaf) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_leaves, lv.data(), sizeof(lbm3d_leaf) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_leaves);
+        cudaFree(d_status);
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "3-D upscale set-up: %s",
+                    cudaGetErrorString(e));
+    }
+    lbm_status s = lbm3d_local_keff_batch(p, kappa_dev, d_leaves, (int32_t)n, g_const, tol_rel, max_steps, 64,
+                                          keff_coarse_dev, d_status, nullptr, cuda_stream);
+    if (n_notconv && (s == LBM_OK || s == LBM_ENOTCONV || s == LBM_ETIMEOUT)) {
+        std::vector<int32_t> stat((size_t)n);
+        if (cudaMemcpyAsync(stat.data(), d_status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess) {
+            for (int32_t v : stat) *n_notconv += v != LBM_OK;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    cudaFree(d_leaves);
+    cudaFree(d_status);
+    return s;
 }
 
 }  // extern "C"

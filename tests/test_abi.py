@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("lbm_grid_create", "lbm_grid_destroy", "lbm_step", "lbm_get_fields",
                      "lbm_mean_velocity", "lbm_last_error", "lbm3d_grid_create", "lbm3d_local_keff_batch",
-                     "lbm3d_coarse_grid_create", "lbm3d_block_average"):
+                     "lbm3d_coarse_grid_create", "lbm3d_block_average", "lbm3d_upscale"):
         assert required in names
 
 
@@ -124,3 +124,7 @@ def test_3d_host_side_validation(lib):
     assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 1, 0.0, 1e-8, 1000, 64, None, None, None, None) == 1
     assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 1, 1e-6, 1e-8, 0, 64, None, None, None, None) == 1
     assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 0, 1e-6, 1e-8, 1000, 64, None, None, None, None) == 0
+    nnc = C.c_int32(-1)
+    assert lib.lbm3d_upscale(C.byref(p), None, 3, 1e-6, 1e-8, 1000, None, C.byref(nnc), None) == 1   # 8 % 3
+    assert nnc.value == 0
+    assert lib.lbm3d_upscale(C.byref(p), None, 4, 1e-6, 1e-8, 1000, None, None, None) == 1           # NULL keff

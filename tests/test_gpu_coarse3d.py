@@ -157,3 +157,20 @@ def test_upscaled_pipeline_small():
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * scale)
     err = np.sqrt(sum(((a - b) ** 2).sum() for a, b in zip((uc, vc, wc), avg)) / sum((b ** 2).sum() for b in avg))
     assert err < 0.35, err
+
+
+def test_upscale3_is_the_local_problem_per_block():
+    """lbm3d_upscale: one cubic leaf per coarse cell, K* in the coarse grid's layout, the same
+    values as the batched local problems on the same cubes (also with oversampling)."""
+    import torch
+    lbm = _lbm()
+    n, r = 24, 8
+    kap = torch.from_numpy(synth.lognormal_kappa3d(n, n, n, 3.0, 1.0, seed=96)).cuda()
+    for m in (0, 2):
+        p = lbm.Params3D(nx=n, ny=n, nz=n, tau=1.0, eps=1.0, margin=m)
+        kc, nnc, st = lbm.lbm3d_upscale(p, kap, r, 1e-6, 0.0, 300)
+        assert kc.shape == (3, 3, 3, 3, 3) and nnc == 0 and st == 0
+        cubes = torch.tensor([(x, y, z, r) for z in range(0, n, r) for y in range(0, n, r) for x in range(0, n, r)],
+                             dtype=torch.int32, device="cuda")
+        ke, _, _, _ = lbm.local_keff3(p, kap, cubes, 1e-6, 0.0, 300, 64)
+        np.testing.assert_array_equal(kc.reshape(-1, 3, 3).cpu().numpy(), ke.cpu().numpy())
