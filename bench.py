@@ -253,6 +253,8 @@ def measure_d3q19(lbm, torch, n=256, steps=200, ws=1, rank=0):
             t = (time.perf_counter() - t0) / k
         out[name] = {"mlups": n ** 3 / t / 1e6, "bytes_per_lup": bpl,
                      "hbm_frac": bpl * n ** 3 / t / 1e9 / peaks["hbm_gbs"]}
+    if rank == 0:
+        out["error_vs_oracle"] = measure_storage_error3(lbm, torch, kap.cpu().numpy())
     # three-dimensional local problems (Eq. 17 in 3-D): every 16^3 cube of the box, three drives
     b = 16
     from paper_1312_0195_gb300.shard import leaf_shard
@@ -299,6 +301,28 @@ def measure_d3q19(lbm, torch, n=256, steps=200, ws=1, rank=0):
                        "coarse_seconds": t_coarse,
                        "rel_l2_vs_fine": float(torch.sqrt(num / sum((a ** 2).sum() for a in avg))),
                        "coarse_over_fine_mean_u": float(uc.double().mean() / avg[0].mean())}
+    return out
+
+
+def measure_storage_error3(lbm, torch, kap_np, crop=32, steps=500):
+    """Error of each D3Q19 storage type against the FP64 oracle: the crop^3 corner of the d3q19
+    field run as its own periodic box for `steps` steps on both sides (tau 0.6, nu = nu_eff,
+    G = (1e-6, 0, 0)); relative L2 error of (u, v, w)."""
+    import oracle
+    sub = np.ascontiguousarray(kap_np[:crop, :crop, :crop])
+    prob = oracle.Problem3D(TAU, NU, 1.0, kappa=sub.astype(np.float64), g=(1e-6, 0.0, 0.0))
+    f = prob.rest()
+    prob.run(f, steps)
+    _, uo, vo, wo = prob.fields(f)
+    den = np.sqrt((uo ** 2 + vo ** 2 + wo ** 2).sum())
+    out = {"workload": f"{crop}^3 corner of the d3q19 field as its own periodic box, {steps} steps"}
+    for name, st in (("f32", lbm.LBM_F32), ("f16", lbm.LBM_F16), ("f64", lbm.LBM_F64)):
+        p = lbm.Params3D(nx=crop, ny=crop, nz=crop, tau=TAU, nu=NU, eps=1.0, gx=1e-6, storage=st)
+        with lbm.Grid3D(p, torch.from_numpy(sub).cuda()) as g:
+            g.step(steps)
+            _, u, v, w = (t.cpu().numpy().astype(np.float64) for t in g.fields())
+        num = np.sqrt(((u - uo) ** 2 + (v - vo) ** 2 + (w - wo) ** 2).sum())
+        out[name] = {"rel_l2_error_uvw": float(num / den)}
     return out
 
 
