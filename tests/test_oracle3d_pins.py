@@ -301,3 +301,34 @@ def test_oversampled_local3_uniform_and_inner_layers():
     full = oracle.local_keff3(kap, ex["tau"], ex["nu"], ex["eps"], 1e-6, tol=1e-11, max_steps=20000)
     np.testing.assert_allclose([full["keff"][1, 1], full["keff"][2, 2]], cols.mean(), rtol=2e-6)
     assert abs(full["keff"][1, 1] - inner) > 0.5 * inner
+
+
+def test_tensor_layers_darcy_closed_form():
+    """Layered full-tensor medium in the Darcy setting of Table 2 (tau = 1/2, E3's nu): K*(x)
+    varies along x in bands of two cells, with non-symmetric K_xy, K_yx and K_zx; G along y.
+    Steady Darcy flow u = K* (G - grad p) / nu with grad p = (p'(x), 0, 0): continuity makes u_x
+    a constant c, periodicity makes p' average to zero, so c = G sum(K_xy / K_xx) /
+    (nu sum(1 / K_xx)), p' = (K_xy G - nu c) / K_xx, u_y = (K_yy G - K_yx p') / nu and
+    u_z = -K_zx p' / nu. A transposed or sign-flipped off-diagonal changes these at order one."""
+    ex = synth.paper_experiment("E3", ratio=10.0, ny=1)
+    k1 = float(ex["kappa"][0, 0])
+    tau, nu, eps, g = ex["tau"], ex["nu"], ex["eps"], 1e-6
+    band = lambda *v: np.repeat(np.array(v), 2) * k1          # noqa: E731
+    kxx, kyy = band(2, 4, 1, 3), band(1, 5, 2, 8)
+    kxy, kyx, kzx = band(0.3, -0.5, 0.2, 0.4), band(-0.2, 0.6, 0.1, -0.3), band(0.1, 0.2, -0.1, 0.3)
+    nx = kxx.size
+    K = np.zeros((3, 3, nx, 3, 3))
+    K[..., 0, 0], K[..., 1, 1], K[..., 2, 2] = kxx, kyy, 3 * k1
+    K[..., 0, 1], K[..., 1, 0], K[..., 2, 0] = kxy, kyx, kzx
+    p = oracle.Problem3D(tau, nu, eps, ktensor=K, g=(0.0, g, 0.0))
+    f = p.rest()
+    p.run(f, 8000)
+    _, u, v, w = p.fields(f)
+    c = g * np.sum(kxy / kxx) / (nu * np.sum(1.0 / kxx))
+    dp = (kxy * g - nu * c) / kxx
+    np.testing.assert_allclose(u[1, 1, :], c, rtol=1e-5)
+    np.testing.assert_allclose(v[1, 1, :], (kyy * g - kyx * dp) / nu, rtol=1e-5)
+    uz = -kzx * dp / nu
+    np.testing.assert_allclose(w[1, 1, :], uz, rtol=0, atol=1e-5 * np.abs(uz).max())
+    for a in (u, v, w):                                    # uniform along y and z
+        np.testing.assert_allclose(a, np.broadcast_to(a[1, 1, :], a.shape), rtol=0, atol=1e-12 * np.abs(v).max())
