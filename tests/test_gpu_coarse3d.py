@@ -174,3 +174,27 @@ def test_upscale3_is_the_local_problem_per_block():
                              dtype=torch.int32, device="cuda")
         ke, _, _, _ = lbm.local_keff3(p, kap, cubes, 1e-6, 0.0, 300, 64)
         np.testing.assert_array_equal(kc.reshape(-1, 3, 3).cpu().numpy(), ke.cpu().numpy())
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_tensor_layers_darcy_closed_form_on_gpu(storage):
+    """The oracle pin's closed form on the GPU tensor grid: Darcy flow (tau = 1/2, E3's nu) through
+    two-cell layers of a non-symmetric K*, driven along y; u_x constant, u_y and u_z from K_yx,
+    K_zx and the layer pressure gradient."""
+    ex = synth.paper_experiment("E3", ratio=10.0, ny=1)
+    k1 = float(ex["kappa"][0, 0])
+    tau, nu, eps, g = ex["tau"], ex["nu"], ex["eps"], 1e-6
+    band = lambda *v: np.repeat(np.array(v), 2) * k1          # noqa: E731
+    kxx, kyy = band(2, 4, 1, 3), band(1, 5, 2, 8)
+    kxy, kyx, kzx = band(0.3, -0.5, 0.2, 0.4), band(-0.2, 0.6, 0.1, -0.3), band(0.1, 0.2, -0.1, 0.3)
+    K = np.zeros((2, 2, kxx.size, 3, 3))
+    K[..., 0, 0], K[..., 1, 1], K[..., 2, 2] = kxx, kyy, 3 * k1
+    K[..., 0, 1], K[..., 1, 0], K[..., 2, 0] = kxy, kyx, kzx
+    (r, u, v, w), _, _ = _gpu_tensor_run(K, tau, nu, eps, (0.0, g, 0.0), 8000, storage)
+    c = g * np.sum(kxy / kxx) / (nu * np.sum(1.0 / kxx))
+    dp = (kxy * g - nu * c) / kxx
+    tol = 1e-5 if storage == 2 else 2e-3
+    np.testing.assert_allclose(u[0, 0, :], c, rtol=tol)
+    np.testing.assert_allclose(v[0, 0, :], (kyy * g - kyx * dp) / nu, rtol=tol)
+    uz = -kzx * dp / nu
+    np.testing.assert_allclose(w[0, 0, :], uz, rtol=0, atol=tol * np.abs(uz).max())
