@@ -348,6 +348,14 @@ lbm_status lbm3d_step(lbm3d_grid *g, int64_t steps);
 lbm_status lbm3d_get_fields(lbm3d_grid *g, float *rho_dev, float *u_dev, float *v_dev, float *w_dev);
 /* Volume average of the flow velocity, FP64 in a fixed order; HOST out[3]. */
 lbm_status lbm3d_mean_velocity(lbm3d_grid *g, double out_mean_uvw[3]);
+/* Checkpoint: copies the grid's current state (19 planes of the storage type,
+ * plane a at offset a * plane with plane = nx ny nz rounded up to a multiple of
+ * 64, deviations from w_a rho0 times the FP16 scale for LBM_F16) to or from
+ * caller-owned DEVICE memory of lbm3d_grid_state_bytes(g) bytes (-1 for NULL).
+ * A grid created with the same parameters and field continues bit for bit. */
+int64_t lbm3d_grid_state_bytes(const lbm3d_grid *g);
+lbm_status lbm3d_grid_save_state(lbm3d_grid *g, void *state_dev);
+lbm_status lbm3d_grid_load_state(lbm3d_grid *g, const void *state_dev);
 
 /* Coarse-grid parameters for blocks of block^3 fine cells (Section 3 in 3-D: the
  * same rho0, nu_eff, eps, nu and G in physical units with dx and dt scaled by

@@ -495,6 +495,19 @@ class Grid3D:
     def mean_velocity(self):
         return lbm3d_mean_velocity(self.handle)
 
+    def save_state(self, out=None):
+        """The grid's state as a CUDA uint8 tensor (or into `out`), for load_state on a grid created
+        with the same parameters and field."""
+        import torch
+        n = int(_abi.lib().lbm3d_grid_state_bytes(self.handle))
+        if out is None:
+            out = torch.empty((n,), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+        _check(_abi.lib().lbm3d_grid_save_state(self.handle, _ptr(out)))
+        return out
+
+    def load_state(self, state) -> None:
+        _check(_abi.lib().lbm3d_grid_load_state(self.handle, _ptr(state)))
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             lbm3d_grid_destroy(self.handle)

@@ -1247,6 +1247,31 @@ lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void
     return grid3_create_impl(p, kappa_dev, nullptr, 1.0, cuda_stream, out);
 }
 
+int64_t lbm3d_grid_state_bytes(const lbm3d_grid *g)
+{
+    return g ? (int64_t)Q19 * g->plane * (int64_t)g->esz : -1;
+}
+
+lbm_status lbm3d_grid_save_state(lbm3d_grid *g, void *state_dev)
+{
+    if (!g) return fail(LBM_EINVAL, "grid is NULL");
+    if (!is_device_ptr(state_dev)) return fail(LBM_EINVAL, "state_dev must be a device pointer");
+    L3_CUDA(cudaMemcpyAsync(state_dev, g->buf[g->cur], (size_t)lbm3d_grid_state_bytes(g), cudaMemcpyDeviceToDevice,
+                            g->st));
+    L3_CUDA(cudaStreamSynchronize(g->st));
+    return LBM_OK;
+}
+
+lbm_status lbm3d_grid_load_state(lbm3d_grid *g, const void *state_dev)
+{
+    if (!g) return fail(LBM_EINVAL, "grid is NULL");
+    if (!is_device_ptr(state_dev)) return fail(LBM_EINVAL, "state_dev must be a device pointer");
+    L3_CUDA(cudaMemcpyAsync(g->buf[g->cur], state_dev, (size_t)lbm3d_grid_state_bytes(g), cudaMemcpyDeviceToDevice,
+                            g->st));
+    L3_CUDA(cudaStreamSynchronize(g->st));
+    return LBM_OK;
+}
+
 lbm_status lbm3d_coarse_params(const lbm3d_params *fine_p, int32_t block, lbm3d_params *coarse_out)
 {
     if (!fine_p || !coarse_out) return fail(LBM_EINVAL, "params and out must not be NULL");
