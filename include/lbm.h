@@ -135,17 +135,23 @@ lbm_status lbm_mean_velocity(lbm_grid *g, double out_mean_uv[2]);
 int64_t lbm_grid_steps(const lbm_grid *g);
 
 /* Checkpoint: copies the grid's state to or from caller-owned DEVICE memory of
- * lbm_grid_state_bytes(g) bytes, together with the step count. The state is
- * both distribution buffers, the current one first (the previous one is kept so
- * that the convergence test after a restart compares the same two states as an
- * uninterrupted run). Each buffer holds 9 planes of the storage type, plane a at
- * offset a * plane where plane = nx * ny rounded up to a multiple of 64, cell
- * (x, y) at y * nx + x; the values are deviations from w_a rho0, multiplied by
- * the FP16 scale for LBM_F16. The layout is opaque to callers that only save and
- * load it on grids created with the same parameters. */
+ * exactly lbm_grid_state_bytes(g) bytes (nbytes must equal it, else LBM_EINVAL),
+ * together with the step count. The first 256 bytes are a header: magic
+ * "LBM2CKPT", version, storage type, nx, ny, the FP16 scale S and a hash of the
+ * parameters the update depends on (tau, nu, eps, G, bc, force model, scalar or
+ * tensor drag, force field or not). Loading compares it with the loading grid's
+ * own and returns LBM_EINVAL on any difference, so a state saved by a grid of
+ * another size, storage, scale or parameter set is never misread. The header is
+ * followed by both distribution buffers, the current one first (the previous one
+ * is kept so that the convergence test after a restart compares the same two
+ * states as an uninterrupted run). Each buffer holds 9 planes of the storage
+ * type, plane a at offset a * plane where plane = nx * ny rounded up to a
+ * multiple of 64, cell (x, y) at y * nx + x; the values are deviations from
+ * w_a rho0, multiplied by the FP16 scale for LBM_F16. The permeability field is
+ * not part of the state: load it into a grid created on the same field. */
 int64_t lbm_grid_state_bytes(const lbm_grid *g);
-lbm_status lbm_grid_save_state(lbm_grid *g, void *state_dev, int64_t *steps);
-lbm_status lbm_grid_load_state(lbm_grid *g, const void *state_dev, int64_t steps);
+lbm_status lbm_grid_save_state(lbm_grid *g, void *state_dev, int64_t nbytes, int64_t *steps);
+lbm_status lbm_grid_load_state(lbm_grid *g, const void *state_dev, int64_t nbytes, int64_t steps);
 
 /* Storage scale S in use (1 for LBM_F32 / LBM_F64). */
 double lbm_grid_scale(const lbm_grid *g);
@@ -163,8 +169,11 @@ typedef struct {
 } lbm_leaf;
 
 /* Solves all leaves in one launch. p: nx, ny are the FIELD dimensions and tau,
- * nu (< 0: nu_eff), eps the lattice parameters; bc, gx, gy, storage and scale
- * are ignored (leaves are periodic, FP32 deviation storage, FP64 means).
+ * nu (< 0: nu_eff), eps the lattice parameters; bc, gx, gy and scale are
+ * ignored (leaves are periodic). storage = LBM_F64 runs the solver in FP64
+ * (deviations and arithmetic; leaves up to 45 cells including twice the
+ * margin); any other value runs it with FP32 deviations and FP32 arithmetic
+ * (leaves up to 64 cells). The mean velocities are reduced in FP64 either way.
  * kappa_dev: float [ny][nx] field; leaves_dev: DEVICE array of n_leaves leaves,
  * each inside the field. Stopping test per drive d, every check_every steps t:
  *   |ubar_d(t) - ubar_d(t - check_every)| <= tol_rel * check_every * |ubar_d(t)|;
@@ -195,11 +204,15 @@ lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, con
  * lbm_local_keff_batch: always one persistent launch; at most 131072 leaves
  * per call (more gives LBM_EINVAL); p->margin must be 0 (plain local
  * problems); leaves are validated on the device (a bad leaf gives LBM_EINVAL
- * before the solver starts). The first call on each
- * device looks up the array's device address, so make it before any stream
- * capture. Every call reuses the same array (it is cleared at the start of each
- * call), so calls that overlap on the GPU (other streams or threads) race on
- * it and must be serialised by the caller. Results match lbm_local_keff_batch. */
+ * before the solver starts). storage selects the FP32 or FP64 solver exactly as
+ * for lbm_local_keff_batch (leaves up to 45 cells in FP64). The first call on
+ * each device looks up the array's device address, so make it before any stream
+ * capture. Every call reads the class table and the status flags back to the
+ * host and synchronises the stream before it returns. Every call reuses the same
+ * array (it is cleared at the start of each call), so calls that overlap on the
+ * GPU (other streams or threads) race on it and must be serialised by the
+ * caller. The results are those of lbm_local_keff_batch with persistent != 0,
+ * bit for bit. */
 lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
                                         int32_t n_leaves, double g_const, double tol_rel, int64_t max_steps,
                                         int32_t check_every, double *keff_dev, int32_t *status_dev,
@@ -348,14 +361,18 @@ lbm_status lbm3d_step(lbm3d_grid *g, int64_t steps);
 lbm_status lbm3d_get_fields(lbm3d_grid *g, float *rho_dev, float *u_dev, float *v_dev, float *w_dev);
 /* Volume average of the flow velocity, FP64 in a fixed order; HOST out[3]. */
 lbm_status lbm3d_mean_velocity(lbm3d_grid *g, double out_mean_uvw[3]);
-/* Checkpoint: copies the grid's current state (19 planes of the storage type,
- * plane a at offset a * plane with plane = nx ny nz rounded up to a multiple of
- * 64, deviations from w_a rho0 times the FP16 scale for LBM_F16) to or from
- * caller-owned DEVICE memory of lbm3d_grid_state_bytes(g) bytes (-1 for NULL).
- * A grid created with the same parameters and field continues bit for bit. */
+/* Checkpoint: copies the grid's current state to or from caller-owned DEVICE
+ * memory of exactly lbm3d_grid_state_bytes(g) bytes (-1 for NULL; nbytes must
+ * equal it, else LBM_EINVAL): a 256-byte header (magic "LBM3CKPT", version,
+ * storage, nx, ny, nz, the FP16 scale S and a hash of tau, nu, eps, G and the
+ * scalar or tensor drag), then 19 planes of the storage type, plane a at offset
+ * a * plane with plane = nx ny nz rounded up to a multiple of 64, holding the
+ * deviations from w_a rho0 (times S for LBM_F16). Loading a state whose header
+ * differs from the loading grid's own gives LBM_EINVAL. A grid created with the
+ * same parameters and field continues bit for bit. */
 int64_t lbm3d_grid_state_bytes(const lbm3d_grid *g);
-lbm_status lbm3d_grid_save_state(lbm3d_grid *g, void *state_dev);
-lbm_status lbm3d_grid_load_state(lbm3d_grid *g, const void *state_dev);
+lbm_status lbm3d_grid_save_state(lbm3d_grid *g, void *state_dev, int64_t nbytes);
+lbm_status lbm3d_grid_load_state(lbm3d_grid *g, const void *state_dev, int64_t nbytes);
 
 /* Coarse-grid parameters for blocks of block^3 fine cells (Section 3 in 3-D: the
  * same rho0, nu_eff, eps, nu and G in physical units with dx and dt scaled by

@@ -29,7 +29,12 @@ Q = 9
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with the system C compiler (plain -O2, OpenMP).
+    """Compile the oracle with the system C compiler (-O3, no FMA contraction, OpenMP).
+
+    -O3 without -ffast-math keeps IEEE semantics, and -ffp-contract=off forbids
+    fused multiply-adds, so every result is the one the plain C expressions define.
+    No -march=native: the same source must build and give the same results on the
+    x86 and Arm hosts.
 
     ``LBM_ORACLE_LIB`` names a prebuilt oracle library to load instead (the
     mutation tests point it at copies with planted mistakes).
@@ -39,10 +44,15 @@ def build(force: bool = False) -> str:
         return alt
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O3", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """Thread count of the oracle's OpenMP loops (the CPU baseline is timed at 1 and at all cores)."""
+    _L().orc_set_threads(int(n))
 
 
 class _Problem(C.Structure):
@@ -65,8 +75,9 @@ def _L():
         _lib.orc_init_rest.argtypes = [C.POINTER(_Problem), dp]
         _lib.orc_velocity.argtypes = [C.POINTER(_Problem), dp, dp, dp, dp]
         _lib.orc_step.argtypes = [C.POINTER(_Problem), dp, dp]
-        _lib.orc_run.argtypes = [C.POINTER(_Problem), dp, C.c_long, C.c_double, C.c_int,
+        _lib.orc_run.argtypes = [C.POINTER(_Problem), dp, C.c_void_p, C.c_long, C.c_double, C.c_int,
                                  dp, C.POINTER(C.c_int)]
+        _lib.orc_set_threads.argtypes = [C.c_int]
         _lib.orc_run.restype = C.c_long
         _lib.orc_mean_velocity.argtypes = [C.POINTER(_Problem), dp, dp]
         _lib.orc_local_keff.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double,
@@ -231,13 +242,17 @@ class Problem:
         _L().orc_step(C.byref(self._s), _dp(f), _dp(out))
         return out
 
-    def run(self, f: np.ndarray, max_steps: int, tol: float = 0.0, check_every: int = 0):
-        """Step ``f`` in place; returns (steps, residual, converged)."""
+    def run(self, f: np.ndarray, max_steps: int, tol: float = 0.0, check_every: int = 0, work=None):
+        """Step ``f`` in place; returns (steps, residual, converged). ``work`` (optional, same shape
+        and dtype as f) is the second state the steps alternate with; without it one is allocated
+        per call."""
         assert f.flags.c_contiguous and f.dtype == np.float64
+        if work is not None:
+            assert work.flags.c_contiguous and work.dtype == np.float64 and work.size == f.size
         r = C.c_double(-1.0)
         conv = C.c_int(0)
-        n = _L().orc_run(C.byref(self._s), _dp(f), int(max_steps), float(tol), int(check_every),
-                         C.byref(r), C.byref(conv))
+        n = _L().orc_run(C.byref(self._s), _dp(f), None if work is None else work.ctypes.data, int(max_steps),
+                         float(tol), int(check_every), C.byref(r), C.byref(conv))
         return int(n), float(r.value), bool(conv.value)
 
     def run_mean_steady(self, f: np.ndarray, d: int, tol: float, max_steps: int,

@@ -34,6 +34,9 @@
  *   - nu = 0 or eps = 0 means no drag at all (then kappa is not used).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -269,13 +272,17 @@ static double max_abs_diff_uv(long n, const double *u0, const double *v0,
  * the last two steps is measured: resid = max|u^n - u^(n-1)| / max|u^n|
  * (max over cells and both components). Stops when tol > 0 and resid <= tol.
  * Returns the number of steps taken; *resid_out gets the last residual (or -1).
+ * work: a second state of nx * ny * 9 doubles the steps alternate with (NULL:
+ * allocated and freed here); after an odd number of steps the result is copied
+ * back into f once.
  */
-long orc_run(const orc_problem *p, double *f, long max_steps, double tol, int check_every,
+long orc_run(const orc_problem *p, double *f, double *work, long max_steps, double tol, int check_every,
              double *resid_out, int *converged)
 {
     lattice_init();
     long n = (long)p->nx * p->ny;
-    double *g = (double *)malloc(sizeof(double) * n * Q);
+    double *own = work ? NULL : (double *)malloc(sizeof(double) * n * Q);
+    double *cur = f, *nxt = work ? work : own;
     double *u0 = NULL, *v0 = NULL, *u1 = NULL, *v1 = NULL;
     if (check_every > 0) {
         u0 = (double *)malloc(sizeof(double) * n);
@@ -287,26 +294,39 @@ long orc_run(const orc_problem *p, double *f, long max_steps, double tol, int ch
     int conv = 0;
     long s = 0;
     /* u0/v0 hold u(f^(s-1)) whenever s is a check step (s % check_every == 0) */
-    if (check_every == 1) orc_velocity(p, f, NULL, u0, v0);
+    if (check_every == 1) orc_velocity(p, cur, NULL, u0, v0);
     while (s < max_steps) {
-        orc_step(p, f, g);
-        memcpy(f, g, sizeof(double) * n * Q);
+        orc_step(p, cur, nxt);
+        double *t = cur;
+        cur = nxt;
+        nxt = t;
         ++s;
         if (check_every > 0) {
             if (s % check_every == 0) {
                 double um;
-                orc_velocity(p, f, NULL, u1, v1);
+                orc_velocity(p, cur, NULL, u1, v1);
                 double d = max_abs_diff_uv(n, u0, v0, u1, v1, &um);
                 resid = um > 0.0 ? d / um : d;
                 if (tol > 0.0 && resid <= tol) { conv = 1; break; }
             }
-            if ((s + 1) % check_every == 0) orc_velocity(p, f, NULL, u0, v0);
+            if ((s + 1) % check_every == 0) orc_velocity(p, cur, NULL, u0, v0);
         }
     }
-    free(g); free(u0); free(v0); free(u1); free(v1);
+    if (cur != f) memcpy(f, cur, sizeof(double) * n * Q);
+    free(own); free(u0); free(v0); free(u1); free(v1);
     if (resid_out) *resid_out = resid;
     if (converged) *converged = conv;
     return s;
+}
+
+/* Thread count of the OpenMP loops (the timed CPU baseline runs at 1 and at all cores). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
 }
 
 /* Volume average (arithmetic mean over cells) of the flow velocity, Section 3. */

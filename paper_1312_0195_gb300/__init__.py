@@ -121,14 +121,27 @@ def lbm_grid_state_bytes(grid) -> int:
     return int(_abi.lib().lbm_grid_state_bytes(grid))
 
 
+CKPT_HEADER_BYTES = 256        # checkpoint header in front of the distribution planes
+
+
+def _state_bytes(state) -> int:
+    """Byte size of a checkpoint tensor; it must be a contiguous CUDA tensor on the current device."""
+    import torch
+    if not (state.is_cuda and state.is_contiguous()):
+        raise ValueError("a checkpoint state must be a contiguous CUDA tensor")
+    if state.device.index != torch.cuda.current_device():
+        raise ValueError(f"checkpoint state on {state.device}, grid on cuda:{torch.cuda.current_device()}")
+    return state.numel() * state.element_size()
+
+
 def lbm_grid_save_state(grid, state) -> int:
     steps = C.c_int64(0)
-    _check(_abi.lib().lbm_grid_save_state(grid, _ptr(state), C.byref(steps)))
+    _check(_abi.lib().lbm_grid_save_state(grid, _ptr(state), _state_bytes(state), C.byref(steps)))
     return int(steps.value)
 
 
 def lbm_grid_load_state(grid, state, steps: int) -> None:
-    _check(_abi.lib().lbm_grid_load_state(grid, _ptr(state), int(steps)))
+    _check(_abi.lib().lbm_grid_load_state(grid, _ptr(state), _state_bytes(state), int(steps)))
 
 
 def lbm_grid_scale(grid) -> float:
@@ -502,11 +515,11 @@ class Grid3D:
         n = int(_abi.lib().lbm3d_grid_state_bytes(self.handle))
         if out is None:
             out = torch.empty((n,), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
-        _check(_abi.lib().lbm3d_grid_save_state(self.handle, _ptr(out)))
+        _check(_abi.lib().lbm3d_grid_save_state(self.handle, _ptr(out), _state_bytes(out)))
         return out
 
     def load_state(self, state) -> None:
-        _check(_abi.lib().lbm3d_grid_load_state(self.handle, _ptr(state)))
+        _check(_abi.lib().lbm3d_grid_load_state(self.handle, _ptr(state), _state_bytes(state)))
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -60,8 +60,8 @@ SIGNATURES = {
     "lbm_mean_velocity": (C.c_int, [_P, C.POINTER(_D)]),
     "lbm_grid_steps": (_I64, [_P]),
     "lbm_grid_state_bytes": (_I64, [_P]),
-    "lbm_grid_save_state": (C.c_int, [_P, _P, C.POINTER(_I64)]),
-    "lbm_grid_load_state": (C.c_int, [_P, _P, _I64]),
+    "lbm_grid_save_state": (C.c_int, [_P, _P, _I64, C.POINTER(_I64)]),
+    "lbm_grid_load_state": (C.c_int, [_P, _P, _I64, _I64]),
     "lbm_grid_scale": (_D, [_P]),
     "lbm_local_keff_batch": (C.c_int, [_PP, _P, _P, _I32, _D, _D, _I64, _I32, _I32, _P, _P, _P, _P]),
     "lbm_set_time_limit": (C.c_int, [_D]),
@@ -79,8 +79,8 @@ SIGNATURES = {
     "lbm3d_block_average": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P, _P]),
     "lbm3d_upscale": (C.c_int, [C.POINTER(lbm3d_params), _P, _I32, _D, _D, _I64, _P, C.POINTER(_I32), _P]),
     "lbm3d_grid_state_bytes": (_I64, [_P]),
-    "lbm3d_grid_save_state": (C.c_int, [_P, _P]),
-    "lbm3d_grid_load_state": (C.c_int, [_P, _P]),
+    "lbm3d_grid_save_state": (C.c_int, [_P, _P, _I64]),
+    "lbm3d_grid_load_state": (C.c_int, [_P, _P, _I64]),
     "lbm_coarse_run": (C.c_int, [_PP, _I32, _P, _P, _I64, _D, _I32, _P, _P, _P, C.POINTER(_I64), _P]),
     "lbm_block_average": (C.c_int, [_P, _I32, _I32, _I32, _P, _P]),
     "lbm_surrogate_param_count": (_I64, []),

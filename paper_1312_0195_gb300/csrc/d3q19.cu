@@ -1249,25 +1249,70 @@ lbm_status lbm3d_grid_create(const lbm3d_params *p, const float *kappa_dev, void
 
 int64_t lbm3d_grid_state_bytes(const lbm3d_grid *g)
 {
-    return g ? (int64_t)Q19 * g->plane * (int64_t)g->esz : -1;
+    return g ? CKPT_HEADER_BYTES + (int64_t)Q19 * g->plane * (int64_t)g->esz : -1;
 }
 
-lbm_status lbm3d_grid_save_state(lbm3d_grid *g, void *state_dev)
+}  // extern "C"
+
+namespace {
+
+// The header a checkpoint of 3-D grid g carries (and a loaded one must match).
+CkptHeader grid3_header(const lbm3d_grid *g)
+{
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBM3CKPT", 8);
+    h.version = 1;
+    h.storage = g->p.storage;
+    h.nx = g->p.nx;
+    h.ny = g->p.ny;
+    h.nz = g->p.nz;
+    h.scale = g->S;
+    const double d[6] = {g->p.tau, g->p.nu, g->p.eps, g->p.gx, g->p.gy, g->p.gz};
+    const int32_t t = g->tensor;
+    h.params_hash = fnv1a(&t, sizeof t, fnv1a(d, sizeof d));
+    h.steps = 0;
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm3d_grid_save_state(lbm3d_grid *g, void *state_dev, int64_t nbytes)
 {
     if (!g) return fail(LBM_EINVAL, "grid is NULL");
+    if (nbytes != lbm3d_grid_state_bytes(g))
+        return fail(LBM_EINVAL, "state buffer holds %lld bytes, the grid's state is %lld", (long long)nbytes,
+                    (long long)lbm3d_grid_state_bytes(g));
     if (!is_device_ptr(state_dev)) return fail(LBM_EINVAL, "state_dev must be a device pointer");
-    L3_CUDA(cudaMemcpyAsync(state_dev, g->buf[g->cur], (size_t)lbm3d_grid_state_bytes(g), cudaMemcpyDeviceToDevice,
-                            g->st));
+    const CkptHeader h = grid3_header(g);
+    char *dst = static_cast<char *>(state_dev);
+    L3_CUDA(cudaMemcpyAsync(dst, &h, sizeof h, cudaMemcpyHostToDevice, g->st));
+    L3_CUDA(cudaMemcpyAsync(dst + CKPT_HEADER_BYTES, g->buf[g->cur], (size_t)(nbytes - CKPT_HEADER_BYTES),
+                            cudaMemcpyDeviceToDevice, g->st));
     L3_CUDA(cudaStreamSynchronize(g->st));
     return LBM_OK;
 }
 
-lbm_status lbm3d_grid_load_state(lbm3d_grid *g, const void *state_dev)
+lbm_status lbm3d_grid_load_state(lbm3d_grid *g, const void *state_dev, int64_t nbytes)
 {
     if (!g) return fail(LBM_EINVAL, "grid is NULL");
+    if (nbytes != lbm3d_grid_state_bytes(g))
+        return fail(LBM_EINVAL, "state buffer holds %lld bytes, the grid's state is %lld", (long long)nbytes,
+                    (long long)lbm3d_grid_state_bytes(g));
     if (!is_device_ptr(state_dev)) return fail(LBM_EINVAL, "state_dev must be a device pointer");
-    L3_CUDA(cudaMemcpyAsync(g->buf[g->cur], state_dev, (size_t)lbm3d_grid_state_bytes(g), cudaMemcpyDeviceToDevice,
-                            g->st));
+    CkptHeader saved;
+    L3_CUDA(cudaMemcpyAsync(&saved, state_dev, sizeof saved, cudaMemcpyDeviceToHost, g->st));
+    L3_CUDA(cudaStreamSynchronize(g->st));
+    const CkptHeader mine = grid3_header(g);
+    if (std::memcmp(saved.magic, mine.magic, 8) || saved.version != mine.version || saved.storage != mine.storage ||
+        saved.nx != mine.nx || saved.ny != mine.ny || saved.nz != mine.nz || saved.scale != mine.scale ||
+        saved.params_hash != mine.params_hash)
+        return fail(LBM_EINVAL, "the state was saved by a grid of another size, storage, scale or parameter set");
+    const char *src = static_cast<const char *>(state_dev);
+    L3_CUDA(cudaMemcpyAsync(g->buf[g->cur], src + CKPT_HEADER_BYTES, (size_t)(nbytes - CKPT_HEADER_BYTES),
+                            cudaMemcpyDeviceToDevice, g->st));
     L3_CUDA(cudaStreamSynchronize(g->st));
     return LBM_OK;
 }

@@ -623,33 +623,78 @@ int64_t lbm_grid_steps(const lbm_grid *g) { return g ? g->t : -1; }
 
 int64_t lbm_grid_state_bytes(const lbm_grid *g)
 {
-    return g ? (int64_t)(2 * 9 * g->plane * storage_bytes(g->p.storage)) : -1;
+    return g ? CKPT_HEADER_BYTES + (int64_t)(2 * 9 * g->plane * storage_bytes(g->p.storage)) : -1;
 }
 
-lbm_status lbm_grid_save_state(lbm_grid *g, void *state_dev, int64_t *steps)
+}  // extern "C"
+
+namespace lbm {
+
+// The header a checkpoint of grid g carries (and a loaded one must match).
+static CkptHeader grid_header(const lbm_grid *g)
+{
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBM2CKPT", 8);
+    h.version = 1;
+    h.storage = g->p.storage;
+    h.nx = g->p.nx;
+    h.ny = g->p.ny;
+    h.nz = 1;
+    h.scale = g->S;
+    const double d[5] = {g->p.tau, g->nu, g->p.eps, g->p.gx, g->p.gy};
+    const int32_t i[4] = {g->p.bc, g->p.force_model, g->coef_mode, g->has_g ? 1 : 0};
+    h.params_hash = fnv1a(i, sizeof i, fnv1a(d, sizeof d));
+    h.steps = g->t;
+    return h;
+}
+
+}  // namespace lbm
+
+extern "C" {
+
+lbm_status lbm_grid_save_state(lbm_grid *g, void *state_dev, int64_t nbytes, int64_t *steps)
 {
     if (!g || !state_dev) return fail(LBM_EINVAL, "grid or state is NULL");
+    if (nbytes != lbm_grid_state_bytes(g))
+        return fail(LBM_EINVAL, "state buffer holds %lld bytes, the grid's state is %lld", (long long)nbytes,
+                    (long long)lbm_grid_state_bytes(g));
     if (!is_device_ptr(state_dev)) return fail(LBM_EINVAL, "state_dev is not a device pointer");
     DeviceGuard dg(g->dev);
     const size_t half = 9 * g->plane * storage_bytes(g->p.storage);
-    LBM_CUDA(cudaMemcpyAsync(state_dev, g->buf[g->cur], half, cudaMemcpyDeviceToDevice, g->stream));
-    LBM_CUDA(cudaMemcpyAsync(static_cast<char *>(state_dev) + half, g->buf[1 - g->cur], half,
-                             cudaMemcpyDeviceToDevice, g->stream));
+    const CkptHeader h = grid_header(g);
+    char *dst = static_cast<char *>(state_dev);
+    LBM_CUDA(cudaMemcpyAsync(dst, &h, sizeof h, cudaMemcpyHostToDevice, g->stream));
+    LBM_CUDA(cudaMemcpyAsync(dst + CKPT_HEADER_BYTES, g->buf[g->cur], half, cudaMemcpyDeviceToDevice, g->stream));
+    LBM_CUDA(cudaMemcpyAsync(dst + CKPT_HEADER_BYTES + half, g->buf[1 - g->cur], half, cudaMemcpyDeviceToDevice,
+                             g->stream));
     LBM_CUDA(cudaStreamSynchronize(g->stream));
     if (steps) *steps = g->t;
     return LBM_OK;
 }
 
-lbm_status lbm_grid_load_state(lbm_grid *g, const void *state_dev, int64_t steps)
+lbm_status lbm_grid_load_state(lbm_grid *g, const void *state_dev, int64_t nbytes, int64_t steps)
 {
     if (!g || !state_dev) return fail(LBM_EINVAL, "grid or state is NULL");
     if (steps < 0) return fail(LBM_EINVAL, "steps must be >= 0");
+    if (nbytes != lbm_grid_state_bytes(g))
+        return fail(LBM_EINVAL, "state buffer holds %lld bytes, the grid's state is %lld", (long long)nbytes,
+                    (long long)lbm_grid_state_bytes(g));
     if (!is_device_ptr(state_dev)) return fail(LBM_EINVAL, "state_dev is not a device pointer");
     DeviceGuard dg(g->dev);
+    CkptHeader saved;
+    LBM_CUDA(cudaMemcpyAsync(&saved, state_dev, sizeof saved, cudaMemcpyDeviceToHost, g->stream));
+    LBM_CUDA(cudaStreamSynchronize(g->stream));
+    const CkptHeader mine = grid_header(g);
+    if (std::memcmp(saved.magic, mine.magic, 8) || saved.version != mine.version || saved.storage != mine.storage ||
+        saved.nx != mine.nx || saved.ny != mine.ny || saved.nz != mine.nz || saved.scale != mine.scale ||
+        saved.params_hash != mine.params_hash)
+        return fail(LBM_EINVAL, "the state was saved by a grid of another size, storage, scale or parameter set");
     const size_t half = 9 * g->plane * storage_bytes(g->p.storage);
-    LBM_CUDA(cudaMemcpyAsync(g->buf[g->cur], state_dev, half, cudaMemcpyDeviceToDevice, g->stream));
-    LBM_CUDA(cudaMemcpyAsync(g->buf[1 - g->cur], static_cast<const char *>(state_dev) + half, half,
-                             cudaMemcpyDeviceToDevice, g->stream));
+    const char *src = static_cast<const char *>(state_dev);
+    LBM_CUDA(cudaMemcpyAsync(g->buf[g->cur], src + CKPT_HEADER_BYTES, half, cudaMemcpyDeviceToDevice, g->stream));
+    LBM_CUDA(cudaMemcpyAsync(g->buf[1 - g->cur], src + CKPT_HEADER_BYTES + half, half, cudaMemcpyDeviceToDevice,
+                             g->stream));
     LBM_CUDA(cudaStreamSynchronize(g->stream));
     g->t = steps;
     return LBM_OK;

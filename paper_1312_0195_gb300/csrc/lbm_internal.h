@@ -79,3 +79,36 @@ bool step_vec_ok(int storage, int nx, int vec);   // is this cells-per-thread va
 void count_launches(int64_t n);
 
 }  // namespace lbm
+
+namespace lbm {
+
+// ---- checkpoints (lbm_api.cu, d3q19.cu) -----------------------------------------
+// A saved state starts with this 256-byte header, then the distribution planes.
+// Loading compares every field with the loading grid's own header, so a state
+// saved by a grid of another size, storage type, FP16 scale or parameter set is
+// rejected instead of being misread.
+constexpr int64_t CKPT_HEADER_BYTES = 256;
+struct CkptHeader {
+    char magic[8];          // "LBM2CKPT" (D2Q9) or "LBM3CKPT" (D3Q19)
+    int32_t version;        // 1
+    int32_t storage;        // lbm_storage
+    int64_t nx, ny, nz;     // nz = 1 for D2Q9
+    double scale;           // FP16 storage scale S (1 otherwise)
+    uint64_t params_hash;   // FNV-1a over the parameters the update depends on
+    int64_t steps;          // steps taken when saved (D2Q9; 0 for D3Q19)
+    uint8_t pad[CKPT_HEADER_BYTES - 64];
+};
+static_assert(sizeof(CkptHeader) == CKPT_HEADER_BYTES, "checkpoint header is 256 bytes");
+
+// 64-bit FNV-1a (Fowler, Noll, Vo) of a byte range, continuing from h.
+inline uint64_t fnv1a(const void *data, size_t n, uint64_t h = 0xcbf29ce484222325ull)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+}  // namespace lbm

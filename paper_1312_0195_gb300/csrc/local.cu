@@ -51,7 +51,6 @@ template <typename T> struct LocalCfg {
 };
 constexpr int MAXSLOTS = 64;
 constexpr int MAXCLASS = 64;
-constexpr size_t LOCAL_SMEM = LocalCfg<float>::SMEM;
 
 struct LocalArgs {
     const float *kappa;       // field [ny][nx]
@@ -605,9 +604,12 @@ double local_time_limit() { return g_time_limit_s; }
 // it until the process exits. Its device address is looked up with
 // cudaGetSymbolAddress once per device, by the first call on that device with
 // the device current; that first call should therefore happen before any
-// stream capture. All calls share the array and it keeps the last call's
-// contents, so each call clears what must start at zero; calls that overlap
-// on the GPU (different streams or threads) race on it.
+// stream capture. Every call also reads the class table and the status flags
+// back to the host and synchronises the stream before it returns. All calls
+// share the array and it keeps the last call's contents, so each call clears
+// what must start at zero; calls that overlap on the GPU (different streams or
+// threads) race on it. storage = LBM_F64 runs the FP64 solver (leaves up to 45
+// cells), any other storage the FP32 one, as in lbm_local_keff_batch.
 // ---------------------------------------------------------------------------
 namespace lbm {
 namespace {
@@ -626,11 +628,12 @@ static __device__ __align__(256) int g_noalloc_scratch[NA_TOTAL];
 
 std::atomic<int *> g_noalloc_ptr[64];   // device address of the array, per device
 
-__global__ void noalloc_count_kernel(const int *leaves, int n, int nx, int ny, int *scr)
+// smax: the largest leaf the solver's shared memory holds (64 in FP32, 45 in FP64)
+__global__ void noalloc_count_kernel(const int *leaves, int n, int nx, int ny, int smax, int *scr)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int x0 = leaves[3 * i], y0 = leaves[3 * i + 1], s = leaves[3 * i + 2];
-        if (s < 1 || s > 64 || x0 < 0 || y0 < 0 || (long long)x0 + s > nx || (long long)y0 + s > ny) {
+        if (s < 1 || s > smax || x0 < 0 || y0 < 0 || (long long)x0 + s > nx || (long long)y0 + s > ny) {
             atomicOr(&scr[NA_FLAGS], 1);
             continue;
         }
@@ -729,14 +732,17 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     if (steps_dev) NA_CUDA(cudaMemsetAsync(steps_dev, 0, sizeof(int32_t) * 2 * n_leaves, st));
     const int *lv = reinterpret_cast<const int *>(leaves_dev);
     const int nb = (n_leaves + 255) / 256 < 1024 ? (n_leaves + 255) / 256 : 1024;
-    noalloc_count_kernel<<<nb, 256, 0, st>>>(lv, n_leaves, p->nx, p->ny, scr);
+    const bool f64 = p->storage == LBM_F64;           // the FP64 solver, as lbm_local_keff_batch
+    const int smax = f64 ? 45 : 64;
+    noalloc_count_kernel<<<nb, 256, 0, st>>>(lv, n_leaves, p->nx, p->ny, smax, scr);
     noalloc_table_kernel<<<1, 32, 0, st>>>(scr);
     NA_CUDA(cudaGetLastError());
     int head[NA_HEADER];
     NA_CUDA(cudaMemcpyAsync(head, scr, sizeof head, cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
     count_launches(2);
-    if (head[NA_FLAGS]) return fail(LBM_EINVAL, "a leaf has a size outside [1, 64] or lies outside the field");
+    if (head[NA_FLAGS])
+        return fail(LBM_EINVAL, "a leaf has a size outside [1, %d] or lies outside the field", smax);
     noalloc_scatter_kernel<<<nb, 256, 0, st>>>(lv, n_leaves, scr);
     NA_CUDA(cudaGetLastError());
     count_launches(1);
@@ -773,10 +779,12 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     a.worst = scr + NA_FLAGS + 1;
     a.abort_flag = scr + NA_FLAGS + 2;
     a.time_limit_ns = (unsigned long long)(g_time_limit_s * 1e9);
-    NA_CUDA(cudaFuncSetAttribute(local_keff_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LOCAL_SMEM));
+    auto kern = f64 ? local_keff_kernel<double> : local_keff_kernel<float>;
+    const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
+    NA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int blocks = sm_count(dev);
     if (blocks > 2 * n_leaves) blocks = 2 * n_leaves;
-    local_keff_kernel<float><<<blocks, LOCAL_THREADS, LOCAL_SMEM, st>>>(a);
+    kern<<<blocks, LOCAL_THREADS, smem, st>>>(a);
     NA_CUDA(cudaGetLastError());
     count_launches(1);
     int flags[2] = {0, 0};

@@ -125,7 +125,7 @@ def test_3d_host_side_validation(lib):
     assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 1, 1e-6, 1e-8, 0, 64, None, None, None, None) == 1
     assert lib.lbm3d_local_keff_batch(C.byref(p), None, None, 0, 1e-6, 1e-8, 1000, 64, None, None, None, None) == 0
     assert lib.lbm3d_grid_state_bytes(None) == -1
-    assert lib.lbm3d_grid_save_state(None, None) == 1 and lib.lbm3d_grid_load_state(None, None) == 1
+    assert lib.lbm3d_grid_save_state(None, None, 0) == 1 and lib.lbm3d_grid_load_state(None, None, 0) == 1
     nnc = C.c_int32(-1)
     assert lib.lbm3d_upscale(C.byref(p), None, 3, 1e-6, 1e-8, 1000, None, C.byref(nnc), None) == 1   # 8 % 3
     assert nnc.value == 0

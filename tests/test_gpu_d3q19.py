@@ -316,3 +316,12 @@ def test_d3q19_checkpoint_restart_is_bitwise(storage):
         fb = [t.cpu().numpy() for t in b.fields()]
     for x, y in zip(fa, fb):
         np.testing.assert_array_equal(x, y)
+    # another parameter set (or a buffer of the wrong size) is rejected, not misread
+    p2 = lbm.Params3D(nx=12, ny=8, nz=6, tau=0.9, nu=0.1, eps=0.9, gx=1e-6, gy=-0.5e-6, storage=storage)
+    with lbm.Grid3D(p2, kap) as c:
+        with pytest.raises(lbm.LbmError) as ei:
+            c.load_state(st)
+        assert ei.value.status == lbm.LBM_EINVAL
+        with pytest.raises(lbm.LbmError) as ei:
+            c.load_state(st[:-16])
+        assert ei.value.status == lbm.LBM_EINVAL

@@ -205,7 +205,8 @@ def test_full_size_4096_sampled_against_oracle_windows():
         # mass: the sum of all stored deviations (= sum of drho) stays at its initial 0
         state = torch.empty(lbm.lbm_grid_state_bytes(G.handle), dtype=torch.uint8, device="cuda")
         lbm.lbm_grid_save_state(G.handle, state)
-        cur = state[: state.numel() // 2].view(torch.float32)
+        hdr = lbm.CKPT_HEADER_BYTES
+        cur = state[hdr: hdr + (state.numel() - hdr) // 2].view(torch.float32)
         total_drho = float(cur.double().sum())
     rng = np.random.default_rng(0)
     pts = [(0, 0), (N - 1, N - 1), (0, N - 1), (N - 1, 0)] + [tuple(rng.integers(0, N, 2)) for _ in range(12)]
@@ -250,7 +251,8 @@ def test_full_size_16384_channelised_sampled():
         del rho, u, v
         full = torch.empty(lbm.lbm_grid_state_bytes(G.handle), dtype=torch.uint8, device="cuda")
         lbm.lbm_grid_save_state(G.handle, full)
-        total_drho = float(full[: full.numel() // 2].view(torch.float32).sum(dtype=torch.float64))
+        hdr = lbm.CKPT_HEADER_BYTES
+        total_drho = float(full[hdr: hdr + (full.numel() - hdr) // 2].view(torch.float32).sum(dtype=torch.float64))
         del full
     W = 2 * n + 9
     h = W // 2
@@ -326,6 +328,24 @@ def test_mean_velocity_bitwise_repeatable_and_checkpoint():
     with lbm.Grid(p, kt) as B:
         B.step(100, 0.0, 0)
         assert B.mean_velocity() == m1
+    # the header rejects a state saved under other parameters, and the byte count must match
+    for other in (lbm.Params(nx=64, ny=64, tau=0.9, eps=1.0, gx=1e-6),
+                  lbm.Params(nx=64, ny=64, tau=0.8, eps=1.0, gx=1e-6, storage=2)):
+        with lbm.Grid(other, kt) as Cg:
+            n_other = lbm.lbm_grid_state_bytes(Cg.handle)
+            buf = state if n_other == state.numel() else torch.zeros(n_other, dtype=torch.uint8, device="cuda")
+            if buf is not state:
+                buf[: state.numel()].copy_(state)
+            with pytest.raises(lbm.LbmError) as ei:
+                lbm.lbm_grid_load_state(Cg.handle, buf, 100)
+            assert ei.value.status == lbm.LBM_EINVAL
+    with lbm.Grid(p, kt) as D:
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_grid_load_state(D.handle, state[:-16], 100)
+        assert ei.value.status == lbm.LBM_EINVAL
+        lbm.lbm_grid_load_state(D.handle, state, t)
+        D.step(57, 0.0, 0)
+        assert torch.equal(D.fields()[1].cpu(), ref)
 
 
 @pytest.mark.parametrize("storage,vecs", [(0, (1, 4, 8)), (1, (1, 2, 4, 8)), (2, (1, 2))])
