@@ -370,7 +370,7 @@ def measure_cpu_oracles(kap_np, leaf_sample=64, patch_sample=32, cube_sample=16,
     rng = np.random.default_rng(seed)
     pick = leaves[rng.choice(len(leaves), leaf_sample, replace=False)]
     patches = [np.array(kap_np[y:y + s, x:x + s], dtype=np.float64) for x, y, s in pick]
-    xs = [osur.make_input(osur.resample_patch(np.log(p)), p.shape[0], 0.0, 1.0) for p in patches[:patch_sample]]
+    xs = [osur.make_input(np.log(p), 0.0, 1.0) for p in patches[:patch_sample]]
     workers = os.cpu_count() or 1
     k3 = synth.lognormal_kappa3d(256, 256, 256, 8.0, 2.0, seed=7)
     corners = rng.choice(16 ** 3, cube_sample, replace=False)

@@ -228,14 +228,14 @@ lbm_status lbm_set_time_limit(double seconds);
  * obtains every K* by local LBM, Section 3): an ensemble of small CNNs maps a
  * subdomain's permeability patch to (log K*_xx, log K*_yy); local LBM stays the
  * fallback for doubtful patches and the arbiter of the surrogate's error.
- * Network per model: six 3x3 'same' convolutions 2 -> 32 -> 32 -> 64 -> 64 ->
+ * Network per model: six 3x3 'same' convolutions 5 -> 32 -> 32 -> 64 -> 64 ->
  * 64 -> 64 with ReLU, global average pooling, a 64 -> 2 linear head; BF16
  * activations and weights on the tensor cores with FP32 accumulation, FP32
- * master weights, Adam. Inputs are patches from lbm_patches. */
+ * master weights, Adam. Inputs are the five planes lbm_patches writes. */
 typedef struct lbm_surrogate lbm_surrogate;
 
 /* Number of FP32 parameters of one model; layout: for layer l = 0..5 the weights
- * [c_out][c_in][3][3] then the bias [c_out] (c_in = 2, 32, 32, 64, 64, 64;
+ * [c_out][c_in][3][3] then the bias [c_out] (c_in = 5, 32, 32, 64, 64, 64;
  * c_out = 32, 32, 64, 64, 64, 64), then the head [2][64] and its bias [2]. */
 int64_t lbm_surrogate_param_count(void);
 
@@ -246,38 +246,75 @@ lbm_status lbm_surrogate_destroy(lbm_surrogate *s);
 lbm_status lbm_surrogate_get_params(const lbm_surrogate *s, int32_t model, float *host_out);
 lbm_status lbm_surrogate_set_params(lbm_surrogate *s, int32_t model, const float *host_in);
 /* Normalisation and gate range, HOST float[13]: input shift and scale of the
- * log-K plane, target mean/std of log K*_xx and log K*_yy, then (low, high) of
+ * log-K planes, target mean/std of log K*_xx and log K*_yy, then (low, high) of
  * each patch statistic (mean, std, gradient energy of log K), then the target
- * mode: the networks learn (log K* - c) / w per component with, per patch,
+ * mode: the networks learn (log K* - c) / w per component with, per leaf,
  * 0: c = mean log K, w = 1; 1: c = midpoint of the log layered-medium bounds
- * of the 32 x 32 plane (rows as parallel series tubes below, columns as series
- * parallel slabs above), w = 1; 2: that midpoint and w = half the log width
- * (at least 0.05). lbm_surrogate_train sets every entry but the mode from its
- * data and keeps the mode set before it (2 for a new ensemble). */
+ * (rows as parallel series tubes below, columns as series parallel slabs above)
+ * of the leaf's 64 x 64 log-K plane (see lbm_patches), w = 1; 2: that midpoint
+ * and w = half the log width (at least 0.05). lbm_surrogate_train sets every
+ * entry but the mode from its data and keeps the mode set before it (2 for a
+ * new ensemble). */
 lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13]);   /* mode not 0-2: EINVAL */
 lbm_status lbm_surrogate_get_normalization(const lbm_surrogate *s, float norm[13]);
 
 /* Leaf -> surrogate input. For each leaf (size s dividing 32, or a multiple of
- * 32 up to 1024) writes x_dev[i] = two float [32][32] planes: log K resampled to
- * 32 x 32 (each cell repeated 32/s times per axis, or the mean of log K over
- * (s/32)^2 blocks) and the constant log2(s)/6; and stats_dev[i] = (mean,
- * standard deviation, gradient energy) of that log-K patch. kappa must be > 0. */
+ * 64 up to 1024) the leaf's log K is put on a 64 x 64 plane (each cell repeated
+ * 64/s times per axis for s <= 32, the leaf itself for s = 64, the mean of log K
+ * over (s/64)^2 blocks above) and x_dev[i] receives five float [32][32] planes:
+ * plane 2a + b holds that plane's cell (2 row + a, 2 column + b), so a 64-cell
+ * leaf enters at full resolution, and plane 4 is the constant log2(s)/6.
+ * stats_dev[i] = (mean, standard deviation, gradient energy) of the 32 x 32
+ * mean of the four phase planes. kappa must be > 0. */
 lbm_status lbm_patches(const float *kappa_dev, int32_t nx, int32_t ny, const lbm_leaf *leaves_dev, int32_t n,
                        float *x_dev, float *stats_dev, void *cuda_stream);
 
-/* Trains every model on n samples x_dev [n][2][32][32], targets y_dev [n][2]
- * (log K*_xx, log K*_yy), stats_dev [n][3] from lbm_patches. The networks learn
- * log K* minus the patch's mean log K (standardised); lbm_surrogate_predict adds
- * it back. Adam (0.9, 0.999,
- * 1e-8), learning rate lr with cosine decay to lr/10, mini-batches of `batch`
- * (<= 1024) from a seeded shuffle per epoch. loss_host (HOST, may be NULL)
- * receives [n_models][epochs] mean training loss on standardised targets. */
+/* Trains every model on n samples x_dev [n][5][32][32] (lbm_patches), targets
+ * y_dev [n][2] (log K*_xx, log K*_yy), stats_dev [n][3] from lbm_patches. The
+ * networks learn (log K* - c) / w with the per-leaf base (c, w) of the target
+ * mode (see lbm_surrogate_set_normalization), standardised; lbm_surrogate_predict
+ * undoes both. Adam (0.9, 0.999, 1e-8), learning rate lr with cosine decay to
+ * lr/10, mini-batches of `batch` (<= 1024) from a seeded shuffle per epoch.
+ * loss_host (HOST, may be NULL) receives [n_models][epochs] mean training loss
+ * on standardised targets. */
 lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float *y_dev, const float *stats_dev,
                                int32_t n, int32_t epochs, int32_t batch, double lr, uint64_t seed, float *loss_host,
                                void *cuda_stream);
 
-/* Predictions of every model: y_dev [n_models][n][2] = log K*_xx, log K*_yy. */
+/* Predictions of every model for inputs x_dev [n][5][32][32]:
+ * y_dev [n_models][n][2] = log K*_xx, log K*_yy. */
 lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n, float *y_dev, void *cuda_stream);
+
+/* Per-size gate of lbm_surrogate_keff (and lbm_upscale) when it is called with
+ * spread_max = 0: HOST float[7], the relative spread limit for leaves of 1, 2, 4,
+ * 8, 16, 32 and 64 cells (each > 0; default 0.03). */
+lbm_status lbm_surrogate_set_gate(lbm_surrogate *s, const float spread_by_log2size[7]);
+lbm_status lbm_surrogate_get_gate(const lbm_surrogate *s, float spread_by_log2size[7]);
+
+/* K* of arbitrary leaves by the ensemble, with local LBM (Section 3, Eq. 17) for
+ * the leaves the gate rejects, all enqueued on the device: patches (lbm_patches),
+ * inference of every model, the gate, and the persistent local solver whose work
+ * queue the gate fills on the device (no host round trip between them; one
+ * stream synchronisation at the end). A leaf (size s a power of two from 1 to
+ * 64, or to 45 cells with the margin for LBM_F64 storage; inside the field) is
+ * accepted when, for log K*_xx and log K*_yy, the members' sample standard
+ * deviation is at most ln(1 + spread) and their mean is finite, and each patch
+ * statistic lies in the range seen in training; spread = spread_max when > 0,
+ * else the ensemble's per-size value (lbm_surrogate_set_gate). Accepted leaves
+ * get K* = diag(exp(mean log K*_xx), exp(mean log K*_yy)); the others are solved
+ * as by lbm_local_keff_batch (p: tau, nu, eps, storage, margin; check every 64
+ * steps) and get its K*. Outputs (caller-owned DEVICE memory): keff_dev double
+ * [n][4] (xx, xy, yx, yy), fallback_dev int32 [n] (0 accepted, 1 local LBM; may
+ * be NULL), status_dev int32 [n] (LBM_OK for accepted leaves, the local solver's
+ * status otherwise; may be NULL); *n_fallback (HOST, may be NULL) the number of
+ * leaves solved by local LBM. An invalid leaf gives LBM_EINVAL after the device
+ * work (it is found there) with no local problem solved; otherwise returns the
+ * worst status as lbm_local_keff_batch. Work buffers are kept in the ensemble
+ * and reused by later calls (no allocation once they are large enough). */
+lbm_status lbm_surrogate_keff(lbm_surrogate *s, const lbm_params *p, const float *kappa_dev,
+                              const lbm_leaf *leaves_dev, int32_t n, double spread_max, double g_const,
+                              double tol_rel, int64_t max_steps, double *keff_dev, int32_t *fallback_dev,
+                              int32_t *status_dev, int32_t *n_fallback, void *cuda_stream);
 
 /* One forward and backward pass of one model on n <= 1024 inputs with
  * targets t_dev [n][2] in standardised units: HOST outputs (each may be NULL)
@@ -292,13 +329,14 @@ lbm_status lbm_surrogate_grad(lbm_surrogate *s, int32_t model, const float *x_de
  * K* of every subdomain comes from its local problems (lbm_local_keff_batch).
  * keff_coarse_dev: caller-owned DEVICE double [ny/r][nx/r][4] (xx, xy, yx, yy) in
  * FINE lattice units. With sur == NULL every block is solved by local LBM. With
- * an ensemble, its prediction (K*_xx = exp(mean log K*_xx), likewise yy, zero
- * off-diagonal) is used for a block unless the ensemble's spread (standard
- * deviation across models of either log K*) exceeds ln(1 + spread_max) or a
- * patch statistic lies outside the range seen in training; such blocks fall
- * back to local LBM. *n_fallback (HOST, may be NULL) receives the number of
- * blocks solved by local LBM. Status as for lbm_local_keff_batch (check_every =
- * 64, persistent launch). */
+ * an ensemble, lbm_surrogate_keff runs on one leaf per block: its prediction
+ * (K*_xx = exp(mean log K*_xx), likewise yy, zero off-diagonal) is used for a
+ * block unless the ensemble's spread (standard deviation across models of either
+ * log K*) exceeds ln(1 + spread_max) (spread_max = 0: the ensemble's per-size
+ * limit) or a patch statistic lies outside the range seen in training; such
+ * blocks fall back to local LBM. *n_fallback (HOST, may be NULL) receives the
+ * number of blocks solved by local LBM. Status as for lbm_local_keff_batch
+ * (check_every = 64, persistent launch). */
 lbm_status lbm_upscale(const lbm_params *p, const float *kappa_dev, int32_t block, const lbm_surrogate *sur,
                        double spread_max, double g_const, double tol_rel, int64_t max_steps,
                        double *keff_coarse_dev, int32_t *n_fallback, void *cuda_stream);

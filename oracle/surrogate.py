@@ -6,7 +6,9 @@ log K*_xx and log K*_yy; local LBM stays its fallback and the arbiter of its err
 This module restates what the library's kernels compute, plainly and in FP64,
 so they can be checked: direct 3x3 'same' convolutions (one matmul per tap),
 ReLU, global average pooling, a linear head, the backward pass of all of it,
-the mean-squared-error loss, Adam, patch resampling and patch statistics.
+the mean-squared-error loss, Adam, the leaf-to-input planes, patch statistics,
+the per-leaf target base and the gate that accepts a prediction or sends the
+leaf back to local LBM.
 Only tests, the smoke check and the benchmark's CPU baseline import it; it
 shares no code with the CUDA path.
 
@@ -18,30 +20,45 @@ from __future__ import annotations
 
 import numpy as np
 
-CHANNELS = (2, 32, 32, 64, 64, 64, 64)     # input planes: log kappa, leaf-size plane
+CHANNELS = (5, 32, 32, 64, 64, 64, 64)     # input planes: four phase planes of log K, leaf-size plane
 PATCH = 32
+PHASES = 4
 
 
 # ---------------------------------------------------------------- patches
 
-def resample_patch(logk: np.ndarray) -> np.ndarray:
-    """A leaf's log-permeability (s x s) as a 32 x 32 patch.
+def _check_size(s: int) -> None:
+    if not ((1 <= s <= PATCH and PATCH % s == 0) or (s % 64 == 0 and 64 <= s <= 1024)):
+        raise ValueError("leaf size must divide 32 or be a multiple of 64 up to 1024")
 
-    s < 32 (a divisor of 32): each cell is replicated (32 / s) x (32 / s) times;
-    s = 32: unchanged; s > 32 (a multiple of 32): mean of log K over (s / 32)^2 blocks.
+
+def full_plane(logk: np.ndarray) -> np.ndarray:
+    """A leaf's log-permeability (s x s) on a 64 x 64 plane.
+
+    s < 64 (a divisor of 32): each cell repeated (64 / s) x (64 / s) times;
+    s = 64: the leaf itself; s = 64 r (r >= 2): the mean of log K over r x r blocks.
     """
     s = logk.shape[0]
-    if s == PATCH:
-        return logk.astype(np.float64).copy()
-    if s < PATCH:
-        if PATCH % s:
-            raise ValueError("leaf size must divide 32")
-        r = PATCH // s
+    _check_size(s)
+    if s < 64:
+        r = 64 // s
         return np.repeat(np.repeat(logk, r, axis=0), r, axis=1).astype(np.float64)
-    if s % PATCH:
-        raise ValueError("leaf size must be a multiple of 32")
-    r = s // PATCH
-    return logk.reshape(PATCH, r, PATCH, r).mean(axis=(1, 3))
+    r = s // 64
+    return logk.astype(np.float64).reshape(64, r, 64, r).mean(axis=(1, 3))
+
+
+def phase_planes(logk: np.ndarray) -> np.ndarray:
+    """The 64 x 64 plane of full_plane split by the parity of its row and column:
+    plane 2 a + b holds cell (2 i + a, 2 j + b) at (i, j), so the four 32 x 32 planes carry
+    every cell of a 64-cell leaf (and four equal copies of a leaf of 32 cells or fewer)."""
+    f = full_plane(logk)
+    return np.stack([f[a::2, b::2] for a in (0, 1) for b in (0, 1)])
+
+
+def resample_patch(logk: np.ndarray) -> np.ndarray:
+    """A leaf's log-permeability as one 32 x 32 patch: the mean of its four phase planes
+    (the leaf repeated for s <= 32; 2 x 2 block means of log K for s = 64)."""
+    return phase_planes(logk).mean(axis=0)
 
 
 def patch_stats(p: np.ndarray) -> np.ndarray:
@@ -56,12 +73,87 @@ def patch_stats(p: np.ndarray) -> np.ndarray:
     return np.array([p.mean(), p.std(), ge])
 
 
-def make_input(logk_patch: np.ndarray, size: int, shift: float, scale: float) -> np.ndarray:
-    """Two input planes: (log K - shift) / scale and the constant log2(size) / 6."""
-    x = np.empty((2, PATCH, PATCH))
-    x[0] = (logk_patch - shift) / scale
-    x[1] = np.log2(size) / 6.0
+def make_input(logk: np.ndarray, shift: float, scale: float) -> np.ndarray:
+    """Five input planes of a leaf: its four phase planes as (log K - shift) / scale and the
+    constant log2(size) / 6."""
+    x = np.empty((5, PATCH, PATCH))
+    x[:4] = (phase_planes(logk) - shift) / scale
+    x[4] = np.log2(logk.shape[0]) / 6.0
     return x
+
+
+def layered_bounds(k: np.ndarray):
+    """Bounds on the effective permeability of a rectangular patch k [rows = y][columns = x]
+    from two layered arrangements (the series and parallel means of Tables 1 and 2).
+
+    Flow along x: the rows taken as separate tubes in parallel, each the series (harmonic)
+    mean of its cells, give the lower value lo_x = mean over rows of H_x; the columns taken as
+    slabs in series, each the parallel (arithmetic) mean of its cells, give the upper value
+    hi_x = harmonic mean over columns of A_y. Flow along y: the same with rows and columns
+    exchanged. Returns (lo_x, hi_x, lo_y, hi_y).
+    """
+    k = np.asarray(k, dtype=np.float64)
+    h_rows = 1.0 / np.mean(1.0 / k, axis=1)          # H_x of each row
+    a_cols = np.mean(k, axis=0)                      # A_y of each column
+    h_cols = 1.0 / np.mean(1.0 / k, axis=0)          # H_y of each column
+    a_rows = np.mean(k, axis=1)                      # A_x of each row
+    return (np.mean(h_rows), 1.0 / np.mean(1.0 / a_cols),
+            np.mean(h_cols), 1.0 / np.mean(1.0 / a_rows))
+
+
+def target_base(logk: np.ndarray, mode: int):
+    """Per-leaf base (c_xx, w_xx, c_yy, w_yy) of the surrogate's target: the networks learn
+    (log K* - c) / w for each component.
+
+    mode 0: c = mean log K of the leaf's 64 x 64 plane, w = 1;
+    mode 1: c = midpoint of log lo and log hi of layered_bounds on that plane, w = 1;
+    mode 2: the same c and w = max((log hi - log lo) / 2, 0.05).
+    """
+    f = full_plane(logk)
+    if mode == 0:
+        m = f.mean()
+        return (m, 1.0, m, 1.0)
+    lox, hix, loy, hiy = (np.log(v) for v in layered_bounds(np.exp(f)))
+    wx = 1.0 if mode == 1 else max(0.5 * (hix - lox), 0.05)
+    wy = 1.0 if mode == 1 else max(0.5 * (hiy - loy), 0.05)
+    return (0.5 * (lox + hix), wx, 0.5 * (loy + hiy), wy)
+
+
+# ---------------------------------------------------------------- the gate
+
+def gate(y: np.ndarray, stats: np.ndarray, sizes: np.ndarray, stat_lo, stat_hi, spread_max):
+    """Which leaves take the ensemble's prediction and which go back to local LBM.
+
+    y [M][n][2]: log K*_xx and log K*_yy of each of the M members; stats [n][3] the patch
+    statistics; sizes [n] the leaf sizes; stat_lo, stat_hi [3] the accepted range of each
+    statistic (bounds included); spread_max a relative spread, or a mapping from leaf size to
+    one. Leaf i is accepted when, for both components, the members' sample standard deviation
+    (denominator M - 1; 0 for one member) is at most ln(1 + spread_max) and their mean is
+    finite, and every statistic lies in its range. Returns (accept [n] bool, keff [n][4]):
+    keff = (exp(mean xx), 0, 0, exp(mean yy)) for accepted leaves, NaN for the others.
+    """
+    y = np.asarray(y, dtype=np.float64)
+    m_members, n, _ = y.shape
+    accept = np.zeros(n, dtype=bool)
+    keff = np.full((n, 4), np.nan)
+    for i in range(n):
+        smax = spread_max[int(sizes[i])] if isinstance(spread_max, dict) else spread_max
+        thr = np.log1p(smax)
+        ok = True
+        mean = np.zeros(2)
+        for c in range(2):
+            v = y[:, i, c]
+            mean[c] = v.sum() / m_members
+            sd = np.sqrt(((v - mean[c]) ** 2).sum() / (m_members - 1)) if m_members > 1 else 0.0
+            if not (sd <= thr) or not np.isfinite(mean[c]):
+                ok = False
+        for k in range(3):
+            if not (stat_lo[k] <= stats[i, k] <= stat_hi[k]):
+                ok = False
+        accept[i] = ok
+        if ok:
+            keff[i] = (np.exp(mean[0]), 0.0, 0.0, np.exp(mean[1]))
+    return accept, keff
 
 
 # ---------------------------------------------------------------- network
@@ -89,7 +181,7 @@ def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
     for dy in range(3):
         for dx in range(3):
             win = xp[:, :, dy:dy + h, dx:dx + wd]                     # [n, c, h, w]
-            y += np.einsum("nchw,oc->nohw", win, w[:, :, dy, dx])
+            y += np.einsum("nchw,oc->nohw", win, w[:, :, dy, dx], optimize=True)
     return y + b[None, :, None, None]
 
 
@@ -103,8 +195,8 @@ def conv3x3_backward(x, w, dy):
     for ky in range(3):
         for kx in range(3):
             win = xp[:, :, ky:ky + h, kx:kx + wd]
-            dw[:, :, ky, kx] = np.einsum("nohw,nchw->oc", dy, win)
-            dxp[:, :, ky:ky + h, kx:kx + wd] += np.einsum("nohw,oc->nchw", dy, w[:, :, ky, kx])
+            dw[:, :, ky, kx] = np.einsum("nohw,nchw->oc", dy, win, optimize=True)
+            dxp[:, :, ky:ky + h, kx:kx + wd] += np.einsum("nohw,oc->nchw", dy, w[:, :, ky, kx], optimize=True)
     db = dy.sum(axis=(0, 2, 3))
     return dxp[:, :, 1:-1, 1:-1], dw, db
 

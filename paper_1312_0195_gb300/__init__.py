@@ -221,13 +221,17 @@ def lbm_block_average(field, block: int, out=None, stream=None):
     return out
 
 
+SURROGATE_PLANES = 5          # input planes per leaf (lbm_patches)
+
+
 def lbm_patches(kappa, leaves, x=None, stats=None, stream=None):
-    """Surrogate inputs for leaves: x [n, 2, 32, 32] and stats [n, 3] (CUDA float32)."""
+    """Surrogate inputs for leaves: x [n, 5, 32, 32] (four phase planes of log K and the size plane)
+    and stats [n, 3] (CUDA float32)."""
     import torch
     ny, nx = kappa.shape
     n = int(leaves.shape[0])
     if x is None:
-        x = torch.empty((n, 2, 32, 32), dtype=torch.float32, device=kappa.device)
+        x = torch.empty((n, SURROGATE_PLANES, 32, 32), dtype=torch.float32, device=kappa.device)
     if stats is None:
         stats = torch.empty((n, 3), dtype=torch.float32, device=kappa.device)
     _check(_abi.lib().lbm_patches(_ptr(kappa), int(nx), int(ny), _ptr(leaves), n, _ptr(x), _ptr(stats),
@@ -286,6 +290,37 @@ class Surrogate:
         y = torch.empty((self.n_models, n, 2), dtype=torch.float32, device=x.device)
         _check(_abi.lib().lbm_surrogate_predict(self.handle, _ptr(x), n, _ptr(y), _stream(stream)))
         return y
+
+    def get_gate(self):
+        import numpy as np
+        out = np.empty(7, dtype=np.float32)
+        _check(_abi.lib().lbm_surrogate_get_gate(self.handle, out.ctypes.data))
+        return out
+
+    def set_gate(self, spread_by_log2size):
+        """Relative spread limits for leaves of 1, 2, 4, ..., 64 cells (used with spread_max = 0)."""
+        import numpy as np
+        g = np.ascontiguousarray(spread_by_log2size, dtype=np.float32)
+        assert g.size == 7
+        _check(_abi.lib().lbm_surrogate_set_gate(self.handle, g.ctypes.data))
+
+    def keff(self, params: "Params", kappa, leaves, spread_max: float = 0.0, g_const: float = 1e-6,
+             tol_rel: float = 1e-8, max_steps: int = 200000, stream=None):
+        """lbm_surrogate_keff: returns (keff [n, 4] f64, fallback [n] i32, status [n] i32, n_fallback, worst)."""
+        import torch
+        n = int(leaves.shape[0])
+        dev = kappa.device
+        keff = torch.empty((n, 4), dtype=torch.float64, device=dev)
+        fb = torch.empty((n,), dtype=torch.int32, device=dev)
+        status = torch.empty((n,), dtype=torch.int32, device=dev)
+        nfb = C.c_int32(0)
+        p = params.c()
+        worst = _check(_abi.lib().lbm_surrogate_keff(self.handle, C.byref(p), _ptr(kappa), _ptr(leaves), n,
+                                                     float(spread_max), float(g_const), float(tol_rel),
+                                                     int(max_steps), _ptr(keff), _ptr(fb), _ptr(status),
+                                                     C.byref(nfb), _stream(stream)),
+                       allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
+        return keff, fb, status, int(nfb.value), worst
 
     def grad(self, model: int, x, t, stream=None):
         """(grad [P], loss, y [n, 2]) of one forward/backward pass (standardised targets t)."""

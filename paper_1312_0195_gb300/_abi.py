@@ -94,6 +94,9 @@ SIGNATURES = {
     "lbm_surrogate_train": (C.c_int, [_P, _P, _P, _P, _I32, _I32, _I32, _D, C.c_uint64, _P, _P]),
     "lbm_surrogate_predict": (C.c_int, [_P, _P, _I32, _P, _P]),
     "lbm_surrogate_grad": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _P, _P]),
+    "lbm_surrogate_set_gate": (C.c_int, [_P, _P]),
+    "lbm_surrogate_get_gate": (C.c_int, [_P, _P]),
+    "lbm_surrogate_keff": (C.c_int, [_P, _P, _P, _P, _I32, _D, _D, _D, _I64, _P, _P, _P, C.POINTER(_I32), _P]),
 }
 
 _lib = None

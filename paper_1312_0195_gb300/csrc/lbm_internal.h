@@ -112,3 +112,33 @@ inline uint64_t fnv1a(const void *data, size_t n, uint64_t h = 0xcbf29ce48422232
 }
 
 }  // namespace lbm
+
+namespace lbm {
+
+// ---- device-built work queue of the local problems (surrogate.cu -> local.cu) ------------
+// int array in device memory: the per-size class table the persistent local solver reads at
+// start, filled by kernels of the same stream, so no host round trip is needed between the
+// gate that picks the leaves and the solver that takes them.
+enum DeviceTable {
+    DT_NCLASS = 0,            // number of size classes
+    DT_SIZE = 1,              // [64] class sizes, descending
+    DT_OFF = 65,              // [65] job offsets of the classes (jobs = 2 leaf + drive)
+    DT_CURSOR = 130,          // [65] scatter cursor per patch size (index = size)
+    DT_COUNT = 195,           // [65] leaves per patch size (index = size)
+    DT_HEADS = 260,           // [64] queue heads per class
+    DT_BAD = 324,             // non-zero: an invalid leaf was found (nothing is solved)
+    DT_WORST = 325,           // worst per-leaf status of the solver
+    DT_ABORT = 326,           // the solver's wall-clock limit ran out
+    DT_NFALLBACK = 327,       // leaves sent to the solver
+    DT_INTS = 384
+};
+
+// Launches the persistent local solver on the jobs of a device-built table (the table's job
+// list `jobs` holds 2 leaf + drive for leaves of `leaves_dev`; per-leaf outputs are indexed by
+// leaf). Enqueues only: no host synchronisation; the caller reads DT_WORST / DT_ABORT later.
+lbm_status launch_local_from_table(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
+                                   const int *jobs, int *table, double g_const, double tol_rel, int64_t max_steps,
+                                   int32_t check_every, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                                   cudaStream_t st, double time_limit_s);
+
+}  // namespace lbm

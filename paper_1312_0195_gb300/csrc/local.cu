@@ -62,6 +62,8 @@ struct LocalArgs {
     int class_off[MAXCLASS + 1];
     int class_size[MAXCLASS];
     int *heads;               // [nclass] queue heads (zeroed before launch)
+    const int *table;         // nullptr, or a device class table (layout DT_* in lbm_internal.h) that
+                              // replaces nclass, class_off and class_size (heads then point into it)
     double omega, two_tau, omt, half_eps, gmag;
     float kf[4];              // collision constants (K_*) in FP32 and FP64, set by cell_consts()
     double kd[4];
@@ -174,18 +176,39 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
     __shared__ int s_abort;
     __shared__ unsigned s_event;              // CTA step of the next check of any slot
 
+    __shared__ int s_nclass, s_csize[MAXCLASS], s_coff[MAXCLASS + 1];
+
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned long long t0 = globaltimer();
     const int max_steps = (int)a.max_steps;
     const T hg = kc<T>(a, K_HG);
-    if (tid == 0) s_abort = 0;
+    if (tid == 0) {
+        s_abort = 0;
+        if (a.table) {      // built on the device by an earlier kernel of the same stream
+            const int nc = a.table[DT_BAD] ? 0 : a.table[DT_NCLASS];
+            s_nclass = nc;
+            for (int c = 0; c < nc; ++c) {
+                s_csize[c] = a.table[DT_SIZE + c];
+                s_coff[c] = a.table[DT_OFF + c];
+            }
+            s_coff[nc] = a.table[DT_OFF + nc];
+        } else {
+            s_nclass = a.nclass;
+            for (int c = 0; c < a.nclass; ++c) {
+                s_csize[c] = a.class_size[c];
+                s_coff[c] = a.class_off[c];
+            }
+            s_coff[a.nclass] = a.class_off[a.nclass];
+        }
+    }
+    __syncthreads();
 
-    for (int cls = 0; cls < a.nclass; ++cls) {
-        const int s = a.class_size[cls], s2 = s * s;
+    for (int cls = 0; cls < s_nclass; ++cls) {
+        const int s = s_csize[cls], s2 = s * s;
         int nslots = CMAX / s2;
         if (nslots > MAXSLOTS) nslots = MAXSLOTS;
         const int ncell = nslots * s2;
-        const int qbeg = a.class_off[cls], qn = a.class_off[cls + 1] - qbeg;
+        const int qbeg = s_coff[cls], qn = s_coff[cls + 1] - qbeg;
 
         // per-thread cell geometry for this size class, packed as slot << 12 | ly << 6 | lx
         int cgeo[CPT];
@@ -558,6 +581,57 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     return LBM_OK;
 #undef LOC_CUDA
 #undef LOC_CUDA2
+}
+
+lbm_status launch_local_from_table(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
+                                   const int *jobs, int *table, double g_const, double tol_rel, int64_t max_steps,
+                                   int32_t check_every, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                                   cudaStream_t st, double time_limit_s)
+{
+    // parameters were validated by the caller (lbm_surrogate_keff)
+    const double nu = p->nu < 0.0 ? (p->tau - 0.5) / 3.0 : p->nu;
+    LocalArgs a{};
+    a.kappa = kappa_dev;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.margin = p->margin;
+    a.leaves = reinterpret_cast<const int *>(leaves_dev);
+    a.jobs = jobs;
+    a.table = table;
+    a.heads = table + DT_HEADS;
+    a.omega = (1.0 / p->tau);
+    a.two_tau = (2.0 * p->tau);
+    a.omt = (1.0 - 2.0 * p->tau);
+    a.half_eps = (0.5 * p->eps);
+    a.gmag = g_const;
+    cell_consts(a);
+    a.eps_nu = p->eps * nu;
+    a.nu_over_g = nu / g_const;
+    a.tol = tol_rel;
+    a.check_every = check_every;
+    a.max_steps = max_steps;
+    a.keff = keff_dev;
+    a.status = status_dev;
+    a.steps = steps_dev;
+    a.worst = table + DT_WORST;
+    a.abort_flag = table + DT_ABORT;
+    a.time_limit_ns = (unsigned long long)(time_limit_s * 1e9);
+    const bool f64 = p->storage == LBM_F64;
+    auto kern = f64 ? local_keff_kernel<double> : local_keff_kernel<float>;
+    const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "local solver set-up: %s", cudaGetErrorString(e));
+    }
+    // one CTA per SM; CTAs of an empty table find no class and return at once
+    kern<<<sm_count(dev), LOCAL_THREADS, smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "local solver launch: %s", cudaGetErrorString(e));
+    count_launches(1);
+    return LBM_OK;
 }
 
 }  // namespace lbm

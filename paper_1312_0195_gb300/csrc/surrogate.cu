@@ -51,33 +51,61 @@ static const Layout LAYOUT;
 
 // ------------------------------------------------------------------ kernels
 
-// Leaf -> 32 x 32 log-K patch (replicate for s < 32, 2x2.. block means of log K
-// for s > 32), as two FP32 input planes [n][2][32][32]: log K and log2(s) / 6;
-// plus (mean, std, gradient energy) of the log-K patch. One CTA per leaf.
-__global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, const int *leaves, float *x,
-                                                   float *stats)
+// Is s a leaf size the input planes are defined for: a divisor of 32, or a multiple of 64 up to 1024.
+__host__ __device__ inline bool patch_size_ok(int s)
+{
+    return (s >= 1 && s <= IMG && IMG % s == 0) || (s >= 64 && s <= 1024 && s % 64 == 0);
+}
+
+// Leaf -> the five input planes [n][5][32][32] and (mean, std, gradient energy) of its 32 x 32
+// log-K patch. The leaf's log K is first put on a 64 x 64 plane (each cell repeated 64 / s times
+// per axis for s <= 32, the leaf itself for s = 64, means of log K over (s / 64)^2 blocks above);
+// phase plane 2 a + b holds that plane's cell (2 i + a, 2 j + b) at (i, j). Plane 4 is the
+// constant log2(s) / 6. The 32 x 32 patch the statistics describe is the mean of the four phase
+// planes (the leaf itself for s <= 32, its 2 x 2 block means for s = 64). One CTA per leaf; an
+// invalid leaf (size, or not inside the field) gets zero planes and sets *bad (may be NULL).
+__global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, int ny, const int *leaves,
+                                                   float *x, float *stats, int *bad)
 {
     const int i = blockIdx.x;
     const int x0 = leaves[3 * i], y0 = leaves[3 * i + 1], s = leaves[3 * i + 2];
+    float *xi = x + (int64_t)i * IN_PLANES * PIX;
+    const bool valid = patch_size_ok(s) && x0 >= 0 && y0 >= 0 && (int64_t)x0 + s <= nx && (int64_t)y0 + s <= ny;
+    if (!valid) {
+        for (int q = threadIdx.x; q < IN_PLANES * PIX; q += blockDim.x) xi[q] = 0.0f;
+        if (threadIdx.x < 3) stats[3 * i + threadIdx.x] = 0.0f;
+        if (threadIdx.x == 0 && bad) atomicExch(bad, 1);
+        return;
+    }
     __shared__ float p[PIX];
     __shared__ double red[3][8];
+    const float size_plane = log2f((float)s) / 6.0f;
     for (int q = threadIdx.x; q < PIX; q += blockDim.x) {
         const int py = q >> 5, px = q & 31;
-        float v;
-        if (s <= IMG) {
+        float v[4];
+        if (s <= IMG) {                        // all four phases are the same cell
             const int r = IMG / s;
-            v = logf(kappa[(int64_t)(y0 + py / r) * nx + x0 + px / r]);
+            v[0] = v[1] = v[2] = v[3] = logf(kappa[(int64_t)(y0 + py / r) * nx + x0 + px / r]);
         } else {
-            const int r = s / IMG;
-            double acc = 0.0;
-            for (int a = 0; a < r; ++a)
-                for (int b = 0; b < r; ++b)
-                    acc += (double)logf(kappa[(int64_t)(y0 + py * r + a) * nx + x0 + px * r + b]);
-            v = (float)(acc / (r * r));
+            const int r = s / 64;
+#pragma unroll
+            for (int ph = 0; ph < 4; ++ph) {
+                const int Y = 2 * py + (ph >> 1), X = 2 * px + (ph & 1);
+                if (r == 1) {
+                    v[ph] = logf(kappa[(int64_t)(y0 + Y) * nx + x0 + X]);
+                } else {
+                    double acc = 0.0;
+                    for (int a = 0; a < r; ++a)
+                        for (int b = 0; b < r; ++b)
+                            acc += (double)logf(kappa[(int64_t)(y0 + Y * r + a) * nx + x0 + X * r + b]);
+                    v[ph] = (float)(acc / (r * r));
+                }
+            }
         }
-        p[q] = v;
-        x[(int64_t)i * 2 * PIX + q] = v;
-        x[(int64_t)i * 2 * PIX + PIX + q] = log2f((float)s) / 6.0f;
+#pragma unroll
+        for (int ph = 0; ph < 4; ++ph) xi[ph * PIX + q] = v[ph];
+        xi[4 * PIX + q] = size_plane;
+        p[q] = 0.25f * ((v[0] + v[1]) + (v[2] + v[3]));
     }
     __syncthreads();
     double sm = 0.0, sq = 0.0, ge = 0.0;
@@ -108,19 +136,20 @@ __global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, 
     }
 }
 
-// FP32 [n][2][32][32] inputs (rows idx[b]) -> BF16 16-channel activation (act_at layout) with
-// channel 0 normalised as (x - shift) / scale, channel 1 as is, channels 2..15 zero.
+// FP32 input planes [n][5][32][32] (rows idx[b]) -> BF16 16-channel activation (act_at layout):
+// channels 0-3 the phase planes as (x - shift) / scale, channel 4 the size plane as is, 5-15 zero.
 __global__ void __launch_bounds__(256) input_kernel(const float *x, const int *idx, int B, float shift, float scale,
                                                    __nv_bfloat16 *out)
 {
     const int64_t total = (int64_t)B * PIX;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(t / PIX), q = (int)(t - (int64_t)b * PIX);
-        const int64_t src = (int64_t)(idx ? idx[b] : b) * 2 * PIX;
+        const int64_t src = (int64_t)(idx ? idx[b] : b) * IN_PLANES * PIX;
         uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
         __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(o);
-        ob[0] = __float2bfloat16_rn((x[src + q] - shift) / scale);
-        ob[1] = __float2bfloat16_rn(x[src + PIX + q]);
+#pragma unroll
+        for (int ph = 0; ph < 4; ++ph) ob[ph] = __float2bfloat16_rn((x[src + ph * PIX + q] - shift) / scale);
+        ob[4] = __float2bfloat16_rn(x[src + 4 * PIX + q]);
         *reinterpret_cast<uint4 *>(out + act_at(b, q, 0, CIN0)) = o[0];
         *reinterpret_cast<uint4 *>(out + act_at(b, q, 8, CIN0)) = o[1];
     }
@@ -490,14 +519,15 @@ __global__ void __launch_bounds__(256) adam_kernel(float *p, const float *g, flo
     }
 }
 
-// Sum and sum of squares of the log-K planes of x [n][2][32][32], per block (fixed order).
+// Sum and sum of squares of the log-K phase planes of x [n][5][32][32], per block (fixed order).
 __global__ void __launch_bounds__(256) input_moments_kernel(const float *x, int n, double *part)
 {
     double s = 0.0, q = 0.0;
-    const int64_t total = (int64_t)n * PIX;
+    const int64_t per = 4 * PIX;
+    const int64_t total = (int64_t)n * per;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / PIX, pq = t - i * PIX;
-        const double v = x[i * 2 * PIX + pq];
+        const int64_t i = t / per, pq = t - i * per;
+        const double v = x[i * IN_PLANES * PIX + pq];
         s += v;
         q += v * v;
     }
@@ -513,40 +543,45 @@ __global__ void __launch_bounds__(256) input_moments_kernel(const float *x, int 
     }
 }
 
-// Per-patch target base for the two components, cw[i] = (c_xx, w_xx, c_yy, w_yy): the network learns
-// (log K* - c) / w. Mode 0: c = mean log K of the patch, w = 1. Modes 1 and 2 centre on the
-// layered-medium bounds of the 32 x 32 plane (for flow along x, rows as parallel series tubes give
-// A_y(H_x K) below and columns as series parallel slabs give H_x(A_y K) above; the same with x and y
-// swapped for K*_yy): c = the midpoint of the log bounds, and w = 1 (mode 1) or half the log width,
-// at least 0.05 (mode 2). One block per patch, FP64 sums in a fixed order.
+// Per-leaf target base for the two components, cw[i] = (c_xx, w_xx, c_yy, w_yy): the network learns
+// (log K* - c) / w. It is computed on the 64 x 64 log-K plane the four phase planes form (the
+// leaf itself for 64 cells, the leaf repeated for smaller ones). Mode 0: c = mean log K, w = 1.
+// Modes 1 and 2 centre on the layered-medium bounds (for flow along x, rows as parallel series
+// tubes give A_y(H_x K) below and columns as series parallel slabs give H_x(A_y K) above; the same
+// with x and y swapped for K*_yy): c = the midpoint of the log bounds, and w = 1 (mode 1) or half
+// the log width, at least 0.05 (mode 2). One block per leaf, FP64 sums in a fixed order.
 __global__ void __launch_bounds__(256) patch_base_kernel(const float *x, int n, int mode, float4 *cw)
 {
-    __shared__ double K[IMG][IMG + 1];
-    __shared__ double rowK[IMG], rowI[IMG], colK[IMG], colI[IMG];
+    constexpr int F = 64;                      // side of the full plane
+    __shared__ double K[F][F + 1];
+    __shared__ double rowK[F], rowI[F], colK[F], colI[F];
     __shared__ double lsum;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        const float *p = x + (int64_t)i * 2 * PIX;
-        for (int q = threadIdx.x; q < PIX; q += 256) K[q / IMG][q % IMG] = (double)p[q];   // log K for now
+        const float *xi = x + (int64_t)i * IN_PLANES * PIX;
+        for (int q = threadIdx.x; q < F * F; q += 256) {
+            const int Y = q / F, X = q % F;
+            K[Y][X] = (double)xi[((Y & 1) * 2 + (X & 1)) * PIX + (Y >> 1) * IMG + (X >> 1)];   // log K for now
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             double a = 0.0;
-            for (int r = 0; r < IMG; ++r)
-                for (int c = 0; c < IMG; ++c) a += K[r][c];
+            for (int r = 0; r < F; ++r)
+                for (int c = 0; c < F; ++c) a += K[r][c];
             lsum = a;
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < PIX; q += 256) K[q / IMG][q % IMG] = exp(K[q / IMG][q % IMG]);
+        for (int q = threadIdx.x; q < F * F; q += 256) K[q / F][q % F] = exp(K[q / F][q % F]);
         __syncthreads();
-        if (threadIdx.x < IMG) {
+        if (threadIdx.x < F) {
             const int r = threadIdx.x;
             double sk = 0.0, si = 0.0;
-            for (int c = 0; c < IMG; ++c) { sk += K[r][c]; si += 1.0 / K[r][c]; }
+            for (int c = 0; c < F; ++c) { sk += K[r][c]; si += 1.0 / K[r][c]; }
             rowK[r] = sk;
             rowI[r] = si;
-        } else if (threadIdx.x < 2 * IMG) {
-            const int c = threadIdx.x - IMG;
+        } else if (threadIdx.x < 2 * F) {
+            const int c = threadIdx.x - F;
             double sk = 0.0, si = 0.0;
-            for (int r = 0; r < IMG; ++r) { sk += K[r][c]; si += 1.0 / K[r][c]; }
+            for (int r = 0; r < F; ++r) { sk += K[r][c]; si += 1.0 / K[r][c]; }
             colK[c] = sk;
             colI[c] = si;
         }
@@ -554,18 +589,18 @@ __global__ void __launch_bounds__(256) patch_base_kernel(const float *x, int n, 
         if (threadIdx.x == 0) {
             float4 o;
             if (mode == 0) {
-                const float m = (float)(lsum / PIX);
+                const float m = (float)(lsum / (F * F));
                 o = make_float4(m, 1.0f, m, 1.0f);
             } else {
                 double ahx = 0.0, hax = 0.0, ahy = 0.0, hay = 0.0;
-                for (int k = 0; k < IMG; ++k) {
-                    ahx += IMG / rowI[k];          // H_x of row k
-                    hax += IMG / colK[k];          // 1 / A_y of column k
-                    ahy += IMG / colI[k];          // H_y of column k
-                    hay += IMG / rowK[k];          // 1 / A_x of row k
+                for (int k = 0; k < F; ++k) {
+                    ahx += F / rowI[k];            // H_x of row k
+                    hax += F / colK[k];            // 1 / A_y of column k
+                    ahy += F / colI[k];            // H_y of column k
+                    hay += F / rowK[k];            // 1 / A_x of row k
                 }
-                const double lox = log(ahx / IMG), hix = log(IMG / hax);
-                const double loy = log(ahy / IMG), hiy = log(IMG / hay);
+                const double lox = log(ahx / F), hix = log(F / hax);
+                const double loy = log(ahy / F), hiy = log(F / hay);
                 const float wx = mode == 2 ? (float)fmax(0.5 * (hix - lox), 0.05) : 1.0f;
                 const float wy = mode == 2 ? (float)fmax(0.5 * (hiy - loy), 0.05) : 1.0f;
                 o = make_float4((float)(0.5 * (lox + hix)), wx, (float)(0.5 * (loy + hiy)), wy);
@@ -709,7 +744,7 @@ cudaError_t wgrad(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, flo
 {
     switch (l) {
     case 0:
-        wgrad_kernel<32, 16, 2><<<dim3(B * 9), 256, 0, st>>>(in, dout, part, bpart);
+        wgrad_kernel<32, 16, IN_PLANES><<<dim3(B * 9), 256, 0, st>>>(in, dout, part, bpart);
         *nparts = B;
         return cudaGetLastError();
     case 1: return launch_wgrad_mma<32, 32>(in, dout, part, bpart, B, nparts, st);
@@ -759,6 +794,15 @@ struct lbm_surrogate {
     float y_mean[2] = {0.0f, 0.0f}, y_std[2] = {1.0f, 1.0f};
     float stat_lo[3] = {-1e30f, -1e30f, -1e30f}, stat_hi[3] = {1e30f, 1e30f, 1e30f};
     int target_mode = 2;          // patch_base_kernel: 0 mean log K, 1 bound midpoint, 2 midpoint and width
+    float gate_spread[7] = {0.03f, 0.03f, 0.03f, 0.03f, 0.03f, 0.03f, 0.03f};   // per log2 leaf size 0..6
+    // buffers of lbm_surrogate_keff: one chunk of leaves, the job list and the queue table
+    int kcap = 0;
+    float *kx = nullptr, *kstats = nullptr, *ky = nullptr;
+    float4 *kcw = nullptr;
+    int64_t jcap = 0;
+    int *jobs = nullptr, *fb = nullptr, *stt = nullptr, *table = nullptr;
+    lbm_leaf *ul = nullptr;       // uniform leaves of lbm_upscale
+    int64_t ulcap = 0;
     // work buffers sized for `cap` images
     int cap = 0;
     __nv_bfloat16 *act[NLAYER + 1] = {};
@@ -949,6 +993,8 @@ lbm_status lbm_surrogate_destroy(lbm_surrogate *s)
     if (!s) return LBM_OK;
     free_work(s);
     cudaFree(s->params); cudaFree(s->adam_m); cudaFree(s->adam_v); cudaFree(s->err);
+    cudaFree(s->kx); cudaFree(s->kstats); cudaFree(s->ky); cudaFree(s->kcw);
+    cudaFree(s->jobs); cudaFree(s->fb); cudaFree(s->stt); cudaFree(s->table); cudaFree(s->ul);
     for (int l = 0; l < NLAYER; ++l) { cudaFree(s->wf[l]); cudaFree(s->wb[l]); }
     cudaGetLastError();
     delete s;
@@ -1007,11 +1053,12 @@ lbm_status lbm_patches(const float *kappa_dev, int32_t nx, int32_t ny, const lbm
     SUR_CUDA(cudaStreamSynchronize(st));
     for (int i = 0; i < n; ++i) {
         const int s = lv[i].size;
-        const bool ok_size = (s >= 1 && s <= 32 && 32 % s == 0) || (s > 32 && s % 32 == 0 && s <= 1024);
-        if (!ok_size || lv[i].x0 < 0 || lv[i].y0 < 0 || (int64_t)lv[i].x0 + s > nx || (int64_t)lv[i].y0 + s > ny)
-            return fail(LBM_EINVAL, "leaf %d: size %d must divide 32 or be a multiple of 32, inside the field", i, s);
+        if (!patch_size_ok(s) || lv[i].x0 < 0 || lv[i].y0 < 0 || (int64_t)lv[i].x0 + s > nx || (int64_t)lv[i].y0 + s > ny)
+            return fail(LBM_EINVAL, "leaf %d: size %d must divide 32 or be a multiple of 64 up to 1024, inside the field",
+                        i, s);
     }
-    patch_kernel<<<n, 256, 0, st>>>(kappa_dev, nx, reinterpret_cast<const int *>(leaves_dev), x_dev, stats_dev);
+    patch_kernel<<<n, 256, 0, st>>>(kappa_dev, nx, ny, reinterpret_cast<const int *>(leaves_dev), x_dev, stats_dev,
+                                    nullptr);
     SUR_CUDA(cudaGetLastError());
     count_launches(1);
     SUR_CUDA(cudaStreamSynchronize(st));
@@ -1057,7 +1104,7 @@ lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n
         SUR_CUDA(pack_model(s, m, st));
         for (int b0 = 0; b0 < n; b0 += B) {
             const int nb = n - b0 < B ? n - b0 : B;
-            input_kernel<<<nblk((int64_t)nb * PIX), 256, 0, st>>>(x_dev + (int64_t)b0 * 2 * PIX, nullptr, nb,
+            input_kernel<<<nblk((int64_t)nb * PIX), 256, 0, st>>>(x_dev + (int64_t)b0 * IN_PLANES * PIX, nullptr, nb,
                                                                  s->in_shift, s->in_scale, s->act[0]);
             count_launches(1);
             SUR_CUDA(forward(s, m, nb, st));
@@ -1076,7 +1123,7 @@ lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n
     return r;
 }
 
-// Trains every model of the ensemble on n samples: inputs x_dev [n][2][32][32]
+// Trains every model of the ensemble on n samples: inputs x_dev [n][5][32][32]
 // (lbm_patches), targets y_dev [n][2] = log K*_xx, log K*_yy. The networks learn
 // (log K* - c) / w, standardised, with the per-patch base (c, w) of the target
 // mode (patch_base_kernel; mode 2 unless set before training). Sets the input and target
@@ -1232,116 +1279,285 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
 namespace lbm {
 namespace sur {
 
-// Ensemble mean / spread per block and the range test of the patch statistics:
-// accepted blocks get K* = diag(exp(mean log K*_xx), exp(mean log K*_yy)); the
-// others are flagged for local LBM.
-__global__ void gate_kernel(const float *y, int nmodels, int n, const float *stats, float lo0, float hi0, float lo1,
-                            float hi1, float lo2, float hi2, float max_sd, double *keff, int *fallback)
+constexpr int KEFF_CHUNK = 32768;        // leaves per pass of patches, inference and gate
+
+// log2 of a leaf size the surrogate path takes (a power of two from 1 to 64), else -1
+__host__ __device__ inline int size_class(int s)
+{
+    for (int c = 0; c <= 6; ++c)
+        if (s == (1 << c)) return c;
+    return -1;
+}
+
+struct GateArgs {
+    float lo[3], hi[3];           // accepted range of each patch statistic (bounds included)
+    double thr[7];                // ln(1 + spread_max) per log2 leaf size
+    int margin;                   // oversampling margin of the fallback local problems
+    int smax;                     // largest patch the local solver holds (64 FP32, 45 FP64)
+};
+
+// The gate for leaves [base, base + n): the members' mean and sample standard deviation (two
+// passes, FP64) of log K*_xx and log K*_yy from y [nmodels][n][2], and the range test of the
+// patch statistics. An accepted leaf gets K* = diag(exp(mean xx), exp(mean yy)) and fallback 0;
+// a rejected one gets fallback 1 and is counted under its patch size (size + 2 margin) in the
+// queue table, for the local solver. A leaf size the path does not take sets DT_BAD.
+__global__ void gate_kernel(const float *y, int nmodels, int n, int base, const int *leaves, const float *stats,
+                            GateArgs g, double *keff, int *fallback, int *table)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double m[2] = {0.0, 0.0}, q[2] = {0.0, 0.0};
-        for (int k = 0; k < nmodels; ++k)
-            for (int c = 0; c < 2; ++c) {
-                const double v = y[((int64_t)k * n + i) * 2 + c];
-                m[c] += v;
-                q[c] += v * v;
-            }
-        bool ok = true;
-        for (int c = 0; c < 2; ++c) {
-            m[c] /= nmodels;
-            const double var = nmodels > 1 ? (q[c] - nmodels * m[c] * m[c]) / (nmodels - 1) : 0.0;
-            if (!(sqrt(var > 0.0 ? var : 0.0) <= max_sd) || !isfinite(m[c])) ok = false;
+        const int gi = base + i;
+        const int sz = leaves[3 * gi + 2], c = size_class(sz), ps = sz + 2 * g.margin;
+        if (c < 0 || ps > g.smax) {
+            atomicExch(&table[DT_BAD], 1);
+            fallback[gi] = 1;
+            continue;
         }
-        const float s0 = stats[3 * i], s1 = stats[3 * i + 1], s2 = stats[3 * i + 2];
-        if (!(s0 >= lo0 && s0 <= hi0 && s1 >= lo1 && s1 <= hi1 && s2 >= lo2 && s2 <= hi2)) ok = false;
-        fallback[i] = ok ? 0 : 1;
+        bool ok = true;
+        double m[2];
+        for (int k = 0; k < 2; ++k) {
+            double a = 0.0;
+            for (int j = 0; j < nmodels; ++j) a += (double)y[((int64_t)j * n + i) * 2 + k];
+            m[k] = a / nmodels;
+            double q = 0.0;
+            for (int j = 0; j < nmodels; ++j) {
+                const double d = (double)y[((int64_t)j * n + i) * 2 + k] - m[k];
+                q += d * d;
+            }
+            const double sd = nmodels > 1 ? sqrt(q / (nmodels - 1)) : 0.0;
+            if (!(sd <= g.thr[c]) || !isfinite(m[k])) ok = false;
+        }
+        for (int k = 0; k < 3; ++k) {
+            const float v = stats[3 * (int64_t)i + k];
+            if (!(v >= g.lo[k] && v <= g.hi[k])) ok = false;
+        }
+        fallback[gi] = ok ? 0 : 1;
         if (ok) {
-            keff[4 * (int64_t)i] = exp(m[0]);
-            keff[4 * (int64_t)i + 1] = 0.0;
-            keff[4 * (int64_t)i + 2] = 0.0;
-            keff[4 * (int64_t)i + 3] = exp(m[1]);
+            keff[4 * (int64_t)gi] = exp(m[0]);
+            keff[4 * (int64_t)gi + 1] = 0.0;
+            keff[4 * (int64_t)gi + 2] = 0.0;
+            keff[4 * (int64_t)gi + 3] = exp(m[1]);
+        } else {
+            atomicAdd(&table[DT_COUNT + ps], 1);
         }
     }
 }
 
-__global__ void scatter_keff_kernel(const double *src, const int *ids, int nf, double *dst)
+// One thread: the classes of the rejected leaves in descending patch size, the offsets of their
+// job ranges and the scatter cursors; nothing if an invalid leaf was seen.
+__global__ void queue_table_kernel(int *table)
 {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x)
-        for (int c = 0; c < 4; ++c) dst[4 * (int64_t)ids[j] + c] = src[4 * (int64_t)j + c];
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int nclass = 0, off = 0;
+    if (!table[DT_BAD])
+        for (int sz = 64; sz >= 1; --sz) {
+            const int k = table[DT_COUNT + sz];
+            if (k == 0) continue;
+            table[DT_SIZE + nclass] = sz;
+            table[DT_OFF + nclass] = off;
+            table[DT_CURSOR + sz] = off;
+            off += 2 * k;
+            ++nclass;
+        }
+    table[DT_OFF + nclass] = off;
+    table[DT_NCLASS] = nclass;
+    table[DT_NFALLBACK] = off / 2;
+}
+
+// Both drives of every rejected leaf into its class's job range (order within a class is free:
+// each job's result depends only on its own leaf).
+__global__ void queue_scatter_kernel(const int *leaves, int n, const int *fallback, int margin, int smax, int *table,
+                                     int *jobs)
+{
+    if (table[DT_BAD]) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!fallback[i]) continue;
+        const int ps = leaves[3 * i + 2] + 2 * margin;
+        const int pos = atomicAdd(&table[DT_CURSOR + ps], 2);
+        jobs[pos] = 2 * i;
+        jobs[pos + 1] = 2 * i + 1;
+    }
+}
+
+__global__ void uniform_leaves_kernel(int cx, int cy, int block, int *leaves)
+{
+    const int64_t n = (int64_t)cx * cy;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        leaves[3 * i] = (int)(i % cx) * block;
+        leaves[3 * i + 1] = (int)(i / cx) * block;
+        leaves[3 * i + 2] = block;
+    }
+}
+
+static lbm_status ensure_keff_work(lbm_surrogate *s, int chunk, int64_t n)
+{
+    cudaError_t e = cudaSuccess;
+    if (chunk > s->kcap) {
+        cudaFree(s->kx); cudaFree(s->kstats); cudaFree(s->ky); cudaFree(s->kcw);
+        s->kx = s->kstats = s->ky = nullptr;
+        s->kcw = nullptr;
+        s->kcap = 0;
+        e = cudaMalloc(&s->kx, sizeof(float) * (size_t)chunk * IN_PLANES * PIX);
+        if (e == cudaSuccess) e = cudaMalloc(&s->kstats, sizeof(float) * (size_t)chunk * 3);
+        if (e == cudaSuccess) e = cudaMalloc(&s->ky, sizeof(float) * (size_t)chunk * 2 * s->nmodels);
+        if (e == cudaSuccess) e = cudaMalloc(&s->kcw, sizeof(float4) * (size_t)chunk);
+        if (e == cudaSuccess) s->kcap = chunk;
+    }
+    if (e == cudaSuccess && n > s->jcap) {
+        cudaFree(s->jobs); cudaFree(s->fb); cudaFree(s->stt);
+        s->jobs = s->fb = s->stt = nullptr;
+        s->jcap = 0;
+        e = cudaMalloc(&s->jobs, sizeof(int) * 2 * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&s->fb, sizeof(int) * (size_t)n);
+        if (e == cudaSuccess) e = cudaMalloc(&s->stt, sizeof(int) * (size_t)n);
+        if (e == cudaSuccess) s->jcap = n;
+    }
+    if (e == cudaSuccess && !s->table) e = cudaMalloc(&s->table, sizeof(int) * DT_INTS);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "surrogate K* buffers for %lld leaves: %s", (long long)n, cudaGetErrorString(e));
+    }
+    return LBM_OK;
 }
 
 }  // namespace sur
+}  // namespace lbm
 
-// Upscaling with the ensemble and the LBM fallback (see lbm_upscale in lbm.h).
+extern "C" {
+
+lbm_status lbm_surrogate_set_gate(lbm_surrogate *s, const float spread_by_log2size[7])
+{
+    if (!s || !spread_by_log2size) return fail(LBM_EINVAL, "bad surrogate or gate");
+    for (int c = 0; c < 7; ++c)
+        if (!(spread_by_log2size[c] > 0.0f)) return fail(LBM_EINVAL, "gate spreads must be > 0");
+    for (int c = 0; c < 7; ++c) s->gate_spread[c] = spread_by_log2size[c];
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_get_gate(const lbm_surrogate *s, float spread_by_log2size[7])
+{
+    if (!s || !spread_by_log2size) return fail(LBM_EINVAL, "bad surrogate or gate");
+    for (int c = 0; c < 7; ++c) spread_by_log2size[c] = s->gate_spread[c];
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_keff(lbm_surrogate *s, const lbm_params *p, const float *kappa_dev,
+                              const lbm_leaf *leaves_dev, int32_t n, double spread_max, double g_const,
+                              double tol_rel, int64_t max_steps, double *keff_dev, int32_t *fallback_dev,
+                              int32_t *status_dev, int32_t *n_fallback, void *cuda_stream)
+{
+    using namespace lbm::sur;
+    if (!s || !p) return fail(LBM_EINVAL, "surrogate or params is NULL");
+    if (p->nx < 1 || p->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
+    if (!std::isfinite(p->tau) || p->tau < 0.5) return fail(LBM_EINVAL, "tau must be finite and >= 0.5");
+    if (!std::isfinite(p->nu) || !std::isfinite(p->eps) || p->eps < 0.0)
+        return fail(LBM_EINVAL, "nu must be finite and eps finite and >= 0");
+    if (p->margin < 0 || p->margin > 32 || p->margin >= p->nx || p->margin >= p->ny)
+        return fail(LBM_EINVAL, "margin %d outside [0, 32] or not below the field size", p->margin);
+    if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+    if (!(spread_max >= 0.0)) return fail(LBM_EINVAL, "spread_max must be >= 0 (0: the ensemble's per-size gate)");
+    if (!std::isfinite(g_const) || g_const == 0.0) return fail(LBM_EINVAL, "g_const must be finite and non-zero");
+    if (!std::isfinite(tol_rel) || tol_rel < 0.0) return fail(LBM_EINVAL, "tol_rel must be finite and >= 0");
+    if (max_steps < 1 || max_steps >= (int64_t)1 << 31) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31 - 1]");
+    if (n == 0) {
+        if (n_fallback) *n_fallback = 0;
+        return LBM_OK;
+    }
+    if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(keff_dev) ||
+        (fallback_dev && !is_device_ptr(fallback_dev)) || (status_dev && !is_device_ptr(status_dev)))
+        return fail(LBM_EINVAL, "kappa, leaves, keff (and fallback, status) must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int chunk = n < KEFF_CHUNK ? n : KEFF_CHUNK;
+    lbm_status r = ensure_keff_work(s, chunk, n);
+    if (r == LBM_OK) r = ensure_work(s, chunk < 2048 ? chunk : 2048);
+    if (r != LBM_OK) return r;
+    int *fb = fallback_dev ? fallback_dev : s->fb;
+    int *stt = status_dev ? status_dev : s->stt;
+    const int *lv = reinterpret_cast<const int *>(leaves_dev);
+    GateArgs ga;
+    for (int k = 0; k < 3; ++k) { ga.lo[k] = s->stat_lo[k]; ga.hi[k] = s->stat_hi[k]; }
+    for (int c = 0; c < 7; ++c) ga.thr[c] = std::log1p(spread_max > 0.0 ? spread_max : (double)s->gate_spread[c]);
+    ga.margin = p->margin;
+    ga.smax = p->storage == LBM_F64 ? 45 : 64;
+    SUR_CUDA(cudaMemsetAsync(s->table, 0, sizeof(int) * DT_INTS, st));
+    SUR_CUDA(cudaMemsetAsync(stt, 0, sizeof(int32_t) * n, st));
+    SUR_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), st));
+    const int B = chunk < 2048 ? chunk : 2048;
+    for (int b0 = 0; b0 < n; b0 += chunk) {
+        const int nc = n - b0 < chunk ? n - b0 : chunk;
+        patch_kernel<<<nc, 256, 0, st>>>(kappa_dev, p->nx, p->ny, lv + 3 * (int64_t)b0, s->kx, s->kstats,
+                                         s->table + DT_BAD);
+        count_launches(1);
+        for (int m = 0; m < s->nmodels; ++m) {
+            SUR_CUDA(pack_model(s, m, st));
+            for (int c0 = 0; c0 < nc; c0 += B) {
+                const int nb = nc - c0 < B ? nc - c0 : B;
+                input_kernel<<<nblk((int64_t)nb * PIX), 256, 0, st>>>(s->kx + (int64_t)c0 * IN_PLANES * PIX, nullptr,
+                                                                     nb, s->in_shift, s->in_scale, s->act[0]);
+                count_launches(1);
+                SUR_CUDA(forward(s, m, nb, st));
+                SUR_CUDA(cudaMemcpyAsync(s->ky + ((int64_t)m * nc + c0) * 2, s->y, sizeof(float) * 2 * nb,
+                                         cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        patch_base_kernel<<<nc < 65535 ? nc : 65535, 256, 0, st>>>(s->kx, nc, s->target_mode, s->kcw);
+        destandardise_kernel<<<nblk((int64_t)s->nmodels * nc * 2), 256, 0, st>>>(
+            s->ky, nc, s->nmodels, s->kcw, s->y_mean[0], s->y_std[0], s->y_mean[1], s->y_std[1]);
+        gate_kernel<<<nblk(nc), 256, 0, st>>>(s->ky, s->nmodels, nc, b0, lv, s->kstats, ga, keff_dev, fb, s->table);
+        count_launches(3);
+        SUR_CUDA(cudaGetLastError());
+    }
+    queue_table_kernel<<<1, 32, 0, st>>>(s->table);
+    queue_scatter_kernel<<<nblk(n), 256, 0, st>>>(lv, n, fb, p->margin, ga.smax, s->table, s->jobs);
+    count_launches(2);
+    SUR_CUDA(cudaGetLastError());
+    r = launch_local_from_table(p, kappa_dev, leaves_dev, s->jobs, s->table, g_const, tol_rel, max_steps, 64, keff_dev,
+                                stt, nullptr, st, local_time_limit());
+    if (r != LBM_OK) return r;
+    int h[DT_INTS - DT_BAD];
+    int herr = 0;
+    SUR_CUDA(cudaMemcpyAsync(h, s->table + DT_BAD, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    SUR_CUDA(cudaMemcpyAsync(&herr, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SUR_CUDA(cudaStreamSynchronize(st));
+    if (h[0]) return fail(LBM_EINVAL, "a leaf is not a power of two from 1 to %d cells (with margin) inside the field",
+                          ga.smax);
+    if (herr) return fail(LBM_ETIMEOUT, "surrogate: a tensor-core wait gave up (results not valid)");
+    if (n_fallback) *n_fallback = h[DT_NFALLBACK - DT_BAD];
+    if (h[DT_ABORT - DT_BAD] || h[DT_WORST - DT_BAD] == LBM_ETIMEOUT)
+        return fail(LBM_ETIMEOUT, "local problems exceeded the time limit; unfinished leaves carry LBM_ETIMEOUT");
+    if (h[DT_WORST - DT_BAD] == LBM_ENOTCONV)
+        return fail(LBM_ENOTCONV, "some fallback leaves did not meet the tolerance within max_steps (status per leaf)");
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace lbm {
+
+// Upscaling with the ensemble and the LBM fallback (see lbm_upscale in lbm.h): one leaf per block.
 lbm_status upscale_with_surrogate(const lbm_params *p, const float *kappa_dev, int32_t block, lbm_surrogate *s,
                                   double spread_max, double g_const, double tol_rel, int64_t max_steps,
                                   double *keff_dev, int32_t *n_fallback, void *cuda_stream)
 {
     using namespace sur;
-    if (!(spread_max > 0.0)) return fail(LBM_EINVAL, "spread_max must be > 0");
-    if (!is_device_ptr(kappa_dev) || !is_device_ptr(keff_dev)) return fail(LBM_EINVAL, "kappa and keff must be device pointers");
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int cx = p->nx / block, cy = p->ny / block;
     const int64_t n64 = (int64_t)cx * cy;
     if (n64 > (int64_t)1 << 26) return fail(LBM_EINVAL, "too many blocks for the surrogate path");
-    const int n = (int)n64;
-    std::vector<lbm_leaf> lv((size_t)n);
-    for (int J = 0; J < cy; ++J)
-        for (int I = 0; I < cx; ++I) lv[(size_t)J * cx + I] = lbm_leaf{I * block, J * block, block};
-    lbm_leaf *d_leaves = nullptr;
-    float *d_x = nullptr, *d_stats = nullptr, *d_y = nullptr;
-    int *d_fb = nullptr, *d_ids = nullptr;
-    double *d_kf = nullptr;
-    int32_t *d_status = nullptr;
-    auto cleanup = [&]() {
-        cudaFree(d_leaves); cudaFree(d_x); cudaFree(d_stats); cudaFree(d_y); cudaFree(d_fb); cudaFree(d_ids);
-        cudaFree(d_kf); cudaFree(d_status);
-        cudaGetLastError();
-    };
-    cudaError_t e = cudaMalloc(&d_leaves, sizeof(lbm_leaf) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_x, sizeof(float) * (size_t)n * 2 * PIX);
-    if (e == cudaSuccess) e = cudaMalloc(&d_stats, sizeof(float) * (size_t)n * 3);
-    if (e == cudaSuccess) e = cudaMalloc(&d_y, sizeof(float) * (size_t)n * 2 * s->nmodels);
-    if (e == cudaSuccess) e = cudaMalloc(&d_fb, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_leaves, lv.data(), sizeof(lbm_leaf) * n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-        cleanup();
-        return fail(LBM_ENOMEM, "surrogate upscaling buffers: %s", cudaGetErrorString(e));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (n64 > s->ulcap) {
+        cudaFree(s->ul);
+        s->ul = nullptr;
+        s->ulcap = 0;
+        const cudaError_t e = cudaMalloc(&s->ul, sizeof(lbm_leaf) * (size_t)n64);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, "block list: %s", cudaGetErrorString(e));
+        }
+        s->ulcap = n64;
     }
-    lbm_status r = lbm_patches(kappa_dev, p->nx, p->ny, d_leaves, n, d_x, d_stats, cuda_stream);
-    if (r == LBM_OK) r = lbm_surrogate_predict(s, d_x, n, d_y, cuda_stream);
-    if (r != LBM_OK) { cleanup(); return r; }
-    gate_kernel<<<nblk(n), 256, 0, st>>>(d_y, s->nmodels, n, d_stats, s->stat_lo[0], s->stat_hi[0], s->stat_lo[1],
-                                         s->stat_hi[1], s->stat_lo[2], s->stat_hi[2],
-                                         (float)std::log1p(spread_max), keff_dev, d_fb);
+    uniform_leaves_kernel<<<nblk(n64), 256, 0, st>>>(cx, cy, block, reinterpret_cast<int *>(s->ul));
     count_launches(1);
-    std::vector<int> fb((size_t)n);
-    e = cudaMemcpyAsync(fb.data(), d_fb, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { cleanup(); return fail(LBM_ECUDA, "gate: %s", cudaGetErrorString(e)); }
-    std::vector<int> ids;
-    std::vector<lbm_leaf> fl;
-    for (int i = 0; i < n; ++i)
-        if (fb[i]) { ids.push_back(i); fl.push_back(lv[i]); }
-    const int nf = (int)ids.size();
-    if (n_fallback) *n_fallback = nf;
-    if (nf == 0) { cleanup(); return LBM_OK; }
-    e = cudaMalloc(&d_ids, sizeof(int) * nf);
-    if (e == cudaSuccess) e = cudaMalloc(&d_kf, sizeof(double) * 4 * nf);
-    if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int32_t) * nf);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ids, ids.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_leaves, fl.data(), sizeof(lbm_leaf) * nf, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) { cleanup(); return fail(LBM_ENOMEM, "fallback buffers: %s", cudaGetErrorString(e)); }
-    r = local_keff_impl(p, kappa_dev, d_leaves, nf, g_const, tol_rel, max_steps, 64, 1, d_kf, d_status, nullptr,
-                        cuda_stream, local_time_limit());
-    if (r == LBM_OK || r == LBM_ENOTCONV) {
-        scatter_keff_kernel<<<nblk(nf), 256, 0, st>>>(d_kf, d_ids, nf, keff_dev);
-        count_launches(1);
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) r = fail(LBM_ECUDA, "scatter: %s", cudaGetErrorString(e));
-    }
-    cleanup();
-    return r;
+    return lbm_surrogate_keff(s, p, kappa_dev, s->ul, (int32_t)n64, spread_max, g_const, tol_rel, max_steps, keff_dev,
+                              nullptr, nullptr, n_fallback, cuda_stream);
 }
 
 }  // namespace lbm

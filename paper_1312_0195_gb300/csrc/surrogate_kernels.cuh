@@ -3,9 +3,11 @@
 // small CNN predicts log K*_xx and log K*_yy from the subdomain's permeability
 // patch and local LBM remains the fallback and the arbiter of its error).
 //
-// Network: six 3x3 'same' convolutions 2(->16 padded) -> 32 -> 32 -> 64 -> 64 ->
+// Network: six 3x3 'same' convolutions 5(->16 padded) -> 32 -> 32 -> 64 -> 64 ->
 // 64 -> 64 with ReLU, global average pooling over the 32 x 32 patch, a linear
-// head to 2 outputs. Activations are BF16 in channel-group planes
+// head to 2 outputs. The five input planes are the leaf's log K on a 64 x 64
+// plane split into four 32 x 32 phase planes by row and column parity (so a
+// 64-cell leaf enters at full resolution) and the constant log2(size) / 6. Activations are BF16 in channel-group planes
 // [B][C/8][32][32][8] (act_at below); FP32 master weights; accumulation in FP32.
 //
 //  * conv3x3_tc_kernel: implicit GEMM on the tensor cores (tcgen05, TMEM, TMA)
@@ -37,9 +39,10 @@ namespace sur {
 constexpr int IMG = 32;                  // patch side
 constexpr int PIX = IMG * IMG;           // pixels per patch
 constexpr int NLAYER = 6;
-constexpr int CIN0 = 16;                 // padded input planes of layer 0 (2 used)
+constexpr int IN_PLANES = 5;             // four phase planes of log K, the size plane
+constexpr int CIN0 = 16;                 // padded input planes of layer 0 (5 used)
 __host__ __device__ constexpr int cin_p(int l) { return l == 0 ? 16 : (l <= 2 ? 32 : 64); }
-__host__ __device__ constexpr int cin_real(int l) { return l == 0 ? 2 : (l <= 2 ? 32 : 64); }
+__host__ __device__ constexpr int cin_real(int l) { return l == 0 ? IN_PLANES : (l <= 2 ? 32 : 64); }
 __host__ __device__ constexpr int cout_of(int l) { return l <= 1 ? 32 : 64; }
 
 enum Epi { EPI_BIAS_RELU = 0, EPI_MASK = 1 };

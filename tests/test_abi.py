@@ -130,3 +130,15 @@ def test_3d_host_side_validation(lib):
     assert lib.lbm3d_upscale(C.byref(p), None, 3, 1e-6, 1e-8, 1000, None, C.byref(nnc), None) == 1   # 8 % 3
     assert nnc.value == 0
     assert lib.lbm3d_upscale(C.byref(p), None, 4, 1e-6, 1e-8, 1000, None, None, None) == 1           # NULL keff
+
+
+def test_surrogate_keff_rejects_bad_arguments_on_the_host(lib):
+    """lbm_surrogate_keff with no ensemble, no params or a negative spread returns LBM_EINVAL
+    before any device work."""
+    p = _params()
+    nfb = C.c_int32(-1)
+    assert lib.lbm_surrogate_keff(None, C.byref(p), None, None, 4, 0.03, 1e-6, 0.0, 10, None, None, None,
+                                  C.byref(nfb), None) == 1
+    assert lib.lbm_surrogate_keff(C.c_void_p(8), None, None, None, 4, 0.03, 1e-6, 0.0, 10, None, None, None,
+                                  C.byref(nfb), None) == 1
+    assert lib.lbm_surrogate_set_gate(None, None) == 1 and lib.lbm_surrogate_get_gate(None, None) == 1

@@ -283,8 +283,9 @@ def test_local_keff3_margin_limits_are_rejected():
 
 def test_d3q19_fp16_storage_error_is_bounded():
     """FP16 scaled storage on the D3Q19 grid keeps 11 bits per population; in this Darcy-like
-    regime the density deviations dominate every population, so u is resolved to a few percent
-    (as on the D2Q9 grid). The error is reported."""
+    regime the density deviations dominate every population. On this 12 x 16 x 40 box the
+    error is measured at 1.199e-3 relative L2 (GB300, bit-reproducible); the test holds it to
+    10 % above that."""
     kap = _field(12, 16, 40, seed=64)
     args = (kap, 1.0, 1.0 / 6.0, 1.0, (1e-6, 0.0, 0.0), 1500)
     (r, u, v, w), mean = gpu3(*args, storage=1)
@@ -292,8 +293,9 @@ def test_d3q19_fp16_storage_error_is_bounded():
     num = np.sqrt(((u - uo) ** 2 + (v - vo) ** 2 + (w - wo) ** 2).sum())
     err = num / np.sqrt((uo ** 2 + vo ** 2 + wo ** 2).sum())
     print(f"D3Q19 FP16 storage rel L2 error on u: {err:.3e}")
-    assert err < 5e-2
-    assert abs(mean[0] - mo[0]) <= 5e-2 * abs(mo[0])
+    print(f"D3Q19 FP16 storage rel error of the mean u_x: {abs(mean[0] - mo[0]) / abs(mo[0]):.3e}")
+    assert err < 1.1 * 1.199e-3
+    assert abs(mean[0] - mo[0]) <= 3e-3 * abs(mo[0])
     np.testing.assert_allclose(r, ro, rtol=0, atol=1e-3)
 
 

@@ -5,7 +5,9 @@ Element-wise checks early in a run use |gpu - oracle| <= 1e-5 max|u|:
 FP32 deviation storage rounds each population to ~6e-8 of its own size and a
 cell's velocity sums nine of them, so a few hundred steps stay far below that.
 FP64 storage must agree to ~1e-11 (only summation order differs). FP16 storage
-(11-bit mantissa) is held to 2e-2 relative L2 and its error is reported.
+(11-bit mantissa) has a fixed, deterministic error on its test case, measured on
+a GB300 at 2.08e-2 (periodic) and 2.13e-2 (walls) relative L2; the test holds it
+to 10 % above those values, so a change that makes FP16 storage worse fails.
 """
 
 import numpy as np
@@ -139,14 +141,16 @@ def test_fp64_storage_matches_to_roundoff():
 def test_fp16_storage_error_is_bounded(walls):
     """FP16 storage keeps 11 significant bits per population. In this Darcy-like regime
     the density deviations are ~500x the velocity (grad p ~ eps nu u / kappa), and they
-    sit in every population, so u is resolved to ~1-3 %. The error is reported."""
+    sit in every population, so u is resolved to ~2 %: measured 2.081e-2 periodic and
+    2.128e-2 with walls (3000 steps), bounded at 10 % above each."""
     kap = synth.lognormal_kappa(128, 64, 8.0, 1.0, seed=11)
     args = (kap, 1.0, 1.0 / 6.0, 1.0, (1e-6, 0.0), walls, 3000)
     a = gpu_run(*args, storage=1)
     b = oracle_run(*args)
     err = rel_l2(a["u"], b["u"])
     print(f"FP16 storage rel L2 error on u: {err:.3e}")
-    assert err < 5e-2
+    measured = 2.128e-2 if walls else 2.081e-2          # GB300, this case, bit-reproducible
+    assert err < 1.1 * measured
 
 
 def test_residual_definition_matches_oracle():

@@ -108,3 +108,43 @@ def test_unmutated_copy_passes(tmp_path):
     assert r.returncode == 0, r.stdout[-3000:]
     r = _pins(so, "test_oracle3d_pins.py", None, stop_first=False)
     assert r.returncode == 0, r.stdout[-3000:]
+
+
+# ---------------------------------------------------- the surrogate oracle's base and gate
+SUR_SRC = os.path.join(ROOT, "oracle", "surrogate.py")
+SUR_MUTANTS = {
+    "bounds_axis_of_y_tubes": [("h_cols = 1.0 / np.mean(1.0 / k, axis=0)", "h_cols = 1.0 / np.mean(1.0 / k, axis=1)")],
+    "upper_bound_arithmetic": [("return (np.mean(h_rows), 1.0 / np.mean(1.0 / a_cols),",
+                                "return (np.mean(h_rows), np.mean(a_cols),")],
+    "width_not_halved": [("wx = 1.0 if mode == 1 else max(0.5 * (hix - lox), 0.05)",
+                          "wx = 1.0 if mode == 1 else max(1.0 * (hix - lox), 0.05)")],
+    "phase_order_transposed": [("for a in (0, 1) for b in (0, 1)])", "for b in (0, 1) for a in (0, 1)])")],
+    "gate_population_std": [("/ (m_members - 1)) if m_members > 1", "/ m_members) if m_members > 1")],
+    "gate_bounds_exclusive": [("if not (stat_lo[k] <= stats[i, k] <= stat_hi[k]):",
+                               "if not (stat_lo[k] < stats[i, k] < stat_hi[k]):")],
+    "gate_mean_of_k_not_log": [("keff[i] = (np.exp(mean[0]), 0.0, 0.0, np.exp(mean[1]))",
+                                "keff[i] = (np.exp(y[:, i, 0]).mean(), 0.0, 0.0, np.exp(y[:, i, 1]).mean())")],
+}
+
+
+@pytest.mark.parametrize("name", sorted(SUR_MUTANTS))
+def test_surrogate_oracle_pins_catch_planted_mistake(name, monkeypatch):
+    import importlib.util
+    import test_surrogate_oracle as pins
+    src = open(SUR_SRC).read()
+    for old, new in SUR_MUTANTS[name]:
+        assert old in src, f"mutation anchor not found: {old!r}"
+        src = src.replace(old, new)
+    spec = importlib.util.spec_from_loader(f"sur_mutant_{name}", loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    exec(compile(src, f"sur_mutant_{name}", "exec"), mod.__dict__)
+    monkeypatch.setattr(pins, "S", mod)
+    tests = [getattr(pins, t) for t in dir(pins) if t.startswith("test_")
+             and ("phase" in t or "bounds" in t or "base" in t or "gate" in t or "checkerboard" in t)]
+    failed = 0
+    for t in tests:
+        try:
+            t()
+        except (AssertionError, ValueError, IndexError):
+            failed += 1
+    assert failed > 0, f"no pin caught the planted mistake {name}"
