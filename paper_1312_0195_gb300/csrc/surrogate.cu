@@ -1182,7 +1182,7 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
         cudaFree(d_part);
         if (e2 != cudaSuccess) { cudaGetLastError(); return fail(LBM_ECUDA, "input moments: %s", cudaGetErrorString(e2)); }
         for (int k = 0; k < NB; ++k) { mx += hp[2 * k]; sx += hp[2 * k + 1]; }
-        const double cnt = (double)n * PIX;
+        const double cnt = (double)n * 4 * PIX;     // the four phase planes of every sample
         mx /= cnt;
         sx = std::sqrt(std::max(sx / cnt - mx * mx, 1e-12));
     }

@@ -195,6 +195,22 @@ def test_training_fits_a_smooth_target():
     assert np.median(err[:, 0]) < 0.1
 
 
+def _base_from_predict(sur, x, mode, n_models=1):
+    """(c, w) per leaf as the library computes them: with every weight zero the network outputs 0,
+    so the prediction is c + w * mean; two calls with target means 0 and 1 give c and w."""
+    import torch
+    lbm = _lbm()
+    for m in range(n_models):
+        sur.set_params(m, np.zeros(lbm.lbm_surrogate_param_count(), dtype=np.float32))
+    out = []
+    for mean in (0.0, 1.0):
+        norm = np.array([0, 1, mean, 1, mean, 1, -1e30, 1e30, -1e30, 1e30, -1e30, 1e30, mode], dtype=np.float32)
+        sur.set_normalization(norm)
+        out.append(sur.predict(torch.from_numpy(np.ascontiguousarray(x)).cuda()).cpu().numpy()[0].astype(np.float64))
+    c, cw = out
+    return c, cw - c
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_target_base_matches_oracle_full_batch(mode):
     """The per-leaf base (c, w) of every target mode against the oracle's target_base on 640
