@@ -450,29 +450,80 @@ def measure_local_keff(lbm, torch, kap, ws, rank=0, sample=512, seed=11):
     }
 
 
-def _surrogate_set(nfields, seed0, side=256):
-    """Seeded log-normal fields (sigma ~ U[0.5, 3], ell ~ U[2, 16]) stacked along y, with quadtree leaves."""
+def _surrogate_fields(nfields, seed0, side):
+    """Seeded log-normal fields (sigma ~ U[0.5, 3], ell ~ U[2, 16]) stacked along y."""
     import synth
     rng = np.random.default_rng(seed0)
-    ks, leaves = [], []
+    ks = []
     for f in range(nfields):
         sigma, ell = rng.uniform(0.5, 3.0), rng.uniform(2.0, 16.0)
         ks.append(synth.lognormal_kappa(side, side, ell, sigma, seed=seed0 * 10000 + f).astype(np.float32))
+    return np.concatenate(ks, axis=0)
+
+
+def _surrogate_set(nfields, seed0, side=256):
+    """Held-out set: seeded log-normal fields with their quadtree leaves (the natural mix of sizes)."""
+    import synth
+    kap = _surrogate_fields(nfields, seed0, side)
+    leaves = []
+    for f in range(nfields):
         lv = synth.quadtree_leaves(side, side, seed=seed0 * 10000 + f)
         lv[:, 1] += f * side
         leaves.append(lv)
-    return np.concatenate(ks, axis=0), np.concatenate(leaves, axis=0)
+    return kap, np.concatenate(leaves, axis=0)
 
 
-def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=20, spread_max=0.03):
-    """The learned K* surrogate against the batched local LBM on held-out patches.
+def _surrogate_train_set(nfields, seed0, per_size, side=512):
+    """Training set stratified by leaf size: per field, `per_size[s]` seeded tiles of each size."""
+    import synth
+    kap = _surrogate_fields(nfields, seed0, side)
+    leaves = []
+    for f in range(nfields):
+        lv = synth.stratified_tiles(side, side, per_size, seed=seed0 * 10000 + f)
+        lv[:, 1] += f * side
+        leaves.append(lv)
+    return kap, np.concatenate(leaves, axis=0)
 
-    Labels: local LBM (FP32, tau = 1, G = 1e-6, tol 1e-8, persistent launch). The ensemble of
-    4 CNNs is trained on the training patches; on held-out fields it predicts every patch,
-    the gate (spread <= ln(1 + spread_max), statistics in the training range) accepts some,
-    the rest fall back to local LBM. Reports patches/s of LBM alone, of ensemble inference
-    with the gate, and end to end (inference + gate + LBM on the rejected patches), and the
-    relative K* error of accepted predictions against their LBM labels."""
+
+SUR_SIZES = (1, 2, 4, 8, 16, 32, 64)       # leaf sizes of the per-size gate (index = log2 size)
+
+
+def _calibrate_gate(sd, in_range, rel, sizes, p99_max=0.04, med_max=0.015):
+    """Per leaf size, the largest spread limit (from a log grid) whose accepted leaves keep the
+    relative K* error at p99 <= p99_max and median <= med_max on the calibration set; sizes
+    with no such limit get the smallest grid value (nearly everything falls back)."""
+    grid = np.geomspace(1e-3, 0.3, 60)
+    out = []
+    for s in SUR_SIZES:
+        sel = sizes == s
+        best = grid[0]
+        if sel.any():
+            for g in grid:
+                acc = sel & in_range & (sd <= np.log1p(g))
+                if acc.sum() < 10:
+                    continue
+                e = rel[acc]
+                if np.percentile(e, 99) <= p99_max and np.median(e) <= med_max:
+                    best = g
+        out.append(float(best))
+    return np.array(out, dtype=np.float32)
+
+
+def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=48, test_fields=24, epochs=20,
+                      spread_max=0.03):
+    """The learned K* surrogate against the batched local LBM on held-out leaves.
+
+    Training set (config 4's size): ~200k leaves cut from seeded log-normal 512^2 fields
+    (sigma ~ U[0.5, 3], ell ~ U[2, 16]), stratified by size (equal counts of 8, 16, 32 and 64
+    cells: the 64-cell leaves carry most of the LBM cost); labels by local LBM (FP32, tau = 1,
+    G = 1e-6, tol 1e-8, persistent launch); non-converged labels are left out. An ensemble of 4
+    is trained on it. The gate's spread limit is calibrated per leaf size on separate held-out
+    fields; the test leaves are the quadtree leaves of further held-out fields (the natural mix).
+    Reports patches/s of LBM alone and end to end through lbm_surrogate_keff (patches, inference
+    of all members, gate and local LBM on the rejected leaves, one call), and the relative K*
+    error of accepted predictions against their LBM labels."""
+    per_size = per_size or {8: 64, 16: 64, 32: 64, 64: 64}
+
     def label(kap, leaves):
         p = lbm.Params(nx=kap.shape[1], ny=kap.shape[0], tau=1.0, eps=1.0)
         kt, lt = torch.from_numpy(kap).cuda(), torch.from_numpy(leaves).cuda()
@@ -483,98 +534,111 @@ def measure_surrogate(lbm, torch, train_fields=200, test_fields=24, epochs=20, s
         dt = time.perf_counter() - t0
         x, stats = lbm.lbm_patches(kt, lt)
         y = torch.log(torch.stack([ke[:, 0], ke[:, 3]], dim=1)).float()
-        return kt, lt, p, x, stats, y, st, dt, steps.cpu().numpy().astype(np.float64)
+        return kt, lt, p, x, stats, y, ke, st, dt, steps.cpu().numpy().astype(np.float64)
 
-    ktr, ltr = _surrogate_set(train_fields, 10)
-    kte, lte = _surrogate_set(test_fields, 1000)
-    _, _, _, xtr, str_, ytr, sttr, _, _ = label(ktr, ltr)
-    kt, lt, p, xte, ste, yte, stte, t_lbm, steps_te = label(kte, lte)
+    def rel_err(keff, ke):
+        return torch.maximum((keff[:, 0] / ke[:, 0] - 1.0).abs(), (keff[:, 3] / ke[:, 3] - 1.0).abs())
+
+    t0 = time.perf_counter()
+    ktr, ltr = _surrogate_train_set(train_fields, 10, per_size)
+    t_gen = time.perf_counter() - t0
+    _, _, _, xtr, str_, ytr, _, sttr, t_label, _ = label(ktr, ltr)
     ok = sttr == 0
     sur = lbm.Surrogate(4, 3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sur.train(xtr[ok], ytr[ok], str_[ok], epochs=epochs, batch=256, lr=2e-3, seed=1)
+    loss = sur.train(xtr[ok], ytr[ok], str_[ok], epochs=epochs, batch=256, lr=2e-3, seed=1)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    n = len(lte)
+    n_train = int(ok.sum())
+    del xtr, str_, ytr
     norm = sur.get_normalization()
 
-    def infer_and_gate(leaves):
-        x, stats = lbm.lbm_patches(kt, leaves)
-        pred = sur.predict(x)
-        sd = pred.std(dim=0).max(dim=1).values
-        in_range = torch.ones(len(leaves), dtype=torch.bool, device="cuda")
-        for k in range(3):
-            in_range &= (stats[:, k] >= float(norm[6 + 2 * k])) & (stats[:, k] <= float(norm[7 + 2 * k]))
-        return pred, (sd <= float(np.log1p(spread_max))) & in_range
+    # per-size gate limits from a calibration split
+    kca, lca = _surrogate_set(calib_fields, 2000)
+    kc, lc, pc, xc, stc, _, kec, stt_c, _, _ = label(kca, lca)
+    pred_c = sur.predict(xc)
+    sd_c = pred_c.std(dim=0).max(dim=1).values.cpu().numpy()
+    inr = np.ones(len(lca), dtype=bool)
+    for k in range(3):
+        v = stc[:, k].cpu().numpy()
+        inr &= (v >= norm[6 + 2 * k]) & (v <= norm[7 + 2 * k])
+    keff_c = torch.exp(pred_c.double().mean(dim=0))
+    rel_c = torch.maximum((keff_c[:, 0] / kec[:, 0] - 1).abs(), (keff_c[:, 1] / kec[:, 3] - 1).abs()).cpu().numpy()
+    good_c = stt_c.cpu().numpy() == 0
+    gate = _calibrate_gate(sd_c, inr & good_c, rel_c, lca[:, 2])
+    sur.set_gate(gate)
 
-    infer_and_gate(lt)                                   # warm-up: work buffers, launch set-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    pred, accept = infer_and_gate(lt)
-    torch.cuda.synchronize()
-    t_inf = time.perf_counter() - t0
-    # end to end: inference + gate + local LBM on the rejected leaves
-    rej = torch.nonzero(~accept).flatten()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    if rej.numel():
-        lbm.local_keff(p, kt, lt[rej].contiguous(), 1e-6, 1e-8, 200000, 64, True)
-    torch.cuda.synchronize()
-    t_fb = time.perf_counter() - t0
-    good = (stte == 0)
-    rel = (torch.exp(pred.mean(dim=0)) / torch.exp(yte) - 1.0).abs()
-    acc = (accept & good)
-    rel_acc = rel[acc].flatten().cpu().numpy()
-    rel_all = rel[good].flatten().cpu().numpy()
-    flops = 4 * 2 * 1024 * 9 * (2 * 32 + 32 * 32 + 32 * 64 + 3 * 64 * 64)      # ensemble, per patch
-    # tighter gates on the same predictions, each with its own LBM fallback
-    sd = pred.std(dim=0).max(dim=1).values
-    tighter = {}
-    for thr in (0.01, 0.02):
-        acc_t = accept & (sd <= float(np.log1p(thr)))
-        rej_t = torch.nonzero(~acc_t).flatten()
+    # held-out test leaves: LBM alone, then the surrogate end to end (one call)
+    kte, lte = _surrogate_set(test_fields, 1000)
+    kt, lt, p, xte, ste, yte, ke_te, stte, t_lbm, steps_te = label(kte, lte)
+    n = len(lte)
+    sur.keff(p, kt, lt[:64].contiguous(), 0.0, 1e-6, 1e-8, 200000)      # warm-up: buffers, launch set-up
+    results = {}
+    for name, smax in (("per_size", 0.0), ("uniform_3pct", spread_max)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if rej_t.numel():
-            lbm.local_keff(p, kt, lt[rej_t].contiguous(), 1e-6, 1e-8, 200000, 64, True)
+        keff, fb, status, nfb, _ = sur.keff(p, kt, lt, smax, 1e-6, 1e-8, 200000)
         torch.cuda.synchronize()
-        t_fb_t = time.perf_counter() - t0
-        rel_t = rel[acc_t & good].flatten().cpu().numpy()
-        tighter[f"gate_{int(round(thr * 100))}pct"] = {
-            "accepted_fraction": float((acc_t & good).float().mean()),
-            "accepted_rel_err_median": float(np.median(rel_t)) if rel_t.size else None,
-            "accepted_rel_err_p99": float(np.percentile(rel_t, 99)) if rel_t.size else None,
-            "end_to_end_patches_per_s": n / (t_inf + t_fb_t),
-            "speedup_end_to_end": (n / (t_inf + t_fb_t)) / (n / t_lbm)}
+        t_e2e = time.perf_counter() - t0
+        good = (stte == 0)
+        acc = (fb == 0)
+        rel = rel_err(keff, ke_te)
+        rel_acc = rel[acc & good].cpu().numpy()
+        results[name] = {
+            "end_to_end_patches_per_s": n / t_e2e, "speedup_end_to_end": t_lbm / t_e2e,
+            "accepted_fraction": float(acc.float().mean()),
+            "accepted_rel_err_median": float(np.median(rel_acc)) if rel_acc.size else None,
+            "accepted_rel_err_p99": float(np.percentile(rel_acc, 99)) if rel_acc.size else None,
+            "fallback_leaves": nfb}
+        if name == "per_size":
+            acc_np, rel_np, good_np = acc.cpu().numpy(), rel.cpu().numpy(), good.cpu().numpy()
+    # inference alone: patches, all members and the gate, with every leaf accepted
+    x_warm, _ = lbm.lbm_patches(kt, lt)
+    sur.predict(x_warm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x_i, st_i = lbm.lbm_patches(kt, lt)
+    sur.predict(x_i)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
     # where the LBM time goes, by leaf size (cost = cells x steps of both drives)
     sz = lte[:, 2]
     cost = sz.astype(np.float64) ** 2 * steps_te.sum(axis=1)
-    acc_np, rel_np, good_np = acc.cpu().numpy(), rel.max(dim=1).values.cpu().numpy(), good.cpu().numpy()
     by_size = {}
     for size in (8, 16, 32, 64):
         sel = sz == size
         if sel.any():
-            by_size[str(size)] = {"leaves": int(sel.sum()), "lbm_cost_share": float(cost[sel].sum() / cost.sum()),
-                                  "accepted": float(acc_np[sel].mean()),
-                                  "median_rel_err": float(np.median(rel_np[sel & good_np]))}
+            e = rel_np[sel & good_np & acc_np]
+            by_size[str(size)] = {
+                "leaves": int(sel.sum()), "lbm_cost_share": float(cost[sel].sum() / cost.sum()),
+                "gate_spread": float(gate[SUR_SIZES.index(size)]),
+                "accepted": float(acc_np[sel].mean()),
+                "accepted_cost_share": float(cost[sel & acc_np].sum() / cost[sel].sum()),
+                "accepted_rel_err_median": float(np.median(e)) if e.size else None,
+                "accepted_rel_err_p99": float(np.percentile(e, 99)) if e.size else None,
+                "all_rel_err_median": float(np.median(rel_np[sel & good_np]))}
+    rej_cost = cost[~acc_np].sum() / cost.sum()
+    flops = 4 * 2 * 1024 * 9 * (5 * 32 + 32 * 32 + 32 * 64 + 3 * 64 * 64)      # ensemble, per patch
     sur.close()
     return {
-        "workload": f"{train_fields} training / {test_fields} held-out 256^2 log-normal fields (sigma U[0.5,3], "
-                    "ell U[2,16]), quadtree leaves 8-64, labels by local LBM tol 1e-8; ensemble of 4, "
-                    "target (log K* - c) / w on the layered-medium bounds (mode 2), "
-                    f"gate: spread <= {spread_max:.0%} and statistics in the training range",
-        "train_patches": int(ok.sum()), "test_patches": n, "epochs": epochs, "train_seconds": t_train,
+        "workload": f"train: {n_train} leaves ({train_fields} seeded 512^2 log-normal fields, sigma U[0.5,3], "
+                    f"ell U[2,16], {per_size} tiles per field by size); gate calibrated per size on "
+                    f"{calib_fields} held-out 256^2 fields; test: quadtree leaves 8-64 of {test_fields} further "
+                    "held-out fields; labels by local LBM tol 1e-8; ensemble of 4, five input planes (phase "
+                    "planes of the 64x64 log-K plane + size), target (log K* - c) / w on the layered-medium "
+                    "bounds (mode 2)",
+        "train_patches": n_train, "test_patches": n, "epochs": epochs,
+        "seconds": {"fields": t_gen, "labels": t_label, "train": t_train},
+        "final_train_loss": [float(l[-1]) for l in loss],
         "lbm_patches_per_s": n / t_lbm,
         "surrogate_patches_per_s": n / t_inf,
-        "end_to_end_patches_per_s": n / (t_inf + t_fb),
-        "speedup_end_to_end": (n / (t_inf + t_fb)) / (n / t_lbm),
-        "accepted_fraction": float(acc.float().mean()),
-        "accepted_rel_err_median": float(np.median(rel_acc)) if rel_acc.size else None,
-        "accepted_rel_err_p99": float(np.percentile(rel_acc, 99)) if rel_acc.size else None,
-        "all_rel_err_median": float(np.median(rel_all)), "all_rel_err_p99": float(np.percentile(rel_all, 99)),
         "inference_tflops": flops * n / t_inf / 1e12,
-        **tighter,
+        "gate_spread_by_size": {str(s): float(g) for s, g in zip(SUR_SIZES, gate)},
+        **results["per_size"],
+        "rejected_lbm_cost_share": float(rej_cost),
+        "ideal_speedup": float(1.0 / (rej_cost + t_inf / t_lbm)),
+        "uniform_3pct_gate": results["uniform_3pct"],
         "by_leaf_size": by_size,
     }
 
@@ -694,7 +758,8 @@ def run_ours(args, ws, rank, local):
         d3 = measure_d3q19(lbm, torch, ws=ws, rank=rank)
         local = measure_local_keff(lbm, torch, kap, ws, rank)
         if not args.no_surrogate:
-            surrogate = measure_surrogate(lbm, torch)
+            surrogate = measure_surrogate(lbm, torch, train_fields=args.surrogate_fields,
+                                          epochs=args.surrogate_epochs)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -746,6 +811,10 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the storage variants, the local-problem and the surrogate measurements")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
+    ap.add_argument("--surrogate-only", action="store_true",
+                    help="run only the surrogate measurement (config 4) and print its JSON")
+    ap.add_argument("--surrogate-fields", type=int, default=800, help="training fields of the surrogate block")
+    ap.add_argument("--surrogate-epochs", type=int, default=20, help="training epochs of the surrogate block")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling mode: create the grid, run this many plain lattice steps, exit")
     ap.add_argument("--profile-local", type=int, default=0,
@@ -781,6 +850,13 @@ def main(argv=None):
         return run_profile_local(args, local)
     if args.profile_surrogate > 0:
         return run_profile_surrogate(args, local)
+    if args.surrogate_only:
+        import torch
+        import paper_1312_0195_gb300 as lbm
+        torch.cuda.set_device(local)
+        print(json.dumps(measure_surrogate(lbm, torch, train_fields=args.surrogate_fields,
+                                          epochs=args.surrogate_epochs)), flush=True)
+        return 0
     if args.profile_3d > 0:
         return run_profile_3d(args, local)
     if args.profile_local3d > 0:

@@ -12,6 +12,7 @@ from .fields import (  # noqa: F401
     lognormal_kappa3d,
     quadtree_leaves,
     uniform_leaves,
+    stratified_tiles,
     channel_kappa,
     block_kappa_eq22,
     layered_kappa,

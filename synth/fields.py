@@ -93,6 +93,18 @@ def quadtree_leaves(nx: int, ny: int, seed: int, root: int = 64, min_size: int =
     return np.asarray(out, dtype=np.int32).reshape(-1, 3)
 
 
+def stratified_tiles(nx: int, ny: int, per_size: dict, seed: int) -> np.ndarray:
+    """Seeded leaf set with a fixed count per size: for each size s, ``per_size[s]`` distinct
+    s-aligned tiles of the field (all of them when the field has fewer). int32 ``[n, 3]``."""
+    rng = _rng(seed)
+    out = []
+    for size in sorted(per_size):
+        tiles = uniform_leaves(nx, ny, size)
+        k = min(int(per_size[size]), len(tiles))
+        out.append(tiles[np.sort(rng.choice(len(tiles), k, replace=False))])
+    return np.concatenate(out, axis=0).astype(np.int32)
+
+
 def uniform_leaves(nx: int, ny: int, size: int) -> np.ndarray:
     """Row-major tiling of the field into ``size``-square blocks, int32 ``[n, 3]``."""
     if nx % size or ny % size:
