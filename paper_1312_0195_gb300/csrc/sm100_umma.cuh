@@ -10,6 +10,9 @@
 //    groups are SBO = (K / 8) * 128 bytes apart.
 //  * One MMA instruction is M x N x 16 (kind::f16, BF16 in, FP32 accumulate in
 //    TMEM); its K-slice starts 2 core matrices (256 bytes) further along K.
+//  * MN-major operands (idesc_bf16_f32_mn) use the same descriptor fields with
+//    the core matrix turned around: 8 K-rows of 16 bytes, each 8 MN elements;
+//    LBO is again the step between core matrices along K and SBO along M/N.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,6 +41,14 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t 
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with both operands MN-major (bits 15 and 16 set): element (r, k) of an R x K
+// operand sits at (r / 8) * SBO + (k / 8) * LBO + (k % 8) * 16 + (r % 8) * 2, i.e. a core
+// matrix is 8 K-rows of 16 bytes, each holding 8 consecutive MN elements.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N)
+{
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -100,6 +111,17 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, uint64_
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4, %5}], [%6];"
         :: "r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+           "r"(smem_addr(bar))
+        : "memory");
+}
+// TMA: one box of a 5-D tiled tensor map into shared memory (as tma_load_4d).
+__device__ __forceinline__ void tma_load_5d(void *dst, const void *tmap, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3, int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+        :: "r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
            "r"(smem_addr(bar))
         : "memory");
 }

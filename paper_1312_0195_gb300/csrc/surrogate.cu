@@ -257,249 +257,48 @@ __global__ void __launch_bounds__(256) gap_backward_kernel(const float *dpool, c
     }
 }
 
-// Weight gradient of one conv layer for one (image, tap) on CUDA cores in FP32:
-//   part[b][tap][co][ci] = sum_p dout[b][p][co] * in[b][p + off(tap)][ci]
-// and, for tap 0, the bias partial sum_p dout[b][p][co]. Each thread owns a
-// 4 x TCI block of (co, ci); rows of 32 pixels are staged in shared memory.
-template <int COUT, int CINP, int CIN>
-__global__ void __launch_bounds__(256) wgrad_kernel(const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part,
-                                                   float *bpart)
+// Bias gradient partials: bpart[g][co] = sum over images g, g + G, ... and all their pixels of
+// dout[img][p][co] (dout holds the ReLU-masked gradient of the layer's output). Thread t sums
+// channel t % COUT over pixels p = t / COUT (mod 256 / COUT); the phases are folded in order.
+template <int COUT>
+__global__ void __launch_bounds__(256) bias_grad_kernel(const __nv_bfloat16 *dout, int B, float *bpart)
 {
-    constexpr int TCI = (COUT * CIN) / 1024 > 0 ? (COUT * CIN) / 1024 : 1;
-    constexpr int NCOB = COUT / 4, NCIB = CIN / TCI;
-    const int b = blockIdx.x / 9, tap = blockIdx.x % 9, dy = tap / 3, dx = tap % 3;
-    __shared__ float sO[IMG][COUT];
-    __shared__ float sI[IMG][CIN];
-    const int tid = threadIdx.x;
-    const bool active = tid < NCOB * NCIB;
-    const int cob = tid % NCOB, cib = tid / NCOB;
-    float acc[4][TCI];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < TCI; ++j) acc[i][j] = 0.0f;
-    float bacc = 0.0f;   // bias partial for channel tid (tap 0)
-    for (int row = 0; row < IMG; ++row) {
-        // q -> (8-channel group, pixel, channel in group): consecutive threads read a plane's row
-        for (int q = tid; q < IMG * COUT; q += 256) {
-            const int px = (q >> 3) & (IMG - 1), c = (q >> 8) * 8 + (q & 7);
-            sO[px][c] = __bfloat162float(dout[act_at(b, row * IMG + px, c, COUT)]);
-        }
-        const int ys = row + dy - 1;
-        for (int q = tid; q < IMG * CIN; q += 256) {
-            const int px = CIN >= 8 ? (q >> 3) & (IMG - 1) : q / CIN;
-            const int c = CIN >= 8 ? (q >> 8) * 8 + (q & 7) : q - px * CIN;
-            const int xs = px + dx - 1;
-            float v = 0.0f;
-            if (ys >= 0 && ys < IMG && xs >= 0 && xs < IMG)
-                v = __bfloat162float(in[act_at(b, ys * IMG + xs, c, CINP)]);
-            sI[px][c] = v;
-        }
-        __syncthreads();
-        if (active) {
-            for (int px = 0; px < IMG; ++px) {
-                float o4[4], iv[TCI];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) o4[i] = sO[px][cob * 4 + i];
-#pragma unroll
-                for (int j = 0; j < TCI; ++j) iv[j] = sI[px][cib * TCI + j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < TCI; ++j) acc[i][j] += o4[i] * iv[j];
-            }
-        }
-        if (tap == 0 && tid < COUT)
-            for (int px = 0; px < IMG; ++px) bacc += sO[px][tid];
-        __syncthreads();
-    }
-    if (active) {
-        float *dst = part + ((int64_t)b * 9 + tap) * COUT * CIN;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < TCI; ++j) dst[(cob * 4 + i) * CIN + cib * TCI + j] = acc[i][j];
-    }
-    if (tap == 0 && tid < COUT) bpart[(int64_t)b * COUT + tid] = bacc;
-}
-
-// ------------------------------------------------ weight gradient on the tensor cores (layers 1..5)
-// dW[tap][co][ci] = sum over pixels p of dout[p][co] * in[p + off(tap)][ci] as warp-level BF16 MMAs
-// (mma.sync m16n8k16, FP32 accumulate). A work item is a quarter image (8 rows x 32 columns);
-// cp.async stages its dout tile and its input tile with a one-pixel zero halo in shared memory as
-// 8-channel planes (16 bytes per pixel), double-buffered. ldmatrix.trans turns 8 pixels x 8
-// channels into fragments: A = dout^T (16 co x 16 pixels), B = shifted input (16 pixels x 8 ci),
-// and a tap is just another row address. Each warp owns one 16-channel co tile and NJ 8-channel ci
-// tiles for all 9 taps; a CTA accumulates its items in registers and writes one partial, and
-// wgrad_reduce_kernel folds the partials in CTA order (deterministic). The warps of the first ci
-// group also sum their A fragments: the bias gradient.
-constexpr int WG_THREADS = 256;
-constexpr int WG_ROWS = 8;                                    // output rows per work item
-constexpr int WG_HW = IMG + 2, WG_HH = WG_ROWS + 2;           // input tile with halo: 10 x 34 pixels
-constexpr uint32_t WG_IPLANE = WG_HH * WG_HW * 16;            // bytes per 8-channel input plane
-constexpr uint32_t WG_OPLANE = WG_ROWS * IMG * 16;            // bytes per 8-channel dout plane
-
-template <int COUT, int CIN>
-struct WgShape {
-    static constexpr int CT = COUT / 16, NT = CIN / 8, NJ = CT * NT / 8;
-    static constexpr uint32_t STAGE = (CIN / 8) * WG_IPLANE + (COUT / 8) * WG_OPLANE;
-    static constexpr uint32_t SMEM = 2 * STAGE;
-    static_assert((CT * NT) % 8 == 0 && NJ >= 1 && (NJ == 1 || NJ % 2 == 0), "8 warps share the tiles evenly");
-};
-
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g, uint32_t src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(saddr), "l"(g), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t saddr, uint32_t (&r)[4])
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(saddr));
-}
-__device__ __forceinline__ void ldsm_x2_t(uint32_t saddr, uint32_t (&r)[2])
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(saddr));
-}
-__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-                 "{%8, %9}, {%0, %1, %2, %3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ float bf16x2_sum(uint32_t v)
-{
-    return __uint_as_float(v << 16) + __uint_as_float(v & 0xffff0000u);
-}
-
-template <int COUT, int CIN>
-__global__ void __launch_bounds__(WG_THREADS, 1) wgrad_mma_kernel(const __nv_bfloat16 *in, const __nv_bfloat16 *dout,
-                                                                 int nimg, float *part, float *bpart)
-{
-    using W = WgShape<COUT, CIN>;
-    constexpr int CT = W::CT, NJ = W::NJ, IPI = IMG / WG_ROWS;
-    extern __shared__ __align__(128) uint8_t wsm[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ct = warp % CT, j0 = (warp / CT) * NJ;        // co tile and first ci tile of this warp
-    const int mat = lane >> 3, row = lane & 7;               // ldmatrix: matrix and row this lane addresses
-    const int nitems = nimg * IPI;
-
-    float acc[9][NJ][4];
-#pragma unroll
-    for (int t = 0; t < 9; ++t)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[t][j][q] = 0.0f;
-    float bsum0 = 0.0f, bsum1 = 0.0f;                        // bias partials of co = 16 ct + g, + 8
-
-    auto load = [&](int item, int buf) {
-        const int img = item / IPI, y0 = (item - img * IPI) * WG_ROWS;
-        const uint32_t ibase = umma::smem_addr(wsm + buf * W::STAGE);
-        for (int i = tid; i < (CIN / 8) * WG_HH * WG_HW; i += WG_THREADS) {
-            const int g = i / (WG_HH * WG_HW), rem = i - g * (WG_HH * WG_HW);
-            const int r = rem / WG_HW, c = rem - r * WG_HW;
-            const int y = y0 - 1 + r, x = c - 1;
-            const bool ok = y >= 0 && y < IMG && x >= 0 && x < IMG;
-            cp_async16(ibase + g * WG_IPLANE + rem * 16, ok ? in + act_at(img, y * IMG + x, 8 * g, CIN) : in,
-                       ok ? 16u : 0u);
-        }
-        const uint32_t obase = ibase + (CIN / 8) * WG_IPLANE;
-        for (int i = tid; i < (COUT / 8) * WG_ROWS * IMG; i += WG_THREADS) {
-            const int g = i / (WG_ROWS * IMG), pp = i - g * (WG_ROWS * IMG);
-            cp_async16(obase + g * WG_OPLANE + pp * 16, dout + act_at(img, y0 * IMG + pp, 8 * g, COUT), 16u);
-        }
-    };
-
-    int k = 0;
-    if ((int)blockIdx.x < nitems) load(blockIdx.x, 0);
-    cp_async_commit();
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
-        if (item + (int)gridDim.x < nitems) load(item + gridDim.x, (k + 1) & 1);
-        cp_async_commit();                                   // one group per iteration, possibly empty
-        cp_async_wait<1>();                                  // this item's tiles have landed
-        __syncthreads();
-        const uint32_t ib = umma::smem_addr(wsm + (k & 1) * W::STAGE);
-        const uint32_t ob = ib + (CIN / 8) * WG_IPLANE;
-#pragma unroll 1
-        for (int r = 0; r < WG_ROWS; ++r) {
-#pragma unroll
-            for (int x0 = 0; x0 < IMG; x0 += 16) {
-                // A: (co 0-7, px 0-7), (co 8-15, px 0-7), (co 0-7, px 8-15), (co 8-15, px 8-15)
-                uint32_t a[4];
-                ldsm_x4_t(ob + (2 * ct + (mat & 1)) * WG_OPLANE + (r * IMG + x0 + (mat >> 1) * 8 + row) * 16, a);
-                if (warp < CT) {
-                    bsum0 += bf16x2_sum(a[0]) + bf16x2_sum(a[2]);
-                    bsum1 += bf16x2_sum(a[1]) + bf16x2_sum(a[3]);
-                }
-#pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = tap / 3, dx = tap % 3;
-                    const uint32_t prow = (uint32_t)(((r + dy) * WG_HW + x0 + dx) * 16);
-                    if constexpr (NJ == 1) {
-                        uint32_t b[2];    // (ci tile j0, px 0-7), (j0, px 8-15)
-                        ldsm_x2_t(ib + j0 * WG_IPLANE + prow + ((mat & 1) * 8 + row) * 16, b);
-                        mma_16816(acc[tap][0], a, b[0], b[1]);
-                    } else {
-#pragma unroll
-                        for (int jj = 0; jj < NJ; jj += 2) {
-                            uint32_t b[4];    // (j, px 0-7), (j, px 8-15), (j + 1, px 0-7), (j + 1, px 8-15)
-                            ldsm_x4_t(ib + (j0 + jj + (mat >> 1)) * WG_IPLANE + prow + ((mat & 1) * 8 + row) * 16, b);
-                            mma_16816(acc[tap][jj], a, b[0], b[1]);
-                            mma_16816(acc[tap][jj + 1], a, b[2], b[3]);
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();                                     // buffer k & 1 is refilled next iteration
-    }
-    cp_async_wait<0>();
-    // partial [tap][co][ci] of this CTA; thread (g, t4) holds rows g, g + 8 and columns 2 t4, 2 t4 + 1 of each tile
-    const int g = lane >> 2, t4 = lane & 3;
-    float *dst = part + (int64_t)blockIdx.x * 9 * COUT * CIN;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) {
-            const int co = ct * 16 + g, ci = (j0 + jj) * 8 + 2 * t4;
-            float *d0 = dst + ((int64_t)tap * COUT + co) * CIN + ci;
-            float *d1 = d0 + 8 * CIN;
-            d0[0] = acc[tap][jj][0];
-            d0[1] = acc[tap][jj][1];
-            d1[0] = acc[tap][jj][2];
-            d1[1] = acc[tap][jj][3];
-        }
-    if (warp < CT) {
-        bsum0 += __shfl_xor_sync(0xffffffffu, bsum0, 1);
-        bsum1 += __shfl_xor_sync(0xffffffffu, bsum1, 1);
-        bsum0 += __shfl_xor_sync(0xffffffffu, bsum0, 2);
-        bsum1 += __shfl_xor_sync(0xffffffffu, bsum1, 2);
-        if (t4 == 0) {
-            bpart[(int64_t)blockIdx.x * COUT + ct * 16 + g] = bsum0;
-            bpart[(int64_t)blockIdx.x * COUT + ct * 16 + g + 8] = bsum1;
-        }
+    constexpr int NPH = 256 / COUT;
+    const int t = threadIdx.x, co = t % COUT, ph = t / COUT;
+    float acc = 0.0f;
+    for (int img = blockIdx.x; img < B; img += gridDim.x)
+        for (int p = ph; p < PIX; p += NPH) acc += __bfloat162float(dout[act_at(img, p, co, COUT)]);
+    __shared__ float red[256];
+    red[t] = acc;
+    __syncthreads();
+    if (t < COUT) {
+        float v = 0.0f;
+        for (int k = 0; k < NPH; ++k) v += red[k * COUT + t];
+        bpart[(int64_t)blockIdx.x * COUT + t] = v;
     }
 }
 
-// Fold the per-image partials in image order into the layer's gradient slots.
-__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float *part, const float *bpart, int B, int cout,
-                                                          int cin, float *gw, float *gb)
+// Folds the per-CTA partials of wgrad_tc_kernel (CTA b holds input-channel part b % P; its rows h
+// are separate partials) into W's gradient [co][ci][3][3] and the bias partials into b's, in a
+// fixed order (deterministic).
+__global__ void __launch_bounds__(256) wgrad_tc_reduce_kernel(const float *part, int grid, int P, int HM, int cout,
+                                                             int cip, int cin, const float *bpart, int nb, float *gw,
+                                                             float *gb)
 {
     const int nw = cout * cin * 9;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nw + cout; t += gridDim.x * blockDim.x) {
         if (t < nw) {
             const int co = t / (cin * 9), rem = t - co * cin * 9, ci = rem / 9, tap = rem - ci * 9;
+            const int pp = ci / cip, c = ci - pp * cip;
             float acc = 0.0f;
-            for (int b = 0; b < B; ++b) acc += part[(((int64_t)b * 9 + tap) * cout + co) * cin + ci];
+            for (int b = pp; b < grid; b += P)
+                for (int h = 0; h < HM; ++h)
+                    acc += part[((((int64_t)b * HM + h) * 9 + tap) * cout + co) * cip + c];
             gw[t] = acc;
         } else {
             const int co = t - nw;
             float acc = 0.0f;
-            for (int b = 0; b < B; ++b) acc += bpart[(int64_t)b * cout + co];
+            for (int b = 0; b < nb; ++b) acc += bpart[(int64_t)b * cout + co];
             gb[co] = acc;
         }
     }
@@ -633,6 +432,8 @@ __global__ void destandardise_kernel(float *y, int n, int nmodels, const float4 
 
 // ---------------------------------------------------------------- launchers
 
+int nblk(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b)); }
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time libcuda dependency)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -718,42 +519,70 @@ cudaError_t conv_dgrad(int l, const ConvArgs &a, cudaStream_t st)
     }
 }
 
-template <int COUT, int CIN>
-static cudaError_t launch_wgrad_mma(const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part, float *bpart,
-                                    int B, int *nparts, cudaStream_t st)
+// Tensor map over BF16 activations [nimg][C/8][32][32][8] seen as 5-D (8 channels, 32 columns,
+// C/8 channel groups, 32 rows, nimg), so that a box lands in shared memory row by row:
+// [rows][groups][columns][8]. Out-of-range pixels read as zero.
+static cudaError_t encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *act, int c, int nimg, int box_w,
+                                   int box_groups, int box_h)
 {
-    using W = WgShape<COUT, CIN>;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {8, IMG, (cuuint64_t)(c / 8), IMG, (cuuint64_t)nimg};
+    const cuuint64_t strides[4] = {8 * 2, (cuuint64_t)PIX * 8 * 2, (cuuint64_t)IMG * 8 * 2,
+                                   (cuuint64_t)(c / 8) * PIX * 8 * 2};
+    const cuuint32_t box[5] = {8, (cuuint32_t)box_w, (cuuint32_t)box_groups, (cuuint32_t)box_h, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(act), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Weight and bias gradient of one layer: wgrad_tc_kernel, bias partials, and the fixed-order fold
+// into gw [cout][cin][3][3] and gb [cout].
+template <int COUT, int CIN_P, int CIP>
+static cudaError_t launch_wgrad_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part, float *bpart,
+                                   int B, int cin, int *err, float *gw, float *gb, cudaStream_t st)
+{
+    using W = WgtShape<COUT, CIN_P, CIP>;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
-        const cudaError_t e = cudaFuncSetAttribute(wgrad_mma_kernel<COUT, CIN>,
+        const cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<COUT, CIN_P, CIP>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::SMEM);
         if (e != cudaSuccess) return e;
         sms = sm_count(dev);
     }
-    const int grid = B < sms ? B : sms;          // partial buffers hold B slices
-    wgrad_mma_kernel<COUT, CIN><<<grid, WG_THREADS, W::SMEM, st>>>(in, dout, B, part, bpart);
-    *nparts = grid;
+    CUtensorMap tin, tout;
+    cudaError_t e = encode_rows_map(&tin, in, CIN_P, B, HALO_W, CIP / 8, W::ROWS + 2);
+    if (e == cudaSuccess) e = encode_rows_map(&tout, dout, COUT, B, IMG, COUT / 8, W::ROWS);
+    if (e != cudaSuccess) return e;
+    const int units = 2 * B * W::P;
+    int grid = units < sms ? units : sms;
+    grid -= grid % W::P;
+    WgtArgs a{part, B, err};
+    wgrad_tc_kernel<COUT, CIN_P, CIP><<<grid, CONV_THREADS, W::SMEM, st>>>(tin, tout, a);
+    const int nb = B < 128 ? B : 128;
+    bias_grad_kernel<COUT><<<nb, 256, 0, st>>>(dout, B, bpart);
+    wgrad_tc_reduce_kernel<<<nblk((int64_t)COUT * cin * 9 + COUT), 256, 0, st>>>(part, grid, W::P, W::HM, COUT, CIP,
+                                                                                cin, bpart, nb, gw, gb);
+    count_launches(3);
     return cudaGetLastError();
 }
 
-// Weight and bias gradient partials of layer l; *nparts partials of [9][cout][cin] (+ [cout]) to fold.
+// Weight and bias gradient of layer l into gw, gb (the layer's slots of the gradient vector).
 cudaError_t wgrad(int l, const __nv_bfloat16 *in, const __nv_bfloat16 *dout, float *part, float *bpart, int B,
-                  int *nparts, cudaStream_t st)
+                  int *err, float *gw, float *gb, cudaStream_t st)
 {
     switch (l) {
-    case 0:
-        wgrad_kernel<32, 16, IN_PLANES><<<dim3(B * 9), 256, 0, st>>>(in, dout, part, bpart);
-        *nparts = B;
-        return cudaGetLastError();
-    case 1: return launch_wgrad_mma<32, 32>(in, dout, part, bpart, B, nparts, st);
-    case 2: return launch_wgrad_mma<64, 32>(in, dout, part, bpart, B, nparts, st);
-    default: return launch_wgrad_mma<64, 64>(in, dout, part, bpart, B, nparts, st);
+    case 0: return launch_wgrad_tc<32, 16, 16>(in, dout, part, bpart, B, IN_PLANES, err, gw, gb, st);
+    case 1: return launch_wgrad_tc<32, 32, 16>(in, dout, part, bpart, B, 32, err, gw, gb, st);
+    case 2: return launch_wgrad_tc<64, 32, 32>(in, dout, part, bpart, B, 32, err, gw, gb, st);
+    default: return launch_wgrad_tc<64, 64, 32>(in, dout, part, bpart, B, 64, err, gw, gb, st);
     }
 }
 
-int nblk(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b)); }
 
 // splitmix64 (Steele, Lea, Flood 2014) for the library's own initialisation and shuffles
 struct SplitMix {
@@ -843,7 +672,10 @@ static lbm_status ensure_work(lbm_surrogate *s, int B)
     if (e == cudaSuccess) e = cudaMalloc(&s->dpool, sizeof(float) * (size_t)B * 64);
     if (e == cudaSuccess) e = cudaMalloc(&s->grad, sizeof(float) * (size_t)LAYOUT.total);
     if (e == cudaSuccess) e = cudaMalloc(&s->loss, sizeof(float) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(float) * (size_t)B * 9 * 64 * 64);
+    // weight-gradient partials: one [HM][9][COUT][CIP] block (128 x 9 x 32 floats at most) per CTA
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) sms = sm_count(dev);
+    if (e == cudaSuccess) e = cudaMalloc(&s->part, sizeof(float) * (size_t)sms * 128 * 9 * 32);
     if (e == cudaSuccess) e = cudaMalloc(&s->bpart, sizeof(float) * (size_t)B * 64);
     if (e == cudaSuccess) e = cudaMalloc(&s->idx, sizeof(int) * (size_t)B);
     if (e != cudaSuccess) {
@@ -893,13 +725,9 @@ static cudaError_t backward(lbm_surrogate *s, int m, int B, cudaStream_t st)
     count_launches(2);
     int cur = 0;
     for (int l = NLAYER - 1; l >= 0; --l) {
-        int nparts = 0;
-        cudaError_t e = wgrad(l, s->act[l], s->dact[cur], s->part, s->bpart, B, &nparts, st);
+        cudaError_t e = wgrad(l, s->act[l], s->dact[cur], s->part, s->bpart, B, s->err, G + LAYOUT.w[l],
+                              G + LAYOUT.b[l], st);
         if (e != cudaSuccess) return e;
-        const int co = cout_of(l), ci = cin_real(l);
-        wgrad_reduce_kernel<<<nblk((int64_t)co * ci * 9 + co), 256, 0, st>>>(s->part, s->bpart, nparts, co, ci,
-                                                                           G + LAYOUT.w[l], G + LAYOUT.b[l]);
-        count_launches(2);
         if (l >= 1) {
             // dL/d(act_l) masked by act_l > 0: the masked gradient of layer l-1's output
             ConvArgs a{s->dact[cur], s->wb[l], nullptr, s->act[l], s->dact[1 - cur], B, s->err};

@@ -25,8 +25,8 @@
 //    TMA loads, warp 1 the MMAs, warps 2-5 drain the other TMEM buffer
 //    (epilogue: bias + ReLU for the forward pass, ReLU mask for the input
 //    gradient, which runs with flipped, transposed weights).
-//  * wgrad_kernel: weight gradient per (image, tap) on CUDA cores in FP32,
-//    written as per-image partials and folded in a fixed order (deterministic).
+//  * wgrad_tc_kernel: the weight gradient as an implicit GEMM over pixels on the
+//    tensor cores (see below), per-CTA partials folded in a fixed order.
 #pragma once
 
 #include "sm100_umma.cuh"
@@ -247,6 +247,186 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a)
             umma::fence_before();
             __syncwarp();
             if (lane == 0) umma::mbar_arrive(&tempty[b]);
+        }
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (tid == 0 && *s_fail) atomicExch(a.err, 1);
+    if (warp == 1) {
+        umma::fence_after();
+        umma::tmem_dealloc(tmem, S::TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------ weight gradient (tcgen05)
+//
+// dW[tap][co][ci] = sum over the pixels p of every image of dout[p][co] in[p + off(tap)][ci], as an
+// implicit GEMM on the tensor cores with K = pixels. Both operands come straight from the
+// activation layout (a pixel's 8 channels are 16 contiguous bytes), so they are MN-major: a core
+// matrix is 8 consecutive pixels (K) of 8 channels (M or N).
+//
+// One MMA has M = HM output rows x COUT channels of dout (HM = 128 / COUT) and N = HM + 2
+// consecutive padded input rows x CIP input channels, K = 16 pixels of a row. TMA lays both tiles
+// out row by row, [row][channel group][pixel][8], so the M and N core-matrix groups are evenly
+// spaced across rows: block (h, r) of the product pairs dout row y + h with padded input row y + r,
+// which is the vertical tap dy = r - h of output row y + h. Per dx (a 16-byte shift of the B
+// start address) one MMA therefore covers all three vertical taps of HM output rows (3 HM of the
+// HM (HM + 2) blocks are used: 3/4 for COUT = 64, 1/2 for COUT = 32). The three dx accumulators
+// take 3 N <= 384 TMEM columns for the whole run of a CTA.
+//
+// Work units are (half image, input-channel part of CIP channels); a CTA keeps one part and
+// takes every (grid / P)-th half image. Warp 0 issues the TMA loads (two stages), warp 1 the MMAs,
+// and warps 2-5 read the accumulators once at the end, writing one partial
+// [HM][9][COUT][CIP] per CTA (the rows h of a tap are separate partials), folded in a fixed order
+// by wgrad_tc_reduce_kernel.
+template <int COUT, int CIN_P, int CIP>
+struct WgtShape {
+    static constexpr int HM = 128 / COUT;                          // output rows per M tile
+    static constexpr int NR = HM + 2;                              // padded input rows per N tile
+    static constexpr int N = NR * CIP;
+    static constexpr int P = CIN_P / CIP;                          // input-channel parts
+    static constexpr int ROWS = IMG / 2;                           // output rows per work item
+    static constexpr uint32_t A_ROW = (COUT / 8) * IMG * 16;       // one dout row, all channel groups
+    static constexpr uint32_t A_BYTES = ROWS * A_ROW;
+    static constexpr uint32_t B_ROW = (CIP / 8) * HALO_W * 16;     // one padded input row
+    static constexpr uint32_t B_BYTES = (ROWS + 2) * B_ROW;
+    static constexpr uint32_t B_PAD = (B_BYTES + 127u) / 128u * 128u;
+    static constexpr uint32_t STAGE = A_BYTES + B_PAD;
+    // at least 116 KB so that only one CTA (and its 512 TMEM columns) fits on an SM
+    static constexpr uint32_t NEED = CTRL + 2 * STAGE + 128;
+    static constexpr uint32_t SMEM = NEED > 118784u ? NEED : 118784u;
+    static constexpr uint32_t TMEM_COLS = 512;
+    static_assert(HM * COUT == 128, "M = 128");
+    static_assert(N % 16 == 0 && N <= 256 && 3 * N <= (int)TMEM_COLS, "three accumulators fit TMEM");
+    static_assert(CIN_P % CIP == 0 && CIP % 8 == 0, "channel parts of whole groups");
+    static_assert(A_BYTES % 128 == 0, "stages stay 128-byte aligned");
+};
+
+struct WgtArgs {
+    float *part;                 // [grid][HM][9][COUT][CIP]
+    int nimg;
+    int *err;                    // set to 1 if a bounded wait gave up
+};
+
+template <int COUT, int CIN_P, int CIP>
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+wgrad_tc_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, WgtArgs a)
+{
+    using S = WgtShape<COUT, CIN_P, CIP>;
+    constexpr uint32_t IDESC = umma::idesc_bf16_f32_mn(128, S::N);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((128u - (umma::smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);      // [2] tiles landed (TMA bytes)
+    uint64_t *empty = full + 2;                               // [2] MMAs finished reading the stage
+    uint64_t *tfull = full + 4;                               // accumulators complete
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem + 64);
+    volatile int *s_fail = reinterpret_cast<volatile int *>(smem + 68);
+    uint8_t *stage0 = smem + CTRL;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int part = blockIdx.x % S::P, cstride = gridDim.x / S::P;
+    const int nitems = a.nimg * 2;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            umma::mbar_init(&full[i], 1);
+            umma::mbar_init(&empty[i], 1);
+        }
+        umma::mbar_init(tfull, 1);
+        umma::fence_mbar_init();
+        *s_fail = 0;
+        umma::prefetch_tmap(&tin);
+        umma::prefetch_tmap(&tout);
+    }
+    if (warp == 1) umma::tmem_alloc(s_taddr, S::TMEM_COLS);
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = *s_taddr;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int k = 0;
+            for (int item = blockIdx.x / S::P; item < nitems; item += cstride, ++k) {
+                const int b = k & 1;
+                if (k >= 2 && !umma::mbar_wait_bounded(&empty[b], ((k >> 1) - 1) & 1, WAIT_LIMIT)) {
+                    *s_fail = 1;
+                    break;
+                }
+                if (*s_fail) break;
+                const int img = item >> 1, y0 = (item & 1) * S::ROWS;
+                uint8_t *st = stage0 + b * S::STAGE;
+                umma::mbar_arrive_expect_tx(&full[b], S::A_BYTES + S::B_BYTES);
+                umma::tma_load_5d(st, &tout, &full[b], 0, 0, 0, y0, img);
+                umma::tma_load_5d(st + S::A_BYTES, &tin, &full[b], 0, -1, part * (CIP / 8), y0 - 1, img);
+            }
+            if (*s_fail)     // loads already issued land before shared memory is released
+                for (int kk = k - 2 < 0 ? 0 : k - 2; kk < k; ++kk)
+                    umma::mbar_wait_bounded(&full[kk & 1], (kk >> 1) & 1, WAIT_LIMIT);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int k = 0;
+            uint32_t acc = 0;
+            for (int item = blockIdx.x / S::P; item < nitems; item += cstride, ++k) {
+                const int b = k & 1;
+                if (!umma::mbar_wait_bounded(&full[b], (k >> 1) & 1, WAIT_LIMIT)) {
+                    *s_fail = 1;
+                    break;
+                }
+                if (*s_fail) break;
+                umma::fence_after();
+                const uint32_t a_base = umma::smem_addr(stage0 + b * S::STAGE);
+                const uint32_t b_base = a_base + S::A_BYTES;
+#pragma unroll 1
+                for (int rt = 0; rt < S::ROWS / S::HM; ++rt) {
+#pragma unroll
+                    for (int x0 = 0; x0 < IMG; x0 += 16) {
+                        const uint64_t ad = umma::desc(a_base + (uint32_t)(rt * S::HM) * S::A_ROW + x0 * 16, 128,
+                                                       IMG * 16);
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint64_t bd = umma::desc(b_base + (uint32_t)(rt * S::HM) * S::B_ROW + (x0 + dx) * 16,
+                                                           128, HALO_W * 16);
+                            umma::mma_bf16(tmem + (uint32_t)(dx * S::N), ad, bd, IDESC, acc);
+                        }
+                        acc = 1u;
+                    }
+                }
+                umma::commit(&empty[b]);
+            }
+            umma::commit(tfull);
+            // the last commits land before TMEM and shared memory are released
+            umma::mbar_wait_bounded(tfull, 0, WAIT_LIMIT);
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue, warps 2-5
+        const int q = warp & 3;                   // TMEM lane quarter: lanes 32 q .. 32 q + 31
+        const bool ok = umma::mbar_wait_bounded(tfull, 0, WAIT_LIMIT);
+        if (!__all_sync(0xffffffffu, ok)) {
+            *s_fail = 1;
+        } else if (!*s_fail) {
+            umma::fence_after();
+            const int L = 32 * q + lane, h = L / COUT, co = L % COUT;   // h is the same across a warp
+            float *dst = a.part + (int64_t)blockIdx.x * S::HM * 9 * COUT * CIP;
+#pragma unroll 1
+            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll 1
+                for (int r = 0; r < S::NR; ++r) {
+                    const int dy = r - h;
+                    if (dy < 0 || dy > 2) continue;            // warp-uniform
+                    float *o = dst + (((int64_t)h * 9 + dy * 3 + dx) * COUT + co) * CIP;
+#pragma unroll
+                    for (int c0 = 0; c0 < CIP; c0 += 16) {
+                        float v[16];
+                        umma::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(dx * S::N + r * CIP + c0), v);
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4 *>(o + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    }
+                }
         }
     }
     umma::fence_before();
