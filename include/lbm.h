@@ -228,14 +228,14 @@ lbm_status lbm_set_time_limit(double seconds);
  * obtains every K* by local LBM, Section 3): an ensemble of small CNNs maps a
  * subdomain's permeability patch to (log K*_xx, log K*_yy); local LBM stays the
  * fallback for doubtful patches and the arbiter of the surrogate's error.
- * Network per model: six 3x3 'same' convolutions 5 -> 32 -> 32 -> 64 -> 64 ->
+ * Network per model: six 3x3 'same' convolutions 9 -> 32 -> 32 -> 64 -> 64 ->
  * 64 -> 64 with ReLU, global average pooling, a 64 -> 2 linear head; BF16
  * activations and weights on the tensor cores with FP32 accumulation, FP32
- * master weights, Adam. Inputs are the five planes lbm_patches writes. */
+ * master weights, Adam. Inputs are the nine planes lbm_patches writes. */
 typedef struct lbm_surrogate lbm_surrogate;
 
 /* Number of FP32 parameters of one model; layout: for layer l = 0..5 the weights
- * [c_out][c_in][3][3] then the bias [c_out] (c_in = 5, 32, 32, 64, 64, 64;
+ * [c_out][c_in][3][3] then the bias [c_out] (c_in = 9, 32, 32, 64, 64, 64;
  * c_out = 32, 32, 64, 64, 64, 64), then the head [2][64] and its bias [2]. */
 int64_t lbm_surrogate_param_count(void);
 
@@ -261,15 +261,18 @@ lbm_status lbm_surrogate_get_normalization(const lbm_surrogate *s, float norm[13
 /* Leaf -> surrogate input. For each leaf (size s dividing 32, or a multiple of
  * 64 up to 1024) the leaf's log K is put on a 64 x 64 plane (each cell repeated
  * 64/s times per axis for s <= 32, the leaf itself for s = 64, the mean of log K
- * over (s/64)^2 blocks above) and x_dev[i] receives five float [32][32] planes:
+ * over (s/64)^2 blocks above) and x_dev[i] receives nine float [32][32] planes:
  * plane 2a + b holds that plane's cell (2 row + a, 2 column + b), so a 64-cell
- * leaf enters at full resolution, and plane 4 is the constant log2(s)/6.
- * stats_dev[i] = (mean, standard deviation, gradient energy) of the 32 x 32
- * mean of the four phase planes. kappa must be > 0. */
+ * leaf enters at full resolution; plane 4 is the constant log2(s)/6; planes 5-8
+ * are the context of the 32 x 32 mean of the four phase planes: the harmonic and
+ * the arithmetic mean of K along each of its rows (repeated across the row),
+ * then along each column (repeated down the column), as log K.
+ * stats_dev[i] = (mean, standard deviation, gradient energy) of that 32 x 32
+ * mean patch. kappa must be > 0. */
 lbm_status lbm_patches(const float *kappa_dev, int32_t nx, int32_t ny, const lbm_leaf *leaves_dev, int32_t n,
                        float *x_dev, float *stats_dev, void *cuda_stream);
 
-/* Trains every model on n samples x_dev [n][5][32][32] (lbm_patches), targets
+/* Trains every model on n samples x_dev [n][9][32][32] (lbm_patches), targets
  * y_dev [n][2] (log K*_xx, log K*_yy), stats_dev [n][3] from lbm_patches. The
  * networks learn (log K* - c) / w with the per-leaf base (c, w) of the target
  * mode (see lbm_surrogate_set_normalization), standardised; lbm_surrogate_predict
@@ -281,7 +284,7 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
                                int32_t n, int32_t epochs, int32_t batch, double lr, uint64_t seed, float *loss_host,
                                void *cuda_stream);
 
-/* Predictions of every model for inputs x_dev [n][5][32][32]:
+/* Predictions of every model for inputs x_dev [n][9][32][32]:
  * y_dev [n_models][n][2] = log K*_xx, log K*_yy. */
 lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n, float *y_dev, void *cuda_stream);
 

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-CHANNELS = (5, 32, 32, 64, 64, 64, 64)     # input planes: four phase planes of log K, leaf-size plane
+CHANNELS = (9, 32, 32, 64, 64, 64, 64)     # input planes: 4 phase planes, size plane, 4 context planes
 PATCH = 32
 PHASES = 4
 
@@ -73,12 +73,30 @@ def patch_stats(p: np.ndarray) -> np.ndarray:
     return np.array([p.mean(), p.std(), ge])
 
 
+def context_planes(p: np.ndarray) -> np.ndarray:
+    """Four 32 x 32 planes of row and column means of K = exp(p) over a 32 x 32 log-K patch p, in
+    log K: the harmonic and the arithmetic mean along x of each row (the same value across the
+    row), then the harmonic and the arithmetic mean along y of each column (the same value down
+    the column). These are the series and parallel means the layered arrangements are made of."""
+    k = np.exp(np.asarray(p, dtype=np.float64))
+    hx = -np.log(np.mean(1.0 / k, axis=1))
+    ax = np.log(np.mean(k, axis=1))
+    hy = -np.log(np.mean(1.0 / k, axis=0))
+    ay = np.log(np.mean(k, axis=0))
+    n = k.shape[0]
+    return np.stack([np.repeat(hx[:, None], n, axis=1), np.repeat(ax[:, None], n, axis=1),
+                     np.repeat(hy[None, :], n, axis=0), np.repeat(ay[None, :], n, axis=0)])
+
+
 def make_input(logk: np.ndarray, shift: float, scale: float) -> np.ndarray:
-    """Five input planes of a leaf: its four phase planes as (log K - shift) / scale and the
-    constant log2(size) / 6."""
-    x = np.empty((5, PATCH, PATCH))
-    x[:4] = (phase_planes(logk) - shift) / scale
+    """Nine input planes of a leaf: its four phase planes as (log K - shift) / scale, the
+    constant log2(size) / 6, and the four context planes of its 32 x 32 patch (resample_patch),
+    also as (log K - shift) / scale."""
+    x = np.empty((9, PATCH, PATCH))
+    ph = phase_planes(logk)
+    x[:4] = (ph - shift) / scale
     x[4] = np.log2(logk.shape[0]) / 6.0
+    x[5:] = (context_planes(ph.mean(axis=0)) - shift) / scale
     return x
 
 

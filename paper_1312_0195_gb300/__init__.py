@@ -221,12 +221,12 @@ def lbm_block_average(field, block: int, out=None, stream=None):
     return out
 
 
-SURROGATE_PLANES = 5          # input planes per leaf (lbm_patches)
+SURROGATE_PLANES = 9          # input planes per leaf (lbm_patches)
 
 
 def lbm_patches(kappa, leaves, x=None, stats=None, stream=None):
-    """Surrogate inputs for leaves: x [n, 5, 32, 32] (four phase planes of log K and the size plane)
-    and stats [n, 3] (CUDA float32)."""
+    """Surrogate inputs for leaves: x [n, 9, 32, 32] (four phase planes of log K, the size plane, four
+    context planes) and stats [n, 3] (CUDA float32)."""
     import torch
     ny, nx = kappa.shape
     n = int(leaves.shape[0])

@@ -57,13 +57,15 @@ __host__ __device__ inline bool patch_size_ok(int s)
     return (s >= 1 && s <= IMG && IMG % s == 0) || (s >= 64 && s <= 1024 && s % 64 == 0);
 }
 
-// Leaf -> the five input planes [n][5][32][32] and (mean, std, gradient energy) of its 32 x 32
+// Leaf -> the nine input planes [n][9][32][32] and (mean, std, gradient energy) of its 32 x 32
 // log-K patch. The leaf's log K is first put on a 64 x 64 plane (each cell repeated 64 / s times
 // per axis for s <= 32, the leaf itself for s = 64, means of log K over (s / 64)^2 blocks above);
 // phase plane 2 a + b holds that plane's cell (2 i + a, 2 j + b) at (i, j). Plane 4 is the
 // constant log2(s) / 6. The 32 x 32 patch the statistics describe is the mean of the four phase
-// planes (the leaf itself for s <= 32, its 2 x 2 block means for s = 64). One CTA per leaf; an
-// invalid leaf (size, or not inside the field) gets zero planes and sets *bad (may be NULL).
+// planes (the leaf itself for s <= 32, its 2 x 2 block means for s = 64). Planes 5-8 are its
+// context: the harmonic and arithmetic means of K along each row of that patch, then along each
+// column, in log K, repeated across the row or down the column. One CTA per leaf; an invalid leaf
+// (size, or not inside the field) gets zero planes and sets *bad (may be NULL).
 __global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, int ny, const int *leaves,
                                                    float *x, float *stats, int *bad)
 {
@@ -108,6 +110,29 @@ __global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, 
         p[q] = 0.25f * ((v[0] + v[1]) + (v[2] + v[3]));
     }
     __syncthreads();
+    // context planes: harmonic and arithmetic means of K = exp(p) along each row and each column
+    __shared__ double rk[IMG], ri[IMG], ck[IMG], ci[IMG];
+    if (threadIdx.x < IMG) {
+        const int r = threadIdx.x;
+        double a = 0.0, b = 0.0;
+        for (int c = 0; c < IMG; ++c) { a += exp((double)p[r * IMG + c]); b += exp(-(double)p[r * IMG + c]); }
+        rk[r] = a;
+        ri[r] = b;
+    } else if (threadIdx.x < 2 * IMG) {
+        const int c = threadIdx.x - IMG;
+        double a = 0.0, b = 0.0;
+        for (int r = 0; r < IMG; ++r) { a += exp((double)p[r * IMG + c]); b += exp(-(double)p[r * IMG + c]); }
+        ck[c] = a;
+        ci[c] = b;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < PIX; q += blockDim.x) {
+        const int py = q >> 5, px = q & 31;
+        xi[5 * PIX + q] = (float)(-log(ri[py] / IMG));
+        xi[6 * PIX + q] = (float)log(rk[py] / IMG);
+        xi[7 * PIX + q] = (float)(-log(ci[px] / IMG));
+        xi[8 * PIX + q] = (float)log(ck[px] / IMG);
+    }
     double sm = 0.0, sq = 0.0, ge = 0.0;
     for (int q = threadIdx.x; q < PIX; q += blockDim.x) {
         const int py = q >> 5, px = q & 31;
@@ -136,8 +161,8 @@ __global__ void __launch_bounds__(256) patch_kernel(const float *kappa, int nx, 
     }
 }
 
-// FP32 input planes [n][5][32][32] (rows idx[b]) -> BF16 16-channel activation (act_at layout):
-// channels 0-3 the phase planes as (x - shift) / scale, channel 4 the size plane as is, 5-15 zero.
+// FP32 input planes [n][9][32][32] (rows idx[b]) -> BF16 16-channel activation (act_at layout):
+// channels 0-3 and 5-8 (log-K planes) as (x - shift) / scale, channel 4 (size) as is, 9-15 zero.
 __global__ void __launch_bounds__(256) input_kernel(const float *x, const int *idx, int B, float shift, float scale,
                                                    __nv_bfloat16 *out)
 {
@@ -148,8 +173,10 @@ __global__ void __launch_bounds__(256) input_kernel(const float *x, const int *i
         uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
         __nv_bfloat16 *ob = reinterpret_cast<__nv_bfloat16 *>(o);
 #pragma unroll
-        for (int ph = 0; ph < 4; ++ph) ob[ph] = __float2bfloat16_rn((x[src + ph * PIX + q] - shift) / scale);
-        ob[4] = __float2bfloat16_rn(x[src + 4 * PIX + q]);
+        for (int c = 0; c < IN_PLANES; ++c) {
+            const float v = x[src + c * PIX + q];
+            ob[c] = __float2bfloat16_rn(c == 4 ? v : (v - shift) / scale);
+        }
         *reinterpret_cast<uint4 *>(out + act_at(b, q, 0, CIN0)) = o[0];
         *reinterpret_cast<uint4 *>(out + act_at(b, q, 8, CIN0)) = o[1];
     }
@@ -318,7 +345,7 @@ __global__ void __launch_bounds__(256) adam_kernel(float *p, const float *g, flo
     }
 }
 
-// Sum and sum of squares of the log-K phase planes of x [n][5][32][32], per block (fixed order).
+// Sum and sum of squares of the log-K phase planes of x [n][9][32][32], per block (fixed order).
 __global__ void __launch_bounds__(256) input_moments_kernel(const float *x, int n, double *part)
 {
     double s = 0.0, q = 0.0;
@@ -951,7 +978,7 @@ lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n
     return r;
 }
 
-// Trains every model of the ensemble on n samples: inputs x_dev [n][5][32][32]
+// Trains every model of the ensemble on n samples: inputs x_dev [n][9][32][32]
 // (lbm_patches), targets y_dev [n][2] = log K*_xx, log K*_yy. The networks learn
 // (log K* - c) / w, standardised, with the per-patch base (c, w) of the target
 // mode (patch_base_kernel; mode 2 unless set before training). Sets the input and target

@@ -3,11 +3,13 @@
 // small CNN predicts log K*_xx and log K*_yy from the subdomain's permeability
 // patch and local LBM remains the fallback and the arbiter of its error).
 //
-// Network: six 3x3 'same' convolutions 5(->16 padded) -> 32 -> 32 -> 64 -> 64 ->
+// Network: six 3x3 'same' convolutions 9(->16 padded) -> 32 -> 32 -> 64 -> 64 ->
 // 64 -> 64 with ReLU, global average pooling over the 32 x 32 patch, a linear
-// head to 2 outputs. The five input planes are the leaf's log K on a 64 x 64
+// head to 2 outputs. The nine input planes are the leaf's log K on a 64 x 64
 // plane split into four 32 x 32 phase planes by row and column parity (so a
-// 64-cell leaf enters at full resolution) and the constant log2(size) / 6. Activations are BF16 in channel-group planes
+// 64-cell leaf enters at full resolution), the constant log2(size) / 6, and
+// four context planes: the harmonic and arithmetic means of K along each row
+// and along each column of the 32 x 32 patch, in log K, broadcast across it. Activations are BF16 in channel-group planes
 // [B][C/8][32][32][8] (act_at below); FP32 master weights; accumulation in FP32.
 //
 //  * conv3x3_tc_kernel: implicit GEMM on the tensor cores (tcgen05, TMEM, TMA)
@@ -39,8 +41,8 @@ namespace sur {
 constexpr int IMG = 32;                  // patch side
 constexpr int PIX = IMG * IMG;           // pixels per patch
 constexpr int NLAYER = 6;
-constexpr int IN_PLANES = 5;             // four phase planes of log K, the size plane
-constexpr int CIN0 = 16;                 // padded input planes of layer 0 (5 used)
+constexpr int IN_PLANES = 9;             // four phase planes of log K, the size plane, four context planes
+constexpr int CIN0 = 16;                 // padded input planes of layer 0 (9 used)
 __host__ __device__ constexpr int cin_p(int l) { return l == 0 ? 16 : (l <= 2 ? 32 : 64); }
 __host__ __device__ constexpr int cin_real(int l) { return l == 0 ? IN_PLANES : (l <= 2 ? 32 : 64); }
 __host__ __device__ constexpr int cout_of(int l) { return l <= 1 ? 32 : 64; }

@@ -75,14 +75,14 @@ def _leaves_logk(n, seed):
 
 
 def _inputs(n, seed, leaves=None):
-    """Surrogate inputs [n, 5, 32, 32] of the oracle (phase planes unnormalised, size plane)."""
+    """Surrogate inputs [n, 9, 32, 32] of the oracle (log-K planes unnormalised)."""
     leaves = _leaves_logk(n, seed) if leaves is None else leaves
     return np.stack([S.make_input(lk, 0.0, 1.0) for lk in leaves]).astype(np.float32)
 
 
 def test_param_count_matches_oracle_layout():
     lbm = _lbm()
-    assert lbm.lbm_surrogate_param_count() == _flat(S.init_params(0)).size == 140130
+    assert lbm.lbm_surrogate_param_count() == _flat(S.init_params(0)).size == 141282
 
 
 def test_single_image_forward_matches_oracle():
@@ -156,9 +156,10 @@ def test_adam_step_matches_oracle():
 
 
 def test_patches_match_oracle():
-    """Five planes per leaf against the oracle: the four phase planes of the leaf's 64 x 64 log-K
+    """Nine planes per leaf against the oracle: the four phase planes of the leaf's 64 x 64 log-K
     plane (a 64-cell leaf at full resolution, a 128-cell one as 2 x 2 means, smaller ones
-    repeated), the size plane, and the statistics of the 32 x 32 mean patch."""
+    repeated), the size plane, the four row and column context planes, and the statistics of the
+    32 x 32 mean patch."""
     import torch
     lbm = _lbm()
     kap = synth.lognormal_kappa(128, 128, 6.0, 1.5, seed=9).astype(np.float32)
@@ -170,6 +171,9 @@ def test_patches_match_oracle():
         lk = np.log(kap[y0:y0 + s, x0:x0 + s].astype(np.float64))
         np.testing.assert_allclose(x[i, :4], S.phase_planes(lk), rtol=1e-5, atol=1e-5)
         np.testing.assert_allclose(x[i, 4], np.log2(s) / 6.0, rtol=1e-6)
+        # context of the FP32 mean patch the device forms
+        pm = x[i, :4].astype(np.float64).mean(axis=0)
+        np.testing.assert_allclose(x[i, 5:], S.context_planes(pm), rtol=1e-5, atol=1e-5)
         np.testing.assert_allclose(st[i], S.patch_stats(S.resample_patch(lk)), rtol=1e-4, atol=1e-5)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_patches(_t(kap), torch.tensor([[0, 0, 96]], dtype=torch.int32, device="cuda"))
@@ -279,6 +283,7 @@ def test_predict_full_batch_matches_oracle():
     shift, scale, m0, s0, m1, s1 = -4.0, 1.3, 0.2, 0.7, -0.1, 0.9
     xn = x.copy()
     xn[:, :4] = (x[:, :4] - shift) / scale
+    xn[:, 5:] = (x[:, 5:] - shift) / scale
     with lbm.Surrogate(2, 0) as sur:
         c, w = _base_from_predict(sur, x, 2, n_models=2)
         sur.set_params(0, _flat(pa))

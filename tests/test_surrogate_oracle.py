@@ -80,7 +80,7 @@ def test_resample_and_stats():
 
 def test_forward_shapes_and_pool_linearity():
     p = S.init_params(1)
-    x = RNG.standard_normal((2, 5, 32, 32))
+    x = RNG.standard_normal((2, 9, 32, 32))
     y, (acts, pooled) = S.forward(p, x)
     assert y.shape == (2, 2) and pooled.shape == (2, 64) and len(acts) == 7
     np.testing.assert_allclose(y, pooled @ p["wh"].T + p["bh"], rtol=1e-14)
@@ -110,6 +110,7 @@ def test_phase_planes_carry_every_cell():
             S.phase_planes(np.zeros((bad, bad)))
     x = S.make_input(np.log(np.full((16, 16), 0.01)), np.log(0.01), 2.0)
     assert np.array_equal(x[:4], np.zeros((4, 32, 32))) and np.all(x[4] == 4.0 / 6.0)
+    assert np.abs(x[5:]).max() < 1e-15
 
 
 def test_layered_bounds_reproduce_tables_1_and_2():
@@ -199,3 +200,24 @@ def test_gate_hand_made_spreads():
     # a single member has no spread
     acc4, keff4 = S.gate(y[:1, :1], st[:1], np.array([32]), lo, hi, 1e-9)
     assert acc4.tolist() == [True] and keff4[0, 0] == np.exp(y[0, 0, 0])
+
+
+def test_context_planes_are_row_and_column_means():
+    """A patch of layers across x: every row has the same series (harmonic) and parallel
+    (arithmetic) mean along x; each column is uniform, so its means along y are its own value.
+    Checked against scipy's means; transposing the patch exchanges the row and column planes."""
+    stats = pytest.importorskip("scipy.stats")
+    layers = np.exp(RNG.uniform(-6.0, 0.0, 32))
+    p = np.tile(np.log(layers), (32, 1))
+    c = S.context_planes(p)
+    np.testing.assert_allclose(c[0], np.log(stats.hmean(layers)), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(c[1], np.log(np.mean(layers)), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(c[2], p, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(c[3], p, rtol=0, atol=1e-13)
+    q = RNG.normal(-3.0, 1.0, (32, 32))
+    a, b = S.context_planes(q), S.context_planes(q.T.copy())
+    np.testing.assert_allclose(b[0], a[2].T, rtol=1e-13)
+    np.testing.assert_allclose(b[3], a[1].T, rtol=1e-13)
+    x = S.make_input(q, -3.0, 2.0)
+    assert x.shape == (9, 32, 32)
+    np.testing.assert_allclose(x[5:], (a - (-3.0)) / 2.0, rtol=1e-14)
