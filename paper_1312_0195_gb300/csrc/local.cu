@@ -104,10 +104,10 @@ __device__ __forceinline__ double coef_e(float k, double eps_nu)
 
 // Per-slot values every cell reads each step, packed for one 16-byte shared load.
 struct SlotHot {
-    int tstart;       // CTA step counter at the job's step 0 (differences taken modulo 2^32)
+    int tstart;       // CTA step of the job's step 0 (always even; differences taken modulo 2^32)
     int next_check;   // job step of the next steady-state check
-    int flags;        // bit 0: active, bit 1: driven along y
-    int pad;
+    int flags;        // bit 0: active, bit 1: driven along y, bit 2: cells not yet set up
+    int store;        // CTA step at which the cells store their velocity: tstart + min(next_check, max_steps)
 };
 
 // Collision constants (host-computed in the storage precision, so the FMAs read them from the
@@ -132,8 +132,9 @@ template <> __device__ __forceinline__ double kc<double>(const LocalArgs &a, int
 // rho u = (1 - e) r, rho u_eq = 2 tau rho u + (1 - 2 tau) j, g_eq = w_a (drho + 3 e_a . rho u_eq),
 // and BGK as g + omega (g_eq - g): the difference is formed first, so the rounding of the update
 // stays at the size of the non-equilibrium part (FP32 solves in the Darcy regime depend on it).
-// Returns rho u and rho.
-template <typename T>
+// TAU1: tau = 1 exactly, where Eq. 16 reads rho u_eq = 2 rho u - j and Eq. 13 with omega = 1
+// leaves the equilibrium itself, so g_eq is stored directly. Returns rho u and rho.
+template <typename T, bool TAU1>
 __device__ __forceinline__ void collide_d2q9(T (&g)[Q], T e, T hgx, T hgy, const LocalArgs &a, T &rux, T &ruy,
                                              T &rho)
 {
@@ -146,23 +147,97 @@ __device__ __forceinline__ void collide_d2q9(T (&g)[Q], T e, T hgx, T hgy, const
     const T rx = fma(hgx, rho, jx), ry = fma(hgy, rho, jy);
     rux = fma(-e, rx, rx);
     ruy = fma(-e, ry, ry);
-    const T uex = fma(kc<T>(a, K_TWO_TAU), rux, kc<T>(a, K_OMT) * jx);
-    const T uey = fma(kc<T>(a, K_TWO_TAU), ruy, kc<T>(a, K_OMT) * jy);
-    const T om = kc<T>(a, K_OMEGA);
+    T uex, uey;
+    if constexpr (TAU1) {
+        uex = fma(T(2), rux, -jx);
+        uey = fma(T(2), ruy, -jy);
+    } else {
+        uex = fma(kc<T>(a, K_TWO_TAU), rux, kc<T>(a, K_OMT) * jx);
+        uey = fma(kc<T>(a, K_TWO_TAU), ruy, kc<T>(a, K_OMT) * jy);
+    }
     const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
     const T tx = T(3) * uex, ty = T(3) * uey, sp = tx + ty, sm = tx - ty;
-    g[0] = fma(om, T(4.0 / 9.0) * drho - g[0], g[0]);
-    g[1] = fma(om, w1 * (drho + tx) - g[1], g[1]);
-    g[3] = fma(om, w1 * (drho - tx) - g[3], g[3]);
-    g[2] = fma(om, w1 * (drho + ty) - g[2], g[2]);
-    g[4] = fma(om, w1 * (drho - ty) - g[4], g[4]);
-    g[5] = fma(om, w2 * (drho + sp) - g[5], g[5]);
-    g[7] = fma(om, w2 * (drho - sp) - g[7], g[7]);
-    g[8] = fma(om, w2 * (drho + sm) - g[8], g[8]);
-    g[6] = fma(om, w2 * (drho - sm) - g[6], g[6]);
+    if constexpr (TAU1) {
+        g[0] = T(4.0 / 9.0) * drho;
+        g[1] = w1 * (drho + tx);
+        g[3] = w1 * (drho - tx);
+        g[2] = w1 * (drho + ty);
+        g[4] = w1 * (drho - ty);
+        g[5] = w2 * (drho + sp);
+        g[7] = w2 * (drho - sp);
+        g[8] = w2 * (drho + sm);
+        g[6] = w2 * (drho - sm);
+    } else {
+        const T om = kc<T>(a, K_OMEGA);
+        g[0] = fma(om, T(4.0 / 9.0) * drho - g[0], g[0]);
+        g[1] = fma(om, w1 * (drho + tx) - g[1], g[1]);
+        g[3] = fma(om, w1 * (drho - tx) - g[3], g[3]);
+        g[2] = fma(om, w1 * (drho + ty) - g[2], g[2]);
+        g[4] = fma(om, w1 * (drho - ty) - g[4], g[4]);
+        g[5] = fma(om, w2 * (drho + sp) - g[5], g[5]);
+        g[7] = fma(om, w2 * (drho - sp) - g[7], g[7]);
+        g[8] = fma(om, w2 * (drho + sm) - g[8], g[8]);
+        g[6] = fma(om, w2 * (drho - sm) - g[6], g[6]);
+    }
 }
 
-template <typename T>
+// One lattice step of every active slot; ODD selects the half of the AA pattern. Job starts are
+// aligned to even CTA steps, so the parity of a job's step is the CTA step's, the same for all.
+template <typename T, bool TAU1, bool ODD>
+__device__ __forceinline__ void local_step(T *F, const T *D, T *UX, T *UY, const int4 *hot, const int (&cgeo)[LocalCfg<T>::CPT],
+                                           int s, int s2, unsigned Tcta, T hg, const LocalArgs &a, int tid)
+{
+    constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT;
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int geo = cgeo[i];
+        if (geo < 0) continue;
+        const int4 h = hot[geo >> 12];
+        if (!(h.z & 1)) continue;
+        const int c = tid + i * LOCAL_THREADS;
+        T g[Q];
+        // odd steps: the 8 neighbours with periodic closure on the leaf; cell x - e_a is read for
+        // population a and cell x + e_a written, so each index serves both
+        int n1 = 0, n2 = 0, n3 = 0, n4 = 0, n5 = 0, n6 = 0, n7 = 0, n8 = 0;
+        if constexpr (!ODD) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) g[q] = F[q * CMAX + c];
+        } else {
+            const int cly = (geo >> 6) & 63, clx = geo & 63;
+            const int row = c - clx;                                  // cell (0, cly) of the slot
+            const int xm = (clx == 0 ? s : clx) - 1, xp = clx + 1 == s ? 0 : clx + 1;
+            const int rm = cly == 0 ? row + s2 - s : row - s;        // row y - 1
+            const int rp = cly + 1 == s ? row - s2 + s : row + s;    // row y + 1
+            n1 = row + xp; n3 = row + xm; n2 = rp + clx; n4 = rm + clx;     // x + e_a for a = 1..4
+            n5 = rp + xp; n6 = rp + xm; n7 = rm + xm; n8 = rm + xp;         // a = 5..8
+            g[0] = F[c];
+            g[1] = F[3 * CMAX + n3]; g[3] = F[1 * CMAX + n1];
+            g[2] = F[4 * CMAX + n4]; g[4] = F[2 * CMAX + n2];
+            g[5] = F[7 * CMAX + n7]; g[7] = F[5 * CMAX + n5];
+            g[6] = F[8 * CMAX + n8]; g[8] = F[6 * CMAX + n6];
+        }
+        const T e = D[c];
+        const bool along_y = (h.z & 2) != 0;
+        T rux, ruy, rho;
+        collide_d2q9<T, TAU1>(g, e, along_y ? T(0) : hg, along_y ? hg : T(0), a, rux, ruy, rho);
+        if (Tcta == (unsigned)h.w) {
+            UX[c] = rux / rho;                                   // Eq. 15
+            UY[c] = ruy / rho;
+        }
+        if constexpr (!ODD) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) F[opp(q) * CMAX + c] = g[q];
+        } else {
+            F[c] = g[0];
+            F[1 * CMAX + n1] = g[1]; F[3 * CMAX + n3] = g[3];
+            F[2 * CMAX + n2] = g[2]; F[4 * CMAX + n4] = g[4];
+            F[5 * CMAX + n5] = g[5]; F[7 * CMAX + n7] = g[7];
+            F[6 * CMAX + n6] = g[6]; F[8 * CMAX + n8] = g[8];
+        }
+    }
+}
+
+template <typename T, bool TAU1>
 __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs a)
 {
     constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT;
@@ -174,15 +249,15 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
     __shared__ Slot slots[MAXSLOTS];
     __shared__ int4 hot[MAXSLOTS];            // SlotHot
     __shared__ int s_abort;
-    __shared__ unsigned s_event;              // CTA step of the next check of any slot
+    __shared__ unsigned s_event;              // CTA step of the next velocity store of any slot
 
     __shared__ int s_nclass, s_csize[MAXCLASS], s_coff[MAXCLASS + 1];
+    __shared__ unsigned long long s_t0;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned long long t0 = globaltimer();
-    const int max_steps = (int)a.max_steps;
     const T hg = kc<T>(a, K_HG);
     if (tid == 0) {
+        s_t0 = globaltimer();
         s_abort = 0;
         if (a.table) {      // built on the device by an earlier kernel of the same stream
             const int nc = a.table[DT_BAD] ? 0 : a.table[DT_NCLASS];
@@ -208,7 +283,6 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
         int nslots = CMAX / s2;
         if (nslots > MAXSLOTS) nslots = MAXSLOTS;
         const int ncell = nslots * s2;
-        const int qbeg = s_coff[cls], qn = s_coff[cls + 1] - qbeg;
 
         // per-thread cell geometry for this size class, packed as slot << 12 | ly << 6 | lx
         int cgeo[CPT];
@@ -225,10 +299,11 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
             }
         }
         __syncthreads();
-        unsigned Tcta = 0;           // CTA step counter
+        unsigned Tcta = 0;           // CTA step counter: the next step to run
         if (tid < nslots) {
             Slot sl;
             sl.job = -1;
+            const int qbeg = s_coff[cls], qn = s_coff[cls + 1] - qbeg;
             int q = s_abort ? qn : atomicAdd(&a.heads[cls], 1);
             if (q < qn) {
                 sl.job = a.jobs[qbeg + q];
@@ -239,173 +314,157 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 sl.prev = 0.0;
             }
             slots[tid] = sl;
-            hot[tid] = make_int4(0, a.check_every, sl.job >= 0 ? 1 | (sl.drive << 1) : 0, 0);
+            hot[tid] = make_int4(0, a.check_every, sl.job >= 0 ? 1 | (sl.drive << 1) | 4 : 0,
+                                 min(a.check_every, (int)a.max_steps));
         }
-        if (tid == 0) s_event = (unsigned)min(a.check_every, max_steps);
-        int any = __syncthreads_or(tid < nslots && hot[tid].z);
+        if (tid == 0) s_event = (unsigned)min(a.check_every, (int)a.max_steps);
+        bool fresh = true;           // some slot was just (re)filled: set its cells up before stepping
 
-        while (any) {
-            // ---------------------------------------------------------- one step
+        for (;;) {
+            if (fresh) {
+                // rest state (zero deviations) and the drag fraction of the cells of new jobs
+                __syncthreads();
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                const int geo = cgeo[i];
-                if (geo < 0) continue;
-                const int j = geo >> 12, cly = (geo >> 6) & 63, clx = geo & 63;
-                const int4 h = hot[j];
-                if (!(h.z & 1)) continue;
-                const int t = (int)(Tcta - (unsigned)h.x);
-                const int c = tid + i * LOCAL_THREADS;
-                T g[Q];
-                // odd steps: the 8 neighbours with periodic closure on the leaf; cell x - e_a is
-                // read for population a and cell x + e_a written, so each index serves both
-                int n1 = 0, n2 = 0, n3 = 0, n4 = 0, n5 = 0, n6 = 0, n7 = 0, n8 = 0;
-                if (t == 0) {
+                for (int i = 0; i < CPT; ++i) {
+                    const int geo = cgeo[i];
+                    if (geo < 0) continue;
+                    const int j = geo >> 12;
+                    if (!(hot[j].z & 4)) continue;
+                    const int c = tid + i * LOCAL_THREADS;
                     // patch origin may lie outside the field when oversampling: periodic wrap
-                    int gx = slots[j].x0 + clx, gy = slots[j].y0 + cly;
+                    int gx = slots[j].x0 + (geo & 63), gy = slots[j].y0 + ((geo >> 6) & 63);
                     gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
                     gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
                     D[c] = (T)coef_e(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) g[q] = T(0);      // rest state
-                } else if ((t & 1) == 0) {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) g[q] = F[q * CMAX + c];
-                } else {
-                    const int row = c - clx;                                  // cell (0, cly) of the slot
-                    const int xm = (clx == 0 ? s : clx) - 1, xp = clx + 1 == s ? 0 : clx + 1;
-                    const int rm = cly == 0 ? row + s2 - s : row - s;        // row y - 1
-                    const int rp = cly + 1 == s ? row - s2 + s : row + s;    // row y + 1
-                    n1 = row + xp; n3 = row + xm; n2 = rp + clx; n4 = rm + clx;     // x + e_a for a = 1..4
-                    n5 = rp + xp; n6 = rp + xm; n7 = rm + xm; n8 = rm + xp;         // a = 5..8
-                    g[0] = F[c];
-                    g[1] = F[3 * CMAX + n3]; g[3] = F[1 * CMAX + n1];
-                    g[2] = F[4 * CMAX + n4]; g[4] = F[2 * CMAX + n2];
-                    g[5] = F[7 * CMAX + n7]; g[7] = F[5 * CMAX + n5];
-                    g[6] = F[8 * CMAX + n8]; g[8] = F[6 * CMAX + n6];
+                    for (int q = 0; q < Q; ++q) F[q * CMAX + c] = T(0);
                 }
-                const T e = D[c];
-                const bool along_y = (h.z & 2) != 0;
-                T rux, ruy, rho;
-                collide_d2q9<T>(g, e, along_y ? T(0) : hg, along_y ? hg : T(0), a, rux, ruy, rho);
-                if (t == h.y || t == max_steps) {
-                    UX[c] = rux / rho;                                   // Eq. 15
-                    UY[c] = ruy / rho;
-                }
-                if ((t & 1) == 0) {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) F[opp(q) * CMAX + c] = g[q];
-                } else {
-                    F[c] = g[0];
-                    F[1 * CMAX + n1] = g[1]; F[3 * CMAX + n3] = g[3];
-                    F[2 * CMAX + n2] = g[2]; F[4 * CMAX + n4] = g[4];
-                    F[5 * CMAX + n5] = g[5]; F[7 * CMAX + n7] = g[7];
-                    F[6 * CMAX + n6] = g[6]; F[8 * CMAX + n8] = g[8];
+                __syncthreads();
+                if (tid < nslots) hot[tid].z &= ~4;
+            }
+            if (!__syncthreads_or(tid < nslots && (hot[tid].z & 1))) break;
+
+            // ------------------------------------------------------ two steps (even, odd)
+            local_step<T, TAU1, false>(F, D, UX, UY, hot, cgeo, s, s2, Tcta, hg, a, tid);
+            ++Tcta;
+            __syncthreads();
+            local_step<T, TAU1, true>(F, D, UX, UY, hot, cgeo, s, s2, Tcta, hg, a, tid);
+            ++Tcta;
+            __syncthreads();
+
+            // ------------------------------------- bookkeeping, only after a velocity store
+            // (and every 256 steps for the wall-clock limit); s_event is uniform
+            fresh = false;
+            if ((int)(Tcta - s_event) <= 0 && (Tcta & 255u) != 0) continue;
+            if (tid == 0 && !s_abort) {
+                if (*(volatile int *)a.abort_flag) s_abort = 1;
+                else if (globaltimer() - s_t0 > a.time_limit_ns) {
+                    s_abort = 1;
+                    atomicExch(a.abort_flag, 1);
                 }
             }
             __syncthreads();
-
-            // ------------------------------------- bookkeeping, only at check steps
-            // (and every 256 steps for the wall-clock limit); s_event is uniform
-            if (Tcta == s_event || (Tcta & 255u) == 255u) {
-                if (tid == 0 && !s_abort) {
-                    if (*(volatile int *)a.abort_flag) s_abort = 1;
-                    else if (globaltimer() - t0 > a.time_limit_ns) {
-                        s_abort = 1;
-                        atomicExch(a.abort_flag, 1);
-                    }
-                }
-                __syncthreads();
-                const bool abort_now = s_abort != 0;
-                for (int j = wid; j < nslots; j += LOCAL_THREADS / 32) {
-                    int4 h = hot[j];
-                    if (!(h.z & 1)) continue;
-                    Slot sl = slots[j];
-                    const int t = (int)(Tcta - (unsigned)h.x);
-                    const bool check = t == h.y || t == max_steps;
-                    if (!check && !abort_now) continue;
-                    int st = -1;   // -1: keep going
-                    double ux = 0.0, uy = 0.0;
-                    if (check) {
-                        // mean over the leaf: all s2 cells, or the inner window when oversampling
-                        const int m = a.margin, hi = s - m;
-                        for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
-                            const int loc = c - j * s2, ly = loc / s, lx = loc - ly * s;
-                            if (m == 0 || (lx >= m && lx < hi && ly >= m && ly < hi)) {
-                                ux += (double)UX[c];
-                                uy += (double)UY[c];
-                            }
-                        }
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) {
-                            ux += __shfl_xor_sync(0xffffffffu, ux, off);
-                            uy += __shfl_xor_sync(0xffffffffu, uy, off);
-                        }
-                        const double inner = (double)(s - 2 * a.margin) * (double)(s - 2 * a.margin);
-                        ux /= inner;
-                        uy /= inner;
-                        const double cur = sl.drive == 0 ? ux : uy;
-                        const bool regular = t == h.y;
-                        if (regular) h.y += a.check_every;
-                        if (a.tol > 0.0 && t > a.check_every && regular &&
-                            fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur))
-                            st = LBM_OK;
-                        else if (t == max_steps)
-                            st = a.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
-                        sl.prev = cur;
-                    }
-                    if (abort_now && st < 0) st = LBM_ETIMEOUT;
-                    if (lane == 0) {
-                        if (st >= 0) {
-                            // Eq. 17: column `drive` of K* from the mean velocity (NaN if abandoned unchecked)
-                            const double kx = check ? a.nu_over_g * ux : __longlong_as_double(0x7ff8000000000000LL);
-                            const double ky = check ? a.nu_over_g * uy : __longlong_as_double(0x7ff8000000000000LL);
-                            a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 0 : 1)] = kx;
-                            a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 2 : 3)] = ky;
-                            if (a.steps) a.steps[2 * (int64_t)sl.leaf + sl.drive] = t;
-                            if (st != LBM_OK) {
-                                atomicMax(&a.status[sl.leaf], st);
-                                atomicMax(a.worst, st);
-                            }
-                            // refill the slot from this size's queue
-                            int q = abort_now ? qn : atomicAdd(&a.heads[cls], 1);
-                            if (q < qn) {
-                                sl.job = a.jobs[qbeg + q];
-                                sl.leaf = sl.job >> 1;
-                                sl.drive = sl.job & 1;
-                                sl.x0 = a.leaves[3 * sl.leaf] - a.margin;
-                                sl.y0 = a.leaves[3 * sl.leaf + 1] - a.margin;
-                                sl.prev = 0.0;
-                                h = make_int4((int)(Tcta + 1u), a.check_every, 1 | (sl.drive << 1), 0);
-                            } else {
-                                sl.job = -1;
-                                h.z = 0;
-                            }
-                        }
-                        slots[j] = sl;
-                        hot[j] = h;
-                    }
-                    __syncwarp();
-                }
-                __syncthreads();   // slot updates of every warp are visible before they are read
-                // next event: the earliest step at which an active slot reaches min(next check, max_steps)
-                if (wid == 0) {
-                    unsigned best = 0xffffffffu;
-                    for (int j = lane; j < nslots; j += 32) {
-                        const int4 h = hot[j];
-                        if (h.z & 1) {
-                            const int t = (int)(Tcta - (unsigned)h.x);
-                            best = min(best, (unsigned)(min(h.y, max_steps) - t));
+            const bool abort_now = s_abort != 0;
+            for (int j = wid; j < nslots; j += LOCAL_THREADS / 32) {
+                int4 h = hot[j];
+                if (!(h.z & 1)) continue;
+                Slot sl = slots[j];
+                const bool check = (int)(Tcta - (unsigned)h.w) > 0;     // the store step has run
+                if (!check && !abort_now) continue;
+                // job step of the check (or, abandoned unchecked, the step reached)
+                const int t = (int)((check ? (unsigned)h.w : Tcta) - (unsigned)h.x);
+                int st = -1;   // -1: keep going
+                double ux = 0.0, uy = 0.0;
+                if (check) {
+                    // mean over the leaf: all s2 cells, or the inner window when oversampling
+                    const int m = a.margin, hi = s - m;
+                    for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
+                        const int loc = c - j * s2, ly = loc / s, lx = loc - ly * s;
+                        if (m == 0 || (lx >= m && lx < hi && ly >= m && ly < hi)) {
+                            ux += (double)UX[c];
+                            uy += (double)UY[c];
                         }
                     }
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
-                    if (lane == 0) s_event = Tcta + best;
+                    for (int off = 16; off > 0; off >>= 1) {
+                        ux += __shfl_xor_sync(0xffffffffu, ux, off);
+                        uy += __shfl_xor_sync(0xffffffffu, uy, off);
+                    }
+                    const double inner = (double)(s - 2 * a.margin) * (double)(s - 2 * a.margin);
+                    ux /= inner;
+                    uy /= inner;
+                    const double cur = sl.drive == 0 ? ux : uy;
+                    const bool regular = t == h.y;
+                    if (regular) h.y += a.check_every;
+                    if (a.tol > 0.0 && t > a.check_every && regular &&
+                        fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur))
+                        st = LBM_OK;
+                    else if (t == (int)a.max_steps)
+                        st = a.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
+                    sl.prev = cur;
+                    h.w = (int)((unsigned)h.x + (unsigned)min(h.y, (int)a.max_steps));
                 }
-                any = __syncthreads_or(tid < nslots && (hot[tid].z & 1));
+                if (abort_now && st < 0) st = LBM_ETIMEOUT;
+                if (lane == 0) {
+                    if (st >= 0) {
+                        // Eq. 17: column `drive` of K* from the mean velocity (NaN if abandoned unchecked)
+                        const double kx = check ? a.nu_over_g * ux : __longlong_as_double(0x7ff8000000000000LL);
+                        const double ky = check ? a.nu_over_g * uy : __longlong_as_double(0x7ff8000000000000LL);
+                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 0 : 1)] = kx;
+                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 2 : 3)] = ky;
+                        if (a.steps) a.steps[2 * (int64_t)sl.leaf + sl.drive] = t;
+                        if (st != LBM_OK) {
+                            atomicMax(&a.status[sl.leaf], st);
+                            atomicMax(a.worst, st);
+                        }
+                        // refill the slot from this size's queue; the new job starts at the next
+                        // (even) CTA step
+                        const int qbeg = s_coff[cls], qn = s_coff[cls + 1] - qbeg;
+                        int q = abort_now ? qn : atomicAdd(&a.heads[cls], 1);
+                        if (q < qn) {
+                            sl.job = a.jobs[qbeg + q];
+                            sl.leaf = sl.job >> 1;
+                            sl.drive = sl.job & 1;
+                            sl.x0 = a.leaves[3 * sl.leaf] - a.margin;
+                            sl.y0 = a.leaves[3 * sl.leaf + 1] - a.margin;
+                            sl.prev = 0.0;
+                            h = make_int4((int)Tcta, a.check_every, 1 | (sl.drive << 1) | 4,
+                                          (int)(Tcta + (unsigned)min(a.check_every, (int)a.max_steps)));
+                        } else {
+                            sl.job = -1;
+                            h.z = 0;
+                        }
+                    }
+                    slots[j] = sl;
+                    hot[j] = h;
+                }
+                __syncwarp();
             }
-            ++Tcta;
+            __syncthreads();   // slot updates of every warp are visible before they are read
+            // next event: the earliest velocity store of an active slot
+            if (wid == 0) {
+                unsigned best = 0xffffffffu;
+                for (int j = lane; j < nslots; j += 32) {
+                    const int4 h = hot[j];
+                    if (h.z & 1) best = min(best, (unsigned)h.w - Tcta);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
+                if (lane == 0) s_event = Tcta + best;
+            }
+            fresh = __syncthreads_or(tid < nslots && (hot[tid].z & 4)) != 0;
         }
     }
+}
+
+using LocalKernel = void (*)(LocalArgs);
+
+// The solver variant for a storage type and tau (tau = 1 exactly has its own collision form).
+LocalKernel local_kernel(bool f64, double tau)
+{
+    const bool t1 = tau == 1.0;
+    if (f64) return t1 ? local_keff_kernel<double, true> : local_keff_kernel<double, false>;
+    return t1 ? local_keff_kernel<float, true> : local_keff_kernel<float, false>;
 }
 
 }  // namespace
@@ -538,7 +597,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.abort_flag = d_flags + 1;
 
     const bool f64 = p->storage == LBM_F64;
-    auto kern = f64 ? local_keff_kernel<double> : local_keff_kernel<float>;
+    const LocalKernel kern = local_kernel(f64, p->tau);
     const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     LOC_CUDA2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0;
@@ -617,7 +676,7 @@ lbm_status launch_local_from_table(const lbm_params *p, const float *kappa_dev, 
     a.abort_flag = table + DT_ABORT;
     a.time_limit_ns = (unsigned long long)(time_limit_s * 1e9);
     const bool f64 = p->storage == LBM_F64;
-    auto kern = f64 ? local_keff_kernel<double> : local_keff_kernel<float>;
+    const LocalKernel kern = local_kernel(f64, p->tau);
     const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -853,7 +912,7 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     a.worst = scr + NA_FLAGS + 1;
     a.abort_flag = scr + NA_FLAGS + 2;
     a.time_limit_ns = (unsigned long long)(g_time_limit_s * 1e9);
-    auto kern = f64 ? local_keff_kernel<double> : local_keff_kernel<float>;
+    const LocalKernel kern = local_kernel(f64, p->tau);
     const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     NA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int blocks = sm_count(dev);
