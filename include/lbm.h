@@ -252,10 +252,14 @@ lbm_status lbm_surrogate_set_params(lbm_surrogate *s, int32_t model, const float
  * 0: c = mean log K, w = 1; 1: c = midpoint of the log layered-medium bounds
  * (rows as parallel series tubes below, columns as series parallel slabs above)
  * of the leaf's 64 x 64 log-K plane (see lbm_patches), w = 1; 2: that midpoint
- * and w = half the log width (at least 0.05). lbm_surrogate_train sets every
+ * and w = half the log width (at least 0.05); 3: c = log of the leaf's Darcy K*
+ * (finite volumes on the leaf, harmonic face permeabilities, periodic, unit
+ * drive along x and along y; solved on the device by preconditioned conjugate
+ * gradients in FP64), w = 1, so the networks learn the Brinkman and
+ * discretisation correction to Darcy flow. lbm_surrogate_train sets every
  * entry but the mode from its data and keeps the mode set before it (2 for a
  * new ensemble). */
-lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13]);   /* mode not 0-2: EINVAL */
+lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13]);   /* mode not 0-3: EINVAL */
 lbm_status lbm_surrogate_get_normalization(const lbm_surrogate *s, float norm[13]);
 
 /* Leaf -> surrogate input. For each leaf (size s dividing 32, or a multiple of

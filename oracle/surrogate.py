@@ -119,14 +119,57 @@ def layered_bounds(k: np.ndarray):
             np.mean(h_cols), 1.0 / np.mean(1.0 / a_rows))
 
 
+def darcy_keff(k: np.ndarray):
+    """Effective permeability (K*_xx, K*_yy) of a periodic patch k [rows = y][columns = x] under
+    Darcy's law, by finite volumes: the flux across the face between two neighbouring cells is
+    k_f (p_i - p_j + G . (x_j - x_i)) with k_f the harmonic mean of the two cells, every cell
+    conserves mass, the patch is periodic, and a unit force G drives the flow along x, then y.
+    K* along the drive is the mean face flux per unit force (unit viscosity). The pressure system
+    is solved by a sparse direct solve with one pressure fixed (it is defined up to a constant)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    k = np.asarray(k, dtype=np.float64)
+    n_y, n_x = k.shape
+    cells = n_x * n_y
+    idx = np.arange(cells).reshape(n_y, n_x)
+    faces = []                                            # (neighbour index, face permeability, axis)
+    for axis in (1, 0):
+        kn = np.roll(k, -1, axis=axis)
+        faces.append((np.roll(idx, -1, axis=axis).ravel(), (2.0 * k * kn / (k + kn)).ravel(), axis))
+    i = idx.ravel()
+    rows, cols, vals = [], [], []
+    for j, kf, _ in faces:
+        rows += [i, i, j, j]
+        cols += [i, j, j, i]
+        vals += [kf, -kf, kf, -kf]
+    a = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(cells, cells))
+    a = (a + sp.csr_matrix(([1.0], ([0], [0])), shape=(cells, cells))).tocsc()
+    out = []
+    for drive in (1, 0):                                  # axis 1 = x, axis 0 = y
+        b = np.zeros(cells)
+        for j, kf, axis in faces:
+            if axis == drive:                             # the force pushes flux from i to j
+                np.add.at(b, i, -kf)
+                np.add.at(b, j, kf)
+        p = sla.spsolve(a, b)
+        j, kf, _ = faces[0 if drive == 1 else 1]
+        out.append(np.mean(kf * (p[i] - p[j] + 1.0)))
+    return out[0], out[1]
+
+
 def target_base(logk: np.ndarray, mode: int):
     """Per-leaf base (c_xx, w_xx, c_yy, w_yy) of the surrogate's target: the networks learn
     (log K* - c) / w for each component.
 
     mode 0: c = mean log K of the leaf's 64 x 64 plane, w = 1;
     mode 1: c = midpoint of log lo and log hi of layered_bounds on that plane, w = 1;
-    mode 2: the same c and w = max((log hi - log lo) / 2, 0.05).
+    mode 2: the same c and w = max((log hi - log lo) / 2, 0.05);
+    mode 3: c = log of darcy_keff on the leaf itself (its 64 x 64 plane above 64 cells), w = 1.
     """
+    if mode == 3:
+        leaf = logk if logk.shape[0] <= 64 else full_plane(logk)
+        kxx, kyy = darcy_keff(np.exp(np.asarray(leaf, dtype=np.float64)))
+        return (np.log(kxx), 1.0, np.log(kyy), 1.0)
     f = full_plane(logk)
     if mode == 0:
         m = f.mean()

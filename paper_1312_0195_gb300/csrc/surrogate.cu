@@ -437,6 +437,155 @@ __global__ void __launch_bounds__(256) patch_base_kernel(const float *x, int n, 
     }
 }
 
+// ------------------------------------------------------------ Darcy base (target mode 3)
+// The Darcy K* of each leaf by finite volumes: the flux across the face between two neighbouring
+// cells is k_f (p_i - p_j + G . (x_j - x_i)) with k_f the harmonic mean of the two cells, every cell
+// conserves mass, the leaf is periodic, and a unit force drives the flow along x, then along y.
+// K* along the drive is the mean face flux. The pressure system is solved by conjugate gradients
+// with the diagonal as preconditioner, in FP64, to a relative residual of 1e-10. The leaf's log K
+// is read back from the input planes (phase plane 0 sampled every 32 / s pixels for s <= 32, the
+// four phase planes for 64 cells; above 64 cells the 64 x 64 plane stands for the leaf). One CTA
+// per leaf; faces and the four CG vectors live in shared memory (6 x 4096 doubles).
+constexpr int DB_THREADS = 512;
+constexpr int DB_N = 64;
+constexpr int DB_CELLS = DB_N * DB_N;
+constexpr size_t DB_SMEM = 6 * DB_CELLS * sizeof(double);
+constexpr int DB_MAXIT = 4000;
+
+// (a, b) summed over the CTA in a fixed order; every thread gets the sums.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[2], double *out)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = a;
+        red[threadIdx.x >> 5][1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { x += red[k][0]; y += red[k][1]; }
+        out[0] = x;
+        out[1] = y;
+    }
+    __syncthreads();
+    a = out[0];
+    b = out[1];
+}
+
+__device__ __forceinline__ double harmonic2(double a, double b)
+{
+    if (isinf(a)) return isinf(b) ? a : 2.0 * b;
+    if (isinf(b)) return 2.0 * a;
+    return a + b > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+__global__ void __launch_bounds__(DB_THREADS) darcy_base_kernel(const float *x, int n, float4 *cw)
+{
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    double *KX = reinterpret_cast<double *>(dsm_raw);   // face to the +x neighbour
+    double *KY = KX + DB_CELLS;                          // face to the +y neighbour
+    double *P = KY + DB_CELLS, *R = P + DB_CELLS, *Dv = R + DB_CELLS, *AD = Dv + DB_CELLS;
+    __shared__ double red[DB_THREADS / 32][2];
+    __shared__ double s_out[2];
+    const int tid = threadIdx.x;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const float *xi = x + (int64_t)i * IN_PLANES * PIX;
+        int s = (int)lrintf(exp2f(6.0f * xi[4 * PIX]));        // the size plane holds log2(s) / 6
+        s = s < 1 ? 1 : (s > DB_N ? DB_N : s);
+        const int nc = s * s;
+        for (int c = tid; c < nc; c += DB_THREADS) {
+            const int y = c / s, xx = c - y * s;
+            float v;
+            if (s <= IMG) {
+                const int r = IMG / s;
+                v = xi[(y * r) * IMG + xx * r];
+            } else {
+                v = xi[((y & 1) * 2 + (xx & 1)) * PIX + (y >> 1) * IMG + (xx >> 1)];
+            }
+            P[c] = exp((double)v);                       // permeability, for now
+        }
+        __syncthreads();
+        for (int c = tid; c < nc; c += DB_THREADS) {
+            const int y = c / s, xx = c - y * s;
+            KX[c] = harmonic2(P[c], P[y * s + (xx + 1 == s ? 0 : xx + 1)]);
+            KY[c] = harmonic2(P[c], P[(y + 1 == s ? 0 : y + 1) * s + xx]);
+        }
+        __syncthreads();
+        double kd[2];
+        for (int drive = 0; drive < 2; ++drive) {
+            // A p = b with (A p)_c = sum over the faces of c of k_f (p_c - p_neighbour) and
+            // b_c = k_f(behind c) - k_f(ahead of c) along the drive
+            double rr = 0.0, rz = 0.0;
+            for (int c = tid; c < nc; c += DB_THREADS) {
+                const int y = c / s, xx = c - y * s;
+                const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
+                const double b = drive == 0 ? KX[cl] - KX[c] : KY[cd] - KY[c];
+                const double dg = KX[c] + KX[cl] + KY[c] + KY[cd];
+                const double z = dg > 0.0 ? b / dg : 0.0;
+                P[c] = 0.0;
+                R[c] = b;
+                Dv[c] = z;
+                rr += b * b;
+                rz += b * z;
+            }
+            block_sum2(rr, rz, red, s_out);
+            const double stop = 1e-20 * rr;                  // (1e-10 relative residual)^2
+            for (int it = 0; it < DB_MAXIT && rr > stop; ++it) {
+                double dad = 0.0, unused = 0.0;
+                for (int c = tid; c < nc; c += DB_THREADS) {
+                    const int y = c / s, xx = c - y * s;
+                    const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cr = y * s + (xx + 1 == s ? 0 : xx + 1);
+                    const int cd = (y == 0 ? s - 1 : y - 1) * s + xx, cu = (y + 1 == s ? 0 : y + 1) * s + xx;
+                    const double dc = Dv[c];
+                    const double ad = KX[c] * (dc - Dv[cr]) + KX[cl] * (dc - Dv[cl]) + KY[c] * (dc - Dv[cu]) +
+                                      KY[cd] * (dc - Dv[cd]);
+                    AD[c] = ad;
+                    dad += dc * ad;
+                }
+                block_sum2(dad, unused, red, s_out);
+                if (!(dad > 0.0)) break;                      // search direction in the null space
+                const double alpha = rz / dad;
+                double rr2 = 0.0, rz2 = 0.0;
+                for (int c = tid; c < nc; c += DB_THREADS) {
+                    const int y = c / s, xx = c - y * s;
+                    const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
+                    P[c] += alpha * Dv[c];
+                    const double r = R[c] - alpha * AD[c];
+                    R[c] = r;
+                    const double dg = KX[c] + KX[cl] + KY[c] + KY[cd];
+                    rr2 += r * r;
+                    rz2 += dg > 0.0 ? r * r / dg : 0.0;
+                }
+                block_sum2(rr2, rz2, red, s_out);
+                const double beta = rz2 / rz;
+                rz = rz2;
+                rr = rr2;
+                for (int c = tid; c < nc; c += DB_THREADS) {
+                    const int y = c / s, xx = c - y * s;
+                    const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
+                    const double dg = KX[c] + KX[cl] + KY[c] + KY[cd];
+                    Dv[c] = (dg > 0.0 ? R[c] / dg : 0.0) + beta * Dv[c];
+                }
+                __syncthreads();
+            }
+            // mean face flux along the drive
+            double q = 0.0, unused = 0.0;
+            for (int c = tid; c < nc; c += DB_THREADS) {
+                const int y = c / s, xx = c - y * s;
+                q += drive == 0 ? KX[c] * (P[c] - P[y * s + (xx + 1 == s ? 0 : xx + 1)] + 1.0)
+                                : KY[c] * (P[c] - P[(y + 1 == s ? 0 : y + 1) * s + xx] + 1.0);
+            }
+            block_sum2(q, unused, red, s_out);
+            kd[drive] = q / nc;
+        }
+        if (tid == 0) cw[i] = make_float4((float)log(kd[0]), 1.0f, (float)log(kd[1]), 1.0f);
+        __syncthreads();
+    }
+}
+
 // Targets of a mini-batch: t[b] = ty[idx[b]] (two components).
 __global__ void gather_targets_kernel(const float *ty, const int *idx, int B, float *t)
 {
@@ -460,6 +609,25 @@ __global__ void destandardise_kernel(float *y, int n, int nmodels, const float4 
 // ---------------------------------------------------------------- launchers
 
 int nblk(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b)); }
+
+// Per-leaf target base of the given mode: patch_base_kernel (modes 0-2) or the batched Darcy
+// solve (mode 3, one CTA per leaf on every SM).
+cudaError_t launch_base(const float *x, int n, int mode, float4 *cw, cudaStream_t st)
+{
+    if (mode == 3) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(darcy_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DB_SMEM);
+        if (e != cudaSuccess) return e;
+        const int sms = sm_count(dev);
+        darcy_base_kernel<<<n < sms ? n : sms, DB_THREADS, DB_SMEM, st>>>(x, n, cw);
+    } else {
+        patch_base_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x, n, mode, cw);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time libcuda dependency)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -649,7 +817,7 @@ struct lbm_surrogate {
     float in_shift = 0.0f, in_scale = 1.0f;
     float y_mean[2] = {0.0f, 0.0f}, y_std[2] = {1.0f, 1.0f};
     float stat_lo[3] = {-1e30f, -1e30f, -1e30f}, stat_hi[3] = {1e30f, 1e30f, 1e30f};
-    int target_mode = 2;          // patch_base_kernel: 0 mean log K, 1 bound midpoint, 2 midpoint and width
+    int target_mode = 2;          // 0 mean log K, 1 bound midpoint, 2 midpoint and width, 3 Darcy K*
     float gate_spread[7] = {0.03f, 0.03f, 0.03f, 0.03f, 0.03f, 0.03f, 0.03f};   // per log2 leaf size 0..6
     // buffers of lbm_surrogate_keff: one chunk of leaves, the job list and the queue table
     int kcap = 0;
@@ -879,7 +1047,7 @@ lbm_status lbm_surrogate_set_normalization(lbm_surrogate *s, const float norm[13
     s->in_shift = norm[0]; s->in_scale = norm[1];
     s->y_mean[0] = norm[2]; s->y_std[0] = norm[3]; s->y_mean[1] = norm[4]; s->y_std[1] = norm[5];
     const int mode = (int)norm[12];
-    if (!(norm[12] == (float)mode) || mode < 0 || mode > 2) return fail(LBM_EINVAL, "target mode must be 0, 1 or 2");
+    if (!(norm[12] == (float)mode) || mode < 0 || mode > 3) return fail(LBM_EINVAL, "target mode must be 0, 1, 2 or 3");
     for (int k = 0; k < 3; ++k) { s->stat_lo[k] = norm[6 + 2 * k]; s->stat_hi[k] = norm[7 + 2 * k]; }
     s->target_mode = mode;
     return LBM_OK;
@@ -969,10 +1137,15 @@ lbm_status lbm_surrogate_predict(lbm_surrogate *s, const float *x_dev, int32_t n
     }
     float4 *d_cw = nullptr;
     SUR_CUDA(cudaMalloc(&d_cw, sizeof(float4) * n));
-    patch_base_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, s->target_mode, d_cw);
+    cudaError_t eb = launch_base(x_dev, n, s->target_mode, d_cw, st);
+    if (eb != cudaSuccess) {
+        cudaFree(d_cw);
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "target base: %s", cudaGetErrorString(eb));
+    }
     destandardise_kernel<<<nblk((int64_t)s->nmodels * n * 2), 256, 0, st>>>(y_dev, n, s->nmodels, d_cw, s->y_mean[0],
                                                                           s->y_std[0], s->y_mean[1], s->y_std[1]);
-    count_launches(2);
+    count_launches(1);
     r = check_err(s, st);
     cudaFree(d_cw);
     return r;
@@ -1003,9 +1176,8 @@ lbm_status lbm_surrogate_train(lbm_surrogate *s, const float *x_dev, const float
     {
         float4 *d_cw = nullptr;
         SUR_CUDA(cudaMalloc(&d_cw, sizeof(float4) * n));
-        patch_base_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x_dev, n, s->target_mode, d_cw);
-        count_launches(1);
-        cudaError_t e1 = cudaMemcpy(cw.data(), d_cw, sizeof(float4) * n, cudaMemcpyDeviceToHost);
+        cudaError_t e1 = launch_base(x_dev, n, s->target_mode, d_cw, st);
+        if (e1 == cudaSuccess) e1 = cudaMemcpy(cw.data(), d_cw, sizeof(float4) * n, cudaMemcpyDeviceToHost);
         cudaFree(d_cw);
         if (e1 != cudaSuccess) { cudaGetLastError(); return fail(LBM_ECUDA, "patch bases: %s", cudaGetErrorString(e1)); }
     }
@@ -1354,11 +1526,11 @@ lbm_status lbm_surrogate_keff(lbm_surrogate *s, const lbm_params *p, const float
                                          cudaMemcpyDeviceToDevice, st));
             }
         }
-        patch_base_kernel<<<nc < 65535 ? nc : 65535, 256, 0, st>>>(s->kx, nc, s->target_mode, s->kcw);
+        SUR_CUDA(launch_base(s->kx, nc, s->target_mode, s->kcw, st));
         destandardise_kernel<<<nblk((int64_t)s->nmodels * nc * 2), 256, 0, st>>>(
             s->ky, nc, s->nmodels, s->kcw, s->y_mean[0], s->y_std[0], s->y_mean[1], s->y_std[1]);
         gate_kernel<<<nblk(nc), 256, 0, st>>>(s->ky, s->nmodels, nc, b0, lv, s->kstats, ga, keff_dev, fb, s->table);
-        count_launches(3);
+        count_launches(2);
         SUR_CUDA(cudaGetLastError());
     }
     queue_table_kernel<<<1, 32, 0, st>>>(s->table);

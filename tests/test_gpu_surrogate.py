@@ -215,11 +215,12 @@ def _base_from_predict(sur, x, mode, n_models=1):
     return c, cw - c
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_target_base_matches_oracle_full_batch(mode):
     """The per-leaf base (c, w) of every target mode against the oracle's target_base on 640
-    leaves of 8 to 64 cells, plus layers across x (the Table 1 and 2 means) and a checkerboard
-    (Table 3's geometric mean)."""
+    leaves of 8 to 64 cells, plus layers across x (the Table 1 and 2 means, exact for the layered
+    bounds and for the finite-volume Darcy K* of mode 3) and a checkerboard (Table 3's geometric
+    mean for the bounds' midpoint)."""
     lbm = _lbm()
     leaves = _leaves_logk(640, 31)
     layers = np.exp(np.random.default_rng(81).uniform(-6.0, 0.0, 64))
@@ -238,9 +239,10 @@ def test_target_base_matches_oracle_full_batch(mode):
     if mode:
         l32 = layers.astype(np.float32).astype(np.float64)
         np.testing.assert_allclose(c[0], [np.log(1.0 / (1.0 / l32).mean()), np.log(l32.mean())], atol=3e-5)
+    if mode in (1, 2):
         np.testing.assert_allclose(c[2], [0.5 * np.log(1e-3 * 2e-2)] * 2, atol=3e-5)
     with lbm.Surrogate(1, 0) as sur, pytest.raises(lbm.LbmError):
-        sur.set_normalization(np.array([0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 3], dtype=np.float32))
+        sur.set_normalization(np.array([0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 0, 1, 4], dtype=np.float32))
 
 
 def test_full_batch_forward_and_gradients_match_oracle():

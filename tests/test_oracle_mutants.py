@@ -122,6 +122,10 @@ SUR_MUTANTS = {
     "gate_population_std": [("/ (m_members - 1)) if m_members > 1", "/ m_members) if m_members > 1")],
     "gate_bounds_exclusive": [("if not (stat_lo[k] <= stats[i, k] <= stat_hi[k]):",
                                "if not (stat_lo[k] < stats[i, k] < stat_hi[k]):")],
+    "darcy_arithmetic_faces": [("faces.append((np.roll(idx, -1, axis=axis).ravel(), (2.0 * k * kn / (k + kn)).ravel(), axis))",
+                                "faces.append((np.roll(idx, -1, axis=axis).ravel(), (0.5 * (k + kn)).ravel(), axis))")],
+    "darcy_drive_reversed": [("        out.append(np.mean(kf * (p[i] - p[j] + 1.0)))",
+                              "        out.append(np.mean(kf * (p[j] - p[i] + 1.0)))")],
     "gate_mean_of_k_not_log": [("keff[i] = (np.exp(mean[0]), 0.0, 0.0, np.exp(mean[1]))",
                                 "keff[i] = (np.exp(y[:, i, 0]).mean(), 0.0, 0.0, np.exp(y[:, i, 1]).mean())")],
 }
@@ -140,7 +144,8 @@ def test_surrogate_oracle_pins_catch_planted_mistake(name, monkeypatch):
     exec(compile(src, f"sur_mutant_{name}", "exec"), mod.__dict__)
     monkeypatch.setattr(pins, "S", mod)
     tests = [getattr(pins, t) for t in dir(pins) if t.startswith("test_")
-             and ("phase" in t or "bounds" in t or "base" in t or "gate" in t or "checkerboard" in t)]
+             and ("phase" in t or "bounds" in t or "base" in t or "gate" in t or "checkerboard" in t
+                  or "darcy" in t)]
     failed = 0
     for t in tests:
         try:

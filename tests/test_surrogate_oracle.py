@@ -221,3 +221,29 @@ def test_context_planes_are_row_and_column_means():
     x = S.make_input(q, -3.0, 2.0)
     assert x.shape == (9, 32, 32)
     np.testing.assert_allclose(x[5:], (a - (-3.0)) / 2.0, rtol=1e-14)
+
+
+def test_darcy_keff_closed_forms():
+    """Finite-volume Darcy K* of a periodic patch: a uniform patch gives its permeability; layers
+    across x give the harmonic mean along x and the arithmetic mean along y exactly (Tables 1 and
+    2's analytic columns); on a checkerboard of single cells every face has the same harmonic
+    permeability 2 k1 k2 / (k1 + k2), which is then K* in both directions; transposing a random
+    patch exchanges K*_xx and K*_yy and a periodic shift changes nothing."""
+    stats = pytest.importorskip("scipy.stats")
+    np.testing.assert_allclose(S.darcy_keff(np.full((8, 8), 0.3)), [0.3, 0.3], rtol=1e-13)
+    layers = np.exp(RNG.uniform(-6.0, 0.0, 16))
+    kxx, kyy = S.darcy_keff(np.tile(layers, (16, 1)))
+    np.testing.assert_allclose([kxx, kyy], [stats.hmean(layers), np.mean(layers)], rtol=1e-11)
+    for k1, k2 in ((1.0, 2.0), (3e-3, 7e-6)):
+        idx = np.add.outer(np.arange(12), np.arange(12)) % 2
+        kc = np.where(idx == 0, k1, k2)
+        np.testing.assert_allclose(S.darcy_keff(kc), [2 * k1 * k2 / (k1 + k2)] * 2, rtol=1e-11)
+    q = np.exp(RNG.normal(-3.0, 1.5, (16, 16)))
+    a, b = S.darcy_keff(q), S.darcy_keff(q.T.copy())
+    np.testing.assert_allclose([a[1], a[0]], b, rtol=1e-11)
+    np.testing.assert_allclose(S.darcy_keff(np.roll(q, (5, 3), axis=(0, 1))), a, rtol=1e-11)
+    # lies between the layered bounds of Tables 1 and 2 (harmonic of arithmetic, arithmetic of harmonic)
+    lox, hix, loy, hiy = S.layered_bounds(q)
+    assert lox <= a[0] <= hix and loy <= a[1] <= hiy
+    # mode 3 of the target base is its log (the leaf itself, width 1)
+    np.testing.assert_allclose(S.target_base(np.log(q), 3), [np.log(a[0]), 1.0, np.log(a[1]), 1.0], rtol=1e-13)
