@@ -753,7 +753,7 @@ static cudaError_t launch_wgrad_tc(const __nv_bfloat16 *in, const __nv_bfloat16 
     cudaError_t e = encode_rows_map(&tin, in, CIN_P, B, HALO_W, CIP / 8, W::ROWS + 2);
     if (e == cudaSuccess) e = encode_rows_map(&tout, dout, COUT, B, IMG, COUT / 8, W::ROWS);
     if (e != cudaSuccess) return e;
-    const int units = 2 * B * W::P;
+    const int units = W::ITEMS * B * W::P;
     int grid = units < sms ? units : sms;
     grid -= grid % W::P;
     WgtArgs a{part, B, err};

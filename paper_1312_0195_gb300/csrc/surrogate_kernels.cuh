@@ -276,8 +276,9 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a)
 // HM (HM + 2) blocks are used: 3/4 for COUT = 64, 1/2 for COUT = 32). The three dx accumulators
 // take 3 N <= 384 TMEM columns for the whole run of a CTA.
 //
-// Work units are (half image, input-channel part of CIP channels); a CTA keeps one part and
-// takes every (grid / P)-th half image. Warp 0 issues the TMA loads (two stages), warp 1 the MMAs,
+// Work units are (quarter image, input-channel part of CIP channels); a CTA keeps one part and
+// takes every (grid / P)-th quarter image. Warp 0 issues the TMA loads (STAGES stages, so that
+// several tiles are in flight while the MMAs run), warp 1 the MMAs,
 // and warps 2-5 read the accumulators once at the end, writing one partial
 // [HM][9][COUT][CIP] per CTA (the rows h of a tap are separate partials), folded in a fixed order
 // by wgrad_tc_reduce_kernel.
@@ -287,7 +288,9 @@ struct WgtShape {
     static constexpr int NR = HM + 2;                              // padded input rows per N tile
     static constexpr int N = NR * CIP;
     static constexpr int P = CIN_P / CIP;                          // input-channel parts
-    static constexpr int ROWS = IMG / 2;                           // output rows per work item
+    static constexpr int ITEMS = 4;                                // work items per image
+    static constexpr int ROWS = IMG / ITEMS;                       // output rows per work item
+    static constexpr int STAGES = 4;
     static constexpr uint32_t A_ROW = (COUT / 8) * IMG * 16;       // one dout row, all channel groups
     static constexpr uint32_t A_BYTES = ROWS * A_ROW;
     static constexpr uint32_t B_ROW = (CIP / 8) * HALO_W * 16;     // one padded input row
@@ -295,13 +298,14 @@ struct WgtShape {
     static constexpr uint32_t B_PAD = (B_BYTES + 127u) / 128u * 128u;
     static constexpr uint32_t STAGE = A_BYTES + B_PAD;
     // at least 116 KB so that only one CTA (and its 512 TMEM columns) fits on an SM
-    static constexpr uint32_t NEED = CTRL + 2 * STAGE + 128;
+    static constexpr uint32_t NEED = CTRL + STAGES * STAGE + 128;
     static constexpr uint32_t SMEM = NEED > 118784u ? NEED : 118784u;
     static constexpr uint32_t TMEM_COLS = 512;
     static_assert(HM * COUT == 128, "M = 128");
     static_assert(N % 16 == 0 && N <= 256 && 3 * N <= (int)TMEM_COLS, "three accumulators fit TMEM");
     static_assert(CIN_P % CIP == 0 && CIP % 8 == 0, "channel parts of whole groups");
     static_assert(A_BYTES % 128 == 0, "stages stay 128-byte aligned");
+    static_assert(ROWS % HM == 0 && NEED <= 232448u, "row tiles per item; shared memory per CTA");
 };
 
 struct WgtArgs {
@@ -318,19 +322,20 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__
     constexpr uint32_t IDESC = umma::idesc_bf16_f32_mn(128, S::N);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((128u - (umma::smem_addr(smem_raw) & 127u)) & 127u);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);      // [2] tiles landed (TMA bytes)
-    uint64_t *empty = full + 2;                               // [2] MMAs finished reading the stage
-    uint64_t *tfull = full + 4;                               // accumulators complete
-    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem + 64);
-    volatile int *s_fail = reinterpret_cast<volatile int *>(smem + 68);
+    constexpr int NS = S::STAGES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);      // [NS] tiles landed (TMA bytes)
+    uint64_t *empty = full + NS;                              // [NS] MMAs finished reading the stage
+    uint64_t *tfull = full + 2 * NS;                          // accumulators complete
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem + 8 * (2 * NS + 1));
+    volatile int *s_fail = reinterpret_cast<volatile int *>(smem + 8 * (2 * NS + 1) + 4);
     uint8_t *stage0 = smem + CTRL;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int part = blockIdx.x % S::P, cstride = gridDim.x / S::P;
-    const int nitems = a.nimg * 2;
+    const int nitems = a.nimg * S::ITEMS;
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NS; ++i) {
             umma::mbar_init(&full[i], 1);
             umma::mbar_init(&empty[i], 1);
         }
@@ -351,21 +356,21 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__
         if (lane == 0) {
             int k = 0;
             for (int item = blockIdx.x / S::P; item < nitems; item += cstride, ++k) {
-                const int b = k & 1;
-                if (k >= 2 && !umma::mbar_wait_bounded(&empty[b], ((k >> 1) - 1) & 1, WAIT_LIMIT)) {
+                const int b = k % NS;
+                if (k >= NS && !umma::mbar_wait_bounded(&empty[b], ((k / NS) - 1) & 1, WAIT_LIMIT)) {
                     *s_fail = 1;
                     break;
                 }
                 if (*s_fail) break;
-                const int img = item >> 1, y0 = (item & 1) * S::ROWS;
+                const int img = item / S::ITEMS, y0 = (item % S::ITEMS) * S::ROWS;
                 uint8_t *st = stage0 + b * S::STAGE;
                 umma::mbar_arrive_expect_tx(&full[b], S::A_BYTES + S::B_BYTES);
                 umma::tma_load_5d(st, &tout, &full[b], 0, 0, 0, y0, img);
                 umma::tma_load_5d(st + S::A_BYTES, &tin, &full[b], 0, -1, part * (CIP / 8), y0 - 1, img);
             }
             if (*s_fail)     // loads already issued land before shared memory is released
-                for (int kk = k - 2 < 0 ? 0 : k - 2; kk < k; ++kk)
-                    umma::mbar_wait_bounded(&full[kk & 1], (kk >> 1) & 1, WAIT_LIMIT);
+                for (int kk = k - NS < 0 ? 0 : k - NS; kk < k; ++kk)
+                    umma::mbar_wait_bounded(&full[kk % NS], (kk / NS) & 1, WAIT_LIMIT);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMA issuer
@@ -373,8 +378,8 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__
             int k = 0;
             uint32_t acc = 0;
             for (int item = blockIdx.x / S::P; item < nitems; item += cstride, ++k) {
-                const int b = k & 1;
-                if (!umma::mbar_wait_bounded(&full[b], (k >> 1) & 1, WAIT_LIMIT)) {
+                const int b = k % NS;
+                if (!umma::mbar_wait_bounded(&full[b], (k / NS) & 1, WAIT_LIMIT)) {
                     *s_fail = 1;
                     break;
                 }
