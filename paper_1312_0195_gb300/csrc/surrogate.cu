@@ -733,6 +733,24 @@ static cudaError_t encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *act, i
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Tensor map over BF16 activations [nimg][C/8][32][32][8] seen as 4-D (a row of 32 pixels x 8 channels,
+// C/8 channel groups, 32 rows, nimg): a box of whole rows lands in shared memory as
+// [rows][groups][32 pixels][8], with 512-byte rows for the copy engine (no halo needed).
+static cudaError_t encode_fullrow_map(CUtensorMap *map, const __nv_bfloat16 *act, int c, int nimg, int box_groups,
+                                      int box_h)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)IMG * 8, (cuuint64_t)(c / 8), IMG, (cuuint64_t)nimg};
+    const cuuint64_t strides[3] = {(cuuint64_t)PIX * 8 * 2, (cuuint64_t)IMG * 8 * 2, (cuuint64_t)(c / 8) * PIX * 8 * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)IMG * 8, (cuuint32_t)box_groups, (cuuint32_t)box_h, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(act), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Weight and bias gradient of one layer: wgrad_tc_kernel, bias partials, and the fixed-order fold
 // into gw [cout][cin][3][3] and gb [cout].
 template <int COUT, int CIN_P, int CIP>
@@ -751,7 +769,7 @@ static cudaError_t launch_wgrad_tc(const __nv_bfloat16 *in, const __nv_bfloat16 
     }
     CUtensorMap tin, tout;
     cudaError_t e = encode_rows_map(&tin, in, CIN_P, B, HALO_W, CIP / 8, W::ROWS + 2);
-    if (e == cudaSuccess) e = encode_rows_map(&tout, dout, COUT, B, IMG, COUT / 8, W::ROWS);
+    if (e == cudaSuccess) e = encode_fullrow_map(&tout, dout, COUT, B, COUT / 8, W::ROWS);
     if (e != cudaSuccess) return e;
     const int units = W::ITEMS * B * W::P;
     int grid = units < sms ? units : sms;

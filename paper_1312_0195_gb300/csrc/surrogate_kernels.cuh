@@ -269,7 +269,8 @@ conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, ConvArgs a)
 //
 // One MMA has M = HM output rows x COUT channels of dout (HM = 128 / COUT) and N = HM + 2
 // consecutive padded input rows x CIP input channels, K = 16 pixels of a row. TMA lays both tiles
-// out row by row, [row][channel group][pixel][8], so the M and N core-matrix groups are evenly
+// out row by row, [row][channel group][pixel][8] (the output gradient in 512-byte pixel rows, the
+// input with its zero halo in 16-byte channel groups), so the M and N core-matrix groups are evenly
 // spaced across rows: block (h, r) of the product pairs dout row y + h with padded input row y + r,
 // which is the vertical tap dy = r - h of output row y + h. Per dx (a 16-byte shift of the B
 // start address) one MMA therefore covers all three vertical taps of HM output rows (3 HM of the
@@ -365,7 +366,7 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__
                 const int img = item / S::ITEMS, y0 = (item % S::ITEMS) * S::ROWS;
                 uint8_t *st = stage0 + b * S::STAGE;
                 umma::mbar_arrive_expect_tx(&full[b], S::A_BYTES + S::B_BYTES);
-                umma::tma_load_5d(st, &tout, &full[b], 0, 0, 0, y0, img);
+                umma::tma_load_4d(st, &tout, &full[b], 0, 0, y0, img);
                 umma::tma_load_5d(st + S::A_BYTES, &tin, &full[b], 0, -1, part * (CIP / 8), y0 - 1, img);
             }
             if (*s_fail)     // loads already issued land before shared memory is released
