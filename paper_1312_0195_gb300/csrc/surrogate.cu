@@ -442,146 +442,195 @@ __global__ void __launch_bounds__(256) patch_base_kernel(const float *x, int n, 
 // cells is k_f (p_i - p_j + G . (x_j - x_i)) with k_f the harmonic mean of the two cells, every cell
 // conserves mass, the leaf is periodic, and a unit force drives the flow along x, then along y.
 // K* along the drive is the mean face flux. The pressure system is solved by conjugate gradients
-// with the diagonal as preconditioner, in FP64, to a relative residual of 1e-10. The leaf's log K
-// is read back from the input planes (phase plane 0 sampled every 32 / s pixels for s <= 32, the
-// four phase planes for 64 cells; above 64 cells the 64 x 64 plane stands for the leaf). One CTA
-// per leaf; faces and the four CG vectors live in shared memory (6 x 4096 doubles).
-constexpr int DB_THREADS = 512;
+// with the diagonal as preconditioner, in FP32 with the cross-thread sums in FP64, to a relative
+// residual of 1e-5 (K* then agrees with an FP64 direct solve to a few 1e-6). The leaf's log K is
+// read back from the input planes (phase plane 0 sampled every 32 / s pixels for s <= 32, the four
+// phase planes for 64 cells; above 64 cells the 64 x 64 plane stands for the leaf).
+// Leaves of up to 32 cells are solved by one warp each (darcy_small_kernel), larger ones by a
+// CTA each (darcy_big_kernel); each kernel passes over the leaves of the other kind.
 constexpr int DB_N = 64;
 constexpr int DB_CELLS = DB_N * DB_N;
-constexpr size_t DB_SMEM = 6 * DB_CELLS * sizeof(double);
 constexpr int DB_MAXIT = 4000;
+constexpr int DBS_WARPS = 8;                                 // warps per CTA of the small-leaf kernel
+constexpr int DBS_CELLS = IMG * IMG;                         // cells per warp (leaves up to 32)
+constexpr size_t DBS_SMEM = (size_t)DBS_WARPS * 6 * DBS_CELLS * sizeof(float);
+constexpr int DBB_THREADS = 256;
+constexpr size_t DBB_SMEM = (size_t)6 * DB_CELLS * sizeof(float);
 
-// (a, b) summed over the CTA in a fixed order; every thread gets the sums.
-__device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[2], double *out)
+__device__ __forceinline__ int darcy_size(const float *xi)
 {
-    for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, off);
-        b += __shfl_xor_sync(0xffffffffu, b, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5][0] = a;
-        red[threadIdx.x >> 5][1] = b;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0.0, y = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { x += red[k][0]; y += red[k][1]; }
-        out[0] = x;
-        out[1] = y;
-    }
-    __syncthreads();
-    a = out[0];
-    b = out[1];
+    const int s = (int)lrintf(exp2f(6.0f * xi[4 * PIX]));   // the size plane holds log2(s) / 6
+    return s < 1 ? 1 : (s > DB_N ? DB_N : s);
 }
 
-__device__ __forceinline__ double harmonic2(double a, double b)
+__device__ __forceinline__ float harmonic2f(double a, double b)
 {
-    if (isinf(a)) return isinf(b) ? a : 2.0 * b;
-    if (isinf(b)) return 2.0 * a;
-    return a + b > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
+    if (isinf(a)) return (float)(isinf(b) ? a : 2.0 * b);
+    if (isinf(b)) return (float)(2.0 * a);
+    return a + b > 0.0 ? (float)(2.0 * a * b / (a + b)) : 0.0f;
 }
 
-__global__ void __launch_bounds__(DB_THREADS) darcy_base_kernel(const float *x, int n, float4 *cw)
-{
-    extern __shared__ __align__(16) unsigned char dsm_raw[];
-    double *KX = reinterpret_cast<double *>(dsm_raw);   // face to the +x neighbour
-    double *KY = KX + DB_CELLS;                          // face to the +y neighbour
-    double *P = KY + DB_CELLS, *R = P + DB_CELLS, *Dv = R + DB_CELLS, *AD = Dv + DB_CELLS;
-    __shared__ double red[DB_THREADS / 32][2];
-    __shared__ double s_out[2];
-    const int tid = threadIdx.x;
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        const float *xi = x + (int64_t)i * IN_PLANES * PIX;
-        int s = (int)lrintf(exp2f(6.0f * xi[4 * PIX]));        // the size plane holds log2(s) / 6
-        s = s < 1 ? 1 : (s > DB_N ? DB_N : s);
-        const int nc = s * s;
-        for (int c = tid; c < nc; c += DB_THREADS) {
-            const int y = c / s, xx = c - y * s;
-            float v;
-            if (s <= IMG) {
-                const int r = IMG / s;
-                v = xi[(y * r) * IMG + xx * r];
-            } else {
-                v = xi[((y & 1) * 2 + (xx & 1)) * PIX + (y >> 1) * IMG + (xx >> 1)];
+// A group of NT threads solving one leaf: one warp (NT = 32) or the whole CTA.
+template <int NT> struct DarcyGroup {
+    __device__ static int rank() { return threadIdx.x % NT; }
+    __device__ static void sync()
+    {
+        if constexpr (NT == 32) __syncwarp(); else __syncthreads();
+    }
+    // (a, b) summed over the group in a fixed order; every thread gets the sums
+    __device__ static void sum2(double &a, double &b, double (*red)[2])
+    {
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, off);
+            b += __shfl_xor_sync(0xffffffffu, b, off);
+        }
+        if constexpr (NT > 32) {
+            if ((threadIdx.x & 31) == 0) {
+                red[threadIdx.x >> 5][0] = a;
+                red[threadIdx.x >> 5][1] = b;
             }
-            P[c] = exp((double)v);                       // permeability, for now
+            __syncthreads();
+            double x = 0.0, y = 0.0;
+            for (int k = 0; k < NT / 32; ++k) { x += red[k][0]; y += red[k][1]; }
+            __syncthreads();
+            a = x;
+            b = y;
         }
-        __syncthreads();
-        for (int c = tid; c < nc; c += DB_THREADS) {
+    }
+};
+
+// K*_xx and K*_yy of the leaf whose input planes start at xi; the group's work arrays hold cap cells.
+template <int NT>
+__device__ void darcy_leaf(const float *xi, int s, float *KX, float *KY, float *P, float *R, float *Dv, float *AD,
+                          double (*red)[2], double (&kd)[2])
+{
+    using G = DarcyGroup<NT>;
+    const int nc = s * s, r0 = G::rank();
+    for (int c = r0; c < nc; c += NT) {
+        const int y = c / s, xx = c - y * s;
+        float v;
+        if (s <= IMG) {
+            const int r = IMG / s;
+            v = xi[(y * r) * IMG + xx * r];
+        } else {
+            v = xi[((y & 1) * 2 + (xx & 1)) * PIX + (y >> 1) * IMG + (xx >> 1)];
+        }
+        P[c] = v;                                          // log K, for now
+    }
+    G::sync();
+    for (int c = r0; c < nc; c += NT) {
+        const int y = c / s, xx = c - y * s;
+        const double k = exp((double)P[c]);
+        KX[c] = harmonic2f(k, exp((double)P[y * s + (xx + 1 == s ? 0 : xx + 1)]));
+        KY[c] = harmonic2f(k, exp((double)P[(y + 1 == s ? 0 : y + 1) * s + xx]));
+    }
+    G::sync();
+    for (int drive = 0; drive < 2; ++drive) {
+        // A p = b with (A p)_c = sum over the faces of c of k_f (p_c - p_neighbour) and
+        // b_c = k_f(behind c) - k_f(ahead of c) along the drive
+        float prr = 0.0f, prz = 0.0f;
+        for (int c = r0; c < nc; c += NT) {
             const int y = c / s, xx = c - y * s;
-            KX[c] = harmonic2(P[c], P[y * s + (xx + 1 == s ? 0 : xx + 1)]);
-            KY[c] = harmonic2(P[c], P[(y + 1 == s ? 0 : y + 1) * s + xx]);
+            const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
+            const float b = drive == 0 ? KX[cl] - KX[c] : KY[cd] - KY[c];
+            const float dg = KX[c] + KX[cl] + KY[c] + KY[cd];
+            const float z = dg > 0.0f ? b / dg : 0.0f;
+            P[c] = 0.0f;
+            R[c] = b;
+            Dv[c] = z;
+            prr = fmaf(b, b, prr);
+            prz = fmaf(b, z, prz);
         }
-        __syncthreads();
-        double kd[2];
-        for (int drive = 0; drive < 2; ++drive) {
-            // A p = b with (A p)_c = sum over the faces of c of k_f (p_c - p_neighbour) and
-            // b_c = k_f(behind c) - k_f(ahead of c) along the drive
-            double rr = 0.0, rz = 0.0;
-            for (int c = tid; c < nc; c += DB_THREADS) {
+        double rr = prr, rz = prz;
+        G::sum2(rr, rz, red);
+        const double stop = 1e-10 * rr;                    // (1e-5 relative residual)^2
+        for (int it = 0; it < DB_MAXIT && rr > stop; ++it) {
+            float pdad = 0.0f;
+            for (int c = r0; c < nc; c += NT) {
+                const int y = c / s, xx = c - y * s;
+                const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cr = y * s + (xx + 1 == s ? 0 : xx + 1);
+                const int cd = (y == 0 ? s - 1 : y - 1) * s + xx, cu = (y + 1 == s ? 0 : y + 1) * s + xx;
+                const float dc = Dv[c];
+                const float ad = KX[c] * (dc - Dv[cr]) + KX[cl] * (dc - Dv[cl]) + KY[c] * (dc - Dv[cu]) +
+                                 KY[cd] * (dc - Dv[cd]);
+                AD[c] = ad;
+                pdad = fmaf(dc, ad, pdad);
+            }
+            double dad = pdad, unused = 0.0;
+            G::sum2(dad, unused, red);
+            if (!(dad > 0.0)) break;                          // a direction in the null space
+            const float alpha = (float)(rz / dad);
+            float prr2 = 0.0f, prz2 = 0.0f;
+            for (int c = r0; c < nc; c += NT) {
                 const int y = c / s, xx = c - y * s;
                 const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
-                const double b = drive == 0 ? KX[cl] - KX[c] : KY[cd] - KY[c];
-                const double dg = KX[c] + KX[cl] + KY[c] + KY[cd];
-                const double z = dg > 0.0 ? b / dg : 0.0;
-                P[c] = 0.0;
-                R[c] = b;
-                Dv[c] = z;
-                rr += b * b;
-                rz += b * z;
+                P[c] = fmaf(alpha, Dv[c], P[c]);
+                const float r = fmaf(-alpha, AD[c], R[c]);
+                R[c] = r;
+                const float dg = KX[c] + KX[cl] + KY[c] + KY[cd];
+                prr2 = fmaf(r, r, prr2);
+                prz2 = dg > 0.0f ? fmaf(r, r / dg, prz2) : prz2;
             }
-            block_sum2(rr, rz, red, s_out);
-            const double stop = 1e-20 * rr;                  // (1e-10 relative residual)^2
-            for (int it = 0; it < DB_MAXIT && rr > stop; ++it) {
-                double dad = 0.0, unused = 0.0;
-                for (int c = tid; c < nc; c += DB_THREADS) {
-                    const int y = c / s, xx = c - y * s;
-                    const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cr = y * s + (xx + 1 == s ? 0 : xx + 1);
-                    const int cd = (y == 0 ? s - 1 : y - 1) * s + xx, cu = (y + 1 == s ? 0 : y + 1) * s + xx;
-                    const double dc = Dv[c];
-                    const double ad = KX[c] * (dc - Dv[cr]) + KX[cl] * (dc - Dv[cl]) + KY[c] * (dc - Dv[cu]) +
-                                      KY[cd] * (dc - Dv[cd]);
-                    AD[c] = ad;
-                    dad += dc * ad;
-                }
-                block_sum2(dad, unused, red, s_out);
-                if (!(dad > 0.0)) break;                      // search direction in the null space
-                const double alpha = rz / dad;
-                double rr2 = 0.0, rz2 = 0.0;
-                for (int c = tid; c < nc; c += DB_THREADS) {
-                    const int y = c / s, xx = c - y * s;
-                    const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
-                    P[c] += alpha * Dv[c];
-                    const double r = R[c] - alpha * AD[c];
-                    R[c] = r;
-                    const double dg = KX[c] + KX[cl] + KY[c] + KY[cd];
-                    rr2 += r * r;
-                    rz2 += dg > 0.0 ? r * r / dg : 0.0;
-                }
-                block_sum2(rr2, rz2, red, s_out);
-                const double beta = rz2 / rz;
-                rz = rz2;
-                rr = rr2;
-                for (int c = tid; c < nc; c += DB_THREADS) {
-                    const int y = c / s, xx = c - y * s;
-                    const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
-                    const double dg = KX[c] + KX[cl] + KY[c] + KY[cd];
-                    Dv[c] = (dg > 0.0 ? R[c] / dg : 0.0) + beta * Dv[c];
-                }
-                __syncthreads();
-            }
-            // mean face flux along the drive
-            double q = 0.0, unused = 0.0;
-            for (int c = tid; c < nc; c += DB_THREADS) {
+            double rr2 = prr2, rz2 = prz2;
+            G::sum2(rr2, rz2, red);
+            const float beta = (float)(rz2 / rz);
+            rz = rz2;
+            rr = rr2;
+            for (int c = r0; c < nc; c += NT) {
                 const int y = c / s, xx = c - y * s;
-                q += drive == 0 ? KX[c] * (P[c] - P[y * s + (xx + 1 == s ? 0 : xx + 1)] + 1.0)
-                                : KY[c] * (P[c] - P[(y + 1 == s ? 0 : y + 1) * s + xx] + 1.0);
+                const int cl = y * s + (xx == 0 ? s - 1 : xx - 1), cd = (y == 0 ? s - 1 : y - 1) * s + xx;
+                const float dg = KX[c] + KX[cl] + KY[c] + KY[cd];
+                Dv[c] = fmaf(beta, Dv[c], dg > 0.0f ? R[c] / dg : 0.0f);
             }
-            block_sum2(q, unused, red, s_out);
-            kd[drive] = q / nc;
+            G::sync();
         }
-        if (tid == 0) cw[i] = make_float4((float)log(kd[0]), 1.0f, (float)log(kd[1]), 1.0f);
+        // mean face flux along the drive
+        float pq = 0.0f;
+        for (int c = r0; c < nc; c += NT) {
+            const int y = c / s, xx = c - y * s;
+            pq += drive == 0 ? KX[c] * (P[c] - P[y * s + (xx + 1 == s ? 0 : xx + 1)] + 1.0f)
+                             : KY[c] * (P[c] - P[(y + 1 == s ? 0 : y + 1) * s + xx] + 1.0f);
+        }
+        double q = pq, unused = 0.0;
+        G::sum2(q, unused, red);
+        kd[drive] = q / nc;
+        G::sync();
+    }
+}
+
+// Leaves of up to 32 cells: one warp per leaf, eight warps per CTA, each with its own work arrays.
+__global__ void __launch_bounds__(DBS_WARPS * 32) darcy_small_kernel(const float *x, int n, float4 *cw)
+{
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *base = reinterpret_cast<float *>(dsm_raw) + (size_t)w * 6 * DBS_CELLS;
+    float *KX = base, *KY = KX + DBS_CELLS, *P = KY + DBS_CELLS, *R = P + DBS_CELLS, *Dv = R + DBS_CELLS,
+          *AD = Dv + DBS_CELLS;
+    for (int i = blockIdx.x * DBS_WARPS + w; i < n; i += gridDim.x * DBS_WARPS) {
+        const float *xi = x + (int64_t)i * IN_PLANES * PIX;
+        const int s = darcy_size(xi);
+        if (s > IMG) continue;                              // the CTA kernel's leaf
+        double kd[2];
+        darcy_leaf<32>(xi, s, KX, KY, P, R, Dv, AD, nullptr, kd);
+        if (lane == 0) cw[i] = make_float4((float)log(kd[0]), 1.0f, (float)log(kd[1]), 1.0f);
+        __syncwarp();
+    }
+}
+
+// Leaves of 64 cells and more: one CTA per leaf.
+__global__ void __launch_bounds__(DBB_THREADS) darcy_big_kernel(const float *x, int n, float4 *cw)
+{
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    float *KX = reinterpret_cast<float *>(dsm_raw);
+    float *KY = KX + DB_CELLS, *P = KY + DB_CELLS, *R = P + DB_CELLS, *Dv = R + DB_CELLS, *AD = Dv + DB_CELLS;
+    __shared__ double red[DBB_THREADS / 32][2];
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const float *xi = x + (int64_t)i * IN_PLANES * PIX;
+        const int s = darcy_size(xi);
+        if (s <= IMG) continue;                             // the warp kernel's leaf
+        double kd[2];
+        darcy_leaf<DBB_THREADS>(xi, s, KX, KY, P, R, Dv, AD, red, kd);
+        if (threadIdx.x == 0) cw[i] = make_float4((float)log(kd[0]), 1.0f, (float)log(kd[1]), 1.0f);
         __syncthreads();
     }
 }
@@ -611,17 +660,22 @@ __global__ void destandardise_kernel(float *y, int n, int nmodels, const float4 
 int nblk(int64_t n) { int64_t b = (n + 255) / 256; return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b)); }
 
 // Per-leaf target base of the given mode: patch_base_kernel (modes 0-2) or the batched Darcy
-// solve (mode 3, one CTA per leaf on every SM).
+// solve (mode 3: a warp per leaf up to 32 cells, a CTA per larger leaf).
 cudaError_t launch_base(const float *x, int n, int mode, float4 *cw, cudaStream_t st)
 {
     if (mode == 3) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(darcy_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DB_SMEM);
+            e = cudaFuncSetAttribute(darcy_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DBS_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(darcy_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DBB_SMEM);
         if (e != cudaSuccess) return e;
         const int sms = sm_count(dev);
-        darcy_base_kernel<<<n < sms ? n : sms, DB_THREADS, DB_SMEM, st>>>(x, n, cw);
+        const int gs = (n + DBS_WARPS - 1) / DBS_WARPS;
+        darcy_small_kernel<<<gs < sms ? gs : sms, DBS_WARPS * 32, DBS_SMEM, st>>>(x, n, cw);
+        darcy_big_kernel<<<n < 2 * sms ? n : 2 * sms, DBB_THREADS, DBB_SMEM, st>>>(x, n, cw);
+        count_launches(1);
     } else {
         patch_base_kernel<<<n < 65535 ? n : 65535, 256, 0, st>>>(x, n, mode, cw);
     }
