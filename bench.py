@@ -509,7 +509,7 @@ def _calibrate_gate(sd, in_range, rel, sizes, p99_max=0.04, med_max=0.015):
     return np.array(out, dtype=np.float32)
 
 
-def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=48, test_fields=100, epochs=40,
+def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=100, test_fields=100, epochs=40,
                       spread_max=0.03):
     """The learned K* surrogate against the batched local LBM on held-out leaves.
 
@@ -558,7 +558,7 @@ def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=
     norm = sur.get_normalization()
 
     # per-size gate limits from a calibration split
-    kca, lca = _surrogate_set(calib_fields, 2000)
+    kca, lca = _surrogate_set(calib_fields, 2000)     # calibration split (seeds 20000000...)
     kc, lc, pc, xc, stc, _, kec, stt_c, _, _ = label(kca, lca)
     pred_c = sur.predict(xc)
     sd_c = pred_c.std(dim=0).max(dim=1).values.cpu().numpy()
@@ -569,7 +569,7 @@ def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=
     keff_c = torch.exp(pred_c.double().mean(dim=0))
     rel_c = torch.maximum((keff_c[:, 0] / kec[:, 0] - 1).abs(), (keff_c[:, 1] / kec[:, 3] - 1).abs()).cpu().numpy()
     good_c = stt_c.cpu().numpy() == 0
-    gate = _calibrate_gate(sd_c, inr & good_c, rel_c, lca[:, 2], p99_max=0.04, med_max=0.015)
+    gate = _calibrate_gate(sd_c, inr & good_c, rel_c, lca[:, 2], p99_max=0.045, med_max=0.018)
     sur.set_gate(gate)
 
     # held-out test leaves: LBM alone, then the surrogate end to end (one call)
@@ -640,7 +640,7 @@ def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=
                     f"{calib_fields} held-out 256^2 fields; test: quadtree leaves 8-64 of {test_fields} further "
                     "held-out fields; labels by local LBM tol 1e-8; ensemble of 4, nine input planes (phase "
                     "planes of the 64x64 log-K plane, size, row and column context), target log K* minus the leaf's "
-                    "finite-volume Darcy log K* (mode 3), gate calibrated to p99 <= 4 % and median <= 1.5 % per size",
+                    "finite-volume Darcy log K* (mode 3), gate calibrated to p99 <= 4.5 % and median <= 1.8 % per size",
         "train_patches": n_train, "test_patches": n, "epochs": epochs,
         "seconds": {"fields": t_gen, "labels": t_label, "train": t_train},
         "final_train_loss": [float(l[-1]) for l in loss],
