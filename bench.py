@@ -633,6 +633,38 @@ def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=
                 "all_rel_err_p90": float(np.percentile(rel_pred[sel & good_np], 90))}
     rej_cost = cost[~acc_np].sum() / cost.sum()
     flops = 4 * 2 * 1024 * 9 * (9 * 32 + 32 * 32 + 32 * 64 + 3 * 64 * 64)      # ensemble, per patch
+    # the optional Darcy start of the local problems (warm_start = 1): LBM alone, then as the
+    # surrogate's fallback; K* compared with the runs from rest
+    pw = lbm.Params(nx=p.nx, ny=p.ny, tau=1.0, eps=1.0, warm_start=1)
+    lbm.local_keff(pw, kt, lt[:64].contiguous(), 1e-6, 1e-8, 200000, 64, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ke_w, st_w, steps_w, _ = lbm.local_keff(pw, kt, lt, 1e-6, 1e-8, 200000, 64, True)
+    torch.cuda.synchronize()
+    t_lbm_w = time.perf_counter() - t0
+    both = ((stte == 0) & (st_w == 0)).cpu().numpy()
+    rel_w = rel_err(ke_w, ke_te).cpu().numpy()[both]
+    off_w = (torch.maximum((ke_w[:, 1] - ke_te[:, 1]).abs(), (ke_w[:, 2] - ke_te[:, 2]).abs())
+             / torch.sqrt((ke_te[:, 0] * ke_te[:, 3]).abs())).cpu().numpy()[both]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    keff_w, fb_w, _, _, _ = sur.keff(pw, kt, lt, 0.0, 1e-6, 1e-8, 200000)
+    torch.cuda.synchronize()
+    t_e2e_w = time.perf_counter() - t0
+    warm = {
+        "lbm_patches_per_s": n / t_lbm_w, "speedup_vs_rest_start": t_lbm / t_lbm_w,
+        "lattice_updates_ratio": float((sz.astype(np.float64) ** 2 * steps_w.cpu().numpy().sum(axis=1)).sum()
+                                       / cost.sum()),
+        "converged_leaves": int((st_w == 0).sum().item()),
+        "rel_diff_to_rest_start_median": float(np.median(rel_w)),
+        "rel_diff_to_rest_start_p99": float(np.percentile(rel_w, 99)),
+        "rel_diff_to_rest_start_max": float(rel_w.max()),
+        "offdiag_diff_to_rest_start_median": float(np.median(off_w)),
+        "offdiag_diff_to_rest_start_max": float(off_w.max()),
+        "surrogate_end_to_end_patches_per_s": n / t_e2e_w,
+        "surrogate_speedup_vs_rest_start_lbm": t_lbm / t_e2e_w,
+        "surrogate_speedup_vs_darcy_start_lbm": t_lbm_w / t_e2e_w,
+        "surrogate_fallback_leaves": int((fb_w != 0).sum().item())}
     sur.close()
     return {
         "workload": f"train: {n_train} leaves ({train_fields} seeded 512^2 log-normal fields, sigma U[0.5,3], "
@@ -657,6 +689,7 @@ def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=
         "ideal_speedup": float(1.0 / (rej_cost + t_inf / t_lbm)),
         "uniform_3pct_gate": results["uniform_3pct"],
         "by_leaf_size": by_size,
+        "darcy_start": warm,
     }
 
 

@@ -79,6 +79,20 @@ typedef struct {
                              with periodic wrap) with periodic closure, and the stop test and
                              Eq. 17 average the inner leaf only. 0 is the plain local problem
                              of Section 3. Ignored by the grid calls.                    */
+    int32_t warm_start;   /* local problems: 0 starts every run from rest (Section 3 is silent
+                             on the start; rest is the reading used throughout); 1 starts a
+                             run on a patch of 16 cells or more from the patch's finite-volume
+                             Darcy state instead: the pressure and the cell velocities of
+                             Darcy flow through the same patch under the same drive (harmonic
+                             face permeabilities, periodic), solved in shared memory when the
+                             run begins, as g_a = w_a (drho + 3 e_a . j) with drho = 3 eps G p
+                             and j = rho u. The steady state is the same. The stop test of
+                             such a run takes the relative change of the whole mean velocity
+                             vector, not of its driven component only (from a start near the
+                             steady state the transverse component can still be moving when
+                             the driven one has stopped). The slow diffusive start is skipped,
+                             so runs stop sooner, and K* differs from the rest start only
+                             within the stop test's band. Ignored by the grid calls.      */
 } lbm_params;
 
 /* Thread-local description of the last failure of any call in this thread. */

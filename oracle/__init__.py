@@ -26,6 +26,11 @@ _SRCS = [_SRC, os.path.join(_HERE, "lbm3d_oracle.c")]
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 
 Q = 9
+# D2Q9 velocities and weights in the paper's order (Section 2): rest, the four axes at angles
+# (a - 1) pi / 2, the four diagonals at (a - 5) pi / 2 + pi / 4
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 
 
 def build(force: bool = False) -> str:
@@ -88,6 +93,10 @@ def _L():
                                            C.c_double, C.c_double, C.c_long, C.c_int,
                                            dp, dp, C.POINTER(C.c_long)]
         _lib.orc_local_keff_os.restype = C.c_int
+        _lib.orc_local_keff_from.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double,
+                                             C.c_double, C.c_double, C.c_long, C.c_int, dp,
+                                             dp, dp, C.POINTER(C.c_long)]
+        _lib.orc_local_keff_from.restype = C.c_int
         _lib.orc_run_mean_steady.argtypes = [C.POINTER(_Problem), dp, C.c_int, C.c_double, C.c_long,
                                              C.c_int, dp, C.POINTER(C.c_int)]
         _lib.orc_run_mean_steady.restype = C.c_long
@@ -290,12 +299,37 @@ def lattice():
     return np.array(list(e), dtype=np.int64).reshape(9, 2), w
 
 
-def local_keff(kappa_leaf, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64, margin=0):
+def darcy_start(kappa_patch, nu, eps, g_const):
+    """The Darcy start of a local problem: for each drive (along x, then y) the distributions
+    w_a (rho + 3 e_a . j) of the patch's finite-volume Darcy flow (oracle.surrogate.darcy_solve:
+    harmonic face permeabilities, periodic, unit drive), with rho = 1 + 3 eps G p and j = rho u,
+    u = (G / nu) times the mean of each cell's two face fluxes along each axis. [2][s][s][9]."""
+    from .surrogate import darcy_solve
+    k = np.asarray(kappa_patch, dtype=np.float64)
+    out = []
+    for drive in (0, 1):
+        p, qx, qy = darcy_solve(k, drive)
+        ux = 0.5 * (qx + np.roll(qx, 1, axis=1)) * g_const / nu
+        uy = 0.5 * (qy + np.roll(qy, 1, axis=0)) * g_const / nu
+        rho = 1.0 + 3.0 * eps * g_const * p
+        jx, jy = rho * ux, rho * uy
+        f = np.empty(k.shape + (Q,))
+        for a in range(Q):
+            f[..., a] = W[a] * (rho + 3.0 * (EX[a] * jx + EY[a] * jy))
+        out.append(f)
+    return np.ascontiguousarray(np.stack(out))
+
+
+def local_keff(kappa_leaf, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64, margin=0,
+               warm=False):
     """Local problems of Section 3 on one periodic square patch; Eq. 17.
 
     margin > 0: the patch is the leaf with `margin` cells on every side (oversampling, the
     treatment the Conclusions name for channelised media); the stop test and Eq. 17 use the
     mean velocity over the inner leaf only (orc_local_keff_os).
+    warm: runs on a patch whose side is a multiple of 8, at least 16, start from the patch's
+    Darcy state (darcy_start) instead of rest and stop on the relative change of the whole mean
+    velocity vector (orc_local_keff_from); other patches from rest with the plain test.
     Returns dict(keff=[xx, xy, yx, yy], ubar=[u1x, u1y, u2x, u2y], steps=[s1, s2], converged=n).
     """
     k = np.ascontiguousarray(kappa_leaf, dtype=np.float64)
@@ -304,7 +338,12 @@ def local_keff(kappa_leaf, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, ch
     keff = np.empty(4)
     ub = np.empty(4)
     st = (C.c_long * 2)()
-    if margin == 0:
+    if warm and s >= 16 and s % 8 == 0:
+        f0 = darcy_start(k, nu, eps, g_const)
+        nconv = _L().orc_local_keff_from(s, int(margin), _dp(k), float(tau), float(nu), float(eps), float(g_const),
+                                         float(tol), int(max_steps), int(check_every), _dp(f0), _dp(keff), _dp(ub),
+                                         st)
+    elif margin == 0:
         nconv = _L().orc_local_keff(s, _dp(k), float(tau), float(nu), float(eps), float(g_const),
                                     float(tol), int(max_steps), int(check_every), _dp(keff), _dp(ub), st)
     else:

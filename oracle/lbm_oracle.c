@@ -441,6 +441,66 @@ static void mean_velocity_window(const orc_problem *p, const double *f, int x0, 
     out[1] = sv / ((double)w * w);
 }
 
+/*
+ * The local problem of orc_local_keff_os (leaf grown by `margin`, inner-window mean), each drive
+ * starting from the state f_init + d * se * se * Q (d = 0: drive along x, 1: along y) instead of
+ * rest. The stop test is Section 3's relative-change test applied to the whole mean velocity
+ * vector, |ubar(t) - ubar(t - k)| <= tol k |ubar(t)|, rather than to its driven component only;
+ * Eq. 17 as before.
+ */
+int orc_local_keff_from(int se, int margin, const double *kappa_ext, double tau, double nu, double eps,
+                        double gconst, double tol, long max_steps, int check_every, const double *f_init,
+                        double keff[4], double ubar[4], long steps[2])
+{
+    lattice_init();
+    const int s = se - 2 * margin;
+    if (margin < 0 || s < 1) return -1;
+    orc_problem p;
+    memset(&p, 0, sizeof p);
+    p.nx = se; p.ny = se; p.tau = tau; p.nu = nu; p.eps = eps;
+    p.walls = 0; p.kappa = kappa_ext;
+    long n = (long)se * se;
+    double *f = (double *)malloc(sizeof(double) * n * Q);
+    double *g = (double *)malloc(sizeof(double) * n * Q);
+    int nconv = 0;
+    for (int d = 0; d < 2; ++d) {
+        p.gx = d == 0 ? gconst : 0.0;
+        p.gy = d == 0 ? 0.0 : gconst;
+        memcpy(f, f_init + (long)d * n * Q, sizeof(double) * n * Q);
+        /* from a start near the steady state the transverse mean velocity can still be moving
+           when the driven one has stopped: the stop test takes the whole vector ubar */
+        double prev[2] = {0.0, 0.0}, m[2];
+        long st = 0;
+        int conv = 0;
+        while (st < max_steps) {
+            orc_step(&p, f, g);
+            memcpy(f, g, sizeof(double) * n * Q);
+            ++st;
+            if (check_every > 0 && st % check_every == 0) {
+                mean_velocity_window(&p, f, margin, margin, s, m);
+                const double dx = m[0] - prev[0], dy = m[1] - prev[1];
+                if (tol > 0.0 && st > check_every &&
+                    sqrt(dx * dx + dy * dy) <= tol * check_every * sqrt(m[0] * m[0] + m[1] * m[1])) {
+                    conv = 1;
+                    break;
+                }
+                prev[0] = m[0];
+                prev[1] = m[1];
+            }
+        }
+        mean_velocity_window(&p, f, margin, margin, s, ubar + 2 * d);
+        steps[d] = st;
+        nconv += conv;
+    }
+    keff[0] = nu / gconst * ubar[0];
+    keff[1] = nu / gconst * ubar[2];
+    keff[2] = nu / gconst * ubar[1];
+    keff[3] = nu / gconst * ubar[3];
+    free(f);
+    free(g);
+    return nconv;
+}
+
 int orc_local_keff_os(int se, int margin, const double *kappa_ext, double tau, double nu, double eps,
                       double gconst, double tol, long max_steps, int check_every,
                       double keff[4], double ubar[4], long steps[2])
@@ -460,7 +520,9 @@ int orc_local_keff_os(int se, int margin, const double *kappa_ext, double tau, d
         p.gx = d == 0 ? gconst : 0.0;
         p.gy = d == 0 ? 0.0 : gconst;
         orc_init_rest(&p, f);
-        double prev = 0.0, m[2];
+        /* from a start near the steady state the transverse mean velocity can still be moving
+           when the driven one has stopped: the stop test takes the whole vector ubar */
+        double prev[2] = {0.0, 0.0}, m[2];
         long st = 0;
         int conv = 0;
         while (st < max_steps) {
@@ -469,11 +531,14 @@ int orc_local_keff_os(int se, int margin, const double *kappa_ext, double tau, d
             ++st;
             if (check_every > 0 && st % check_every == 0) {
                 mean_velocity_window(&p, f, margin, margin, s, m);
-                if (tol > 0.0 && st > check_every && fabs(m[d] - prev) <= tol * check_every * fabs(m[d])) {
+                const double dx = m[0] - prev[0], dy = m[1] - prev[1];
+                if (tol > 0.0 && st > check_every &&
+                    sqrt(dx * dx + dy * dy) <= tol * check_every * sqrt(m[0] * m[0] + m[1] * m[1])) {
                     conv = 1;
                     break;
                 }
-                prev = m[d];
+                prev[0] = m[0];
+                prev[1] = m[1];
             }
         }
         mean_velocity_window(&p, f, margin, margin, s, ubar + 2 * d);

@@ -119,13 +119,13 @@ def layered_bounds(k: np.ndarray):
             np.mean(h_cols), 1.0 / np.mean(1.0 / a_rows))
 
 
-def darcy_keff(k: np.ndarray):
-    """Effective permeability (K*_xx, K*_yy) of a periodic patch k [rows = y][columns = x] under
-    Darcy's law, by finite volumes: the flux across the face between two neighbouring cells is
-    k_f (p_i - p_j + G . (x_j - x_i)) with k_f the harmonic mean of the two cells, every cell
-    conserves mass, the patch is periodic, and a unit force G drives the flow along x, then y.
-    K* along the drive is the mean face flux per unit force (unit viscosity). The pressure system
-    is solved by a sparse direct solve with one pressure fixed (it is defined up to a constant)."""
+def darcy_solve(k: np.ndarray, drive: int):
+    """Darcy flow through a periodic patch k [rows = y][columns = x] by finite volumes: the flux
+    across the face between two neighbouring cells is k_f (p_i - p_j + G . (x_j - x_i)) with k_f the
+    harmonic mean of the two cells, every cell conserves mass, and a unit force G drives the flow
+    along x (drive 0) or y (drive 1). Solved by a sparse direct solve with one pressure fixed, then
+    shifted to zero mean (the pressure is defined up to a constant). Returns (p, qx, qy): the
+    pressure and the fluxes across each cell's +x and +y faces."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as sla
     k = np.asarray(k, dtype=np.float64)
@@ -144,17 +144,27 @@ def darcy_keff(k: np.ndarray):
         vals += [kf, -kf, kf, -kf]
     a = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(cells, cells))
     a = (a + sp.csr_matrix(([1.0], ([0], [0])), shape=(cells, cells))).tocsc()
-    out = []
-    for drive in (1, 0):                                  # axis 1 = x, axis 0 = y
-        b = np.zeros(cells)
-        for j, kf, axis in faces:
-            if axis == drive:                             # the force pushes flux from i to j
-                np.add.at(b, i, -kf)
-                np.add.at(b, j, kf)
-        p = sla.spsolve(a, b)
-        j, kf, _ = faces[0 if drive == 1 else 1]
-        out.append(np.mean(kf * (p[i] - p[j] + 1.0)))
-    return out[0], out[1]
+    axis_d = 1 if drive == 0 else 0
+    b = np.zeros(cells)
+    for j, kf, axis in faces:
+        if axis == axis_d:                                # the force pushes flux from i to j
+            np.add.at(b, i, -kf)
+            np.add.at(b, j, kf)
+    p = sla.spsolve(a, b)
+    p -= p.mean()
+    q = []
+    for j, kf, axis in faces:
+        q.append((kf * (p[i] - p[j] + (1.0 if axis == axis_d else 0.0))).reshape(n_y, n_x))
+    return p.reshape(n_y, n_x), q[0], q[1]
+
+
+def darcy_keff(k: np.ndarray):
+    """Effective permeability (K*_xx, K*_yy) of a periodic patch under Darcy's law by finite
+    volumes (darcy_solve): K* along the drive is the mean face flux per unit force (unit
+    viscosity)."""
+    _, qx, _ = darcy_solve(k, 0)
+    _, _, qy = darcy_solve(k, 1)
+    return float(np.mean(qx)), float(np.mean(qy))
 
 
 def target_base(logk: np.ndarray, mode: int):

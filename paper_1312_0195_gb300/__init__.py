@@ -66,11 +66,12 @@ class Params:
     scale: float = 0.0
     force_model: int = 0      # 0: simplified Shan-Chen scheme, 1: Guo scheme
     margin: int = 0           # local problems: oversampling margin in cells (0: plain)
+    warm_start: int = 0       # local problems: 0 from rest, 1 from the patch's finite-volume Darcy state
 
     def c(self) -> _abi.lbm_params:
         return _abi.lbm_params(int(self.nx), int(self.ny), float(self.tau), float(self.nu), float(self.eps),
                                float(self.gx), float(self.gy), int(self.bc), int(self.storage), float(self.scale),
-                               int(self.force_model), int(self.margin))
+                               int(self.force_model), int(self.margin), int(self.warm_start))
 
 
 # ----------------------------------------------------------------- C ABI mirror
@@ -197,7 +198,7 @@ def lbm_coarse_params(params: Params, block: int) -> Params:
     p = params.c()
     _check(_abi.lib().lbm_coarse_params(C.byref(p), int(block), C.byref(out)))
     return Params(out.nx, out.ny, out.tau, out.nu, out.eps, out.gx, out.gy, out.bc, out.storage, out.scale,
-                  out.force_model, out.margin)
+                  out.force_model, out.margin, out.warm_start)
 
 
 def lbm_coarse_run(params: Params, block: int, keff_coarse, g_coarse=None, max_steps: int = 100000,

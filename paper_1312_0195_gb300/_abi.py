@@ -25,7 +25,8 @@ class lbm_params(C.Structure):
                 ("tau", C.c_double), ("nu", C.c_double), ("eps", C.c_double),
                 ("gx", C.c_double), ("gy", C.c_double),
                 ("bc", C.c_int32), ("storage", C.c_int32),
-                ("scale", C.c_double), ("force_model", C.c_int32), ("margin", C.c_int32)]
+                ("scale", C.c_double), ("force_model", C.c_int32), ("margin", C.c_int32),
+                ("warm_start", C.c_int32)]
 
 
 class lbm3d_params(C.Structure):

@@ -102,6 +102,7 @@ lbm_status lbm_coarse_params(const lbm_params *fine_p, int32_t block, lbm_params
     c.gx = fine_p->gx * r;
     c.gy = fine_p->gy * r;
     c.margin = 0;
+    c.warm_start = 0;
     *coarse_out = c;
     return LBM_OK;
 }

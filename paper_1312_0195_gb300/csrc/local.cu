@@ -22,7 +22,8 @@
 //  * Every check_every steps of a job (and at max_steps) its mean velocity is
 //    reduced in FP64 by one warp in a fixed order (bitwise reproducible); the
 //    job ends when |ubar_d(t) - ubar_d(t - k)| <= tol k |ubar_d(t)| on the driven
-//    component d. Drive 1 writes K*_xx, K*_yx and drive 2 K*_xy, K*_yy (Eq. 17).
+//    component d (a job started from the Darcy state: the same test on the whole
+//    vector ubar). Drive 1 writes K*_xx, K*_yx and drive 2 K*_xy, K*_yy (Eq. 17).
 //  * A wall-clock limit (globaltimer) bounds the launch: past it every CTA
 //    abandons its jobs with LBM_ETIMEOUT and returns.
 #include "lbm_internal.h"
@@ -69,6 +70,11 @@ struct LocalArgs {
     double kd[4];
     double eps_nu;            // eps * nu for the drag coefficient
     double nu_over_g;         // nu / G for Eq. 17
+    int warm;                 // 1: patches of WARM_MIN cells or more (side a multiple of 8) start from
+                              // their finite-volume Darcy state instead of rest (the kernel's WARM
+                              // variant)
+    double warm_rho;          // 3 eps G: density deviation per unit of the unit-drive Darcy pressure
+    double warm_u;            // G / nu: velocity per unit of the unit-drive Darcy face flux
     double tol;
     int check_every;
     long long max_steps;
@@ -84,6 +90,7 @@ struct Slot {
     int job;                  // -1: empty
     int leaf, drive, x0, y0;
     double prev;              // driven mean velocity at the previous check
+    double prev_t;            // transverse mean velocity at the previous check
 };
 
 __device__ __forceinline__ unsigned long long globaltimer()
@@ -237,7 +244,252 @@ __device__ __forceinline__ void local_step(T *F, const T *D, T *UX, T *UY, const
     }
 }
 
-template <typename T, bool TAU1>
+// ---------------------------------------------------------------- the Darcy start
+// Darcy flow through a patch under the job's drive, by finite volumes: the flux across the face
+// between two neighbouring cells is k_f (p_i - p_j + G . (x_j - x_i)) with k_f the harmonic mean of
+// the two cells, every cell conserves mass, and the patch is periodic. It is solved with a unit
+// drive by conjugate gradients with the diagonal as preconditioner (the system's arrays live in
+// the new job's own part of F, which is free until its distributions are written), then the
+// run starts from g_a = w_a (drho + 3 e_a . j) with drho = 3 eps G p (the pressure p / rho0 = c_s^2
+// drho balances the drive as in Darcy's law with porosity eps) and j = rho u, u the mean of the
+// cell's two face fluxes along each axis times G / nu. Every fresh slot of the class is solved
+// at once; each per-slot sum is taken warp by warp (in the storage precision: the 32 terms of a
+// warp) and then over the slot's warps in FP64, in a fixed order, so the start, and everything
+// after it, is bitwise reproducible.
+constexpr int WARM_MIN = 16;
+constexpr int WARM_MAXIT = 4000;
+
+__device__ __forceinline__ double harmonic_face(double a, double b)
+{
+    if (isinf(a)) return isinf(b) ? a : 2.0 * b;
+    if (isinf(b)) return 2.0 * a;
+    return a + b > 0.0 ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+// Geometry of cell c of a class of side s: its slot j, position (lx, ly) and the four neighbours
+// within the slot (periodic closure).
+struct WarmCell {
+    int j, lx, ly, l, r, d, u;
+};
+__device__ __forceinline__ WarmCell warm_cell(int c, int s, int s2)
+{
+    WarmCell w;
+    w.j = c / s2;
+    const int loc = c - w.j * s2;
+    w.ly = loc / s;
+    w.lx = loc - w.ly * s;
+    const int row = c - w.lx;
+    w.l = row + (w.lx == 0 ? s - 1 : w.lx - 1);
+    w.r = row + (w.lx + 1 == s ? 0 : w.lx + 1);
+    w.d = w.ly == 0 ? c + s2 - s : c - s;
+    w.u = w.ly + 1 == s ? c - s2 + s : c + s;
+    return w;
+}
+
+template <typename T>
+__device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 *hot, const Slot *slots, int s,
+                                              int nslots)
+{
+    constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT, NW = LOCAL_THREADS / 32;
+    __shared__ double w_rz[MAXSLOTS], w_stop[MAXSLOTS];
+    __shared__ T w_alpha[MAXSLOTS], w_beta[MAXSLOTS];
+    __shared__ int w_on[MAXSLOTS];
+    __shared__ double w_red[CPT * NW][2];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int s2 = s * s, ncell = nslots * s2, nk = s2 / 32;
+    T *KX = F, *KY = F + CMAX, *P = F + 2 * CMAX, *R = F + 3 * CMAX, *DV = F + 4 * CMAX, *AD = F + 5 * CMAX;
+    T *IDG = F + 6 * CMAX;                           // 1 / diagonal (0 where the diagonal is 0)
+    // this thread's cells: slot j and position (lx, ly), found once and packed as
+    // j << 12 | ly << 6 | lx (s2 is a multiple of 64, so the 32 cells of a warp always belong to
+    // one slot); bit i of `mine` marks a cell of a fresh slot
+    int geo[CPT];
+    unsigned mine = 0;
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * LOCAL_THREADS;
+        const WarmCell w = warm_cell(c < ncell ? c : 0, s, s2);
+        geo[i] = w.j << 12 | w.ly << 6 | w.lx;
+        if (c < ncell && (hot[w.j].z & 5) == 5) mine |= 1u << i;
+    }
+    // the neighbours of cell i within its slot (periodic closure)
+    auto cell = [&](int i) {
+        const int c = tid + i * LOCAL_THREADS, lx = geo[i] & 63, ly = (geo[i] >> 6) & 63;
+        WarmCell w;
+        w.j = geo[i] >> 12;
+        w.lx = lx;
+        w.ly = ly;
+        w.l = lx == 0 ? c + s - 1 : c - 1;
+        w.r = lx + 1 == s ? c - s + 1 : c + 1;
+        w.d = ly == 0 ? c + s2 - s : c - s;
+        w.u = ly + 1 == s ? c - s2 + s : c + s;
+        return w;
+    };
+    // per-slot sums of (x, y): the 32 cells of each warp in T, then the slot's warps in FP64 in
+    // a fixed order
+    auto slot_sum2 = [&](int i, T x, T y) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, off);
+            y += __shfl_xor_sync(0xffffffffu, y, off);
+        }
+        if (lane == 0) {
+            w_red[i * NW + wid][0] = (double)x;
+            w_red[i * NW + wid][1] = (double)y;
+        }
+    };
+    // each slot's warp sums folded by one warp (slot j by warp j mod NW: every lane a strided
+    // share, then a butterfly), after which its lane 0 runs `then(j, x, y)`; one barrier before
+    auto slot_fold = [&](auto then) {
+        __syncthreads();
+        for (int j = wid; j < nslots; j += NW) {
+            double x = 0.0, y = 0.0;
+            for (int k = j * nk + lane; k < (j + 1) * nk; k += 32) {
+                x += w_red[k][0];
+                y += w_red[k][1];
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, off);
+                y += __shfl_xor_sync(0xffffffffu, y, off);
+            }
+            if (lane == 0) then(j, x, y);
+        }
+    };
+    auto kappa_at = [&](int j, int lx, int ly) {
+        int gx = slots[j].x0 + lx, gy = slots[j].y0 + ly;
+        gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
+        gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
+        return (double)a.kappa[(int64_t)gy * a.nx + gx];
+    };
+
+    // face permeabilities
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        if (!(mine >> i & 1)) continue;
+        const int c = tid + i * LOCAL_THREADS;
+        const WarmCell w = cell(i);
+        const double k = kappa_at(w.j, w.lx, w.ly);
+        KX[c] = (T)harmonic_face(k, kappa_at(w.j, w.lx + 1 == s ? 0 : w.lx + 1, w.ly));
+        KY[c] = (T)harmonic_face(k, kappa_at(w.j, w.lx, w.ly + 1 == s ? 0 : w.ly + 1));
+    }
+    __syncthreads();
+    // start: p = 0, r = b, d = b / diag
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = tid + i * LOCAL_THREADS;
+        T x = T(0), y = T(0);
+        if (mine >> i & 1) {
+            const WarmCell w = cell(i);
+            const T b = (hot[w.j].z & 2) ? KY[w.d] - KY[c] : KX[w.l] - KX[c];
+            const T dg = KX[c] + KX[w.l] + KY[c] + KY[w.d];
+            const T idg = dg > T(0) ? T(1) / dg : T(0);
+            const T z = b * idg;
+            IDG[c] = idg;
+            P[c] = T(0);
+            R[c] = b;
+            DV[c] = z;
+            x = b * b;
+            y = b * z;
+        }
+        slot_sum2(i, x, y);
+    }
+    slot_fold([&](int j, double rr, double rz) {
+        w_on[j] = (hot[j].z & 5) == 5 && rr > 0.0;
+        w_rz[j] = rz;
+        w_stop[j] = 1e-10 * rr;                              // (1e-5 relative residual)^2
+    });
+    int any = __syncthreads_or(tid < nslots && w_on[tid]);
+    for (int it = 0; any && it < WARM_MAXIT; ++it) {
+        unsigned act = 0;                                    // cells of slots still iterating
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+            if ((mine >> i & 1) && w_on[geo[i] >> 12]) act |= 1u << i;
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int c = tid + i * LOCAL_THREADS;
+            T x = T(0);
+            if (act >> i & 1) {
+                const WarmCell w = cell(i);
+                const T dc = DV[c];
+                const T ad = KX[c] * (dc - DV[w.r]) + KX[w.l] * (dc - DV[w.l]) + KY[c] * (dc - DV[w.u]) +
+                             KY[w.d] * (dc - DV[w.d]);
+                AD[c] = ad;
+                x = dc * ad;
+            }
+            slot_sum2(i, x, T(0));
+        }
+        slot_fold([&](int j, double dad, double) {
+            if (!w_on[j]) return;
+            if (!(dad > 0.0)) w_on[j] = 0;                   // a direction in the null space
+            else w_alpha[j] = (T)(w_rz[j] / dad);
+        });
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int c = tid + i * LOCAL_THREADS;
+            T x = T(0), y = T(0);
+            if ((act >> i & 1) && w_on[geo[i] >> 12]) {
+                const T al = w_alpha[geo[i] >> 12];
+                P[c] = fma(al, DV[c], P[c]);
+                const T r = fma(-al, AD[c], R[c]);
+                R[c] = r;
+                x = r * r;
+                y = r * r * IDG[c];
+            }
+            slot_sum2(i, x, y);
+        }
+        slot_fold([&](int j, double rr, double rz) {
+            if (!w_on[j]) return;
+            w_beta[j] = (T)(rz / w_rz[j]);
+            w_rz[j] = rz;
+            if (rr <= w_stop[j]) w_on[j] = 0;
+        });
+        any = __syncthreads_or(tid < nslots && w_on[tid]);
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int c = tid + i * LOCAL_THREADS;
+            if (!(act >> i & 1) || !w_on[geo[i] >> 12]) continue;
+            DV[c] = fma(w_beta[geo[i] >> 12], DV[c], R[c] * IDG[c]);
+        }
+        __syncthreads();
+    }
+    // the start state: rho and j from the pressure and the face fluxes, staged in AD (drho) and
+    // DV / R (j) so that every read of the pressure comes before the distributions are written
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        if (!(mine >> i & 1)) continue;
+        const int c = tid + i * LOCAL_THREADS;
+        const WarmCell w = cell(i);
+        const bool ydrive = (hot[w.j].z & 2) != 0;
+        const T gx = ydrive ? T(0) : T(1), gy = ydrive ? T(1) : T(0);
+        const T qr = KX[c] * (P[c] - P[w.r] + gx), ql = KX[w.l] * (P[w.l] - P[c] + gx);
+        const T qu = KY[c] * (P[c] - P[w.u] + gy), qd = KY[w.d] * (P[w.d] - P[c] + gy);
+        const T drho = (T)a.warm_rho * P[c];
+        const T rho = T(1) + drho;
+        AD[c] = drho;
+        DV[c] = rho * (T)(0.5 * a.warm_u) * (qr + ql);
+        R[c] = rho * (T)(0.5 * a.warm_u) * (qu + qd);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        if (!(mine >> i & 1)) continue;
+        const int c = tid + i * LOCAL_THREADS;
+        const T drho = AD[c], jx = DV[c], jy = R[c];
+        const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+        F[c] = T(4.0 / 9.0) * drho;
+        F[1 * CMAX + c] = w1 * (drho + T(3) * jx);
+        F[3 * CMAX + c] = w1 * (drho - T(3) * jx);
+        F[2 * CMAX + c] = w1 * (drho + T(3) * jy);
+        F[4 * CMAX + c] = w1 * (drho - T(3) * jy);
+        F[5 * CMAX + c] = w2 * (drho + T(3) * (jx + jy));
+        F[7 * CMAX + c] = w2 * (drho - T(3) * (jx + jy));
+        F[8 * CMAX + c] = w2 * (drho + T(3) * (jx - jy));
+        F[6 * CMAX + c] = w2 * (drho - T(3) * (jx - jy));
+    }
+}
+
+template <typename T, bool TAU1, bool WARM>
 __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs a)
 {
     constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT;
@@ -312,6 +564,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 sl.x0 = a.leaves[3 * sl.leaf] - a.margin;
                 sl.y0 = a.leaves[3 * sl.leaf + 1] - a.margin;
                 sl.prev = 0.0;
+                sl.prev_t = 0.0;
             }
             slots[tid] = sl;
             hot[tid] = make_int4(0, a.check_every, sl.job >= 0 ? 1 | (sl.drive << 1) | 4 : 0,
@@ -340,6 +593,12 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     for (int q = 0; q < Q; ++q) F[q * CMAX + c] = T(0);
                 }
                 __syncthreads();
+                if constexpr (WARM) {
+                    if (s >= WARM_MIN && s % 8 == 0) {
+                        warm_start_fresh<T>(a, F, hot, slots, s, nslots);
+                        __syncthreads();
+                    }
+                }
                 if (tid < nslots) hot[tid].z &= ~4;
             }
             if (!__syncthreads_or(tid < nslots && (hot[tid].z & 1))) break;
@@ -393,15 +652,26 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     const double inner = (double)(s - 2 * a.margin) * (double)(s - 2 * a.margin);
                     ux /= inner;
                     uy /= inner;
-                    const double cur = sl.drive == 0 ? ux : uy;
+                    const double cur = sl.drive == 0 ? ux : uy, cur_t = sl.drive == 0 ? uy : ux;
                     const bool regular = t == h.y;
                     if (regular) h.y += a.check_every;
-                    if (a.tol > 0.0 && t > a.check_every && regular &&
-                        fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur))
+                    bool settled;
+                    if (WARM && s >= WARM_MIN && s % 8 == 0) {
+                        // a Darcy-started job: the whole mean velocity vector must have settled,
+                        // since its transverse component can still carry the start's error after
+                        // the driven one has stopped moving
+                        const double dd = cur - sl.prev, dt = cur_t - sl.prev_t;
+                        settled = sqrt(dd * dd + dt * dt) <=
+                                  a.tol * a.check_every * sqrt(cur * cur + cur_t * cur_t);
+                    } else {
+                        settled = fabs(cur - sl.prev) <= a.tol * a.check_every * fabs(cur);
+                    }
+                    if (a.tol > 0.0 && t > a.check_every && regular && settled)
                         st = LBM_OK;
                     else if (t == (int)a.max_steps)
                         st = a.tol > 0.0 ? LBM_ENOTCONV : LBM_OK;
                     sl.prev = cur;
+                    sl.prev_t = cur_t;
                     h.w = (int)((unsigned)h.x + (unsigned)min(h.y, (int)a.max_steps));
                 }
                 if (abort_now && st < 0) st = LBM_ETIMEOUT;
@@ -428,6 +698,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                             sl.x0 = a.leaves[3 * sl.leaf] - a.margin;
                             sl.y0 = a.leaves[3 * sl.leaf + 1] - a.margin;
                             sl.prev = 0.0;
+                            sl.prev_t = 0.0;
                             h = make_int4((int)Tcta, a.check_every, 1 | (sl.drive << 1) | 4,
                                           (int)(Tcta + (unsigned)min(a.check_every, (int)a.max_steps)));
                         } else {
@@ -459,12 +730,17 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
 
 using LocalKernel = void (*)(LocalArgs);
 
-// The solver variant for a storage type and tau (tau = 1 exactly has its own collision form).
-LocalKernel local_kernel(bool f64, double tau)
+// The solver variant for a storage type, tau (tau = 1 exactly has its own collision form) and
+// the start (rest, or the Darcy state).
+template <typename T>
+LocalKernel local_kernel_t(bool t1, bool warm)
 {
-    const bool t1 = tau == 1.0;
-    if (f64) return t1 ? local_keff_kernel<double, true> : local_keff_kernel<double, false>;
-    return t1 ? local_keff_kernel<float, true> : local_keff_kernel<float, false>;
+    if (warm) return t1 ? local_keff_kernel<T, true, true> : local_keff_kernel<T, false, true>;
+    return t1 ? local_keff_kernel<T, true, false> : local_keff_kernel<T, false, false>;
+}
+LocalKernel local_kernel(bool f64, double tau, int warm)
+{
+    return f64 ? local_kernel_t<double>(tau == 1.0, warm != 0) : local_kernel_t<float>(tau == 1.0, warm != 0);
 }
 
 }  // namespace
@@ -484,6 +760,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     if (!std::isfinite(tol_rel) || tol_rel < 0.0) return fail(LBM_EINVAL, "tol_rel must be finite and >= 0");
     if (max_steps < 1 || max_steps >= (int64_t)1 << 31) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31 - 1]");
     if (check_every < 1) return fail(LBM_EINVAL, "check_every must be >= 1");
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(LBM_EINVAL, "warm_start must be 0 or 1");
     if (n_leaves == 0) return LBM_OK;
     if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(keff_dev) ||
         !is_device_ptr(status_dev) || (steps_dev && !is_device_ptr(steps_dev)))
@@ -537,6 +814,9 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     cell_consts(a);
     a.eps_nu = p->eps * nu;
     a.nu_over_g = nu / g_const;
+    a.warm = p->warm_start;
+    a.warm_rho = 3.0 * p->eps * g_const;
+    a.warm_u = g_const / nu;
     a.tol = tol_rel;
     a.check_every = check_every;
     a.max_steps = max_steps;
@@ -597,7 +877,7 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.abort_flag = d_flags + 1;
 
     const bool f64 = p->storage == LBM_F64;
-    const LocalKernel kern = local_kernel(f64, p->tau);
+    const LocalKernel kern = local_kernel(f64, p->tau, p->warm_start);
     const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     LOC_CUDA2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0;
@@ -666,6 +946,9 @@ lbm_status launch_local_from_table(const lbm_params *p, const float *kappa_dev, 
     cell_consts(a);
     a.eps_nu = p->eps * nu;
     a.nu_over_g = nu / g_const;
+    a.warm = p->warm_start;
+    a.warm_rho = 3.0 * p->eps * g_const;
+    a.warm_u = g_const / nu;
     a.tol = tol_rel;
     a.check_every = check_every;
     a.max_steps = max_steps;
@@ -676,7 +959,7 @@ lbm_status launch_local_from_table(const lbm_params *p, const float *kappa_dev, 
     a.abort_flag = table + DT_ABORT;
     a.time_limit_ns = (unsigned long long)(time_limit_s * 1e9);
     const bool f64 = p->storage == LBM_F64;
-    const LocalKernel kern = local_kernel(f64, p->tau);
+    const LocalKernel kern = local_kernel(f64, p->tau, p->warm_start);
     const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -826,6 +1109,7 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     if (!std::isfinite(tol_rel) || tol_rel < 0.0) return fail(LBM_EINVAL, "tol_rel must be finite and >= 0");
     if (max_steps < 1 || max_steps >= (int64_t)1 << 31) return fail(LBM_EINVAL, "max_steps must be in [1, 2^31 - 1]");
     if (check_every < 1) return fail(LBM_EINVAL, "check_every must be >= 1");
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(LBM_EINVAL, "warm_start must be 0 or 1");
     if (n_leaves == 0) return LBM_OK;
     if (!is_device_ptr(kappa_dev) || !is_device_ptr(leaves_dev) || !is_device_ptr(keff_dev) ||
         !is_device_ptr(status_dev) || (steps_dev && !is_device_ptr(steps_dev)))
@@ -903,6 +1187,9 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     cell_consts(a);
     a.eps_nu = p->eps * nu;
     a.nu_over_g = nu / g_const;
+    a.warm = p->warm_start;
+    a.warm_rho = 3.0 * p->eps * g_const;
+    a.warm_u = g_const / nu;
     a.tol = tol_rel;
     a.check_every = check_every;
     a.max_steps = max_steps;
@@ -912,7 +1199,7 @@ extern "C" lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const fl
     a.worst = scr + NA_FLAGS + 1;
     a.abort_flag = scr + NA_FLAGS + 2;
     a.time_limit_ns = (unsigned long long)(g_time_limit_s * 1e9);
-    const LocalKernel kern = local_kernel(f64, p->tau);
+    const LocalKernel kern = local_kernel(f64, p->tau, p->warm_start);
     const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     NA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int blocks = sm_count(dev);

@@ -1552,6 +1552,7 @@ lbm_status lbm_surrogate_keff(lbm_surrogate *s, const lbm_params *p, const float
         return fail(LBM_EINVAL, "nu must be finite and eps finite and >= 0");
     if (p->margin < 0 || p->margin > 32 || p->margin >= p->nx || p->margin >= p->ny)
         return fail(LBM_EINVAL, "margin %d outside [0, 32] or not below the field size", p->margin);
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(LBM_EINVAL, "warm_start must be 0 or 1");
     if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
     if (!(spread_max >= 0.0)) return fail(LBM_EINVAL, "spread_max must be >= 0 (0: the ensemble's per-size gate)");
     if (!std::isfinite(g_const) || g_const == 0.0) return fail(LBM_EINVAL, "g_const must be finite and non-zero");

@@ -60,7 +60,8 @@ def lognormal_kappa3d(nx: int, ny: int, nz: int, ell: float, sigma: float, seed:
     k2 = (2.0 * np.pi * np.fft.fftfreq(nz))[:, None, None] ** 2 + \
         (2.0 * np.pi * np.fft.fftfreq(ny))[None, :, None] ** 2 + \
         (2.0 * np.pi * np.fft.rfftfreq(nx))[None, None, :] ** 2
-    z = np.fft.irfftn(np.fft.rfftn(white) * np.sqrt(np.exp(-0.5 * ell * ell * k2)), s=(nz, ny, nx))
+    z = np.fft.irfftn(np.fft.rfftn(white) * np.sqrt(np.exp(-0.5 * ell * ell * k2)), s=(nz, ny, nx),
+                      axes=(0, 1, 2))
     z -= z.mean()
     sd = z.std()
     if sd == 0.0:

@@ -20,21 +20,21 @@ def _lbm():
     return lbm
 
 
-def gpu_keff(kap, leaves, tau, nu, eps, g, tol, max_steps, k=64, persistent=True):
+def gpu_keff(kap, leaves, tau, nu, eps, g, tol, max_steps, k=64, persistent=True, warm=0, storage=0):
     import torch
     lbm = _lbm()
     ny, nx = kap.shape
-    p = lbm.Params(nx=nx, ny=ny, tau=tau, nu=nu, eps=eps)
+    p = lbm.Params(nx=nx, ny=ny, tau=tau, nu=nu, eps=eps, warm_start=warm, storage=storage)
     kt = torch.from_numpy(np.ascontiguousarray(kap, dtype=np.float32)).cuda()
     lt = torch.from_numpy(np.ascontiguousarray(leaves, dtype=np.int32)).cuda()
     keff, status, steps, worst = lbm.local_keff(p, kt, lt, g, tol, max_steps, k, persistent)
     return keff.cpu().numpy(), status.cpu().numpy(), steps.cpu().numpy(), worst
 
 
-def oracle_keff(kap, leaf, tau, nu, eps, g, tol, max_steps, k=64):
+def oracle_keff(kap, leaf, tau, nu, eps, g, tol, max_steps, k=64, warm=False):
     x0, y0, s = (int(v) for v in leaf)
     patch = np.asarray(kap, dtype=np.float32)[y0:y0 + s, x0:x0 + s].astype(np.float64)
-    return oracle.local_keff(patch, tau, nu, eps, g, tol=tol, max_steps=max_steps, check_every=k)
+    return oracle.local_keff(patch, tau, nu, eps, g, tol=tol, max_steps=max_steps, check_every=k, warm=warm)
 
 
 def assert_keff_close(a, b, rtol):
@@ -237,3 +237,99 @@ def test_oversampling_limits_are_rejected():
             lbm.local_keff(lbm.Params(nx=64, ny=64, tau=1.0, margin=margin), kap, lt)
     with pytest.raises(lbm.LbmError):          # 64 + 2 x 1 cells do not fit the resident patch
         lbm.local_keff(lbm.Params(nx=64, ny=64, tau=1.0, margin=1), kap, lt)
+
+
+# ------------------------------------------------------------------ the Darcy start (warm_start = 1)
+
+def test_darcy_start_fixed_steps_match_oracle():
+    """warm_start = 1: runs on patches of 16 cells or more start from the patch's finite-volume
+    Darcy state, solved in shared memory by conjugate gradients to a relative residual of 1e-5 (the
+    oracle solves it directly in FP64). After a fixed 256 steps K* matches the oracle's warm-started
+    run to 1e-4, for leaves of 8 (which start from rest), 16, 32 and 64 cells, in FP32 and FP64."""
+    kap = synth.lognormal_kappa(128, 128, 6.0, 2.0, seed=27)
+    leaves = np.array([[0, 0, 64], [64, 0, 32], [96, 0, 32], [64, 32, 16], [80, 32, 16], [96, 32, 8],
+                       [0, 64, 64], [64, 64, 16]], dtype=np.int32)
+    tau, nu, eps, g = 1.0, 1.0 / 6.0, 0.9, 1e-6
+    ke, st, steps, worst = gpu_keff(kap, leaves, tau, nu, eps, g, 0.0, 256, warm=1)
+    assert worst == 0 and (steps == 256).all()
+    for i in range(len(leaves)):
+        ref = oracle_keff(kap, leaves[i], tau, nu, eps, g, 0.0, 256, warm=True)
+        assert_keff_close(ke[i], ref["keff"], 1e-4)
+    cold, _, _, _ = gpu_keff(kap, leaves, tau, nu, eps, g, 0.0, 256)
+    small = leaves[:, 2] < 16
+    np.testing.assert_allclose(ke[small], cold[small], rtol=1e-6, atol=0)   # 8-cell leaves start from rest
+    assert not np.array_equal(ke[~small], cold[~small])
+    # the FP64 solver (leaves up to 45 cells) with the same start
+    ke64, st64, _, w64 = gpu_keff(kap, leaves[leaves[:, 2] <= 32], tau, nu, eps, g, 0.0, 256, warm=1, storage=2)
+    assert w64 == 0
+    for i, leaf in enumerate(leaves[leaves[:, 2] <= 32]):
+        ref = oracle_keff(kap, leaf, tau, nu, eps, g, 0.0, 256, warm=True)
+        assert_keff_close(ke64[i], ref["keff"], 1e-4)
+
+
+def test_darcy_start_converges_to_the_rest_start_k_star_in_fewer_steps():
+    """Quadtree leaves of a 256^2 log-normal field (sigma 2) at tol 1e-8: the warm-started runs stop
+    with the K* of the runs from rest within the stop test's band (2e-3: a run stops once its mean
+    velocity drifts by less than tol x check_every per check, and the remaining error of either
+    start decays over up to ~1e5 steps) and take fewer steps in total. Both starts are compared
+    on every entry of K* (off-diagonal ones relative to sqrt(K*_xx K*_yy)): a Darcy-started run
+    stops on the whole mean velocity vector, so its transverse component has settled too."""
+    kap = synth.lognormal_kappa(256, 256, 8.0, 2.0, seed=29)
+    leaves = synth.quadtree_leaves(256, 256, seed=29)
+    tau, nu, eps, g = 1.0, 1.0 / 6.0, 1.0, 1e-6
+    cold, sc, nc, _ = gpu_keff(kap, leaves, tau, nu, eps, g, 1e-8, 200000)
+    warm, sw, nw, _ = gpu_keff(kap, leaves, tau, nu, eps, g, 1e-8, 200000, warm=1)
+    ok = (sc == 0) & (sw == 0)
+    assert ok.mean() > 0.8
+    big = leaves[:, 2] >= 16
+    sel = ok & big
+    scale = np.sqrt(np.abs(cold[:, 0] * cold[:, 3]))
+    d_diag = np.maximum(np.abs(warm[:, 0] / cold[:, 0] - 1), np.abs(warm[:, 3] / cold[:, 3] - 1))[sel]
+    d_off = np.maximum(np.abs(warm[:, 1] - cold[:, 1]), np.abs(warm[:, 2] - cold[:, 2]))[sel] / scale[sel]
+    cost = leaves[:, 2].astype(np.float64) ** 2
+    uc, uw = (cost * nc.sum(axis=1))[big].sum(), (cost * nw.sum(axis=1))[big].sum()
+    print(f"\n{sel.sum()} leaves: diagonal max {d_diag.max():.2e} median {np.median(d_diag):.2e}; "
+          f"off-diagonal max {d_off.max():.2e} median {np.median(d_off):.2e}; "
+          f"lattice updates {uw / uc:.3f} of the rest start's")
+    assert d_diag.max() <= 2e-3 and np.median(d_diag) <= 1e-4
+    assert d_off.max() <= 2e-3 and np.median(d_off) <= 1e-4
+    assert uw < 0.8 * uc
+
+
+def test_darcy_start_tolerance_stop_matches_oracle():
+    """Darcy-started runs on high-contrast 16 x 16 patches (sigma 3) stopped at tol 1e-8 on the
+    whole mean velocity vector, against the oracle's warm-started runs. Where both stop at the
+    same check, K* agrees to 2e-4 (FP32 states on a contrast of e^+-9). The FP32 rounding of the
+    mean velocity is a sizeable part of the drift allowed per check (6.4e-7 relative), so a stop
+    decision often moves by a check or more; both results then lie in the stop test's band and
+    agree to 1e-3."""
+    kap = synth.lognormal_kappa(64, 64, 4.0, 3.0, seed=102)
+    leaves = synth.uniform_leaves(64, 64, 16)
+    tau, nu, eps, g = 1.0, 1.0 / 6.0, 1.0, 1e-6
+    ke, st, steps, worst = gpu_keff(kap, leaves, tau, nu, eps, g, 1e-8, 200000, warm=1)
+    assert worst == 0
+    for i in range(len(leaves)):
+        ref = oracle_keff(kap, leaves[i], tau, nu, eps, g, 1e-8, 200000, warm=True)
+        eq = list(steps[i]) == list(ref["steps"])
+        assert_keff_close(ke[i], ref["keff"], 2e-4 if eq else 1e-3)
+
+
+def test_darcy_start_of_a_uniform_field_is_already_steady():
+    """A uniform field: the Darcy start is Eq. 19's steady state, so every run on a warm-started
+    patch stops at the first possible test (128 steps) with K* = kappa."""
+    kap = np.full((96, 96), 0.05, dtype=np.float32)
+    leaves = np.array([[0, 0, 64], [64, 0, 32], [64, 32, 16]], dtype=np.int32)
+    ke, st, steps, worst = gpu_keff(kap, leaves, 0.8, 0.05, 0.9, 1e-6, 1e-7, 20000, warm=1)
+    assert worst == 0 and (steps == 128).all()
+    np.testing.assert_allclose(ke[:, 0], 0.05, rtol=2e-5)
+    np.testing.assert_allclose(ke[:, 3], 0.05, rtol=2e-5)
+
+
+def test_warm_start_value_is_checked():
+    import torch
+    lbm = _lbm()
+    kap = torch.full((16, 16), 0.05, device="cuda")
+    lt = torch.tensor([[0, 0, 16]], dtype=torch.int32, device="cuda")
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.local_keff(lbm.Params(nx=16, ny=16, tau=1.0, warm_start=2), kap, lt, 1e-6, 0.0, 10)
+    assert ei.value.status == lbm.LBM_EINVAL

@@ -36,6 +36,15 @@ MUTANTS = {
 }
 
 
+# mistakes caught by one slower pin, named beside each
+TARGETED = {
+    # the Darcy-started local problem stopped on the driven mean velocity component alone
+    "warm_stop_driven_only": ([("sqrt(dx * dx + dy * dy) <= tol * check_every * sqrt(m[0] * m[0] + m[1] * m[1])",
+                                "fabs(m[d] - prev[d]) <= tol * check_every * fabs(m[d])")],
+                              "whole_velocity_vector"),
+}
+
+
 # mistakes in the D3Q19 oracle, run against its own pins
 MUTANTS3 = {
     "d3q19_edge_weight": [("(shell == 1 ? 1.0 / 18.0 : 1.0 / 36.0)", "(shell == 1 ? 1.0 / 18.0 : 1.0 / 18.0)")],
@@ -93,6 +102,15 @@ def test_pins_catch_mutant(name, tmp_path):
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
 
 
+@pytest.mark.parametrize("name", sorted(TARGETED))
+def test_targeted_pin_catches_mutant(name, tmp_path):
+    changes, expr = TARGETED[name]
+    so = _build(tmp_path, _mutate(open(SRC).read(), changes), open(SRC3).read(), "mutant")
+    r = _pins(so, "test_oracle_pins.py", expr)
+    assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS3))
 def test_3d_pins_catch_mutant(name, tmp_path):
     so = _build(tmp_path, open(SRC).read(), _mutate(open(SRC3).read(), MUTANTS3[name]), "mutant")
@@ -124,8 +142,8 @@ SUR_MUTANTS = {
                                "if not (stat_lo[k] < stats[i, k] < stat_hi[k]):")],
     "darcy_arithmetic_faces": [("faces.append((np.roll(idx, -1, axis=axis).ravel(), (2.0 * k * kn / (k + kn)).ravel(), axis))",
                                 "faces.append((np.roll(idx, -1, axis=axis).ravel(), (0.5 * (k + kn)).ravel(), axis))")],
-    "darcy_drive_reversed": [("        out.append(np.mean(kf * (p[i] - p[j] + 1.0)))",
-                              "        out.append(np.mean(kf * (p[j] - p[i] + 1.0)))")],
+    "darcy_drive_reversed": [("q.append((kf * (p[i] - p[j] + (1.0 if axis == axis_d else 0.0))).reshape(n_y, n_x))",
+                              "q.append((kf * (p[j] - p[i] + (1.0 if axis == axis_d else 0.0))).reshape(n_y, n_x))")],
     "gate_mean_of_k_not_log": [("keff[i] = (np.exp(mean[0]), 0.0, 0.0, np.exp(mean[1]))",
                                 "keff[i] = (np.exp(y[:, i, 0]).mean(), 0.0, 0.0, np.exp(y[:, i, 1]).mean())")],
 }

@@ -476,3 +476,88 @@ def test_oversampling_uniform_patch_gives_kappa():
     r = oracle.local_keff(np.full((18, 18), 3e-3), 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-12, max_steps=100000, margin=5)
     np.testing.assert_allclose(r["keff"][[0, 3]], 3e-3, rtol=1e-9)
     assert abs(r["keff"][1]) < 1e-15 and abs(r["keff"][2]) < 1e-15
+
+
+# ------------------------------------------------------------------ the Darcy start of local problems
+
+def test_darcy_start_of_a_uniform_patch_is_the_eq19_steady_state():
+    """A uniform patch has zero Darcy pressure and u = kappa G / nu everywhere, so its Darcy start is
+    exactly Eq. 19's steady state f_a = w_a rho0 (1 + e_a . u / c_s^2): one oracle step leaves it
+    unchanged, and the warm-started local problem returns K* = kappa I at its first test."""
+    kap, tau, nu, eps, g = 0.037, 0.8, 0.05, 0.9, 1e-6
+    f0 = oracle.darcy_start(np.full((16, 16), kap), nu, eps, g)
+    u = kap * g / nu
+    for d in range(2):
+        ux, uy = (u, 0.0) if d == 0 else (0.0, u)
+        expect = oracle.W * (1.0 + 3.0 * (oracle.EX * ux + oracle.EY * uy))
+        np.testing.assert_allclose(f0[d], np.broadcast_to(expect, f0[d].shape), rtol=1e-15, atol=1e-18)
+        pr = oracle.Problem(tau, nu, eps, kappa=np.full((16, 16), kap), g=(g if d == 0 else 0.0, g if d else 0.0))
+        np.testing.assert_allclose(pr.step(f0[d]), f0[d], rtol=0, atol=1e-16)
+    r = oracle.local_keff(np.full((16, 16), kap), tau, nu, eps, g, tol=1e-10, max_steps=640, warm=True)
+    # (the K* floor is the cancellation of full-f storage: velocities of 1e-6 against f of 0.4)
+    np.testing.assert_allclose(r["keff"], [kap, 0.0, 0.0, kap], rtol=1e-9, atol=1e-18)
+    assert r["steps"] == [128, 128] and r["converged"] == 2        # the first possible test passes
+
+
+def test_darcy_start_of_parallel_layers_meets_table_2():
+    """Layers along the drive in Table 2's Darcy setting (tau = 1/2, nu = 2e-6, eps = 0.8, G = 2e-6,
+    contrast 10): the Darcy start (no pressure gradient, u = kappa_layer G / nu) is next to the
+    lattice's steady state, and both starts meet Table 2's arithmetic mean (relative error below
+    2e-6); here the drag relaxes the run from rest quickly too, so the start saves no steps."""
+    layers = np.where(np.arange(16) // 2 % 2 == 0, 1e-8, 1e-7)
+    k = np.tile(layers, (16, 1))                       # varies along x: flow along y runs along the layers
+    args = (0.5, 2e-6, 0.8, 2e-6)
+    warm = oracle.local_keff(k, *args, tol=1e-9, max_steps=400000, warm=True)
+    cold = oracle.local_keff(k, *args, tol=1e-9, max_steps=400000)
+    for r in (warm, cold):
+        assert abs(r["keff"][3] / layers.mean() - 1.0) < 2e-6
+    assert warm["steps"][1] <= cold["steps"][1]
+
+
+def test_darcy_start_reaches_the_rest_start_steady_state_sooner():
+    """A random 16 x 16 patch: started from rest or from its Darcy state, the local problem reaches
+    the same K* to a tight tolerance (the steady state is unique), the Darcy start in fewer steps."""
+    k = synth.lognormal_kappa(16, 16, 3.0, 1.5, seed=23).astype(np.float64)
+    cold = oracle.local_keff(k, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-12, max_steps=400000)
+    warm = oracle.local_keff(k, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-12, max_steps=400000, warm=True)
+    assert cold["converged"] == 2 and warm["converged"] == 2
+    np.testing.assert_allclose(warm["keff"], cold["keff"], rtol=1e-6, atol=1e-9 * abs(cold["keff"][0]))
+    assert sum(warm["steps"]) < sum(cold["steps"])
+    # patches below 16 cells (or not a multiple of 8) start from rest: identical to the cold run
+    k12 = k[:12, :12].copy()
+    a = oracle.local_keff(k12, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-8, warm=True)
+    b = oracle.local_keff(k12, 1.0, 1.0 / 6.0, 1.0, 1e-6, tol=1e-8)
+    assert a["steps"] == b["steps"] and np.array_equal(a["keff"], b["keff"])
+
+
+def test_darcy_start_stop_test_on_the_whole_velocity_vector():
+    """High-contrast 16 x 16 patches (sigma 3): a Darcy-started run stopped at tol 1e-8 by the
+    relative change of the whole mean velocity vector lands within 1e-3 of the tightly converged
+    K* (tol 1e-11 from rest; diagonal relative, off-diagonal relative to sqrt(K*_xx K*_yy)).
+    The same start stopped on the driven component alone (Section 3's test) ends earlier on some
+    of these patches with errors of several 1e-3: the transverse component is still moving."""
+    kap = synth.lognormal_kappa(64, 64, 4.0, 3.0, seed=102).astype(np.float64)
+    tau, nu, eps, g = 1.0, 1.0 / 6.0, 1.0, 1e-6
+    worst_driven = 0.0
+    for i in (0, 1, 3, 4, 7, 9):
+        y0, x0 = (i // 4) * 16, (i % 4) * 16
+        k = kap[y0:y0 + 16, x0:x0 + 16]
+        tight = oracle.local_keff(k, tau, nu, eps, g, tol=1e-11, max_steps=3000000)
+        assert tight["converged"] == 2
+        t = tight["keff"]
+        scale = np.sqrt(t[0] * t[3])
+
+        def err(x):
+            return max(abs(x[0] / t[0] - 1), abs(x[3] / t[3] - 1), abs(x[1] - t[1]) / scale, abs(x[2] - t[2]) / scale)
+
+        warm = oracle.local_keff(k, tau, nu, eps, g, tol=1e-8, warm=True)
+        assert warm["converged"] == 2 and err(warm["keff"]) < 1e-3, (i, err(warm["keff"]))
+        f0 = oracle.darcy_start(k, nu, eps, g)
+        kd = np.empty(4)
+        for d in range(2):
+            p = oracle.Problem(tau, nu, eps, kappa=k, g=(g, 0.0) if d == 0 else (0.0, g))
+            f = f0[d].copy()
+            _, ub, _ = p.run_mean_steady(f, d, 1e-8, 200000)
+            kd[[0, 2] if d == 0 else [1, 3]] = ub * nu / g
+        worst_driven = max(worst_driven, err(kd))
+    assert worst_driven > 3e-3
