@@ -66,7 +66,7 @@ class _Problem(C.Structure):
                 ("walls", C.c_int),
                 ("gx", C.c_double), ("gy", C.c_double),
                 ("kappa", C.c_void_p), ("ktensor", C.c_void_p), ("gfield", C.c_void_p),
-                ("force_model", C.c_int)]
+                ("force_model", C.c_int), ("fixed", C.c_void_p)]
 
 
 _lib = None
@@ -97,6 +97,9 @@ def _L():
                                              C.c_double, C.c_double, C.c_long, C.c_int, dp,
                                              dp, dp, C.POINTER(C.c_long)]
         _lib.orc_local_keff_from.restype = C.c_int
+        _lib.orc_local_lg.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_long, C.c_int, dp, dp, dp, C.POINTER(C.c_long)]
+        _lib.orc_local_lg.restype = C.c_int
         _lib.orc_run_mean_steady.argtypes = [C.POINTER(_Problem), dp, C.c_int, C.c_double, C.c_long,
                                              C.c_int, dp, C.POINTER(C.c_int)]
         _lib.orc_run_mean_steady.restype = C.c_long
@@ -350,6 +353,49 @@ def local_keff(kappa_leaf, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, ch
         nconv = _L().orc_local_keff_os(s, int(margin), _dp(k), float(tau), float(nu), float(eps), float(g_const),
                                        float(tol), int(max_steps), int(check_every), _dp(keff), _dp(ub), st)
     return dict(keff=keff, ubar=ub, steps=[st[0], st[1]], converged=int(nconv))
+
+
+def coarse_to_fine(fields, r, x0, y0, se):
+    """Cell-centred coarse fields [k][ny/r][nx/r] (coarse cell (i, j) covers the fine cells
+    [i r, (i + 1) r) x [j r, (j + 1) r)) sampled at the centres of the se x se fine cells from fine
+    cell (x0, y0) on (which may lie outside the field: periodic), by bilinear interpolation between
+    the four nearest coarse centres, periodic. Returns [k][se][se]."""
+    fc = np.asarray(fields, dtype=np.float64)
+    _, nyc, nxc = fc.shape
+    X = (x0 + np.arange(se) + 0.5) / r - 0.5
+    Y = (y0 + np.arange(se) + 0.5) / r - 0.5
+    i0 = np.floor(X).astype(np.int64)
+    j0 = np.floor(Y).astype(np.int64)
+    fx = (X - i0)[None, None, :]
+    fy = (Y - j0)[None, :, None]
+    i0, i1 = i0 % nxc, (i0 + 1) % nxc
+    j0, j1 = j0 % nyc, (j0 + 1) % nyc
+    f00 = fc[:, j0][:, :, i0]
+    f01 = fc[:, j0][:, :, i1]
+    f10 = fc[:, j1][:, :, i0]
+    f11 = fc[:, j1][:, :, i1]
+    return (1 - fy) * ((1 - fx) * f00 + fx * f01) + fy * ((1 - fx) * f10 + fx * f11)
+
+
+def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64):
+    """Local-global local problem of one leaf (orc_local_lg): the se x se patch kappa_ext (the leaf
+    grown by `margin` >= 1 cells on every side) under the drive G along x, then y, closed by a ring
+    of cells fixed at the equilibrium of `state` [2][se][se][3] ((drho, u, v) per cell and drive,
+    from a global coarse solution; also the start). K* = nu U F^-1 from the inner window's mean
+    velocity U and mean force per unit mass F = G e_d - grad(rho) / (3 eps) (Section 2's Brinkman
+    equation at steady state; Eq. 17 when the patch is periodic).
+    Returns dict(keff=[xx, xy, yx, yy], window=[2][4] (mean u, v, d rho/dx, d rho/dy per drive),
+    steps=[s1, s2], converged=n)."""
+    k = np.ascontiguousarray(kappa_ext, dtype=np.float64)
+    se = k.shape[0]
+    st0 = np.ascontiguousarray(state, dtype=np.float64)
+    assert k.shape == (se, se) and st0.shape == (2, se, se, 3) and margin >= 1 and se - 2 * margin >= 1
+    win = np.empty(8)
+    keff = np.empty(4)
+    st = (C.c_long * 2)()
+    nconv = _L().orc_local_lg(se, int(margin), _dp(k), float(tau), float(nu), float(eps), float(g_const),
+                              float(tol), int(max_steps), int(check_every), _dp(st0), _dp(win), _dp(keff), st)
+    return dict(keff=keff, window=win.reshape(2, 4), steps=[st[0], st[1]], converged=int(nconv))
 
 
 def block_average(a, r):

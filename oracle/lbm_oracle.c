@@ -51,6 +51,11 @@ typedef struct {
     const double *ktensor;   /* [ny][nx][4] (xx, xy, yx, yy), used when kappa == NULL */
     const double *gfield;    /* [2][ny][nx] body force, or NULL */
     int force_model;         /* 0: simplified Shan-Chen scheme (Section 2.2); 1: Guo scheme (Section 2.1) */
+    const double *fixed;     /* [ny][nx][4] (flag, drho, u, v), or NULL: a cell with a non-zero flag
+                                emits, every step, instead of its collision result, what a cell at
+                                rest in the state (rho = 1 + drho, u, v) emits at tau = 1: the
+                                equilibrium of Eq. 2 at its post-collision momentum rho u + rho f_m / 2
+                                (f_m of Eq. 5 at u; zero where kappa = 0) (local-global ring) */
 } orc_problem;
 
 /* D2Q9 velocities and weights, built from the angle definitions of Section 2. */
@@ -228,6 +233,7 @@ void orc_step(const orc_problem *p, const double *f, double *fnew)
                 uex = 2.0 * tau * ux + (1.0 - 2.0 * tau) * jx / rho;        /* Eq. 16 */
                 uey = 2.0 * tau * uy + (1.0 - 2.0 * tau) * jy / rho;
             }
+            const double *fx = p->fixed && p->fixed[c * 4] != 0.0 ? p->fixed + c * 4 : NULL;
             for (int a = 0; a < Q; ++a) {
                 double eu = E[a][0] * uex + E[a][1] * uey;
                 double feq = W[a] * rho * (1.0 + eu / cs2);                 /* Eq. 2 */
@@ -235,6 +241,18 @@ void orc_step(const orc_problem *p, const double *f, double *fnew)
                 if (p->force_model == 1) {
                     double ef = E[a][0] * fmx + E[a][1] * fmy;
                     fpost += W[a] * rho * (1.0 - 1.0 / (2.0 * tau)) * ef / cs2;   /* dt F_a, Eqs. 1, 4 */
+                }
+                if (fx) {
+                    const double rb = 1.0 + fx[1];
+                    double Gx, Gy, jpx = 0.0, jpy = 0.0;
+                    force_at(p, c, &Gx, &Gy);
+                    const double kap = p->kappa ? p->kappa[c] : INFINITY;
+                    if (kap != 0.0) {
+                        const double drag = (p->eps * p->nu == 0.0 || isinf(kap)) ? 0.0 : p->eps * p->nu / kap;
+                        jpx = rb * fx[2] + 0.5 * rb * (p->eps * Gx - drag * fx[2]);
+                        jpy = rb * fx[3] + 0.5 * rb * (p->eps * Gy - drag * fx[3]);
+                    }
+                    fpost = W[a] * (rb + (E[a][0] * jpx + E[a][1] * jpy) / cs2);
                 }
                 int xd = x + E[a][0];
                 int yd = y + E[a][1];
@@ -498,6 +516,113 @@ int orc_local_keff_from(int se, int margin, const double *kappa_ext, double tau,
     keff[3] = nu / gconst * ubar[3];
     free(f);
     free(g);
+    return nconv;
+}
+
+/* Mean over the w x w window at (x0, y0) of the density gradient, by central differences cell by
+   cell: (rho(x + 1, y) - rho(x - 1, y)) / 2 and (rho(x, y + 1) - rho(x, y - 1)) / 2. The window
+   must leave one cell on every side inside the lattice. */
+static void mean_density_gradient_window(const orc_problem *p, const double *f, int x0, int y0, int w,
+                                         double out[2])
+{
+    double sx = 0.0, sy = 0.0;
+    for (int y = y0; y < y0 + w; ++y)
+        for (int x = x0; x < x0 + w; ++x) {
+            double r[4] = {0.0, 0.0, 0.0, 0.0};
+            const long nb[4] = {(long)y * p->nx + x + 1, (long)y * p->nx + x - 1, (long)(y + 1) * p->nx + x,
+                                (long)(y - 1) * p->nx + x};
+            for (int k = 0; k < 4; ++k)
+                for (int a = 0; a < Q; ++a) r[k] += f[nb[k] * Q + a];
+            sx += 0.5 * (r[0] - r[1]);
+            sy += 0.5 * (r[2] - r[3]);
+        }
+    out[0] = sx / ((double)w * w);
+    out[1] = sy / ((double)w * w);
+}
+
+/*
+ * Local-global local problem (the treatment the Conclusions name beside oversampling for
+ * high-contrast media): the leaf grown by `margin` >= 1 cells on every side (se = s + 2 margin),
+ * under the constant drive G along x (d = 0) or y (d = 1) as in Section 3, but closed by a ring of
+ * fixed cells instead of periodicity: the outermost cells of the patch emit, every step, the
+ * equilibrium of a given state (drho, u, v) taken from a global coarse solution, and the whole
+ * patch starts from the equilibrium of that state. Stop test as orc_local_keff_from (the whole
+ * mean velocity vector of the inner window). state: [2][se][se][3] (drho, u, v per cell, one
+ * block per drive). win: [2][4], per drive the inner window's mean u, mean v, mean d(rho)/dx and
+ * mean d(rho)/dy.
+ * K* follows from the Brinkman equation of Section 2 at steady state, averaged over the window:
+ * <u> = (K* / nu) <F> with the force per unit mass F = G e_d - grad(p) / (eps rho0), p = c_s^2 rho,
+ * rho0 = 1. With U and F the 2 x 2 matrices whose columns are the two drives, K* = nu U F^-1,
+ * written to keff as (xx, xy, yx, yy). A periodic patch has <grad rho> = 0 and this is Eq. 17.
+ */
+int orc_local_lg(int se, int margin, const double *kappa_ext, double tau, double nu, double eps, double gconst,
+                 double tol, long max_steps, int check_every, const double *state, double win[8], double keff[4],
+                 long steps[2])
+{
+    lattice_init();
+    const int s = se - 2 * margin;
+    if (margin < 1 || s < 1) return -1;
+    orc_problem p;
+    memset(&p, 0, sizeof p);
+    p.nx = se; p.ny = se; p.tau = tau; p.nu = nu; p.eps = eps;
+    p.walls = 0; p.kappa = kappa_ext;
+    long n = (long)se * se;
+    double *f = (double *)malloc(sizeof(double) * n * Q);
+    double *g = (double *)malloc(sizeof(double) * n * Q);
+    double *fixed = (double *)malloc(sizeof(double) * n * 4);
+    int nconv = 0;
+    for (int d = 0; d < 2; ++d) {
+        p.gx = d == 0 ? gconst : 0.0;
+        p.gy = d == 0 ? 0.0 : gconst;
+        const double *sd = state + (long)d * n * 3;
+        for (long c = 0; c < n; ++c) {
+            const int x = (int)(c % se), y = (int)(c / se);
+            fixed[c * 4] = (x == 0 || y == 0 || x == se - 1 || y == se - 1) ? 1.0 : 0.0;
+            fixed[c * 4 + 1] = sd[c * 3];
+            fixed[c * 4 + 2] = sd[c * 3 + 1];
+            fixed[c * 4 + 3] = sd[c * 3 + 2];
+            const double rho = 1.0 + sd[c * 3];
+            for (int a = 0; a < Q; ++a)
+                f[c * Q + a] = W[a] * rho * (1.0 + 3.0 * (E[a][0] * sd[c * 3 + 1] + E[a][1] * sd[c * 3 + 2]));
+        }
+        p.fixed = fixed;
+        double prev[2] = {0.0, 0.0}, m[2];
+        long st = 0;
+        int conv = 0;
+        while (st < max_steps) {
+            orc_step(&p, f, g);
+            memcpy(f, g, sizeof(double) * n * Q);
+            ++st;
+            if (check_every > 0 && st % check_every == 0) {
+                mean_velocity_window(&p, f, margin, margin, s, m);
+                const double dx = m[0] - prev[0], dy = m[1] - prev[1];
+                if (tol > 0.0 && st > check_every &&
+                    sqrt(dx * dx + dy * dy) <= tol * check_every * sqrt(m[0] * m[0] + m[1] * m[1])) {
+                    conv = 1;
+                    break;
+                }
+                prev[0] = m[0];
+                prev[1] = m[1];
+            }
+        }
+        mean_velocity_window(&p, f, margin, margin, s, win + 4 * d);
+        mean_density_gradient_window(&p, f, margin, margin, s, win + 4 * d + 2);
+        steps[d] = st;
+        nconv += conv;
+    }
+    /* columns: drives; rows: components */
+    const double u11 = win[0], u21 = win[1], u12 = win[4], u22 = win[5];
+    const double f11 = gconst - win[2] / (3.0 * eps), f21 = -win[3] / (3.0 * eps);
+    const double f12 = -win[6] / (3.0 * eps), f22 = gconst - win[7] / (3.0 * eps);
+    const double det = f11 * f22 - f12 * f21;
+    const double i11 = f22 / det, i12 = -f12 / det, i21 = -f21 / det, i22 = f11 / det;
+    keff[0] = nu * (u11 * i11 + u12 * i21);   /* K*_xx */
+    keff[1] = nu * (u11 * i12 + u12 * i22);   /* K*_xy */
+    keff[2] = nu * (u21 * i11 + u22 * i21);   /* K*_yx */
+    keff[3] = nu * (u21 * i12 + u22 * i22);   /* K*_yy */
+    free(f);
+    free(g);
+    free(fixed);
     return nconv;
 }
 

@@ -42,6 +42,20 @@ TARGETED = {
     "warm_stop_driven_only": ([("sqrt(dx * dx + dy * dy) <= tol * check_every * sqrt(m[0] * m[0] + m[1] * m[1])",
                                 "fabs(m[d] - prev[d]) <= tol * check_every * fabs(m[d])")],
                               "whole_velocity_vector"),
+    # the local-global ring emitting the equilibrium at rho u, without the half force of Eq. 6
+    "lg_ring_without_half_force": ([("jpx = rb * fx[2] + 0.5 * rb * (p->eps * Gx - drag * fx[2]);", "jpx = rb * fx[2];"),
+                                    ("jpy = rb * fx[3] + 0.5 * rb * (p->eps * Gy - drag * fx[3]);", "jpy = rb * fx[3];")],
+                                   "local_global"),
+    # the pressure term of the mean force with the wrong sign
+    "lg_pressure_term_sign": ([("const double f11 = gconst - win[2] / (3.0 * eps), f21 = -win[3] / (3.0 * eps);",
+                                "const double f11 = gconst + win[2] / (3.0 * eps), f21 = win[3] / (3.0 * eps);"),
+                               ("const double f12 = -win[6] / (3.0 * eps), f22 = gconst - win[7] / (3.0 * eps);",
+                                "const double f12 = win[6] / (3.0 * eps), f22 = gconst + win[7] / (3.0 * eps);")],
+                              "local_global"),
+    # the window's density gradient by a one-sided difference
+    "lg_gradient_not_halved": ([("sx += 0.5 * (r[0] - r[1]);", "sx += (r[0] - r[1]);"),
+                                ("sy += 0.5 * (r[2] - r[3]);", "sy += (r[2] - r[3]);")],
+                               "local_global"),
 }
 
 

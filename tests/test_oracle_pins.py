@@ -561,3 +561,104 @@ def test_darcy_start_stop_test_on_the_whole_velocity_vector():
             kd[[0, 2] if d == 0 else [1, 3]] = ub * nu / g
         worst_driven = max(worst_driven, err(kd))
     assert worst_driven > 3e-3
+
+
+# ------------------------------------------------------------------ local-global local problems
+
+def test_coarse_to_fine_interpolation():
+    """Bilinear interpolation of cell-centred coarse fields: constants stay constant, an affine
+    field is reproduced exactly away from the periodic wrap, and a fine cell whose centre is a
+    coarse centre (odd r) takes the coarse value."""
+    r = 5
+    c = np.full((1, 6, 7), 0.25)
+    np.testing.assert_array_equal(oracle.coarse_to_fine(c, r, -7, 3, 12), np.full((1, 12, 12), 0.25))
+    jj, ii = np.meshgrid(np.arange(6), np.arange(7), indexing="ij")
+    aff = (1.0 + 0.3 * ii - 0.7 * jj)[None]
+    out = oracle.coarse_to_fine(aff, r, 3, 3, 20)[0]          # fine cells 3..22: coarse x in [0.1, 4.1]
+    X = (3 + np.arange(20) + 0.5) / r - 0.5
+    np.testing.assert_allclose(out, 1.0 + 0.3 * X[None, :] - 0.7 * X[:, None], rtol=0, atol=1e-13)
+    rnd = np.random.default_rng(3).normal(size=(2, 6, 7))
+    cen = oracle.coarse_to_fine(rnd, r, 0, 0, 30)
+    np.testing.assert_allclose(cen[:, 2::r, 2::r][:, :6, :6], rnd[:, :6, :6], rtol=0, atol=1e-14)
+
+
+def _lg_state_uniform(kap0, nu, eps, g, se, grads):
+    """Exact steady states of a uniform medium under drive d with a linear density field of gradient
+    grads[d] (in units of 3 eps G): u = (kappa / nu) (G e_d - grad rho / (3 eps))."""
+    xs = np.arange(se) - (se - 1) / 2
+    X, Y = np.meshgrid(xs, xs)
+    state = np.empty((2, se, se, 3))
+    for d, (a, b) in enumerate(grads):
+        state[d, ..., 0] = 3 * eps * g * (a * X + b * Y)
+        state[d, ..., 1] = kap0 / nu * ((g if d == 0 else 0.0) - g * a)
+        state[d, ..., 2] = kap0 / nu * ((g if d == 1 else 0.0) - g * b)
+    return state
+
+
+def test_local_global_uniform_medium_under_a_pressure_gradient():
+    """A uniform medium whose ring holds a linear pressure field and the matching Darcy velocity
+    (a steady state of the lattice for any tau): K* = kappa I, although the mean force matrix F
+    (columns: the two drives) is far from G I. A wrong sign or factor of the pressure term in F,
+    or a transposed U F^-1, gives another tensor."""
+    kap0, tau, nu, eps, g, r, m = 0.02, 0.8, 0.1, 0.9, 1e-6, 12, 3
+    se = r + 2 * m
+    state = _lg_state_uniform(kap0, nu, eps, g, se, [(0.3, 0.2), (-0.1, 0.4)])
+    res = oracle.local_keff_lg(np.full((se, se), kap0), m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000)
+    assert res["converged"] == 2
+    np.testing.assert_allclose(res["keff"] / kap0, [1.0, 0.0, 0.0, 1.0], rtol=0, atol=1e-8)
+    # the window's mean density gradient is the imposed one
+    np.testing.assert_allclose(res["window"][0, 2:] / (3 * eps * g), [0.3, 0.2], rtol=1e-7)
+
+
+def _layered_global_state(kx, ny, tau, nu, eps, g):
+    kap = np.tile(kx, (ny, 1)).astype(np.float64)
+    st = []
+    for d in range(2):
+        p = oracle.Problem(tau, nu, eps, kappa=kap, g=(g, 0.0) if d == 0 else (0.0, g))
+        f = p.rest()
+        p.run(f, 200000, tol=1e-11, check_every=100)
+        rho, u, v = p.fields(f)
+        st.append(np.stack([rho - 1.0, u, v], axis=-1))
+    return kap, st
+
+
+def test_local_global_across_layers_gives_the_windows_harmonic_mean():
+    """Layers across x (widths 4, kappa 1e-2 / 1e-3, tau = 1, Brinkman), ring data from the
+    converged global periodic solution: the velocity is uniform, so the window's K*_xx is the
+    harmonic mean of the window's own columns (Table 1's formula), also for windows that cut the
+    layers off their period; and K* is diagonal. The window's pressure drop is taken by central
+    differences, so each edge of the window and the cell beyond it lie in one layer (where the
+    density is linear)."""
+    kx = np.where((np.arange(16) // 4) % 2 == 0, 1e-2, 1e-3)
+    tau, nu, eps, g = 1.0, 1.0 / 6.0, 1.0, 1e-6
+    kap, st = _layered_global_state(kx, 8, tau, nu, eps, g)
+    m = 5
+    for r, x0w in ((6, 9), (5, 9), (4, 10), (9, 9)):     # 3 + 3, 3 + 2, 2 + 2, 3 + 4 + 2 columns
+        se = r + 2 * m
+        xs = (x0w - m + np.arange(se)) % 16
+        ys = np.arange(se) % 8
+        state = np.stack([s_[np.ix_(ys, xs)] for s_ in st])
+        res = oracle.local_keff_lg(kap[np.ix_(ys, xs)], m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000)
+        k = res["keff"]
+        hm = 1.0 / np.mean(1.0 / kx[(x0w + np.arange(r)) % 16])
+        assert abs(k[0] / hm - 1.0) < 1e-6, (x0w, k[0], hm)
+        assert abs(k[1]) < 1e-8 * hm and abs(k[2]) < 1e-8 * hm
+
+
+def test_local_global_with_whole_periods_is_the_periodic_local_problem():
+    """The same layers, a window of one whole period: with the global solution on the ring the
+    window sees the global flow, so K* equals the periodic local problem of that period (Eq. 17),
+    including K*_yy along the layers where the Brinkman term makes it differ from Table 2's
+    arithmetic mean."""
+    kx = np.where((np.arange(16) // 4) % 2 == 0, 1e-2, 1e-3)
+    tau, nu, eps, g = 1.0, 1.0 / 6.0, 1.0, 1e-6
+    kap, st = _layered_global_state(kx, 8, tau, nu, eps, g)
+    r, m, x0w = 8, 4, 8
+    se = r + 2 * m
+    xs = (x0w - m + np.arange(se)) % 16
+    ys = np.arange(se) % 8
+    state = np.stack([s_[np.ix_(ys, xs)] for s_ in st])
+    lg = oracle.local_keff_lg(kap[np.ix_(ys, xs)], m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000)
+    per = oracle.local_keff(kap[:8, 8:16], tau, nu, eps, g, tol=1e-13, max_steps=1000000)
+    np.testing.assert_allclose(lg["keff"][[0, 3]], per["keff"][[0, 3]], rtol=1e-6)
+    assert abs(lg["keff"][3] / np.mean(kx[8:16]) - 1.0) > 1e-3      # not the Darcy arithmetic mean
