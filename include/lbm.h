@@ -232,6 +232,45 @@ lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_
                                         int32_t check_every, double *keff_dev, int32_t *status_dev,
                                         int32_t *steps_dev, void *cuda_stream);
 
+/* Local-global local problems: the Conclusions name local-global treatments,
+ * beside oversampling, for channelised and high-contrast media, without detail;
+ * this is the library's reading. Every block x block block of the field is a
+ * leaf; its patch is the block grown by p->margin cells on every side (periodic
+ * wrap at the field's edges), driven by G = g_const along x, then along y, as
+ * in Section 3, but closed by a ring of fixed cells instead of periodicity.
+ * The ring holds a global coarse solution: coarse_dev is a caller-owned DEVICE
+ * float [2][3][ny/block][nx/block] array with, for the coarse run driven along
+ * x and then the one driven along y, the density deviation rho - 1 and the
+ * velocity components u and v of each coarse cell (Eq. 15, lbm_coarse_run's
+ * rho/u/v outputs; coarse and fine lattice units share the velocity and
+ * density scale). That state is interpolated bilinearly (periodic) from the
+ * coarse cell centres to every cell of the patch, the density deviation taken
+ * relative to the block's own coarse cell (rho0 = 1 at the block: the global
+ * pressure level is arbitrary); all cells start from its
+ * equilibrium, and each ring cell emits, every step, what a cell in that state
+ * emits after a collision at tau = 1: the equilibrium (Eq. 2) at momentum
+ * rho u + rho f_m / 2 (f_m of Eq. 5 at the ring cell's own kappa; zero where
+ * kappa = 0). A run stops on the relative change of the inner window's whole
+ * mean velocity vector (test as for warm_start = 1). K* follows from Section 2's
+ * Brinkman equation at steady state averaged over the block (the inner window):
+ * <u> = (K* / nu) <F> with F = G e_d - grad(rho) / (3 eps) (p = c_s^2 rho,
+ * rho0 = 1), grad(rho) by central differences cell by cell; with U and F the
+ * 2 x 2 matrices of the two drives' window means, K* = nu U F^-1 (Eq. 17 when
+ * the window's mean density gradient vanishes). K* is not symmetrised.
+ * Requirements: nx, ny multiples of block; p->margin >= 2 and
+ * block + 2 margin <= 64; storage FP32 (LBM_F64 gives LBM_EINVAL);
+ * warm_start = 0; eps > 0. Outputs (caller-owned DEVICE memory):
+ *   keff_dev   double [ny/block][nx/block][4] (xx, xy, yx, yy), fine lattice units;
+ *   status_dev int32  [ny/block][nx/block] as lbm_local_keff_batch;
+ *   steps_dev  int32  [ny/block][nx/block][2], or NULL;
+ *   window_dev double [ny/block][nx/block][2][4], or NULL: per drive the window's
+ *              mean u, mean v, mean d(rho)/dx and mean d(rho)/dy.
+ * Returns as lbm_local_keff_batch; synchronises the stream. */
+lbm_status lbm_local_keff_lg(const lbm_params *p, const float *kappa_dev, int32_t block, const float *coarse_dev,
+                             double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
+                             double *keff_dev, int32_t *status_dev, int32_t *steps_dev, double *window_dev,
+                             void *cuda_stream);
+
 /* Wall-clock bound (seconds, > 0) of one local-problem launch; past it the
  * kernel abandons its remaining jobs with LBM_ETIMEOUT instead of running on.
  * Process-wide; default 600 s. */

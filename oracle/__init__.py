@@ -377,19 +377,24 @@ def coarse_to_fine(fields, r, x0, y0, se):
     return (1 - fy) * ((1 - fx) * f00 + fx * f01) + fy * ((1 - fx) * f10 + fx * f11)
 
 
-def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64):
+def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64,
+                  rho_ref=(0.0, 0.0)):
     """Local-global local problem of one leaf (orc_local_lg): the se x se patch kappa_ext (the leaf
     grown by `margin` >= 1 cells on every side) under the drive G along x, then y, closed by a ring
     of cells fixed at the equilibrium of `state` [2][se][se][3] ((drho, u, v) per cell and drive,
     from a global coarse solution; also the start). K* = nu U F^-1 from the inner window's mean
     velocity U and mean force per unit mass F = G e_d - grad(rho) / (3 eps) (Section 2's Brinkman
-    equation at steady state; Eq. 17 when the patch is periodic).
+    equation at steady state; Eq. 17 when the patch is periodic). rho_ref[d] is subtracted from
+    drive d's density deviations first (the library takes the block's own coarse value, so that
+    rho0 = 1 sits at the block).
     Returns dict(keff=[xx, xy, yx, yy], window=[2][4] (mean u, v, d rho/dx, d rho/dy per drive),
     steps=[s1, s2], converged=n)."""
     k = np.ascontiguousarray(kappa_ext, dtype=np.float64)
     se = k.shape[0]
-    st0 = np.ascontiguousarray(state, dtype=np.float64)
+    st0 = np.array(state, dtype=np.float64, order="C")
     assert k.shape == (se, se) and st0.shape == (2, se, se, 3) and margin >= 1 and se - 2 * margin >= 1
+    for d in range(2):
+        st0[d, ..., 0] -= rho_ref[d]
     win = np.empty(8)
     keff = np.empty(4)
     st = (C.c_long * 2)()

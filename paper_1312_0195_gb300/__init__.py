@@ -180,6 +180,27 @@ def local_keff(params: Params, kappa, leaves, g_const: float = 1e-6, tol_rel: fl
     return keff, status, steps, worst
 
 
+def local_keff_lg(params: Params, kappa, block: int, coarse, g_const: float = 1e-6, tol_rel: float = 1e-8,
+                  max_steps: int = 200000, check_every: int = 64, stream=None):
+    """Allocating convenience over lbm_local_keff_lg (local-global local problems of every
+    block x block block; params.margin >= 2). coarse: float32 [2, 3, ny/block, nx/block] device tensor
+    of the coarse runs' (rho - 1, u, v) driven along x, then y. Returns (keff [nby, nbx, 4] f64,
+    status [nby, nbx], steps [nby, nbx, 2], window [nby, nbx, 2, 4] f64, worst)."""
+    import torch
+    dev = kappa.device
+    nby, nbx = params.ny // block, params.nx // block
+    keff = torch.empty((nby, nbx, 4), dtype=torch.float64, device=dev)
+    status = torch.empty((nby, nbx), dtype=torch.int32, device=dev)
+    steps = torch.empty((nby, nbx, 2), dtype=torch.int32, device=dev)
+    window = torch.empty((nby, nbx, 2, 4), dtype=torch.float64, device=dev)
+    p = params.c()
+    worst = _check(_abi.lib().lbm_local_keff_lg(C.byref(p), _ptr(kappa), int(block), _ptr(coarse), float(g_const),
+                                                float(tol_rel), int(max_steps), int(check_every), _ptr(keff),
+                                                _ptr(status), _ptr(steps), _ptr(window), _stream(stream)),
+                   allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
+    return keff, status, steps, window, worst
+
+
 def lbm_upscale(params: Params, kappa, block: int, keff_coarse, g_const: float = 1e-6, tol_rel: float = 1e-8,
                 max_steps: int = 200000, surrogate=None, spread_max: float = 0.03, stream=None):
     """K* per block x block subdomain (Section 3). Returns (status, n_fallback)."""

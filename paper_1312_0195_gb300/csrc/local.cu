@@ -75,6 +75,9 @@ struct LocalArgs {
                               // variant)
     double warm_rho;          // 3 eps G: density deviation per unit of the unit-drive Darcy pressure
     double warm_u;            // G / nu: velocity per unit of the unit-drive Darcy face flux
+    const float *lg_state;    // local-global jobs: coarse (drho, u, v) [2 drives][3][lg_nyc][lg_nxc]
+    int lg_r, lg_nxc, lg_nyc; // coarse cell size in fine cells, coarse lattice size
+    double *lg_win;           // [n][2][4]: the inner window's mean u, v, d(drho)/dx, d(drho)/dy per drive
     double tol;
     int check_every;
     long long max_steps;
@@ -143,10 +146,10 @@ template <> __device__ __forceinline__ double kc<double>(const LocalArgs &a, int
 // leaves the equilibrium itself, so g_eq is stored directly. Returns rho u and rho.
 template <typename T, bool TAU1>
 __device__ __forceinline__ void collide_d2q9(T (&g)[Q], T e, T hgx, T hgy, const LocalArgs &a, T &rux, T &ruy,
-                                             T &rho)
+                                             T &rho, T &drho)
 {
     const T s13 = g[1] + g[3], s24 = g[2] + g[4], s57 = g[5] + g[7], s68 = g[6] + g[8];
-    const T drho = g[0] + ((s13 + s24) + (s57 + s68));
+    drho = g[0] + ((s13 + s24) + (s57 + s68));
     const T d57 = g[5] - g[7], d86 = g[8] - g[6];
     const T jx = (g[1] - g[3]) + (d57 + d86);
     const T jy = (g[2] - g[4]) + (d57 - d86);
@@ -190,9 +193,13 @@ __device__ __forceinline__ void collide_d2q9(T (&g)[Q], T e, T hgx, T hgy, const
 
 // One lattice step of every active slot; ODD selects the half of the AA pattern. Job starts are
 // aligned to even CTA steps, so the parity of a job's step is the CTA step's, the same for all.
-template <typename T, bool TAU1, bool ODD>
-__device__ __forceinline__ void local_step(T *F, const T *D, T *UX, T *UY, const int4 *hot, const int (&cgeo)[LocalCfg<T>::CPT],
-                                           int s, int s2, unsigned Tcta, T hg, const LocalArgs &a, int tid)
+// LG (local-global jobs): the patch's outermost cells emit a fixed state instead of their
+// collision result: the equilibrium at density deviation D and momentum (UX, UY), set up when the
+// job starts; the other cells also store their density deviation (RHO) with their velocity.
+template <typename T, bool TAU1, bool ODD, bool LG>
+__device__ __forceinline__ void local_step(T *F, const T *D, T *UX, T *UY, T *RHO, const int4 *hot,
+                                           const int (&cgeo)[LocalCfg<T>::CPT], int s, int s2, unsigned Tcta, T hg,
+                                           const LocalArgs &a, int tid)
 {
     constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT;
 #pragma unroll
@@ -225,11 +232,26 @@ __device__ __forceinline__ void local_step(T *F, const T *D, T *UX, T *UY, const
         }
         const T e = D[c];
         const bool along_y = (h.z & 2) != 0;
-        T rux, ruy, rho;
-        collide_d2q9<T, TAU1>(g, e, along_y ? T(0) : hg, along_y ? hg : T(0), a, rux, ruy, rho);
-        if (Tcta == (unsigned)h.w) {
+        T rux, ruy, rho, drho;
+        collide_d2q9<T, TAU1>(g, e, along_y ? T(0) : hg, along_y ? hg : T(0), a, rux, ruy, rho, drho);
+        bool ring = false;
+        if constexpr (LG) {
+            const int lx = geo & 63, ly = (geo >> 6) & 63;
+            ring = lx == 0 || ly == 0 || lx == s - 1 || ly == s - 1;
+            if (ring) {
+                const T dr = D[c], tx = T(3) * UX[c], ty = T(3) * UY[c], sp = tx + ty, sm = tx - ty;
+                const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+                g[0] = T(4.0 / 9.0) * dr;
+                g[1] = w1 * (dr + tx); g[3] = w1 * (dr - tx);
+                g[2] = w1 * (dr + ty); g[4] = w1 * (dr - ty);
+                g[5] = w2 * (dr + sp); g[7] = w2 * (dr - sp);
+                g[8] = w2 * (dr + sm); g[6] = w2 * (dr - sm);
+            }
+        }
+        if (Tcta == (unsigned)h.w && !ring) {
             UX[c] = rux / rho;                                   // Eq. 15
             UY[c] = ruy / rho;
+            if constexpr (LG) RHO[c] = drho;
         }
         if constexpr (!ODD) {
 #pragma unroll
@@ -489,15 +511,86 @@ __device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 
     }
 }
 
-template <typename T, bool TAU1, bool WARM>
+// ---------------------------------------------------------------- local-global jobs
+// The job's patch (its leaf grown by the margin) is closed by a ring of fixed cells instead of
+// periodicity. The coarse solution of the job's drive, (drho, u, v) at the coarse cell centres,
+// is interpolated bilinearly (periodic) to every cell of the patch, drho taken relative to the
+// block's own coarse cell; every cell starts from the
+// equilibrium of that state, and the outermost cells keep emitting, every step, what a cell in
+// that state emits after a collision at tau = 1: the equilibrium at density deviation drho and
+// momentum rho u + rho f_m / 2 (f_m of Eq. 5 at u, the drive along the job's axis; zero momentum
+// where kappa = 0).
+template <typename T>
+__device__ __forceinline__ void lg_start_cell(const LocalArgs &a, T *F, T *D, T *UX, T *UY, int c, const Slot &sl,
+                                              int geo, int s, float kap)
+{
+    constexpr int CMAX = LocalCfg<T>::CMAX;
+    const int lx = geo & 63, ly = (geo >> 6) & 63;
+    // position in coarse cell units (coarse centre i at fine x = (i + 1/2) r - 1/2)
+    const double X = ((double)(sl.x0 + lx) + 0.5) / a.lg_r - 0.5;
+    const double Y = ((double)(sl.y0 + ly) + 0.5) / a.lg_r - 0.5;
+    const double fx0 = floor(X), fy0 = floor(Y);
+    const double wx = X - fx0, wy = Y - fy0;
+    int i0 = (int)fx0 % a.lg_nxc, j0 = (int)fy0 % a.lg_nyc;
+    i0 += i0 < 0 ? a.lg_nxc : 0;
+    j0 += j0 < 0 ? a.lg_nyc : 0;
+    const int i1 = i0 + 1 == a.lg_nxc ? 0 : i0 + 1, j1 = j0 + 1 == a.lg_nyc ? 0 : j0 + 1;
+    const int64_t nc = (int64_t)a.lg_nxc * a.lg_nyc;
+    const float *S = a.lg_state + (int64_t)sl.drive * 3 * nc;
+    double v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float *P = S + k * nc;
+        const double f00 = P[(int64_t)j0 * a.lg_nxc + i0], f01 = P[(int64_t)j0 * a.lg_nxc + i1];
+        const double f10 = P[(int64_t)j1 * a.lg_nxc + i0], f11 = P[(int64_t)j1 * a.lg_nxc + i1];
+        v[k] = (1.0 - wy) * ((1.0 - wx) * f00 + wx * f01) + wy * ((1.0 - wx) * f10 + wx * f11);
+    }
+    // densities relative to the block's own coarse cell: the local problem keeps rho0 = 1 at the
+    // block (the global pressure level is arbitrary and would swamp FP32 deviations)
+    const int bxc = (sl.x0 + a.margin) / a.lg_r, byc = (sl.y0 + a.margin) / a.lg_r;
+    v[0] -= (double)S[(int64_t)byc * a.lg_nxc + bxc];
+    const double rho = 1.0 + v[0];
+    const T drho = (T)v[0], jx = (T)(rho * v[1]), jy = (T)(rho * v[2]);
+    const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+    F[c] = T(4.0 / 9.0) * drho;
+    F[1 * CMAX + c] = w1 * (drho + T(3) * jx);
+    F[3 * CMAX + c] = w1 * (drho - T(3) * jx);
+    F[2 * CMAX + c] = w1 * (drho + T(3) * jy);
+    F[4 * CMAX + c] = w1 * (drho - T(3) * jy);
+    F[5 * CMAX + c] = w2 * (drho + T(3) * (jx + jy));
+    F[7 * CMAX + c] = w2 * (drho - T(3) * (jx + jy));
+    F[8 * CMAX + c] = w2 * (drho + T(3) * (jx - jy));
+    F[6 * CMAX + c] = w2 * (drho - T(3) * (jx - jy));
+    if (lx == 0 || ly == 0 || lx == s - 1 || ly == s - 1) {
+        double jpx = 0.0, jpy = 0.0;
+        if (kap != 0.0f) {
+            const double drag = (a.eps_nu == 0.0 || isinf(kap)) ? 0.0 : a.eps_nu / (double)kap;
+            const double hg = a.half_eps * a.gmag;                 // eps G / 2 along the drive
+            jpx = rho * v[1] + rho * ((sl.drive == 0 ? hg : 0.0) - 0.5 * drag * v[1]);
+            jpy = rho * v[2] + rho * ((sl.drive == 1 ? hg : 0.0) - 0.5 * drag * v[2]);
+        }
+        D[c] = drho;
+        UX[c] = (T)jpx;
+        UY[c] = (T)jpy;
+    } else {
+        D[c] = (T)coef_e(kap, a.eps_nu);
+    }
+}
+
+// MODE: 0 local problems from rest, 1 from the Darcy state (warm_start), 2 local-global jobs
+enum { MODE_REST = 0, MODE_WARM = 1, MODE_LG = 2 };
+
+template <typename T, bool TAU1, int MODE>
 __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs a)
 {
     constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT;
+    constexpr bool WARM = MODE == MODE_WARM, LG = MODE == MODE_LG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *F = reinterpret_cast<T *>(smem_raw);   // [9][CMAX]
-    T *D = F + 9 * CMAX;                      // [CMAX] drag fraction e of each cell
-    T *UX = D + CMAX;                         // [CMAX]
-    T *UY = UX + CMAX;                        // [CMAX]
+    T *D = F + 9 * CMAX;                      // [CMAX] drag fraction e of each cell (ring cells: drho)
+    T *UX = D + CMAX;                         // [CMAX] (ring cells: emitted momentum x)
+    T *UY = UX + CMAX;                        // [CMAX] (ring cells: emitted momentum y)
+    T *RHO = UY + CMAX;                       // [CMAX] density deviation (local-global jobs only)
     __shared__ Slot slots[MAXSLOTS];
     __shared__ int4 hot[MAXSLOTS];            // SlotHot
     __shared__ int s_abort;
@@ -588,9 +681,14 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     int gx = slots[j].x0 + (geo & 63), gy = slots[j].y0 + ((geo >> 6) & 63);
                     gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
                     gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
-                    D[c] = (T)coef_e(a.kappa[(int64_t)gy * a.nx + gx], a.eps_nu);
+                    const float kap = a.kappa[(int64_t)gy * a.nx + gx];
+                    if constexpr (LG) {
+                        lg_start_cell<T>(a, F, D, UX, UY, c, slots[j], geo, s, kap);
+                    } else {
+                        D[c] = (T)coef_e(kap, a.eps_nu);
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) F[q * CMAX + c] = T(0);
+                        for (int q = 0; q < Q; ++q) F[q * CMAX + c] = T(0);
+                    }
                 }
                 __syncthreads();
                 if constexpr (WARM) {
@@ -604,10 +702,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
             if (!__syncthreads_or(tid < nslots && (hot[tid].z & 1))) break;
 
             // ------------------------------------------------------ two steps (even, odd)
-            local_step<T, TAU1, false>(F, D, UX, UY, hot, cgeo, s, s2, Tcta, hg, a, tid);
+            local_step<T, TAU1, false, LG>(F, D, UX, UY, RHO, hot, cgeo, s, s2, Tcta, hg, a, tid);
             ++Tcta;
             __syncthreads();
-            local_step<T, TAU1, true>(F, D, UX, UY, hot, cgeo, s, s2, Tcta, hg, a, tid);
+            local_step<T, TAU1, true, LG>(F, D, UX, UY, RHO, hot, cgeo, s, s2, Tcta, hg, a, tid);
             ++Tcta;
             __syncthreads();
 
@@ -633,7 +731,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                 // job step of the check (or, abandoned unchecked, the step reached)
                 const int t = (int)((check ? (unsigned)h.w : Tcta) - (unsigned)h.x);
                 int st = -1;   // -1: keep going
-                double ux = 0.0, uy = 0.0;
+                double ux = 0.0, uy = 0.0, gxd = 0.0, gyd = 0.0;
                 if (check) {
                     // mean over the leaf: all s2 cells, or the inner window when oversampling
                     const int m = a.margin, hi = s - m;
@@ -652,11 +750,35 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     const double inner = (double)(s - 2 * a.margin) * (double)(s - 2 * a.margin);
                     ux /= inner;
                     uy /= inner;
+                    if constexpr (LG) {
+                        // the inner window's mean density gradient by central differences, summed
+                        // cell by cell, telescopes to its two edge columns (rows) and the ones beyond
+                        double gxs = 0.0, gys = 0.0;
+                        for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
+                            const int loc = c - j * s2, ly = loc / s, lx = loc - ly * s;
+                            const double rc = (double)RHO[c];
+                            if (ly >= m && ly < hi) {
+                                if (lx == hi - 1 || lx == hi) gxs += 0.5 * rc;
+                                if (lx == m || lx == m - 1) gxs -= 0.5 * rc;
+                            }
+                            if (lx >= m && lx < hi) {
+                                if (ly == hi - 1 || ly == hi) gys += 0.5 * rc;
+                                if (ly == m || ly == m - 1) gys -= 0.5 * rc;
+                            }
+                        }
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            gxs += __shfl_xor_sync(0xffffffffu, gxs, off);
+                            gys += __shfl_xor_sync(0xffffffffu, gys, off);
+                        }
+                        gxd = gxs / inner;
+                        gyd = gys / inner;
+                    }
                     const double cur = sl.drive == 0 ? ux : uy, cur_t = sl.drive == 0 ? uy : ux;
                     const bool regular = t == h.y;
                     if (regular) h.y += a.check_every;
                     bool settled;
-                    if (WARM && s >= WARM_MIN && s % 8 == 0) {
+                    if (LG || (WARM && s >= WARM_MIN && s % 8 == 0)) {
                         // a Darcy-started job: the whole mean velocity vector must have settled,
                         // since its transverse component can still carry the start's error after
                         // the driven one has stopped moving
@@ -680,8 +802,18 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                         // Eq. 17: column `drive` of K* from the mean velocity (NaN if abandoned unchecked)
                         const double kx = check ? a.nu_over_g * ux : __longlong_as_double(0x7ff8000000000000LL);
                         const double ky = check ? a.nu_over_g * uy : __longlong_as_double(0x7ff8000000000000LL);
-                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 0 : 1)] = kx;
-                        a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 2 : 3)] = ky;
+                        if constexpr (LG) {
+                            // K* needs both drives: the window means go out, K* is formed afterwards
+                            double *w = a.lg_win + 4 * (2 * (int64_t)sl.leaf + sl.drive);
+                            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+                            w[0] = check ? ux : nan;
+                            w[1] = check ? uy : nan;
+                            w[2] = check ? gxd : nan;
+                            w[3] = check ? gyd : nan;
+                        } else {
+                            a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 0 : 1)] = kx;
+                            a.keff[4 * (int64_t)sl.leaf + (sl.drive == 0 ? 2 : 3)] = ky;
+                        }
                         if (a.steps) a.steps[2 * (int64_t)sl.leaf + sl.drive] = t;
                         if (st != LBM_OK) {
                             atomicMax(&a.status[sl.leaf], st);
@@ -735,20 +867,51 @@ using LocalKernel = void (*)(LocalArgs);
 template <typename T>
 LocalKernel local_kernel_t(bool t1, bool warm)
 {
-    if (warm) return t1 ? local_keff_kernel<T, true, true> : local_keff_kernel<T, false, true>;
-    return t1 ? local_keff_kernel<T, true, false> : local_keff_kernel<T, false, false>;
+    if (warm) return t1 ? local_keff_kernel<T, true, MODE_WARM> : local_keff_kernel<T, false, MODE_WARM>;
+    return t1 ? local_keff_kernel<T, true, MODE_REST> : local_keff_kernel<T, false, MODE_REST>;
 }
 LocalKernel local_kernel(bool f64, double tau, int warm)
 {
     return f64 ? local_kernel_t<double>(tau == 1.0, warm != 0) : local_kernel_t<float>(tau == 1.0, warm != 0);
 }
+// local-global jobs: FP32 only, one more value per cell (the density deviation)
+LocalKernel local_kernel_lg(double tau)
+{
+    return tau == 1.0 ? local_keff_kernel<float, true, MODE_LG> : local_keff_kernel<float, false, MODE_LG>;
+}
+constexpr size_t LG_SMEM = LocalCfg<float>::SMEM + LocalCfg<float>::CMAX * sizeof(float);
 
-}  // namespace
+// K* of each local-global leaf from its two drives' window means (the Brinkman equation of
+// Section 2 at steady state, averaged over the window): <u> = (K* / nu) <F> with
+// F = G e_d - grad(drho) / (3 eps) per drive, so with U and F the 2 x 2 matrices whose columns
+// are the drives, K* = nu U F^-1 (Eq. 17 when grad(drho) = 0).
+__global__ void lg_keff_kernel(const double *win, int64_t n, double nu, double g, double eps, double *keff)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *w = win + 8 * i;
+    const double u11 = w[0], u21 = w[1], u12 = w[4], u22 = w[5];
+    const double f11 = g - w[2] / (3.0 * eps), f21 = -w[3] / (3.0 * eps);
+    const double f12 = -w[6] / (3.0 * eps), f22 = g - w[7] / (3.0 * eps);
+    const double det = f11 * f22 - f12 * f21;
+    const double i11 = f22 / det, i12 = -f12 / det, i21 = -f21 / det, i22 = f11 / det;
+    keff[4 * i + 0] = nu * (u11 * i11 + u12 * i21);
+    keff[4 * i + 1] = nu * (u11 * i12 + u12 * i22);
+    keff[4 * i + 2] = nu * (u21 * i11 + u22 * i21);
+    keff[4 * i + 3] = nu * (u21 * i12 + u22 * i22);
+}
 
-lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev, int32_t n_leaves,
+// what the local-global variant of the solver needs beyond the plain local problems
+struct LgInput {
+    const float *state;   // coarse (drho, u, v) [2][3][nyc][nxc]
+    int r, nxc, nyc;
+    double *win;          // [n][2][4]
+};
+
+lbm_status local_keff_core(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev, int32_t n_leaves,
                            double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
                            int32_t persistent, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
-                           void *cuda_stream, double time_limit_s)
+                           void *cuda_stream, double time_limit_s, const LgInput *lg)
 {
     if (!p) return fail(LBM_EINVAL, "params is NULL");
     if (p->nx < 1 || p->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
@@ -817,6 +980,13 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.warm = p->warm_start;
     a.warm_rho = 3.0 * p->eps * g_const;
     a.warm_u = g_const / nu;
+    if (lg) {
+        a.lg_state = lg->state;
+        a.lg_r = lg->r;
+        a.lg_nxc = lg->nxc;
+        a.lg_nyc = lg->nyc;
+        a.lg_win = lg->win;
+    }
     a.tol = tol_rel;
     a.check_every = check_every;
     a.max_steps = max_steps;
@@ -876,9 +1046,9 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     a.worst = d_flags;
     a.abort_flag = d_flags + 1;
 
-    const bool f64 = p->storage == LBM_F64;
-    const LocalKernel kern = local_kernel(f64, p->tau, p->warm_start);
-    const size_t smem = f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
+    const bool f64 = p->storage == LBM_F64 && !lg;
+    const LocalKernel kern = lg ? local_kernel_lg(p->tau) : local_kernel(f64, p->tau, p->warm_start);
+    const size_t smem = lg ? LG_SMEM : f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     LOC_CUDA2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0;
     LOC_CUDA2(cudaGetDevice(&dev));
@@ -920,6 +1090,78 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
     return LBM_OK;
 #undef LOC_CUDA
 #undef LOC_CUDA2
+}
+
+}  // namespace
+
+lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev, int32_t n_leaves,
+                           double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
+                           int32_t persistent, double *keff_dev, int32_t *status_dev, int32_t *steps_dev,
+                           void *cuda_stream, double time_limit_s)
+{
+    return local_keff_core(p, kappa_dev, leaves_dev, n_leaves, g_const, tol_rel, max_steps, check_every, persistent,
+                           keff_dev, status_dev, steps_dev, cuda_stream, time_limit_s, nullptr);
+}
+
+lbm_status local_keff_lg_impl(const lbm_params *p, const float *kappa_dev, int32_t block, const float *coarse_dev,
+                              double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
+                              double *keff_dev, int32_t *status_dev, int32_t *steps_dev, double *window_dev,
+                              void *cuda_stream, double time_limit_s)
+{
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 1 || p->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
+    if (block < 1 || p->nx % block || p->ny % block)
+        return fail(LBM_EINVAL, "nx, ny must be multiples of block %d", block);
+    const int m = p->margin;
+    if (m < 2 || block + 2 * m > 64)
+        return fail(LBM_EINVAL, "local-global patches need margin >= 2 and block + 2 x margin <= 64 (got %d, %d)",
+                    block, m);
+    if (p->storage == LBM_F64) return fail(LBM_EINVAL, "local-global local problems run in FP32 only");
+    if (p->warm_start != 0) return fail(LBM_EINVAL, "local-global jobs start from the coarse state (warm_start 0)");
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(LBM_EINVAL, "eps must be finite and > 0");
+    if (!coarse_dev || !is_device_ptr(coarse_dev)) return fail(LBM_EINVAL, "coarse_dev must be a device pointer");
+    if (window_dev && !is_device_ptr(window_dev)) return fail(LBM_EINVAL, "window_dev must be a device pointer");
+    if (!keff_dev || !status_dev || !is_device_ptr(keff_dev) || !is_device_ptr(status_dev) ||
+        (steps_dev && !is_device_ptr(steps_dev)))
+        return fail(LBM_EINVAL, "keff, status (and steps) must be device pointers");
+    const int nbx = p->nx / block, nby = p->ny / block;
+    const int64_t n = (int64_t)nbx * nby;
+    if (n > INT32_MAX / 2) return fail(LBM_EINVAL, "too many blocks");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<lbm_leaf> lv((size_t)n);
+    for (int by = 0; by < nby; ++by)
+        for (int bx = 0; bx < nbx; ++bx) lv[(size_t)by * nbx + bx] = lbm_leaf{bx * block, by * block, block};
+    lbm_leaf *d_leaves = nullptr;
+    double *d_win = nullptr;
+    auto release = [&]() {
+        cudaFree(d_leaves);
+        cudaFree(d_win);
+        cudaGetLastError();
+    };
+    cudaError_t e = cudaMalloc(&d_leaves, sizeof(lbm_leaf) * n);
+    if (e == cudaSuccess && !window_dev) e = cudaMalloc(&d_win, sizeof(double) * 8 * n);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_leaves, lv.data(), sizeof(lbm_leaf) * n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        release();
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "local-global set-up: %s",
+                    cudaGetErrorString(e));
+    }
+    LgInput lg{coarse_dev, block, nbx, nby, window_dev ? window_dev : d_win};
+    lbm_status s = local_keff_core(p, kappa_dev, d_leaves, (int32_t)n, g_const, tol_rel, max_steps, check_every, 1,
+                                   keff_dev, status_dev, steps_dev, cuda_stream, time_limit_s, &lg);
+    if (s == LBM_OK || s == LBM_ENOTCONV || s == LBM_ETIMEOUT) {
+        const double nu = p->nu < 0.0 ? (p->tau - 0.5) / 3.0 : p->nu;
+        lg_keff_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lg.win, n, nu, g_const, p->eps, keff_dev);
+        count_launches(1);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            release();
+            return fail(LBM_ECUDA, "local-global K*: %s", cudaGetErrorString(e));
+        }
+    }
+    release();
+    return s;
 }
 
 lbm_status launch_local_from_table(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
@@ -991,6 +1233,15 @@ lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, con
 {
     return lbm::local_keff_impl(p, kappa_dev, leaves_dev, n_leaves, g_const, tol_rel, max_steps, check_every,
                                 persistent, keff_dev, status_dev, steps_dev, cuda_stream, g_time_limit_s);
+}
+
+lbm_status lbm_local_keff_lg(const lbm_params *p, const float *kappa_dev, int32_t block, const float *coarse_dev,
+                             double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
+                             double *keff_dev, int32_t *status_dev, int32_t *steps_dev, double *window_dev,
+                             void *cuda_stream)
+{
+    return lbm::local_keff_lg_impl(p, kappa_dev, block, coarse_dev, g_const, tol_rel, max_steps, check_every,
+                                   keff_dev, status_dev, steps_dev, window_dev, cuda_stream, g_time_limit_s);
 }
 
 lbm_status lbm_set_time_limit(double seconds)

@@ -1,0 +1,134 @@
+"""GPU local-global local problems (lbm_local_keff_lg) against the oracle (orc_local_lg).
+
+Inputs on both sides are the same: the field, and coarse (rho - 1, u, v) arrays per drive that
+the GPU interpolates to the patch itself while the oracle takes them through
+oracle.coarse_to_fine. The GPU stores FP32 deviations and reduces window means in FP64."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _lbm():
+    import paper_1312_0195_gb300 as lbm
+    return lbm
+
+
+def _coarse_state(nbx, nby, seed, g, eps, kap_scale, nu):
+    """Smooth, seeded coarse states of the size a coarse run gives: rho - 1 ~ 3 eps G x (a few
+    cells), velocities ~ kappa G / nu."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((2, 3, nby, nbx), dtype=np.float32)
+    jj, ii = np.meshgrid(np.arange(nby), np.arange(nbx), indexing="ij")
+    for d in range(2):
+        ph = rng.uniform(0, 2 * np.pi, 3)
+        out[d, 0] = 3 * eps * g * 8 * (np.sin(2 * np.pi * ii / nbx + ph[0]) + 0.5 * np.cos(2 * np.pi * jj / nby + ph[1]))
+        u = kap_scale * g / nu * (1.0 + 0.3 * np.sin(2 * np.pi * (ii + jj) / nbx + ph[2]))
+        out[d, 1] = u if d == 0 else 0.2 * u
+        out[d, 2] = 0.2 * u if d == 0 else u
+    return out
+
+
+def _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, tol, max_steps):
+    import torch
+    lbm = _lbm()
+    ny, nx = kap.shape
+    p = lbm.Params(nx=nx, ny=ny, tau=tau, nu=nu, eps=eps, margin=margin)
+    kt = torch.from_numpy(np.ascontiguousarray(kap, dtype=np.float32)).cuda()
+    ct = torch.from_numpy(np.ascontiguousarray(coarse, dtype=np.float32)).cuda()
+    ke, st, steps, win, worst = lbm.local_keff_lg(p, kt, block, ct, g, tol, max_steps)
+    return ke.cpu().numpy(), st.cpu().numpy(), steps.cpu().numpy(), win.cpu().numpy(), worst
+
+
+def _run_oracle(kap, block, margin, coarse, bx, by, tau, nu, eps, g, tol, max_steps):
+    ny, nx = kap.shape
+    se = block + 2 * margin
+    x0, y0 = bx * block - margin, by * block - margin
+    xs, ys = (x0 + np.arange(se)) % nx, (y0 + np.arange(se)) % ny
+    k = np.asarray(kap, dtype=np.float32)[np.ix_(ys, xs)].astype(np.float64)
+    st = np.stack([oracle.coarse_to_fine(coarse[d].astype(np.float64), block, x0, y0, se).transpose(1, 2, 0)
+                   for d in range(2)])
+    ref = [float(coarse[d, 0, by, bx]) for d in range(2)]          # the block's own coarse density
+    return oracle.local_keff_lg(k, margin, st, tau, nu, eps, g, tol=tol, max_steps=max_steps, rho_ref=ref)
+
+
+def test_fixed_steps_match_oracle():
+    """A log-normal field (sigma 1.5), 16-cell blocks grown by 4, a smooth coarse state, 384 fixed
+    steps: every block's window means (u, v and the density gradient, per drive) and K* match the
+    oracle to 1e-4 of their scales, tau = 1 and tau = 0.8."""
+    kap = synth.lognormal_kappa(64, 64, 6.0, 1.5, seed=41)
+    eps, g = 0.9, 1e-6
+    for tau in (1.0, 0.8):
+        nu = (tau - 0.5) / 3.0
+        coarse = _coarse_state(4, 4, 7, g, eps, 1e-2, nu)
+        ke, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 0.0, 384)
+        assert worst == 0 and (steps == 384).all()
+        for by in range(4):
+            for bx in range(4):
+                ref = _run_oracle(kap, 16, 4, coarse, bx, by, tau, nu, eps, g, 0.0, 384)
+                w, wr = win[by, bx], ref["window"]
+                for d in range(2):
+                    us = np.hypot(*wr[d, :2])
+                    gs = np.hypot(*wr[d, 2:]) + 3 * eps * g
+                    assert np.abs(w[d, :2] - wr[d, :2]).max() <= 1e-4 * us, (tau, bx, by, d, w[d], wr[d])
+                    assert np.abs(w[d, 2:] - wr[d, 2:]).max() <= 1e-4 * gs, (tau, bx, by, d, w[d], wr[d])
+                k, kr = ke[by, bx], ref["keff"]
+                scale = np.sqrt(abs(kr[0] * kr[3]))
+                assert np.abs(k - kr).max() <= 1e-4 * scale, (tau, bx, by, k, kr)
+
+
+def test_tolerance_stop_matches_oracle():
+    """The same set-up at tol 1e-8 (stop on the whole window velocity vector): K* agrees with the
+    oracle's within the stop test's band, 1e-3 of the tensor's scale."""
+    kap = synth.lognormal_kappa(64, 64, 6.0, 1.5, seed=43)
+    tau, eps, g = 1.0, 1.0, 1e-6
+    nu = (tau - 0.5) / 3.0
+    coarse = _coarse_state(4, 4, 9, g, eps, 1e-2, nu)
+    ke, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 1e-8, 200000)
+    assert worst == 0
+    for by in range(4):
+        for bx in range(4):
+            ref = _run_oracle(kap, 16, 4, coarse, bx, by, tau, nu, eps, g, 1e-8, 200000)
+            kr = ref["keff"]
+            scale = np.sqrt(abs(kr[0] * kr[3]))
+            assert np.abs(ke[by, bx] - kr).max() <= 1e-3 * scale, (bx, by, ke[by, bx], kr)
+
+
+def test_uniform_medium_under_a_linear_state_gives_kappa():
+    """A uniform medium whose coarse state is a linear pressure field with the matching Darcy
+    velocity (bilinear interpolation reproduces it exactly away from the periodic wrap): every
+    block whose grown patch does not wrap gets K* = kappa I in FP32 (1e-4), although the
+    window's mean force is far from G I."""
+    kap0, tau, eps, g, block, margin = 0.02, 1.0, 0.9, 1e-6, 16, 4
+    nu = (tau - 0.5) / 3.0
+    nb = 8
+    kap = np.full((nb * block, nb * block), kap0, dtype=np.float32)
+    X = (np.arange(nb) + 0.5) * block - 0.5 - nb * block / 2           # coarse centres in fine units
+    Xc, Yc = np.meshgrid(X, X)
+    coarse = np.empty((2, 3, nb, nb), dtype=np.float32)
+    for d, (a, b) in enumerate([(0.3, 0.2), (-0.1, 0.4)]):
+        coarse[d, 0] = 3 * eps * g * (a * Xc + b * Yc)
+        coarse[d, 1] = kap0 / nu * ((g if d == 0 else 0.0) - g * a)
+        coarse[d, 2] = kap0 / nu * ((g if d == 1 else 0.0) - g * b)
+    ke, st, steps, win, worst = _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, 1e-9, 200000)
+    inner = ke[1:nb - 1, 1:nb - 1].reshape(-1, 4) / kap0
+    np.testing.assert_allclose(inner, np.tile([1.0, 0.0, 0.0, 1.0], (len(inner), 1)), rtol=0, atol=1e-4)
+    np.testing.assert_allclose(win[2, 3, 0, 2:] / (3 * eps * g), [0.3, 0.2], rtol=1e-4)
+
+
+def test_rejections():
+    import torch
+    lbm = _lbm()
+    kap = torch.full((32, 32), 0.01, device="cuda")
+    coarse = torch.zeros((2, 3, 2, 2), device="cuda")
+    for kw in (dict(margin=1), dict(margin=25), dict(margin=4, storage=2)):
+        p = lbm.Params(nx=32, ny=32, tau=1.0, **kw)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.local_keff_lg(p, kap, 16, coarse, 1e-6, 1e-8, 100)
+        assert ei.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError):
+        lbm.local_keff_lg(lbm.Params(nx=32, ny=32, tau=1.0, margin=4), kap, 16, coarse.cpu(), 1e-6, 1e-8, 100)
