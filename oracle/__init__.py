@@ -98,7 +98,7 @@ def _L():
                                              dp, dp, C.POINTER(C.c_long)]
         _lib.orc_local_keff_from.restype = C.c_int
         _lib.orc_local_lg.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double, C.c_double,
-                                      C.c_double, C.c_long, C.c_int, dp, dp, dp, C.POINTER(C.c_long)]
+                                      C.c_double, C.c_long, C.c_int, C.c_int, dp, dp, dp, C.POINTER(C.c_long)]
         _lib.orc_local_lg.restype = C.c_int
         _lib.orc_run_mean_steady.argtypes = [C.POINTER(_Problem), dp, C.c_int, C.c_double, C.c_long,
                                              C.c_int, dp, C.POINTER(C.c_int)]
@@ -378,7 +378,7 @@ def coarse_to_fine(fields, r, x0, y0, se):
 
 
 def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max_steps=200000, check_every=64,
-                  rho_ref=(0.0, 0.0)):
+                  rho_ref=(0.0, 0.0), ring=2):
     """Local-global local problem of one leaf (orc_local_lg): the se x se patch kappa_ext (the leaf
     grown by `margin` >= 1 cells on every side) under the drive G along x, then y, closed by a ring
     of cells fixed at the equilibrium of `state` [2][se][se][3] ((drho, u, v) per cell and drive,
@@ -386,7 +386,9 @@ def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max
     velocity U and mean force per unit mass F = G e_d - grad(rho) / (3 eps) (Section 2's Brinkman
     equation at steady state; Eq. 17 when the patch is periodic). rho_ref[d] is subtracted from
     drive d's density deviations first (the library takes the block's own coarse value, so that
-    rho0 = 1 sits at the block).
+    rho0 = 1 sits at the block). ring = 2 (pressure only): the ring keeps the state's density and
+    takes its velocity from the inward neighbours at every check (orc_local_lg); ring = 1 keeps the
+    state's velocity too.
     Returns dict(keff=[xx, xy, yx, yy], window=[2][4] (mean u, v, d rho/dx, d rho/dy per drive),
     steps=[s1, s2], converged=n)."""
     k = np.ascontiguousarray(kappa_ext, dtype=np.float64)
@@ -399,7 +401,8 @@ def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max
     keff = np.empty(4)
     st = (C.c_long * 2)()
     nconv = _L().orc_local_lg(se, int(margin), _dp(k), float(tau), float(nu), float(eps), float(g_const),
-                              float(tol), int(max_steps), int(check_every), _dp(st0), _dp(win), _dp(keff), st)
+                              float(tol), int(max_steps), int(check_every), int(ring), _dp(st0),
+                              _dp(win), _dp(keff), st)
     return dict(keff=keff, window=win.reshape(2, 4), steps=[st[0], st[1]], converged=int(nconv))
 
 

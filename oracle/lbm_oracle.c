@@ -550,14 +550,18 @@ static void mean_density_gradient_window(const orc_problem *p, const double *f, 
  * mean velocity vector of the inner window). state: [2][se][se][3] (drho, u, v per cell, one
  * block per drive). win: [2][4], per drive the inner window's mean u, mean v, mean d(rho)/dx and
  * mean d(rho)/dy.
+ * ring = 1: the ring keeps the state's velocity. ring = 2 (pressure only): the ring keeps the
+ * state's density, and its velocity follows the flow inside: at every check (every check_every
+ * steps) each ring cell takes the velocity (Eq. 15) of its inward neighbour (the diagonal one at a
+ * corner) in the state of that check, and emits with it from the second step after the check on.
  * K* follows from the Brinkman equation of Section 2 at steady state, averaged over the window:
  * <u> = (K* / nu) <F> with the force per unit mass F = G e_d - grad(p) / (eps rho0), p = c_s^2 rho,
  * rho0 = 1. With U and F the 2 x 2 matrices whose columns are the two drives, K* = nu U F^-1,
  * written to keff as (xx, xy, yx, yy). A periodic patch has <grad rho> = 0 and this is Eq. 17.
  */
 int orc_local_lg(int se, int margin, const double *kappa_ext, double tau, double nu, double eps, double gconst,
-                 double tol, long max_steps, int check_every, const double *state, double win[8], double keff[4],
-                 long steps[2])
+                 double tol, long max_steps, int check_every, int ring, const double *state, double win[8],
+                 double keff[4], long steps[2])
 {
     lattice_init();
     const int s = se - 2 * margin;
@@ -570,6 +574,7 @@ int orc_local_lg(int se, int margin, const double *kappa_ext, double tau, double
     double *f = (double *)malloc(sizeof(double) * n * Q);
     double *g = (double *)malloc(sizeof(double) * n * Q);
     double *fixed = (double *)malloc(sizeof(double) * n * 4);
+    double *pend = (double *)malloc(sizeof(double) * n * 2);     /* ring velocities taken at a check */
     int nconv = 0;
     for (int d = 0; d < 2; ++d) {
         p.gx = d == 0 ? gconst : 0.0;
@@ -587,9 +592,15 @@ int orc_local_lg(int se, int margin, const double *kappa_ext, double tau, double
         }
         p.fixed = fixed;
         double prev[2] = {0.0, 0.0}, m[2];
-        long st = 0;
+        long st = 0, apply_at = -1;
         int conv = 0;
         while (st < max_steps) {
+            if (st == apply_at)
+                for (long c = 0; c < n; ++c)
+                    if (fixed[c * 4] != 0.0) {
+                        fixed[c * 4 + 2] = pend[c * 2];
+                        fixed[c * 4 + 3] = pend[c * 2 + 1];
+                    }
             orc_step(&p, f, g);
             memcpy(f, g, sizeof(double) * n * Q);
             ++st;
@@ -603,6 +614,18 @@ int orc_local_lg(int se, int margin, const double *kappa_ext, double tau, double
                 }
                 prev[0] = m[0];
                 prev[1] = m[1];
+                if (ring == 2) {
+                    for (long c = 0; c < n; ++c) {
+                        if (fixed[c * 4] == 0.0) continue;
+                        const int x = (int)(c % se), y = (int)(c / se);
+                        const int xi = x == 0 ? 1 : (x == se - 1 ? se - 2 : x);
+                        const int yi = y == 0 ? 1 : (y == se - 1 ? se - 2 : y);
+                        const long ci = (long)yi * se + xi;
+                        double r2, jx2, jy2;
+                        cell_velocity(&p, ci, f + ci * Q, &r2, &jx2, &jy2, pend + c * 2, pend + c * 2 + 1);
+                    }
+                    apply_at = st + 2;
+                }
             }
         }
         mean_velocity_window(&p, f, margin, margin, s, win + 4 * d);
@@ -623,6 +646,7 @@ int orc_local_lg(int se, int margin, const double *kappa_ext, double tau, double
     free(f);
     free(g);
     free(fixed);
+    free(pend);
     return nconv;
 }
 

@@ -52,6 +52,12 @@ TARGETED = {
                                ("const double f12 = -win[6] / (3.0 * eps), f22 = gconst - win[7] / (3.0 * eps);",
                                 "const double f12 = win[6] / (3.0 * eps), f22 = gconst + win[7] / (3.0 * eps);")],
                               "local_global"),
+    # the pressure-only ring refreshed from the ring cell itself instead of its inward neighbour
+    "lg_ring_velocity_from_itself": ([("const long ci = (long)yi * se + xi;", "const long ci = c; (void)xi; (void)yi;")],
+                                     "local_global"),
+    # the pressure-only ring never refreshed
+    "lg_ring_never_refreshed": ([("                    apply_at = st + 2;", "                    apply_at = -1;")],
+                                "local_global"),
     # the window's density gradient by a one-sided difference
     "lg_gradient_not_halved": ([("sx += 0.5 * (r[0] - r[1]);", "sx += (r[0] - r[1]);"),
                                 ("sy += 0.5 * (r[2] - r[3]);", "sy += (r[2] - r[3]);")],

@@ -595,7 +595,8 @@ def _lg_state_uniform(kap0, nu, eps, g, se, grads):
     return state
 
 
-def test_local_global_uniform_medium_under_a_pressure_gradient():
+@pytest.mark.parametrize("ring", [1, 2])
+def test_local_global_uniform_medium_under_a_pressure_gradient(ring):
     """A uniform medium whose ring holds a linear pressure field and the matching Darcy velocity
     (a steady state of the lattice for any tau): K* = kappa I, although the mean force matrix F
     (columns: the two drives) is far from G I. A wrong sign or factor of the pressure term in F,
@@ -603,7 +604,8 @@ def test_local_global_uniform_medium_under_a_pressure_gradient():
     kap0, tau, nu, eps, g, r, m = 0.02, 0.8, 0.1, 0.9, 1e-6, 12, 3
     se = r + 2 * m
     state = _lg_state_uniform(kap0, nu, eps, g, se, [(0.3, 0.2), (-0.1, 0.4)])
-    res = oracle.local_keff_lg(np.full((se, se), kap0), m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000)
+    res = oracle.local_keff_lg(np.full((se, se), kap0), m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000,
+                               ring=ring)
     assert res["converged"] == 2
     np.testing.assert_allclose(res["keff"] / kap0, [1.0, 0.0, 0.0, 1.0], rtol=0, atol=1e-8)
     # the window's mean density gradient is the imposed one
@@ -622,7 +624,8 @@ def _layered_global_state(kx, ny, tau, nu, eps, g):
     return kap, st
 
 
-def test_local_global_across_layers_gives_the_windows_harmonic_mean():
+@pytest.mark.parametrize("ring", [1, 2])
+def test_local_global_across_layers_gives_the_windows_harmonic_mean(ring):
     """Layers across x (widths 4, kappa 1e-2 / 1e-3, tau = 1, Brinkman), ring data from the
     converged global periodic solution: the velocity is uniform, so the window's K*_xx is the
     harmonic mean of the window's own columns (Table 1's formula), also for windows that cut the
@@ -638,7 +641,8 @@ def test_local_global_across_layers_gives_the_windows_harmonic_mean():
         xs = (x0w - m + np.arange(se)) % 16
         ys = np.arange(se) % 8
         state = np.stack([s_[np.ix_(ys, xs)] for s_ in st])
-        res = oracle.local_keff_lg(kap[np.ix_(ys, xs)], m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000)
+        res = oracle.local_keff_lg(kap[np.ix_(ys, xs)], m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000,
+                                   ring=ring)
         k = res["keff"]
         hm = 1.0 / np.mean(1.0 / kx[(x0w + np.arange(r)) % 16])
         assert abs(k[0] / hm - 1.0) < 1e-6, (x0w, k[0], hm)
@@ -646,10 +650,11 @@ def test_local_global_across_layers_gives_the_windows_harmonic_mean():
 
 
 def test_local_global_with_whole_periods_is_the_periodic_local_problem():
-    """The same layers, a window of one whole period: with the global solution on the ring the
-    window sees the global flow, so K* equals the periodic local problem of that period (Eq. 17),
-    including K*_yy along the layers where the Brinkman term makes it differ from Table 2's
-    arithmetic mean."""
+    """The same layers, a window of one whole period: with the global solution held on the ring
+    (ring = 1) the window sees the global flow, so K* equals the periodic local problem of that
+    period (Eq. 17), including K*_yy along the layers where the Brinkman term makes it differ
+    from Table 2's arithmetic mean. (A pressure-only ring copies velocities across a layer
+    boundary there and is not exact.)"""
     kx = np.where((np.arange(16) // 4) % 2 == 0, 1e-2, 1e-3)
     tau, nu, eps, g = 1.0, 1.0 / 6.0, 1.0, 1e-6
     kap, st = _layered_global_state(kx, 8, tau, nu, eps, g)
@@ -658,7 +663,26 @@ def test_local_global_with_whole_periods_is_the_periodic_local_problem():
     xs = (x0w - m + np.arange(se)) % 16
     ys = np.arange(se) % 8
     state = np.stack([s_[np.ix_(ys, xs)] for s_ in st])
-    lg = oracle.local_keff_lg(kap[np.ix_(ys, xs)], m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000)
+    lg = oracle.local_keff_lg(kap[np.ix_(ys, xs)], m, state, tau, nu, eps, g, tol=1e-12, max_steps=400000,
+                              ring=1)
     per = oracle.local_keff(kap[:8, 8:16], tau, nu, eps, g, tol=1e-13, max_steps=1000000)
     np.testing.assert_allclose(lg["keff"][[0, 3]], per["keff"][[0, 3]], rtol=1e-6)
     assert abs(lg["keff"][3] / np.mean(kx[8:16]) - 1.0) > 1e-3      # not the Darcy arithmetic mean
+
+
+def test_local_global_pressure_only_ring_lets_the_flow_choose_its_velocity():
+    """A permeable uniform medium (kappa = 2, so the Brinkman layer at the ring spans a few cells)
+    under a linear pressure field whose given velocity is wrong (half the Darcy value): the
+    pressure-only ring (ring = 2) takes its velocity from the flow inside and still gives
+    K* = kappa I; a ring that holds the given velocity (ring = 1) drags the window's flow and is
+    off by more than 1 %."""
+    kap0, tau, nu, eps, g, r, m = 2.0, 1.0, 1.0 / 6.0, 1.0, 1e-6, 12, 3
+    se = r + 2 * m
+    state = _lg_state_uniform(kap0, nu, eps, g, se, [(0.3, 0.2), (-0.1, 0.4)])
+    state[..., 1:] *= 0.5
+    kw = dict(tol=1e-12, max_steps=400000)
+    r2 = oracle.local_keff_lg(np.full((se, se), kap0), m, state, tau, nu, eps, g, ring=2, **kw)
+    r1 = oracle.local_keff_lg(np.full((se, se), kap0), m, state, tau, nu, eps, g, ring=1, **kw)
+    assert r2["converged"] == 2
+    np.testing.assert_allclose(r2["keff"] / kap0, [1.0, 0.0, 0.0, 1.0], rtol=0, atol=1e-8)
+    assert np.abs(r1["keff"] / kap0 - [1.0, 0.0, 0.0, 1.0]).max() > 1e-2
