@@ -886,6 +886,11 @@ def main(argv=None):
     ap.add_argument("--pipeline-epochs", type=int, default=10, help="surrogate training epochs of --pipeline")
     ap.add_argument("--pipeline-margins", default="0,4",
                     help="oversampling margins of the local-LBM upscaling runs of --pipeline")
+    ap.add_argument("--pipeline-lg", default="4",
+                    help="margins of the local-global upscaling runs of --pipeline (empty: none)")
+    ap.add_argument("--pipeline-lg-iters", type=int, default=1, help="local-global passes of --pipeline")
+    ap.add_argument("--pipeline-lg-steps", type=int, default=200000,
+                    help="step limit of the local-global local problems (unconverged blocks fall back)")
     args = ap.parse_args(argv)
     ws, rank, local = dist_init()
     if args.pipeline > 0:
@@ -922,9 +927,11 @@ def run_pipeline(args, local):
     Fine run (FP32, tau = 1, nu = nu_eff, eps = 1, G = (1e-6, 0)) for `steps` steps; K* of every r x r
     block (Eq. 17) by the surrogate ensemble with local-LBM fallback (trained on the r x r blocks of
     a 4096^2 channelised field of another seed) and by local LBM alone for each oversampling margin
-    of --pipeline-margins (0: the paper's plain local problems); coarse runs (Eq. 18, tensor
-    K*, scaled parameters) for steps / r steps, the same physical time; relative L2 error of the
-    coarse velocity against the r x r block average of the fine velocity. Prints one JSON line."""
+    of --pipeline-margins (0: the paper's plain local problems); with --pipeline-lg, local-global
+    K* (pressure-only ring held at the steady coarse runs with the plain K*, margins as given,
+    --pipeline-lg-iters passes, falling back to the plain K* block by block); coarse runs (Eq. 18,
+    tensor K*, scaled parameters) for steps / r steps, the same physical time; relative L2 error of
+    the coarse velocity against the r x r block average of the fine velocity. Prints one JSON line."""
     import torch
     import paper_1312_0195_gb300 as lbm
     import synth
@@ -981,6 +988,32 @@ def run_pipeline(args, local):
         pm = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, gx=1e-6, gy=0.0, margin=m)
         (st_l, _), t_l = timed(lambda: lbm.lbm_upscale(pm, kt, r, keff[f"lbm_m{m}"], 1e-6, 1e-8, 200000))
         out["upscale"][f"lbm_margin{m}"] = {"seconds": t_l, "blocks_per_s": nb * nb / t_l, "status": st_l}
+    # local-global local problems (pressure-only ring) from the steady coarse runs with the plain
+    # K*, falling back to it for blocks that do not converge or give an unusable tensor
+    lg_margins = [int(v) for v in args.pipeline_lg.split(",") if v.strip()]
+    if lg_margins and 0 in margins:
+        for m in lg_margins:
+            kcur = keff["lbm_m0"]
+            for it in range(args.pipeline_lg_iters):
+                cs = torch.empty((2, 3, nb, nb), dtype=torch.float32, device="cuda")
+
+                def states():
+                    for d in range(2):
+                        pd = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, gx=1e-6 if d == 0 else 0.0,
+                                        gy=0.0 if d == 0 else 1e-6)
+                        lbm.lbm_coarse_run(pd, r, kcur, None, 400000, 1e-7, 64, cs[d, 0], cs[d, 1], cs[d, 2])
+                        cs[d, 0] -= 1.0
+                _, t_cs = timed(states)
+                pm = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, margin=m)
+                (kl, st_l, _, _, _, nfb_l), t_l = timed(lambda: lbm.local_keff_lg(
+                    pm, kt, r, cs, 1e-6, 1e-8, args.pipeline_lg_steps, ring=2, fallback=keff["lbm_m0"]))
+                name = f"local_global_m{m}" + (f"_it{it + 1}" if it else "")
+                keff[name] = kl
+                out["upscale"][name] = {"coarse_states_seconds": t_cs, "seconds": t_l, "blocks_per_s": nb * nb / t_l,
+                                        "not_converged": int((st_l != 0).sum()), "fallback_blocks": nfb_l,
+                                        "max_steps": args.pipeline_lg_steps}
+                kcur = kl
+                del cs
     if 0 in margins:
         kl, ks = keff["lbm_m0"], keff["surrogate"]
         rel = torch.stack([(ks[..., 0] / kl[..., 0] - 1).abs(), (ks[..., 3] / kl[..., 3] - 1).abs()]).flatten()

@@ -246,17 +246,29 @@ lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_
  * density scale). That state is interpolated bilinearly (periodic) from the
  * coarse cell centres to every cell of the patch, the density deviation taken
  * relative to the block's own coarse cell (rho0 = 1 at the block: the global
- * pressure level is arbitrary); all cells start from its
- * equilibrium, and each ring cell emits, every step, what a cell in that state
- * emits after a collision at tau = 1: the equilibrium (Eq. 2) at momentum
- * rho u + rho f_m / 2 (f_m of Eq. 5 at the ring cell's own kappa; zero where
- * kappa = 0). A run stops on the relative change of the inner window's whole
- * mean velocity vector (test as for warm_start = 1). K* follows from Section 2's
+ * pressure level is arbitrary); all cells start from its equilibrium. Each ring
+ * cell emits, every step, what a cell at its density emits after a collision at
+ * tau = 1: the equilibrium (Eq. 2) at momentum rho u + rho f_m / 2 (f_m of Eq. 5
+ * at the ring cell's own kappa; zero where kappa = 0). ring = 1: u is the coarse
+ * state's velocity. ring = 2 (pressure only): u starts there and is refreshed at
+ * every check from the velocity of the ring cell's inward neighbour (diagonal at
+ * corners), acting from the second step after the check; check_every must be
+ * even. A run stops on the relative change of the inner window's whole mean
+ * velocity vector (test as for warm_start = 1). K* follows from Section 2's
  * Brinkman equation at steady state averaged over the block (the inner window):
  * <u> = (K* / nu) <F> with F = G e_d - grad(rho) / (3 eps) (p = c_s^2 rho,
  * rho0 = 1), grad(rho) by central differences cell by cell; with U and F the
  * 2 x 2 matrices of the two drives' window means, K* = nu U F^-1 (Eq. 17 when
- * the window's mean density gradient vanishes). K* is not symmetrised.
+ * the window's mean density gradient vanishes). A block whose whole patch has
+ * one kappa runs no local problem: Darcy flow through a uniform medium gives
+ * K* = kappa I under any boundary pressure; it gets that, status LBM_OK, 0 steps
+ * and a NaN window.
+ * keff_fallback_dev: NULL (K* as computed, not symmetrised), or a caller-owned
+ * DEVICE double [ny/block][nx/block][4] of tensors to fall back to (e.g. the
+ * periodic local problems' K*): a block then keeps its K*, symmetrised, only
+ * when its run met the tolerance, the symmetrised tensor is positive definite
+ * and the 2-norm condition number of its F is at most 10; otherwise it takes
+ * the fallback, and *n_fallback (HOST, may be NULL) counts those blocks.
  * Requirements: nx, ny multiples of block; p->margin >= 2 and
  * block + 2 margin <= 64; storage FP32 (LBM_F64 gives LBM_EINVAL);
  * warm_start = 0; eps > 0. Outputs (caller-owned DEVICE memory):
@@ -267,9 +279,9 @@ lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_
  *              mean u, mean v, mean d(rho)/dx and mean d(rho)/dy.
  * Returns as lbm_local_keff_batch; synchronises the stream. */
 lbm_status lbm_local_keff_lg(const lbm_params *p, const float *kappa_dev, int32_t block, const float *coarse_dev,
-                             double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
-                             double *keff_dev, int32_t *status_dev, int32_t *steps_dev, double *window_dev,
-                             void *cuda_stream);
+                             double g_const, double tol_rel, int64_t max_steps, int32_t check_every, int32_t ring,
+                             const double *keff_fallback_dev, double *keff_dev, int32_t *status_dev,
+                             int32_t *steps_dev, double *window_dev, int32_t *n_fallback, void *cuda_stream);
 
 /* Wall-clock bound (seconds, > 0) of one local-problem launch; past it the
  * kernel abandons its remaining jobs with LBM_ETIMEOUT instead of running on.

@@ -406,6 +406,31 @@ def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max
     return dict(keff=keff, window=win.reshape(2, 4), steps=[st[0], st[1]], converged=int(nconv))
 
 
+def lg_select(keff_lg, window, ok, keff_ref, g_const, eps, cond_max=10.0):
+    """Which local-global K* to keep (the library's rule when it is given fallback tensors): a
+    block keeps its local-global K*, symmetrised (K*_xy = K*_yx = their mean), when its run met
+    the tolerance (ok), that symmetrised tensor is positive definite, and the 2-norm condition
+    number of its force matrix F (columns: the two drives' G e_d - grad(rho) / (3 eps)) is at most
+    cond_max; otherwise it takes keff_ref. Arrays [n][4], window [n][2][4], ok [n] bool.
+    Returns (keff [n][4], used_fallback [n] bool)."""
+    k = np.array(keff_lg, dtype=np.float64).reshape(-1, 4)
+    w = np.asarray(window, dtype=np.float64).reshape(-1, 2, 4)
+    ref = np.asarray(keff_ref, dtype=np.float64).reshape(-1, 4)
+    out = np.empty_like(k)
+    fb = np.empty(len(k), dtype=bool)
+    for i in range(len(k)):
+        sym = 0.5 * (k[i, 1] + k[i, 2])
+        ks = np.array([[k[i, 0], sym], [sym, k[i, 3]]])
+        F = np.array([[g_const - w[i, 0, 2] / (3 * eps), -w[i, 1, 2] / (3 * eps)],
+                      [-w[i, 0, 3] / (3 * eps), g_const - w[i, 1, 3] / (3 * eps)]])
+        sv = np.linalg.svd(F, compute_uv=False) if np.all(np.isfinite(F)) else np.array([1.0, 0.0])
+        good = bool(ok[i]) and np.all(np.isfinite(ks)) and ks[0, 0] > 0 and np.linalg.det(ks) > 0 \
+            and sv[1] > 0 and sv[0] / sv[1] <= cond_max
+        fb[i] = not good
+        out[i] = [ks[0, 0], sym, sym, ks[1, 1]] if good else ref[i]
+    return out, fb
+
+
 def block_average(a, r):
     a = np.ascontiguousarray(a, dtype=np.float64)
     ny, nx = a.shape

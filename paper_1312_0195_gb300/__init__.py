@@ -181,11 +181,13 @@ def local_keff(params: Params, kappa, leaves, g_const: float = 1e-6, tol_rel: fl
 
 
 def local_keff_lg(params: Params, kappa, block: int, coarse, g_const: float = 1e-6, tol_rel: float = 1e-8,
-                  max_steps: int = 200000, check_every: int = 64, stream=None):
+                  max_steps: int = 200000, check_every: int = 64, ring: int = 2, fallback=None, stream=None):
     """Allocating convenience over lbm_local_keff_lg (local-global local problems of every
     block x block block; params.margin >= 2). coarse: float32 [2, 3, ny/block, nx/block] device tensor
-    of the coarse runs' (rho - 1, u, v) driven along x, then y. Returns (keff [nby, nbx, 4] f64,
-    status [nby, nbx], steps [nby, nbx, 2], window [nby, nbx, 2, 4] f64, worst)."""
+    of the coarse runs' (rho - 1, u, v) driven along x, then y; ring 2 = pressure only, 1 = the
+    coarse velocity held; fallback: None or float64 [nby, nbx, 4] device tensor of tensors to fall
+    back to. Returns (keff [nby, nbx, 4] f64, status [nby, nbx], steps [nby, nbx, 2],
+    window [nby, nbx, 2, 4] f64, worst, n_fallback)."""
     import torch
     dev = kappa.device
     nby, nbx = params.ny // block, params.nx // block
@@ -193,12 +195,14 @@ def local_keff_lg(params: Params, kappa, block: int, coarse, g_const: float = 1e
     status = torch.empty((nby, nbx), dtype=torch.int32, device=dev)
     steps = torch.empty((nby, nbx, 2), dtype=torch.int32, device=dev)
     window = torch.empty((nby, nbx, 2, 4), dtype=torch.float64, device=dev)
+    nfb = C.c_int32(0)
     p = params.c()
     worst = _check(_abi.lib().lbm_local_keff_lg(C.byref(p), _ptr(kappa), int(block), _ptr(coarse), float(g_const),
-                                                float(tol_rel), int(max_steps), int(check_every), _ptr(keff),
-                                                _ptr(status), _ptr(steps), _ptr(window), _stream(stream)),
+                                                float(tol_rel), int(max_steps), int(check_every), int(ring),
+                                                _ptr(fallback), _ptr(keff), _ptr(status), _ptr(steps), _ptr(window),
+                                                C.byref(nfb), _stream(stream)),
                    allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
-    return keff, status, steps, window, worst
+    return keff, status, steps, window, worst, int(nfb.value)
 
 
 def lbm_upscale(params: Params, kappa, block: int, keff_coarse, g_const: float = 1e-6, tol_rel: float = 1e-8,

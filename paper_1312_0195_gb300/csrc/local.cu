@@ -77,6 +77,8 @@ struct LocalArgs {
     double warm_u;            // G / nu: velocity per unit of the unit-drive Darcy face flux
     const float *lg_state;    // local-global jobs: coarse (drho, u, v) [2 drives][3][lg_nyc][lg_nxc]
     int lg_r, lg_nxc, lg_nyc; // coarse cell size in fine cells, coarse lattice size
+    int lg_ring;              // 1: the ring holds the coarse velocity; 2: pressure only (velocity
+                              // refreshed from the inward neighbours at every check)
     double *lg_win;           // [n][2][4]: the inner window's mean u, v, d(drho)/dx, d(drho)/dy per drive
     double tol;
     int check_every;
@@ -520,6 +522,28 @@ __device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 
 // that state emits after a collision at tau = 1: the equilibrium at density deviation drho and
 // momentum rho u + rho f_m / 2 (f_m of Eq. 5 at u, the drive along the job's axis; zero momentum
 // where kappa = 0).
+// The momentum a ring cell emits with: rho u + rho f_m / 2 for its density 1 + D[c] and the
+// velocity (ux, uy), f_m of Eq. 5 at the cell's own kappa (zero momentum where kappa = 0).
+template <typename T>
+__device__ __forceinline__ void lg_ring_momentum(const LocalArgs &a, const T *D, T *UX, T *UY, int c, const Slot &sl,
+                                                 int lx, int ly, double ux, double uy)
+{
+    int gx = sl.x0 + lx, gy = sl.y0 + ly;
+    gx = gx < 0 ? gx + a.nx : (gx >= a.nx ? gx - a.nx : gx);
+    gy = gy < 0 ? gy + a.ny : (gy >= a.ny ? gy - a.ny : gy);
+    const float kap = a.kappa[(int64_t)gy * a.nx + gx];
+    const double rho = 1.0 + (double)D[c];
+    double jpx = 0.0, jpy = 0.0;
+    if (kap != 0.0f) {
+        const double drag = (a.eps_nu == 0.0 || isinf(kap)) ? 0.0 : a.eps_nu / (double)kap;
+        const double hg = a.half_eps * a.gmag;                     // eps G / 2 along the drive
+        jpx = rho * ux + rho * ((sl.drive == 0 ? hg : 0.0) - 0.5 * drag * ux);
+        jpy = rho * uy + rho * ((sl.drive == 1 ? hg : 0.0) - 0.5 * drag * uy);
+    }
+    UX[c] = (T)jpx;
+    UY[c] = (T)jpy;
+}
+
 template <typename T>
 __device__ __forceinline__ void lg_start_cell(const LocalArgs &a, T *F, T *D, T *UX, T *UY, int c, const Slot &sl,
                                               int geo, int s, float kap)
@@ -562,16 +586,8 @@ __device__ __forceinline__ void lg_start_cell(const LocalArgs &a, T *F, T *D, T 
     F[8 * CMAX + c] = w2 * (drho + T(3) * (jx - jy));
     F[6 * CMAX + c] = w2 * (drho - T(3) * (jx - jy));
     if (lx == 0 || ly == 0 || lx == s - 1 || ly == s - 1) {
-        double jpx = 0.0, jpy = 0.0;
-        if (kap != 0.0f) {
-            const double drag = (a.eps_nu == 0.0 || isinf(kap)) ? 0.0 : a.eps_nu / (double)kap;
-            const double hg = a.half_eps * a.gmag;                 // eps G / 2 along the drive
-            jpx = rho * v[1] + rho * ((sl.drive == 0 ? hg : 0.0) - 0.5 * drag * v[1]);
-            jpy = rho * v[2] + rho * ((sl.drive == 1 ? hg : 0.0) - 0.5 * drag * v[2]);
-        }
         D[c] = drho;
-        UX[c] = (T)jpx;
-        UY[c] = (T)jpy;
+        lg_ring_momentum<T>(a, D, UX, UY, c, sl, lx, ly, v[1], v[2]);
     } else {
         D[c] = (T)coef_e(kap, a.eps_nu);
     }
@@ -773,6 +789,19 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                         }
                         gxd = gxs / inner;
                         gyd = gys / inner;
+                        if (a.lg_ring == 2) {
+                            // pressure-only ring: each ring cell takes the velocity its inward
+                            // neighbour stored at this check; the CTA's next step is the second
+                            // after the check (checks fall on even job steps)
+                            for (int c = j * s2 + lane; c < (j + 1) * s2; c += 32) {
+                                const int loc = c - j * s2, ly = loc / s, lx = loc - ly * s;
+                                if (!(lx == 0 || ly == 0 || lx == s - 1 || ly == s - 1)) continue;
+                                const int xi = lx == 0 ? 1 : (lx == s - 1 ? s - 2 : lx);
+                                const int yi = ly == 0 ? 1 : (ly == s - 1 ? s - 2 : ly);
+                                const int ci = j * s2 + yi * s + xi;
+                                lg_ring_momentum<T>(a, D, UX, UY, c, sl, lx, ly, (double)UX[ci], (double)UY[ci]);
+                            }
+                        }
                     }
                     const double cur = sl.drive == 0 ? ux : uy, cur_t = sl.drive == 0 ? uy : ux;
                     const bool regular = t == h.y;
@@ -885,26 +914,98 @@ constexpr size_t LG_SMEM = LocalCfg<float>::SMEM + LocalCfg<float>::CMAX * sizeo
 // Section 2 at steady state, averaged over the window): <u> = (K* / nu) <F> with
 // F = G e_d - grad(drho) / (3 eps) per drive, so with U and F the 2 x 2 matrices whose columns
 // are the drives, K* = nu U F^-1 (Eq. 17 when grad(drho) = 0).
-__global__ void lg_keff_kernel(const double *win, int64_t n, double nu, double g, double eps, double *keff)
+// One warp per block: kuni[i] = kappa if every cell of the block's patch (the block grown by m,
+// periodic) has the same kappa, else -1. Such a block's local-global K* is kappa I exactly (Darcy
+// flow through a uniform medium under any boundary pressure), so it needs no local problem.
+__global__ void lg_uniform_kernel(const float *kappa, int nx, int ny, int block, int m, int nbx, int64_t n,
+                                  float *kuni)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const int by = (int)(w / nbx), bx = (int)(w - (int64_t)by * nbx), se = block + 2 * m;
+    auto at = [&](int c) {
+        const int ly = c / se, lx = c - ly * se;
+        int x = bx * block - m + lx, y = by * block - m + ly;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        return kappa[(int64_t)y * nx + x];
+    };
+    const float k0 = at(0);
+    bool same = k0 >= 0.0f;
+    for (int c = lane; c < se * se && same; c += 32) same = at(c) == k0;
+    same = __all_sync(0xffffffffu, same);
+    if (lane == 0) kuni[w] = same ? k0 : -1.0f;
+}
+
+// Per block: a uniform patch takes K* = kappa I (status LBM_OK, no steps, window NaN). Otherwise
+// K* from its two drives' window means (the Brinkman equation of Section 2 at steady state,
+// averaged over the window): <u> = (K* / nu) <F> with F = G e_d - grad(drho) / (3 eps) per drive,
+// so with U and F the 2 x 2 matrices whose columns are the drives, K* = nu U F^-1 (Eq. 17 when
+// grad(drho) = 0). With fallback tensors (kref) such a block keeps its K*, symmetrised, only when
+// its run met the tolerance, the symmetrised tensor is positive definite and the 2-norm condition
+// number of F is at most LG_COND_MAX; otherwise it takes kref (counted in nfb).
+constexpr double LG_COND_MAX = 10.0;
+__global__ void lg_finish_kernel(int64_t n, const int *pos, const float *kuni, const double *win_h,
+                                 const int32_t *status_h, const int32_t *steps_h, double nu, double g, double eps,
+                                 const double *kref, double *keff, int32_t *status, int32_t *steps, double *window,
+                                 int *nfb)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double *w = win + 8 * i;
+    const int j = pos[i];
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (j < 0) {
+        const double k0 = kuni[i];
+        keff[4 * i + 0] = k0;
+        keff[4 * i + 1] = 0.0;
+        keff[4 * i + 2] = 0.0;
+        keff[4 * i + 3] = k0;
+        status[i] = LBM_OK;
+        if (steps) steps[2 * i] = steps[2 * i + 1] = 0;
+        if (window)
+            for (int q = 0; q < 8; ++q) window[8 * i + q] = nan;
+        return;
+    }
+    const double *w = win_h + 8 * (int64_t)j;
+    status[i] = status_h[j];
+    if (steps) {
+        steps[2 * i] = steps_h[2 * (int64_t)j];
+        steps[2 * i + 1] = steps_h[2 * (int64_t)j + 1];
+    }
+    if (window)
+        for (int q = 0; q < 8; ++q) window[8 * i + q] = w[q];
     const double u11 = w[0], u21 = w[1], u12 = w[4], u22 = w[5];
     const double f11 = g - w[2] / (3.0 * eps), f21 = -w[3] / (3.0 * eps);
     const double f12 = -w[6] / (3.0 * eps), f22 = g - w[7] / (3.0 * eps);
     const double det = f11 * f22 - f12 * f21;
     const double i11 = f22 / det, i12 = -f12 / det, i21 = -f21 / det, i22 = f11 / det;
-    keff[4 * i + 0] = nu * (u11 * i11 + u12 * i21);
-    keff[4 * i + 1] = nu * (u11 * i12 + u12 * i22);
-    keff[4 * i + 2] = nu * (u21 * i11 + u22 * i21);
-    keff[4 * i + 3] = nu * (u21 * i12 + u22 * i22);
+    double k[4] = {nu * (u11 * i11 + u12 * i21), nu * (u11 * i12 + u12 * i22), nu * (u21 * i11 + u22 * i21),
+                   nu * (u21 * i12 + u22 * i22)};
+    if (kref) {
+        const double sym = 0.5 * (k[1] + k[2]);
+        // singular values of F from its Frobenius norm and determinant
+        const double fro = f11 * f11 + f12 * f12 + f21 * f21 + f22 * f22;
+        const double disc = sqrt(fmax(fro * fro - 4.0 * det * det, 0.0));
+        const double smax = sqrt(0.5 * (fro + disc)), smin = sqrt(fmax(0.5 * (fro - disc), 0.0));
+        const bool good = status_h[j] == LBM_OK && isfinite(k[0]) && isfinite(sym) && isfinite(k[3]) && k[0] > 0.0 &&
+                          k[0] * k[3] - sym * sym > 0.0 && smin > 0.0 && smax <= LG_COND_MAX * smin;
+        if (good) {
+            k[1] = sym;
+            k[2] = sym;
+        } else {
+            for (int q = 0; q < 4; ++q) k[q] = kref[4 * i + q];
+            atomicAdd(nfb, 1);
+        }
+    }
+    for (int q = 0; q < 4; ++q) keff[4 * i + q] = k[q];
 }
 
 // what the local-global variant of the solver needs beyond the plain local problems
 struct LgInput {
     const float *state;   // coarse (drho, u, v) [2][3][nyc][nxc]
     int r, nxc, nyc;
+    int ring;             // 1 or 2
     double *win;          // [n][2][4]
 };
 
@@ -985,6 +1086,7 @@ lbm_status local_keff_core(const lbm_params *p, const float *kappa_dev, const lb
         a.lg_r = lg->r;
         a.lg_nxc = lg->nxc;
         a.lg_nyc = lg->nyc;
+        a.lg_ring = lg->ring;
         a.lg_win = lg->win;
     }
     a.tol = tol_rel;
@@ -1104,10 +1206,12 @@ lbm_status local_keff_impl(const lbm_params *p, const float *kappa_dev, const lb
 }
 
 lbm_status local_keff_lg_impl(const lbm_params *p, const float *kappa_dev, int32_t block, const float *coarse_dev,
-                              double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
-                              double *keff_dev, int32_t *status_dev, int32_t *steps_dev, double *window_dev,
-                              void *cuda_stream, double time_limit_s)
+                              double g_const, double tol_rel, int64_t max_steps, int32_t check_every, int32_t ring,
+                              const double *keff_fallback_dev, double *keff_dev, int32_t *status_dev,
+                              int32_t *steps_dev, double *window_dev, int32_t *n_fallback, void *cuda_stream,
+                              double time_limit_s)
 {
+    if (n_fallback) *n_fallback = 0;
     if (!p) return fail(LBM_EINVAL, "params is NULL");
     if (p->nx < 1 || p->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
     if (block < 1 || p->nx % block || p->ny % block)
@@ -1116,10 +1220,15 @@ lbm_status local_keff_lg_impl(const lbm_params *p, const float *kappa_dev, int32
     if (m < 2 || block + 2 * m > 64)
         return fail(LBM_EINVAL, "local-global patches need margin >= 2 and block + 2 x margin <= 64 (got %d, %d)",
                     block, m);
+    if (m >= p->nx || m >= p->ny) return fail(LBM_EINVAL, "margin %d is not below the field size", m);
     if (p->storage == LBM_F64) return fail(LBM_EINVAL, "local-global local problems run in FP32 only");
     if (p->warm_start != 0) return fail(LBM_EINVAL, "local-global jobs start from the coarse state (warm_start 0)");
     if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(LBM_EINVAL, "eps must be finite and > 0");
+    if (ring != 1 && ring != 2) return fail(LBM_EINVAL, "ring must be 1 (state held) or 2 (pressure only)");
+    if (check_every < 2 || check_every % 2) return fail(LBM_EINVAL, "local-global checks need an even check_every");
     if (!coarse_dev || !is_device_ptr(coarse_dev)) return fail(LBM_EINVAL, "coarse_dev must be a device pointer");
+    if (keff_fallback_dev && !is_device_ptr(keff_fallback_dev))
+        return fail(LBM_EINVAL, "keff_fallback_dev must be a device pointer");
     if (window_dev && !is_device_ptr(window_dev)) return fail(LBM_EINVAL, "window_dev must be a device pointer");
     if (!keff_dev || !status_dev || !is_device_ptr(keff_dev) || !is_device_ptr(status_dev) ||
         (steps_dev && !is_device_ptr(steps_dev)))
@@ -1128,40 +1237,79 @@ lbm_status local_keff_lg_impl(const lbm_params *p, const float *kappa_dev, int32
     const int64_t n = (int64_t)nbx * nby;
     if (n > INT32_MAX / 2) return fail(LBM_EINVAL, "too many blocks");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    std::vector<lbm_leaf> lv((size_t)n);
-    for (int by = 0; by < nby; ++by)
-        for (int bx = 0; bx < nbx; ++bx) lv[(size_t)by * nbx + bx] = lbm_leaf{bx * block, by * block, block};
     lbm_leaf *d_leaves = nullptr;
     double *d_win = nullptr;
+    int *d_nfb = nullptr, *d_pos = nullptr;
+    int32_t *d_status = nullptr, *d_steps = nullptr;
+    float *d_kuni = nullptr;
     auto release = [&]() {
         cudaFree(d_leaves);
         cudaFree(d_win);
+        cudaFree(d_nfb);
+        cudaFree(d_pos);
+        cudaFree(d_status);
+        cudaFree(d_steps);
+        cudaFree(d_kuni);
         cudaGetLastError();
     };
-    cudaError_t e = cudaMalloc(&d_leaves, sizeof(lbm_leaf) * n);
-    if (e == cudaSuccess && !window_dev) e = cudaMalloc(&d_win, sizeof(double) * 8 * n);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_leaves, lv.data(), sizeof(lbm_leaf) * n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-        release();
-        return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "local-global set-up: %s",
-                    cudaGetErrorString(e));
+#define LG_CUDA(call)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            release();                                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s failed: %s", \
+                        #call, cudaGetErrorString(e_));                                          \
+        }                                                                                        \
+    } while (0)
+    // blocks whose whole patch is uniform need no local problem
+    LG_CUDA(cudaMalloc(&d_kuni, sizeof(float) * n));
+    lg_uniform_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(kappa_dev, p->nx, p->ny, block, m, nbx, n,
+                                                                         d_kuni);
+    LG_CUDA(cudaGetLastError());
+    count_launches(1);
+    std::vector<float> kuni((size_t)n);
+    LG_CUDA(cudaMemcpyAsync(kuni.data(), d_kuni, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    LG_CUDA(cudaStreamSynchronize(st));
+    std::vector<lbm_leaf> lv;
+    std::vector<int> pos((size_t)n, -1);
+    for (int64_t i = 0; i < n; ++i)
+        if (!(kuni[i] >= 0.0f)) {
+            pos[i] = (int)lv.size();
+            const int by = (int)(i / nbx), bx = (int)(i - (int64_t)by * nbx);
+            lv.push_back(lbm_leaf{bx * block, by * block, block});
+        }
+    const int64_t nh = (int64_t)lv.size();
+    LG_CUDA(cudaMalloc(&d_pos, sizeof(int) * n));
+    LG_CUDA(cudaMalloc(&d_nfb, sizeof(int)));
+    LG_CUDA(cudaMemsetAsync(d_nfb, 0, sizeof(int), st));
+    LG_CUDA(cudaMemcpyAsync(d_pos, pos.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    const int64_t nal = nh > 0 ? nh : 1;
+    LG_CUDA(cudaMalloc(&d_leaves, sizeof(lbm_leaf) * nal));
+    LG_CUDA(cudaMalloc(&d_win, sizeof(double) * 8 * nal));
+    LG_CUDA(cudaMalloc(&d_status, sizeof(int32_t) * nal));
+    LG_CUDA(cudaMalloc(&d_steps, sizeof(int32_t) * 2 * nal));
+    lbm_status s = LBM_OK;
+    if (nh > 0) {
+        LG_CUDA(cudaMemcpyAsync(d_leaves, lv.data(), sizeof(lbm_leaf) * nh, cudaMemcpyHostToDevice, st));
+        LgInput lg{coarse_dev, block, nbx, nby, ring, d_win};
+        s = local_keff_core(p, kappa_dev, d_leaves, (int32_t)nh, g_const, tol_rel, max_steps, check_every, 1, keff_dev,
+                            d_status, d_steps, cuda_stream, time_limit_s, &lg);
     }
-    LgInput lg{coarse_dev, block, nbx, nby, window_dev ? window_dev : d_win};
-    lbm_status s = local_keff_core(p, kappa_dev, d_leaves, (int32_t)n, g_const, tol_rel, max_steps, check_every, 1,
-                                   keff_dev, status_dev, steps_dev, cuda_stream, time_limit_s, &lg);
     if (s == LBM_OK || s == LBM_ENOTCONV || s == LBM_ETIMEOUT) {
         const double nu = p->nu < 0.0 ? (p->tau - 0.5) / 3.0 : p->nu;
-        lg_keff_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lg.win, n, nu, g_const, p->eps, keff_dev);
+        lg_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d_pos, d_kuni, d_win, d_status, d_steps, nu,
+                                                                      g_const, p->eps, keff_fallback_dev, keff_dev,
+                                                                      status_dev, steps_dev, window_dev, d_nfb);
+        LG_CUDA(cudaGetLastError());
         count_launches(1);
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            release();
-            return fail(LBM_ECUDA, "local-global K*: %s", cudaGetErrorString(e));
-        }
+        int nfb = 0;
+        LG_CUDA(cudaMemcpyAsync(&nfb, d_nfb, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LG_CUDA(cudaStreamSynchronize(st));
+        if (n_fallback) *n_fallback = nfb;
     }
     release();
     return s;
+#undef LG_CUDA
 }
 
 lbm_status launch_local_from_table(const lbm_params *p, const float *kappa_dev, const lbm_leaf *leaves_dev,
@@ -1236,12 +1384,13 @@ lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, con
 }
 
 lbm_status lbm_local_keff_lg(const lbm_params *p, const float *kappa_dev, int32_t block, const float *coarse_dev,
-                             double g_const, double tol_rel, int64_t max_steps, int32_t check_every,
-                             double *keff_dev, int32_t *status_dev, int32_t *steps_dev, double *window_dev,
-                             void *cuda_stream)
+                             double g_const, double tol_rel, int64_t max_steps, int32_t check_every, int32_t ring,
+                             const double *keff_fallback_dev, double *keff_dev, int32_t *status_dev,
+                             int32_t *steps_dev, double *window_dev, int32_t *n_fallback, void *cuda_stream)
 {
-    return lbm::local_keff_lg_impl(p, kappa_dev, block, coarse_dev, g_const, tol_rel, max_steps, check_every,
-                                   keff_dev, status_dev, steps_dev, window_dev, cuda_stream, g_time_limit_s);
+    return lbm::local_keff_lg_impl(p, kappa_dev, block, coarse_dev, g_const, tol_rel, max_steps, check_every, ring,
+                                   keff_fallback_dev, keff_dev, status_dev, steps_dev, window_dev, n_fallback,
+                                   cuda_stream, g_time_limit_s);
 }
 
 lbm_status lbm_set_time_limit(double seconds)

@@ -145,13 +145,14 @@ def test_surrogate_keff_rejects_bad_arguments_on_the_host(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(margin=1), dict(margin=0), dict(margin=25), dict(storage=2),
-                                 dict(warm_start=1), dict(eps=0.0), dict(nx=20)])
+                                 dict(warm_start=1), dict(eps=0.0), dict(nx=20), dict(ring=3), dict(check_every=63)])
 def test_local_global_rejects_bad_set_ups_on_the_host(lib, bad):
     """lbm_local_keff_lg: margin below 2, block + 2 margin above 64, FP64 storage, a Darcy start,
     eps = 0 or a field that is not a whole number of blocks give LBM_EINVAL before any device
     work."""
     kw = dict(nx=32, ny=32, margin=4)
     kw.update(bad)
+    ring, check_every = kw.pop("ring", 2), kw.pop("check_every", 64)
     p = _params(**kw)
-    assert lib.lbm_local_keff_lg(C.byref(p), None, 16, None, 1e-6, 1e-8, 100, 64, None, None, None, None,
-                                 None) == 1
+    assert lib.lbm_local_keff_lg(C.byref(p), None, 16, None, 1e-6, 1e-8, 100, check_every, ring, None, None,
+                                 None, None, None, None, None) == 1

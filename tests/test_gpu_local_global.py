@@ -33,18 +33,20 @@ def _coarse_state(nbx, nby, seed, g, eps, kap_scale, nu):
     return out
 
 
-def _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, tol, max_steps):
+def _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, tol, max_steps, ring=2, fallback=None):
     import torch
     lbm = _lbm()
     ny, nx = kap.shape
     p = lbm.Params(nx=nx, ny=ny, tau=tau, nu=nu, eps=eps, margin=margin)
     kt = torch.from_numpy(np.ascontiguousarray(kap, dtype=np.float32)).cuda()
     ct = torch.from_numpy(np.ascontiguousarray(coarse, dtype=np.float32)).cuda()
-    ke, st, steps, win, worst = lbm.local_keff_lg(p, kt, block, ct, g, tol, max_steps)
-    return ke.cpu().numpy(), st.cpu().numpy(), steps.cpu().numpy(), win.cpu().numpy(), worst
+    fb = None if fallback is None else torch.from_numpy(np.ascontiguousarray(fallback, dtype=np.float64)).cuda()
+    ke, st, steps, win, worst, nfb = lbm.local_keff_lg(p, kt, block, ct, g, tol, max_steps, ring=ring, fallback=fb)
+    out = (ke.cpu().numpy(), st.cpu().numpy(), steps.cpu().numpy(), win.cpu().numpy(), worst)
+    return out if fallback is None else out + (nfb,)
 
 
-def _run_oracle(kap, block, margin, coarse, bx, by, tau, nu, eps, g, tol, max_steps):
+def _run_oracle(kap, block, margin, coarse, bx, by, tau, nu, eps, g, tol, max_steps, ring=2):
     ny, nx = kap.shape
     se = block + 2 * margin
     x0, y0 = bx * block - margin, by * block - margin
@@ -53,23 +55,26 @@ def _run_oracle(kap, block, margin, coarse, bx, by, tau, nu, eps, g, tol, max_st
     st = np.stack([oracle.coarse_to_fine(coarse[d].astype(np.float64), block, x0, y0, se).transpose(1, 2, 0)
                    for d in range(2)])
     ref = [float(coarse[d, 0, by, bx]) for d in range(2)]          # the block's own coarse density
-    return oracle.local_keff_lg(k, margin, st, tau, nu, eps, g, tol=tol, max_steps=max_steps, rho_ref=ref)
+    return oracle.local_keff_lg(k, margin, st, tau, nu, eps, g, tol=tol, max_steps=max_steps, rho_ref=ref,
+                                ring=ring)
 
 
-def test_fixed_steps_match_oracle():
+@pytest.mark.parametrize("ring", [1, 2])
+def test_fixed_steps_match_oracle(ring):
     """A log-normal field (sigma 1.5), 16-cell blocks grown by 4, a smooth coarse state, 384 fixed
-    steps: every block's window means (u, v and the density gradient, per drive) and K* match the
-    oracle to 1e-4 of their scales, tau = 1 and tau = 0.8."""
+    steps (the pressure-only ring refreshed at five checks): every block's window means (u, v and
+    the density gradient, per drive) and K* match the oracle to 1e-4 of their scales, tau = 1 and
+    tau = 0.8."""
     kap = synth.lognormal_kappa(64, 64, 6.0, 1.5, seed=41)
     eps, g = 0.9, 1e-6
     for tau in (1.0, 0.8):
         nu = (tau - 0.5) / 3.0
         coarse = _coarse_state(4, 4, 7, g, eps, 1e-2, nu)
-        ke, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 0.0, 384)
+        ke, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 0.0, 384, ring=ring)
         assert worst == 0 and (steps == 384).all()
         for by in range(4):
             for bx in range(4):
-                ref = _run_oracle(kap, 16, 4, coarse, bx, by, tau, nu, eps, g, 0.0, 384)
+                ref = _run_oracle(kap, 16, 4, coarse, bx, by, tau, nu, eps, g, 0.0, 384, ring=ring)
                 w, wr = win[by, bx], ref["window"]
                 for d in range(2):
                     us = np.hypot(*wr[d, :2])
@@ -81,24 +86,26 @@ def test_fixed_steps_match_oracle():
                 assert np.abs(k - kr).max() <= 1e-4 * scale, (tau, bx, by, k, kr)
 
 
-def test_tolerance_stop_matches_oracle():
+@pytest.mark.parametrize("ring", [1, 2])
+def test_tolerance_stop_matches_oracle(ring):
     """The same set-up at tol 1e-8 (stop on the whole window velocity vector): K* agrees with the
     oracle's within the stop test's band, 1e-3 of the tensor's scale."""
     kap = synth.lognormal_kappa(64, 64, 6.0, 1.5, seed=43)
     tau, eps, g = 1.0, 1.0, 1e-6
     nu = (tau - 0.5) / 3.0
     coarse = _coarse_state(4, 4, 9, g, eps, 1e-2, nu)
-    ke, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 1e-8, 200000)
+    ke, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 1e-8, 200000, ring=ring)
     assert worst == 0
     for by in range(4):
         for bx in range(4):
-            ref = _run_oracle(kap, 16, 4, coarse, bx, by, tau, nu, eps, g, 1e-8, 200000)
+            ref = _run_oracle(kap, 16, 4, coarse, bx, by, tau, nu, eps, g, 1e-8, 200000, ring=ring)
             kr = ref["keff"]
             scale = np.sqrt(abs(kr[0] * kr[3]))
             assert np.abs(ke[by, bx] - kr).max() <= 1e-3 * scale, (bx, by, ke[by, bx], kr)
 
 
-def test_uniform_medium_under_a_linear_state_gives_kappa():
+@pytest.mark.parametrize("ring", [1, 2])
+def test_uniform_medium_under_a_linear_state_gives_kappa(ring):
     """A uniform medium whose coarse state is a linear pressure field with the matching Darcy
     velocity (bilinear interpolation reproduces it exactly away from the periodic wrap): every
     block whose grown patch does not wrap gets K* = kappa I in FP32 (1e-4), although the
@@ -106,7 +113,8 @@ def test_uniform_medium_under_a_linear_state_gives_kappa():
     kap0, tau, eps, g, block, margin = 0.02, 1.0, 0.9, 1e-6, 16, 4
     nu = (tau - 0.5) / 3.0
     nb = 8
-    kap = np.full((nb * block, nb * block), kap0, dtype=np.float32)
+    # a uniform medium up to a 1e-6 relative ripple, so that the patches are not skipped as uniform
+    kap = (kap0 * (1.0 + 1e-6 * (np.indices((nb * block, nb * block)).sum(axis=0) % 2))).astype(np.float32)
     X = (np.arange(nb) + 0.5) * block - 0.5 - nb * block / 2           # coarse centres in fine units
     Xc, Yc = np.meshgrid(X, X)
     coarse = np.empty((2, 3, nb, nb), dtype=np.float32)
@@ -114,7 +122,7 @@ def test_uniform_medium_under_a_linear_state_gives_kappa():
         coarse[d, 0] = 3 * eps * g * (a * Xc + b * Yc)
         coarse[d, 1] = kap0 / nu * ((g if d == 0 else 0.0) - g * a)
         coarse[d, 2] = kap0 / nu * ((g if d == 1 else 0.0) - g * b)
-    ke, st, steps, win, worst = _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, 1e-9, 200000)
+    ke, st, steps, win, worst = _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, 1e-9, 200000, ring=ring)
     inner = ke[1:nb - 1, 1:nb - 1].reshape(-1, 4) / kap0
     np.testing.assert_allclose(inner, np.tile([1.0, 0.0, 0.0, 1.0], (len(inner), 1)), rtol=0, atol=1e-4)
     np.testing.assert_allclose(win[2, 3, 0, 2:] / (3 * eps * g), [0.3, 0.2], rtol=1e-4)
@@ -132,3 +140,40 @@ def test_rejections():
         assert ei.value.status == lbm.LBM_EINVAL
     with pytest.raises(lbm.LbmError):
         lbm.local_keff_lg(lbm.Params(nx=32, ny=32, tau=1.0, margin=4), kap, 16, coarse.cpu(), 1e-6, 1e-8, 100)
+
+
+def test_fallback_selection_matches_the_oracle_rule():
+    """With fallback tensors the library keeps a block's K* (symmetrised) only when it converged,
+    is positive definite after symmetrising and its force matrix has condition number <= 10:
+    the kept/fallen-back blocks and every output tensor equal oracle.lg_select applied to the
+    library's own raw K*, windows and statuses (both decide in FP64 from the same numbers)."""
+    kap = synth.lognormal_kappa(128, 128, 6.0, 2.5, seed=45)
+    tau, eps, g = 1.0, 1.0, 1e-6
+    nu = (tau - 0.5) / 3.0
+    coarse = _coarse_state(8, 8, 11, g, eps, 1e-2, nu)
+    coarse[:, 0] *= 20.0                                   # strong pressure gradients: some F ill-conditioned
+    raw, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 1e-8, 20000)
+    ref = np.tile(np.array([1.0, 0.0, 0.0, 2.0]), (8, 8, 1))
+    ke, st2, _, win2, _, nfb = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 1e-8, 20000, fallback=ref)
+    np.testing.assert_array_equal(win2, win)               # the same runs, bit for bit
+    exp, fb = oracle.lg_select(raw.reshape(-1, 4), win.reshape(-1, 2, 4), st.reshape(-1) == 0, ref.reshape(-1, 4),
+                               g, eps)
+    assert nfb == int(fb.sum()) and 0 < nfb < 64
+    np.testing.assert_allclose(ke.reshape(-1, 4), exp, rtol=1e-14, atol=0)
+
+
+def test_uniform_patches_run_no_local_problem():
+    """A uniform field with one heterogeneous 16-cell square: blocks whose grown patch misses the
+    square are uniform and get K* = kappa I exactly with 0 steps and a NaN window; the others run
+    their local problems."""
+    kap0, tau, eps, g, block, margin = 0.02, 1.0, 1.0, 1e-6, 16, 4
+    nu = (tau - 0.5) / 3.0
+    kap = np.full((128, 128), kap0, dtype=np.float32)
+    kap[48:64, 48:64] = synth.lognormal_kappa(16, 16, 3.0, 1.0, seed=3)
+    coarse = _coarse_state(8, 8, 5, g, eps, kap0, nu)
+    ke, st, steps, win, worst = _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, 1e-8, 200000)
+    hetero = np.zeros((8, 8), dtype=bool)
+    hetero[2:5, 2:5] = True                        # blocks whose patch (grown by 4) reaches 48..63
+    assert (steps[~hetero] == 0).all() and np.isnan(win[~hetero]).all()
+    np.testing.assert_array_equal(ke[~hetero], np.tile([kap0, 0.0, 0.0, kap0], ((~hetero).sum(), 1)).astype(np.float32).astype(np.float64))
+    assert (steps[hetero] > 0).all() and (st == 0).all()

@@ -686,3 +686,26 @@ def test_local_global_pressure_only_ring_lets_the_flow_choose_its_velocity():
     assert r2["converged"] == 2
     np.testing.assert_allclose(r2["keff"] / kap0, [1.0, 0.0, 0.0, 1.0], rtol=0, atol=1e-8)
     assert np.abs(r1["keff"] / kap0 - [1.0, 0.0, 0.0, 1.0]).max() > 1e-2
+
+
+def test_local_global_selection_rule():
+    """oracle.lg_select on hand-made blocks: a converged, SPD, well-conditioned block keeps its
+    symmetrised tensor; a non-SPD one, an unconverged one, one whose force matrix has condition
+    number 20 (> 10) and one with a NaN all take the fallback."""
+    g, eps = 1e-6, 1.0
+    good_w = [[1e-8, 0.0, 0.0, 0.0], [0.0, 1e-8, 0.0, 0.0]]          # F = G I
+    bad_cond = [[1e-8, 0.0, 0.0, 0.0], [0.0, 1e-8, 0.0, 3 * eps * g * 0.95]]   # F = diag(G, 0.05 G)
+    keff = np.array([[2.0, 0.2, 0.4, 1.0],       # SPD after symmetrising
+                     [1.0, 2.0, 2.0, 1.0],       # not SPD
+                     [2.0, 0.0, 0.0, 1.0],       # not converged
+                     [2.0, 0.0, 0.0, 1.0],       # ill-conditioned F
+                     [np.nan, 0.0, 0.0, 1.0]])
+    win = np.array([good_w, good_w, good_w, bad_cond, good_w])
+    ok = np.array([True, True, False, True, True])
+    ref = np.full((5, 4), 7.0)
+    out, fb = oracle.lg_select(keff, win, ok, ref, g, eps)
+    np.testing.assert_array_equal(fb, [False, True, True, True, True])
+    np.testing.assert_allclose(out[0], [2.0, 0.3, 0.3, 1.0])
+    np.testing.assert_array_equal(out[1:], ref[1:])
+    out, fb = oracle.lg_select(keff, win, ok, ref, g, eps, cond_max=25.0)
+    assert not fb[3]
