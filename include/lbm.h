@@ -269,9 +269,9 @@ lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_
  * when its run met the tolerance, the symmetrised tensor is positive definite
  * and the 2-norm condition number of its F is at most 10; otherwise it takes
  * the fallback, and *n_fallback (HOST, may be NULL) counts those blocks.
- * Requirements: nx, ny multiples of block; p->margin >= 2 and
- * block + 2 margin <= 64; storage FP32 (LBM_F64 gives LBM_EINVAL);
- * warm_start = 0; eps > 0. Outputs (caller-owned DEVICE memory):
+ * Requirements: nx, ny multiples of block; p->margin >= 2, below nx and ny, and
+ * block + 2 margin <= 64 (<= 45 with storage = LBM_F64, which runs the local
+ * problems in FP64); warm_start = 0; eps > 0. Outputs (caller-owned DEVICE memory):
  *   keff_dev   double [ny/block][nx/block][4] (xx, xy, yx, yy), fine lattice units;
  *   status_dev int32  [ny/block][nx/block] as lbm_local_keff_batch;
  *   steps_dev  int32  [ny/block][nx/block][2], or NULL;

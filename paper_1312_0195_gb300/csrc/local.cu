@@ -903,12 +903,13 @@ LocalKernel local_kernel(bool f64, double tau, int warm)
 {
     return f64 ? local_kernel_t<double>(tau == 1.0, warm != 0) : local_kernel_t<float>(tau == 1.0, warm != 0);
 }
-// local-global jobs: FP32 only, one more value per cell (the density deviation)
-LocalKernel local_kernel_lg(double tau)
+// local-global jobs: one more value per cell (the density deviation)
+LocalKernel local_kernel_lg(bool f64, double tau)
 {
+    if (f64) return tau == 1.0 ? local_keff_kernel<double, true, MODE_LG> : local_keff_kernel<double, false, MODE_LG>;
     return tau == 1.0 ? local_keff_kernel<float, true, MODE_LG> : local_keff_kernel<float, false, MODE_LG>;
 }
-constexpr size_t LG_SMEM = LocalCfg<float>::SMEM + LocalCfg<float>::CMAX * sizeof(float);
+template <typename T> constexpr size_t lg_smem() { return LocalCfg<T>::SMEM + LocalCfg<T>::CMAX * sizeof(T); }
 
 // K* of each local-global leaf from its two drives' window means (the Brinkman equation of
 // Section 2 at steady state, averaged over the window): <u> = (K* / nu) <F> with
@@ -1148,9 +1149,10 @@ lbm_status local_keff_core(const lbm_params *p, const float *kappa_dev, const lb
     a.worst = d_flags;
     a.abort_flag = d_flags + 1;
 
-    const bool f64 = p->storage == LBM_F64 && !lg;
-    const LocalKernel kern = lg ? local_kernel_lg(p->tau) : local_kernel(f64, p->tau, p->warm_start);
-    const size_t smem = lg ? LG_SMEM : f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
+    const bool f64 = p->storage == LBM_F64;
+    const LocalKernel kern = lg ? local_kernel_lg(f64, p->tau) : local_kernel(f64, p->tau, p->warm_start);
+    const size_t smem = lg ? (f64 ? lg_smem<double>() : lg_smem<float>())
+                           : f64 ? LocalCfg<double>::SMEM : LocalCfg<float>::SMEM;
     LOC_CUDA2(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0;
     LOC_CUDA2(cudaGetDevice(&dev));
@@ -1217,11 +1219,11 @@ lbm_status local_keff_lg_impl(const lbm_params *p, const float *kappa_dev, int32
     if (block < 1 || p->nx % block || p->ny % block)
         return fail(LBM_EINVAL, "nx, ny must be multiples of block %d", block);
     const int m = p->margin;
-    if (m < 2 || block + 2 * m > 64)
-        return fail(LBM_EINVAL, "local-global patches need margin >= 2 and block + 2 x margin <= 64 (got %d, %d)",
-                    block, m);
+    const int smax = p->storage == LBM_F64 ? 45 : 64;   // FP64 patches hold 2048 cells per CTA
+    if (m < 2 || block + 2 * m > smax)
+        return fail(LBM_EINVAL, "local-global patches need margin >= 2 and block + 2 x margin <= %d (got %d, %d)",
+                    smax, block, m);
     if (m >= p->nx || m >= p->ny) return fail(LBM_EINVAL, "margin %d is not below the field size", m);
-    if (p->storage == LBM_F64) return fail(LBM_EINVAL, "local-global local problems run in FP32 only");
     if (p->warm_start != 0) return fail(LBM_EINVAL, "local-global jobs start from the coarse state (warm_start 0)");
     if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(LBM_EINVAL, "eps must be finite and > 0");
     if (ring != 1 && ring != 2) return fail(LBM_EINVAL, "ring must be 1 (state held) or 2 (pressure only)");

@@ -33,11 +33,11 @@ def _coarse_state(nbx, nby, seed, g, eps, kap_scale, nu):
     return out
 
 
-def _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, tol, max_steps, ring=2, fallback=None):
+def _run_gpu(kap, block, margin, coarse, tau, nu, eps, g, tol, max_steps, ring=2, fallback=None, storage=0):
     import torch
     lbm = _lbm()
     ny, nx = kap.shape
-    p = lbm.Params(nx=nx, ny=ny, tau=tau, nu=nu, eps=eps, margin=margin)
+    p = lbm.Params(nx=nx, ny=ny, tau=tau, nu=nu, eps=eps, margin=margin, storage=storage)
     kt = torch.from_numpy(np.ascontiguousarray(kap, dtype=np.float32)).cuda()
     ct = torch.from_numpy(np.ascontiguousarray(coarse, dtype=np.float32)).cuda()
     fb = None if fallback is None else torch.from_numpy(np.ascontiguousarray(fallback, dtype=np.float64)).cuda()
@@ -133,7 +133,7 @@ def test_rejections():
     lbm = _lbm()
     kap = torch.full((32, 32), 0.01, device="cuda")
     coarse = torch.zeros((2, 3, 2, 2), device="cuda")
-    for kw in (dict(margin=1), dict(margin=25), dict(margin=4, storage=2)):
+    for kw in (dict(margin=1), dict(margin=25), dict(margin=15, storage=2)):
         p = lbm.Params(nx=32, ny=32, tau=1.0, **kw)
         with pytest.raises(lbm.LbmError) as ei:
             lbm.local_keff_lg(p, kap, 16, coarse, 1e-6, 1e-8, 100)
@@ -177,3 +177,27 @@ def test_uniform_patches_run_no_local_problem():
     assert (steps[~hetero] == 0).all() and np.isnan(win[~hetero]).all()
     np.testing.assert_array_equal(ke[~hetero], np.tile([kap0, 0.0, 0.0, kap0], ((~hetero).sum(), 1)).astype(np.float32).astype(np.float64))
     assert (steps[hetero] > 0).all() and (st == 0).all()
+
+
+@pytest.mark.parametrize("ring", [1, 2])
+def test_fp64_matches_oracle_to_roundoff(ring):
+    """storage = LBM_F64 runs the local-global problems in FP64 (patches up to 45 cells): at 384
+    fixed steps every window mean and K* matches the FP64 oracle to 1e-8 of its scale (the oracle
+    stores full distributions of ~0.1 for velocities of ~4e-8: its own rounding is ~1e-9 of them)."""
+    kap = synth.lognormal_kappa(64, 64, 6.0, 1.5, seed=47)
+    tau, eps, g = 0.8, 0.9, 1e-6
+    nu = (tau - 0.5) / 3.0
+    coarse = _coarse_state(4, 4, 13, g, eps, 1e-2, nu)
+    ke, st, steps, win, worst = _run_gpu(kap, 16, 4, coarse, tau, nu, eps, g, 0.0, 384, ring=ring, storage=2)
+    assert worst == 0 and (steps == 384).all()
+    for by in range(4):
+        for bx in range(4):
+            ref = _run_oracle(kap, 16, 4, coarse, bx, by, tau, nu, eps, g, 0.0, 384, ring=ring)
+            w, wr = win[by, bx], ref["window"]
+            for d in range(2):
+                us = np.hypot(*wr[d, :2])
+                gs = np.hypot(*wr[d, 2:]) + 3 * eps * g
+                assert np.abs(w[d, :2] - wr[d, :2]).max() <= 1e-8 * us, (bx, by, d, w[d], wr[d])
+                assert np.abs(w[d, 2:] - wr[d, 2:]).max() <= 1e-8 * gs, (bx, by, d, w[d], wr[d])
+            kr = ref["keff"]
+            assert np.abs(ke[by, bx] - kr).max() <= 1e-8 * np.sqrt(abs(kr[0] * kr[3]))
