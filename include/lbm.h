@@ -246,7 +246,12 @@ lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_
  * density scale). That state is interpolated bilinearly (periodic) from the
  * coarse cell centres to every cell of the patch, the density deviation taken
  * relative to the block's own coarse cell (rho0 = 1 at the block: the global
- * pressure level is arbitrary); all cells start from its equilibrium. Each ring
+ * pressure level is arbitrary); all cells start from its equilibrium, or, with
+ * p->warm_start = 1 and block + 2 margin a multiple of 8, the inner cells start
+ * from the Darcy flow through the patch with the ring's pressures held (finite
+ * volumes as for warm_start on periodic patches, the ring's rho - 1 as
+ * 3 eps G p on the boundary; conjugate gradients to a relative residual of
+ * 1e-7 in shared memory when the job starts). Each ring
  * cell emits, every step, what a cell at its density emits after a collision at
  * tau = 1: the equilibrium (Eq. 2) at momentum rho u + rho f_m / 2 (f_m of Eq. 5
  * at the ring cell's own kappa; zero where kappa = 0). ring = 1: u is the coarse
@@ -271,7 +276,7 @@ lbm_status lbm_local_keff_batch_noalloc(const lbm_params *p, const float *kappa_
  * the fallback, and *n_fallback (HOST, may be NULL) counts those blocks.
  * Requirements: nx, ny multiples of block; p->margin >= 2, below nx and ny, and
  * block + 2 margin <= 64 (<= 45 with storage = LBM_F64, which runs the local
- * problems in FP64); warm_start = 0; eps > 0. Outputs (caller-owned DEVICE memory):
+ * problems in FP64); warm_start 0 or 1; eps > 0. Outputs (caller-owned DEVICE memory):
  *   keff_dev   double [ny/block][nx/block][4] (xx, xy, yx, yy), fine lattice units;
  *   status_dev int32  [ny/block][nx/block] as lbm_local_keff_batch;
  *   steps_dev  int32  [ny/block][nx/block][2], or NULL;

@@ -406,6 +406,59 @@ def local_keff_lg(kappa_ext, margin, state, tau, nu, eps, g_const, tol=1e-8, max
     return dict(keff=keff, window=win.reshape(2, 4), steps=[st[0], st[1]], converged=int(nconv))
 
 
+def lg_darcy_state(kappa_ext, state, nu, eps, g_const):
+    """Start state of a local-global patch from Darcy flow (warm_start = 1 with local-global
+    problems): per drive, the finite-volume Darcy flow through the patch (harmonic face
+    permeabilities, no wrap) with the ring cells' pressures held at the given state's
+    (p = drho / (3 eps G) in unit-drive units, as in darcy_start) and unit drive along the axis;
+    interior cells get drho = 3 eps G p and j = rho u with u = (G / nu) times the mean of their two
+    face fluxes along each axis; ring cells keep the given state. state, result: [2][se][se][3]."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    k = np.asarray(kappa_ext, dtype=np.float64)
+    se = k.shape[0]
+    out = np.array(state, dtype=np.float64, order="C")
+    ring = np.zeros((se, se), dtype=bool)
+    ring[0, :] = ring[-1, :] = ring[:, 0] = ring[:, -1] = True
+    inner = np.flatnonzero(~ring.ravel())
+    pos = -np.ones(se * se, dtype=np.int64)
+    pos[inner] = np.arange(inner.size)
+    hx = 2.0 * k[:, :-1] * k[:, 1:] / (k[:, :-1] + k[:, 1:])      # face between (y, x) and (y, x + 1)
+    hy = 2.0 * k[:-1, :] * k[1:, :] / (k[:-1, :] + k[1:, :])      # face between (y, x) and (y + 1, x)
+    for d in range(2):
+        pb = (out[d, ..., 0] / (3.0 * eps * g_const)).ravel()
+        rows, cols, vals = [], [], []
+        b = np.zeros(inner.size)
+        faces = [(y * se + x, y * se + x + 1, hx[y, x], 0) for y in range(se) for x in range(se - 1)] + \
+                [(y * se + x, (y + 1) * se + x, hy[y, x], 1) for y in range(se - 1) for x in range(se)]
+        for i, j, kf, axis in faces:
+            drive = 1.0 if axis == d else 0.0        # e_d . (x_j - x_i)
+            for a, c, sgn in ((i, j, 1.0), (j, i, -1.0)):
+                if pos[a] < 0:
+                    continue
+                # flux out of a: kf (p_a - p_c + e_d . (x_c - x_a)); its sum over faces is zero
+                rows.append(pos[a]); cols.append(pos[a]); vals.append(kf)
+                if pos[c] >= 0:
+                    rows.append(pos[a]); cols.append(pos[c]); vals.append(-kf)
+                else:
+                    b[pos[a]] += kf * pb[c]
+                b[pos[a]] -= kf * drive * sgn
+        A = sp.csr_matrix((vals, (rows, cols)), shape=(inner.size, inner.size))
+        ph = pb.copy()
+        ph[inner] = sla.spsolve(A.tocsc(), b)
+        P = ph.reshape(se, se)
+        qx = hx * (P[:, :-1] - P[:, 1:] + (1.0 if d == 0 else 0.0))   # flux +x through each x-face
+        qy = hy * (P[:-1, :] - P[1:, :] + (1.0 if d == 1 else 0.0))
+        for y in range(1, se - 1):
+            for x in range(1, se - 1):
+                drho = 3.0 * eps * g_const * P[y, x]
+                rho = 1.0 + drho
+                ux = g_const / nu * 0.5 * (qx[y, x - 1] + qx[y, x])
+                uy = g_const / nu * 0.5 * (qy[y - 1, x] + qy[y, x])
+                out[d, y, x] = (drho, ux, uy)
+    return out
+
+
 def lg_select(keff_lg, window, ok, keff_ref, g_const, eps, cond_max=10.0):
     """Which local-global K* to keep (the library's rule when it is given fallback tensors): a
     block keeps its local-global K*, symmetrised (K*_xy = K*_yx = their mean), when its run met

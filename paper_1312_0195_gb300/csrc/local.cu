@@ -310,9 +310,12 @@ __device__ __forceinline__ WarmCell warm_cell(int c, int s, int s2)
     return w;
 }
 
-template <typename T>
-__device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 *hot, const Slot *slots, int s,
-                                              int nslots)
+// DIR (local-global patches): the patch's outermost ring is not periodic closure but Dirichlet
+// data, its pressure held at the ring state's drho / (3 eps G) (D holds the ring's drho); only the
+// inner cells are unknowns, and only they get the Darcy start.
+template <typename T, bool DIR>
+__device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, const T *D, int4 *hot, const Slot *slots,
+                                              int s, int nslots)
 {
     constexpr int CMAX = LocalCfg<T>::CMAX, CPT = LocalCfg<T>::CPT, NW = LOCAL_THREADS / 32;
     __shared__ double w_rz[MAXSLOTS], w_stop[MAXSLOTS];
@@ -335,6 +338,16 @@ __device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 
         geo[i] = w.j << 12 | w.ly << 6 | w.lx;
         if (c < ncell && (hot[w.j].z & 5) == 5) mine |= 1u << i;
     }
+    // DIR: bit i of `ringm` marks a ring cell of a fresh slot (fixed pressure, not an unknown)
+    unsigned ringm = 0;
+    if constexpr (DIR) {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int lx = geo[i] & 63, ly = (geo[i] >> 6) & 63;
+            if ((mine >> i & 1) && (lx == 0 || ly == 0 || lx == s - 1 || ly == s - 1)) ringm |= 1u << i;
+        }
+    }
+    const unsigned unk = mine & ~ringm;                      // the unknowns of this thread
     // the neighbours of cell i within its slot (periodic closure)
     auto cell = [&](int i) {
         const int c = tid + i * LOCAL_THREADS, lx = geo[i] & 63, ly = (geo[i] >> 6) & 63;
@@ -397,14 +410,34 @@ __device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 
         KY[c] = (T)harmonic_face(k, kappa_at(w.j, w.lx, w.ly + 1 == s ? 0 : w.ly + 1));
     }
     __syncthreads();
-    // start: p = 0, r = b, d = b / diag
+    if constexpr (DIR) {
+        // the ring's pressures, and zero directions there
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            if (!(ringm >> i & 1)) continue;
+            const int c = tid + i * LOCAL_THREADS;
+            P[c] = D[c] / (T)a.warm_rho;
+            DV[c] = T(0);
+            R[c] = T(0);
+            IDG[c] = T(0);
+        }
+        __syncthreads();
+    }
+    // start: p = 0 on the unknowns, r = b - A p, d = r / diag
 #pragma unroll
     for (int i = 0; i < CPT; ++i) {
         const int c = tid + i * LOCAL_THREADS;
         T x = T(0), y = T(0);
-        if (mine >> i & 1) {
+        if (unk >> i & 1) {
             const WarmCell w = cell(i);
-            const T b = (hot[w.j].z & 2) ? KY[w.d] - KY[c] : KX[w.l] - KX[c];
+            T b = (hot[w.j].z & 2) ? KY[w.d] - KY[c] : KX[w.l] - KX[c];
+            if constexpr (DIR) {
+                // minus A p for p = 0 here and the ring's pressures on its ring neighbours
+                auto pr = [&](int n, int nl) { return nl ? P[n] : T(0); };
+                const int lx = w.lx, ly = w.ly;
+                b += KX[c] * pr(w.r, lx + 1 == s - 1) + KX[w.l] * pr(w.l, lx - 1 == 0) +
+                     KY[c] * pr(w.u, ly + 1 == s - 1) + KY[w.d] * pr(w.d, ly - 1 == 0);
+            }
             const T dg = KX[c] + KX[w.l] + KY[c] + KY[w.d];
             const T idg = dg > T(0) ? T(1) / dg : T(0);
             const T z = b * idg;
@@ -420,14 +453,16 @@ __device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 
     slot_fold([&](int j, double rr, double rz) {
         w_on[j] = (hot[j].z & 5) == 5 && rr > 0.0;
         w_rz[j] = rz;
-        w_stop[j] = 1e-10 * rr;                              // (1e-5 relative residual)^2
+        // (1e-5 relative residual)^2; with a Dirichlet ring the initial residual carries the ring's
+        // whole pressure level, so the flow-carrying differences need 1e-7
+        w_stop[j] = (DIR ? 1e-14 : 1e-10) * rr;
     });
     int any = __syncthreads_or(tid < nslots && w_on[tid]);
     for (int it = 0; any && it < WARM_MAXIT; ++it) {
-        unsigned act = 0;                                    // cells of slots still iterating
+        unsigned act = 0;                                    // unknowns of slots still iterating
 #pragma unroll
         for (int i = 0; i < CPT; ++i)
-            if ((mine >> i & 1) && w_on[geo[i] >> 12]) act |= 1u << i;
+            if ((unk >> i & 1) && w_on[geo[i] >> 12]) act |= 1u << i;
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
             const int c = tid + i * LOCAL_THREADS;
@@ -479,9 +514,10 @@ __device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 
     }
     // the start state: rho and j from the pressure and the face fluxes, staged in AD (drho) and
     // DV / R (j) so that every read of the pressure comes before the distributions are written
+    // (DIR: the ring's cells keep their own start; they emit their fixed state from the first step)
 #pragma unroll
     for (int i = 0; i < CPT; ++i) {
-        if (!(mine >> i & 1)) continue;
+        if (!(unk >> i & 1)) continue;
         const int c = tid + i * LOCAL_THREADS;
         const WarmCell w = cell(i);
         const bool ydrive = (hot[w.j].z & 2) != 0;
@@ -497,7 +533,7 @@ __device__ __forceinline__ void warm_start_fresh(const LocalArgs &a, T *F, int4 
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < CPT; ++i) {
-        if (!(mine >> i & 1)) continue;
+        if (!(unk >> i & 1)) continue;
         const int c = tid + i * LOCAL_THREADS;
         const T drho = AD[c], jx = DV[c], jy = R[c];
         const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
@@ -707,9 +743,16 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_keff_kernel(LocalArgs 
                     }
                 }
                 __syncthreads();
+                if constexpr (LG) {
+                    // the Darcy start of the inner cells, the ring's pressures held (warm_start = 1)
+                    if (a.warm && s % 8 == 0) {
+                        warm_start_fresh<T, true>(a, F, D, hot, slots, s, nslots);
+                        __syncthreads();
+                    }
+                }
                 if constexpr (WARM) {
                     if (s >= WARM_MIN && s % 8 == 0) {
-                        warm_start_fresh<T>(a, F, hot, slots, s, nslots);
+                        warm_start_fresh<T, false>(a, F, D, hot, slots, s, nslots);
                         __syncthreads();
                     }
                 }
@@ -1224,7 +1267,7 @@ lbm_status local_keff_lg_impl(const lbm_params *p, const float *kappa_dev, int32
         return fail(LBM_EINVAL, "local-global patches need margin >= 2 and block + 2 x margin <= %d (got %d, %d)",
                     smax, block, m);
     if (m >= p->nx || m >= p->ny) return fail(LBM_EINVAL, "margin %d is not below the field size", m);
-    if (p->warm_start != 0) return fail(LBM_EINVAL, "local-global jobs start from the coarse state (warm_start 0)");
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(LBM_EINVAL, "warm_start must be 0 or 1");
     if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(LBM_EINVAL, "eps must be finite and > 0");
     if (ring != 1 && ring != 2) return fail(LBM_EINVAL, "ring must be 1 (state held) or 2 (pressure only)");
     if (check_every < 2 || check_every % 2) return fail(LBM_EINVAL, "local-global checks need an even check_every");

@@ -145,9 +145,9 @@ def test_surrogate_keff_rejects_bad_arguments_on_the_host(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(margin=1), dict(margin=0), dict(margin=25), dict(storage=2, margin=15),
-                                 dict(warm_start=1), dict(eps=0.0), dict(nx=20), dict(ring=3), dict(check_every=63)])
+                                 dict(warm_start=2), dict(eps=0.0), dict(nx=20), dict(ring=3), dict(check_every=63)])
 def test_local_global_rejects_bad_set_ups_on_the_host(lib, bad):
-    """lbm_local_keff_lg: margin below 2, block + 2 margin above 64 (45 in FP64), a Darcy start,
+    """lbm_local_keff_lg: margin below 2, block + 2 margin above 64 (45 in FP64), warm_start 2,
     eps = 0 or a field that is not a whole number of blocks give LBM_EINVAL before any device
     work."""
     kw = dict(nx=32, ny=32, margin=4)

@@ -709,3 +709,28 @@ def test_local_global_selection_rule():
     np.testing.assert_array_equal(out[1:], ref[1:])
     out, fb = oracle.lg_select(keff, win, ok, ref, g, eps, cond_max=25.0)
     assert not fb[3]
+
+
+def test_local_global_darcy_start_reproduces_closed_forms():
+    """oracle.lg_darcy_state (the Darcy start of a ring-closed patch): for a uniform medium whose
+    ring holds a linear pressure the interior gets that linear state exactly; for layers across x
+    whose ring holds the piecewise-linear pressure of a uniform flux q0 along x (each x-face:
+    k_f (p_i - p_(i+1) + 1) = q0, no flux along y), the interior gets that pressure and the uniform
+    velocity (G / nu) q0."""
+    kap0, nu, eps, g, se = 0.02, 0.1, 0.9, 1e-6, 18
+    st = _lg_state_uniform(kap0, nu, eps, g, se, [(0.3, 0.2), (-0.1, 0.4)])
+    d = oracle.lg_darcy_state(np.full((se, se), kap0), st, nu, eps, g)
+    np.testing.assert_allclose(d, st, rtol=0, atol=1e-12 * np.abs(st).max())
+    kx = np.where((np.arange(se) // 3) % 2 == 0, 0.01, 0.002)
+    k = np.tile(kx, (se, 1))
+    kf = 2 * kx[:-1] * kx[1:] / (kx[:-1] + kx[1:])
+    q0 = 0.4
+    p = np.concatenate([[0.0], np.cumsum(1.0 - q0 / kf)])          # p_(i+1) = p_i + 1 - q0 / k_f
+    state = np.zeros((2, se, se, 3))
+    state[0, ..., 0] = 3 * eps * g * np.tile(p, (se, 1))
+    state[1] = st[1]                                                # drive y: any ring data
+    d = oracle.lg_darcy_state(k, state, nu, eps, g)
+    np.testing.assert_allclose(d[0, 1:-1, 1:-1, 0], state[0, 1:-1, 1:-1, 0], rtol=1e-10, atol=1e-18)
+    np.testing.assert_allclose(d[0, 1:-1, 1:-1, 1], g / nu * q0, rtol=1e-10)
+    np.testing.assert_allclose(d[0, 1:-1, 1:-1, 2], 0.0, atol=1e-10 * g / nu * q0)
+    np.testing.assert_array_equal(d[:, 0], state[:, 0])             # the ring keeps its state
