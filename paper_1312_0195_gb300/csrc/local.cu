@@ -26,6 +26,10 @@
 //    vector ubar). Drive 1 writes K*_xx, K*_yx and drive 2 K*_xy, K*_yy (Eq. 17).
 //  * A wall-clock limit (globaltimer) bounds the launch: past it every CTA
 //    abandons its jobs with LBM_ETIMEOUT and returns.
+//  * Variants of the same kernel (template MODE): jobs from rest (the paper's
+//    local problems), jobs from the patch's Darcy state (warm_start), and
+//    local-global jobs, whose patch is closed by a ring of cells held at a
+//    coarse solution instead of periodicity (lbm_local_keff_lg).
 #include "lbm_internal.h"
 
 #include <algorithm>
