@@ -513,7 +513,7 @@ def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=
                       spread_max=0.03):
     """The learned K* surrogate against the batched local LBM on held-out leaves.
 
-    Training set (config 4's size): ~200k leaves cut from seeded log-normal 512^2 fields
+    Training set: ~200k leaves cut from seeded log-normal 512^2 fields
     (sigma ~ U[0.5, 3], ell ~ U[2, 16]), stratified by size (equal counts of 8, 16, 32 and 64
     cells: the 64-cell leaves carry most of the LBM cost); labels by local LBM (FP32, tau = 1,
     G = 1e-6, tol 1e-8, persistent launch); non-converged labels are left out. An ensemble of 4
@@ -862,7 +862,7 @@ def main(argv=None):
                     help="skip the storage variants, the local-problem and the surrogate measurements")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
     ap.add_argument("--surrogate-only", action="store_true",
-                    help="run only the surrogate measurement (config 4) and print its JSON")
+                    help="run only the surrogate measurement (200k training leaves) and print its JSON")
     ap.add_argument("--surrogate-fields", type=int, default=800, help="training fields of the surrogate block")
     ap.add_argument("--surrogate-epochs", type=int, default=40, help="training epochs of the surrogate block")
     ap.add_argument("--profile-steps", type=int, default=0,

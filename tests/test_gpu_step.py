@@ -55,7 +55,7 @@ def rel_l2(a, b, ref=None):
     return np.linalg.norm(a - b) / np.linalg.norm(ref)
 
 
-# ------------------------------------------------------------------ config 1
+# ------------------------------------------------------------------ the 128x64 walled channel
 
 def test_channel_128x64_steady_parity():
     """128x64, walls in y, tau = 1, eps = 1, nu = nu_eff, G = (1e-6, 0), log-normal K (ell = 8, sigma = 1).
