@@ -890,8 +890,9 @@ def main(argv=None):
                     help="margins of the local-global upscaling runs of --pipeline (empty: none)")
     ap.add_argument("--pipeline-lg-iters", type=int, default=1, help="local-global passes of --pipeline")
     ap.add_argument("--pipeline-lg-f64", action="store_true", help="run the local-global problems in FP64")
-    ap.add_argument("--pipeline-lg-warm", action="store_true",
-                    help="start the local-global problems from the Darcy flow with the ring's pressures held")
+    ap.add_argument("--pipeline-lg-start", default="darcy", choices=["darcy", "coarse"],
+                    help="start of the local-global problems: the Darcy flow with the ring's pressures held, "
+                         "or the coarse state's equilibrium")
     ap.add_argument("--pipeline-lg-steps", type=int, default=200000,
                     help="step limit of the local-global local problems (unconverged blocks fall back)")
     args = ap.parse_args(argv)
@@ -1008,7 +1009,7 @@ def run_pipeline(args, local):
                         cs[d, 0] -= 1.0
                 _, t_cs = timed(states)
                 pm = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, margin=m, storage=2 if args.pipeline_lg_f64 else 0,
-                                warm_start=1 if args.pipeline_lg_warm else 0)
+                                warm_start=1 if args.pipeline_lg_start == "darcy" else 0)
                 (kl, st_l, _, _, _, nfb_l), t_l = timed(lambda: lbm.local_keff_lg(
                     pm, kt, r, cs, 1e-6, 1e-8, args.pipeline_lg_steps, ring=2, fallback=keff["lbm_m0"]))
                 name = f"local_global_m{m}" + (f"_it{it + 1}" if it else "")
@@ -1017,7 +1018,7 @@ def run_pipeline(args, local):
                                         "not_converged": int((st_l != 0).sum()), "fallback_blocks": nfb_l,
                                         "max_steps": args.pipeline_lg_steps,
                                         "storage": "f64" if args.pipeline_lg_f64 else "f32",
-                                        "start": "darcy" if args.pipeline_lg_warm else "coarse state"}
+                                        "start": args.pipeline_lg_start}
                 kcur = kl
                 del cs
     if 0 in margins:
