@@ -418,6 +418,24 @@ lbm_status lbm_upscale(const lbm_params *p, const float *kappa_dev, int32_t bloc
                        double spread_max, double g_const, double tol_rel, int64_t max_steps,
                        double *keff_coarse_dev, int32_t *n_fallback, void *cuda_stream);
 
+/* Local-global upscaling in one call (the treatment of lbm_local_keff_lg):
+ * K* of every block x block block by the periodic local problems of Section 3
+ * (lbm_upscale with margin 0, from rest), then `passes` local-global passes:
+ * each runs the coarse model with the current K* (lbm_coarse_run, from rest,
+ * at most coarse_max_steps steps, stopping test coarse_tol; periodic, FP32)
+ * driven by G = g_const along x and along y, and solves lbm_local_keff_lg on the two
+ * steady states (p->margin >= 2, the pressure-only ring, p->warm_start for its
+ * Darcy start, check_every 64) with the periodic K* as the fallback tensors.
+ * p: as for lbm_local_keff_lg (nx, ny the fine field; gx, gy ignored).
+ * keff_coarse_dev: caller-owned DEVICE double [ny/block][nx/block][4], the
+ * final K* (the periodic K* when passes = 0). *n_fallback (HOST, may be NULL):
+ * blocks of the last pass that took the periodic K*. Returns the worst status
+ * of the local problems (LBM_OK, LBM_ENOTCONV or LBM_ETIMEOUT), or the error of
+ * a failing step. Synchronises the stream. */
+lbm_status lbm_upscale_lg(const lbm_params *p, const float *kappa_dev, int32_t block, int32_t passes,
+                          double g_const, double tol_rel, int64_t max_steps, int64_t coarse_max_steps,
+                          double coarse_tol, double *keff_coarse_dev, int32_t *n_fallback, void *cuda_stream);
+
 /* Coarse lattice parameters for a fine set-up coarsened by `block` (= r):
  * nx/r x ny/r cells, tau_c = 1/2 + (tau_f - 1/2)/r, nu_c = nu_f/r, G_c = r G_f,
  * same eps, bc and storage (the paper keeps rho0, nu_eff, eps, nu and G and

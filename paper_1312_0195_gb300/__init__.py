@@ -218,6 +218,20 @@ def lbm_upscale(params: Params, kappa, block: int, keff_coarse, g_const: float =
     return st, int(nfb.value)
 
 
+def lbm_upscale_lg(params: Params, kappa, block: int, keff_coarse, passes: int = 1, g_const: float = 1e-6,
+                   tol_rel: float = 1e-8, max_steps: int = 200000, coarse_max_steps: int = 400000,
+                   coarse_tol: float = 1e-7, stream=None):
+    """Local-global K* per block x block block in one call (params.margin >= 2; warm_start = 1 for
+    the Darcy start). Returns (status, n_fallback of the last pass)."""
+    p = params.c()
+    nfb = C.c_int32(0)
+    st = _check(_abi.lib().lbm_upscale_lg(C.byref(p), _ptr(kappa), int(block), int(passes), float(g_const),
+                                          float(tol_rel), int(max_steps), int(coarse_max_steps), float(coarse_tol),
+                                          _ptr(keff_coarse), C.byref(nfb), _stream(stream)),
+                allow=(LBM_OK, LBM_ENOTCONV, LBM_ETIMEOUT))
+    return st, int(nfb.value)
+
+
 def lbm_coarse_params(params: Params, block: int) -> Params:
     out = _abi.lbm_params()
     p = params.c()

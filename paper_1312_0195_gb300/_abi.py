@@ -70,6 +70,7 @@ SIGNATURES = {
     "lbm_local_keff_lg": (C.c_int, [_PP, _P, _I32, _P, _D, _D, _I64, _I32, _I32, _P, _P, _P, _P, _P,
                                     C.POINTER(_I32), _P]),
     "lbm_upscale": (C.c_int, [_PP, _P, _I32, _P, _D, _D, _D, _I64, _P, C.POINTER(_I32), _P]),
+    "lbm_upscale_lg": (C.c_int, [_PP, _P, _I32, _I32, _D, _D, _I64, _I64, _D, _P, C.POINTER(_I32), _P]),
     "lbm_coarse_params": (C.c_int, [_PP, _I32, _PP]),
     "lbm3d_grid_create": (C.c_int, [C.POINTER(lbm3d_params), _P, _P, C.POINTER(_P)]),
     "lbm3d_grid_destroy": (C.c_int, [_P]),

@@ -55,6 +55,13 @@ __global__ void __launch_bounds__(256) scale_force_kernel(const float *in, float
         out[i] = in[i] * r;
 }
 
+// rho -> rho - 1 in place (the coarse run's density to the deviation the local-global ring takes)
+__global__ void __launch_bounds__(256) minus_one_kernel(float *a, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] -= 1.0f;
+}
+
 int blocks_for(int64_t n)
 {
     int64_t b = (n + 255) / 256;
@@ -187,6 +194,92 @@ lbm_status lbm_upscale(const lbm_params *p, const float *kappa_dev, int32_t bloc
     cudaFree(d_status);
     if (n_fallback) *n_fallback = (int32_t)nl;
     return s;
+}
+
+lbm_status lbm_upscale_lg(const lbm_params *p, const float *kappa_dev, int32_t block, int32_t passes,
+                          double g_const, double tol_rel, int64_t max_steps, int64_t coarse_max_steps,
+                          double coarse_tol, double *keff_coarse_dev, int32_t *n_fallback, void *cuda_stream)
+{
+    if (n_fallback) *n_fallback = 0;
+    lbm_status s = validate_params(p);
+    if (s != LBM_OK) return s;
+    if (passes < 0) return fail(LBM_EINVAL, "passes must be >= 0");
+    if (block < 1 || block > 64 || p->nx % block || p->ny % block)
+        return fail(LBM_EINVAL, "block must be in [1, 64] and divide nx, ny");
+    if (coarse_max_steps < 1 || !std::isfinite(coarse_tol) || coarse_tol < 0.0)
+        return fail(LBM_EINVAL, "coarse_max_steps must be >= 1 and coarse_tol finite and >= 0");
+    if (!keff_coarse_dev || !is_device_ptr(keff_coarse_dev))
+        return fail(LBM_EINVAL, "keff_coarse_dev must be a device pointer");
+    const int64_t nb = (int64_t)(p->nx / block) * (p->ny / block);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double *kref = nullptr;
+    float *cs = nullptr;
+    int32_t *status = nullptr;
+    auto release = [&]() {
+        cudaFree(kref);
+        cudaFree(cs);
+        cudaFree(status);
+        cudaGetLastError();
+    };
+    cudaError_t e = cudaMalloc(&kref, sizeof(double) * 4 * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&cs, sizeof(float) * 6 * nb);
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int32_t) * nb);
+    if (e != cudaSuccess) {
+        release();
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "upscale set-up: %s",
+                    cudaGetErrorString(e));
+    }
+    // the paper's local problems: periodic, from rest
+    lbm_params p0 = *p;
+    p0.margin = 0;
+    p0.warm_start = 0;
+    s = lbm_upscale(&p0, kappa_dev, block, nullptr, 0.0, g_const, tol_rel, max_steps, kref, nullptr, cuda_stream);
+    if (s != LBM_OK && s != LBM_ENOTCONV) {
+        release();
+        return s;
+    }
+    lbm_status worst = s;
+    const double *kcur = kref;
+    for (int pass = 0; pass < passes; ++pass) {
+        // the global coarse solutions driven along x and along y, to steady state
+        for (int d = 0; d < 2; ++d) {
+            lbm_params pd = p0;
+            pd.gx = d == 0 ? g_const : 0.0;
+            pd.gy = d == 1 ? g_const : 0.0;
+            pd.bc = LBM_BC_PERIODIC;
+            pd.storage = LBM_F32;
+            pd.scale = 0.0;
+            float *c = cs + (int64_t)3 * d * nb;
+            s = lbm_coarse_run(&pd, block, kcur, nullptr, coarse_max_steps, coarse_tol, 64, c, c + nb, c + 2 * nb,
+                               nullptr, cuda_stream);
+            if (s != LBM_OK && s != LBM_ENOTCONV) {
+                release();
+                return s;
+            }
+            minus_one_kernel<<<blocks_for(nb), 256, 0, st>>>(c, nb);
+            count_launches(1);
+        }
+        int32_t nfb = 0;
+        s = lbm_local_keff_lg(p, kappa_dev, block, cs, g_const, tol_rel, max_steps, 64, 2, kref, keff_coarse_dev,
+                              status, nullptr, nullptr, &nfb, cuda_stream);
+        if (s != LBM_OK && s != LBM_ENOTCONV && s != LBM_ETIMEOUT) {
+            release();
+            return s;
+        }
+        if (s > worst) worst = s;
+        if (n_fallback) *n_fallback = nfb;
+        kcur = keff_coarse_dev;
+    }
+    if (passes == 0) {
+        e = cudaMemcpyAsync(keff_coarse_dev, kref, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            release();
+            return fail(LBM_ECUDA, "upscale copy: %s", cudaGetErrorString(e));
+        }
+    }
+    release();
+    return worst;
 }
 
 }  // extern "C"

@@ -246,3 +246,31 @@ def test_darcy_start_matches_oracle():
           f"max {du.max():.1e}; gradient median {np.median(dg):.1e} max {dg.max():.1e}")
     assert np.median(du) <= 1e-4 and np.percentile(du, 90) <= 2e-3
     assert np.median(dg) <= 1e-4 and np.percentile(dg, 90) <= 2e-3
+
+
+def test_upscale_lg_is_the_sequence_of_its_calls():
+    """lbm_upscale_lg equals, bit for bit, the calls it stands for: lbm_upscale (periodic, margin 0),
+    two steady coarse runs (G along x, then y) with that K*, and lbm_local_keff_lg from their
+    (rho - 1, u, v) with the periodic K* as fallback; passes = 0 returns the periodic K*."""
+    import torch
+    lbm = _lbm()
+    n, r = 256, 16
+    nb = n // r
+    kt = torch.from_numpy(synth.channel_kappa(n, n, seed=5)).cuda()
+    p = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, margin=4, warm_start=1)
+    kw = dict(g_const=1e-6, tol_rel=1e-8, max_steps=30000, coarse_max_steps=20000, coarse_tol=1e-7)
+    k1 = torch.empty((nb, nb, 4), dtype=torch.float64, device="cuda")
+    st1, nfb1 = lbm.lbm_upscale_lg(p, kt, r, k1, passes=1, **kw)
+    kp = torch.empty_like(k1)
+    lbm.lbm_upscale(lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0), kt, r, kp, 1e-6, 1e-8, 30000)
+    k0 = torch.empty_like(k1)
+    lbm.lbm_upscale_lg(p, kt, r, k0, passes=0, **kw)
+    assert torch.equal(k0, kp)
+    cs = torch.empty((2, 3, nb, nb), dtype=torch.float32, device="cuda")
+    for d in range(2):
+        pd = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, gx=1e-6 if d == 0 else 0.0, gy=1e-6 if d == 1 else 0.0)
+        lbm.lbm_coarse_run(pd, r, kp, None, 20000, 1e-7, 64, cs[d, 0], cs[d, 1], cs[d, 2])
+        cs[d, 0] -= 1.0
+    k2, st2, _, _, _, nfb2 = lbm.local_keff_lg(p, kt, r, cs, 1e-6, 1e-8, 30000, fallback=kp)
+    assert torch.equal(k1, k2) and nfb1 == nfb2
+    assert 0 < nfb1 < nb * nb
