@@ -92,7 +92,9 @@ typedef struct {
                              steady state the transverse component can still be moving when
                              the driven one has stopped). The slow diffusive start is skipped,
                              so runs stop sooner, and K* differs from the rest start only
-                             within the stop test's band. Ignored by the grid calls.      */
+                             within the stop test's band. With lbm_local_keff_lg: the
+                             inner cells start from the Darcy flow with the ring's
+                             pressures held. Ignored by the grid calls.                   */
 } lbm_params;
 
 /* Thread-local description of the last failure of any call in this thread. */
