@@ -869,6 +869,8 @@ def main(argv=None):
                     help="profiling mode: create the grid, run this many plain lattice steps, exit")
     ap.add_argument("--profile-local", type=int, default=0,
                     help="profiling mode: this many quadtree leaves of the 4096^2 field, 2000 fixed steps, exit")
+    ap.add_argument("--profile-lg", type=int, default=0,
+                    help="profiling mode: local-global upscaling of an n^2 channelised field, 2000 fixed steps, exit")
     ap.add_argument("--profile-train", type=int, default=0,
                     help="profiling mode: one surrogate training step (one model) on this many patches, exit")
     ap.add_argument("--profile-3d", type=int, default=0,
@@ -907,6 +909,8 @@ def main(argv=None):
         return run_profile(args, local)
     if args.profile_local > 0:
         return run_profile_local(args, local)
+    if args.profile_lg > 0:
+        return run_profile_lg(args, local)
     if args.profile_surrogate > 0:
         return run_profile_surrogate(args, local)
     if args.surrogate_only:
@@ -1105,6 +1109,24 @@ def run_pipeline3d(args, local):
                                          "mean_velocity": [float(c.double().mean()) for c in (uc, vc, wc)]}
         out[f"margin{m}"] = res
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_profile_lg(args, local):
+    """Fixed launch sequence for ncu: local-global upscaling (lbm_upscale_lg, one pass, margin 4,
+    Darcy start) of the 16 x 16 blocks of an n^2 channelised field, every local problem and coarse
+    run for a fixed 2000 steps. The second local_keff launch is the local-global one."""
+    import torch
+    import paper_1312_0195_gb300 as lbm
+    import synth
+    torch.cuda.set_device(local)
+    n, r = args.profile_lg, 16
+    kt = torch.from_numpy(synth.channel_kappa(n, n, seed=5)).cuda()
+    p = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, margin=4, warm_start=1)
+    keff = torch.empty((n // r, n // r, 4), dtype=torch.float64, device="cuda")
+    lbm.lbm_upscale_lg(p, kt, r, keff, passes=1, g_const=1e-6, tol_rel=0.0, max_steps=2000, coarse_max_steps=2000,
+                       coarse_tol=0.0)
+    torch.cuda.synchronize()
     return 0
 
 
