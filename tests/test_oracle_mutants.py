@@ -13,6 +13,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -189,5 +190,60 @@ def test_surrogate_oracle_pins_catch_planted_mistake(name, monkeypatch):
         try:
             t()
         except (AssertionError, ValueError, IndexError):
+            failed += 1
+    assert failed > 0, f"no pin caught the planted mistake {name}"
+
+
+# ---------------------------------------------------- the Python oracle's start states and rules
+# Each mutant rewrites one function of oracle/__init__.py (its source, one textual change),
+# compiled in the module's own namespace and swapped in for the duration of the pins named
+# beside it; at least one of those pins must fail.
+PY_MUTANTS = {
+    "lg_darcy_drive_sign": ("lg_darcy_state", [("b[pos[a]] -= kf * drive * sgn", "b[pos[a]] += kf * drive * sgn")],
+                            "local_global_darcy_start"),
+    "lg_darcy_ring_pressure_dropped": ("lg_darcy_state", [("b[pos[a]] += kf * pb[c]", "b[pos[a]] += 0.0 * pb[c]")],
+                                       "local_global_darcy_start"),
+    "lg_darcy_velocity_one_face": ("lg_darcy_state", [("ux = g_const / nu * 0.5 * (qx[y, x - 1] + qx[y, x])",
+                                                       "ux = g_const / nu * qx[y, x]")],
+                                   "mirror_symmetry"),
+    "coarse_to_fine_weights_swapped": ("coarse_to_fine", [("fx = (X - i0)[None, None, :]", "fx = (Y - j0)[None, None, :]"),
+                                                          ("fy = (Y - j0)[None, :, None]", "fy = (X - i0)[None, :, None]")],
+                                       "coarse_to_fine"),
+    "lg_select_condition_inverted": ("lg_select", [("sv[0] / sv[1] <= cond_max", "sv[0] / sv[1] >= cond_max")],
+                                     "selection_rule"),
+    "lg_select_unsymmetrised": ("lg_select", [("out[i] = [ks[0, 0], sym, sym, ks[1, 1]] if good else ref[i]",
+                                               "out[i] = k[i] if good else ref[i]")],
+                                "selection_rule"),
+    "darcy_start_velocity_one_face": ("darcy_start", [("ux = 0.5 * (qx + np.roll(qx, 1, axis=1)) * g_const / nu",
+                                                       "ux = qx * g_const / nu")],
+                                      "mirror_symmetry"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_python_oracle_pins_catch_planted_mistake(name, monkeypatch):
+    import inspect
+    import textwrap
+    import oracle
+    import test_oracle_pins as pins
+    fname, changes, expr = PY_MUTANTS[name]
+    src = textwrap.dedent(inspect.getsource(getattr(oracle, fname)))
+    for old, new in changes:
+        assert old in src, f"mutation anchor not found: {old!r}"
+        src = src.replace(old, new)
+    ns = dict(vars(oracle))
+    exec(compile(src, f"mutant_{name}", "exec"), ns)
+    monkeypatch.setattr(oracle, fname, ns[fname])
+    tests = [getattr(pins, t) for t in dir(pins) if t.startswith("test_") and expr in t]
+    assert tests, f"no pin matches {expr!r}"
+    failed = 0
+    for t in tests:
+        try:
+            if "ring" in inspect.signature(t).parameters:
+                for ring in (1, 2):
+                    t(ring)
+            else:
+                t()
+        except (AssertionError, ValueError, IndexError, np.linalg.LinAlgError):
             failed += 1
     assert failed > 0, f"no pin caught the planted mistake {name}"

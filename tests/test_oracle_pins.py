@@ -574,9 +574,10 @@ def test_coarse_to_fine_interpolation():
     np.testing.assert_array_equal(oracle.coarse_to_fine(c, r, -7, 3, 12), np.full((1, 12, 12), 0.25))
     jj, ii = np.meshgrid(np.arange(6), np.arange(7), indexing="ij")
     aff = (1.0 + 0.3 * ii - 0.7 * jj)[None]
-    out = oracle.coarse_to_fine(aff, r, 3, 3, 20)[0]          # fine cells 3..22: coarse x in [0.1, 4.1]
-    X = (3 + np.arange(20) + 0.5) / r - 0.5
-    np.testing.assert_allclose(out, 1.0 + 0.3 * X[None, :] - 0.7 * X[:, None], rtol=0, atol=1e-13)
+    out = oracle.coarse_to_fine(aff, r, 3, 6, 18)[0]          # fine x 3..20, y 6..23: inside the coarse centres
+    X = (3 + np.arange(18) + 0.5) / r - 0.5
+    Y = (6 + np.arange(18) + 0.5) / r - 0.5
+    np.testing.assert_allclose(out, 1.0 + 0.3 * X[None, :] - 0.7 * Y[:, None], rtol=0, atol=1e-13)
     rnd = np.random.default_rng(3).normal(size=(2, 6, 7))
     cen = oracle.coarse_to_fine(rnd, r, 0, 0, 30)
     np.testing.assert_allclose(cen[:, 2::r, 2::r][:, :6, :6], rnd[:, :6, :6], rtol=0, atol=1e-14)
@@ -734,3 +735,22 @@ def test_local_global_darcy_start_reproduces_closed_forms():
     np.testing.assert_allclose(d[0, 1:-1, 1:-1, 1], g / nu * q0, rtol=1e-10)
     np.testing.assert_allclose(d[0, 1:-1, 1:-1, 2], 0.0, atol=1e-10 * g / nu * q0)
     np.testing.assert_array_equal(d[:, 0], state[:, 0])             # the ring keeps its state
+
+
+def test_darcy_starts_keep_the_mirror_symmetry_of_the_patch():
+    """A uniform patch with a low-permeability 2 x 2 inclusion in its middle is symmetric under
+    the mirror x -> s - 1 - x. Under a drive along x the Darcy flow is too, and so is each cell's
+    velocity in both Darcy starts (darcy_start on the periodic patch, lg_darcy_state with a
+    uniform ring pressure), since it is the mean of the cell's two face fluxes: a one-sided face
+    flux would shift the field by half a cell and break the symmetry."""
+    s, nu, eps, g = 16, 0.1, 1.0, 1e-6
+    k = np.full((s, s), 0.01)
+    k[7:9, 7:9] = 0.001
+    f = oracle.darcy_start(k, nu, eps, g)[0]
+    ux = (f * oracle.EX).sum(-1) / f.sum(-1)                    # u (rho = 1 + 3 eps G p is not symmetric)
+    assert np.abs(ux - ux[:, ::-1]).max() <= 1e-9 * np.abs(ux).max()
+    assert np.abs(ux - ux[:, 7:8]).max() > 1e-3 * np.abs(ux).max()      # the field is not uniform
+    state = np.zeros((2, s, s, 3))
+    d = oracle.lg_darcy_state(k, state, nu, eps, g)
+    ux = d[0, 1:-1, 1:-1, 1]
+    assert np.abs(ux - ux[:, ::-1]).max() <= 1e-12 * np.abs(ux).max()
