@@ -222,8 +222,8 @@ lbm_status lbm_local_keff_batch(const lbm_params *p, const float *kappa_dev, con
  * problems); leaves are validated on the device (a bad leaf gives LBM_EINVAL
  * before the solver starts). storage selects the FP32 or FP64 solver exactly as
  * for lbm_local_keff_batch (leaves up to 45 cells in FP64). The first call on
- * each device looks up the array's device address, so make it before any stream
- * capture. Every call reads the class table and the status flags back to the
+ * each device looks up the array's device address (cudaGetSymbolAddress).
+ * Every call reads the class table and the status flags back to the
  * host and synchronises the stream before it returns. Every call reuses the same
  * array (it is cleared at the start of each call), so calls that overlap on the
  * GPU (other streams or threads) race on it and must be serialised by the

@@ -1468,8 +1468,7 @@ double local_time_limit() { return g_time_limit_s; }
 // leaves (1 MiB plus a small header); every GPU that loads this library keeps
 // it until the process exits. Its device address is looked up with
 // cudaGetSymbolAddress once per device, by the first call on that device with
-// the device current; that first call should therefore happen before any
-// stream capture. Every call also reads the class table and the status flags
+// the device current. Every call also reads the class table and the status flags
 // back to the host and synchronises the stream before it returns. All calls
 // share the array and it keeps the last call's contents, so each call clears
 // what must start at zero; calls that overlap on the GPU (different streams or
