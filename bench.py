@@ -509,6 +509,54 @@ def _calibrate_gate(sd, in_range, rel, sizes, p99_max=0.04, med_max=0.015):
     return np.array(out, dtype=np.float32)
 
 
+def measure_local_global(lbm, torch, n=4096, r=16, margin=4, steps=20000):
+    """Local-global against the paper's periodic local problems on a channelised field (the
+    regime the Conclusions name): fine run for `steps` steps, K* of every r x r block by the
+    periodic local problems and by one local-global pass (lbm_upscale_lg: steady coarse runs with
+    the periodic K*, margin 4, pressure-only ring, Darcy start, periodic fallback), coarse runs for
+    steps / r steps (the same physical time); relative L2 of the coarse velocity against the
+    block-averaged fine velocity."""
+    import synth
+    nb = n // r
+    kt = torch.from_numpy(synth.channel_kappa(n, n, seed=5)).cuda()
+    p = lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, gx=1e-6, gy=0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with lbm.Grid(p, kt) as G:
+        G.step(steps, 0.0, 0)
+        _, u, v = G.fields()
+    torch.cuda.synchronize()
+    t_fine = time.perf_counter() - t0
+    ub, vb = lbm.lbm_block_average(u, r).double(), lbm.lbm_block_average(v, r).double()
+    del u, v
+    den = float(torch.sqrt((ub ** 2 + vb ** 2).sum()))
+
+    def err(ke):
+        uc = torch.empty((nb, nb), dtype=torch.float32, device="cuda")
+        vc, rc = torch.empty_like(uc), torch.empty_like(uc)
+        lbm.lbm_coarse_run(p, r, ke, None, steps // r, 0.0, 64, rc, uc, vc)
+        return float(torch.sqrt(((uc.double() - ub) ** 2 + (vc.double() - vb) ** 2).sum())) / den
+
+    kp = torch.empty((nb, nb, 4), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_upscale(lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0), kt, r, kp, 1e-6, 1e-8, 200000)
+    torch.cuda.synchronize()
+    t_p = time.perf_counter() - t0
+    kl = torch.empty_like(kp)
+    t0 = time.perf_counter()
+    st, nfb = lbm.lbm_upscale_lg(lbm.Params(nx=n, ny=n, tau=1.0, eps=1.0, margin=margin, warm_start=1), kt, r, kl,
+                                 passes=1)
+    torch.cuda.synchronize()
+    t_lg = time.perf_counter() - t0
+    return {"workload": f"{n}^2 channelised (seed 5, K 1e-2 / 1e-6), r = {r}, tau 1, G 1e-6 along x; fine "
+                        f"{steps} steps, coarse {steps // r}; local-global: margin {margin}, pressure-only ring, "
+                        "Darcy start, one pass, periodic K* as fallback",
+            "fine_seconds": t_fine, "periodic_seconds": t_p, "local_global_seconds": t_lg,
+            "local_global_fallback_blocks": nfb, "blocks": nb * nb,
+            "coarse_rel_l2_periodic": err(kp), "coarse_rel_l2_local_global": err(kl)}
+
+
 def measure_surrogate(lbm, torch, train_fields=800, per_size=None, calib_fields=100, test_fields=100, epochs=40,
                       spread_max=0.03):
     """The learned K* surrogate against the batched local LBM on held-out leaves.
@@ -800,13 +848,15 @@ def run_ours(args, ws, rank, local):
            "steps": e2e_steps}
 
     variants = {}
-    local = surrogate = d3 = None
+    local = surrogate = d3 = lg = None
     if not args.no_extras:
         variants = measure_variants(lbm, torch, kap, stream)
         if rank == 0:
             variants["error_vs_oracle"] = measure_storage_error(lbm, torch, kap_np)
         d3 = measure_d3q19(lbm, torch, ws=ws, rank=rank)
         local = measure_local_keff(lbm, torch, kap, ws, rank)
+        if ws == 1:
+            lg = measure_local_global(lbm, torch)
         if not args.no_surrogate:
             surrogate = measure_surrogate(lbm, torch, train_fields=args.surrogate_fields,
                                           epochs=args.surrogate_epochs)
@@ -845,6 +895,8 @@ def run_ours(args, ws, rank, local):
             line["surrogate"] = surrogate
         if d3:
             line["d3q19"] = d3
+        if lg:
+            line["local_global"] = lg
         print(json.dumps(line), flush=True)
     return 0
 
